@@ -1,0 +1,297 @@
+#!/usr/bin/env python
+"""Throughput benchmark: FDTD cell-updates/s on the 4096^2 heterogeneous 2D TMz
+workload (200 seeded ellipses, eps_r ~ U[1,12], sigma ~ U[0,0.05] S/m, uint8
+material map, 16-cell CPML, Gaussian-modulated 2.4 GHz soft source, 4000 steps).
+
+One benchmark step = one complete solve: fields reset, 4000 leapfrog steps with
+the source and 4 probes.  `value` is device time with inputs resident in HBM;
+`e2e` is the same metric through the C ABI from host buffers (context creation
+with the host material map, the solve, Ez and probes copied back).
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_CU = 25.0        # 3 fields x 4 B read + 3 x 4 B written + 1 B material (single sweep)
+WORKLOAD = "tmz2d_4096x4096_ellipses200_cpml16_gaussmod2.4GHz_4000steps"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler run during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[3 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _traffic_record():
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
+    valid only while the kernel source is unchanged."""
+    p = os.path.join(ROOT, "profiles", "k_tmz_fused_traffic.json")
+    src = os.path.join(ROOT, "paper_2405_00814_gb300", "csrc", "k_tmz.cu")
+    if not os.path.exists(p):
+        return None
+    rec = json.load(open(p))
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if rec.get("source_sha256_16") != h:
+        return None
+    return rec.get("dram_bytes_per_launch_full")
+
+
+def cpu_baseline(sc, budget_s=12.0):
+    """The FP64 oracle as it stands, on the host cores, over a bounded prefix of
+    the same workload: chunks of 10 steps until the budget is used."""
+    import oracle
+    sim = oracle.TMz(sc, nsteps_src=sc.nsteps)
+    sim.run(2)
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < budget_s:
+        sim.run(10)
+        steps += 10
+    dt = time.perf_counter() - t0
+    return {"value": sc.cells * steps / dt, "unit": "cell-updates/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"{steps} leapfrog steps of the full {sc.nx}x{sc.ny} scene (FP64, OpenMP over rows)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2405_00814_gb300 import scenes
+    import oracle
+    oracle.lib()
+    sc = scenes.ellipse_scene()
+    sim = oracle.TMz(sc, nsteps_src=sc.nsteps)
+    per = args.ref_sample
+    for _ in range(args.warmup):
+        sim.run(per)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.run(per)
+    dt = time.perf_counter() - t0
+    val = sc.cells * per * args.steps / dt
+    cores = oracle.num_threads()
+    line = {"metric": "FDTD cell-updates/s", "value": val, "unit": "cell-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample_steps_per_bench_step": per},
+            "cpu_baseline": {"value": val, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per} leapfrog steps of the full scene per bench step"},
+            "e2e": {"value": val, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gem", choices=["gem", "reference"])
+    ap.add_argument("--tblock", type=int, default=None)
+    ap.add_argument("--segment", type=int, default=None)
+    ap.add_argument("--warps", type=int, default=None)
+    ap.add_argument("--kernel", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--ref-sample", type=int, default=20)
+    ap.add_argument("--nsteps", type=int, default=None, help="leapfrog steps per solve (default: the workload's 4000)")
+    ap.add_argument("--size", type=int, default=4096, help="grid side (profiling runs use smaller sides)")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2405_00814_gb300 import fdtd, scenes
+
+    sc = scenes.ellipse_scene(side=args.size)
+    nsteps = args.nsteps or sc.nsteps
+    stream = torch.cuda.current_stream()
+    sim = fdtd.from_scene(sc, stream=stream)
+    tune = {"tblock": 4, "segment": 128, "warps": 2}
+    for k in ("tblock", "segment", "warps"):
+        if getattr(args, k) is not None:
+            tune[k] = getattr(args, k)
+    sim.set_option("kernel", args.kernel)
+    for k, v in tune.items():
+        sim.set_option(k, v)
+
+    def solve():
+        sim.reset()
+        sim.step(nsteps)
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = sim.launch_count
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 2)]
+    ev[0].record(stream)
+    for k in range(args.steps):
+        sim.reset()
+        ev[1 + 2 * k].record(stream)
+        sim.step(nsteps)
+        ev[2 + 2 * k].record(stream)
+    ev[-1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = sim.launch_count - l0
+    ms_total = ev[0].elapsed_time(ev[-1])
+    ms_step_only = sum(ev[1 + 2 * k].elapsed_time(ev[2 + 2 * k]) for k in range(args.steps))
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_per = ms_total / args.steps
+    cell_updates = sc.cells * nsteps
+    value = cell_updates * args.steps * world / (ms_total / 1e3)
+
+    # dominant kernel: the fused stream, one launch per tblock steps
+    T = tune["tblock"] if args.kernel == 0 else 1
+    fused_launches = args.steps * math.ceil(nsteps / T)
+    avg_launch_s = (ms_step_only / 1e3) / fused_launches
+    peak, peak_kind = _peaks()
+    alg_bytes = BYTES_PER_CU * sc.cells            # bytes one launch must move (state in + out, material)
+    achieved = alg_bytes / avg_launch_s / 1e9
+    traffic = _traffic_record()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": f"k_tmz_fused<{T}>" if args.kernel == 0 else "k_tmz_h + k_tmz_e",
+                "unit_bytes": "25 B per grid cell per launch (each launch advances every cell T steps)"}
+    hbm_frac_cu = value / world * BYTES_PER_CU / (peak * 1e9)
+
+    workload = WORKLOAD if (args.size == 4096 and nsteps == 4000) else f"tmz2d_{args.size}_ellipses_cpml16_{nsteps}steps"
+    out = {"metric": "FDTD cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": workload, "cells": sc.cells, "leapfrog_steps_per_bench_step": nsteps,
+                      "tblock": T, "segment": tune["segment"], "warps_per_cta": tune["warps"],
+                      "l2": "inputs larger than L2 (fields 2x3x70 MB + material 17 MB)",
+                      "parallelism": "replicas" if world > 1 else "single"},
+           "roofline": roofline,
+           "hbm_roofline_frac_at_25B_per_cell_update": hbm_frac_cu,
+           "gpu_launches": launches, "clocks": clk}
+
+    # end to end through the C ABI from host buffers
+    if not args.no_e2e:
+        import numpy as np
+        sim.close()
+        torch.cuda.synchronize()
+        e2e_steps = max(1, min(args.steps, 3))
+        h2d = sc.mat.nbytes + 24 * len(sc.eps_r)
+        d2h = sc.cells * 4 + 4 * nsteps * len(sc.probes)
+        host_ez = np.empty((sc.ny, sc.nx), np.float32)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            s2 = fdtd.from_scene(sc, stream=stream)
+            for k, v in tune.items():
+                s2.set_option(k, v)
+            s2.step(nsteps)
+            s2.get_field("ez", out=host_ez)
+            for p in s2.probe_ids:
+                s2.read_probe(p, nsteps)
+            s2.close()
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        out["e2e"] = {"value": cell_updates * e2e_steps * world / e2e_s, "unit": "cell-updates/s",
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(sc, args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * gem_fdtd.h -- C ABI of the GB300 (sm_103a) FDTD library.
+ *
+ * The library advances Maxwell's curl equations on a Yee grid with the leapfrog
+ * scheme of "Solving Maxwell's Equations with Non-Trainable Graph Neural Network
+ * Message Passing" (arXiv 2405.00814):
+ *   layer 1 (H from curl E), eqs. (8)(9), Prop. 2 first message-passing step;
+ *   layer 2 (E from curl H), eq. (7),      Prop. 2 second step,
+ * with per-cell update coefficients Ca = A_-/A_+, Cb = dt/(A_+ eps),
+ * A_-/+ = 1 -/+ sigma dt/(2 eps) (Sec. II-B, eq. (7)); Da = 1 and Db = dt/(mu0 d)
+ * because the medium is non-magnetic outside the absorber (Sec. II-A).
+ *
+ * 2D runs are TMz (Ez, Hx, Hy): the paper's TE formulation (Ey, Hx, Hz in the
+ * x-z plane, eqs. (3)-(5)) under the rotation x'=x, y'=z, z'=-y.  3D runs use
+ * the six-component Yee cell the paper says follows directly (Sec. II-B).
+ *
+ * Grid conventions.  Cell (i, j[, k]) owns Ez(i, j) at (i dx, j dy), Hx(i, j) at
+ * (i, j+1/2), Hy(i, j) at (i+1/2, j) (3D: Ex (i+1/2, j, k), Ey (i, j+1/2, k),
+ * Ez (i, j, k+1/2), Hx (i, j+1/2, k+1/2), Hy (i+1/2, j, k+1/2), Hz (i+1/2, j+1/2, k)).
+ * Host arrays are row-major with x fastest: [ny][nx] or [nz][ny][nx].
+ * PEC walls sit at index 0 (stored zeros) and at index N (ghost zeros).
+ * The absorber is a convolutional PML (Roden & Gedney) backed by that PEC; the
+ * paper's own absorber is Berenger's split field (Sec. II-C, eqs. (10)-(13)).
+ *
+ * Ownership.  The library copies every input at call time and keeps no caller
+ * pointer.  It owns all device memory of a context.  Output buffers are
+ * allocated by the caller.  A context is not thread-safe; all of its work is
+ * ordered on the CUDA stream given at creation (NULL = the legacy default
+ * stream).  fdtd_step* only enqueue work; the fdtd_read_* and fdtd_get_* calls
+ * synchronise the stream before they return.
+ *
+ * Errors.  Every int-returning call returns FDTD_OK (0) or a negative code;
+ * fdtd_last_error() then returns a message owned by the context (valid until
+ * the next call on it).  A call that fails leaves the simulation state as it
+ * was, except FDTD_ECUDA, after which the context should be destroyed.
+ */
+#ifndef GEM_FDTD_H
+#define GEM_FDTD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FDTD_OK 0
+#define FDTD_EINVAL (-1)    /* bad argument (out-of-range index, size, kind...) */
+#define FDTD_ENOMEM (-2)    /* device or host allocation failed */
+#define FDTD_ECUDA (-3)     /* a CUDA call failed */
+#define FDTD_EUNSTABLE (-4) /* dt above the Courant limit, or non-finite fields found */
+#define FDTD_ETIMEOUT (-5)  /* a bounded device-side wait gave up */
+#define FDTD_ESTATE (-6)    /* call not valid in the context's current state */
+
+#define FDTD_PEC 0          /* plain PEC box */
+#define FDTD_CPML 1         /* CPML of pml_cells cells on every face, backed by PEC */
+
+/* field components */
+#define FDTD_EX 0
+#define FDTD_EY 1
+#define FDTD_EZ 2
+#define FDTD_HX 3
+#define FDTD_HY 4
+#define FDTD_HZ 5
+
+/* source kinds (waveforms s(t) sampled at t = (n+1) dt after step n) */
+#define FDTD_SRC_RICKER 0    /* params[0] = f_peak: (1-2a) e^{-a}, a = (pi f (t - 1.5/f))^2 */
+#define FDTD_SRC_GAUSS_MOD 1 /* params[0] = f0: e^{-((t-t0)/tg)^2} sin(2 pi f0 (t-t0)), tg = 1/f0, t0 = 4 tg */
+#define FDTD_SRC_GAUSS 2     /* params[0] = f_max: e^{-((t-t0)/tg)^2}, tg = 1/f_max, t0 = 4 tg */
+#define FDTD_SRC_SAMPLED 3   /* samples[n] = s((n+1) dt), n < n_samples; 0 after */
+
+/* options (fdtd_set_option) */
+#define FDTD_OPT_KERNEL 0    /* 0 = fused temporally blocked stream (default), 1 = one H and one E launch per step */
+#define FDTD_OPT_TBLOCK 1    /* time steps per HBM pass of the fused kernel, 1..4 */
+#define FDTD_OPT_SEGMENT 2   /* rows per warp task of the fused kernel (multiple of 8, >= 8) */
+#define FDTD_OPT_WARPS 3     /* warps per CTA of the fused kernel, 1..8 */
+
+typedef struct fdtd_ctx fdtd_ctx;
+
+typedef struct {
+    int dims;       /* 2 (TMz) or 3 */
+    int nx, ny, nz; /* cells per axis (nz ignored for dims == 2); each >= 4 */
+    int pml_cells;  /* CPML depth in cells when boundary == FDTD_CPML */
+    int boundary;   /* FDTD_PEC or FDTD_CPML */
+    double dy, dz;  /* cell sizes in m for y and z; <= 0 means "same as dx" */
+} fdtd_grid;
+
+typedef struct {
+    double eps_r; /* relative permittivity, > 0 */
+    double mu_r;  /* must be 1: the method assumes a non-magnetic medium (Sec. II-A) */
+    double sigma; /* electric conductivity, S/m, >= 0 */
+} fdtd_material;
+
+/* Create a context for one scene (Sec. II-B: grid, dx, dt, material map).
+ * dx: cell size in m (> 0).  dt: time step in s; if dt <= 0 the step is
+ * courant * (Courant limit), courant in (0, 1].  A dt above the limit returns
+ * FDTD_EUNSTABLE.  mat_idx: host uint8 map [ny][nx] (2D) or [nz][ny][nx] (3D) of
+ * indices into table[0..n_mat-1]; 1 <= n_mat <= 255 (index 255 is reserved).
+ * cuda_stream: a cudaStream_t or NULL.  *out receives the context. */
+int fdtd_create(const fdtd_grid* grid, double dx, double dt, double courant, const uint8_t* mat_idx,
+                const fdtd_material* table, int n_mat, void* cuda_stream, fdtd_ctx** out);
+
+/* Create one context holding n_scenes independent 2D scenes of possibly
+ * different sizes (the paper's many-simulation workloads, Sec. V-A); arrays
+ * have one entry per scene.  fdtd_step advances every scene; per-scene calls act
+ * on the scene chosen with fdtd_select_scene (scene 0 initially). */
+int fdtd_create_batch(int n_scenes, const fdtd_grid* grids, const double* dx, const double* dt,
+                      const uint8_t* const* mat_idx, const fdtd_material* const* tables,
+                      const int* n_mat, void* cuda_stream, fdtd_ctx** out);
+int fdtd_select_scene(fdtd_ctx* ctx, int scene);
+int fdtd_num_scenes(const fdtd_ctx* ctx);
+
+void fdtd_destroy(fdtd_ctx* ctx);
+const char* fdtd_last_error(const fdtd_ctx* ctx);
+int fdtd_set_option(fdtd_ctx* ctx, int option, int64_t value);
+int64_t fdtd_get_option(const fdtd_ctx* ctx, int option);
+
+/* Soft (additive) point source of the selected scene: after the E update of
+ * step n the component at (i, j[, k]) gets s((n+1) dt) added (Sec. V-A: sources
+ * at random positions; Sec. V-B: point sources).  2D accepts FDTD_EZ only, at
+ * 1 <= i < nx, 1 <= j < ny.  params: one double per kind (see FDTD_SRC_*);
+ * samples/n_samples for FDTD_SRC_SAMPLED (copied).  Replaces any earlier source. */
+int fdtd_set_source(fdtd_ctx* ctx, int kind, int i, int j, int k, int component, const double* params,
+                    const float* samples, int64_t n_samples);
+
+/* Probe: records the component at (i, j[, k]) after every following step
+ * (after the source) -- the waveforms of Fig. 2d.  *probe_id gets its index.
+ * Probes must be added before the first step after a reset. */
+int fdtd_add_probe(fdtd_ctx* ctx, int i, int j, int k, int component, int* probe_id);
+
+/* Running DFT of Ez at cells: F(f) = sum_{n>=1} Ez^n exp(-i 2 pi f n dt) dt over
+ * all steps taken after the monitor was added (frequency-domain responses via a
+ * Fourier transform of sampled waveforms, Sec. I).  cells: n_cells (i, j) pairs
+ * (2D) or (i, j, k) triples (3D).  Accumulated in compensated (Kahan) FP32. */
+int fdtd_add_dft_monitor(fdtd_ctx* ctx, const int32_t* cells, int n_cells, const double* freqs_hz,
+                         int n_freq, int* mon_id);
+
+/* 3D only: running DFT of the E components in comp_mask (bit c = FDTD_EX+c) over
+ * the whole plane z = k (cell index k), same convention as above. */
+int fdtd_add_dft_plane(fdtd_ctx* ctx, int k, int comp_mask, const double* freqs_hz, int n_freq,
+                       int* mon_id);
+
+/* Advance every scene n_steps leapfrog steps with the implicit-stencil kernels
+ * (layers 1 and 2 fused, temporally blocked; FDTD_OPT_KERNEL selects the
+ * unfused pair).  Asynchronous. */
+int fdtd_step(fdtd_ctx* ctx, int64_t n_steps);
+
+/* Same recurrence computed literally as the paper's two message-passing layers
+ * over an explicit edge list (Prop. 1 numbering, Prop. 2 layers): per step one
+ * sparse gather per layer, h_l = sum_{l_n in N(v_l)} w_{l,l_n} h_{l_n}.  2D only. */
+int fdtd_step_edgelist(fdtd_ctx* ctx, int64_t n_steps);
+
+/* Export layer 1 or 2 of that graph (selected scene): *n_nodes and *n_edges are
+ * always written; src/dst/w (n_edges entries each, caller-allocated, host) are
+ * filled when non-NULL.  Edges are grouped by destination; rows of nodes the
+ * layer does not update carry one self edge of weight 1.  Node numbering:
+ * Prop. 1 with k -> j (u = i + 3 j nx for Hx, q = 2 i + nx(3 j + 1) for Hy,
+ * t = 2 i + 1 + nx(3 j + 1) for Ez), then CPML auxiliary nodes. */
+int fdtd_export_graph(fdtd_ctx* ctx, int layer, int64_t* n_nodes, int64_t* n_edges, int32_t* src,
+                      int32_t* dst, float* w);
+
+/* Copy out n values of a probe (n <= steps recorded).  Synchronises. */
+int fdtd_read_probe(fdtd_ctx* ctx, int probe_id, float* out, int64_t n);
+
+/* Copy out a DFT monitor: re/im [n_cells][n_freq] (cell monitor) or
+ * [n_comp][n_freq][ny][nx] (plane monitor).  Synchronises. */
+int fdtd_read_dft(fdtd_ctx* ctx, int mon_id, float* re, float* im);
+
+/* Copy a field component of the selected scene to out ([ny][nx] or [nz][ny][nx]
+ * floats); on_device != 0 means out is a device pointer.  Synchronises. */
+int fdtd_get_field(fdtd_ctx* ctx, int component, float* out, int on_device);
+/* Overwrite a field component from in (same layout). */
+int fdtd_set_field(fdtd_ctx* ctx, int component, const float* in, int on_device);
+
+/* Zero every field, auxiliary, probe record and DFT accumulator; time -> 0. */
+int fdtd_reset(fdtd_ctx* ctx);
+/* Steps taken since creation or the last reset. */
+int64_t fdtd_time_step(const fdtd_ctx* ctx);
+/* Kernel launches issued by this context so far (all kinds). */
+int64_t fdtd_launch_count(const fdtd_ctx* ctx);
+
+/* Checkpoint: the full state (fields, CPML auxiliaries, DFT accumulators, time)
+ * of every scene.  buf == NULL: *bytes receives the size needed.  Otherwise
+ * *bytes is the buffer's size on input and the bytes written on output; the
+ * buffer is host memory.  fdtd_load_state restores a buffer from the same
+ * context configuration. */
+int fdtd_save_state(fdtd_ctx* ctx, void* buf, size_t* bytes);
+int fdtd_load_state(fdtd_ctx* ctx, const void* buf, size_t bytes);
+
+/* Returns FDTD_EUNSTABLE if any field of any scene is not finite. Synchronises. */
+int fdtd_check_finite(fdtd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GEM_FDTD_H */

@@ -1,0 +1,818 @@
+// Host side of the C ABI (include/gem_fdtd.h): contexts, inputs, coefficient
+// tables, monitors and the step loop.  All arithmetic of the time step runs in
+// the kernels; the host computes the per-material coefficients of eq. (7) and
+// the CPML profiles once, in FP64, and rounds them to FP32.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "gem_internal.h"
+
+using namespace gem;
+
+namespace {
+
+const double kC0 = 299792458.0;
+const double kMu0 = 4.0e-7 * M_PI;
+const double kEps0 = 1.0 / (kMu0 * kC0 * kC0);
+// CPML grading (Roden & Gedney): polynomial order, alpha at the inner interface
+const double kPmlM = 3.0;
+const double kPmlAlphaMax = 0.05;
+
+int fail(fdtd_ctx* c, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+int cuda_fail(fdtd_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, FDTD_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                 \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+template <class P>
+int dalloc(fdtd_ctx* c, P** p, size_t bytes, const char* what) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(c, FDTD_ENOMEM, "cudaMalloc %zu bytes for %s: %s", bytes, what, cudaGetErrorString(e));
+    }
+    return FDTD_OK;
+}
+
+void dfree(void* p) {
+    if (p) cudaFree(p);
+}
+
+double courant_limit_2d(double dx, double dy) { return 1.0 / (kC0 * sqrt(1.0 / (dx * dx) + 1.0 / (dy * dy))); }
+
+// one CPML point: depth rho (cells) from the inner interface of an npml-cell layer
+void cpml_point(double rho, int npml, double delta, double dt, double* b, double* c) {
+    if (rho <= 0.0 || npml <= 0) {
+        *b = 0.0;
+        *c = 0.0;
+        return;
+    }
+    const double eta0 = sqrt(kMu0 / kEps0);
+    const double smax = 0.8 * (kPmlM + 1.0) / (eta0 * delta);
+    const double x = rho / npml;
+    const double sig = smax * pow(x, kPmlM);
+    const double alp = kPmlAlphaMax * (1.0 - x);
+    const double bb = exp(-(sig + alp) * dt / kEps0);   // kappa = 1
+    *b = bb;
+    *c = sig * (bb - 1.0) / (sig + alp);
+}
+
+// profile arrays of one axis in storage coordinates: E nodes at integer
+// positions, H nodes at +1/2; n cells, pad cells before index 0
+void cpml_axis(int n, int npml, double delta, double dt, int pad, int len, float* bE, float* cE, float* bH,
+               float* cH) {
+    for (int k = 0; k < len; k++) bE[k] = cE[k] = bH[k] = cH[k] = 0.f;
+    if (npml <= 0) return;
+    for (int i = 0; i < n; i++) {
+        const double xe = i, xh = i + 0.5, lo = npml, hi = n - npml;
+        double rE = 0, rH = 0;
+        if (xe < lo) rE = lo - xe;
+        if (xe > hi) rE = xe - hi;
+        if (xh < lo) rH = lo - xh;
+        if (xh > hi) rH = xh - hi;
+        double b, c;
+        cpml_point(rE, npml, delta, dt, &b, &c);
+        bE[i + pad] = (float)b;
+        cE[i + pad] = (float)c;
+        cpml_point(rH, npml, delta, dt, &b, &c);
+        bH[i + pad] = (float)b;
+        cH[i + pad] = (float)c;
+    }
+}
+
+// eq. (7): Ca = A_-/A_+, Cb = dt/(A_+ eps), A_-/+ = 1 -/+ sigma dt/(2 eps)
+float4 e_coeffs(double eps_r, double sigma, double dt, double dx, double dy) {
+    const double eps = kEps0 * eps_r;
+    const double am = 1.0 - sigma * dt / (2.0 * eps);
+    const double ap = 1.0 + sigma * dt / (2.0 * eps);
+    const double ca = am / ap, cb = dt / (ap * eps);
+    return make_float4((float)ca, (float)(cb / dx), (float)(cb / dy), (float)cb);
+}
+
+double waveform(int kind, double p, double t) {
+    if (kind == FDTD_SRC_RICKER) {
+        const double tau = t - 1.5 / p;
+        const double a = M_PI * M_PI * p * p * tau * tau;
+        return (1.0 - 2.0 * a) * exp(-a);
+    }
+    const double tg = 1.0 / p, t0 = 4.0 * tg, u = (t - t0) / tg;
+    if (kind == FDTD_SRC_GAUSS_MOD) return exp(-u * u) * sin(2.0 * M_PI * p * (t - t0));
+    if (kind == FDTD_SRC_GAUSS) return exp(-u * u);
+    return 0.0;
+}
+
+Scene2* cur2(fdtd_ctx* c) { return (c->dims == 2 && !c->s2.empty()) ? c->s2[c->cur] : nullptr; }
+
+void scene2_free(Scene2* s) {
+    if (!s) return;
+    for (int f = 0; f < F_COUNT2; f++)
+        for (int p = 0; p < 2; p++) dfree(s->fbuf[f][p]);
+    dfree(s->d_mat);
+    dfree(s->d_coef);
+    dfree(s->d_prof);
+    dfree(s->d_src);
+    dfree(s->d_rec);
+    dfree(s->d_dsg);
+    delete s;
+}
+
+int scene2_init(fdtd_ctx* c, const fdtd_grid* g, double dx, double dt, double courant, const uint8_t* mat,
+                const fdtd_material* table, int n_mat, Scene2** out) {
+    *out = nullptr;
+    if (!g || !mat || !table) return fail(c, FDTD_EINVAL, "NULL grid, material map or table");
+    if (g->dims != 2) return fail(c, FDTD_EINVAL, "scene dims %d: this entry handles 2D", g->dims);
+    if (g->nx < 4 || g->ny < 4) return fail(c, FDTD_EINVAL, "grid %dx%d too small (>= 4 cells per axis)", g->nx, g->ny);
+    if ((int64_t)g->nx * g->ny > (int64_t)1 << 31) return fail(c, FDTD_EINVAL, "grid too large");
+    if (!(dx > 0)) return fail(c, FDTD_EINVAL, "dx must be > 0");
+    const double dy = g->dy > 0 ? g->dy : dx;
+    int npml = 0;
+    if (g->boundary == FDTD_CPML) {
+        npml = g->pml_cells;
+        if (npml < 1 || 2 * npml + 2 > std::min(g->nx, g->ny))
+            return fail(c, FDTD_EINVAL, "pml_cells %d does not fit a %dx%d grid", npml, g->nx, g->ny);
+    } else if (g->boundary != FDTD_PEC) {
+        return fail(c, FDTD_EINVAL, "unknown boundary %d", g->boundary);
+    }
+    const double lim = courant_limit_2d(dx, dy);
+    if (dt <= 0) {
+        if (!(courant > 0 && courant <= 1.0)) return fail(c, FDTD_EINVAL, "courant factor must be in (0, 1]");
+        dt = courant * lim;
+    } else if (dt > lim) {
+        return fail(c, FDTD_EUNSTABLE, "dt %.6g s exceeds the 2D Courant limit %.6g s", dt, lim);
+    }
+    if (n_mat < 1 || n_mat > 255) return fail(c, FDTD_EINVAL, "n_mat %d outside 1..255", n_mat);
+    for (int m = 0; m < n_mat; m++) {
+        if (!(table[m].eps_r > 0)) return fail(c, FDTD_EINVAL, "material %d: eps_r must be > 0", m);
+        if (table[m].mu_r != 1.0) return fail(c, FDTD_EINVAL, "material %d: mu_r must be 1 (non-magnetic medium)", m);
+        if (!(table[m].sigma >= 0)) return fail(c, FDTD_EINVAL, "material %d: sigma must be >= 0", m);
+    }
+    const int64_t ncell = (int64_t)g->nx * g->ny;
+    for (int64_t k = 0; k < ncell; k++)
+        if (mat[k] >= n_mat) return fail(c, FDTD_EINVAL, "material index %d at cell %lld >= n_mat %d", mat[k], (long long)k, n_mat);
+
+    Scene2* s = new Scene2();
+    memset((void*)s->fbuf, 0, sizeof(s->fbuf));
+    s->d_mat = nullptr; s->d_coef = nullptr; s->d_prof = nullptr; s->d_src = nullptr; s->d_rec = nullptr;
+    s->d_dsg = nullptr;
+    s->nx = g->nx; s->ny = g->ny; s->npml = npml;
+    s->dx = dx; s->dy = dy; s->dt = dt;
+    s->pitch = ((PAD_X + g->nx + STRIP) + 31) / 32 * 32;
+    s->rows = g->ny + 2 * PAD_Y;
+    s->mat_host.assign(mat, mat + ncell);
+    s->eps_r.resize(n_mat);
+    s->sigma.resize(n_mat);
+    for (int m = 0; m < n_mat; m++) {
+        s->eps_r[m] = table[m].eps_r;
+        s->sigma[m] = table[m].sigma;
+    }
+    s->src_kind = -1; s->src_i = -1; s->src_j = -1; s->src_param = 0; s->src_cap = 0;
+    s->rec_cap = 0;
+    s->dsg_i0 = s->dsg_j0 = s->dsg_w = s->dsg_h = 0;
+
+    const size_t fbytes = (size_t)s->pitch * s->rows * sizeof(float);
+    for (int f = 0; f < F_COUNT2; f++)
+        for (int p = 0; p < 2; p++) {
+            int rc = dalloc(c, &s->fbuf[f][p], fbytes, "field");
+            if (rc) { scene2_free(s); return rc; }
+            cudaMemsetAsync(s->fbuf[f][p], 0, fbytes, c->stream);
+        }
+    // padded material map: pads and the PEC walls i = 0, j = 0 get PEC_MAT
+    std::vector<uint8_t> pm((size_t)s->pitch * s->rows, (uint8_t)PEC_MAT);
+    for (int j = 0; j < s->ny; j++)
+        for (int i = 0; i < s->nx; i++)
+            pm[(size_t)(j + PAD_Y) * s->pitch + i + PAD_X] =
+                (i == 0 || j == 0) ? (uint8_t)PEC_MAT : mat[(size_t)j * s->nx + i];
+    int rc = dalloc(c, &s->d_mat, pm.size(), "material map");
+    if (rc) { scene2_free(s); return rc; }
+    // coefficient table
+    std::vector<float4> co(256, make_float4(0, 0, 0, 0));
+    for (int m = 0; m < n_mat; m++) co[m] = e_coeffs(table[m].eps_r, table[m].sigma, dt, dx, dy);
+    rc = dalloc(c, &s->d_coef, 256 * sizeof(float4), "coefficients");
+    if (rc) { scene2_free(s); return rc; }
+    // CPML profiles
+    std::vector<float> prof(4 * (size_t)s->pitch + 4 * (size_t)s->rows, 0.f);
+    float* px = prof.data();
+    float* py = prof.data() + 4 * s->pitch;
+    cpml_axis(s->nx, npml, dx, dt, PAD_X, s->pitch, px, px + s->pitch, px + 2 * s->pitch, px + 3 * s->pitch);
+    cpml_axis(s->ny, npml, dy, dt, PAD_Y, s->rows, py, py + s->rows, py + 2 * s->rows, py + 3 * s->rows);
+    rc = dalloc(c, &s->d_prof, prof.size() * sizeof(float), "profiles");
+    if (rc) { scene2_free(s); return rc; }
+    cudaError_t e = cudaMemcpyAsync(s->d_mat, pm.data(), pm.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_coef, co.data(), 256 * sizeof(float4), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_prof, prof.data(), prof.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) { scene2_free(s); return cuda_fail(c, e, "upload scene"); }
+    *out = s;
+    return FDTD_OK;
+}
+
+fdtd_ctx* ctx_new(void* stream) {
+    fdtd_ctx* c = new fdtd_ctx();
+    c->dims = 2;
+    c->stream = (cudaStream_t)stream;
+    c->s3 = nullptr;
+    c->cur = 0;
+    c->t = 0;
+    c->parity = 0;
+    c->launches = 0;
+    c->opt_kernel = 0;
+    c->opt_tblock = 4;
+    c->opt_segment = 128;
+    c->opt_warps = 2;
+    c->dirty = true;
+    c->d_scenes = nullptr;
+    c->d_tasks = nullptr;
+    c->d_samp = nullptr;
+    c->d_samp_scene = nullptr;
+    c->d_samp_off = nullptr;
+    c->n_tasks = 0;
+    c->task_tb = c->task_seg = -1;
+    c->graph = nullptr;
+    return c;
+}
+
+// source waveform and sample record must cover steps [0, t_end)
+int ensure_capacity(fdtd_ctx* c, int64_t t_end) {
+    for (Scene2* s : c->s2) {
+        if (s->src_kind >= 0 && s->src_cap < t_end) {
+            int64_t cap = std::max<int64_t>(t_end, 2 * s->src_cap);
+            cap = std::max<int64_t>(cap, 1024);
+            std::vector<float> w((size_t)cap, 0.f);
+            for (int64_t n = 0; n < cap; n++) {
+                if (s->src_kind == FDTD_SRC_SAMPLED)
+                    w[n] = n < (int64_t)s->src_samples.size() ? s->src_samples[n] : 0.f;
+                else
+                    w[n] = (float)waveform(s->src_kind, s->src_param, (double)(n + 1) * s->dt);
+            }
+            float* d = nullptr;
+            int rc = dalloc(c, &d, (size_t)cap * sizeof(float), "source waveform");
+            if (rc) return rc;
+            CK(cudaMemcpyAsync(d, w.data(), (size_t)cap * sizeof(float), cudaMemcpyHostToDevice, c->stream), "upload waveform");
+            CK(cudaStreamSynchronize(c->stream), "upload waveform");
+            dfree(s->d_src);
+            s->d_src = d;
+            s->src_cap = cap;
+            c->dirty = true;
+        }
+        const int nrec = (int)s->samples.size();
+        if (nrec > 0 && s->rec_cap < t_end) {
+            int64_t cap = std::max<int64_t>(t_end, 2 * s->rec_cap);
+            cap = std::max<int64_t>(cap, 1024);
+            float* d = nullptr;
+            const size_t bytes = (size_t)cap * nrec * sizeof(float);
+            int rc = dalloc(c, &d, bytes, "sample record");
+            if (rc) return rc;
+            CK(cudaMemsetAsync(d, 0, bytes, c->stream), "record memset");
+            if (s->d_rec && s->rec_cap > 0)
+                CK(cudaMemcpyAsync(d, s->d_rec, (size_t)s->rec_cap * nrec * sizeof(float), cudaMemcpyDeviceToDevice,
+                                   c->stream), "record copy");
+            CK(cudaStreamSynchronize(c->stream), "record grow");
+            dfree(s->d_rec);
+            s->d_rec = d;
+            s->rec_cap = cap;
+            c->dirty = true;
+        }
+    }
+    return FDTD_OK;
+}
+
+// device scene descriptors, fused-kernel task list and sample lists
+int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
+    const int ns = (int)c->s2.size();
+    std::vector<TmzDev> dev(ns);
+    for (int k = 0; k < ns; k++) {
+        Scene2* s = c->s2[k];
+        TmzDev& d = dev[k];
+        memset(&d, 0, sizeof(d));
+        for (int f = 0; f < F_COUNT2; f++)
+            for (int p = 0; p < 2; p++) d.f[f][p] = s->fbuf[f][p];
+        d.mat = s->d_mat;
+        d.coef = s->d_coef;
+        d.prof = s->d_prof;
+        d.nx = s->nx; d.ny = s->ny; d.pitch = s->pitch; d.rows = s->rows;
+        d.has_pml = s->npml;
+        d.dbx = (float)(s->dt / (kMu0 * s->dx));
+        d.dby = (float)(s->dt / (kMu0 * s->dy));
+        d.src_i = s->src_kind >= 0 ? s->src_i : -1;
+        d.src_j = s->src_kind >= 0 ? s->src_j : -1;
+        d.src_wave = s->d_src;
+        d.src_len = s->src_kind >= 0 ? s->src_cap : 0;
+        d.rec = s->d_rec;
+        d.n_rec = (int)s->samples.size();
+        d.rec_cap = s->rec_cap;
+        d.dsg_i0 = s->dsg_i0; d.dsg_j0 = s->dsg_j0; d.dsg_w = s->d_dsg ? s->dsg_w : 0; d.dsg_h = s->dsg_h;
+        d.dsg_coef = s->d_dsg;
+    }
+    // tasks: per scene, strips of 120 columns x segments of seg rows, padded to
+    // a whole number of CTAs so that a CTA never mixes scenes
+    const int wout = STRIP - 2 * HALO;
+    std::vector<Task> tasks;
+    std::vector<Sample2> tsamp;
+    for (int k = 0; k < ns; k++) {
+        Scene2* s = c->s2[k];
+        const size_t first = tasks.size();
+        for (int ya = 0; ya < s->ny; ya += seg) {
+            const int yb = std::min(ya + seg, s->ny);
+            for (int x0 = 0; x0 < s->nx; x0 += wout) {
+                Task t;
+                t.scene = k; t.x0 = x0; t.ya = ya; t.yb = yb; t.flags = 0; t.pad = 0;
+                const int lx0 = x0 - HALO, lx1 = x0 - HALO + STRIP;   // loaded columns
+                const int ly0 = ya - MAX_TB, ly1 = yb + MAX_TB;        // widest streamed rows
+                if (s->npml > 0) {
+                    const bool xs = lx0 < s->npml || lx1 > s->nx - s->npml;
+                    const bool ys = ly0 < s->npml || ly1 > s->ny - s->npml;
+                    if (xs || ys) t.flags |= TASK_PML;
+                }
+                if (s->src_kind >= 0 && s->src_i >= lx0 && s->src_i < lx1 && s->src_j >= ly0 && s->src_j < ly1)
+                    t.flags |= TASK_SRC;
+                if (s->d_dsg && s->dsg_i0 < lx1 && s->dsg_i0 + s->dsg_w > lx0 && s->dsg_j0 < ly1 &&
+                    s->dsg_j0 + s->dsg_h > ly0)
+                    t.flags |= TASK_DSG;
+                t.samp_begin = (int)tsamp.size();
+                for (const Sample2& sp : s->samples)
+                    if (sp.i >= x0 && sp.i < x0 + wout && sp.j >= ya && sp.j < yb) tsamp.push_back(sp);
+                t.samp_end = (int)tsamp.size();
+                tasks.push_back(t);
+            }
+        }
+        while ((tasks.size() - first) % warps) {
+            Task t;
+            memset(&t, 0, sizeof(t));
+            t.scene = -1;
+            tasks.push_back(t);
+        }
+    }
+    std::vector<Sample2> ssamp;
+    std::vector<int> soff(ns + 1, 0);
+    for (int k = 0; k < ns; k++) {
+        for (const Sample2& sp : c->s2[k]->samples) ssamp.push_back(sp);
+        soff[k + 1] = (int)ssamp.size();
+    }
+    dfree(c->d_scenes); dfree(c->d_tasks); dfree(c->d_samp); dfree(c->d_samp_scene); dfree(c->d_samp_off);
+    c->d_scenes = nullptr; c->d_tasks = nullptr; c->d_samp = nullptr; c->d_samp_scene = nullptr; c->d_samp_off = nullptr;
+    int rc;
+    if ((rc = dalloc(c, &c->d_scenes, dev.size() * sizeof(TmzDev), "scene descriptors"))) return rc;
+    if ((rc = dalloc(c, &c->d_tasks, tasks.size() * sizeof(Task), "tasks"))) return rc;
+    if ((rc = dalloc(c, &c->d_samp, tsamp.size() * sizeof(Sample2), "samples"))) return rc;
+    if ((rc = dalloc(c, &c->d_samp_scene, ssamp.size() * sizeof(Sample2), "samples"))) return rc;
+    if ((rc = dalloc(c, &c->d_samp_off, soff.size() * sizeof(int), "sample offsets"))) return rc;
+    CK(cudaMemcpyAsync(c->d_scenes, dev.data(), dev.size() * sizeof(TmzDev), cudaMemcpyHostToDevice, c->stream), "upload");
+    CK(cudaMemcpyAsync(c->d_tasks, tasks.data(), tasks.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
+    if (!tsamp.empty())
+        CK(cudaMemcpyAsync(c->d_samp, tsamp.data(), tsamp.size() * sizeof(Sample2), cudaMemcpyHostToDevice, c->stream), "upload");
+    if (!ssamp.empty())
+        CK(cudaMemcpyAsync(c->d_samp_scene, ssamp.data(), ssamp.size() * sizeof(Sample2), cudaMemcpyHostToDevice, c->stream), "upload");
+    CK(cudaMemcpyAsync(c->d_samp_off, soff.data(), soff.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream), "upload");
+    CK(cudaStreamSynchronize(c->stream), "upload task list");
+    c->n_tasks = (int)tasks.size();
+    c->task_tb = T;
+    c->task_seg = seg;
+    c->dirty = false;
+    return FDTD_OK;
+}
+
+int field_slot_2d(int comp) {
+    if (comp == FDTD_EZ) return F_EZ;
+    if (comp == FDTD_HX) return F_HX;
+    if (comp == FDTD_HY) return F_HY;
+    return -1;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int fdtd_create(const fdtd_grid* grid, double dx, double dt, double courant, const uint8_t* mat_idx,
+                const fdtd_material* table, int n_mat, void* cuda_stream, fdtd_ctx** out) {
+    if (!out) return FDTD_EINVAL;
+    *out = nullptr;
+    if (!grid) return FDTD_EINVAL;
+    if (grid->dims == 3) return fdtd_create3(grid, dx, dt, courant, mat_idx, table, n_mat, cuda_stream, out);
+    fdtd_ctx* c = ctx_new(cuda_stream);
+    Scene2* s = nullptr;
+    int rc = scene2_init(c, grid, dx, dt, courant, mat_idx, table, n_mat, &s);
+    if (rc) {
+        // keep the context alive so the caller can read the message
+        *out = c;
+        return rc;
+    }
+    c->s2.push_back(s);
+    *out = c;
+    return FDTD_OK;
+}
+
+int fdtd_create_batch(int n_scenes, const fdtd_grid* grids, const double* dx, const double* dt,
+                      const uint8_t* const* mat_idx, const fdtd_material* const* tables, const int* n_mat,
+                      void* cuda_stream, fdtd_ctx** out) {
+    if (!out) return FDTD_EINVAL;
+    *out = nullptr;
+    fdtd_ctx* c = ctx_new(cuda_stream);
+    *out = c;
+    if (n_scenes < 1 || !grids || !dx || !dt || !mat_idx || !tables || !n_mat)
+        return fail(c, FDTD_EINVAL, "batch needs n_scenes >= 1 and non-NULL arrays");
+    for (int k = 0; k < n_scenes; k++) {
+        Scene2* s = nullptr;
+        int rc = scene2_init(c, &grids[k], dx[k], dt[k], 0.99, mat_idx[k], tables[k], n_mat[k], &s);
+        if (rc) {
+            c->err = "scene " + std::to_string(k) + ": " + c->err;
+            return rc;
+        }
+        c->s2.push_back(s);
+    }
+    return FDTD_OK;
+}
+
+int fdtd_select_scene(fdtd_ctx* c, int scene) {
+    if (!c) return FDTD_EINVAL;
+    const int n = c->dims == 2 ? (int)c->s2.size() : (c->s3 ? 1 : 0);
+    if (scene < 0 || scene >= n) return fail(c, FDTD_EINVAL, "scene %d outside 0..%d", scene, n - 1);
+    c->cur = scene;
+    return FDTD_OK;
+}
+
+int fdtd_num_scenes(const fdtd_ctx* c) {
+    if (!c) return 0;
+    return c->dims == 2 ? (int)c->s2.size() : (c->s3 ? 1 : 0);
+}
+
+void fdtd_destroy(fdtd_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    for (Scene2* s : c->s2) scene2_free(s);
+    for (DftMon& m : c->mons) {
+        dfree(m.d_freq);
+        dfree(m.d_acc);
+    }
+    fdtd_destroy3(c);
+    graph_free(c);
+    dfree(c->d_scenes); dfree(c->d_tasks); dfree(c->d_samp); dfree(c->d_samp_scene); dfree(c->d_samp_off);
+    delete c;
+}
+
+const char* fdtd_last_error(const fdtd_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
+
+int fdtd_set_option(fdtd_ctx* c, int option, int64_t v) {
+    if (!c) return FDTD_EINVAL;
+    switch (option) {
+        case FDTD_OPT_KERNEL:
+            if (v < 0 || v > 1) return fail(c, FDTD_EINVAL, "kernel option %lld outside 0..1", (long long)v);
+            c->opt_kernel = (int)v;
+            return FDTD_OK;
+        case FDTD_OPT_TBLOCK:
+            if (v < 1 || v > MAX_TB) return fail(c, FDTD_EINVAL, "tblock %lld outside 1..%d", (long long)v, MAX_TB);
+            c->opt_tblock = (int)v;
+            return FDTD_OK;
+        case FDTD_OPT_SEGMENT:
+            if (v < 8 || v > (1 << 20) || v % 8) return fail(c, FDTD_EINVAL, "segment %lld must be a multiple of 8 >= 8", (long long)v);
+            c->opt_segment = (int)v;
+            c->dirty = true;
+            return FDTD_OK;
+        case FDTD_OPT_WARPS:
+            if (v < 1 || v > 8) return fail(c, FDTD_EINVAL, "warps %lld outside 1..8", (long long)v);
+            c->opt_warps = (int)v;
+            c->dirty = true;
+            return FDTD_OK;
+    }
+    return fail(c, FDTD_EINVAL, "unknown option %d", option);
+}
+
+int64_t fdtd_get_option(const fdtd_ctx* c, int option) {
+    if (!c) return -1;
+    switch (option) {
+        case FDTD_OPT_KERNEL: return c->opt_kernel;
+        case FDTD_OPT_TBLOCK: return c->opt_tblock;
+        case FDTD_OPT_SEGMENT: return c->opt_segment;
+        case FDTD_OPT_WARPS: return c->opt_warps;
+    }
+    return -1;
+}
+
+int fdtd_set_source(fdtd_ctx* c, int kind, int i, int j, int k, int component, const double* params,
+                    const float* samples, int64_t n_samples) {
+    if (!c) return FDTD_EINVAL;
+    if (c->dims == 3) return fdtd_set_source3(c, kind, i, j, k, component, params, samples, n_samples);
+    Scene2* s = cur2(c);
+    if (!s) return fail(c, FDTD_ESTATE, "no scene");
+    if (component != FDTD_EZ) return fail(c, FDTD_EINVAL, "2D TMz sources drive Ez only");
+    if (i < 1 || i >= s->nx || j < 1 || j >= s->ny)
+        return fail(c, FDTD_EINVAL, "source cell (%d, %d) outside 1..nx-1 x 1..ny-1", i, j);
+    if (kind < FDTD_SRC_RICKER || kind > FDTD_SRC_SAMPLED) return fail(c, FDTD_EINVAL, "unknown source kind %d", kind);
+    if (kind == FDTD_SRC_SAMPLED) {
+        if (!samples || n_samples < 0) return fail(c, FDTD_EINVAL, "sampled source needs samples");
+        s->src_samples.assign(samples, samples + n_samples);
+    } else {
+        if (!params || !(params[0] > 0)) return fail(c, FDTD_EINVAL, "source parameter must be > 0");
+        s->src_param = params[0];
+    }
+    s->src_kind = kind;
+    s->src_i = i;
+    s->src_j = j;
+    s->src_cap = 0;   // regenerate the waveform table
+    c->dirty = true;
+    return FDTD_OK;
+}
+
+int fdtd_add_probe(fdtd_ctx* c, int i, int j, int k, int component, int* probe_id) {
+    if (!c || !probe_id) return FDTD_EINVAL;
+    if (c->dims == 3) return fdtd_add_probe3(c, i, j, k, component, probe_id);
+    Scene2* s = cur2(c);
+    if (!s) return fail(c, FDTD_ESTATE, "no scene");
+    if (c->t != 0) return fail(c, FDTD_ESTATE, "probes must be added before the first step (t = %lld)", (long long)c->t);
+    const int f = field_slot_2d(component);
+    if (f < 0) return fail(c, FDTD_EINVAL, "2D probes record Ez, Hx or Hy");
+    if (i < 0 || i >= s->nx || j < 0 || j >= s->ny) return fail(c, FDTD_EINVAL, "probe cell (%d, %d) outside the grid", i, j);
+    Sample2 sp;
+    sp.i = i; sp.j = j; sp.comp = f; sp.slot = (int)s->samples.size();
+    s->samples.push_back(sp);
+    s->rec_cap = 0;
+    dfree(s->d_rec);
+    s->d_rec = nullptr;
+    Probe p;
+    p.scene = c->cur; p.slot = sp.slot; p.t_start = 0;
+    c->probes.push_back(p);
+    *probe_id = (int)c->probes.size() - 1;
+    c->dirty = true;
+    return FDTD_OK;
+}
+
+int fdtd_add_dft_monitor(fdtd_ctx* c, const int32_t* cells, int n_cells, const double* freqs, int n_freq, int* mon_id) {
+    if (!c || !mon_id) return FDTD_EINVAL;
+    if (c->dims == 3) return fdtd_add_dft_monitor3(c, cells, n_cells, freqs, n_freq, mon_id);
+    Scene2* s = cur2(c);
+    if (!s) return fail(c, FDTD_ESTATE, "no scene");
+    if (c->t != 0) return fail(c, FDTD_ESTATE, "monitors must be added before the first step");
+    if (!cells || n_cells < 1 || !freqs || n_freq < 1) return fail(c, FDTD_EINVAL, "monitor needs cells and frequencies");
+    for (int q = 0; q < n_cells; q++) {
+        const int i = cells[2 * q], j = cells[2 * q + 1];
+        if (i < 0 || i >= s->nx || j < 0 || j >= s->ny) return fail(c, FDTD_EINVAL, "monitor cell (%d, %d) outside the grid", i, j);
+    }
+    for (int f = 0; f < n_freq; f++)
+        if (!(freqs[f] >= 0)) return fail(c, FDTD_EINVAL, "frequencies must be >= 0");
+    DftMon m;
+    m.scene = c->cur; m.n_cells = n_cells; m.n_freq = n_freq; m.slot0 = (int)s->samples.size();
+    m.freqs.assign(freqs, freqs + n_freq);
+    m.t_start = 0; m.plane_k = -1; m.comp_mask = 0;
+    m.d_freq = nullptr; m.d_acc = nullptr;
+    int rc = dalloc(c, &m.d_freq, n_freq * sizeof(double), "dft freqs");
+    if (rc) return rc;
+    rc = dalloc(c, &m.d_acc, (size_t)n_cells * n_freq * sizeof(float4), "dft accumulators");
+    if (rc) { dfree(m.d_freq); return rc; }
+    CK(cudaMemcpyAsync(m.d_freq, freqs, n_freq * sizeof(double), cudaMemcpyHostToDevice, c->stream), "upload freqs");
+    CK(cudaMemsetAsync(m.d_acc, 0, (size_t)n_cells * n_freq * sizeof(float4), c->stream), "dft memset");
+    CK(cudaStreamSynchronize(c->stream), "dft monitor");
+    for (int q = 0; q < n_cells; q++) {
+        Sample2 sp;
+        sp.i = cells[2 * q]; sp.j = cells[2 * q + 1]; sp.comp = F_EZ; sp.slot = (int)s->samples.size();
+        s->samples.push_back(sp);
+    }
+    s->rec_cap = 0;
+    dfree(s->d_rec);
+    s->d_rec = nullptr;
+    c->mons.push_back(m);
+    *mon_id = (int)c->mons.size() - 1;
+    c->dirty = true;
+    return FDTD_OK;
+}
+
+int fdtd_add_dft_plane(fdtd_ctx* c, int k, int comp_mask, const double* freqs, int n_freq, int* mon_id) {
+    if (!c || !mon_id) return FDTD_EINVAL;
+    if (c->dims != 3) return fail(c, FDTD_EINVAL, "plane monitors are 3D only");
+    return fdtd_add_dft_plane3(c, k, comp_mask, freqs, n_freq, mon_id);
+}
+
+int fdtd_step(fdtd_ctx* c, int64_t n_steps) {
+    if (!c) return FDTD_EINVAL;
+    if (n_steps < 0) return fail(c, FDTD_EINVAL, "n_steps < 0");
+    if (n_steps == 0) return FDTD_OK;
+    if (c->dims == 3) return fdtd_step3(c, n_steps);
+    if (c->s2.empty()) return fail(c, FDTD_ESTATE, "no scene");
+    int rc = ensure_capacity(c, c->t + n_steps);
+    if (rc) return rc;
+    const int T = c->opt_tblock;
+    if (c->dirty || c->task_seg != c->opt_segment) {
+        rc = rebuild(c, T, c->opt_segment, c->opt_warps);
+        if (rc) return rc;
+    }
+    int64_t left = n_steps;
+    while (left > 0) {
+        int done;
+        if (c->opt_kernel == 1) {
+            rc = tmz_naive_step(c, c->t);
+            done = 1;
+        } else {
+            done = (int)std::min<int64_t>(T, left);
+            rc = tmz_fused_launch(c, done, c->opt_warps, c->t, c->parity);
+            c->parity ^= 1;
+        }
+        if (rc) return rc;
+        for (const DftMon& m : c->mons) {
+            if (m.plane_k >= 0) continue;
+            rc = dft_cells_launch(c, m, c->t, done);
+            if (rc) return rc;
+        }
+        c->t += done;
+        left -= done;
+    }
+    return FDTD_OK;
+}
+
+int fdtd_read_probe(fdtd_ctx* c, int probe_id, float* out, int64_t n) {
+    if (!c || !out) return FDTD_EINVAL;
+    if (c->dims == 3) return fdtd_read_probe3(c, probe_id, out, n);
+    if (probe_id < 0 || probe_id >= (int)c->probes.size()) return fail(c, FDTD_EINVAL, "no probe %d", probe_id);
+    if (n < 0 || n > c->t) return fail(c, FDTD_EINVAL, "asked for %lld samples, %lld recorded", (long long)n, (long long)c->t);
+    if (n == 0) return FDTD_OK;
+    const Probe& p = c->probes[probe_id];
+    Scene2* s = c->s2[p.scene];
+    const int nrec = (int)s->samples.size();
+    CK(cudaMemcpy2DAsync(out, sizeof(float), s->d_rec + p.slot, (size_t)nrec * sizeof(float), sizeof(float), (size_t)n,
+                         cudaMemcpyDeviceToHost, c->stream), "read probe");
+    CK(cudaStreamSynchronize(c->stream), "read probe");
+    return FDTD_OK;
+}
+
+int fdtd_read_dft(fdtd_ctx* c, int mon_id, float* re, float* im) {
+    if (!c || !re || !im) return FDTD_EINVAL;
+    if (mon_id < 0 || mon_id >= (int)c->mons.size()) return fail(c, FDTD_EINVAL, "no monitor %d", mon_id);
+    const DftMon& m = c->mons[mon_id];
+    if (m.plane_k >= 0) return fdtd_read_dft3(c, mon_id, re, im);
+    const size_t n = (size_t)m.n_cells * m.n_freq;
+    std::vector<float4> acc(n);
+    CK(cudaMemcpyAsync(acc.data(), m.d_acc, n * sizeof(float4), cudaMemcpyDeviceToHost, c->stream), "read dft");
+    CK(cudaStreamSynchronize(c->stream), "read dft");
+    for (size_t q = 0; q < n; q++) {
+        // Kahan: the running compensation holds the negated lost low part
+        re[q] = (float)((double)acc[q].x - (double)acc[q].z);
+        im[q] = (float)((double)acc[q].y - (double)acc[q].w);
+    }
+    return FDTD_OK;
+}
+
+int fdtd_get_field(fdtd_ctx* c, int component, float* out, int on_device) {
+    if (!c || !out) return FDTD_EINVAL;
+    if (c->dims == 3) return fdtd_get_field3(c, component, out, on_device);
+    Scene2* s = cur2(c);
+    if (!s) return fail(c, FDTD_ESTATE, "no scene");
+    const int f = field_slot_2d(component);
+    if (f < 0) return fail(c, FDTD_EINVAL, "2D fields are Ez, Hx, Hy");
+    const float* src = s->fbuf[f][c->parity] + (size_t)PAD_Y * s->pitch + PAD_X;
+    CK(cudaMemcpy2DAsync(out, (size_t)s->nx * sizeof(float), src, (size_t)s->pitch * sizeof(float),
+                         (size_t)s->nx * sizeof(float), (size_t)s->ny,
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream), "get field");
+    CK(cudaStreamSynchronize(c->stream), "get field");
+    return FDTD_OK;
+}
+
+int fdtd_set_field(fdtd_ctx* c, int component, const float* in, int on_device) {
+    if (!c || !in) return FDTD_EINVAL;
+    if (c->dims == 3) return fdtd_set_field3(c, component, in, on_device);
+    Scene2* s = cur2(c);
+    if (!s) return fail(c, FDTD_ESTATE, "no scene");
+    const int f = field_slot_2d(component);
+    if (f < 0) return fail(c, FDTD_EINVAL, "2D fields are Ez, Hx, Hy");
+    float* dst = s->fbuf[f][c->parity] + (size_t)PAD_Y * s->pitch + PAD_X;
+    CK(cudaMemcpy2DAsync(dst, (size_t)s->pitch * sizeof(float), in, (size_t)s->nx * sizeof(float),
+                         (size_t)s->nx * sizeof(float), (size_t)s->ny,
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream), "set field");
+    CK(cudaStreamSynchronize(c->stream), "set field");
+    return FDTD_OK;
+}
+
+int fdtd_reset(fdtd_ctx* c) {
+    if (!c) return FDTD_EINVAL;
+    if (c->dims == 3) return fdtd_reset3(c);
+    for (Scene2* s : c->s2) {
+        const size_t fb = (size_t)s->pitch * s->rows * sizeof(float);
+        for (int f = 0; f < F_COUNT2; f++)
+            for (int p = 0; p < 2; p++) CK(cudaMemsetAsync(s->fbuf[f][p], 0, fb, c->stream), "reset");
+        if (s->d_rec) CK(cudaMemsetAsync(s->d_rec, 0, (size_t)s->rec_cap * s->samples.size() * sizeof(float), c->stream), "reset");
+    }
+    for (DftMon& m : c->mons)
+        CK(cudaMemsetAsync(m.d_acc, 0, (size_t)m.n_cells * m.n_freq * sizeof(float4), c->stream), "reset");
+    CK(cudaStreamSynchronize(c->stream), "reset");
+    c->t = 0;
+    c->parity = 0;
+    return FDTD_OK;
+}
+
+int64_t fdtd_time_step(const fdtd_ctx* c) { return c ? c->t : -1; }
+int64_t fdtd_launch_count(const fdtd_ctx* c) { return c ? c->launches : -1; }
+
+int fdtd_save_state(fdtd_ctx* c, void* buf, size_t* bytes) {
+    if (!c || !bytes) return FDTD_EINVAL;
+    if (c->dims == 3) return fdtd_save_state3(c, buf, bytes);
+    size_t need = 2 * sizeof(int64_t);
+    for (Scene2* s : c->s2) {
+        need += (size_t)F_COUNT2 * s->nx * s->ny * sizeof(float);
+        need += (size_t)c->t * s->samples.size() * sizeof(float);
+    }
+    for (DftMon& m : c->mons) need += (size_t)m.n_cells * m.n_freq * sizeof(float4);
+    if (!buf) {
+        *bytes = need;
+        return FDTD_OK;
+    }
+    if (*bytes < need) return fail(c, FDTD_EINVAL, "state buffer of %zu bytes, %zu needed", *bytes, need);
+    char* p = (char*)buf;
+    int64_t hdr[2] = {c->t, (int64_t)c->s2.size()};
+    memcpy(p, hdr, sizeof(hdr));
+    p += sizeof(hdr);
+    for (Scene2* s : c->s2) {
+        for (int f = 0; f < F_COUNT2; f++) {
+            const float* src = s->fbuf[f][c->parity] + (size_t)PAD_Y * s->pitch + PAD_X;
+            CK(cudaMemcpy2DAsync(p, (size_t)s->nx * sizeof(float), src, (size_t)s->pitch * sizeof(float),
+                                 (size_t)s->nx * sizeof(float), (size_t)s->ny, cudaMemcpyDeviceToHost, c->stream), "save");
+            p += (size_t)s->nx * s->ny * sizeof(float);
+        }
+        const size_t rb = (size_t)c->t * s->samples.size() * sizeof(float);
+        if (rb) CK(cudaMemcpyAsync(p, s->d_rec, rb, cudaMemcpyDeviceToHost, c->stream), "save");
+        p += rb;
+    }
+    for (DftMon& m : c->mons) {
+        const size_t ab = (size_t)m.n_cells * m.n_freq * sizeof(float4);
+        CK(cudaMemcpyAsync(p, m.d_acc, ab, cudaMemcpyDeviceToHost, c->stream), "save");
+        p += ab;
+    }
+    CK(cudaStreamSynchronize(c->stream), "save");
+    *bytes = need;
+    return FDTD_OK;
+}
+
+int fdtd_load_state(fdtd_ctx* c, const void* buf, size_t bytes) {
+    if (!c || !buf) return FDTD_EINVAL;
+    if (c->dims == 3) return fdtd_load_state3(c, buf, bytes);
+    if (bytes < 2 * sizeof(int64_t)) return fail(c, FDTD_EINVAL, "state buffer too small");
+    int64_t hdr[2];
+    memcpy(hdr, buf, sizeof(hdr));
+    if (hdr[1] != (int64_t)c->s2.size()) return fail(c, FDTD_EINVAL, "state has %lld scenes, context %zu", (long long)hdr[1], c->s2.size());
+    size_t need = sizeof(hdr);
+    for (Scene2* s : c->s2)
+        need += (size_t)F_COUNT2 * s->nx * s->ny * sizeof(float) + (size_t)hdr[0] * s->samples.size() * sizeof(float);
+    for (DftMon& m : c->mons) need += (size_t)m.n_cells * m.n_freq * sizeof(float4);
+    if (bytes < need) return fail(c, FDTD_EINVAL, "state buffer of %zu bytes, %zu needed", bytes, need);
+    int rc = ensure_capacity(c, std::max<int64_t>(hdr[0], 1));
+    if (rc) return rc;
+    const char* p = (const char*)buf + sizeof(hdr);
+    c->parity = 0;
+    for (Scene2* s : c->s2) {
+        for (int f = 0; f < F_COUNT2; f++) {
+            float* dst = s->fbuf[f][0] + (size_t)PAD_Y * s->pitch + PAD_X;
+            CK(cudaMemcpy2DAsync(dst, (size_t)s->pitch * sizeof(float), p, (size_t)s->nx * sizeof(float),
+                                 (size_t)s->nx * sizeof(float), (size_t)s->ny, cudaMemcpyHostToDevice, c->stream), "load");
+            p += (size_t)s->nx * s->ny * sizeof(float);
+        }
+        const size_t rb = (size_t)hdr[0] * s->samples.size() * sizeof(float);
+        if (rb) CK(cudaMemcpyAsync(s->d_rec, p, rb, cudaMemcpyHostToDevice, c->stream), "load");
+        p += rb;
+    }
+    for (DftMon& m : c->mons) {
+        const size_t ab = (size_t)m.n_cells * m.n_freq * sizeof(float4);
+        CK(cudaMemcpyAsync(m.d_acc, p, ab, cudaMemcpyHostToDevice, c->stream), "load");
+        p += ab;
+    }
+    CK(cudaStreamSynchronize(c->stream), "load");
+    c->t = hdr[0];
+    return FDTD_OK;
+}
+
+int fdtd_check_finite(fdtd_ctx* c) {
+    if (!c) return FDTD_EINVAL;
+    if (c->dims == 3) return fdtd_check_finite3(c);
+    if (c->dirty) {
+        int rc = rebuild(c, c->opt_tblock, c->opt_segment, c->opt_warps);
+        if (rc) return rc;
+    }
+    int bad = 0;
+    int rc = tmz_finite_check(c, &bad);
+    if (rc) return rc;
+    return bad ? fail(c, FDTD_EUNSTABLE, "non-finite field values") : FDTD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,179 @@
+// Internal structures of the GB300 FDTD library (not part of the C ABI).
+//
+// Device layout of a 2D TMz scene.  Every field and CPML auxiliary is an FP32
+// array of `rows` x `pitch` floats with PAD_Y zero rows below and above the grid
+// and PAD_X zero columns to its left; cell (i, j) lives at
+//     (j + PAD_Y) * pitch + (i + PAD_X).
+// pitch is a multiple of 32 floats, so each row starts on a 128-byte line, and
+// wide enough that the widest warp strip (128 columns from i = x0 - HALO) of the
+// last strip stays inside the row.  Pad cells and the PEC wall cells (i = 0 or
+// j = 0) carry material PEC_MAT, whose coefficients are Ca = Cb = 0: their Ez
+// stays exactly zero, so the zero pads act as the ghost PEC nodes at i, j = N.
+// Fields exist twice (ping-pong): a fused launch reads buffer `parity` and
+// writes buffer 1 - parity, so halos read by one warp are never overwritten by
+// another warp during the launch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "gem_fdtd.h"
+
+namespace gem {
+
+constexpr int PAD_X = 8;
+constexpr int PAD_Y = 8;
+constexpr int PEC_MAT = 255;
+constexpr int MAX_TB = 4;       // deepest temporal blocking of the fused kernel
+constexpr int STRIP = 128;      // columns loaded by one warp (4 per lane)
+constexpr int HALO = 4;         // halo columns each side (one lane): T <= HALO
+
+// field slots of a 2D scene
+enum { F_EZ = 0, F_HX, F_HY, F_PEZX, F_PEZY, F_PHXY, F_PHYX, F_COUNT2 };
+
+// sample (probe / DFT cell) of a 2D scene
+struct Sample2 {
+    int i, j, comp, slot;   // comp: 0 Ez, 1 Hx, 2 Hy; slot: column in the record buffer
+};
+
+// what a warp task of the fused kernel needs to know about its scene
+struct TmzDev {
+    float* f[F_COUNT2][2];      // fields and psi, ping-pong
+    const uint8_t* mat;         // [rows][pitch]
+    const float4* coef;         // [256] (Ca, Cb/dx, Cb/dy, 0)
+    const float* prof;          // 4 x-profiles [pitch] (bEx cEx bHx cHx), then 4 y-profiles [rows]
+    int nx, ny, pitch, rows;
+    int has_pml;
+    float dbx, dby;             // dt / (mu0 dx), dt / (mu0 dy)
+    int src_i, src_j;           // soft source cell or -1
+    const float* src_wave;      // src_wave[n] = s((n+1) dt)
+    long long src_len;
+    float* rec;                 // sample record [cap][n_rec]
+    int n_rec;
+    long long rec_cap;
+    // continuous-permittivity design rectangle (overrides the table inside it)
+    int dsg_i0, dsg_j0, dsg_w, dsg_h;   // dsg_w == 0: none
+    const float4* dsg_coef;             // [dsg_h][dsg_w] (Ca, Cb/dx, Cb/dy, Cb)
+};
+
+// one warp's work in the fused kernel: columns [x0, x0 + STRIP - 2 HALO) and
+// rows [ya, yb) of one scene, plus the samples that fall in that output region
+struct Task {
+    int scene;
+    int x0, ya, yb;
+    int samp_begin, samp_end;   // into the launch's Sample2 list
+    int flags;                  // TASK_* bits
+    int pad;
+};
+enum { TASK_PML = 1, TASK_SRC = 2, TASK_DSG = 4 };
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct DftMon {
+    int scene;
+    int n_cells, n_freq;
+    int slot0;                  // record slots slot0 .. slot0 + n_cells - 1 (Ez at the cells)
+    std::vector<double> freqs;
+    double* d_freq;             // device copy
+    float4* d_acc;              // [n_cells][n_freq] (re, im, comp_re, comp_im)
+    int64_t t_start;            // first step accumulated
+    // 3D plane monitor
+    int plane_k, comp_mask;
+};
+
+struct Probe {
+    int scene, slot;
+    int64_t t_start;
+};
+
+struct Scene2 {
+    int nx, ny, pitch, rows, npml;
+    double dx, dy, dt;
+    std::vector<uint8_t> mat_host;       // [ny][nx] as given
+    std::vector<double> eps_r, sigma;    // material table
+    float* fbuf[F_COUNT2][2];
+    uint8_t* d_mat;
+    float4* d_coef;
+    float* d_prof;
+    // source
+    int src_kind, src_i, src_j;
+    double src_param;
+    std::vector<float> src_samples;
+    float* d_src;
+    long long src_cap;
+    // samples
+    std::vector<Sample2> samples;
+    float* d_rec;
+    long long rec_cap;
+    // design rectangle
+    int dsg_i0, dsg_j0, dsg_w, dsg_h;
+    float4* d_dsg;
+    std::vector<double> dsg_eps;
+};
+
+}  // namespace gem
+
+struct Scene3;
+
+struct fdtd_ctx {
+    int dims;
+    cudaStream_t stream;
+    std::vector<gem::Scene2*> s2;
+    Scene3* s3;
+    int cur;
+    int64_t t;
+    int parity;
+    std::vector<gem::Probe> probes;
+    std::vector<gem::DftMon> mons;
+    std::string err;
+    int64_t launches;
+    // options
+    int opt_kernel, opt_tblock, opt_segment, opt_warps;
+    // device copies for the fused kernel, rebuilt when dirty
+    bool dirty;
+    gem::TmzDev* d_scenes;
+    gem::Task* d_tasks;
+    gem::Sample2* d_samp;          // samples in task order (fused kernel)
+    gem::Sample2* d_samp_scene;    // samples in scene order (unfused kernels)
+    int* d_samp_off;               // [n_scenes + 1] offsets into d_samp_scene
+    int n_tasks;
+    int task_tb, task_seg;     // tblock/segment the task list was built for
+    // edge-list path
+    void* graph;
+};
+
+namespace gem {
+// kernels (k_tmz.cu)
+int tmz_fused_launch(fdtd_ctx* c, int T, int warps, long long n0, int parity);
+int tmz_naive_step(fdtd_ctx* c, long long n);
+int dft_cells_launch(fdtd_ctx* c, const DftMon& m, long long n0, int nsteps);
+int tmz_finite_check(fdtd_ctx* c, int* bad);
+size_t tmz_fused_smem(int T, int warps);
+}  // namespace gem
+
+namespace gem {
+// 3D Yee (k_yee3d.cu)
+int fdtd_create3(const fdtd_grid* grid, double dx, double dt, double courant, const uint8_t* mat,
+                 const fdtd_material* table, int n_mat, void* stream, fdtd_ctx** out);
+void fdtd_destroy3(fdtd_ctx* c);
+int fdtd_set_source3(fdtd_ctx* c, int kind, int i, int j, int k, int comp, const double* params,
+                     const float* samples, int64_t n_samples);
+int fdtd_add_probe3(fdtd_ctx* c, int i, int j, int k, int comp, int* id);
+int fdtd_add_dft_monitor3(fdtd_ctx* c, const int32_t* cells, int n_cells, const double* freqs, int n_freq, int* id);
+int fdtd_add_dft_plane3(fdtd_ctx* c, int k, int comp_mask, const double* freqs, int n_freq, int* id);
+int fdtd_step3(fdtd_ctx* c, int64_t n);
+int fdtd_read_probe3(fdtd_ctx* c, int id, float* out, int64_t n);
+int fdtd_read_dft3(fdtd_ctx* c, int id, float* re, float* im);
+int fdtd_get_field3(fdtd_ctx* c, int comp, float* out, int on_device);
+int fdtd_set_field3(fdtd_ctx* c, int comp, const float* in, int on_device);
+int fdtd_reset3(fdtd_ctx* c);
+int fdtd_save_state3(fdtd_ctx* c, void* buf, size_t* bytes);
+int fdtd_load_state3(fdtd_ctx* c, const void* buf, size_t bytes);
+int fdtd_check_finite3(fdtd_ctx* c);
+// literal edge-list path (k_graph.cu)
+void graph_free(fdtd_ctx* c);
+}  // namespace gem

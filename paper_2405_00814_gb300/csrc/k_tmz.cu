@@ -1,0 +1,583 @@
+// 2D TMz kernels for sm_103a.
+//
+// The leapfrog step of Sec. II-B (eqs. (7)-(9), rotated to TMz) is the two
+// message-passing layers of Prop. 2 with the graph kept implicit in the grid:
+//   layer 1:  Hx -= Db_y (dEz/dy + psi_Hxy),  Hy += Db_x (dEz/dx + psi_Hyx)
+//   layer 2:  Ez  = Ca Ez + Cb/dx (dHy + psi_Ezx) - Cb/dy (dHx + psi_Ezy)
+// with CPML auxiliaries psi = b psi + c dF inside the absorbing slabs.
+//
+// k_tmz_fused -- the hot path.  One warp streams a 128-column strip (4 columns
+// per lane, float4 loads) up a segment of rows.  Each row enters through a
+// cp.async pipeline into lane-private shared-memory stages, then lives in a
+// register ring while T time levels are applied to it in a skewed wavefront:
+// at row r, level t updates row r - t (H then E), so a row leaves the ring
+// T steps newer than it came in.  x-neighbours come from warp shuffles (the
+// right Ez for layer 1, the left Hy for layer 2); y-neighbours are the adjacent
+// ring slots.  The strip's outer lane on each side is a halo whose values go
+// stale by one column per level, so T <= 4 keeps the 120 inner columns exact.
+// Each launch reads buffer `parity` and writes 1 - parity.  HBM traffic per
+// cell and launch is the 12 B of fields + 1 B of material read and 12 B written
+// (plus halo re-reads), for T steps: the single-sweep 25 B per cell-update is
+// divided by T.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gem_internal.h"
+
+namespace gem {
+
+constexpr int PF = 3;          // rows in flight per warp
+constexpr int NSLOT = 7;       // float4 slots per lane per stage: Ez Hx Hy pEzx pEzy pHxy pHyx
+constexpr int STAGE_F4 = NSLOT * 32 + 8;   // + 32 uint32 material words
+
+__host__ __device__ constexpr int stages_for(int T) { return T + PF; }
+
+size_t tmz_fused_smem(int T, int warps) {
+    return (size_t)warps * stages_for(T) * STAGE_F4 * sizeof(float4);
+}
+
+__device__ __forceinline__ size_t sidx(int pitch, int i, int j) {
+    return (size_t)(j + PAD_Y) * (size_t)pitch + (size_t)(i + PAD_X);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool pred) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    int n = pred ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ float comp4(const float4& v, int c) {
+    return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
+
+__device__ __forceinline__ void add4(float4& v, int c, float a) {
+    if (c == 0) v.x += a;
+    else if (c == 1) v.y += a;
+    else if (c == 2) v.z += a;
+    else v.w += a;
+}
+
+// Ez = Ca Ez + Cb/dx (dhy + psi_x) - Cb/dy (dhx + psi_y)
+__device__ __forceinline__ float e_upd(float e, float dhy, float dhx, const float4& co) {
+    return co.x * e + co.y * dhy - co.z * dhx;
+}
+
+struct Prof {
+    const float* p;
+    int pitch, rows;
+    __device__ __forceinline__ float bEx(int cs) const { return p[cs]; }
+    __device__ __forceinline__ float cEx(int cs) const { return p[pitch + cs]; }
+    __device__ __forceinline__ float bHx(int cs) const { return p[2 * pitch + cs]; }
+    __device__ __forceinline__ float cHx(int cs) const { return p[3 * pitch + cs]; }
+    __device__ __forceinline__ float bEy(int rs) const { return p[4 * pitch + rs]; }
+    __device__ __forceinline__ float cEy(int rs) const { return p[4 * pitch + rows + rs]; }
+    __device__ __forceinline__ float bHy(int rs) const { return p[4 * pitch + 2 * rows + rs]; }
+    __device__ __forceinline__ float cHy(int rs) const { return p[4 * pitch + 3 * rows + rs]; }
+};
+
+// ===========================================================================
+// fused, temporally blocked kernel
+// ===========================================================================
+template <int T>
+__global__ void __launch_bounds__(256) k_tmz_fused(const TmzDev* __restrict__ scenes,
+                                                   const Task* __restrict__ tasks, int n_tasks,
+                                                   const Sample2* __restrict__ samps, int parity,
+                                                   long long n0) {
+    constexpr int Q = stages_for(T);
+    extern __shared__ float4 smem_f4[];
+    __shared__ float4 coef_s[256];
+
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int warps = blockDim.x >> 5;
+    const int tid = blockIdx.x * warps + wib;
+
+    // every block holds tasks of one scene: stage its coefficient table
+    const int blk_scene = tasks[blockIdx.x * warps].scene;
+    const TmzDev* S = scenes + blk_scene;
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) coef_s[k] = S->coef[k];
+    __syncthreads();
+    if (tid >= n_tasks) return;
+    const Task tk = tasks[tid];
+    if (tk.scene < 0) return;
+
+    const int pitch = S->pitch, nx = S->nx, ny = S->ny;
+    const float* __restrict__ ez_in = S->f[F_EZ][parity];
+    const float* __restrict__ hx_in = S->f[F_HX][parity];
+    const float* __restrict__ hy_in = S->f[F_HY][parity];
+    float* __restrict__ ez_out = S->f[F_EZ][parity ^ 1];
+    float* __restrict__ hx_out = S->f[F_HX][parity ^ 1];
+    float* __restrict__ hy_out = S->f[F_HY][parity ^ 1];
+    const uint8_t* __restrict__ mat = S->mat;
+    const float dbx = S->dbx, dby = S->dby;
+
+    const int cx = tk.x0 - HALO + 4 * lane;     // first of this lane's 4 columns
+    const int cs = cx + PAD_X;                 // its storage column (>= 4)
+    const bool out_lane = (lane >= HALO / 4) && (lane < 32 - HALO / 4) && (cx < nx);
+    const int s_row = tk.ya - T;               // first row streamed
+    const int r_last = tk.yb + T - 1;          // last row streamed
+
+    // CPML: lanes whose columns touch an x-slab carry psi_Ezx / psi_Hyx
+    const bool pml = (tk.flags & TASK_PML) != 0;
+    const int npml = S->has_pml;
+    const Prof pr{S->prof, pitch, S->rows};
+    bool lane_px = false;
+    float4 bex4 = make_float4(0, 0, 0, 0), cex4 = bex4, bhx4 = bex4, chx4 = bex4;
+    if (pml) {
+        lane_px = (cx < npml) || (cx + 3 >= nx - npml);
+        if (lane_px) {
+            bex4 = make_float4(pr.bEx(cs), pr.bEx(cs + 1), pr.bEx(cs + 2), pr.bEx(cs + 3));
+            cex4 = make_float4(pr.cEx(cs), pr.cEx(cs + 1), pr.cEx(cs + 2), pr.cEx(cs + 3));
+            bhx4 = make_float4(pr.bHx(cs), pr.bHx(cs + 1), pr.bHx(cs + 2), pr.bHx(cs + 3));
+            chx4 = make_float4(pr.cHx(cs), pr.cHx(cs + 1), pr.cHx(cs + 2), pr.cHx(cs + 3));
+        }
+    }
+    float* psi_in[4] = {S->f[F_PEZX][parity], S->f[F_PEZY][parity], S->f[F_PHXY][parity],
+                        S->f[F_PHYX][parity]};
+    float* psi_out[4] = {S->f[F_PEZX][parity ^ 1], S->f[F_PEZY][parity ^ 1],
+                         S->f[F_PHXY][parity ^ 1], S->f[F_PHYX][parity ^ 1]};
+
+    // design rectangle (continuous permittivity)
+    const bool dsg = (tk.flags & TASK_DSG) != 0;
+    // source
+    const bool has_src = (tk.flags & TASK_SRC) != 0;
+    const int src_j = S->src_j, src_d = S->src_i - cx;
+
+    float4* stage0 = smem_f4 + (size_t)wib * Q * STAGE_F4;
+
+    auto issue = [&](int row) {
+        const int q = (row - s_row) % Q;
+        float4* st = stage0 + q * STAGE_F4;
+        const size_t g = (size_t)(row + PAD_Y) * pitch + cs;
+        cp_async16(st + 0 * 32 + lane, ez_in + g, true);
+        cp_async16(st + 1 * 32 + lane, hx_in + g, true);
+        cp_async16(st + 2 * 32 + lane, hy_in + g, true);
+        cp_async4(reinterpret_cast<uint32_t*>(st + NSLOT * 32) + lane, mat + g);
+        if (pml) {
+            const bool yrow = (row < npml) || (row >= ny - npml);
+            if (lane_px) {
+                cp_async16(st + 3 * 32 + lane, psi_in[0] + g, true);
+                cp_async16(st + 6 * 32 + lane, psi_in[3] + g, true);
+            }
+            if (yrow) {
+                cp_async16(st + 4 * 32 + lane, psi_in[1] + g, true);
+                cp_async16(st + 5 * 32 + lane, psi_in[2] + g, true);
+            }
+        }
+    };
+
+    // register ring: slot k holds row r - k
+    float4 E[T + 1], X[T + 2], Y[T + 1];
+    uint32_t M[T + 1];
+#pragma unroll
+    for (int k = 0; k < T + 1; k++) {
+        E[k] = make_float4(0, 0, 0, 0);
+        Y[k] = E[k];
+        M[k] = 0;
+    }
+#pragma unroll
+    for (int k = 0; k < T + 2; k++) X[k] = make_float4(0, 0, 0, 0);
+
+#pragma unroll
+    for (int k = 0; k < PF; k++) {
+        if (s_row + k <= r_last) issue(s_row + k);
+        cp_commit();
+    }
+
+    const float* wave = S->src_wave;
+    float* rec = S->rec;
+    const int n_rec = S->n_rec;
+
+    for (int r = s_row; r <= r_last; ++r) {
+        cp_wait<PF - 1>();
+        // shift the ring and take row r from its stage
+#pragma unroll
+        for (int k = T + 1; k >= 1; k--) X[k] = X[k - 1];
+#pragma unroll
+        for (int k = T; k >= 1; k--) {
+            E[k] = E[k - 1];
+            Y[k] = Y[k - 1];
+            M[k] = M[k - 1];
+        }
+        {
+            const float4* st = stage0 + ((r - s_row) % Q) * STAGE_F4;
+            E[0] = st[0 * 32 + lane];
+            X[0] = st[1 * 32 + lane];
+            Y[0] = st[2 * 32 + lane];
+            M[0] = reinterpret_cast<const uint32_t*>(st + NSLOT * 32)[lane];
+        }
+
+#pragma unroll
+        for (int t = 1; t <= T; t++) {
+            const int a = r - t;
+            if (a < s_row) continue;   // warp-uniform
+            float4* sta = stage0 + ((a - s_row) % Q) * STAGE_F4;
+            // ---- layer 1: H at row a from Ez at level t-1 (rows a, a+1) ----
+            const float4 e = E[t], eu = E[t - 1];
+            const float er = __shfl_down_sync(0xffffffffu, e.x, 1);
+            float4 dey = make_float4(eu.x - e.x, eu.y - e.y, eu.z - e.z, eu.w - e.w);
+            float4 dex = make_float4(e.y - e.x, e.z - e.y, e.w - e.z, er - e.w);
+            if (pml) {
+                const int rs = a + PAD_Y;
+                if ((a < npml) || (a >= ny - npml)) {
+                    const float b = pr.bHy(rs), c = pr.cHy(rs);
+                    float4 p = sta[5 * 32 + lane];
+                    p.x = b * p.x + c * dey.x;
+                    p.y = b * p.y + c * dey.y;
+                    p.z = b * p.z + c * dey.z;
+                    p.w = b * p.w + c * dey.w;
+                    sta[5 * 32 + lane] = p;
+                    dey.x += p.x; dey.y += p.y; dey.z += p.z; dey.w += p.w;
+                }
+                if (lane_px) {
+                    float4 p = sta[6 * 32 + lane];
+                    p.x = bhx4.x * p.x + chx4.x * dex.x;
+                    p.y = bhx4.y * p.y + chx4.y * dex.y;
+                    p.z = bhx4.z * p.z + chx4.z * dex.z;
+                    p.w = bhx4.w * p.w + chx4.w * dex.w;
+                    sta[6 * 32 + lane] = p;
+                    dex.x += p.x; dex.y += p.y; dex.z += p.z; dex.w += p.w;
+                }
+            }
+            X[t].x -= dby * dey.x; X[t].y -= dby * dey.y; X[t].z -= dby * dey.z; X[t].w -= dby * dey.w;
+            Y[t].x += dbx * dex.x; Y[t].y += dbx * dex.y; Y[t].z += dbx * dex.z; Y[t].w += dbx * dex.w;
+
+            // ---- layer 2: Ez at row a from H at level t (rows a, a-1) ----
+            const float4 y = Y[t];
+            const float yl = __shfl_up_sync(0xffffffffu, y.w, 1);
+            float4 dhy = make_float4(y.x - yl, y.y - y.x, y.z - y.y, y.w - y.z);
+            float4 dhx = make_float4(X[t].x - X[t + 1].x, X[t].y - X[t + 1].y, X[t].z - X[t + 1].z,
+                                     X[t].w - X[t + 1].w);
+            if (pml) {
+                const int rs = a + PAD_Y;
+                if ((a < npml) || (a >= ny - npml)) {
+                    const float b = pr.bEy(rs), c = pr.cEy(rs);
+                    float4 p = sta[4 * 32 + lane];
+                    p.x = b * p.x + c * dhx.x;
+                    p.y = b * p.y + c * dhx.y;
+                    p.z = b * p.z + c * dhx.z;
+                    p.w = b * p.w + c * dhx.w;
+                    sta[4 * 32 + lane] = p;
+                    dhx.x += p.x; dhx.y += p.y; dhx.z += p.z; dhx.w += p.w;
+                }
+                if (lane_px) {
+                    float4 p = sta[3 * 32 + lane];
+                    p.x = bex4.x * p.x + cex4.x * dhy.x;
+                    p.y = bex4.y * p.y + cex4.y * dhy.y;
+                    p.z = bex4.z * p.z + cex4.z * dhy.z;
+                    p.w = bex4.w * p.w + cex4.w * dhy.w;
+                    sta[3 * 32 + lane] = p;
+                    dhy.x += p.x; dhy.y += p.y; dhy.z += p.z; dhy.w += p.w;
+                }
+            }
+            const uint32_t m = M[t];
+            float4 c0 = coef_s[m & 255u], c1 = coef_s[(m >> 8) & 255u];
+            float4 c2 = coef_s[(m >> 16) & 255u], c3 = coef_s[m >> 24];
+            if (dsg) {
+                const int dj = a - S->dsg_j0;
+                if (dj >= 0 && dj < S->dsg_h) {
+                    const float4* drow = S->dsg_coef + (size_t)dj * S->dsg_w;
+                    const int di = cx - S->dsg_i0;
+                    if (di >= 0 && di < S->dsg_w) c0 = drow[di];
+                    if (di + 1 >= 0 && di + 1 < S->dsg_w) c1 = drow[di + 1];
+                    if (di + 2 >= 0 && di + 2 < S->dsg_w) c2 = drow[di + 2];
+                    if (di + 3 >= 0 && di + 3 < S->dsg_w) c3 = drow[di + 3];
+                }
+            }
+            E[t].x = e_upd(E[t].x, dhy.x, dhx.x, c0);
+            E[t].y = e_upd(E[t].y, dhy.y, dhx.y, c1);
+            E[t].z = e_upd(E[t].z, dhy.z, dhx.z, c2);
+            E[t].w = e_upd(E[t].w, dhy.w, dhx.w, c3);
+
+            const long long n = n0 + (t - 1);   // this level makes E^{n+1}
+            if (has_src && a == src_j && src_d >= 0 && src_d < 4 && n < S->src_len)
+                add4(E[t], src_d, wave[n]);
+            for (int q = tk.samp_begin; q < tk.samp_end; q++) {
+                const Sample2 sp = samps[q];
+                const int d = sp.i - cx;
+                if (sp.j == a && d >= 0 && d < 4) {
+                    const float v = sp.comp == 0 ? comp4(E[t], d) : (sp.comp == 1 ? comp4(X[t], d) : comp4(Y[t], d));
+                    rec[n * n_rec + sp.slot] = v;
+                }
+            }
+        }
+
+        // ---- row r - T is T steps newer: write it out ----
+        const int o = r - T;
+        if (o >= tk.ya) {
+            const float4* sto = stage0 + ((o - s_row) % Q) * STAGE_F4;
+            if (out_lane) {
+                const size_t g = (size_t)(o + PAD_Y) * pitch + cs;
+                if (cx + 3 < nx) {
+                    *reinterpret_cast<float4*>(ez_out + g) = E[T];
+                    *reinterpret_cast<float4*>(hx_out + g) = X[T];
+                    *reinterpret_cast<float4*>(hy_out + g) = Y[T];
+                    if (pml) {
+                        if ((o < npml) || (o >= ny - npml)) {
+                            *reinterpret_cast<float4*>(psi_out[1] + g) = sto[4 * 32 + lane];
+                            *reinterpret_cast<float4*>(psi_out[2] + g) = sto[5 * 32 + lane];
+                        }
+                        if (lane_px) {
+                            *reinterpret_cast<float4*>(psi_out[0] + g) = sto[3 * 32 + lane];
+                            *reinterpret_cast<float4*>(psi_out[3] + g) = sto[6 * 32 + lane];
+                        }
+                    }
+                } else {
+                    const float4 p0 = sto[3 * 32 + lane], p1 = sto[4 * 32 + lane];
+                    const float4 p2 = sto[5 * 32 + lane], p3 = sto[6 * 32 + lane];
+                    const bool yrow = pml && ((o < npml) || (o >= ny - npml));
+                    for (int c = 0; c < 4; c++) {
+                        if (cx + c >= nx) break;
+                        ez_out[g + c] = comp4(E[T], c);
+                        hx_out[g + c] = comp4(X[T], c);
+                        hy_out[g + c] = comp4(Y[T], c);
+                        if (yrow) {
+                            psi_out[1][g + c] = comp4(p1, c);
+                            psi_out[2][g + c] = comp4(p2, c);
+                        }
+                        if (pml && lane_px) {
+                            psi_out[0][g + c] = comp4(p0, c);
+                            psi_out[3][g + c] = comp4(p3, c);
+                        }
+                    }
+                }
+            }
+        }
+        // the stage of row r - T is free: prefetch row r + PF into it
+        if (r + PF <= r_last) issue(r + PF);
+        cp_commit();
+    }
+    cp_wait<0>();
+}
+
+// ===========================================================================
+// unfused pair: one H launch, one E launch, one source/record launch per step
+// ===========================================================================
+__global__ void k_tmz_h(const TmzDev* __restrict__ scenes, int parity) {
+    const TmzDev& S = scenes[blockIdx.z];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= S.nx || j >= S.ny) return;
+    const int pitch = S.pitch;
+    const size_t c = sidx(pitch, i, j);
+    const float* ez = S.f[F_EZ][parity];
+    const float e = ez[c];
+    float dey = ez[c + pitch] - e;   // row ny is a zero pad row: ghost PEC
+    float dex = ez[c + 1] - e;       // column nx is a zero pad column
+    if (S.has_pml) {
+        const Prof pr{S.prof, pitch, S.rows};
+        const int rs = j + PAD_Y, cs = i + PAD_X;
+        const float by = pr.bHy(rs), cy = pr.cHy(rs);
+        if (by != 0.f || cy != 0.f) {
+            float* p = S.f[F_PHXY][parity];
+            const float v = by * p[c] + cy * dey;
+            p[c] = v;
+            dey += v;
+        }
+        const float bx = pr.bHx(cs), cxx = pr.cHx(cs);
+        if (bx != 0.f || cxx != 0.f) {
+            float* p = S.f[F_PHYX][parity];
+            const float v = bx * p[c] + cxx * dex;
+            p[c] = v;
+            dex += v;
+        }
+    }
+    S.f[F_HX][parity][c] -= S.dby * dey;
+    S.f[F_HY][parity][c] += S.dbx * dex;
+}
+
+__global__ void k_tmz_e(const TmzDev* __restrict__ scenes, int parity) {
+    const TmzDev& S = scenes[blockIdx.z];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= S.nx || j >= S.ny) return;
+    const int pitch = S.pitch;
+    const size_t c = sidx(pitch, i, j);
+    const float* hx = S.f[F_HX][parity];
+    const float* hy = S.f[F_HY][parity];
+    float dhy = hy[c] - hy[c - 1];
+    float dhx = hx[c] - hx[c - pitch];
+    if (S.has_pml) {
+        const Prof pr{S.prof, pitch, S.rows};
+        const int rs = j + PAD_Y, cs = i + PAD_X;
+        const float bx = pr.bEx(cs), cxx = pr.cEx(cs);
+        if (bx != 0.f || cxx != 0.f) {
+            float* p = S.f[F_PEZX][parity];
+            const float v = bx * p[c] + cxx * dhy;
+            p[c] = v;
+            dhy += v;
+        }
+        const float by = pr.bEy(rs), cy = pr.cEy(rs);
+        if (by != 0.f || cy != 0.f) {
+            float* p = S.f[F_PEZY][parity];
+            const float v = by * p[c] + cy * dhx;
+            p[c] = v;
+            dhx += v;
+        }
+    }
+    float4 co = S.coef[S.mat[c]];
+    if (S.dsg_w > 0) {
+        const int di = i - S.dsg_i0, dj = j - S.dsg_j0;
+        if (di >= 0 && di < S.dsg_w && dj >= 0 && dj < S.dsg_h) co = S.dsg_coef[(size_t)dj * S.dsg_w + di];
+    }
+    float* ez = S.f[F_EZ][parity];
+    ez[c] = e_upd(ez[c], dhy, dhx, co);
+}
+
+__global__ void k_tmz_src_rec(const TmzDev* __restrict__ scenes, const Sample2* __restrict__ samps,
+                              const int* __restrict__ samp_off, int parity, long long n) {
+    const TmzDev& S = scenes[blockIdx.x];
+    if (threadIdx.x == 0 && S.src_i >= 0 && n < S.src_len)
+        S.f[F_EZ][parity][sidx(S.pitch, S.src_i, S.src_j)] += S.src_wave[n];
+    __syncthreads();
+    for (int q = samp_off[blockIdx.x] + threadIdx.x; q < samp_off[blockIdx.x + 1]; q += blockDim.x) {
+        const Sample2 sp = samps[q];
+        const int f = sp.comp == 0 ? F_EZ : (sp.comp == 1 ? F_HX : F_HY);
+        S.rec[n * S.n_rec + sp.slot] = S.f[f][parity][sidx(S.pitch, sp.i, sp.j)];
+    }
+}
+
+// ===========================================================================
+// running DFT of recorded samples, compensated FP32
+// ===========================================================================
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+__global__ void k_dft_cells(const float* __restrict__ rec, int n_rec, int slot0, int n_cells,
+                            const double* __restrict__ freq, int n_freq, double dt, float4* acc,
+                            long long n0, int nsteps) {
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n_cells * n_freq) return;
+    const int cell = id / n_freq, f = id % n_freq;
+    float4 a = acc[id];
+    const double fdt = freq[f] * dt;
+    const float fdtf = (float)dt;
+    for (int k = 0; k < nsteps; k++) {
+        const long long n = n0 + k;
+        const float e = rec[n * n_rec + slot0 + cell];
+        double ph = fdt * (double)(n + 1);
+        ph -= floor(ph);
+        double sn, cs;
+        sincospi(2.0 * ph, &sn, &cs);
+        kahan_add(a.x, a.z, e * ((float)cs * fdtf));
+        kahan_add(a.y, a.w, -e * ((float)sn * fdtf));
+    }
+    acc[id] = a;
+}
+
+__global__ void k_tmz_finite(const TmzDev* __restrict__ scenes, int parity, int* bad) {
+    const TmzDev& S = scenes[blockIdx.z];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= S.nx || j >= S.ny) return;
+    const size_t c = sidx(S.pitch, i, j);
+    const float v = S.f[F_EZ][parity][c] + S.f[F_HX][parity][c] + S.f[F_HY][parity][c];
+    if (!isfinite(v)) atomicOr(bad, 1);
+}
+
+// ===========================================================================
+// launchers
+// ===========================================================================
+template <int T>
+static cudaError_t launch_fused_T(fdtd_ctx* c, int warps, long long n0, int parity) {
+    const size_t smem = tmz_fused_smem(T, warps);
+    cudaError_t e = cudaFuncSetAttribute(k_tmz_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int blocks = (c->n_tasks + warps - 1) / warps;
+    k_tmz_fused<T><<<blocks, warps * 32, smem, c->stream>>>(c->d_scenes, c->d_tasks, c->n_tasks, c->d_samp,
+                                                            parity, n0);
+    return cudaGetLastError();
+}
+
+int tmz_fused_launch(fdtd_ctx* c, int T, int warps, long long n0, int parity) {
+    cudaError_t e;
+    switch (T) {
+        case 1: e = launch_fused_T<1>(c, warps, n0, parity); break;
+        case 2: e = launch_fused_T<2>(c, warps, n0, parity); break;
+        case 3: e = launch_fused_T<3>(c, warps, n0, parity); break;
+        case 4: e = launch_fused_T<4>(c, warps, n0, parity); break;
+        default: return FDTD_EINVAL;
+    }
+    c->launches++;
+    if (e != cudaSuccess) {
+        c->err = std::string("fused launch: ") + cudaGetErrorString(e);
+        return FDTD_ECUDA;
+    }
+    return FDTD_OK;
+}
+
+int tmz_naive_step(fdtd_ctx* c, long long n) {
+    int mx = 0, my = 0;
+    for (auto* s : c->s2) {
+        mx = s->nx > mx ? s->nx : mx;
+        my = s->ny > my ? s->ny : my;
+    }
+    const dim3 blk(32, 8);
+    const dim3 grd((mx + 31) / 32, (my + 7) / 8, (unsigned)c->s2.size());
+    k_tmz_h<<<grd, blk, 0, c->stream>>>(c->d_scenes, c->parity);
+    k_tmz_e<<<grd, blk, 0, c->stream>>>(c->d_scenes, c->parity);
+    k_tmz_src_rec<<<(unsigned)c->s2.size(), 128, 0, c->stream>>>(c->d_scenes, c->d_samp_scene,
+                                                                 c->d_samp_off, c->parity, n);
+    c->launches += 3;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        c->err = std::string("naive step: ") + cudaGetErrorString(e);
+        return FDTD_ECUDA;
+    }
+    return FDTD_OK;
+}
+
+int dft_cells_launch(fdtd_ctx* c, const DftMon& m, long long n0, int nsteps) {
+    const Scene2* s = c->s2[m.scene];
+    const int n = m.n_cells * m.n_freq;
+    k_dft_cells<<<(n + 127) / 128, 128, 0, c->stream>>>(s->d_rec, (int)s->samples.size(), m.slot0, m.n_cells,
+                                                       m.d_freq, m.n_freq, s->dt, m.d_acc, n0, nsteps);
+    c->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        c->err = std::string("dft: ") + cudaGetErrorString(e);
+        return FDTD_ECUDA;
+    }
+    return FDTD_OK;
+}
+
+int tmz_finite_check(fdtd_ctx* c, int* bad) {
+    int mx = 0, my = 0;
+    for (auto* s : c->s2) {
+        mx = s->nx > mx ? s->nx : mx;
+        my = s->ny > my ? s->ny : my;
+    }
+    int* d_bad = nullptr;
+    if (cudaMallocAsync(&d_bad, sizeof(int), c->stream) != cudaSuccess) return FDTD_ENOMEM;
+    cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream);
+    const dim3 blk(32, 8);
+    const dim3 grd((mx + 31) / 32, (my + 7) / 8, (unsigned)c->s2.size());
+    k_tmz_finite<<<grd, blk, 0, c->stream>>>(c->d_scenes, c->parity, d_bad);
+    c->launches++;
+    cudaMemcpyAsync(bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    cudaFreeAsync(d_bad, c->stream);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->err = std::string("finite check: ") + cudaGetErrorString(e);
+        return FDTD_ECUDA;
+    }
+    return FDTD_OK;
+}
+
+}  // namespace gem

@@ -1,0 +1,334 @@
+"""Thin ctypes binding of the C ABI in include/gem_fdtd.h.
+
+Argument marshalling only: every step of the time loop runs in the sm_103a
+kernels of libgemfdtd.so.  There is no fallback: if the library has not been
+built, importing works but creating a Simulation raises.
+PyTorch, when used, only supplies device buffers (``get_field(out=tensor)``)
+and the CUDA stream the work is ordered on.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgemfdtd.so")
+_LIB = None
+
+OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6
+PEC, CPML = 0, 1
+COMP = {"ex": 0, "ey": 1, "ez": 2, "hx": 3, "hy": 4, "hz": 5}
+SRC = {"ricker": 0, "gauss_mod": 1, "gauss": 2, "sampled": 3}
+OPT = {"kernel": 0, "tblock": 1, "segment": 2, "warps": 3}
+
+
+class FDTDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class Grid(C.Structure):
+    _fields_ = [("dims", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("pml_cells", C.c_int), ("boundary", C.c_int), ("dy", C.c_double), ("dz", C.c_double)]
+
+
+class Material(C.Structure):
+    _fields_ = [("eps_r", C.c_double), ("mu_r", C.c_double), ("sigma", C.c_double)]
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        vp, i64, dp, fp, ip = C.c_void_p, C.c_int64, C.POINTER(C.c_double), C.c_void_p, C.c_int
+        L.fdtd_create.argtypes = [C.POINTER(Grid), C.c_double, C.c_double, C.c_double, vp,
+                                  C.POINTER(Material), ip, vp, C.POINTER(vp)]
+        L.fdtd_create_batch.argtypes = [ip, C.POINTER(Grid), dp, dp, C.POINTER(vp),
+                                        C.POINTER(C.POINTER(Material)), C.POINTER(C.c_int), vp, C.POINTER(vp)]
+        L.fdtd_select_scene.argtypes = [vp, ip]
+        L.fdtd_num_scenes.argtypes = [vp]
+        L.fdtd_destroy.argtypes = [vp]
+        L.fdtd_destroy.restype = None
+        L.fdtd_last_error.argtypes = [vp]
+        L.fdtd_last_error.restype = C.c_char_p
+        L.fdtd_set_option.argtypes = [vp, ip, i64]
+        L.fdtd_get_option.argtypes = [vp, ip]
+        L.fdtd_get_option.restype = i64
+        L.fdtd_set_source.argtypes = [vp, ip, ip, ip, ip, ip, dp, vp, i64]
+        L.fdtd_add_probe.argtypes = [vp, ip, ip, ip, ip, C.POINTER(C.c_int)]
+        L.fdtd_add_dft_monitor.argtypes = [vp, vp, ip, dp, ip, C.POINTER(C.c_int)]
+        L.fdtd_add_dft_plane.argtypes = [vp, ip, ip, dp, ip, C.POINTER(C.c_int)]
+        L.fdtd_step.argtypes = [vp, i64]
+        L.fdtd_step_edgelist.argtypes = [vp, i64]
+        L.fdtd_export_graph.argtypes = [vp, ip, C.POINTER(i64), C.POINTER(i64), vp, vp, vp]
+        L.fdtd_read_probe.argtypes = [vp, ip, fp, i64]
+        L.fdtd_read_dft.argtypes = [vp, ip, fp, fp]
+        L.fdtd_get_field.argtypes = [vp, ip, vp, ip]
+        L.fdtd_set_field.argtypes = [vp, ip, vp, ip]
+        L.fdtd_reset.argtypes = [vp]
+        L.fdtd_time_step.argtypes = [vp]
+        L.fdtd_time_step.restype = i64
+        L.fdtd_launch_count.argtypes = [vp]
+        L.fdtd_launch_count.restype = i64
+        L.fdtd_save_state.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
+        L.fdtd_load_state.argtypes = [vp, vp, C.c_size_t]
+        L.fdtd_check_finite.argtypes = [vp]
+        _LIB = L
+    return _LIB
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream or None
+    h = getattr(stream, "cuda_stream", None)
+    if h is not None:
+        return h or None
+    raise TypeError("stream must be None, an int handle or a torch.cuda.Stream")
+
+
+def _mat_table(eps_r, sigma):
+    n = len(eps_r)
+    tab = (Material * n)()
+    for k in range(n):
+        tab[k].eps_r, tab[k].mu_r, tab[k].sigma = float(eps_r[k]), 1.0, float(sigma[k])
+    return tab
+
+
+def _grid_of(scene):
+    g = Grid()
+    if hasattr(scene, "nz"):
+        g.dims, g.nx, g.ny, g.nz = 3, scene.nx, scene.ny, scene.nz
+        g.dz = scene.dz
+    else:
+        g.dims, g.nx, g.ny, g.nz = 2, scene.nx, scene.ny, 1
+        g.dz = 0.0
+    g.pml_cells = scene.npml
+    g.boundary = CPML if scene.npml > 0 else PEC
+    g.dy = scene.dy
+    return g
+
+
+class Simulation:
+    """One context of the C ABI: one scene, or a batch of 2D scenes."""
+
+    def __init__(self, scene=None, *, stream=None, _handle=None):
+        self._L = lib()
+        self._h = None
+        self.dims = 2
+        if _handle is not None:
+            self._h = _handle
+            return
+        g = _grid_of(scene)
+        self.dims = g.dims
+        mat = np.ascontiguousarray(scene.mat, np.uint8)
+        tab = _mat_table(scene.eps_r, scene.sigma)
+        h = C.c_void_p()
+        rc = self._L.fdtd_create(C.byref(g), scene.dx, scene.dt, 0.0, mat.ctypes.data, tab, len(scene.eps_r),
+                                 _stream_handle(stream), C.byref(h))
+        self._h = h
+        self._check(rc)
+
+    @classmethod
+    def batch(cls, scenes, *, stream=None):
+        L = lib()
+        n = len(scenes)
+        grids = (Grid * n)(*[_grid_of(s) for s in scenes])
+        dx = (C.c_double * n)(*[s.dx for s in scenes])
+        dt = (C.c_double * n)(*[s.dt for s in scenes])
+        mats = [np.ascontiguousarray(s.mat, np.uint8) for s in scenes]
+        mp = (C.c_void_p * n)(*[m.ctypes.data for m in mats])
+        tabs = [_mat_table(s.eps_r, s.sigma) for s in scenes]
+        tp = (C.POINTER(Material) * n)(*[C.cast(t, C.POINTER(Material)) for t in tabs])
+        nm = (C.c_int * n)(*[len(s.eps_r) for s in scenes])
+        h = C.c_void_p()
+        rc = L.fdtd_create_batch(n, grids, dx, dt, mp, tp, nm, _stream_handle(stream), C.byref(h))
+        sim = cls(_handle=h)
+        sim._check(rc)
+        return sim
+
+    # ---------------------------------------------------------------- basics
+    def _check(self, rc):
+        if rc != OK:
+            msg = self._L.fdtd_last_error(self._h).decode() if self._h else "creation failed"
+            raise FDTDError(rc, msg)
+
+    def close(self):
+        if self._h:
+            self._L.fdtd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def num_scenes(self) -> int:
+        return self._L.fdtd_num_scenes(self._h)
+
+    def select(self, scene: int):
+        self._check(self._L.fdtd_select_scene(self._h, scene))
+        return self
+
+    def set_option(self, name: str, value: int):
+        self._check(self._L.fdtd_set_option(self._h, OPT[name], int(value)))
+
+    def get_option(self, name: str) -> int:
+        return self._L.fdtd_get_option(self._h, OPT[name])
+
+    @property
+    def time_step(self) -> int:
+        return self._L.fdtd_time_step(self._h)
+
+    @property
+    def launch_count(self) -> int:
+        return self._L.fdtd_launch_count(self._h)
+
+    # ---------------------------------------------------------------- inputs
+    def set_source(self, kind, i, j, k=0, component="ez", param=None, samples=None):
+        par = (C.c_double * 1)(float(param) if param is not None else 0.0)
+        if samples is not None:
+            smp = np.ascontiguousarray(samples, np.float32)
+            rc = self._L.fdtd_set_source(self._h, SRC[kind], i, j, k, COMP[component], par, smp.ctypes.data,
+                                         len(smp))
+        else:
+            rc = self._L.fdtd_set_source(self._h, SRC[kind], i, j, k, COMP[component], par, None, 0)
+        self._check(rc)
+
+    def set_scene_source(self, src):
+        if src.kind == "sampled":
+            self.set_source("sampled", src.i, src.j, src.k, src.component, samples=src.samples)
+        else:
+            self.set_source(src.kind, src.i, src.j, src.k, src.component, param=src.params[0])
+
+    def add_probe(self, i, j, k=0, component="ez") -> int:
+        pid = C.c_int()
+        self._check(self._L.fdtd_add_probe(self._h, i, j, k, COMP[component], C.byref(pid)))
+        return pid.value
+
+    def add_dft_monitor(self, cells, freqs) -> int:
+        cells = np.ascontiguousarray(cells, np.int32)
+        fr = np.ascontiguousarray(freqs, np.float64)
+        mid = C.c_int()
+        self._check(self._L.fdtd_add_dft_monitor(self._h, cells.ctypes.data, cells.shape[0],
+                                                 fr.ctypes.data_as(C.POINTER(C.c_double)), len(fr), C.byref(mid)))
+        self._mon_shape = getattr(self, "_mon_shape", {})
+        self._mon_shape[mid.value] = (cells.shape[0], len(fr))
+        return mid.value
+
+    def add_dft_plane(self, k, comps, freqs) -> int:
+        mask = 0
+        for c in comps:
+            mask |= 1 << COMP[c]
+        fr = np.ascontiguousarray(freqs, np.float64)
+        mid = C.c_int()
+        self._check(self._L.fdtd_add_dft_plane(self._h, k, mask, fr.ctypes.data_as(C.POINTER(C.c_double)),
+                                               len(fr), C.byref(mid)))
+        self._mon_shape = getattr(self, "_mon_shape", {})
+        self._mon_shape[mid.value] = (len(comps), len(fr), self._plane_ny, self._plane_nx)
+        return mid.value
+
+    # ---------------------------------------------------------------- stepping
+    def step(self, n: int):
+        self._check(self._L.fdtd_step(self._h, int(n)))
+
+    def step_edgelist(self, n: int):
+        self._check(self._L.fdtd_step_edgelist(self._h, int(n)))
+
+    def reset(self):
+        self._check(self._L.fdtd_reset(self._h))
+
+    def check_finite(self):
+        self._check(self._L.fdtd_check_finite(self._h))
+
+    # ---------------------------------------------------------------- outputs
+    def field_shape(self, scene):
+        return (scene.nz, scene.ny, scene.nx) if hasattr(scene, "nz") else (scene.ny, scene.nx)
+
+    def get_field(self, component, shape=None, out=None):
+        """Copy a field out.  out: a CUDA torch tensor (device copy) or None (host
+        numpy array of the given shape)."""
+        if out is not None and hasattr(out, "data_ptr"):
+            self._check(self._L.fdtd_get_field(self._h, COMP[component], out.data_ptr(), 1))
+            return out
+        arr = np.empty(shape, np.float32) if out is None else out
+        self._check(self._L.fdtd_get_field(self._h, COMP[component], arr.ctypes.data, 0))
+        return arr
+
+    def set_field(self, component, values):
+        if hasattr(values, "data_ptr"):
+            self._check(self._L.fdtd_set_field(self._h, COMP[component], values.data_ptr(), 1))
+            return
+        arr = np.ascontiguousarray(values, np.float32)
+        self._check(self._L.fdtd_set_field(self._h, COMP[component], arr.ctypes.data, 0))
+
+    def read_probe(self, pid, n=None) -> np.ndarray:
+        n = self.time_step if n is None else n
+        out = np.empty(n, np.float32)
+        self._check(self._L.fdtd_read_probe(self._h, pid, out.ctypes.data, n))
+        return out
+
+    def read_dft(self, mid) -> np.ndarray:
+        shape = self._mon_shape[mid]
+        re = np.empty(shape, np.float32)
+        im = np.empty(shape, np.float32)
+        self._check(self._L.fdtd_read_dft(self._h, mid, re.ctypes.data, im.ctypes.data))
+        return re.astype(np.float64) + 1j * im.astype(np.float64)
+
+    def save_state(self) -> bytes:
+        n = C.c_size_t(0)
+        self._check(self._L.fdtd_save_state(self._h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._check(self._L.fdtd_save_state(self._h, buf, C.byref(n)))
+        return buf.raw[:n.value]
+
+    def load_state(self, data: bytes):
+        buf = C.create_string_buffer(data, len(data))
+        self._check(self._L.fdtd_load_state(self._h, buf, len(data)))
+
+    def export_graph(self, layer: int):
+        nn, ne = C.c_int64(), C.c_int64()
+        self._check(self._L.fdtd_export_graph(self._h, layer, C.byref(nn), C.byref(ne), None, None, None))
+        src = np.empty(ne.value, np.int32)
+        dst = np.empty(ne.value, np.int32)
+        w = np.empty(ne.value, np.float32)
+        self._check(self._L.fdtd_export_graph(self._h, layer, C.byref(nn), C.byref(ne), src.ctypes.data,
+                                              dst.ctypes.data, w.ctypes.data))
+        return nn.value, src, dst, w
+
+
+def from_scene(scene, *, stream=None, probes=True, monitors=True, source=True) -> Simulation:
+    """A Simulation for a seeded scene: its source, its probes (Ez) and, if it
+    has monitor cells and frequencies, one DFT monitor over them."""
+    sim = Simulation(scene, stream=stream)
+    if hasattr(scene, "nz"):
+        sim._plane_ny, sim._plane_nx = scene.ny, scene.nx
+    if source and scene.source is not None:
+        sim.set_scene_source(scene.source)
+    sim.probe_ids = []
+    if probes and getattr(scene, "probes", None) is not None:
+        for p in scene.probes:
+            sim.probe_ids.append(sim.add_probe(int(p[0]), int(p[1])))
+    sim.mon_id = None
+    if monitors and getattr(scene, "monitors", None) is not None and scene.freqs is not None:
+        sim.mon_id = sim.add_dft_monitor(scene.monitors, scene.freqs)
+    return sim
