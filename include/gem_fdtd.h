@@ -123,6 +123,14 @@ int64_t fdtd_get_option(const fdtd_ctx* ctx, int option);
 int fdtd_set_source(fdtd_ctx* ctx, int kind, int i, int j, int k, int component, const double* params,
                     const float* samples, int64_t n_samples);
 
+/* Continuous permittivity over a rectangle of the selected 2D scene -- the
+ * design region of inverse design, where every cell has its own eps_r.  Cells
+ * [i0, i0+w) x [j0, j0+h) take eps_r[dj*w + di] and sigma[dj*w + di] (sigma NULL
+ * = 0) instead of their material-table entry; coefficients follow eq. (7).  The
+ * rectangle must avoid the PEC walls: 1 <= i0, i0 + w <= nx, same for j.
+ * Calling it again replaces the values (same rectangle) or the rectangle. */
+int fdtd_set_design(fdtd_ctx* ctx, int i0, int j0, int w, int h, const double* eps_r, const double* sigma);
+
 /* Probe: records the component at (i, j[, k]) after every following step
  * (after the source) -- the waveforms of Fig. 2d.  *probe_id gets its index.
  * Probes must be added before the first step after a reset. */

@@ -405,6 +405,20 @@ int field_slot_2d(int comp) {
 
 }  // namespace
 
+namespace gem {
+// record/waveform capacity and device descriptors for the next n_steps
+int step_prepare(fdtd_ctx* c, int64_t n_steps) {
+    if (c->s2.empty()) return fail(c, FDTD_ESTATE, "no scene");
+    int rc = ensure_capacity(c, c->t + n_steps);
+    if (rc) return rc;
+    if (c->dirty || c->task_seg != c->opt_segment) {
+        rc = rebuild(c, c->opt_tblock, c->opt_segment, c->opt_warps);
+        if (rc) return rc;
+    }
+    return FDTD_OK;
+}
+}  // namespace gem
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -540,6 +554,34 @@ int fdtd_set_source(fdtd_ctx* c, int kind, int i, int j, int k, int component, c
     return FDTD_OK;
 }
 
+int fdtd_set_design(fdtd_ctx* c, int i0, int j0, int w, int h, const double* eps_r, const double* sigma) {
+    if (!c) return FDTD_EINVAL;
+    Scene2* s = cur2(c);
+    if (!s) return fail(c, FDTD_EINVAL, "design regions are 2D only");
+    if (!eps_r || w < 1 || h < 1 || i0 < 1 || j0 < 1 || i0 + w > s->nx || j0 + h > s->ny)
+        return fail(c, FDTD_EINVAL, "design rectangle (%d, %d, %d, %d) must lie in 1..nx-1 x 1..ny-1", i0, j0, w, h);
+    const size_t n = (size_t)w * h;
+    std::vector<float4> co(n);
+    for (size_t q = 0; q < n; q++) {
+        const double sg = sigma ? sigma[q] : 0.0;
+        if (!(eps_r[q] > 0) || !(sg >= 0)) return fail(c, FDTD_EINVAL, "design cell %zu: eps_r must be > 0, sigma >= 0", q);
+        co[q] = e_coeffs(eps_r[q], sg, s->dt, s->dx, s->dy);
+    }
+    if (!s->d_dsg || s->dsg_w != w || s->dsg_h != h) {
+        dfree(s->d_dsg);
+        s->d_dsg = nullptr;
+        int rc = dalloc(c, &s->d_dsg, n * sizeof(float4), "design coefficients");
+        if (rc) return rc;
+    }
+    CK(cudaMemcpyAsync(s->d_dsg, co.data(), n * sizeof(float4), cudaMemcpyHostToDevice, c->stream), "upload design");
+    CK(cudaStreamSynchronize(c->stream), "upload design");
+    s->dsg_eps.assign(eps_r, eps_r + n);
+    s->dsg_i0 = i0; s->dsg_j0 = j0; s->dsg_w = w; s->dsg_h = h;
+    c->dirty = true;
+    graph_free(c);   // the edge-list weights hold the old coefficients
+    return FDTD_OK;
+}
+
 int fdtd_add_probe(fdtd_ctx* c, int i, int j, int k, int component, int* probe_id) {
     if (!c || !probe_id) return FDTD_EINVAL;
     if (c->dims == 3) return fdtd_add_probe3(c, i, j, k, component, probe_id);
@@ -613,14 +655,9 @@ int fdtd_step(fdtd_ctx* c, int64_t n_steps) {
     if (n_steps < 0) return fail(c, FDTD_EINVAL, "n_steps < 0");
     if (n_steps == 0) return FDTD_OK;
     if (c->dims == 3) return fdtd_step3(c, n_steps);
-    if (c->s2.empty()) return fail(c, FDTD_ESTATE, "no scene");
-    int rc = ensure_capacity(c, c->t + n_steps);
+    int rc = step_prepare(c, n_steps);
     if (rc) return rc;
     const int T = c->opt_tblock;
-    if (c->dirty || c->task_seg != c->opt_segment) {
-        rc = rebuild(c, T, c->opt_segment, c->opt_warps);
-        if (rc) return rc;
-    }
     int64_t left = n_steps;
     while (left > 0) {
         int done;

@@ -61,6 +61,7 @@ def lib():
         L.fdtd_get_option.argtypes = [vp, ip]
         L.fdtd_get_option.restype = i64
         L.fdtd_set_source.argtypes = [vp, ip, ip, ip, ip, ip, dp, vp, i64]
+        L.fdtd_set_design.argtypes = [vp, ip, ip, ip, ip, dp, dp]
         L.fdtd_add_probe.argtypes = [vp, ip, ip, ip, ip, C.POINTER(C.c_int)]
         L.fdtd_add_dft_monitor.argtypes = [vp, vp, ip, dp, ip, C.POINTER(C.c_int)]
         L.fdtd_add_dft_plane.argtypes = [vp, ip, ip, dp, ip, C.POINTER(C.c_int)]
@@ -220,6 +221,12 @@ class Simulation:
         else:
             self.set_source(src.kind, src.i, src.j, src.k, src.component, param=src.params[0])
 
+    def set_design(self, i0, j0, eps_r, sigma=None):
+        eps = np.ascontiguousarray(eps_r, np.float64)
+        h, w = eps.shape
+        sg = None if sigma is None else np.ascontiguousarray(sigma, np.float64).ctypes.data_as(C.POINTER(C.c_double))
+        self._check(self._L.fdtd_set_design(self._h, i0, j0, w, h, eps.ctypes.data_as(C.POINTER(C.c_double)), sg))
+
     def add_probe(self, i, j, k=0, component="ez") -> int:
         pid = C.c_int()
         self._check(self._L.fdtd_add_probe(self._h, i, j, k, COMP[component], C.byref(pid)))
@@ -324,6 +331,9 @@ def from_scene(scene, *, stream=None, probes=True, monitors=True, source=True) -
         sim._plane_ny, sim._plane_nx = scene.ny, scene.nx
     if source and scene.source is not None:
         sim.set_scene_source(scene.source)
+    if getattr(scene, "design", None) is not None:
+        i0, j0, w, h = scene.design
+        sim.set_design(i0, j0, scene.design_eps)
     sim.probe_ids = []
     if probes and getattr(scene, "probes", None) is not None:
         for p in scene.probes:
