@@ -190,7 +190,7 @@ def main():
     nsteps = args.nsteps or sc.nsteps
     stream = torch.cuda.current_stream()
     sim = fdtd.from_scene(sc, stream=stream)
-    tune = {"tblock": 4, "segment": 128, "warps": 2}
+    tune = {"tblock": 4, "segment": 64, "warps": 8}
     for k in ("tblock", "segment", "warps"):
         if getattr(args, k) is not None:
             tune[k] = getattr(args, k)

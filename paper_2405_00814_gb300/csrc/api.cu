@@ -242,11 +242,19 @@ fdtd_ctx* ctx_new(void* stream) {
     c->launches = 0;
     c->opt_kernel = 0;
     c->opt_tblock = 4;
-    c->opt_segment = 128;
-    c->opt_warps = 2;
+    c->opt_warps = 8;
+    c->opt_segment = 64;
     c->dirty = true;
     c->d_scenes = nullptr;
     c->d_tasks = nullptr;
+    c->d_tasks_b = nullptr;
+    c->n_tasks_b = 0;
+    c->warps_b = 2;
+    c->aux = nullptr;
+    c->ev_fork = c->ev_join = nullptr;
+    cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
+    cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     c->d_samp = nullptr;
     c->d_samp_scene = nullptr;
     c->d_samp_off = nullptr;
@@ -328,14 +336,17 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
         d.dsg_i0 = s->dsg_i0; d.dsg_j0 = s->dsg_j0; d.dsg_w = s->d_dsg ? s->dsg_w : 0; d.dsg_h = s->dsg_h;
         d.dsg_coef = s->d_dsg;
     }
-    // tasks: per scene, strips of 120 columns x segments of seg rows, padded to
-    // a whole number of CTAs so that a CTA never mixes scenes
+    // tasks: per scene, strips of 120 columns x segments of seg rows.  Tasks
+    // with a CPML slab or the design rectangle within reach go to the boundary
+    // list, the rest to the interior list; each list is padded to whole CTAs
+    // per scene so that a CTA never mixes scenes.
     const int wout = STRIP - 2 * HALO;
-    std::vector<Task> tasks;
+    std::vector<Task> tasks, tasks_b;
     std::vector<Sample2> tsamp;
+    const int warps_b = 2;
     for (int k = 0; k < ns; k++) {
         Scene2* s = c->s2[k];
-        const size_t first = tasks.size();
+        const size_t first = tasks.size(), first_b = tasks_b.size();
         for (int ya = 0; ya < s->ny; ya += seg) {
             const int yb = std::min(ya + seg, s->ny);
             for (int x0 = 0; x0 < s->nx; x0 += wout) {
@@ -357,15 +368,17 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
                 for (const Sample2& sp : s->samples)
                     if (sp.i >= x0 && sp.i < x0 + wout && sp.j >= ya && sp.j < yb) tsamp.push_back(sp);
                 t.samp_end = (int)tsamp.size();
-                tasks.push_back(t);
+                if (t.flags & (TASK_PML | TASK_DSG)) tasks_b.push_back(t);
+                else tasks.push_back(t);
             }
         }
-        while ((tasks.size() - first) % warps) {
-            Task t;
-            memset(&t, 0, sizeof(t));
-            t.scene = -1;
-            tasks.push_back(t);
-        }
+        Task pad;
+        memset(&pad, 0, sizeof(pad));
+        pad.scene = -1;
+        if (tasks.size() > first)
+            while ((tasks.size() - first) % warps) tasks.push_back(pad);
+        if (tasks_b.size() > first_b)
+            while ((tasks_b.size() - first_b) % warps_b) tasks_b.push_back(pad);
     }
     std::vector<Sample2> ssamp;
     std::vector<int> soff(ns + 1, 0);
@@ -373,16 +386,21 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
         for (const Sample2& sp : c->s2[k]->samples) ssamp.push_back(sp);
         soff[k + 1] = (int)ssamp.size();
     }
-    dfree(c->d_scenes); dfree(c->d_tasks); dfree(c->d_samp); dfree(c->d_samp_scene); dfree(c->d_samp_off);
-    c->d_scenes = nullptr; c->d_tasks = nullptr; c->d_samp = nullptr; c->d_samp_scene = nullptr; c->d_samp_off = nullptr;
+    dfree(c->d_scenes); dfree(c->d_tasks); dfree(c->d_tasks_b); dfree(c->d_samp); dfree(c->d_samp_scene); dfree(c->d_samp_off);
+    c->d_scenes = nullptr; c->d_tasks = nullptr; c->d_tasks_b = nullptr; c->d_samp = nullptr; c->d_samp_scene = nullptr;
+    c->d_samp_off = nullptr;
     int rc;
     if ((rc = dalloc(c, &c->d_scenes, dev.size() * sizeof(TmzDev), "scene descriptors"))) return rc;
     if ((rc = dalloc(c, &c->d_tasks, tasks.size() * sizeof(Task), "tasks"))) return rc;
+    if ((rc = dalloc(c, &c->d_tasks_b, tasks_b.size() * sizeof(Task), "tasks"))) return rc;
     if ((rc = dalloc(c, &c->d_samp, tsamp.size() * sizeof(Sample2), "samples"))) return rc;
     if ((rc = dalloc(c, &c->d_samp_scene, ssamp.size() * sizeof(Sample2), "samples"))) return rc;
     if ((rc = dalloc(c, &c->d_samp_off, soff.size() * sizeof(int), "sample offsets"))) return rc;
     CK(cudaMemcpyAsync(c->d_scenes, dev.data(), dev.size() * sizeof(TmzDev), cudaMemcpyHostToDevice, c->stream), "upload");
-    CK(cudaMemcpyAsync(c->d_tasks, tasks.data(), tasks.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
+    if (!tasks.empty())
+        CK(cudaMemcpyAsync(c->d_tasks, tasks.data(), tasks.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
+    if (!tasks_b.empty())
+        CK(cudaMemcpyAsync(c->d_tasks_b, tasks_b.data(), tasks_b.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
     if (!tsamp.empty())
         CK(cudaMemcpyAsync(c->d_samp, tsamp.data(), tsamp.size() * sizeof(Sample2), cudaMemcpyHostToDevice, c->stream), "upload");
     if (!ssamp.empty())
@@ -390,6 +408,8 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     CK(cudaMemcpyAsync(c->d_samp_off, soff.data(), soff.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream), "upload");
     CK(cudaStreamSynchronize(c->stream), "upload task list");
     c->n_tasks = (int)tasks.size();
+    c->n_tasks_b = (int)tasks_b.size();
+    c->warps_b = warps_b;
     c->task_tb = T;
     c->task_seg = seg;
     c->dirty = false;
@@ -487,7 +507,11 @@ void fdtd_destroy(fdtd_ctx* c) {
     }
     fdtd_destroy3(c);
     graph_free(c);
-    dfree(c->d_scenes); dfree(c->d_tasks); dfree(c->d_samp); dfree(c->d_samp_scene); dfree(c->d_samp_off);
+    dfree(c->d_scenes); dfree(c->d_tasks); dfree(c->d_tasks_b); dfree(c->d_samp); dfree(c->d_samp_scene);
+    dfree(c->d_samp_off);
+    if (c->aux) cudaStreamDestroy(c->aux);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
 }
 

@@ -137,6 +137,10 @@ struct fdtd_ctx {
     bool dirty;
     gem::TmzDev* d_scenes;
     gem::Task* d_tasks;
+    gem::Task* d_tasks_b;          // boundary tasks (CPML slab or design rectangle in reach)
+    int n_tasks_b, warps_b;
+    cudaStream_t aux;              // forked stream for the boundary tasks
+    cudaEvent_t ev_fork, ev_join;
     gem::Sample2* d_samp;          // samples in task order (fused kernel)
     gem::Sample2* d_samp_scene;    // samples in scene order (unfused kernels)
     int* d_samp_off;               // [n_scenes + 1] offsets into d_samp_scene
@@ -152,7 +156,7 @@ int tmz_fused_launch(fdtd_ctx* c, int T, int warps, long long n0, int parity);
 int tmz_naive_step(fdtd_ctx* c, long long n);
 int dft_cells_launch(fdtd_ctx* c, const DftMon& m, long long n0, int nsteps);
 int tmz_finite_check(fdtd_ctx* c, int* bad);
-size_t tmz_fused_smem(int T, int warps);
+size_t tmz_fused_smem(int T, int warps, bool pml);
 }  // namespace gem
 
 namespace gem {

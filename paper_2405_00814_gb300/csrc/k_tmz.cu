@@ -26,14 +26,20 @@
 
 namespace gem {
 
-constexpr int PF = 3;          // rows in flight per warp
-constexpr int NSLOT = 7;       // float4 slots per lane per stage: Ez Hx Hy pEzx pEzy pHxy pHyx
-constexpr int STAGE_F4 = NSLOT * 32 + 8;   // + 32 uint32 material words
+// Two variants share one body.  Boundary tasks (a CPML slab or a design
+// rectangle in reach) stage 7 float4 slots per lane per row -- Ez Hx Hy and
+// psi_Ezx psi_Ezy psi_Hxy psi_Hyx -- and keep PF_B rows in flight.  Interior
+// tasks stage only Ez Hx Hy and keep PF_I rows in flight, with a register cap
+// that lets four warps share each SM sub-partition.
+constexpr int PF_B = 3;
+constexpr int PF_I = 4;
+__host__ __device__ constexpr int pf_of(bool pml) { return pml ? PF_B : PF_I; }
+__host__ __device__ constexpr int nslot_of(bool pml) { return pml ? 7 : 3; }
+__host__ __device__ constexpr int stage_f4(bool pml) { return nslot_of(pml) * 32 + 8; }   // + 32 uint32 material words
+__host__ __device__ constexpr int stages_for(int T, bool pml) { return T + pf_of(pml); }
 
-__host__ __device__ constexpr int stages_for(int T) { return T + PF; }
-
-size_t tmz_fused_smem(int T, int warps) {
-    return (size_t)warps * stages_for(T) * STAGE_F4 * sizeof(float4);
+size_t tmz_fused_smem(int T, int warps, bool pml) {
+    return (size_t)warps * stages_for(T, pml) * stage_f4(pml) * sizeof(float4);
 }
 
 __device__ __forceinline__ size_t sidx(int pitch, int i, int j) {
@@ -90,12 +96,15 @@ struct Prof {
 // ===========================================================================
 // fused, temporally blocked kernel
 // ===========================================================================
-template <int T>
-__global__ void __launch_bounds__(256) k_tmz_fused(const TmzDev* __restrict__ scenes,
+template <int T, bool PML>
+__global__ void __launch_bounds__(256, PML ? 1 : 2) k_tmz_fused(const TmzDev* __restrict__ scenes,
                                                    const Task* __restrict__ tasks, int n_tasks,
                                                    const Sample2* __restrict__ samps, int parity,
                                                    long long n0) {
-    constexpr int Q = stages_for(T);
+    constexpr int PF = pf_of(PML);
+    constexpr int NSLOT = nslot_of(PML);
+    constexpr int STAGE_F4 = stage_f4(PML);
+    constexpr int Q = stages_for(T, PML);
     extern __shared__ float4 smem_f4[];
     __shared__ float4 coef_s[256];
 
@@ -130,7 +139,7 @@ __global__ void __launch_bounds__(256) k_tmz_fused(const TmzDev* __restrict__ sc
     const int r_last = tk.yb + T - 1;          // last row streamed
 
     // CPML: lanes whose columns touch an x-slab carry psi_Ezx / psi_Hyx
-    const bool pml = (tk.flags & TASK_PML) != 0;
+    const bool pml = PML && (tk.flags & TASK_PML) != 0;
     const int npml = S->has_pml;
     const Prof pr{S->prof, pitch, S->rows};
     bool lane_px = false;
@@ -150,7 +159,8 @@ __global__ void __launch_bounds__(256) k_tmz_fused(const TmzDev* __restrict__ sc
                          S->f[F_PHXY][parity ^ 1], S->f[F_PHYX][parity ^ 1]};
 
     // design rectangle (continuous permittivity)
-    const bool dsg = (tk.flags & TASK_DSG) != 0;
+    const bool dsg = PML && (tk.flags & TASK_DSG) != 0;
+    const bool has_samp = tk.samp_end > tk.samp_begin;
     // source
     const bool has_src = (tk.flags & TASK_SRC) != 0;
     const int src_j = S->src_j, src_d = S->src_i - cx;
@@ -165,7 +175,7 @@ __global__ void __launch_bounds__(256) k_tmz_fused(const TmzDev* __restrict__ sc
         cp_async16(st + 1 * 32 + lane, hx_in + g, true);
         cp_async16(st + 2 * 32 + lane, hy_in + g, true);
         cp_async4(reinterpret_cast<uint32_t*>(st + NSLOT * 32) + lane, mat + g);
-        if (pml) {
+        if constexpr (PML) if (pml) {
             const bool yrow = (row < npml) || (row >= ny - npml);
             if (lane_px) {
                 cp_async16(st + 3 * 32 + lane, psi_in[0] + g, true);
@@ -223,13 +233,13 @@ __global__ void __launch_bounds__(256) k_tmz_fused(const TmzDev* __restrict__ sc
         for (int t = 1; t <= T; t++) {
             const int a = r - t;
             if (a < s_row) continue;   // warp-uniform
-            float4* sta = stage0 + ((a - s_row) % Q) * STAGE_F4;
+            float4* sta = PML ? stage0 + ((a - s_row) % Q) * STAGE_F4 : stage0;
             // ---- layer 1: H at row a from Ez at level t-1 (rows a, a+1) ----
             const float4 e = E[t], eu = E[t - 1];
             const float er = __shfl_down_sync(0xffffffffu, e.x, 1);
             float4 dey = make_float4(eu.x - e.x, eu.y - e.y, eu.z - e.z, eu.w - e.w);
             float4 dex = make_float4(e.y - e.x, e.z - e.y, e.w - e.z, er - e.w);
-            if (pml) {
+            if constexpr (PML) if (pml) {
                 const int rs = a + PAD_Y;
                 if ((a < npml) || (a >= ny - npml)) {
                     const float b = pr.bHy(rs), c = pr.cHy(rs);
@@ -260,7 +270,7 @@ __global__ void __launch_bounds__(256) k_tmz_fused(const TmzDev* __restrict__ sc
             float4 dhy = make_float4(y.x - yl, y.y - y.x, y.z - y.y, y.w - y.z);
             float4 dhx = make_float4(X[t].x - X[t + 1].x, X[t].y - X[t + 1].y, X[t].z - X[t + 1].z,
                                      X[t].w - X[t + 1].w);
-            if (pml) {
+            if constexpr (PML) if (pml) {
                 const int rs = a + PAD_Y;
                 if ((a < npml) || (a >= ny - npml)) {
                     const float b = pr.bEy(rs), c = pr.cEy(rs);
@@ -285,7 +295,7 @@ __global__ void __launch_bounds__(256) k_tmz_fused(const TmzDev* __restrict__ sc
             const uint32_t m = M[t];
             float4 c0 = coef_s[m & 255u], c1 = coef_s[(m >> 8) & 255u];
             float4 c2 = coef_s[(m >> 16) & 255u], c3 = coef_s[m >> 24];
-            if (dsg) {
+            if constexpr (PML) if (dsg) {
                 const int dj = a - S->dsg_j0;
                 if (dj >= 0 && dj < S->dsg_h) {
                     const float4* drow = S->dsg_coef + (size_t)dj * S->dsg_w;
@@ -304,7 +314,7 @@ __global__ void __launch_bounds__(256) k_tmz_fused(const TmzDev* __restrict__ sc
             const long long n = n0 + (t - 1);   // this level makes E^{n+1}
             if (has_src && a == src_j && src_d >= 0 && src_d < 4 && n < S->src_len)
                 add4(E[t], src_d, wave[n]);
-            for (int q = tk.samp_begin; q < tk.samp_end; q++) {
+            if (has_samp) for (int q = tk.samp_begin; q < tk.samp_end; q++) {
                 const Sample2 sp = samps[q];
                 const int d = sp.i - cx;
                 if (sp.j == a && d >= 0 && d < 4) {
@@ -318,13 +328,14 @@ __global__ void __launch_bounds__(256) k_tmz_fused(const TmzDev* __restrict__ sc
         const int o = r - T;
         if (o >= tk.ya) {
             const float4* sto = stage0 + ((o - s_row) % Q) * STAGE_F4;
+            (void)sto;
             if (out_lane) {
                 const size_t g = (size_t)(o + PAD_Y) * pitch + cs;
                 if (cx + 3 < nx) {
                     *reinterpret_cast<float4*>(ez_out + g) = E[T];
                     *reinterpret_cast<float4*>(hx_out + g) = X[T];
                     *reinterpret_cast<float4*>(hy_out + g) = Y[T];
-                    if (pml) {
+                    if constexpr (PML) if (pml) {
                         if ((o < npml) || (o >= ny - npml)) {
                             *reinterpret_cast<float4*>(psi_out[1] + g) = sto[4 * 32 + lane];
                             *reinterpret_cast<float4*>(psi_out[2] + g) = sto[5 * 32 + lane];
@@ -335,8 +346,11 @@ __global__ void __launch_bounds__(256) k_tmz_fused(const TmzDev* __restrict__ sc
                         }
                     }
                 } else {
-                    const float4 p0 = sto[3 * 32 + lane], p1 = sto[4 * 32 + lane];
-                    const float4 p2 = sto[5 * 32 + lane], p3 = sto[6 * 32 + lane];
+                    float4 p0 = make_float4(0, 0, 0, 0), p1 = p0, p2 = p0, p3 = p0;
+                    if constexpr (PML) {
+                        p0 = sto[3 * 32 + lane]; p1 = sto[4 * 32 + lane];
+                        p2 = sto[5 * 32 + lane]; p3 = sto[6 * 32 + lane];
+                    }
                     const bool yrow = pml && ((o < npml) || (o >= ny - npml));
                     for (int c = 0; c < 4; c++) {
                         if (cx + c >= nx) break;
@@ -494,27 +508,50 @@ __global__ void k_tmz_finite(const TmzDev* __restrict__ scenes, int parity, int*
 // ===========================================================================
 // launchers
 // ===========================================================================
-template <int T>
-static cudaError_t launch_fused_T(fdtd_ctx* c, int warps, long long n0, int parity) {
-    const size_t smem = tmz_fused_smem(T, warps);
-    cudaError_t e = cudaFuncSetAttribute(k_tmz_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int T, bool PML>
+static cudaError_t launch_fused_T(const Task* tasks, int n_tasks, int warps, const fdtd_ctx* c, cudaStream_t st,
+                                  long long n0, int parity) {
+    const size_t smem = tmz_fused_smem(T, warps, PML);
+    cudaError_t e = cudaFuncSetAttribute(k_tmz_fused<T, PML>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int blocks = (c->n_tasks + warps - 1) / warps;
-    k_tmz_fused<T><<<blocks, warps * 32, smem, c->stream>>>(c->d_scenes, c->d_tasks, c->n_tasks, c->d_samp,
-                                                            parity, n0);
+    const int blocks = n_tasks / warps;   // task lists are padded to whole CTAs
+    k_tmz_fused<T, PML><<<blocks, warps * 32, smem, st>>>(c->d_scenes, tasks, n_tasks, c->d_samp, parity, n0);
     return cudaGetLastError();
 }
 
-int tmz_fused_launch(fdtd_ctx* c, int T, int warps, long long n0, int parity) {
-    cudaError_t e;
+template <bool PML>
+static cudaError_t launch_fused(const Task* tasks, int n_tasks, int warps, const fdtd_ctx* c, cudaStream_t st, int T,
+                                long long n0, int parity) {
     switch (T) {
-        case 1: e = launch_fused_T<1>(c, warps, n0, parity); break;
-        case 2: e = launch_fused_T<2>(c, warps, n0, parity); break;
-        case 3: e = launch_fused_T<3>(c, warps, n0, parity); break;
-        case 4: e = launch_fused_T<4>(c, warps, n0, parity); break;
-        default: return FDTD_EINVAL;
+        case 1: return launch_fused_T<1, PML>(tasks, n_tasks, warps, c, st, n0, parity);
+        case 2: return launch_fused_T<2, PML>(tasks, n_tasks, warps, c, st, n0, parity);
+        case 3: return launch_fused_T<3, PML>(tasks, n_tasks, warps, c, st, n0, parity);
+        case 4: return launch_fused_T<4, PML>(tasks, n_tasks, warps, c, st, n0, parity);
     }
-    c->launches++;
+    return cudaErrorInvalidValue;
+}
+
+// one T-step block: interior tasks on the context's stream, boundary tasks on
+// a forked stream, joined before the next block reads the new buffer
+int tmz_fused_launch(fdtd_ctx* c, int T, int warps, long long n0, int parity) {
+    cudaError_t e = cudaSuccess;
+    const bool both = c->n_tasks_b > 0 && c->n_tasks > 0;
+    if (both) {
+        e = cudaEventRecord(c->ev_fork, c->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
+    }
+    if (e == cudaSuccess && c->n_tasks_b > 0) {
+        e = launch_fused<true>(c->d_tasks_b, c->n_tasks_b, c->warps_b, c, both ? c->aux : c->stream, T, n0, parity);
+        c->launches++;
+    }
+    if (e == cudaSuccess && c->n_tasks > 0) {
+        e = launch_fused<false>(c->d_tasks, c->n_tasks, warps, c, c->stream, T, n0, parity);
+        c->launches++;
+    }
+    if (both && e == cudaSuccess) {
+        e = cudaEventRecord(c->ev_join, c->aux);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+    }
     if (e != cudaSuccess) {
         c->err = std::string("fused launch: ") + cudaGetErrorString(e);
         return FDTD_ECUDA;
