@@ -198,6 +198,33 @@ int fdtd_load_state(fdtd_ctx* ctx, const void* buf, size_t bytes);
 /* Returns FDTD_EUNSTABLE if any field of any scene is not finite. Synchronises. */
 int fdtd_check_finite(fdtd_ctx* ctx);
 
+/* Largest graph fdtd_mp_steps_noalloc accepts (nodes). */
+#define FDTD_MP_NOALLOC_MAX_NODES (1 << 22)
+
+/* Allocation-free message passing.  The paper has no counterpart to this
+ * entry point; it exists for callers that cannot allocate device memory -- a
+ * stream being captured into a CUDA graph, a host whose own allocator owns all
+ * device memory, or a real-time loop that cannot absorb the synchronisation of
+ * cudaMalloc/cudaFree.  It runs n_steps applications of h <- W2 (W1 h) for two
+ * layers given as CSR by destination (rowptr[n_nodes + 1], col and w per edge,
+ * as fdtd_export_graph lists them after sorting by destination), with every
+ * pointer a caller-allocated device pointer; h (n_nodes floats) is read and
+ * overwritten.  No soft source is applied.  The state between the layers lives
+ * in a fixed device array of FDTD_MP_NOALLOC_MAX_NODES floats (16 MiB) that
+ * every GPU loading the library keeps until the process exits; it never calls
+ * cudaMalloc, cudaFree or any allocating routine.  The first call on a device
+ * looks that array's address up (cudaGetSymbolAddress with the device
+ * current), so make the first call before any stream capture begins.  All
+ * calls share the array: calls that overlap on the GPU (different streams, or
+ * different host threads on one device) race and corrupt each other's results.
+ * Returns FDTD_EINVAL for NULL pointers, n_nodes < 1 or n_nodes larger than
+ * FDTD_MP_NOALLOC_MAX_NODES, n_steps < 0; FDTD_ECUDA if a launch fails.
+ * Work is enqueued on cuda_stream (NULL = legacy default stream); the call
+ * does not synchronise. */
+int fdtd_mp_steps_noalloc(const int32_t* rowptr1, const int32_t* col1, const float* w1, const int32_t* rowptr2,
+                          const int32_t* col2, const float* w2, float* h, int64_t n_nodes, int64_t n_steps,
+                          void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,6 +80,7 @@ def lib():
         L.fdtd_save_state.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
         L.fdtd_load_state.argtypes = [vp, vp, C.c_size_t]
         L.fdtd_check_finite.argtypes = [vp]
+        L.fdtd_mp_steps_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, i64, vp]
         _LIB = L
     return _LIB
 
@@ -321,6 +322,25 @@ class Simulation:
         self._check(self._L.fdtd_export_graph(self._h, layer, C.byref(nn), C.byref(ne), src.ctypes.data,
                                               dst.ctypes.data, w.ctypes.data))
         return nn.value, src, dst, w
+
+
+MP_NOALLOC_MAX_NODES = 1 << 22
+
+
+def mp_steps_noalloc(layer1, layer2, h, n_steps, stream=None):
+    """Allocation-free two-layer message passing (fdtd_mp_steps_noalloc).
+
+    layer1/layer2: (rowptr, col, w) CUDA tensors (int32, int32, float32); h:
+    CUDA float32 tensor of node values, updated in place.  For callers that
+    cannot allocate device memory (see the C header)."""
+    L = lib()
+    r1, c1, w1 = layer1
+    r2, c2, w2 = layer2
+    rc = L.fdtd_mp_steps_noalloc(r1.data_ptr(), c1.data_ptr(), w1.data_ptr(), r2.data_ptr(), c2.data_ptr(),
+                                 w2.data_ptr(), h.data_ptr(), int(h.numel()), int(n_steps), _stream_handle(stream))
+    if rc != OK:
+        raise FDTDError(rc, "fdtd_mp_steps_noalloc rejected its arguments or failed to launch"
+                        f" (n_nodes {h.numel()}, limit {MP_NOALLOC_MAX_NODES})")
 
 
 def from_scene(scene, *, stream=None, probes=True, monitors=True, source=True) -> Simulation:
