@@ -190,7 +190,7 @@ def main():
     nsteps = args.nsteps or sc.nsteps
     stream = torch.cuda.current_stream()
     sim = fdtd.from_scene(sc, stream=stream)
-    tune = {"tblock": 4, "segment": 64, "warps": 8}
+    tune = {"tblock": 4, "segment": 24, "warps": 8}
     for k in ("tblock", "segment", "warps"):
         if getattr(args, k) is not None:
             tune[k] = getattr(args, k)
@@ -246,7 +246,8 @@ def main():
     traffic = _traffic_record()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": f"k_tmz_fused<{T}>" if args.kernel == 0 else "k_tmz_h + k_tmz_e",
+                "kernel": (f"k_tmz_interior<{T}> + k_tmz_fused<{T},1> (one T-step block, run concurrently)"
+                           if args.kernel == 0 else "k_tmz_h + k_tmz_e"),
                 "unit_bytes": "25 B per grid cell per launch (each launch advances every cell T steps)"}
     hbm_frac_cu = value / world * BYTES_PER_CU / (peak * 1e9)
 

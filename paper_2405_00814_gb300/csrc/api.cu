@@ -347,29 +347,49 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     for (int k = 0; k < ns; k++) {
         Scene2* s = c->s2[k];
         const size_t first = tasks.size(), first_b = tasks_b.size();
+        // Tasks with a CPML slab, the design rectangle, the source or a probe in
+        // reach, or a ragged right edge, run the general kernel ("boundary" list);
+        // the rest run the lean interior kernel.  General warps are heavier per
+        // row, so they get half-height segments.
+        const int seg_b = std::max(8, seg / 2);
+        auto flags_of = [&](int x0, int ya, int yb, bool* general) {
+            int f = 0;
+            const int lx0 = x0 - HALO, lx1 = x0 - HALO + STRIP;   // loaded columns
+            const int ly0 = ya - MAX_TB, ly1 = yb + MAX_TB;        // widest streamed rows
+            if (s->npml > 0 && (lx0 < s->npml || lx1 > s->nx - s->npml || ly0 < s->npml || ly1 > s->ny - s->npml))
+                f |= TASK_PML;
+            if (s->src_kind >= 0 && s->src_i >= lx0 && s->src_i < lx1 && s->src_j >= ly0 && s->src_j < ly1)
+                f |= TASK_SRC;
+            if (s->d_dsg && s->dsg_i0 < lx1 && s->dsg_i0 + s->dsg_w > lx0 && s->dsg_j0 < ly1 && s->dsg_j0 + s->dsg_h > ly0)
+                f |= TASK_DSG;
+            bool samp = false;
+            for (const Sample2& sp : s->samples)
+                if (sp.i >= x0 && sp.i < x0 + wout && sp.j >= ya && sp.j < yb) samp = true;
+            *general = f != 0 || samp || x0 + wout > s->nx;
+            return f;
+        };
+        auto add_task = [&](int x0, int ya, int yb) {
+            Task t;
+            bool general;
+            t.scene = k; t.x0 = x0; t.ya = ya; t.yb = yb; t.pad = 0;
+            t.flags = flags_of(x0, ya, yb, &general);
+            t.samp_begin = (int)tsamp.size();
+            for (const Sample2& sp : s->samples)
+                if (sp.i >= x0 && sp.i < x0 + wout && sp.j >= ya && sp.j < yb) tsamp.push_back(sp);
+            t.samp_end = (int)tsamp.size();
+            if (general) tasks_b.push_back(t);
+            else tasks.push_back(t);
+        };
         for (int ya = 0; ya < s->ny; ya += seg) {
             const int yb = std::min(ya + seg, s->ny);
             for (int x0 = 0; x0 < s->nx; x0 += wout) {
-                Task t;
-                t.scene = k; t.x0 = x0; t.ya = ya; t.yb = yb; t.flags = 0; t.pad = 0;
-                const int lx0 = x0 - HALO, lx1 = x0 - HALO + STRIP;   // loaded columns
-                const int ly0 = ya - MAX_TB, ly1 = yb + MAX_TB;        // widest streamed rows
-                if (s->npml > 0) {
-                    const bool xs = lx0 < s->npml || lx1 > s->nx - s->npml;
-                    const bool ys = ly0 < s->npml || ly1 > s->ny - s->npml;
-                    if (xs || ys) t.flags |= TASK_PML;
+                bool general;
+                flags_of(x0, ya, yb, &general);
+                if (!general) {
+                    add_task(x0, ya, yb);
+                } else {
+                    for (int y = ya; y < yb; y += seg_b) add_task(x0, y, std::min(y + seg_b, yb));
                 }
-                if (s->src_kind >= 0 && s->src_i >= lx0 && s->src_i < lx1 && s->src_j >= ly0 && s->src_j < ly1)
-                    t.flags |= TASK_SRC;
-                if (s->d_dsg && s->dsg_i0 < lx1 && s->dsg_i0 + s->dsg_w > lx0 && s->dsg_j0 < ly1 &&
-                    s->dsg_j0 + s->dsg_h > ly0)
-                    t.flags |= TASK_DSG;
-                t.samp_begin = (int)tsamp.size();
-                for (const Sample2& sp : s->samples)
-                    if (sp.i >= x0 && sp.i < x0 + wout && sp.j >= ya && sp.j < yb) tsamp.push_back(sp);
-                t.samp_end = (int)tsamp.size();
-                if (t.flags & (TASK_PML | TASK_DSG)) tasks_b.push_back(t);
-                else tasks.push_back(t);
             }
         }
         Task pad;

@@ -31,12 +31,14 @@ namespace gem {
 // psi_Ezx psi_Ezy psi_Hxy psi_Hyx -- and keep PF_B rows in flight.  Interior
 // tasks stage only Ez Hx Hy and keep PF_I rows in flight, with a register cap
 // that lets four warps share each SM sub-partition.
+// Interior warps always hold Q_I = 8 stages (a power of two, so the stage of a
+// row is a mask) with 8 - T rows in flight.
 constexpr int PF_B = 3;
-constexpr int PF_I = 4;
-__host__ __device__ constexpr int pf_of(bool pml) { return pml ? PF_B : PF_I; }
+constexpr int Q_I = 8;
 __host__ __device__ constexpr int nslot_of(bool pml) { return pml ? 7 : 3; }
 __host__ __device__ constexpr int stage_f4(bool pml) { return nslot_of(pml) * 32 + 8; }   // + 32 uint32 material words
-__host__ __device__ constexpr int stages_for(int T, bool pml) { return T + pf_of(pml); }
+__host__ __device__ constexpr int stages_for(int T, bool pml) { return pml ? T + PF_B : Q_I; }
+__host__ __device__ constexpr int pf_of(int T, bool pml) { return pml ? PF_B : Q_I - T; }
 
 size_t tmz_fused_smem(int T, int warps, bool pml) {
     return (size_t)warps * stages_for(T, pml) * stage_f4(pml) * sizeof(float4);
@@ -101,7 +103,7 @@ __global__ void __launch_bounds__(256, PML ? 1 : 2) k_tmz_fused(const TmzDev* __
                                                    const Task* __restrict__ tasks, int n_tasks,
                                                    const Sample2* __restrict__ samps, int parity,
                                                    long long n0) {
-    constexpr int PF = pf_of(PML);
+    constexpr int PF = pf_of(T, PML);
     constexpr int NSLOT = nslot_of(PML);
     constexpr int STAGE_F4 = stage_f4(PML);
     constexpr int Q = stages_for(T, PML);
@@ -210,6 +212,7 @@ __global__ void __launch_bounds__(256, PML ? 1 : 2) k_tmz_fused(const TmzDev* __
     float* rec = S->rec;
     const int n_rec = S->n_rec;
 
+#pragma unroll 2
     for (int r = s_row; r <= r_last; ++r) {
         cp_wait<PF - 1>();
         // shift the ring and take row r from its stage
@@ -377,6 +380,144 @@ __global__ void __launch_bounds__(256, PML ? 1 : 2) k_tmz_fused(const TmzDev* __
 }
 
 // ===========================================================================
+// interior kernel: tasks with no CPML slab, design rectangle, source or probe in
+// reach and all 120 output columns inside the grid (every other task runs the
+// general kernel above).  Same wavefront; the steady-state loop body has no
+// data-dependent branches.
+// ===========================================================================
+template <int T>
+struct Ring {
+    float4 E[T + 1], X[T + 2], Y[T + 1];
+    uint32_t M[T + 1];
+};
+
+template <int T>
+__device__ __forceinline__ void ring_shift_in(Ring<T>& R, const float4* st, int lane) {
+#pragma unroll
+    for (int k = T + 1; k >= 1; k--) R.X[k] = R.X[k - 1];
+#pragma unroll
+    for (int k = T; k >= 1; k--) {
+        R.E[k] = R.E[k - 1];
+        R.Y[k] = R.Y[k - 1];
+        R.M[k] = R.M[k - 1];
+    }
+    R.E[0] = st[0 * 32 + lane];
+    R.X[0] = st[1 * 32 + lane];
+    R.Y[0] = st[2 * 32 + lane];
+    R.M[0] = reinterpret_cast<const uint32_t*>(st + 3 * 32)[lane];
+}
+
+// one level t (H then E) on ring slot t
+template <int T>
+__device__ __forceinline__ void level(Ring<T>& R, int t, float dbx, float dby, const float4* coef_s) {
+    const float4 e = R.E[t], eu = R.E[t - 1];
+    const float er = __shfl_down_sync(0xffffffffu, e.x, 1);
+    R.X[t].x -= dby * (eu.x - e.x);
+    R.X[t].y -= dby * (eu.y - e.y);
+    R.X[t].z -= dby * (eu.z - e.z);
+    R.X[t].w -= dby * (eu.w - e.w);
+    R.Y[t].x += dbx * (e.y - e.x);
+    R.Y[t].y += dbx * (e.z - e.y);
+    R.Y[t].z += dbx * (e.w - e.z);
+    R.Y[t].w += dbx * (er - e.w);
+    const float4 y = R.Y[t];
+    const float yl = __shfl_up_sync(0xffffffffu, y.w, 1);
+    const uint32_t m = R.M[t];
+    const float4 c0 = coef_s[m & 255u], c1 = coef_s[(m >> 8) & 255u];
+    const float4 c2 = coef_s[(m >> 16) & 255u], c3 = coef_s[m >> 24];
+    R.E[t].x = e_upd(e.x, y.x - yl, R.X[t].x - R.X[t + 1].x, c0);
+    R.E[t].y = e_upd(e.y, y.y - y.x, R.X[t].y - R.X[t + 1].y, c1);
+    R.E[t].z = e_upd(e.z, y.z - y.y, R.X[t].z - R.X[t + 1].z, c2);
+    R.E[t].w = e_upd(e.w, y.w - y.z, R.X[t].w - R.X[t + 1].w, c3);
+}
+
+template <int T>
+__global__ void __launch_bounds__(256, 2) k_tmz_interior(const TmzDev* __restrict__ scenes,
+                                                        const Task* __restrict__ tasks, int n_tasks,
+                                                        int parity) {
+    constexpr int PF = pf_of(T, false);
+    constexpr int SF4 = stage_f4(false);
+    constexpr int Q = stages_for(T, false);
+    static_assert((Q & (Q - 1)) == 0, "interior stage count must be a power of two");
+    extern __shared__ float4 smem_f4[];
+    __shared__ float4 coef_s[256];
+
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int warps = blockDim.x >> 5;
+    const int tid = blockIdx.x * warps + wib;
+    const TmzDev* S = scenes + tasks[blockIdx.x * warps].scene;
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) coef_s[k] = S->coef[k];
+    __syncthreads();
+    if (tid >= n_tasks) return;
+    const Task tk = tasks[tid];
+    if (tk.scene < 0) return;
+
+    const int pitch = S->pitch;
+    const float* __restrict__ ez_in = S->f[F_EZ][parity];
+    const float* __restrict__ hx_in = S->f[F_HX][parity];
+    const float* __restrict__ hy_in = S->f[F_HY][parity];
+    float* __restrict__ ez_out = S->f[F_EZ][parity ^ 1];
+    float* __restrict__ hx_out = S->f[F_HX][parity ^ 1];
+    float* __restrict__ hy_out = S->f[F_HY][parity ^ 1];
+    const uint8_t* __restrict__ mat = S->mat;
+    const float dbx = S->dbx, dby = S->dby;
+
+    const int cx = tk.x0 - HALO + 4 * lane;
+    const int cs = cx + PAD_X;
+    const bool out_lane = (lane >= HALO / 4) && (lane < 32 - HALO / 4);
+    const int s_row = tk.ya - T;
+    const int r_last = tk.yb + T - 1;
+    float4* stage0 = smem_f4 + (size_t)wib * Q * SF4;
+    // rows past r_last are still inside the pad rows: the prefetch never needs a guard
+    auto issue = [&](int row) {
+        float4* st = stage0 + ((row - s_row) & (Q - 1)) * SF4;
+        const size_t g = (size_t)(row + PAD_Y) * pitch + cs;
+        cp_async16(st + 0 * 32 + lane, ez_in + g, true);
+        cp_async16(st + 1 * 32 + lane, hx_in + g, true);
+        cp_async16(st + 2 * 32 + lane, hy_in + g, true);
+        cp_async4(reinterpret_cast<uint32_t*>(st + 3 * 32) + lane, mat + g);
+    };
+
+    Ring<T> R;
+#pragma unroll
+    for (int k = 0; k < T + 1; k++) {
+        R.E[k] = make_float4(0, 0, 0, 0);
+        R.Y[k] = R.E[k];
+        R.M[k] = 0;
+    }
+#pragma unroll
+    for (int k = 0; k < T + 2; k++) R.X[k] = make_float4(0, 0, 0, 0);
+#pragma unroll
+    for (int k = 0; k < PF; k++) {
+        issue(s_row + k);
+        cp_commit();
+    }
+    // Every level runs on every streamed row, also below the first one (on the
+    // zero-initialised ring): those values are wrong but finite, and wrongness
+    // climbs one row per level, so rows >= ya are exact after T levels.  The
+    // first T steady rows are not stored.
+    const int r_steady = tk.ya + T;
+    for (int r = s_row; r <= r_last; ++r) {
+        cp_wait<PF - 1>();
+        ring_shift_in<T>(R, stage0 + ((r - s_row) & (Q - 1)) * SF4, lane);
+#pragma unroll
+        for (int t = 1; t <= T; t++) level<T>(R, t, dbx, dby, coef_s);
+        if (r >= r_steady) {
+            const size_t g = (size_t)(r - T + PAD_Y) * pitch + cs;
+            if (out_lane) {
+                *reinterpret_cast<float4*>(ez_out + g) = R.E[T];
+                *reinterpret_cast<float4*>(hx_out + g) = R.X[T];
+                *reinterpret_cast<float4*>(hy_out + g) = R.Y[T];
+            }
+        }
+        issue(r + PF);
+        cp_commit();
+    }
+    cp_wait<0>();
+}
+
+// ===========================================================================
 // unfused pair: one H launch, one E launch, one source/record launch per step
 // ===========================================================================
 __global__ void k_tmz_h(const TmzDev* __restrict__ scenes, int parity) {
@@ -512,10 +653,16 @@ template <int T, bool PML>
 static cudaError_t launch_fused_T(const Task* tasks, int n_tasks, int warps, const fdtd_ctx* c, cudaStream_t st,
                                   long long n0, int parity) {
     const size_t smem = tmz_fused_smem(T, warps, PML);
-    cudaError_t e = cudaFuncSetAttribute(k_tmz_fused<T, PML>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     const int blocks = n_tasks / warps;   // task lists are padded to whole CTAs
-    k_tmz_fused<T, PML><<<blocks, warps * 32, smem, st>>>(c->d_scenes, tasks, n_tasks, c->d_samp, parity, n0);
+    if (PML) {
+        cudaError_t e = cudaFuncSetAttribute(k_tmz_fused<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_tmz_fused<T, true><<<blocks, warps * 32, smem, st>>>(c->d_scenes, tasks, n_tasks, c->d_samp, parity, n0);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_tmz_interior<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_tmz_interior<T><<<blocks, warps * 32, smem, st>>>(c->d_scenes, tasks, n_tasks, parity);
+    }
     return cudaGetLastError();
 }
 
