@@ -121,6 +121,39 @@ def cpu_baseline(sc, budget_s=12.0):
             "kind": "oracle", "sample": f"{steps} leapfrog steps of the full {sc.nx}x{sc.ny} scene (FP64, OpenMP over rows)"}
 
 
+def adjoint_ratio(stream, reps=2):
+    """Time of one adjoint gradient (forward with checkpoints every 100 steps +
+    reverse sweep) over the time of one plain forward solve, on the 1024^2
+    inverse-design workload (8 designs, 256^2 design regions, 8 monitors,
+    3000 steps)."""
+    import numpy as np
+    import torch
+    from paper_2405_00814_gb300 import autograd, scenes
+    scs = scenes.adjoint_scenes()
+    eps = np.stack([s.design_eps for s in scs])
+    plain = autograd.DesignBatch(scs, ckpt_every=0, stream=stream)
+    ckpt = autograd.DesignBatch(scs, ckpt_every=100, stream=stream)
+
+    def t_of(fn):
+        best = None
+        for _ in range(reps + 1):          # first run warms up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        return best
+    t_fwd = t_of(lambda: plain.forward(eps))
+    t_grad = t_of(lambda: ckpt.gradient(2.0 * ckpt.forward(eps)))
+    plain.close()
+    ckpt.close()
+    cu = scs[0].cells * len(scs) * scs[0].nsteps
+    return {"workload": "adjoint_tmz2d_1024x1024_x8designs_3000steps_ckpt100", "forward_ms": 1e3 * t_fwd,
+            "gradient_ms": 1e3 * t_grad, "ratio": t_grad / t_fwd, "forward_cups": cu / t_fwd,
+            "timing": "host wall clock around synchronised calls, best of %d after one warm-up" % reps}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -165,6 +198,7 @@ def main():
     ap.add_argument("--nsteps", type=int, default=None, help="leapfrog steps per solve (default: the workload's 4000)")
     ap.add_argument("--size", type=int, default=4096, help="grid side (profiling runs use smaller sides)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the adjoint-ratio measurement")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -286,6 +320,8 @@ def main():
         e2e_s = time.perf_counter() - t0
         out["e2e"] = {"value": cell_updates * e2e_steps * world / e2e_s, "unit": "cell-updates/s",
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    if not args.no_extras:
+        out["adjoint"] = adjoint_ratio(stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sc, args.cpu_budget)
     if rank == 0:

@@ -198,6 +198,29 @@ int fdtd_load_state(fdtd_ctx* ctx, const void* buf, size_t bytes);
 /* Returns FDTD_EUNSTABLE if any field of any scene is not finite. Synchronises. */
 int fdtd_check_finite(fdtd_ctx* ctx);
 
+/* Reverse mode (2D).  The paper notes that message-passing layers are
+ * differentiable (Sec. III-A); these calls compute the discrete adjoint of the
+ * two layers of Prop. 2 -- the transposed layers in reverse time order.
+ *
+ * fdtd_set_checkpointing: from now on, fdtd_step saves the full state of every
+ * scene (fields and CPML auxiliaries) whenever the step count is a multiple of
+ * `every` (0 turns it off and frees the checkpoints).  Checkpoints live in
+ * device memory owned by the context. */
+int fdtd_set_checkpointing(fdtd_ctx* ctx, int every);
+
+/* Gradient of a real loss L(F) of the running DFTs with respect to eps_r over
+ * every scene's design rectangle (fdtd_set_design), after a forward run of N
+ * steps from reset with checkpointing on.  dLdF_re/dLdF_im: dL/dRe F and dL/dIm F
+ * for every cell DFT monitor in creation order, [n_cells][n_freq] each,
+ * concatenated (host).  The adjoint source at a monitor cell for step n is
+ * sum_f (dL/dRe F cos(2 pi f (n+1) dt) - dL/dIm F sin(2 pi f (n+1) dt)) dt.
+ * Segments between checkpoints are recomputed newest first (recording E^n and
+ * curl H^{n+1/2} over the design cells), then reversed.  grad receives
+ * dL/deps_r as [scene][h][w] floats (host, or device when on_device != 0).
+ * The fields are left in an unspecified state: call fdtd_reset before the next
+ * forward run. */
+int fdtd_adjoint_grad(fdtd_ctx* ctx, const float* dLdF_re, const float* dLdF_im, float* grad, int on_device);
+
 /* Largest graph fdtd_mp_steps_noalloc accepts (nodes). */
 #define FDTD_MP_NOALLOC_MAX_NODES (1 << 22)
 

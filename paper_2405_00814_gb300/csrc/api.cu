@@ -261,6 +261,7 @@ fdtd_ctx* ctx_new(void* stream) {
     c->n_tasks = 0;
     c->task_tb = c->task_seg = -1;
     c->graph = nullptr;
+    c->adj = nullptr;
     return c;
 }
 
@@ -527,6 +528,7 @@ void fdtd_destroy(fdtd_ctx* c) {
     }
     fdtd_destroy3(c);
     graph_free(c);
+    adj_free(c);
     dfree(c->d_scenes); dfree(c->d_tasks); dfree(c->d_tasks_b); dfree(c->d_samp); dfree(c->d_samp_scene);
     dfree(c->d_samp_off);
     if (c->aux) cudaStreamDestroy(c->aux);
@@ -620,6 +622,8 @@ int fdtd_set_design(fdtd_ctx* c, int i0, int j0, int w, int h, const double* eps
     CK(cudaMemcpyAsync(s->d_dsg, co.data(), n * sizeof(float4), cudaMemcpyHostToDevice, c->stream), "upload design");
     CK(cudaStreamSynchronize(c->stream), "upload design");
     s->dsg_eps.assign(eps_r, eps_r + n);
+    if (sigma) s->dsg_sig.assign(sigma, sigma + n);
+    else s->dsg_sig.clear();
     s->dsg_i0 = i0; s->dsg_j0 = j0; s->dsg_w = w; s->dsg_h = h;
     c->dirty = true;
     graph_free(c);   // the edge-list weights hold the old coefficients
@@ -705,11 +709,14 @@ int fdtd_step(fdtd_ctx* c, int64_t n_steps) {
     int64_t left = n_steps;
     while (left > 0) {
         int done;
+        rc = adj_checkpoint_if_due(c);
+        if (rc) return rc;
         if (c->opt_kernel == 1) {
             rc = tmz_naive_step(c, c->t);
             done = 1;
         } else {
-            done = (int)std::min<int64_t>(T, left);
+            // a T-step block never crosses a checkpoint boundary
+            done = (int)std::min<int64_t>(std::min<int64_t>(T, left), adj_next_boundary(c, c->t));
             rc = tmz_fused_launch(c, done, c->opt_warps, c->t, c->parity);
             c->parity ^= 1;
         }

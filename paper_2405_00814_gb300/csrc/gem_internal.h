@@ -57,6 +57,16 @@ struct TmzDev {
     // continuous-permittivity design rectangle (overrides the table inside it)
     int dsg_i0, dsg_j0, dsg_w, dsg_h;   // dsg_w == 0: none
     const float4* dsg_coef;             // [dsg_h][dsg_w] (Ca, Cb/dx, Cb/dy, Cb)
+    // reverse mode: forward recompute records E^n and curl H^{n+1/2} over the
+    // design rectangle; the adjoint kernels read them, inject dL/dE^{n+1} at the
+    // monitor cells and accumulate dL/deps_r
+    float* dsg_rec;                     // [steps][2][dsg_h * dsg_w], step n at n - dsg_rec_n0
+    long long dsg_rec_n0, dsg_rec_len;
+    const float2* dsg_dcoef;            // [dsg_h][dsg_w] (dCa/deps_r, dCb/deps_r)
+    float* grad;                        // [dsg_h][dsg_w]
+    const float* adj_src;               // [steps][n_adj]: dL/dE^{n+1} at adjoint source cells
+    int n_adj;
+    float rdx, rdy;                     // 1/dx, 1/dy
 };
 
 // one warp's work in the fused kernel: columns [x0, x0 + STRIP - 2 HALO) and
@@ -112,7 +122,7 @@ struct Scene2 {
     // design rectangle
     int dsg_i0, dsg_j0, dsg_w, dsg_h;
     float4* d_dsg;
-    std::vector<double> dsg_eps;
+    std::vector<double> dsg_eps, dsg_sig;
 };
 
 }  // namespace gem
@@ -148,6 +158,8 @@ struct fdtd_ctx {
     int task_tb, task_seg;     // tblock/segment the task list was built for
     // edge-list path
     void* graph;
+    // reverse mode (k_adjoint.cu): checkpoints of the forward run
+    void* adj;
 };
 
 namespace gem {
@@ -180,4 +192,8 @@ int fdtd_load_state3(fdtd_ctx* c, const void* buf, size_t bytes);
 int fdtd_check_finite3(fdtd_ctx* c);
 // literal edge-list path (k_graph.cu)
 void graph_free(fdtd_ctx* c);
+// reverse mode (k_adjoint.cu)
+int adj_checkpoint_if_due(fdtd_ctx* c);
+int adj_next_boundary(const fdtd_ctx* c, int64_t t);
+void adj_free(fdtd_ctx* c);
 }  // namespace gem

@@ -1,0 +1,813 @@
+// Reverse mode of the 2D leapfrog recurrence: d L / d eps_r over a design
+// rectangle for losses of the running DFT at monitor cells.
+//
+// The paper only remarks that message-passing layers are differentiable
+// (Sec. III-A); this is the discrete adjoint of Prop. 2's two layers: the
+// transposed layers in reverse order.  With the adjoint state (e, hx, hy, psi)
+// holding dL/d(state) after a step, one reverse step is
+//   layer 2 transposed:  gx = (Cb/dx)(1 + cEx) e + cEx psi_ezx,
+//                        gy = -(Cb/dy)(1 + cEy) e + cEy psi_ezy,
+//                        hy(i) += gx(i) - gx(i+1),  hx(j) += gy(j) - gy(j+1),
+//                        psi_ezx <- bEx (psi_ezx + (Cb/dx) e),
+//                        psi_ezy <- bEy (psi_ezy - (Cb/dy) e),  e <- Ca e;
+//   layer 1 transposed:  fx = Db_x (1 + cHx) hy + cHx psi_hyx,
+//                        fy = -Db_y (1 + cHy) hx + cHy psi_hxy,
+//                        e(i,j) += fy(j-1) - fy(j) + fx(i-1) - fx(i),
+//                        psi_hxy <- bHy (psi_hxy - Db_y hx), psi_hyx <- bHx (psi_hyx + Db_x hy),
+// after dL/dE^{n+1} is added at the monitor cells and
+//   dL/deps_r += e (dCa/deps_r E^n + dCb/deps_r curlH^{n+1/2})
+// is accumulated over the design cells from the recomputed forward values.
+//
+// The kernel streams rows like the forward kernel: layer 2 transposed at row a
+// reads row a+1 at the previous level (the same-iteration ring slot), layer 1
+// transposed reads row a-1 at the same level (previous iteration), so the same
+// skewed wavefront applies T reverse steps per HBM pass.  gy of the row above
+// is produced at the end of the previous level (no second coefficient lookup);
+// the general variant keeps fy of the row below in a per-level register ring
+// because that row's psi_hxy has already moved on.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "gem_internal.h"
+
+namespace gem {
+
+int step_prepare(fdtd_ctx* c, int64_t n_steps);
+size_t tmz_fused_smem(int T, int warps, bool pml);
+
+namespace {
+
+constexpr int A_PF_G = 3;
+constexpr int A_Q_I = 8;
+
+__host__ __device__ constexpr int a_nslot(bool gen) { return gen ? 7 : 3; }
+__host__ __device__ constexpr int a_stage_f4(bool gen) { return a_nslot(gen) * 32 + 8; }
+__host__ __device__ constexpr int a_stages(int T, bool gen) { return gen ? T + A_PF_G : A_Q_I; }
+__host__ __device__ constexpr int a_pf(int T, bool gen) { return gen ? A_PF_G : A_Q_I - T; }
+
+size_t adj_smem(int T, int warps, bool gen) { return (size_t)warps * a_stages(T, gen) * a_stage_f4(gen) * sizeof(float4); }
+
+__device__ __forceinline__ void acp16(void* smem, const void* gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void acp4(void* smem, const void* gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void acommit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void await_() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ float& cref(float4& v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w)); }
+__device__ __forceinline__ float cget(const float4& v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w)); }
+
+// Adjoint source entry of a task: cell (i, j) gets adj_src[n * n_adj + slot].
+// Reuses Sample2 {i, j, comp (unused), slot}.
+
+template <int T, bool GEN>
+__global__ void __launch_bounds__(256, GEN ? 1 : 2) k_adj(const TmzDev* __restrict__ scenes,
+                                                          const Task* __restrict__ tasks, int n_tasks,
+                                                          const Sample2* __restrict__ srcs, int parity,
+                                                          long long n_top) {
+    constexpr int Q = a_stages(T, GEN);
+    constexpr int PF = a_pf(T, GEN);
+    constexpr int SF4 = a_stage_f4(GEN);
+    constexpr int NS = a_nslot(GEN);
+    extern __shared__ float4 smem_f4[];
+    __shared__ float4 coef_s[256];
+
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int warps = blockDim.x >> 5;
+    const int tid = blockIdx.x * warps + wib;
+    const TmzDev* S = scenes + tasks[blockIdx.x * warps].scene;
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) coef_s[k] = S->coef[k];
+    __syncthreads();
+    if (tid >= n_tasks) return;
+    const Task tk = tasks[tid];
+    if (tk.scene < 0) return;
+
+    const int pitch = S->pitch, nx = S->nx, ny = S->ny;
+    const float* __restrict__ e_in = S->f[F_EZ][parity];
+    const float* __restrict__ hx_in = S->f[F_HX][parity];
+    const float* __restrict__ hy_in = S->f[F_HY][parity];
+    float* __restrict__ e_out = S->f[F_EZ][parity ^ 1];
+    float* __restrict__ hx_out = S->f[F_HX][parity ^ 1];
+    float* __restrict__ hy_out = S->f[F_HY][parity ^ 1];
+    const uint8_t* __restrict__ mat = S->mat;
+    const float dbx = S->dbx, dby = S->dby;
+
+    const int cx = tk.x0 - HALO + 4 * lane;
+    const int cs = cx + PAD_X;
+    const bool out_lane = (lane >= HALO / 4) && (lane < 32 - HALO / 4) && (cx < nx);
+    const int s_row = tk.ya - T;
+    const int r_last = tk.yb + T - 1;
+
+    const bool pml = GEN && (tk.flags & TASK_PML) != 0;
+    const bool dsg = GEN && (tk.flags & TASK_DSG) != 0;
+    const bool has_src = GEN && tk.samp_end > tk.samp_begin;
+    const int npml = S->has_pml;
+    const float* pr = S->prof;
+    const int prow = S->rows;
+    bool lane_px = false;
+    float bex[4] = {0, 0, 0, 0}, cex[4] = {0, 0, 0, 0}, bhx[4] = {0, 0, 0, 0}, chx[4] = {0, 0, 0, 0};
+    if (GEN && pml) {
+        lane_px = (cx < npml) || (cx + 3 >= nx - npml);
+        if (lane_px)
+            for (int q = 0; q < 4; q++) {
+                bex[q] = pr[cs + q];
+                cex[q] = pr[pitch + cs + q];
+                bhx[q] = pr[2 * pitch + cs + q];
+                chx[q] = pr[3 * pitch + cs + q];
+            }
+    }
+    float* psi_in[4] = {S->f[F_PEZX][parity], S->f[F_PEZY][parity], S->f[F_PHXY][parity], S->f[F_PHYX][parity]};
+    float* psi_out[4] = {S->f[F_PEZX][parity ^ 1], S->f[F_PEZY][parity ^ 1], S->f[F_PHXY][parity ^ 1],
+                         S->f[F_PHYX][parity ^ 1]};
+
+    float4* stage0 = smem_f4 + (size_t)wib * Q * SF4;
+    auto stage_of = [&](int row) { return stage0 + ((row - s_row) % Q) * SF4; };
+    auto yslab = [&](int row) { return (row < npml) || (row >= ny - npml); };
+    auto issue = [&](int row) {
+        float4* st = stage_of(row);
+        const size_t g = (size_t)(row + PAD_Y) * pitch + cs;
+        acp16(st + 0 * 32 + lane, e_in + g);
+        acp16(st + 1 * 32 + lane, hx_in + g);
+        acp16(st + 2 * 32 + lane, hy_in + g);
+        acp4(reinterpret_cast<uint32_t*>(st + NS * 32) + lane, mat + g);
+        if constexpr (GEN) {
+            if (pml) {
+                if (lane_px) {
+                    acp16(st + 3 * 32 + lane, psi_in[0] + g);
+                    acp16(st + 6 * 32 + lane, psi_in[3] + g);
+                }
+                if (yslab(row)) {
+                    acp16(st + 4 * 32 + lane, psi_in[1] + g);
+                    acp16(st + 5 * 32 + lane, psi_in[2] + g);
+                }
+            }
+        }
+    };
+    // coefficients of row `row` (material table, or the design override)
+    auto coefs = [&](uint32_t m, int row, float4* c) {
+        c[0] = coef_s[m & 255u];
+        c[1] = coef_s[(m >> 8) & 255u];
+        c[2] = coef_s[(m >> 16) & 255u];
+        c[3] = coef_s[m >> 24];
+        if constexpr (GEN) {
+            if (dsg) {
+                const int dj = row - S->dsg_j0;
+                if (dj >= 0 && dj < S->dsg_h) {
+                    const float4* drow = S->dsg_coef + (size_t)dj * S->dsg_w;
+                    const int di = cx - S->dsg_i0;
+                    for (int q = 0; q < 4; q++)
+                        if (di + q >= 0 && di + q < S->dsg_w) c[q] = drow[di + q];
+                }
+            }
+        }
+    };
+    // gy of a row whose adjoint state is final for the level just finished
+    auto gy_of = [&](const float4& e, const float4* c, int row, const float4* sta) {
+        float4 g = make_float4(-c[0].z * e.x, -c[1].z * e.y, -c[2].z * e.z, -c[3].z * e.w);
+        if constexpr (GEN) {
+            if (pml && yslab(row)) {
+                const float ce = pr[4 * pitch + prow + row + PAD_Y];
+                const float4 p = sta[4 * 32 + lane];
+                g.x = g.x * (1.f + ce) + ce * p.x;
+                g.y = g.y * (1.f + ce) + ce * p.y;
+                g.z = g.z * (1.f + ce) + ce * p.z;
+                g.w = g.w * (1.f + ce) + ce * p.w;
+            }
+        }
+        return g;
+    };
+
+    // add dL/dE^{m+1} (table row m) at the adjoint source cells of `row`; this
+    // must precede every use of the row's state for reverse step m, including
+    // the gy the row below takes from it
+    auto inject = [&](float4& e, int row, long long m) {
+        if constexpr (GEN) {
+            if (has_src && m >= 0)
+                for (int q = tk.samp_begin; q < tk.samp_end; q++) {
+                    const Sample2 sp = srcs[q];
+                    const int d = sp.i - cx;
+                    if (sp.j == row && d >= 0 && d < 4) cref(e, d) += S->adj_src[m * S->n_adj + sp.slot];
+                }
+        }
+    };
+
+    float4 E[T + 1], X[T + 2], Y[T + 1], GY[T + 1], FY[T + 1];
+    uint32_t M[T + 1];
+#pragma unroll
+    for (int k = 0; k < T + 1; k++) {
+        E[k] = make_float4(0, 0, 0, 0);
+        Y[k] = E[k];
+        GY[k] = E[k];
+        FY[k] = E[k];
+        M[k] = 0;
+    }
+#pragma unroll
+    for (int k = 0; k < T + 2; k++) X[k] = make_float4(0, 0, 0, 0);
+#pragma unroll
+    for (int k = 0; k < PF; k++) {
+        issue(s_row + k);
+        acommit();
+    }
+
+    for (int r = s_row; r <= r_last; ++r) {
+        await_<PF - 1>();
+#pragma unroll
+        for (int k = T + 1; k >= 1; k--) X[k] = X[k - 1];
+#pragma unroll
+        for (int k = T; k >= 1; k--) {
+            E[k] = E[k - 1];
+            Y[k] = Y[k - 1];
+            M[k] = M[k - 1];
+        }
+        {
+            const float4* st = stage_of(r);
+            E[0] = st[0 * 32 + lane];
+            X[0] = st[1 * 32 + lane];
+            Y[0] = st[2 * 32 + lane];
+            M[0] = reinterpret_cast<const uint32_t*>(st + NS * 32)[lane];
+        }
+        // level 1 reverses step n_top: the new row first gets dL/dE^{n_top+1},
+        // then its gy for level 1 of the row below it
+        inject(E[0], r, n_top);
+        {
+            float4 c[4];
+            coefs(M[0], r, c);
+            GY[0] = gy_of(E[0], c, r, stage_of(r));
+        }
+
+#pragma unroll
+        for (int t = 1; t <= T; t++) {
+            const int a = r - t;
+            if constexpr (GEN) {
+                if (a < s_row) continue;
+            }
+            const long long n = n_top - (t - 1);   // forward step being reversed
+            float4* sta = stage_of(a);
+            float4 c[4];
+            coefs(M[t], a, c);
+            // E[t] already holds dL/dE^{n+1} (added when the row's previous level
+            // finished, or when it was loaded): dL/deps_r over owned design cells
+            if constexpr (GEN) {
+                if (dsg && a >= tk.ya && a < tk.yb && out_lane) {
+                    const int dj = a - S->dsg_j0;
+                    const long long nr = n - S->dsg_rec_n0;
+                    if (dj >= 0 && dj < S->dsg_h && nr >= 0 && nr < S->dsg_rec_len) {
+                        const size_t hw = (size_t)S->dsg_w * S->dsg_h;
+                        const float* re = S->dsg_rec + (size_t)nr * 2 * hw + (size_t)dj * S->dsg_w;
+                        const float2* dc = S->dsg_dcoef + (size_t)dj * S->dsg_w;
+                        float* gr = S->grad + (size_t)dj * S->dsg_w;
+                        const int di = cx - S->dsg_i0;
+                        for (int q = 0; q < 4; q++) {
+                            const int d = di + q;
+                            if (d >= 0 && d < S->dsg_w) {
+                                const float2 k2 = dc[d];
+                                gr[d] += cget(E[t], q) * (k2.x * re[d] + k2.y * re[hw + d]);
+                            }
+                        }
+                    }
+                }
+            }
+            // ---- layer 2 transposed ----
+            float4 gx = make_float4(c[0].y * E[t].x, c[1].y * E[t].y, c[2].y * E[t].z, c[3].y * E[t].w);   // (Cb/dx) e
+            float4 ux = gx;
+            float4 gya = make_float4(-c[0].z * E[t].x, -c[1].z * E[t].y, -c[2].z * E[t].z, -c[3].z * E[t].w);
+            float4 uy = make_float4(-gya.x, -gya.y, -gya.z, -gya.w);                                      // (Cb/dy) e
+            if constexpr (GEN) {
+                if (pml) {
+                    if (lane_px) {
+                        const float4 p = sta[3 * 32 + lane];
+                        gx.x = gx.x * (1.f + cex[0]) + cex[0] * p.x;
+                        gx.y = gx.y * (1.f + cex[1]) + cex[1] * p.y;
+                        gx.z = gx.z * (1.f + cex[2]) + cex[2] * p.z;
+                        gx.w = gx.w * (1.f + cex[3]) + cex[3] * p.w;
+                    }
+                    if (yslab(a)) {
+                        const float ce = pr[4 * pitch + prow + a + PAD_Y];
+                        const float4 p = sta[4 * 32 + lane];
+                        gya.x = gya.x * (1.f + ce) + ce * p.x;
+                        gya.y = gya.y * (1.f + ce) + ce * p.y;
+                        gya.z = gya.z * (1.f + ce) + ce * p.z;
+                        gya.w = gya.w * (1.f + ce) + ce * p.w;
+                    }
+                }
+            }
+            const float gxr = __shfl_down_sync(0xffffffffu, gx.x, 1);
+            Y[t].x += gx.x - gx.y;
+            Y[t].y += gx.y - gx.z;
+            Y[t].z += gx.z - gx.w;
+            Y[t].w += gx.w - gxr;
+            const float4 gyu = GY[t - 1];   // gy of row a+1 (final for level t-1)
+            X[t].x += gya.x - gyu.x;
+            X[t].y += gya.y - gyu.y;
+            X[t].z += gya.z - gyu.z;
+            X[t].w += gya.w - gyu.w;
+            if constexpr (GEN) {
+                if (pml) {
+                    if (lane_px) {
+                        float4 p = sta[3 * 32 + lane];
+                        p.x = bex[0] * (p.x + ux.x);
+                        p.y = bex[1] * (p.y + ux.y);
+                        p.z = bex[2] * (p.z + ux.z);
+                        p.w = bex[3] * (p.w + ux.w);
+                        sta[3 * 32 + lane] = p;
+                    }
+                    if (yslab(a)) {
+                        const float be = pr[4 * pitch + a + PAD_Y];
+                        float4 p = sta[4 * 32 + lane];
+                        p.x = be * (p.x - uy.x);
+                        p.y = be * (p.y - uy.y);
+                        p.z = be * (p.z - uy.z);
+                        p.w = be * (p.w - uy.w);
+                        sta[4 * 32 + lane] = p;
+                    }
+                }
+            }
+            E[t].x *= c[0].x;
+            E[t].y *= c[1].x;
+            E[t].z *= c[2].x;
+            E[t].w *= c[3].x;
+            // ---- layer 1 transposed ----
+            float4 fx = make_float4(dbx * Y[t].x, dbx * Y[t].y, dbx * Y[t].z, dbx * Y[t].w);
+            float4 fya = make_float4(-dby * X[t].x, -dby * X[t].y, -dby * X[t].z, -dby * X[t].w);
+            float4 fyd;   // fy of row a-1
+            if constexpr (GEN) {
+                if (pml) {
+                    if (lane_px) {
+                        const float4 p = sta[6 * 32 + lane];
+                        fx.x = fx.x * (1.f + chx[0]) + chx[0] * p.x;
+                        fx.y = fx.y * (1.f + chx[1]) + chx[1] * p.y;
+                        fx.z = fx.z * (1.f + chx[2]) + chx[2] * p.z;
+                        fx.w = fx.w * (1.f + chx[3]) + chx[3] * p.w;
+                    }
+                    if (yslab(a)) {
+                        const float ch = pr[4 * pitch + 3 * prow + a + PAD_Y];
+                        const float4 p = sta[5 * 32 + lane];
+                        fya.x = fya.x * (1.f + ch) + ch * p.x;
+                        fya.y = fya.y * (1.f + ch) + ch * p.y;
+                        fya.z = fya.z * (1.f + ch) + ch * p.z;
+                        fya.w = fya.w * (1.f + ch) + ch * p.w;
+                    }
+                }
+                fyd = FY[t];
+                FY[t] = fya;
+            } else {
+                fyd = make_float4(-dby * X[t + 1].x, -dby * X[t + 1].y, -dby * X[t + 1].z, -dby * X[t + 1].w);
+            }
+            const float fxl = __shfl_up_sync(0xffffffffu, fx.w, 1);
+            E[t].x += fyd.x - fya.x + fxl - fx.x;
+            E[t].y += fyd.y - fya.y + fx.x - fx.y;
+            E[t].z += fyd.z - fya.z + fx.y - fx.z;
+            E[t].w += fyd.w - fya.w + fx.z - fx.w;
+            if constexpr (GEN) {
+                if (pml) {
+                    if (yslab(a)) {
+                        const float bh = pr[4 * pitch + 2 * prow + a + PAD_Y];
+                        float4 p = sta[5 * 32 + lane];
+                        p.x = bh * (p.x - dby * X[t].x);
+                        p.y = bh * (p.y - dby * X[t].y);
+                        p.z = bh * (p.z - dby * X[t].z);
+                        p.w = bh * (p.w - dby * X[t].w);
+                        sta[5 * 32 + lane] = p;
+                    }
+                    if (lane_px) {
+                        float4 p = sta[6 * 32 + lane];
+                        p.x = bhx[0] * (p.x + dbx * Y[t].x);
+                        p.y = bhx[1] * (p.y + dbx * Y[t].y);
+                        p.z = bhx[2] * (p.z + dbx * Y[t].z);
+                        p.w = bhx[3] * (p.w + dbx * Y[t].w);
+                        sta[6 * 32 + lane] = p;
+                    }
+                }
+            }
+            // level t+1 reverses step n-1: add dL/dE^{n} to this row now, then form
+            // its gy for level t+1 of the row below
+            if (t < T) {
+                inject(E[t], a, n - 1);
+                GY[t] = gy_of(E[t], c, a, sta);
+            }
+        }
+
+        const int o = r - T;
+        if (o >= tk.ya) {
+            const size_t g = (size_t)(o + PAD_Y) * pitch + cs;
+            if (out_lane) {
+                if (cx + 3 < nx) {
+                    *reinterpret_cast<float4*>(e_out + g) = E[T];
+                    *reinterpret_cast<float4*>(hx_out + g) = X[T];
+                    *reinterpret_cast<float4*>(hy_out + g) = Y[T];
+                } else {
+                    for (int q = 0; q < 4 && cx + q < nx; q++) {
+                        e_out[g + q] = cget(E[T], q);
+                        hx_out[g + q] = cget(X[T], q);
+                        hy_out[g + q] = cget(Y[T], q);
+                    }
+                }
+                if constexpr (GEN) {
+                    if (pml) {
+                        const float4* sto = stage_of(o);
+                        for (int q = 0; q < 4 && cx + q < nx; q++) {
+                            if (yslab(o)) {
+                                psi_out[1][g + q] = cget(sto[4 * 32 + lane], q);
+                                psi_out[2][g + q] = cget(sto[5 * 32 + lane], q);
+                            }
+                            if (lane_px) {
+                                psi_out[0][g + q] = cget(sto[3 * 32 + lane], q);
+                                psi_out[3][g + q] = cget(sto[6 * 32 + lane], q);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        // rows past r_last stay inside the pad rows
+        issue(r + PF);
+        acommit();
+    }
+    await_<0>();
+}
+
+template <int T>
+cudaError_t launch_adj_T(const fdtd_ctx* c, const TmzDev* dev, const Task* tasks, int n, int warps, const Task* gtasks,
+                         int gn, int gwarps, const Sample2* srcs, int parity, long long n_top, cudaStream_t st_main,
+                         cudaStream_t st_aux) {
+    cudaError_t e = cudaSuccess;
+    if (gn > 0) {
+        const size_t sm = adj_smem(T, gwarps, true);
+        e = cudaFuncSetAttribute(k_adj<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_adj<T, true><<<gn / gwarps, gwarps * 32, sm, st_aux>>>(dev, gtasks, gn, srcs, parity, n_top);
+    }
+    if (n > 0) {
+        const size_t sm = adj_smem(T, warps, false);
+        e = cudaFuncSetAttribute(k_adj<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_adj<T, false><<<n / warps, warps * 32, sm, st_main>>>(dev, tasks, n, srcs, parity, n_top);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host: checkpoints and the reverse sweep
+// ---------------------------------------------------------------------------
+struct AdjState {
+    std::vector<float*> ckpt;      // [slot * n_scenes + scene] -> F_COUNT2 padded arrays
+    int every;
+};
+
+static size_t field_bytes(const Scene2* s) { return (size_t)s->pitch * s->rows * sizeof(float); }
+
+int adj_checkpoint_if_due(fdtd_ctx* c) {
+    AdjState* A = (AdjState*)c->adj;
+    if (!A || A->every <= 0 || c->t % A->every) return FDTD_OK;
+    const int slot = (int)(c->t / A->every);
+    const int ns = (int)c->s2.size();
+    if ((int)A->ckpt.size() < (slot + 1) * ns) A->ckpt.resize((size_t)(slot + 1) * ns, nullptr);
+    for (int k = 0; k < ns; k++) {
+        Scene2* s = c->s2[k];
+        float*& p = A->ckpt[(size_t)slot * ns + k];
+        const size_t fb = field_bytes(s);
+        if (!p && cudaMalloc(&p, F_COUNT2 * fb) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            c->err = "checkpoint: out of device memory";
+            return FDTD_ENOMEM;
+        }
+        for (int f = 0; f < F_COUNT2; f++) {
+            cudaError_t e = cudaMemcpyAsync((char*)p + f * fb, s->fbuf[f][c->parity], fb, cudaMemcpyDeviceToDevice, c->stream);
+            if (e != cudaSuccess) {
+                c->err = std::string("checkpoint copy: ") + cudaGetErrorString(e);
+                return FDTD_ECUDA;
+            }
+        }
+    }
+    c->launches += 0;
+    return FDTD_OK;
+}
+
+int adj_next_boundary(const fdtd_ctx* c, int64_t t) {
+    const AdjState* A = (const AdjState*)c->adj;
+    if (!A || A->every <= 0) return 1 << 30;
+    return (int)(A->every - t % A->every);
+}
+
+void adj_free(fdtd_ctx* c) {
+    AdjState* A = (AdjState*)c->adj;
+    if (!A) return;
+    for (float* p : A->ckpt)
+        if (p) cudaFree(p);
+    delete A;
+    c->adj = nullptr;
+}
+
+}  // namespace gem
+
+using namespace gem;
+
+extern "C" {
+
+int fdtd_set_checkpointing(fdtd_ctx* c, int every) {
+    if (!c) return FDTD_EINVAL;
+    if (c->dims != 2) {
+        c->err = "checkpointed reverse mode is 2D only";
+        return FDTD_EINVAL;
+    }
+    if (every < 0) {
+        c->err = "checkpoint interval must be >= 0";
+        return FDTD_EINVAL;
+    }
+    adj_free(c);
+    if (every > 0) {
+        AdjState* A = new AdjState();
+        A->every = every;
+        c->adj = A;
+    }
+    return FDTD_OK;
+}
+
+int fdtd_adjoint_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, float* grad, int on_device) {
+    if (!c || !dLdF_re || !dLdF_im || !grad) return FDTD_EINVAL;
+    AdjState* A = (AdjState*)c->adj;
+    if (c->dims != 2 || !A || A->every <= 0) {
+        c->err = "fdtd_adjoint_grad needs a 2D forward run with checkpointing enabled";
+        return FDTD_ESTATE;
+    }
+    const int64_t N = c->t;
+    const int ns = (int)c->s2.size();
+    if (N < 1 || (int64_t)A->ckpt.size() < ((N - 1) / A->every + 1) * ns) {
+        c->err = "no checkpointed forward run to reverse";
+        return FDTD_ESTATE;
+    }
+    for (Scene2* s : c->s2)
+        if (!s->d_dsg) {
+            c->err = "every scene needs a design rectangle (fdtd_set_design)";
+            return FDTD_ESTATE;
+        }
+    cudaStream_t st = c->stream;
+    auto cuda_err = [&](cudaError_t e, const char* what) {
+        c->err = std::string(what) + ": " + cudaGetErrorString(e);
+        return FDTD_ECUDA;
+    };
+    // per scene: adjoint source table over all cell monitors of that scene
+    std::vector<std::vector<Sample2>> srcs(ns);
+    std::vector<std::vector<float>> tab(ns);
+    std::vector<int> n_adj(ns, 0);
+    {
+        size_t off = 0;
+        for (const DftMon& m : c->mons) {
+            if (m.plane_k >= 0) continue;
+            n_adj[m.scene] += m.n_cells;
+        }
+        for (int k = 0; k < ns; k++) tab[k].assign((size_t)N * std::max(1, n_adj[k]), 0.f);
+        std::vector<int> used(ns, 0);
+        for (const DftMon& m : c->mons) {
+            if (m.plane_k >= 0) continue;
+            const Scene2* s = c->s2[m.scene];
+            for (int q = 0; q < m.n_cells; q++) {
+                const Sample2 cell = s->samples[m.slot0 + q];
+                Sample2 sp;
+                sp.i = cell.i; sp.j = cell.j; sp.comp = 0; sp.slot = used[m.scene] + q;
+                srcs[m.scene].push_back(sp);
+                for (int64_t n = 0; n < N; n++) {
+                    double g = 0.0;
+                    for (int f = 0; f < m.n_freq; f++) {
+                        const size_t id = off + (size_t)q * m.n_freq + f;
+                        double ph = m.freqs[f] * s->dt * (double)(n + 1);
+                        ph -= floor(ph);
+                        g += ((double)dLdF_re[id] * cos(2.0 * M_PI * ph) - (double)dLdF_im[id] * sin(2.0 * M_PI * ph)) * s->dt;
+                    }
+                    tab[m.scene][(size_t)n * n_adj[m.scene] + sp.slot] = (float)g;
+                }
+            }
+            used[m.scene] += m.n_cells;
+            off += (size_t)m.n_cells * m.n_freq;
+        }
+    }
+    // device buffers: adjoint state (ping-pong), recording, gradient, dC/deps, source tables
+    const int every = A->every;
+    std::vector<float*> abuf;   // [scene][F_COUNT2][2]
+    std::vector<void*> to_free;
+    auto dmalloc = [&](size_t bytes, void** p) {
+        if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        to_free.push_back(*p);
+        return true;
+    };
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(st);
+        for (void* p : to_free) cudaFree(p);
+    };
+    std::vector<TmzDev> fwd(ns), adj(ns);
+    std::vector<Task> tasks, tasks_g;
+    std::vector<Sample2> tsrc;
+    const int T = c->opt_tblock, seg = c->opt_segment, warps = c->opt_warps, gwarps = 2;
+    for (int k = 0; k < ns; k++) {
+        Scene2* s = c->s2[k];
+        const size_t fb = field_bytes(s), hw = (size_t)s->dsg_w * s->dsg_h;
+        float *aset = nullptr, *rec = nullptr, *gr = nullptr, *src = nullptr;
+        float2* dc = nullptr;
+        if (!dmalloc(F_COUNT2 * 2 * fb, (void**)&aset) || !dmalloc((size_t)every * 2 * hw * sizeof(float), (void**)&rec) ||
+            !dmalloc(hw * sizeof(float), (void**)&gr) || !dmalloc(hw * sizeof(float2), (void**)&dc) ||
+            !dmalloc(tab[k].size() * sizeof(float), (void**)&src)) {
+            cleanup();
+            c->err = "adjoint: out of device memory";
+            return FDTD_ENOMEM;
+        }
+        cudaMemsetAsync(aset, 0, F_COUNT2 * 2 * fb, st);
+        cudaMemsetAsync(gr, 0, hw * sizeof(float), st);
+        cudaMemcpyAsync(src, tab[k].data(), tab[k].size() * sizeof(float), cudaMemcpyHostToDevice, st);
+        // dCa/deps_r and dCb/deps_r from eq. (7): with D = eps + sigma dt / 2,
+        // Cb = dt / D, Ca = (eps - sigma dt / 2) / D, dD/deps_r = eps0
+        std::vector<float2> dch(hw);
+        const double eps0 = 1.0 / (4.0e-7 * M_PI * 299792458.0 * 299792458.0);
+        for (size_t q = 0; q < hw; q++) {
+            const double eps = eps0 * s->dsg_eps[q];
+            const double sg = s->dsg_sig.empty() ? 0.0 : s->dsg_sig[q];
+            const double D = eps + sg * s->dt / 2.0;
+            dch[q] = make_float2((float)(eps0 * sg * s->dt / (D * D)), (float)(-eps0 * s->dt / (D * D)));
+        }
+        cudaMemcpyAsync(dc, dch.data(), hw * sizeof(float2), cudaMemcpyHostToDevice, st);
+        for (int f = 0; f < F_COUNT2; f++)
+            for (int p = 0; p < 2; p++) abuf.push_back((float*)((char*)aset + (f * 2 + p) * fb));
+        // forward descriptor for the recompute, adjoint descriptor for the reverse sweep
+        TmzDev d;
+        cudaError_t e = cudaMemcpy(&d, c->d_scenes + k, sizeof(TmzDev), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            cleanup();
+            return cuda_err(e, "adjoint: read descriptor");
+        }
+        d.dsg_rec = rec;
+        d.dsg_rec_len = every;
+        d.dsg_dcoef = dc;
+        d.grad = gr;
+        d.adj_src = src;
+        d.n_adj = std::max(1, n_adj[k]);
+        d.rdx = (float)(1.0 / s->dx);
+        d.rdy = (float)(1.0 / s->dy);
+        fwd[k] = d;
+        TmzDev a = d;
+        for (int f = 0; f < F_COUNT2; f++)
+            for (int p = 0; p < 2; p++) a.f[f][p] = abuf[(size_t)k * F_COUNT2 * 2 + f * 2 + p];
+        a.rec = nullptr;
+        a.n_rec = 0;
+        adj[k] = a;
+        // adjoint tasks: general if a CPML slab, the design rectangle or an
+        // adjoint source is within reach, or the strip is ragged
+        const int wout = STRIP - 2 * HALO;
+        const size_t first = tasks.size(), first_g = tasks_g.size();
+        for (int ya = 0; ya < s->ny; ya += seg) {
+            for (int x0 = 0; x0 < s->nx; x0 += wout) {
+                const int lx0 = x0 - HALO, lx1 = x0 - HALO + STRIP;
+                auto make = [&](int y0, int y1, bool* gen) {
+                    Task t;
+                    t.scene = k; t.x0 = x0; t.ya = y0; t.yb = y1; t.flags = 0; t.pad = 0;
+                    const int ly0 = y0 - MAX_TB, ly1 = y1 + MAX_TB;
+                    if (s->npml > 0 && (lx0 < s->npml || lx1 > s->nx - s->npml || ly0 < s->npml || ly1 > s->ny - s->npml))
+                        t.flags |= TASK_PML;
+                    if (s->dsg_i0 < lx1 && s->dsg_i0 + s->dsg_w > lx0 && s->dsg_j0 < ly1 && s->dsg_j0 + s->dsg_h > ly0)
+                        t.flags |= TASK_DSG;
+                    t.samp_begin = (int)tsrc.size();
+                    for (const Sample2& sp : srcs[k])
+                        if (sp.i >= lx0 && sp.i < lx1 && sp.j >= ly0 && sp.j < ly1) tsrc.push_back(sp);
+                    t.samp_end = (int)tsrc.size();
+                    *gen = t.flags != 0 || t.samp_end > t.samp_begin || x0 + wout > s->nx;
+                    return t;
+                };
+                const int yb = std::min(ya + seg, s->ny);
+                bool gen;
+                const size_t mark = tsrc.size();
+                Task t = make(ya, yb, &gen);
+                if (!gen) {
+                    tasks.push_back(t);
+                } else {
+                    tsrc.resize(mark);
+                    const int segg = std::max(8, seg / 2);
+                    for (int y = ya; y < yb; y += segg) {
+                        bool g2;
+                        Task t2 = make(y, std::min(y + segg, yb), &g2);
+                        tasks_g.push_back(t2);
+                    }
+                }
+            }
+        }
+        Task pad;
+        memset(&pad, 0, sizeof(pad));
+        pad.scene = -1;
+        if (tasks.size() > first)
+            while ((tasks.size() - first) % warps) tasks.push_back(pad);
+        if (tasks_g.size() > first_g)
+            while ((tasks_g.size() - first_g) % gwarps) tasks_g.push_back(pad);
+    }
+    TmzDev *d_fwd = nullptr, *d_adj = nullptr;
+    Task *d_t = nullptr, *d_tg = nullptr;
+    Sample2* d_src = nullptr;
+    if (!dmalloc(ns * sizeof(TmzDev), (void**)&d_fwd) || !dmalloc(ns * sizeof(TmzDev), (void**)&d_adj) ||
+        !dmalloc(tasks.size() * sizeof(Task), (void**)&d_t) || !dmalloc(tasks_g.size() * sizeof(Task), (void**)&d_tg) ||
+        !dmalloc(tsrc.size() * sizeof(Sample2), (void**)&d_src)) {
+        cleanup();
+        c->err = "adjoint: out of device memory";
+        return FDTD_ENOMEM;
+    }
+    cudaMemcpyAsync(d_adj, adj.data(), ns * sizeof(TmzDev), cudaMemcpyHostToDevice, st);
+    if (!tasks.empty()) cudaMemcpyAsync(d_t, tasks.data(), tasks.size() * sizeof(Task), cudaMemcpyHostToDevice, st);
+    if (!tasks_g.empty()) cudaMemcpyAsync(d_tg, tasks_g.data(), tasks_g.size() * sizeof(Task), cudaMemcpyHostToDevice, st);
+    if (!tsrc.empty()) cudaMemcpyAsync(d_src, tsrc.data(), tsrc.size() * sizeof(Sample2), cudaMemcpyHostToDevice, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_err(e, "adjoint: upload");
+    }
+
+    // swap the forward descriptors in for the recompute (recording on)
+    TmzDev* saved_scenes = c->d_scenes;
+    c->d_scenes = d_fwd;
+    int apar = 0;
+    const int64_t nseg = (N - 1) / every + 1;
+    int rc = FDTD_OK;
+    for (int64_t sg = nseg - 1; sg >= 0 && rc == FDTD_OK; sg--) {
+        const int64_t a0 = sg * every, len = std::min<int64_t>(every, N - a0);
+        // restore the checkpoint into buffer 0 and recompute the segment
+        for (int k = 0; k < ns && rc == FDTD_OK; k++) {
+            Scene2* s = c->s2[k];
+            const size_t fb = field_bytes(s);
+            const float* p = A->ckpt[(size_t)sg * ns + k];
+            for (int f = 0; f < F_COUNT2; f++) {
+                e = cudaMemcpyAsync(s->fbuf[f][0], (const char*)p + f * fb, fb, cudaMemcpyDeviceToDevice, st);
+                if (e != cudaSuccess) rc = cuda_err(e, "adjoint: restore");
+            }
+            fwd[k].dsg_rec_n0 = a0;
+            adj[k].dsg_rec_n0 = a0;
+        }
+        if (rc) break;
+        // both descriptor sets see this segment's recording base step
+        cudaMemcpyAsync(d_fwd, fwd.data(), ns * sizeof(TmzDev), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(d_adj, adj.data(), ns * sizeof(TmzDev), cudaMemcpyHostToDevice, st);
+        c->parity = 0;
+        for (int64_t q = 0; q < len && rc == FDTD_OK;) {
+            const int done = (int)std::min<int64_t>(T, len - q);
+            rc = tmz_fused_launch(c, done, warps, a0 + q, c->parity);
+            c->parity ^= 1;
+            q += done;
+        }
+        if (rc) break;
+        // reverse the segment, T reverse steps per launch
+        for (int64_t q = len; q > 0 && rc == FDTD_OK;) {
+            const int done = (int)std::min<int64_t>(T, q);
+            const long long n_top = a0 + q - 1;
+            const bool both = !tasks.empty() && !tasks_g.empty();
+            if (both) {
+                cudaEventRecord(c->ev_fork, st);
+                cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
+            }
+            cudaStream_t sa = both ? c->aux : st;
+            switch (done) {
+                case 1: e = launch_adj_T<1>(c, d_adj, d_t, (int)tasks.size(), warps, d_tg, (int)tasks_g.size(), gwarps, d_src, apar, n_top, st, sa); break;
+                case 2: e = launch_adj_T<2>(c, d_adj, d_t, (int)tasks.size(), warps, d_tg, (int)tasks_g.size(), gwarps, d_src, apar, n_top, st, sa); break;
+                case 3: e = launch_adj_T<3>(c, d_adj, d_t, (int)tasks.size(), warps, d_tg, (int)tasks_g.size(), gwarps, d_src, apar, n_top, st, sa); break;
+                default: e = launch_adj_T<4>(c, d_adj, d_t, (int)tasks.size(), warps, d_tg, (int)tasks_g.size(), gwarps, d_src, apar, n_top, st, sa); break;
+            }
+            c->launches += (tasks.empty() ? 0 : 1) + (tasks_g.empty() ? 0 : 1);
+            if (both) {
+                cudaEventRecord(c->ev_join, c->aux);
+                cudaStreamWaitEvent(st, c->ev_join, 0);
+            }
+            if (e != cudaSuccess) rc = cuda_err(e, "adjoint launch");
+            apar ^= 1;
+            q -= done;
+        }
+    }
+    c->d_scenes = saved_scenes;
+    if (rc == FDTD_OK) {
+        size_t off = 0;
+        for (int k = 0; k < ns; k++) {
+            const size_t hw = (size_t)c->s2[k]->dsg_w * c->s2[k]->dsg_h;
+            e = cudaMemcpyAsync(grad + off, adj[k].grad, hw * sizeof(float),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) {
+                rc = cuda_err(e, "adjoint: gradient copy");
+                break;
+            }
+            off += hw;
+        }
+    }
+    cleanup();
+    return rc;
+}
+
+}  // extern "C"

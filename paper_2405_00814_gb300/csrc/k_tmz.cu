@@ -307,6 +307,23 @@ __global__ void __launch_bounds__(256, PML ? 1 : 2) k_tmz_fused(const TmzDev* __
                     if (di + 1 >= 0 && di + 1 < S->dsg_w) c1 = drow[di + 1];
                     if (di + 2 >= 0 && di + 2 < S->dsg_w) c2 = drow[di + 2];
                     if (di + 3 >= 0 && di + 3 < S->dsg_w) c3 = drow[di + 3];
+                    // reverse-mode recompute: E^n and curl H^{n+1/2} of the owned design cells
+                    const long long nr = n0 + (t - 1) - S->dsg_rec_n0;
+                    if (S->dsg_rec && nr >= 0 && nr < S->dsg_rec_len && a >= tk.ya && a < tk.yb && out_lane) {
+                        const size_t hw = (size_t)S->dsg_w * S->dsg_h;
+                        float* re = S->dsg_rec + (size_t)nr * 2 * hw + (size_t)dj * S->dsg_w;
+                        const float ev[4] = {E[t].x, E[t].y, E[t].z, E[t].w};
+                        const float kv[4] = {dhy.x * S->rdx - dhx.x * S->rdy, dhy.y * S->rdx - dhx.y * S->rdy,
+                                             dhy.z * S->rdx - dhx.z * S->rdy, dhy.w * S->rdx - dhx.w * S->rdy};
+#pragma unroll
+                        for (int q = 0; q < 4; q++) {
+                            const int d = di + q;
+                            if (d >= 0 && d < S->dsg_w && cx + q >= tk.x0 && cx + q < tk.x0 + (STRIP - 2 * HALO)) {
+                                re[d] = ev[q];
+                                re[hw + d] = kv[q];
+                            }
+                        }
+                    }
                 }
             }
             E[t].x = e_upd(E[t].x, dhy.x, dhx.x, c0);

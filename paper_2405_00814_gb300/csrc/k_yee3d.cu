@@ -408,7 +408,7 @@ int fdtd_create3(const fdtd_grid* g, double dx, double dt, double courant, const
     c->d_scenes = nullptr; c->d_tasks = nullptr; c->d_tasks_b = nullptr; c->n_tasks_b = 0; c->warps_b = 2;
     c->aux = nullptr; c->ev_fork = c->ev_join = nullptr;
     c->d_samp = nullptr; c->d_samp_scene = nullptr; c->d_samp_off = nullptr;
-    c->n_tasks = 0; c->task_tb = c->task_seg = -1; c->graph = nullptr;
+    c->n_tasks = 0; c->task_tb = c->task_seg = -1; c->graph = nullptr; c->adj = nullptr;
     *out = c;
     if (!mat || !table) return fail3(c, FDTD_EINVAL, "NULL material map or table");
     if (g->nx < 4 || g->ny < 4 || g->nz < 4) return fail3(c, FDTD_EINVAL, "3D grid needs >= 4 cells per axis");

@@ -80,6 +80,8 @@ def lib():
         L.fdtd_save_state.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
         L.fdtd_load_state.argtypes = [vp, vp, C.c_size_t]
         L.fdtd_check_finite.argtypes = [vp]
+        L.fdtd_set_checkpointing.argtypes = [vp, ip]
+        L.fdtd_adjoint_grad.argtypes = [vp, vp, vp, vp, ip]
         L.fdtd_mp_steps_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, i64, vp]
         _LIB = L
     return _LIB
@@ -312,6 +314,24 @@ class Simulation:
     def load_state(self, data: bytes):
         buf = C.create_string_buffer(data, len(data))
         self._check(self._L.fdtd_load_state(self._h, buf, len(data)))
+
+    def set_checkpointing(self, every: int):
+        self._check(self._L.fdtd_set_checkpointing(self._h, int(every)))
+
+    def adjoint_grad(self, dLdF, grad_shape, out=None):
+        """dL/deps_r over the design rectangles given dL/dF (complex, every cell
+        monitor's [n_cells][n_freq] block concatenated).  Returns a host array of
+        grad_shape, or fills the CUDA tensor `out`."""
+        g = np.ascontiguousarray(np.concatenate([np.ravel(x) for x in dLdF]) if isinstance(dLdF, (list, tuple))
+                                 else np.ravel(dLdF))
+        re = np.ascontiguousarray(g.real, np.float32)
+        im = np.ascontiguousarray(g.imag, np.float32)
+        if out is not None and hasattr(out, "data_ptr"):
+            self._check(self._L.fdtd_adjoint_grad(self._h, re.ctypes.data, im.ctypes.data, out.data_ptr(), 1))
+            return out
+        res = np.empty(grad_shape, np.float32)
+        self._check(self._L.fdtd_adjoint_grad(self._h, re.ctypes.data, im.ctypes.data, res.ctypes.data, 0))
+        return res
 
     def export_graph(self, layer: int):
         nn, ne = C.c_int64(), C.c_int64()
