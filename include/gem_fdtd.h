@@ -70,10 +70,18 @@ extern "C" {
 #define FDTD_SRC_SAMPLED 3   /* samples[n] = s((n+1) dt), n < n_samples; 0 after */
 
 /* options (fdtd_set_option) */
-#define FDTD_OPT_KERNEL 0    /* 0 = fused temporally blocked stream (default), 1 = one H and one E launch per step */
+#define FDTD_OPT_KERNEL 0    /* 0 = fused temporally blocked stream, two kernels per T-step block (default);
+                                1 = one H and one E launch per step;
+                                2 = persistent: one cooperative launch runs many T-step blocks of every scene,
+                                    warps pulling tasks from a shared counter, a bounded grid barrier between blocks */
 #define FDTD_OPT_TBLOCK 1    /* time steps per HBM pass of the fused kernel, 1..4 */
 #define FDTD_OPT_SEGMENT 2   /* rows per warp task of the fused kernel (multiple of 8, >= 8) */
 #define FDTD_OPT_WARPS 3     /* warps per CTA of the fused kernel, 1..8 */
+#define FDTD_OPT_GRAPH 4     /* 1: fdtd_step records its launches into a CUDA graph and replays it when called
+                                again with the same start step, step count and buffer parity (e.g. after fdtd_reset) */
+#define FDTD_OPT_SPIN_LIMIT 5     /* polls (about 0.25 us each) a persistent-kernel barrier wait makes before it gives up */
+#define FDTD_OPT_DEBUG_SKIP_CTA 6 /* test hook: this CTA of the persistent kernel never arrives at the barrier, so the
+                                     others' waits run out (-1 = off); fdtd_sync then returns FDTD_ETIMEOUT */
 
 typedef struct fdtd_ctx fdtd_ctx;
 
@@ -194,6 +202,18 @@ int64_t fdtd_launch_count(const fdtd_ctx* ctx);
  * context configuration. */
 int fdtd_save_state(fdtd_ctx* ctx, void* buf, size_t* bytes);
 int fdtd_load_state(fdtd_ctx* ctx, const void* buf, size_t bytes);
+
+/* Wait for the context's stream.  Returns FDTD_ETIMEOUT if a bounded device
+ * wait (the persistent kernel's grid barrier) gave up since the last call: the
+ * kernel then stopped early, the context stays usable, and the fields hold the
+ * state of an incomplete step sequence. */
+int fdtd_sync(fdtd_ctx* ctx);
+
+/* Batched scenes (Sec. V-A runs many simulations of varying size): time each
+ * candidate setting of (kernel 0 or 2, T 2..4, segment 16..48, warps 4 or 8) for
+ * trial_steps steps on the current scenes and keep the fastest.  Leaves the
+ * context reset (t = 0, zero fields).  *best_ms gets the best time per step. */
+int fdtd_autotune(fdtd_ctx* ctx, int trial_steps, double* best_ms);
 
 /* Returns FDTD_EUNSTABLE if any field of any scene is not finite. Synchronises. */
 int fdtd_check_finite(fdtd_ctx* ctx);

@@ -262,6 +262,24 @@ fdtd_ctx* ctx_new(void* stream) {
     c->task_tb = c->task_seg = -1;
     c->graph = nullptr;
     c->adj = nullptr;
+    c->d_tasks_all = nullptr;
+    c->n_tasks_all = 0;
+    c->d_ctl = nullptr;
+    c->ctl_words = 0;
+    c->h_err = nullptr;
+    if (cudaMallocHost(&c->h_err, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        c->h_err = nullptr;
+    } else {
+        *c->h_err = 0;
+    }
+    c->spin_limit = 4000000;   // about one second of 256 ns polls
+    c->opt_debug_skip = -1;
+    c->opt_graph = 0;
+    c->graph_exec = nullptr;
+    c->graph_t = c->graph_n = -1;
+    c->graph_parity = 0;
+    c->cap_stream = nullptr;
     return c;
 }
 
@@ -407,13 +425,21 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
         for (const Sample2& sp : c->s2[k]->samples) ssamp.push_back(sp);
         soff[k + 1] = (int)ssamp.size();
     }
+    // the persistent kernel takes every task from one list, heavy ones first
+    std::vector<Task> all;
+    for (const Task& t : tasks_b)
+        if (t.scene >= 0) all.push_back(t);
+    for (const Task& t : tasks)
+        if (t.scene >= 0) all.push_back(t);
     dfree(c->d_scenes); dfree(c->d_tasks); dfree(c->d_tasks_b); dfree(c->d_samp); dfree(c->d_samp_scene); dfree(c->d_samp_off);
+    dfree(c->d_tasks_all);
     c->d_scenes = nullptr; c->d_tasks = nullptr; c->d_tasks_b = nullptr; c->d_samp = nullptr; c->d_samp_scene = nullptr;
-    c->d_samp_off = nullptr;
+    c->d_samp_off = nullptr; c->d_tasks_all = nullptr;
     int rc;
     if ((rc = dalloc(c, &c->d_scenes, dev.size() * sizeof(TmzDev), "scene descriptors"))) return rc;
     if ((rc = dalloc(c, &c->d_tasks, tasks.size() * sizeof(Task), "tasks"))) return rc;
     if ((rc = dalloc(c, &c->d_tasks_b, tasks_b.size() * sizeof(Task), "tasks"))) return rc;
+    if ((rc = dalloc(c, &c->d_tasks_all, all.size() * sizeof(Task), "tasks"))) return rc;
     if ((rc = dalloc(c, &c->d_samp, tsamp.size() * sizeof(Sample2), "samples"))) return rc;
     if ((rc = dalloc(c, &c->d_samp_scene, ssamp.size() * sizeof(Sample2), "samples"))) return rc;
     if ((rc = dalloc(c, &c->d_samp_off, soff.size() * sizeof(int), "sample offsets"))) return rc;
@@ -422,6 +448,8 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
         CK(cudaMemcpyAsync(c->d_tasks, tasks.data(), tasks.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
     if (!tasks_b.empty())
         CK(cudaMemcpyAsync(c->d_tasks_b, tasks_b.data(), tasks_b.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
+    if (!all.empty())
+        CK(cudaMemcpyAsync(c->d_tasks_all, all.data(), all.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
     if (!tsamp.empty())
         CK(cudaMemcpyAsync(c->d_samp, tsamp.data(), tsamp.size() * sizeof(Sample2), cudaMemcpyHostToDevice, c->stream), "upload");
     if (!ssamp.empty())
@@ -430,6 +458,7 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     CK(cudaStreamSynchronize(c->stream), "upload task list");
     c->n_tasks = (int)tasks.size();
     c->n_tasks_b = (int)tasks_b.size();
+    c->n_tasks_all = (int)all.size();
     c->warps_b = warps_b;
     c->task_tb = T;
     c->task_seg = seg;
@@ -531,6 +560,11 @@ void fdtd_destroy(fdtd_ctx* c) {
     adj_free(c);
     dfree(c->d_scenes); dfree(c->d_tasks); dfree(c->d_tasks_b); dfree(c->d_samp); dfree(c->d_samp_scene);
     dfree(c->d_samp_off);
+    dfree(c->d_tasks_all);
+    dfree(c->d_ctl);
+    if (c->h_err) cudaFreeHost(c->h_err);
+    if (c->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->aux) cudaStreamDestroy(c->aux);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
@@ -543,8 +577,20 @@ int fdtd_set_option(fdtd_ctx* c, int option, int64_t v) {
     if (!c) return FDTD_EINVAL;
     switch (option) {
         case FDTD_OPT_KERNEL:
-            if (v < 0 || v > 1) return fail(c, FDTD_EINVAL, "kernel option %lld outside 0..1", (long long)v);
+            if (v < 0 || v > 2) return fail(c, FDTD_EINVAL, "kernel option %lld outside 0..2", (long long)v);
             c->opt_kernel = (int)v;
+            return FDTD_OK;
+        case FDTD_OPT_GRAPH:
+            if (v < 0 || v > 1) return fail(c, FDTD_EINVAL, "graph option must be 0 or 1");
+            c->opt_graph = (int)v;
+            return FDTD_OK;
+        case FDTD_OPT_SPIN_LIMIT:
+            if (v < 1) return fail(c, FDTD_EINVAL, "spin limit must be >= 1");
+            c->spin_limit = v;
+            return FDTD_OK;
+        case FDTD_OPT_DEBUG_SKIP_CTA:
+            if (v < -1 || v > (1 << 20)) return fail(c, FDTD_EINVAL, "debug CTA index out of range");
+            c->opt_debug_skip = (int)v;
             return FDTD_OK;
         case FDTD_OPT_TBLOCK:
             if (v < 1 || v > MAX_TB) return fail(c, FDTD_EINVAL, "tblock %lld outside 1..%d", (long long)v, MAX_TB);
@@ -571,6 +617,9 @@ int64_t fdtd_get_option(const fdtd_ctx* c, int option) {
         case FDTD_OPT_TBLOCK: return c->opt_tblock;
         case FDTD_OPT_SEGMENT: return c->opt_segment;
         case FDTD_OPT_WARPS: return c->opt_warps;
+        case FDTD_OPT_GRAPH: return c->opt_graph;
+        case FDTD_OPT_SPIN_LIMIT: return c->spin_limit;
+        case FDTD_OPT_DEBUG_SKIP_CTA: return c->opt_debug_skip;
     }
     return -1;
 }
@@ -698,15 +747,11 @@ int fdtd_add_dft_plane(fdtd_ctx* c, int k, int comp_mask, const double* freqs, i
     return fdtd_add_dft_plane3(c, k, comp_mask, freqs, n_freq, mon_id);
 }
 
-int fdtd_step(fdtd_ctx* c, int64_t n_steps) {
-    if (!c) return FDTD_EINVAL;
-    if (n_steps < 0) return fail(c, FDTD_EINVAL, "n_steps < 0");
-    if (n_steps == 0) return FDTD_OK;
-    if (c->dims == 3) return fdtd_step3(c, n_steps);
-    int rc = step_prepare(c, n_steps);
-    if (rc) return rc;
+// the launches of n_steps steps (no allocation: step_prepare ran before)
+static int step_launches(fdtd_ctx* c, int64_t n_steps) {
     const int T = c->opt_tblock;
     int64_t left = n_steps;
+    int rc = FDTD_OK;
     while (left > 0) {
         int done;
         rc = adj_checkpoint_if_due(c);
@@ -714,6 +759,19 @@ int fdtd_step(fdtd_ctx* c, int64_t n_steps) {
         if (c->opt_kernel == 1) {
             rc = tmz_naive_step(c, c->t);
             done = 1;
+        } else if (c->opt_kernel == 2 && left >= T) {
+            // as many whole T-blocks as fit before the next checkpoint, in one launch
+            const int64_t span = std::min<int64_t>(left, adj_next_boundary(c, c->t));
+            const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(span / T, c->ctl_words - 4));
+            if (span < T) {
+                done = (int)span;
+                rc = tmz_fused_launch(c, done, c->opt_warps, c->t, c->parity);
+                c->parity ^= 1;
+            } else {
+                done = nb * T;
+                rc = tmz_persistent_launch(c, T, c->t, nb, c->parity);
+                c->parity ^= (nb & 1);
+            }
         } else {
             // a T-step block never crosses a checkpoint boundary
             done = (int)std::min<int64_t>(std::min<int64_t>(T, left), adj_next_boundary(c, c->t));
@@ -730,6 +788,144 @@ int fdtd_step(fdtd_ctx* c, int64_t n_steps) {
         left -= done;
     }
     return FDTD_OK;
+}
+
+int fdtd_step(fdtd_ctx* c, int64_t n_steps) {
+    if (!c) return FDTD_EINVAL;
+    if (n_steps < 0) return fail(c, FDTD_EINVAL, "n_steps < 0");
+    if (n_steps == 0) return FDTD_OK;
+    if (c->dims == 3) return fdtd_step3(c, n_steps);
+    int rc = step_prepare(c, n_steps);
+    if (rc) return rc;
+    if (c->opt_kernel == 2) {
+        // control words: 4 + one work counter per T-block of the longest launch
+        const int need = 4 + (int)std::min<int64_t>(n_steps / std::max(1, c->opt_tblock) + 1, 1 << 20);
+        if (c->ctl_words < need) {
+            dfree(c->d_ctl);
+            c->d_ctl = nullptr;
+            c->ctl_words = 0;
+            rc = dalloc(c, &c->d_ctl, (size_t)need * sizeof(unsigned), "persistent control words");
+            if (rc) return rc;
+            c->ctl_words = need;
+        }
+        if (!c->h_err) return fail(c, FDTD_ENOMEM, "no pinned host word for the persistent kernel");
+    }
+    if (!c->opt_graph) return step_launches(c, n_steps);
+    if (c->adj) return fail(c, FDTD_EINVAL, "CUDA-graph stepping and checkpointing cannot be combined");
+    // replay the recorded graph when it was made for this start step, length and parity
+    if (c->graph_exec && c->graph_t == c->t && c->graph_n == n_steps && c->graph_parity == c->parity) {
+        CK(cudaGraphLaunch((cudaGraphExec_t)c->graph_exec, c->stream), "graph launch");
+        const int64_t t0 = c->t;
+        c->t = t0 + n_steps;
+        c->parity = c->graph_parity_after;
+        c->launches += c->graph_launches;
+        return FDTD_OK;
+    }
+    if (c->graph_exec) {
+        cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
+        c->graph_exec = nullptr;
+    }
+    // record: the legacy default stream cannot be captured, so use a private one
+    cudaStream_t user = c->stream;
+    if (!user) {
+        if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream");
+        CK(cudaStreamSynchronize(0), "capture stream");
+        c->stream = c->cap_stream;
+    }
+    const int64_t t0 = c->t;
+    const int p0 = c->parity;
+    const int64_t l0 = c->launches;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        rc = step_launches(c, n_steps);
+        e = cudaStreamEndCapture(c->stream, &g);
+    }
+    c->stream = user;
+    if (e != cudaSuccess || rc) {
+        if (g) cudaGraphDestroy(g);
+        c->t = t0;
+        c->parity = p0;
+        return rc ? rc : fail(c, FDTD_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->t = t0;
+        c->parity = p0;
+        return fail(c, FDTD_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    c->graph_exec = ex;
+    c->graph_t = t0;
+    c->graph_n = n_steps;
+    c->graph_parity = p0;
+    c->graph_parity_after = c->parity;
+    c->graph_launches = c->launches - l0;
+    c->launches = l0;
+    CK(cudaGraphLaunch(ex, c->stream), "graph launch");
+    c->launches += c->graph_launches;
+    return FDTD_OK;
+}
+
+int fdtd_sync(fdtd_ctx* c) {
+    if (!c) return FDTD_EINVAL;
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    if (c->h_err && *c->h_err) {
+        *c->h_err = 0;
+        return fail(c, FDTD_ETIMEOUT, "a grid-barrier wait of the persistent kernel gave up (spin limit %lld)",
+                    (long long)c->spin_limit);
+    }
+    return FDTD_OK;
+}
+
+// time candidate settings on the current scenes; keep the fastest
+int fdtd_autotune(fdtd_ctx* c, int trial_steps, double* best_ms) {
+    if (!c) return FDTD_EINVAL;
+    if (c->dims != 2) return fail(c, FDTD_EINVAL, "autotuning covers the 2D kernels");
+    if (trial_steps < 4) return fail(c, FDTD_EINVAL, "trial_steps must be >= 4");
+    if (c->adj) return fail(c, FDTD_EINVAL, "disable checkpointing before autotuning");
+    struct Cand { int kernel, T, seg, warps; };
+    std::vector<Cand> cand;
+    for (int T = 2; T <= MAX_TB; T++)
+        for (int seg : {16, 24, 32, 48})
+            for (int w : {4, 8}) cand.push_back({0, T, seg, w});
+    for (int T = 2; T <= MAX_TB; T++)
+        for (int seg : {16, 24, 32, 48}) cand.push_back({2, T, seg, 8});
+    const int graph = c->opt_graph;
+    c->opt_graph = 0;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "autotune");
+    CK(cudaEventCreate(&e1), "autotune");
+    double best = 1e30;
+    Cand win = {c->opt_kernel, c->opt_tblock, c->opt_segment, c->opt_warps};
+    int rc = FDTD_OK;
+    for (const Cand& k : cand) {
+        c->opt_kernel = k.kernel; c->opt_tblock = k.T; c->opt_segment = k.seg; c->opt_warps = k.warps;
+        c->dirty = true;
+        if ((rc = fdtd_reset(c))) break;
+        if ((rc = fdtd_step(c, k.T))) break;   // warm-up (and build) outside the timing
+        cudaEventRecord(e0, c->stream);
+        if ((rc = fdtd_step(c, trial_steps))) break;
+        cudaEventRecord(e1, c->stream);
+        if ((rc = fdtd_sync(c))) break;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = ms / trial_steps;
+        if (per < best) {
+            best = per;
+            win = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->opt_kernel = win.kernel; c->opt_tblock = win.T; c->opt_segment = win.seg; c->opt_warps = win.warps;
+    c->opt_graph = graph;
+    c->dirty = true;
+    int rc2 = fdtd_reset(c);
+    if (rc) return rc;
+    if (best_ms) *best_ms = best;
+    return rc2;
 }
 
 int fdtd_read_probe(fdtd_ctx* c, int probe_id, float* out, int64_t n) {

@@ -160,6 +160,21 @@ struct fdtd_ctx {
     void* graph;
     // reverse mode (k_adjoint.cu): checkpoints of the forward run
     void* adj;
+    // persistent kernel: all tasks in one list (general tasks first), control words
+    gem::Task* d_tasks_all;
+    int n_tasks_all;
+    unsigned* d_ctl;
+    int ctl_words;
+    int* h_err;                  // pinned: error flag of the last persistent launch
+    long long spin_limit;        // barrier polls before a CTA gives up
+    int opt_debug_skip;          // CTA that skips its barrier arrivals (-1 none)
+    // CUDA graph of a step sequence
+    int opt_graph;
+    void* graph_exec;
+    int64_t graph_t, graph_n;
+    int graph_parity, graph_parity_after;
+    int64_t graph_launches;
+    cudaStream_t cap_stream;
 };
 
 namespace gem {
@@ -168,6 +183,7 @@ int tmz_fused_launch(fdtd_ctx* c, int T, int warps, long long n0, int parity);
 int tmz_naive_step(fdtd_ctx* c, long long n);
 int dft_cells_launch(fdtd_ctx* c, const DftMon& m, long long n0, int nsteps);
 int tmz_finite_check(fdtd_ctx* c, int* bad);
+int tmz_persistent_launch(fdtd_ctx* c, int T, long long n0, int n_blocks, int parity);
 size_t tmz_fused_smem(int T, int warps, bool pml);
 }  // namespace gem
 

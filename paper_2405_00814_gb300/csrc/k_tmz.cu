@@ -98,32 +98,17 @@ struct Prof {
 // ===========================================================================
 // fused, temporally blocked kernel
 // ===========================================================================
+// One warp's task of the general kernel (any task: CPML slab, design rectangle,
+// source, probes, ragged edge).  coef_s is the scene's coefficient table (shared
+// or global memory); stage0 the warp's Q x STAGE_F4 float4 staging area.
 template <int T, bool PML>
-__global__ void __launch_bounds__(256, PML ? 1 : 2) k_tmz_fused(const TmzDev* __restrict__ scenes,
-                                                   const Task* __restrict__ tasks, int n_tasks,
-                                                   const Sample2* __restrict__ samps, int parity,
-                                                   long long n0) {
+__device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const Task& tk,
+                                             const Sample2* __restrict__ samps, int parity, long long n0,
+                                             const float4* coef_s, float4* stage0, int lane) {
     constexpr int PF = pf_of(T, PML);
     constexpr int NSLOT = nslot_of(PML);
     constexpr int STAGE_F4 = stage_f4(PML);
     constexpr int Q = stages_for(T, PML);
-    extern __shared__ float4 smem_f4[];
-    __shared__ float4 coef_s[256];
-
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int warps = blockDim.x >> 5;
-    const int tid = blockIdx.x * warps + wib;
-
-    // every block holds tasks of one scene: stage its coefficient table
-    const int blk_scene = tasks[blockIdx.x * warps].scene;
-    const TmzDev* S = scenes + blk_scene;
-    for (int k = threadIdx.x; k < 256; k += blockDim.x) coef_s[k] = S->coef[k];
-    __syncthreads();
-    if (tid >= n_tasks) return;
-    const Task tk = tasks[tid];
-    if (tk.scene < 0) return;
-
     const int pitch = S->pitch, nx = S->nx, ny = S->ny;
     const float* __restrict__ ez_in = S->f[F_EZ][parity];
     const float* __restrict__ hx_in = S->f[F_HX][parity];
@@ -167,7 +152,6 @@ __global__ void __launch_bounds__(256, PML ? 1 : 2) k_tmz_fused(const TmzDev* __
     const bool has_src = (tk.flags & TASK_SRC) != 0;
     const int src_j = S->src_j, src_d = S->src_i - cx;
 
-    float4* stage0 = smem_f4 + (size_t)wib * Q * STAGE_F4;
 
     auto issue = [&](int row) {
         const int q = (row - s_row) % Q;
@@ -394,6 +378,157 @@ __global__ void __launch_bounds__(256, PML ? 1 : 2) k_tmz_fused(const TmzDev* __
         cp_commit();
     }
     cp_wait<0>();
+}
+
+template <int T, bool PML>
+__global__ void __launch_bounds__(256, PML ? 1 : 2) k_tmz_fused(const TmzDev* __restrict__ scenes,
+                                                   const Task* __restrict__ tasks, int n_tasks,
+                                                   const Sample2* __restrict__ samps, int parity,
+                                                   long long n0) {
+    constexpr int STAGE_F4 = stage_f4(PML);
+    constexpr int Q = stages_for(T, PML);
+    extern __shared__ float4 smem_f4[];
+    __shared__ float4 coef_s[256];
+
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int warps = blockDim.x >> 5;
+    const int tid = blockIdx.x * warps + wib;
+
+    // every block holds tasks of one scene: stage its coefficient table
+    const TmzDev* S = scenes + tasks[blockIdx.x * warps].scene;
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) coef_s[k] = S->coef[k];
+    __syncthreads();
+    if (tid >= n_tasks) return;
+    const Task tk = tasks[tid];
+    if (tk.scene < 0) return;
+    general_task<T, PML>(S, tk, samps, parity, n0, coef_s, smem_f4 + (size_t)wib * Q * STAGE_F4, lane);
+}
+
+// ===========================================================================
+// persistent kernel: one cooperative launch advances every scene of a batch
+// by n_blocks * T steps.  Warps pull (scene, strip, segment) tasks of all scenes
+// from a per-block work counter, so uneven scene sizes balance themselves; a
+// grid-wide barrier separates T-step blocks (each block reads buffer p and
+// writes 1 - p).  Every wait is bounded: after spin_limit polls a CTA sets the
+// error flag and returns, and the others stop waiting when they see the flag.
+//
+// ctl layout (unsigned): [0] arrivals, [1] generation, [2] error flag,
+// [3] unused, [4 + b] work counter of block b.  skip_cta >= 0 names a CTA
+// that never arrives (a test of the timeout path); -1 in normal runs.
+// ===========================================================================
+__device__ __forceinline__ bool grid_barrier(unsigned* ctl, long long spin_limit, int skip_cta) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = ctl + 1;
+        volatile int* verr = reinterpret_cast<volatile int*>(ctl + 2);
+        const unsigned gen = *vgen;
+        __threadfence();
+        bool ok = true;
+        const bool skip = skip_cta == (int)blockIdx.x;
+        const unsigned arrived = skip ? 0u : atomicAdd(ctl, 1u) + 1u;
+        if (!skip && arrived == gridDim.x) {
+            ctl[0] = 0;
+            __threadfence();
+            atomicAdd(ctl + 1, 1u);
+        } else {
+            long long it = 0;
+            while (*vgen == gen) {
+                if (*verr || ++it > spin_limit) {
+                    atomicExch(reinterpret_cast<int*>(ctl + 2), 1);
+                    ok = false;
+                    break;
+                }
+                __nanosleep(256);
+            }
+        }
+        __threadfence();
+        ok_s = ok && !*verr;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+template <int T>
+__global__ void __launch_bounds__(256, 1) k_tmz_persistent(const TmzDev* __restrict__ scenes,
+                                                          const Task* __restrict__ tasks, int n_tasks,
+                                                          const Sample2* __restrict__ samps, int parity0,
+                                                          long long n0, int n_blocks, unsigned* ctl,
+                                                          long long spin_limit, int skip_cta) {
+    constexpr int STAGE_F4 = stage_f4(true);
+    constexpr int Q = stages_for(T, true);
+    extern __shared__ float4 smem_f4[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    float4* stage0 = smem_f4 + (size_t)wib * Q * STAGE_F4;
+    for (int b = 0; b < n_blocks; b++) {
+        const int parity = parity0 ^ (b & 1);
+        const long long nb = n0 + (long long)b * T;
+        for (;;) {
+            int idx = 0;
+            if (lane == 0) idx = (int)atomicAdd(ctl + 4 + b, 1u);
+            idx = __shfl_sync(0xffffffffu, idx, 0);
+            if (idx >= n_tasks) break;
+            const Task tk = tasks[idx];
+            if (tk.scene >= 0) {
+                const TmzDev* S = scenes + tk.scene;
+                general_task<T, true>(S, tk, samps, parity, nb, S->coef, stage0, lane);
+            }
+        }
+        if (!grid_barrier(ctl, spin_limit, skip_cta)) return;
+    }
+}
+
+template <int T>
+static cudaError_t launch_persistent_T(const fdtd_ctx* c, cudaStream_t st, int parity, long long n0, int n_blocks,
+                                       long long spin_limit, int* grid_out) {
+    const int warps = 8;
+    const size_t smem = (size_t)warps * stages_for(T, true) * stage_f4(true) * sizeof(float4);
+    cudaError_t e = cudaFuncSetAttribute(k_tmz_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tmz_persistent<T>, warps * 32, smem);
+    if (e != cudaSuccess) return e;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int grid = per_sm * sms;
+    *grid_out = grid;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(warps * 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_tmz_persistent<T>, (const TmzDev*)c->d_scenes, (const Task*)c->d_tasks_all,
+                              c->n_tasks_all, (const Sample2*)c->d_samp, parity, n0, n_blocks, c->d_ctl, spin_limit,
+                              c->opt_debug_skip);
+}
+
+// n_blocks T-step blocks in one cooperative launch (control words zeroed first)
+int tmz_persistent_launch(fdtd_ctx* c, int T, long long n0, int n_blocks, int parity) {
+    cudaError_t e = cudaMemsetAsync(c->d_ctl, 0, (size_t)(4 + n_blocks) * sizeof(unsigned), c->stream);
+    int grid = 0;
+    if (e == cudaSuccess) {
+        switch (T) {
+            case 1: e = launch_persistent_T<1>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid); break;
+            case 2: e = launch_persistent_T<2>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid); break;
+            case 3: e = launch_persistent_T<3>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid); break;
+            default: e = launch_persistent_T<4>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid); break;
+        }
+    }
+    c->launches++;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_err, c->d_ctl + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) {
+        c->err = std::string("persistent launch: ") + cudaGetErrorString(e);
+        return FDTD_ECUDA;
+    }
+    return FDTD_OK;
 }
 
 // ===========================================================================

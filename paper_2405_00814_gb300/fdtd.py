@@ -21,7 +21,7 @@ OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, 
 PEC, CPML = 0, 1
 COMP = {"ex": 0, "ey": 1, "ez": 2, "hx": 3, "hy": 4, "hz": 5}
 SRC = {"ricker": 0, "gauss_mod": 1, "gauss": 2, "sampled": 3}
-OPT = {"kernel": 0, "tblock": 1, "segment": 2, "warps": 3}
+OPT = {"kernel": 0, "tblock": 1, "segment": 2, "warps": 3, "graph": 4, "spin_limit": 5, "debug_skip_cta": 6}
 
 
 class FDTDError(RuntimeError):
@@ -80,6 +80,8 @@ def lib():
         L.fdtd_save_state.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
         L.fdtd_load_state.argtypes = [vp, vp, C.c_size_t]
         L.fdtd_check_finite.argtypes = [vp]
+        L.fdtd_sync.argtypes = [vp]
+        L.fdtd_autotune.argtypes = [vp, ip, C.POINTER(C.c_double)]
         L.fdtd_set_checkpointing.argtypes = [vp, ip]
         L.fdtd_adjoint_grad.argtypes = [vp, vp, vp, vp, ip]
         L.fdtd_mp_steps_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, i64, vp]
@@ -269,6 +271,43 @@ class Simulation:
 
     def check_finite(self):
         self._check(self._L.fdtd_check_finite(self._h))
+
+    def sync(self):
+        """Wait for the stream; raises FDTDError(ETIMEOUT) if a bounded device
+        wait gave up since the last call."""
+        self._check(self._L.fdtd_sync(self._h))
+
+    def autotune(self, trial_steps=32, cache=None, key=None):
+        """Pick (kernel, T, segment, warps) by timing candidates on the current
+        scenes (leaves the context reset).  With a cache path, results are kept
+        in a JSON file keyed by `key` and the GPU name."""
+        import json
+        import os
+        name = None
+        try:
+            import torch
+            name = torch.cuda.get_device_name()
+        except Exception:
+            name = "cuda"
+        ck = f"{name}|{key}"
+        if cache and key and os.path.exists(cache):
+            data = json.load(open(cache))
+            if ck in data:
+                for k, v in data[ck]["options"].items():
+                    self.set_option(k, v)
+                return data[ck]
+        best = C.c_double(0.0)
+        self._check(self._L.fdtd_autotune(self._h, int(trial_steps), C.byref(best)))
+        res = {"ms_per_step": best.value,
+               "options": {k: self.get_option(k) for k in ("kernel", "tblock", "segment", "warps")}}
+        if cache and key:
+            data = json.load(open(cache)) if os.path.exists(cache) else {}
+            data[ck] = res
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(data, f, indent=1)
+            os.replace(tmp, cache)
+        return res
 
     # ---------------------------------------------------------------- outputs
     def field_shape(self, scene):

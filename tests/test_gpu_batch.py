@@ -1,0 +1,117 @@
+"""GPU: batched uneven scenes through the persistent kernel, CUDA-graph replay,
+the autotuner, and the persistent kernel's bounded barrier (timeout path)."""
+import numpy as np
+import pytest
+
+from paper_2405_00814_gb300 import scenes
+from tests._helpers import TOL_FIELD, assert_fields_close, oracle_run, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _batch(n=4, nsteps=400, lo=96, hi=320):
+    from paper_2405_00814_gb300 import fdtd
+    scs = scenes.batch_scenes(n_scenes=n, nsteps=nsteps, side_lo=lo, side_hi=hi)
+    sim = fdtd.Simulation.batch(scs)
+    pids = []
+    for k, s in enumerate(scs):
+        sim.select(k)
+        sim.set_scene_source(s.source)
+        pids.append(sim.add_probe(s.nx // 3, s.ny // 2))
+    return scs, sim, pids
+
+
+def _fields(sim, scs):
+    out = []
+    for k, s in enumerate(scs):
+        sim.select(k)
+        out.append({c: sim.get_field(c, (s.ny, s.nx)) for c in ("ez", "hx", "hy")})
+    return out
+
+
+@pytest.mark.parametrize("tblock,segment", [(4, 24), (3, 16), (2, 48)])
+def test_persistent_kernel_batch_parity(tblock, segment):
+    scs, sim, pids = _batch(nsteps=402)
+    sim.set_option("kernel", 2)
+    sim.set_option("tblock", tblock)
+    sim.set_option("segment", segment)
+    sim.step(402)          # whole blocks in the persistent launch, the remainder in a fused launch
+    sim.sync()
+    got = _fields(sim, scs)
+    for k, s in enumerate(scs):
+        o = oracle_run(s, 402, probes=[(s.nx // 3, s.ny // 2)])
+        assert_fields_close(got[k], o)
+        assert rel_l2(sim.read_probe(pids[k], 402), o["probes"][:, 0]) <= TOL_FIELD
+    sim.close()
+
+
+def test_graph_replay_matches_plain_run():
+    scs, sim, _ = _batch(n=3, nsteps=300)
+    sim.step(300)
+    ref = _fields(sim, scs)
+    sim.reset()
+    sim.set_option("graph", 1)
+    sim.step(300)          # records and launches
+    sim.reset()
+    sim.step(300)          # replays
+    sim.sync()
+    got = _fields(sim, scs)
+    for a, b in zip(got, ref):
+        for c in ("ez", "hx", "hy"):
+            assert np.array_equal(a[c], b[c])
+    sim.set_option("kernel", 2)   # persistent kernel inside a graph
+    sim.reset()
+    sim.step(300)
+    sim.reset()
+    sim.step(300)
+    sim.sync()
+    for a, b in zip(_fields(sim, scs), ref):
+        for c in ("ez", "hx", "hy"):
+            assert rel_l2(a[c], b[c]) < 1e-5
+    sim.close()
+
+
+def test_autotune_keeps_results_exact(tmp_path):
+    scs, sim, _ = _batch(n=3, nsteps=200)
+    res = sim.autotune(trial_steps=16, cache=str(tmp_path / "tune.json"), key="test3")
+    assert res["ms_per_step"] > 0
+    assert res["options"]["kernel"] in (0, 2)
+    sim.step(200)
+    sim.sync()
+    got = _fields(sim, scs)
+    for k, s in enumerate(scs):
+        assert_fields_close(got[k], oracle_run(s, 200))
+    again = sim.autotune(trial_steps=16, cache=str(tmp_path / "tune.json"), key="test3")
+    assert again == res          # served from the cache
+    sim.close()
+
+
+def test_persistent_barrier_timeout_is_reported_and_recoverable():
+    """One CTA never arrives at the grid barrier: every other CTA's bounded wait
+    runs out, the kernel returns, fdtd_sync reports FDTD_ETIMEOUT, and the same
+    context then runs correctly."""
+    from paper_2405_00814_gb300 import fdtd
+    scs, sim, _ = _batch(n=2, nsteps=64, lo=96, hi=160)
+    sim.set_option("kernel", 2)
+    sim.set_option("spin_limit", 20000)
+    sim.set_option("debug_skip_cta", 0)
+    sim.step(64)
+    with pytest.raises(fdtd.FDTDError) as ei:
+        sim.sync()
+    assert ei.value.code == fdtd.ETIMEOUT
+    sim.set_option("debug_skip_cta", -1)
+    sim.set_option("spin_limit", 4000000)
+    sim.reset()
+    sim.step(64)
+    sim.sync()
+    got = _fields(sim, scs)
+    for k, s in enumerate(scs):
+        assert_fields_close(got[k], oracle_run(s, 64))
+    sim.close()
