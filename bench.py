@@ -154,6 +154,59 @@ def adjoint_ratio(stream, reps=2):
             "timing": "host wall clock around synchronised calls, best of %d after one warm-up" % reps}
 
 
+def batch_throughput(stream, reps=2):
+    """64 uneven scenes (sides log-uniform 256..2048, 12-cell CPML), 2000 steps:
+    one autotuned context, timed solve (reset + 2000 steps) with CUDA events."""
+    import torch
+    from paper_2405_00814_gb300 import fdtd, scenes
+    scs = scenes.batch_scenes()
+    sim = fdtd.Simulation.batch(scs, stream=stream)
+    for k, s in enumerate(scs):
+        sim.select(k)
+        sim.set_scene_source(s.source)
+    tune = sim.autotune(trial_steps=16)
+    sim.set_option("graph", 1)
+    nsteps = scs[0].nsteps
+    best = None
+    for _ in range(reps + 1):
+        sim.reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(nsteps)
+        e1.record(stream)
+        sim.sync()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    sim.close()
+    cells = sum(s.cells for s in scs)
+    return {"workload": "batch64_tmz2d_sides256-2048_cpml12_2000steps", "cells": cells,
+            "cell_updates_per_s": cells * nsteps / (best / 1e3), "ms_per_solve": best,
+            "autotuned": tune["options"], "graph": True,
+            "timing": "CUDA events around one solve replayed from a CUDA graph, best of %d after one warm-up" % reps}
+
+
+def yee3d_throughput(stream, nsteps=200):
+    """512^3 box workload (64 dielectric boxes, 10-cell CPML, Ez dipole, DFT plane
+    at 3 frequencies): cell-updates/s over nsteps steps."""
+    import torch
+    from paper_2405_00814_gb300 import fdtd, scenes
+    sc = scenes.box_scene()
+    sim = fdtd.from_scene(sc, stream=stream)
+    sim.add_dft_plane(sc.dft_plane_k, ("ex", "ey", "ez"), sc.freqs)
+    sim.step(10)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(nsteps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    sim.close()
+    peak, _ = _peaks()
+    cu = sc.cells * nsteps / (ms / 1e3)
+    return {"workload": "yee3d_512^3_boxes64_cpml10_dftplane", "cell_updates_per_s": cu, "ms_per_step": ms / nsteps,
+            "hbm_roofline_frac_at_49B_per_cell_update": cu * 49.0 / (peak * 1e9)}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -322,6 +375,8 @@ def main():
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
     if not args.no_extras:
         out["adjoint"] = adjoint_ratio(stream)
+        out["batch"] = batch_throughput(stream)
+        out["yee3d"] = yee3d_throughput(stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sc, args.cpu_budget)
     if rank == 0:
