@@ -70,12 +70,14 @@ extern "C" {
 #define FDTD_SRC_SAMPLED 3   /* samples[n] = s((n+1) dt), n < n_samples; 0 after */
 
 /* options (fdtd_set_option) */
-#define FDTD_OPT_KERNEL 0    /* 0 = fused temporally blocked stream, two kernels per T-step block (default);
+#define FDTD_OPT_KERNEL 0    /* 2D: 0 = fused temporally blocked stream, two kernels per T-step block (default);
                                 1 = one H and one E launch per step;
                                 2 = persistent: one cooperative launch runs many T-step blocks of every scene,
-                                    warps pulling tasks from a shared counter, a bounded grid barrier between blocks */
+                                    warps pulling tasks from a shared counter, a bounded grid barrier between blocks.
+                                3D: 0 = fused z-marching kernel, 1 = one H and one E launch per step (default) */
 #define FDTD_OPT_TBLOCK 1    /* time steps per HBM pass of the fused kernel, 1..4 */
-#define FDTD_OPT_SEGMENT 2   /* rows per warp task of the fused kernel (multiple of 8, >= 8) */
+#define FDTD_OPT_SEGMENT 2   /* 2D: rows per warp task of the fused kernel (multiple of 8, >= 8);
+                                3D: planes per z-segment of the fused z-marching kernel (>= 1) */
 #define FDTD_OPT_WARPS 3     /* warps per CTA of the fused kernel, 1..8 */
 #define FDTD_OPT_GRAPH 4     /* 1: fdtd_step records its launches into a CUDA graph and replays it when called
                                 again with the same start step, step count and buffer parity (e.g. after fdtd_reset) */

@@ -597,7 +597,9 @@ int fdtd_set_option(fdtd_ctx* c, int option, int64_t v) {
             c->opt_tblock = (int)v;
             return FDTD_OK;
         case FDTD_OPT_SEGMENT:
-            if (v < 8 || v > (1 << 20) || v % 8) return fail(c, FDTD_EINVAL, "segment %lld must be a multiple of 8 >= 8", (long long)v);
+            // 2D: rows per warp task (multiple of 8); 3D: planes per z-segment (>= 1)
+            if (c->dims == 3 ? (v < 1 || v > (1 << 20)) : (v < 8 || v > (1 << 20) || v % 8))
+                return fail(c, FDTD_EINVAL, "segment %lld: 2D needs a multiple of 8 >= 8, 3D >= 1", (long long)v);
             c->opt_segment = (int)v;
             c->dirty = true;
             return FDTD_OK;

@@ -23,6 +23,10 @@
 
 using namespace gem;
 
+// x offset of cell i = 0 in a row: a 4-float left pad keeps every 32-cell tile
+// row 16-byte aligned for the fused kernel's staging
+constexpr int PX3 = 4;
+
 enum { G_EX = 0, G_EY, G_EZ, G_HX, G_HY, G_HZ,
        P_EXY, P_EXZ, P_EYZ, P_EYX, P_EZX, P_EZY, P_HXY, P_HXZ, P_HYZ, P_HYX, P_HZX, P_HZY, G_COUNT };
 
@@ -33,7 +37,8 @@ struct Sample3 {
 struct Scene3 {
     int nx, ny, nz, pitch, rows, planes, npml;
     double dx, dy, dz, dt;
-    float* f[G_COUNT];
+    float* f[G_COUNT];     // current state (the fused kernel writes g and swaps)
+    float* g[G_COUNT];
     uint8_t* d_mat;
     float4* d_coef;        // (Ca, Cb/dx, Cb/dy, Cb/dz)
     float* d_prof;         // x: bE cE bH cH [pitch]; y: [rows] x4; z: [planes] x4
@@ -47,6 +52,7 @@ struct Scene3 {
     float* d_rec;
     long long rec_cap;
     bool samp_dirty;
+    int kernel;            // 0 fused z-marching (default), 1 one H and one E launch per step
 };
 
 namespace {
@@ -99,8 +105,8 @@ void cpml_pt(double rho, int npml, double delta, double dt, double* b, double* c
     *cc = sig * (bb - 1.0) / (sig + alp);
 }
 
-void axis_prof(int n, int npml, double delta, double dt, int len, float* out) {
-    // out: bE[len] cE[len] bH[len] cH[len], cell i at i + 1
+void axis_prof(int n, int npml, double delta, double dt, int len, int off, float* out) {
+    // out: bE[len] cE[len] bH[len] cH[len], cell i at i + off
     for (int q = 0; q < 4 * len; q++) out[q] = 0.f;
     if (npml <= 0) return;
     for (int i = 0; i < n; i++) {
@@ -112,11 +118,11 @@ void axis_prof(int n, int npml, double delta, double dt, int len, float* out) {
         if (xh > hi) rH = xh - hi;
         double b, cc;
         cpml_pt(rE, npml, delta, dt, &b, &cc);
-        out[i + 1] = (float)b;
-        out[len + i + 1] = (float)cc;
+        out[i + off] = (float)b;
+        out[len + i + off] = (float)cc;
         cpml_pt(rH, npml, delta, dt, &b, &cc);
-        out[2 * len + i + 1] = (float)b;
-        out[3 * len + i + 1] = (float)cc;
+        out[2 * len + i + off] = (float)b;
+        out[3 * len + i + off] = (float)cc;
     }
 }
 
@@ -181,7 +187,7 @@ __global__ void k_h3(Dev3 S) {
     const int k = blockIdx.z;
     if (i >= S.nx || j >= S.ny) return;
     const size_t sy = S.pitch, sz = (size_t)S.pitch * S.rows;
-    const size_t c = ((size_t)(k + 1) * S.rows + (j + 1)) * S.pitch + (i + 1);
+    const size_t c = ((size_t)(k + 1) * S.rows + (j + 1)) * S.pitch + (i + PX3);
     const float* ex = S.f[G_EX];
     const float* ey = S.f[G_EY];
     const float* ez = S.f[G_EZ];
@@ -191,7 +197,7 @@ __global__ void k_h3(Dev3 S) {
     float deyx = ey[c + 1] - eyc, dexy = ex[c + sy] - exc;
     if (S.has_pml) {
         const P3 pr{S.prof, S.pitch, S.rows, S.planes};
-        const float bx = pr.bHx(i + 1), cx = pr.cHx(i + 1);
+        const float bx = pr.bHx(i + PX3), cx = pr.cHx(i + PX3);
         const float by = pr.bHy(j + 1), cy = pr.cHy(j + 1);
         const float bz = pr.bHz(k + 1), cz = pr.cHz(k + 1);
         dezy = cpml(S.f[P_HXY], c, by, cy, dezy);
@@ -213,7 +219,7 @@ __global__ void k_e3(Dev3 S) {
     const int k = blockIdx.z;
     if (i >= S.nx || j >= S.ny) return;
     const size_t sy = S.pitch, sz = (size_t)S.pitch * S.rows;
-    const size_t c = ((size_t)(k + 1) * S.rows + (j + 1)) * S.pitch + (i + 1);
+    const size_t c = ((size_t)(k + 1) * S.rows + (j + 1)) * S.pitch + (i + PX3);
     const float* hx = S.f[G_HX];
     const float* hy = S.f[G_HY];
     const float* hz = S.f[G_HZ];
@@ -234,29 +240,231 @@ __global__ void k_e3(Dev3 S) {
     if (i >= 1 && k >= 1) {
         if (pml) {
             dhxz = cpml(S.f[P_EYZ], c, pr.bEz(k + 1), pr.cEz(k + 1), dhxz);
-            dhzx = cpml(S.f[P_EYX], c, pr.bEx(i + 1), pr.cEx(i + 1), dhzx);
+            dhzx = cpml(S.f[P_EYX], c, pr.bEx(i + PX3), pr.cEx(i + PX3), dhzx);
         }
         S.f[G_EY][c] = co.x * S.f[G_EY][c] + co.w * dhxz - co.y * dhzx;
     }
     if (i >= 1 && j >= 1) {
         if (pml) {
-            dhyx = cpml(S.f[P_EZX], c, pr.bEx(i + 1), pr.cEx(i + 1), dhyx);
+            dhyx = cpml(S.f[P_EZX], c, pr.bEx(i + PX3), pr.cEx(i + PX3), dhyx);
             dhxy = cpml(S.f[P_EZY], c, pr.bEy(j + 1), pr.cEy(j + 1), dhxy);
         }
         S.f[G_EZ][c] = co.x * S.f[G_EZ][c] + co.y * dhyx - co.z * dhxy;
     }
 }
 
+// ---------------------------------------------------------------------------
+// fused z-marching step: one CTA owns a TX x TY tile of (i, j) and a z-segment
+// [kA, kB).  Per plane k it stages E^n(k+1) with a one-cell halo in shared
+// memory, updates H(k) on the tile plus its low halo (i0-1 column, j0-1 row,
+// recomputed from the read-only input so no other CTA is waited on), then E(k)
+// on the tile, with H(k-1) of its own column carried in registers.  Reads
+// buffer `in`, writes buffer `out`.  A segment starting above k = 0 first
+// recomputes H(kA-1) (warm-up plane, nothing stored).
+// ---------------------------------------------------------------------------
+constexpr int TX3 = 32, TY3 = 8;
+
+struct Bufs3 {
+    const float* in[G_COUNT];
+    float* out[G_COUNT];
+};
+
+__device__ __forceinline__ void cpa16(float* smem, const float* gmem, bool valid) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(valid ? 16 : 0) : "memory");
+}
+
+constexpr int EW3 = 40;   // staged E row: storage columns [i0, i0 + 40) = cells i0 - 4 .. i0 + 35
+constexpr int HW3 = 36;   // staged H row: cells i0 - 4 .. i0 + 31
+
+__global__ void __launch_bounds__(TX3 * TY3) k_yee3d_fused(Dev3 S, Bufs3 B, int segz) {
+    __shared__ __align__(16) float Eb[3][3][TY3 + 2][EW3];   // E^n, planes k, k+1, k+2 (ring by plane % 3)
+    __shared__ __align__(16) float Hb[2][3][TY3 + 1][HW3];   // H^{n-1/2}, planes k, k+1 (ring by plane % 2)
+    __shared__ float Ht[3][TY3 + 1][TX3 + 1];                // H^{n+1/2}(k) on the tile and its low halo
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX3 + tx;
+    const int i0 = blockIdx.x * TX3, j0 = blockIdx.y * TY3;
+    const int kA = blockIdx.z * segz, kB = min(kA + segz, S.nz);
+    const size_t plane = (size_t)S.pitch * S.rows;
+    // storage index of (column s of the staged row, row jj, plane k); column 0 is cell i0 - 4
+    auto sidx = [&](int jj, int k) { return ((size_t)(k + 1) * S.rows + (jj + 1)) * S.pitch + i0; };
+    const P3 pr{S.prof, S.pitch, S.rows, S.planes};
+    const bool pml = S.has_pml != 0;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool own = i < S.nx && j < S.ny;
+
+    // staging: 16-byte copies of whole aligned row pieces; rows beyond the
+    // padded array (jj > ny) and planes beyond nz read as zeros
+    auto issue_e = [&](int k) {
+        const int b = k % 3;
+        for (int q = tid; q < 3 * (TY3 + 2) * (EW3 / 4); q += TX3 * TY3) {
+            const int comp = q / ((TY3 + 2) * (EW3 / 4));
+            const int r = q % ((TY3 + 2) * (EW3 / 4));
+            const int qy = r / (EW3 / 4), v = r % (EW3 / 4);
+            const int jj = j0 - 1 + qy;
+            const bool in = jj <= S.ny && k <= S.nz;
+            cpa16(&Eb[b][comp][qy][4 * v], B.in[G_EX + comp] + (in ? sidx(jj, k) + 4 * v : 0), in);
+        }
+    };
+    auto issue_h = [&](int k) {
+        const int b = k & 1;
+        for (int q = tid; q < 3 * (TY3 + 1) * (HW3 / 4); q += TX3 * TY3) {
+            const int comp = q / ((TY3 + 1) * (HW3 / 4));
+            const int r = q % ((TY3 + 1) * (HW3 / 4));
+            const int qy = r / (HW3 / 4), v = r % (HW3 / 4);
+            const int jj = j0 - 1 + qy;
+            const bool in = jj <= S.ny && k < S.nz;
+            cpa16(&Hb[b][comp][qy][4 * v], B.in[G_HX + comp] + (in ? sidx(jj, k) + 4 * v : 0), in);
+        }
+    };
+
+    // this thread's H cells (tile + low halo, (TY3+1) x (TX3+1) = 297 of them)
+    // and their x/y CPML profiles, fixed for the whole march
+    constexpr int NHC = ((TY3 + 1) * (TX3 + 1) + TX3 * TY3 - 1) / (TX3 * TY3);
+    int hq[NHC], hqy[NHC], hqx[NHC];
+    float hbx[NHC], hcx[NHC], hby[NHC], hcy[NHC];
+#pragma unroll
+    for (int u = 0; u < NHC; u++) {
+        hq[u] = tid + u * TX3 * TY3;
+        hqy[u] = hq[u] / (TX3 + 1);
+        hqx[u] = hq[u] % (TX3 + 1);
+        const int ii = i0 - 1 + hqx[u], jj = j0 - 1 + hqy[u];
+        const bool ok = hq[u] < (TY3 + 1) * (TX3 + 1) && ii >= 0 && jj >= 0 && ii < S.nx && jj < S.ny;
+        hbx[u] = ok && pml ? pr.bHx(ii + PX3) : 0.f;
+        hcx[u] = ok && pml ? pr.cHx(ii + PX3) : 0.f;
+        hby[u] = ok && pml ? pr.bHy(jj + 1) : 0.f;
+        hcy[u] = ok && pml ? pr.cHy(jj + 1) : 0.f;
+    }
+    const float ebx = own && pml ? pr.bEx(i + PX3) : 0.f, ecx = own && pml ? pr.cEx(i + PX3) : 0.f;
+    const float eby = own && pml ? pr.bEy(j + 1) : 0.f, ecy = own && pml ? pr.cEy(j + 1) : 0.f;
+
+    const int kf = kA > 0 ? kA - 1 : 0;
+    issue_e(kf);
+    issue_e(kf + 1);
+    issue_h(kf);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    float hx_prev = 0.f, hy_prev = 0.f;   // H(k-1) of this thread's column (zero pad below k = 0)
+    const size_t own_row = ((size_t)(j + 1)) * S.pitch + (i + PX3);
+    uint8_t m_next = own ? S.mat[(size_t)((kf < kA ? kA : kf) + 1) * plane + own_row] : 0;
+    for (int k = kf; k < kB; k++) {
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncthreads();
+        // prefetch plane k+1's inputs while plane k computes (their slots held plane k-1)
+        if (k + 1 < kB) {
+            issue_e(k + 2);
+            issue_h(k + 1);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        const uint8_t m_cur = m_next;
+        if (own && k + 1 < kB) m_next = S.mat[(size_t)(k + 2) * plane + own_row];
+        const int ec = k % 3, en = (k + 1) % 3, hb = k & 1;
+        const float bz = pml ? pr.bHz(k + 1) : 0.f, cz = pml ? pr.cHz(k + 1) : 0.f;
+        // ---- layer 1 on the tile and its low halo ----
+#pragma unroll
+        for (int u = 0; u < NHC; u++) {
+            if (hq[u] >= (TY3 + 1) * (TX3 + 1)) break;
+            const int qy = hqy[u], qx = hqx[u];
+            const int ii = i0 - 1 + qx, jj = j0 - 1 + qy;
+            float hx = 0.f, hy = 0.f, hz = 0.f;
+            if (ii >= 0 && jj >= 0 && ii < S.nx && jj < S.ny) {
+                const int sx = qx + 3;   // staged column of cell ii
+                const size_t c = (size_t)(k + 1) * plane + (size_t)(jj + 1) * S.pitch + (ii + PX3);
+                const float exc = Eb[ec][0][qy][sx], eyc = Eb[ec][1][qy][sx], ezc = Eb[ec][2][qy][sx];
+                float dezy = Eb[ec][2][qy + 1][sx] - ezc;
+                float deyz = Eb[en][1][qy][sx] - eyc;
+                float dexz = Eb[en][0][qy][sx] - exc;
+                float dezx = Eb[ec][2][qy][sx + 1] - ezc;
+                float deyx = Eb[ec][1][qy][sx + 1] - eyc;
+                float dexy = Eb[ec][0][qy + 1][sx] - exc;
+                const bool owned = ii >= i0 && jj >= j0 && k >= kA;   // halo and warm-up values are not stored
+                auto ps = [&](int slot, float bb, float cc, float d) {
+                    if (bb == 0.f && cc == 0.f) return d;
+                    const float vv = bb * B.in[slot][c] + cc * d;
+                    if (owned) B.out[slot][c] = vv;
+                    return d + vv;
+                };
+                if (pml) {
+                    dezy = ps(P_HXY, hby[u], hcy[u], dezy);
+                    deyz = ps(P_HXZ, bz, cz, deyz);
+                    dexz = ps(P_HYZ, bz, cz, dexz);
+                    dezx = ps(P_HYX, hbx[u], hcx[u], dezx);
+                    deyx = ps(P_HZX, hbx[u], hcx[u], deyx);
+                    dexy = ps(P_HZY, hby[u], hcy[u], dexy);
+                }
+                const int hx_ = qx + 3;
+                hx = Hb[hb][0][qy][hx_] - (S.cdy * dezy - S.cdz * deyz);
+                hy = Hb[hb][1][qy][hx_] - (S.cdz * dexz - S.cdx * dezx);
+                hz = Hb[hb][2][qy][hx_] - (S.cdx * deyx - S.cdy * dexy);
+                if (owned) {
+                    B.out[G_HX][c] = hx;
+                    B.out[G_HY][c] = hy;
+                    B.out[G_HZ][c] = hz;
+                }
+            }
+            Ht[0][qy][qx] = hx;
+            Ht[1][qy][qx] = hy;
+            Ht[2][qy][qx] = hz;
+        }
+        __syncthreads();
+        // ---- layer 2 on the tile ----
+        const float hxc = Ht[0][ty + 1][tx + 1], hyc = Ht[1][ty + 1][tx + 1], hzc = Ht[2][ty + 1][tx + 1];
+        if (own && k >= kA) {
+            const size_t c = (size_t)(k + 1) * plane + own_row;
+            const float4 co = S.coef[m_cur];
+            const float bez = pml ? pr.bEz(k + 1) : 0.f, cez = pml ? pr.cEz(k + 1) : 0.f;
+            float dhzy = hzc - Ht[2][ty][tx + 1], dhyz = hyc - hy_prev;
+            float dhxz = hxc - hx_prev, dhzx = hzc - Ht[2][ty + 1][tx];
+            float dhyx = hyc - Ht[1][ty + 1][tx], dhxy = hxc - Ht[0][ty][tx + 1];
+            const int sx = tx + 4;
+            const float exc = Eb[ec][0][ty + 1][sx], eyc = Eb[ec][1][ty + 1][sx], ezc = Eb[ec][2][ty + 1][sx];
+            auto ps = [&](int slot, float bb, float cc, float d) {
+                if (bb == 0.f && cc == 0.f) return d;
+                const float vv = bb * B.in[slot][c] + cc * d;
+                B.out[slot][c] = vv;
+                return d + vv;
+            };
+            float ex = exc, ey = eyc, ez = ezc;
+            if (j >= 1 && k >= 1) {
+                if (pml) {
+                    dhzy = ps(P_EXY, eby, ecy, dhzy);
+                    dhyz = ps(P_EXZ, bez, cez, dhyz);
+                }
+                ex = co.x * exc + co.z * dhzy - co.w * dhyz;
+            }
+            if (i >= 1 && k >= 1) {
+                if (pml) {
+                    dhxz = ps(P_EYZ, bez, cez, dhxz);
+                    dhzx = ps(P_EYX, ebx, ecx, dhzx);
+                }
+                ey = co.x * eyc + co.w * dhxz - co.y * dhzx;
+            }
+            if (i >= 1 && j >= 1) {
+                if (pml) {
+                    dhyx = ps(P_EZX, ebx, ecx, dhyx);
+                    dhxy = ps(P_EZY, eby, ecy, dhxy);
+                }
+                ez = co.x * ezc + co.y * dhyx - co.z * dhxy;
+            }
+            B.out[G_EX][c] = ex;
+            B.out[G_EY][c] = ey;
+            B.out[G_EZ][c] = ez;
+        }
+        hx_prev = hxc;
+        hy_prev = hyc;
+        __syncthreads();
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 __global__ void k_src_rec3(Dev3 S, int si, int sj, int sk, int scomp, const float* wave, long long wlen,
                            const Sample3* samp, int n_samp, float* rec, long long n) {
     if (threadIdx.x == 0 && si >= 0 && n < wlen) {
-        const size_t c = ((size_t)(sk + 1) * S.rows + (sj + 1)) * S.pitch + (si + 1);
+        const size_t c = ((size_t)(sk + 1) * S.rows + (sj + 1)) * S.pitch + (si + PX3);
         S.f[scomp][c] += wave[n];
     }
     __syncthreads();
     for (int q = threadIdx.x; q < n_samp; q += blockDim.x) {
         const Sample3 sp = samp[q];
-        const size_t c = ((size_t)(sp.k + 1) * S.rows + (sp.j + 1)) * S.pitch + (sp.i + 1);
+        const size_t c = ((size_t)(sp.k + 1) * S.rows + (sp.j + 1)) * S.pitch + (sp.i + PX3);
         rec[n * n_samp + sp.slot] = S.f[sp.comp][c];
     }
 }
@@ -274,7 +482,7 @@ __global__ void k_dft_plane3(Dev3 S, int plane_k, int comp_mask, const double* f
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= S.nx || j >= S.ny) return;
-    const size_t c = ((size_t)(plane_k + 1) * S.rows + (j + 1)) * S.pitch + (i + 1);
+    const size_t c = ((size_t)(plane_k + 1) * S.rows + (j + 1)) * S.pitch + (i + PX3);
     const size_t plane = (size_t)S.nx * S.ny;
     const size_t cell = (size_t)j * S.nx + i;
     const float fdt = (float)dt;
@@ -317,7 +525,7 @@ __global__ void k_finite3(Dev3 S, int* bad) {
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
     if (i >= S.nx || j >= S.ny) return;
-    const size_t c = ((size_t)(k + 1) * S.rows + (j + 1)) * S.pitch + (i + 1);
+    const size_t c = ((size_t)(k + 1) * S.rows + (j + 1)) * S.pitch + (i + PX3);
     float v = 0.f;
     for (int q = 0; q < 6; q++) v += S.f[q][c];
     if (!isfinite(v)) atomicOr(bad, 1);
@@ -325,8 +533,10 @@ __global__ void k_finite3(Dev3 S, int* bad) {
 
 void scene3_free(Scene3* s) {
     if (!s) return;
-    for (int q = 0; q < G_COUNT; q++)
+    for (int q = 0; q < G_COUNT; q++) {
         if (s->f[q]) cudaFree(s->f[q]);
+        if (s->g[q]) cudaFree(s->g[q]);
+    }
     if (s->d_mat) cudaFree(s->d_mat);
     if (s->d_coef) cudaFree(s->d_coef);
     if (s->d_prof) cudaFree(s->d_prof);
@@ -439,12 +649,12 @@ int fdtd_create3(const fdtd_grid* g, double dx, double dt, double courant, const
         if (mat[q] >= n_mat) return fail3(c, FDTD_EINVAL, "material index %d >= n_mat %d", mat[q], n_mat);
 
     Scene3* s = new Scene3();
-    for (int q = 0; q < G_COUNT; q++) s->f[q] = nullptr;
+    for (int q = 0; q < G_COUNT; q++) s->f[q] = s->g[q] = nullptr;
     s->d_mat = nullptr; s->d_coef = nullptr; s->d_prof = nullptr; s->d_src = nullptr; s->d_samp = nullptr;
     s->d_rec = nullptr;
     s->nx = g->nx; s->ny = g->ny; s->nz = g->nz; s->npml = npml;
     s->dx = dx; s->dy = dy; s->dz = dz; s->dt = dt;
-    s->pitch = (g->nx + 2 + 31) / 32 * 32;
+    s->pitch = (g->nx + PX3 + 40 + 31) / 32 * 32;   // room for the last tile's 40-float staging rows
     s->rows = g->ny + 2;
     s->planes = g->nz + 2;
     s->src_kind = -1; s->src_i = s->src_j = s->src_k = -1; s->src_comp = G_EZ; s->src_param = 0; s->src_cap = 0;
@@ -455,16 +665,18 @@ int fdtd_create3(const fdtd_grid* g, double dx, double dt, double courant, const
     for (int q = 0; q < G_COUNT; q++) {
         // psi arrays exist only when there is a CPML
         if (q >= P_EXY && npml == 0) break;
-        if (cudaMalloc(&s->f[q], n * sizeof(float)) != cudaSuccess) {
+        // two copies: the fused kernel reads one and writes the other
+        if (cudaMalloc(&s->f[q], n * sizeof(float)) != cudaSuccess || cudaMalloc(&s->g[q], n * sizeof(float)) != cudaSuccess) {
             cudaGetLastError();
             return fail3(c, FDTD_ENOMEM, "3D field array of %zu bytes", n * sizeof(float));
         }
         CK3(cudaMemsetAsync(s->f[q], 0, n * sizeof(float), c->stream), "memset");
+        CK3(cudaMemsetAsync(s->g[q], 0, n * sizeof(float), c->stream), "memset");
     }
     std::vector<uint8_t> pm(n, 0);
     for (int k = 0; k < s->nz; k++)
         for (int j = 0; j < s->ny; j++)
-            memcpy(&pm[((size_t)(k + 1) * s->rows + j + 1) * s->pitch + 1], mat + ((size_t)k * s->ny + j) * s->nx, s->nx);
+            memcpy(&pm[((size_t)(k + 1) * s->rows + j + 1) * s->pitch + PX3], mat + ((size_t)k * s->ny + j) * s->nx, s->nx);
     std::vector<float4> co(256, make_float4(0, 0, 0, 0));
     for (int m = 0; m < n_mat; m++) {
         const double eps = kEps0 * table[m].eps_r;
@@ -473,9 +685,9 @@ int fdtd_create3(const fdtd_grid* g, double dx, double dt, double courant, const
         co[m] = make_float4((float)(am / ap), (float)(cb / dx), (float)(cb / dy), (float)(cb / dz));
     }
     std::vector<float> prof(4 * ((size_t)s->pitch + s->rows + s->planes), 0.f);
-    axis_prof(s->nx, npml, dx, dt, s->pitch, prof.data());
-    axis_prof(s->ny, npml, dy, dt, s->rows, prof.data() + 4 * s->pitch);
-    axis_prof(s->nz, npml, dz, dt, s->planes, prof.data() + 4 * s->pitch + 4 * s->rows);
+    axis_prof(s->nx, npml, dx, dt, s->pitch, PX3, prof.data());
+    axis_prof(s->ny, npml, dy, dt, s->rows, 1, prof.data() + 4 * s->pitch);
+    axis_prof(s->nz, npml, dz, dt, s->planes, 1, prof.data() + 4 * s->pitch + 4 * s->rows);
     if (cudaMalloc(&s->d_mat, n) != cudaSuccess || cudaMalloc(&s->d_coef, 256 * sizeof(float4)) != cudaSuccess ||
         cudaMalloc(&s->d_prof, prof.size() * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
@@ -600,16 +812,30 @@ int fdtd_step3(fdtd_ctx* c, int64_t n_steps) {
     if (!s) return fail3(c, FDTD_ESTATE, "no 3D scene");
     int rc = ensure3(c, c->t + n_steps);
     if (rc) return rc;
-    const Dev3 d = dev_of(s);
+    Dev3 d = dev_of(s);
     const dim3 blk(32, 8);
     const dim3 grd((s->nx + 31) / 32, (s->ny + 7) / 8, s->nz);
     const dim3 grp((s->nx + 31) / 32, (s->ny + 7) / 8, 1);
     const int si = s->src_kind >= 0 ? s->src_i : -1;
+    const int segz = std::max(1, c->opt_segment);
+    const dim3 gfz((s->nx + TX3 - 1) / TX3, (s->ny + TY3 - 1) / TY3, (s->nz + segz - 1) / segz);
     for (int64_t q = 0; q < n_steps; q++) {
         const long long n = c->t + q;
-        k_h3<<<grd, blk, 0, c->stream>>>(d);
-        k_e3<<<grd, blk, 0, c->stream>>>(d);
-        c->launches += 2;
+        if (c->opt_kernel == 1) {
+            k_h3<<<grd, blk, 0, c->stream>>>(d);
+            k_e3<<<grd, blk, 0, c->stream>>>(d);
+            c->launches += 2;
+        } else {
+            Bufs3 b;
+            for (int w = 0; w < G_COUNT; w++) {
+                b.in[w] = s->f[w];
+                b.out[w] = s->g[w];
+            }
+            k_yee3d_fused<<<gfz, dim3(TX3, TY3), 0, c->stream>>>(d, b, segz);
+            c->launches++;
+            for (int w = 0; w < G_COUNT; w++) std::swap(s->f[w], s->g[w]);
+            d = dev_of(s);
+        }
         if (si >= 0 || !s->samples.empty()) {
             k_src_rec3<<<1, 128, 0, c->stream>>>(d, si, s->src_j, s->src_k, s->src_comp, s->d_src,
                                                  s->src_kind >= 0 ? s->src_cap : 0, s->d_samp, (int)s->samples.size(),
@@ -667,7 +893,7 @@ static cudaMemcpy3DParms copy3(const Scene3* s, float* dev_base, float* host, bo
     memset(&p, 0, sizeof(p));
     cudaPitchedPtr dp = make_cudaPitchedPtr(dev_base, (size_t)s->pitch * sizeof(float), s->pitch, s->rows);
     cudaPitchedPtr hp = make_cudaPitchedPtr(host, (size_t)s->nx * sizeof(float), s->nx, s->ny);
-    const cudaPos dpos = make_cudaPos(sizeof(float), 1, 1);
+    const cudaPos dpos = make_cudaPos(PX3 * sizeof(float), 1, 1);
     const cudaPos hpos = make_cudaPos(0, 0, 0);
     if (to_dev) {
         p.srcPtr = hp; p.srcPos = hpos; p.dstPtr = dp; p.dstPos = dpos;
@@ -703,8 +929,10 @@ int fdtd_set_field3(fdtd_ctx* c, int comp, const float* in, int on_device) {
 int fdtd_reset3(fdtd_ctx* c) {
     Scene3* s = S3(c);
     const size_t n = (size_t)s->pitch * s->rows * s->planes * sizeof(float);
-    for (int q = 0; q < G_COUNT; q++)
+    for (int q = 0; q < G_COUNT; q++) {
         if (s->f[q]) CK3(cudaMemsetAsync(s->f[q], 0, n, c->stream), "reset");
+        if (s->g[q]) CK3(cudaMemsetAsync(s->g[q], 0, n, c->stream), "reset");
+    }
     if (s->d_rec) CK3(cudaMemsetAsync(s->d_rec, 0, (size_t)s->rec_cap * s->samples.size() * sizeof(float), c->stream), "reset");
     for (DftMon& m : c->mons) {
         int ncomp = 1;

@@ -71,7 +71,8 @@ def test_3d_cavity_mode_closed_form():
     sim.close()
 
 
-def test_3d_boxes_cpml_probes_plane_dft():
+@pytest.mark.parametrize("kernel,segz", [(0, 64), (0, 7), (1, 64)])
+def test_3d_boxes_cpml_probes_plane_dft(kernel, segz):
     from paper_2405_00814_gb300 import fdtd
     sc = scenes.box_scene(side=40, nsteps=150, npml=6, n_boxes=10)
     sc.source = scenes.Source(20, 20, 20, component="ez", kind="ricker", params=(40e9,))
@@ -80,6 +81,8 @@ def test_3d_boxes_cpml_probes_plane_dft():
     probes = [(12, 14, 22, "ez"), (25, 9, 30, "hx"), (30, 30, 10, "ey")]
     o = _oracle3(sc, 150, samples=probes, plane=True)
     sim = fdtd.from_scene(sc)
+    sim.set_option("kernel", kernel)
+    sim.set_option("segment", segz)
     pids = [sim.add_probe(i, j, k, c) for i, j, k, c in probes]
     mid = sim.add_dft_plane(sc.dft_plane_k, ("ex", "ey", "ez"), sc.freqs)
     sim.step(150)
@@ -101,6 +104,7 @@ def test_3d_full_size_512_light_cone():
     sc = scenes.box_scene()
     n = 110
     sim = fdtd.from_scene(sc)
+    sim.set_option("kernel", 1)
     sim.step(n)
     si, sj, sk = sc.source.i, sc.source.j, sc.source.k
     h = n + 2
