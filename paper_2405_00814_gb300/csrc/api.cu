@@ -250,11 +250,16 @@ fdtd_ctx* ctx_new(void* stream) {
     c->d_tasks_b = nullptr;
     c->n_tasks_b = 0;
     c->warps_b = 2;
-    c->aux = nullptr;
-    c->ev_fork = c->ev_join = nullptr;
+    c->d_tasks_l = nullptr;
+    c->n_tasks_l = 0;
+    c->warps_l = 4;
+    c->aux = c->aux2 = nullptr;
+    c->ev_fork = c->ev_join = c->ev_join2 = nullptr;
     cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
+    cudaStreamCreateWithFlags(&c->aux2, cudaStreamNonBlocking);
     cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming);
     c->d_samp = nullptr;
     c->d_samp_scene = nullptr;
     c->d_samp_off = nullptr;
@@ -360,12 +365,12 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     // list, the rest to the interior list; each list is padded to whole CTAs
     // per scene so that a CTA never mixes scenes.
     const int wout = STRIP - 2 * HALO;
-    std::vector<Task> tasks, tasks_b;
+    std::vector<Task> tasks, tasks_b, tasks_l;
     std::vector<Sample2> tsamp;
-    const int warps_b = 2;
+    const int warps_b = 2, warps_l = 4;
     for (int k = 0; k < ns; k++) {
         Scene2* s = c->s2[k];
-        const size_t first = tasks.size(), first_b = tasks_b.size();
+        const size_t first = tasks.size(), first_b = tasks_b.size(), first_l = tasks_l.size();
         // Tasks with a CPML slab, the design rectangle, the source or a probe in
         // reach, or a ragged right edge, run the general kernel ("boundary" list);
         // the rest run the lean interior kernel.  General warps are heavier per
@@ -396,7 +401,8 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
             for (const Sample2& sp : s->samples)
                 if (sp.i >= x0 && sp.i < x0 + wout && sp.j >= ya && sp.j < yb) tsamp.push_back(sp);
             t.samp_end = (int)tsamp.size();
-            if (general) tasks_b.push_back(t);
+            if (t.flags & TASK_PML) tasks_b.push_back(t);
+            else if (general) tasks_l.push_back(t);
             else tasks.push_back(t);
         };
         for (int ya = 0; ya < s->ny; ya += seg) {
@@ -418,6 +424,8 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
             while ((tasks.size() - first) % warps) tasks.push_back(pad);
         if (tasks_b.size() > first_b)
             while ((tasks_b.size() - first_b) % warps_b) tasks_b.push_back(pad);
+        if (tasks_l.size() > first_l)
+            while ((tasks_l.size() - first_l) % warps_l) tasks_l.push_back(pad);
     }
     std::vector<Sample2> ssamp;
     std::vector<int> soff(ns + 1, 0);
@@ -429,10 +437,14 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     std::vector<Task> all;
     for (const Task& t : tasks_b)
         if (t.scene >= 0) all.push_back(t);
+    for (const Task& t : tasks_l)
+        if (t.scene >= 0) all.push_back(t);
     for (const Task& t : tasks)
         if (t.scene >= 0) all.push_back(t);
     dfree(c->d_scenes); dfree(c->d_tasks); dfree(c->d_tasks_b); dfree(c->d_samp); dfree(c->d_samp_scene); dfree(c->d_samp_off);
     dfree(c->d_tasks_all);
+    dfree(c->d_tasks_l);
+    c->d_tasks_l = nullptr;
     c->d_scenes = nullptr; c->d_tasks = nullptr; c->d_tasks_b = nullptr; c->d_samp = nullptr; c->d_samp_scene = nullptr;
     c->d_samp_off = nullptr; c->d_tasks_all = nullptr;
     int rc;
@@ -440,6 +452,7 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     if ((rc = dalloc(c, &c->d_tasks, tasks.size() * sizeof(Task), "tasks"))) return rc;
     if ((rc = dalloc(c, &c->d_tasks_b, tasks_b.size() * sizeof(Task), "tasks"))) return rc;
     if ((rc = dalloc(c, &c->d_tasks_all, all.size() * sizeof(Task), "tasks"))) return rc;
+    if ((rc = dalloc(c, &c->d_tasks_l, tasks_l.size() * sizeof(Task), "tasks"))) return rc;
     if ((rc = dalloc(c, &c->d_samp, tsamp.size() * sizeof(Sample2), "samples"))) return rc;
     if ((rc = dalloc(c, &c->d_samp_scene, ssamp.size() * sizeof(Sample2), "samples"))) return rc;
     if ((rc = dalloc(c, &c->d_samp_off, soff.size() * sizeof(int), "sample offsets"))) return rc;
@@ -450,6 +463,8 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
         CK(cudaMemcpyAsync(c->d_tasks_b, tasks_b.data(), tasks_b.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
     if (!all.empty())
         CK(cudaMemcpyAsync(c->d_tasks_all, all.data(), all.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
+    if (!tasks_l.empty())
+        CK(cudaMemcpyAsync(c->d_tasks_l, tasks_l.data(), tasks_l.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
     if (!tsamp.empty())
         CK(cudaMemcpyAsync(c->d_samp, tsamp.data(), tsamp.size() * sizeof(Sample2), cudaMemcpyHostToDevice, c->stream), "upload");
     if (!ssamp.empty())
@@ -459,6 +474,8 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     c->n_tasks = (int)tasks.size();
     c->n_tasks_b = (int)tasks_b.size();
     c->n_tasks_all = (int)all.size();
+    c->n_tasks_l = (int)tasks_l.size();
+    c->warps_l = warps_l;
     c->warps_b = warps_b;
     c->task_tb = T;
     c->task_seg = seg;
@@ -565,9 +582,12 @@ void fdtd_destroy(fdtd_ctx* c) {
     if (c->h_err) cudaFreeHost(c->h_err);
     if (c->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    dfree(c->d_tasks_l);
     if (c->aux) cudaStreamDestroy(c->aux);
+    if (c->aux2) cudaStreamDestroy(c->aux2);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_join2) cudaEventDestroy(c->ev_join2);
     delete c;
 }
 

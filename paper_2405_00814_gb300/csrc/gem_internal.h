@@ -59,11 +59,13 @@ struct TmzDev {
     const float4* dsg_coef;             // [dsg_h][dsg_w] (Ca, Cb/dx, Cb/dy, Cb)
     // reverse mode: forward recompute records E^n and curl H^{n+1/2} over the
     // design rectangle; the adjoint kernels read them, inject dL/dE^{n+1} at the
-    // monitor cells and accumulate dL/deps_r
+    // monitor cells and keep dL/dE^{n+1} over the design rectangle, which a
+    // reduction after each segment turns into dL/deps_r
     float* dsg_rec;                     // [steps][2][dsg_h * dsg_w], step n at n - dsg_rec_n0
     long long dsg_rec_n0, dsg_rec_len;
     const float2* dsg_dcoef;            // [dsg_h][dsg_w] (dCa/deps_r, dCb/deps_r)
     float* grad;                        // [dsg_h][dsg_w]
+    float* adj_rec;                     // [steps][dsg_h * dsg_w]: dL/dE^{n+1}, step n at n - dsg_rec_n0
     const float* adj_src;               // [steps][n_adj]: dL/dE^{n+1} at adjoint source cells
     int n_adj;
     float rdx, rdy;                     // 1/dx, 1/dy
@@ -147,10 +149,12 @@ struct fdtd_ctx {
     bool dirty;
     gem::TmzDev* d_scenes;
     gem::Task* d_tasks;
-    gem::Task* d_tasks_b;          // boundary tasks (CPML slab or design rectangle in reach)
+    gem::Task* d_tasks_b;          // CPML tasks (a slab within reach)
     int n_tasks_b, warps_b;
-    cudaStream_t aux;              // forked stream for the boundary tasks
-    cudaEvent_t ev_fork, ev_join;
+    gem::Task* d_tasks_l;          // lite tasks: design, source, probes or ragged edge, no CPML
+    int n_tasks_l, warps_l;
+    cudaStream_t aux, aux2;        // forked streams for the CPML and lite tasks
+    cudaEvent_t ev_fork, ev_join, ev_join2;
     gem::Sample2* d_samp;          // samples in task order (fused kernel)
     gem::Sample2* d_samp_scene;    // samples in scene order (unfused kernels)
     int* d_samp_off;               // [n_scenes + 1] offsets into d_samp_scene

@@ -14,9 +14,10 @@
 //                        fy = -Db_y (1 + cHy) hx + cHy psi_hxy,
 //                        e(i,j) += fy(j-1) - fy(j) + fx(i-1) - fx(i),
 //                        psi_hxy <- bHy (psi_hxy - Db_y hx), psi_hyx <- bHx (psi_hyx + Db_x hy),
-// after dL/dE^{n+1} is added at the monitor cells and
-//   dL/deps_r += e (dCa/deps_r E^n + dCb/deps_r curlH^{n+1/2})
-// is accumulated over the design cells from the recomputed forward values.
+// after dL/dE^{n+1} is added at the monitor cells.  The sweep stores e over the
+// design cells for every step of a checkpoint segment; a reduction then forms
+//   dL/deps_r += sum_n e (dCa/deps_r E^n + dCb/deps_r curlH^{n+1/2})
+// from it and the recomputed forward values (no read-modify-write in the sweep).
 //
 // The kernel streams rows like the forward kernel: layer 2 transposed at row a
 // reads row a+1 at the previous level (the same-iteration ring slot), layer 1
@@ -24,7 +25,9 @@
 // skewed wavefront applies T reverse steps per HBM pass.  gy of the row above
 // is produced at the end of the previous level (no second coefficient lookup);
 // the general variant keeps fy of the row below in a per-level register ring
-// because that row's psi_hxy has already moved on.
+// because that row's psi_hxy has already moved on.  Three variants run side by
+// side on their own streams: CPML strips, strips near the design, adjoint
+// sources or the ragged edge (no CPML state), and clean interior strips.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -72,15 +75,17 @@ __device__ __forceinline__ float cget(const float4& v, int c) { return c == 0 ? 
 // Adjoint source entry of a task: cell (i, j) gets adj_src[n * n_adj + slot].
 // Reuses Sample2 {i, j, comp (unused), slot}.
 
-template <int T, bool GEN>
-__global__ void __launch_bounds__(256, GEN ? 1 : 2) k_adj(const TmzDev* __restrict__ scenes,
+// GEN: design rectangle, adjoint sources, ragged edge; PMLV: CPML auxiliaries
+template <int T, bool GEN, bool PMLV>
+__global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 : (GEN ? 3 : 2)) k_adj(const TmzDev* __restrict__ scenes,
                                                           const Task* __restrict__ tasks, int n_tasks,
                                                           const Sample2* __restrict__ srcs, int parity,
                                                           long long n_top) {
-    constexpr int Q = a_stages(T, GEN);
-    constexpr int PF = a_pf(T, GEN);
-    constexpr int SF4 = a_stage_f4(GEN);
-    constexpr int NS = a_nslot(GEN);
+    constexpr bool PV = GEN && PMLV;
+    constexpr int Q = a_stages(T, PV);
+    constexpr int PF = a_pf(T, PV);
+    constexpr int SF4 = a_stage_f4(PV);
+    constexpr int NS = a_nslot(PV);
     extern __shared__ float4 smem_f4[];
     __shared__ float4 coef_s[256];
 
@@ -111,7 +116,7 @@ __global__ void __launch_bounds__(256, GEN ? 1 : 2) k_adj(const TmzDev* __restri
     const int s_row = tk.ya - T;
     const int r_last = tk.yb + T - 1;
 
-    const bool pml = GEN && (tk.flags & TASK_PML) != 0;
+    const bool pml = PV && (tk.flags & TASK_PML) != 0;
     const bool dsg = GEN && (tk.flags & TASK_DSG) != 0;
     const bool has_src = GEN && tk.samp_end > tk.samp_begin;
     const int npml = S->has_pml;
@@ -119,7 +124,7 @@ __global__ void __launch_bounds__(256, GEN ? 1 : 2) k_adj(const TmzDev* __restri
     const int prow = S->rows;
     bool lane_px = false;
     float bex[4] = {0, 0, 0, 0}, cex[4] = {0, 0, 0, 0}, bhx[4] = {0, 0, 0, 0}, chx[4] = {0, 0, 0, 0};
-    if (GEN && pml) {
+    if (PV && pml) {
         lane_px = (cx < npml) || (cx + 3 >= nx - npml);
         if (lane_px)
             for (int q = 0; q < 4; q++) {
@@ -143,7 +148,7 @@ __global__ void __launch_bounds__(256, GEN ? 1 : 2) k_adj(const TmzDev* __restri
         acp16(st + 1 * 32 + lane, hx_in + g);
         acp16(st + 2 * 32 + lane, hy_in + g);
         acp4(reinterpret_cast<uint32_t*>(st + NS * 32) + lane, mat + g);
-        if constexpr (GEN) {
+        if constexpr (PV) {
             if (pml) {
                 if (lane_px) {
                     acp16(st + 3 * 32 + lane, psi_in[0] + g);
@@ -177,7 +182,7 @@ __global__ void __launch_bounds__(256, GEN ? 1 : 2) k_adj(const TmzDev* __restri
     // gy of a row whose adjoint state is final for the level just finished
     auto gy_of = [&](const float4& e, const float4* c, int row, const float4* sta) {
         float4 g = make_float4(-c[0].z * e.x, -c[1].z * e.y, -c[2].z * e.z, -c[3].z * e.w);
-        if constexpr (GEN) {
+        if constexpr (PV) {
             if (pml && yslab(row)) {
                 const float ce = pr[4 * pitch + prow + row + PAD_Y];
                 const float4 p = sta[4 * 32 + lane];
@@ -262,20 +267,17 @@ __global__ void __launch_bounds__(256, GEN ? 1 : 2) k_adj(const TmzDev* __restri
             // finished, or when it was loaded): dL/deps_r over owned design cells
             if constexpr (GEN) {
                 if (dsg && a >= tk.ya && a < tk.yb && out_lane) {
+                    // keep dL/dE^{n+1} of the owned design cells; a reduction after
+                    // the segment forms dL/deps_r from it and the recorded E^n, curl H
                     const int dj = a - S->dsg_j0;
                     const long long nr = n - S->dsg_rec_n0;
                     if (dj >= 0 && dj < S->dsg_h && nr >= 0 && nr < S->dsg_rec_len) {
                         const size_t hw = (size_t)S->dsg_w * S->dsg_h;
-                        const float* re = S->dsg_rec + (size_t)nr * 2 * hw + (size_t)dj * S->dsg_w;
-                        const float2* dc = S->dsg_dcoef + (size_t)dj * S->dsg_w;
-                        float* gr = S->grad + (size_t)dj * S->dsg_w;
+                        float* er = S->adj_rec + (size_t)nr * hw + (size_t)dj * S->dsg_w;
                         const int di = cx - S->dsg_i0;
                         for (int q = 0; q < 4; q++) {
                             const int d = di + q;
-                            if (d >= 0 && d < S->dsg_w) {
-                                const float2 k2 = dc[d];
-                                gr[d] += cget(E[t], q) * (k2.x * re[d] + k2.y * re[hw + d]);
-                            }
+                            if (d >= 0 && d < S->dsg_w) er[d] = cget(E[t], q);
                         }
                     }
                 }
@@ -285,7 +287,7 @@ __global__ void __launch_bounds__(256, GEN ? 1 : 2) k_adj(const TmzDev* __restri
             float4 ux = gx;
             float4 gya = make_float4(-c[0].z * E[t].x, -c[1].z * E[t].y, -c[2].z * E[t].z, -c[3].z * E[t].w);
             float4 uy = make_float4(-gya.x, -gya.y, -gya.z, -gya.w);                                      // (Cb/dy) e
-            if constexpr (GEN) {
+            if constexpr (PV) {
                 if (pml) {
                     if (lane_px) {
                         const float4 p = sta[3 * 32 + lane];
@@ -314,7 +316,7 @@ __global__ void __launch_bounds__(256, GEN ? 1 : 2) k_adj(const TmzDev* __restri
             X[t].y += gya.y - gyu.y;
             X[t].z += gya.z - gyu.z;
             X[t].w += gya.w - gyu.w;
-            if constexpr (GEN) {
+            if constexpr (PV) {
                 if (pml) {
                     if (lane_px) {
                         float4 p = sta[3 * 32 + lane];
@@ -343,7 +345,7 @@ __global__ void __launch_bounds__(256, GEN ? 1 : 2) k_adj(const TmzDev* __restri
             float4 fx = make_float4(dbx * Y[t].x, dbx * Y[t].y, dbx * Y[t].z, dbx * Y[t].w);
             float4 fya = make_float4(-dby * X[t].x, -dby * X[t].y, -dby * X[t].z, -dby * X[t].w);
             float4 fyd;   // fy of row a-1
-            if constexpr (GEN) {
+            if constexpr (PV) {
                 if (pml) {
                     if (lane_px) {
                         const float4 p = sta[6 * 32 + lane];
@@ -371,7 +373,7 @@ __global__ void __launch_bounds__(256, GEN ? 1 : 2) k_adj(const TmzDev* __restri
             E[t].y += fyd.y - fya.y + fx.x - fx.y;
             E[t].z += fyd.z - fya.z + fx.y - fx.z;
             E[t].w += fyd.w - fya.w + fx.z - fx.w;
-            if constexpr (GEN) {
+            if constexpr (PV) {
                 if (pml) {
                     if (yslab(a)) {
                         const float bh = pr[4 * pitch + 2 * prow + a + PAD_Y];
@@ -415,7 +417,7 @@ __global__ void __launch_bounds__(256, GEN ? 1 : 2) k_adj(const TmzDev* __restri
                         hy_out[g + q] = cget(Y[T], q);
                     }
                 }
-                if constexpr (GEN) {
+                if constexpr (PV) {
                     if (pml) {
                         const float4* sto = stage_of(o);
                         for (int q = 0; q < 4 && cx + q < nx; q++) {
@@ -439,24 +441,41 @@ __global__ void __launch_bounds__(256, GEN ? 1 : 2) k_adj(const TmzDev* __restri
     await_<0>();
 }
 
-template <int T>
-cudaError_t launch_adj_T(const fdtd_ctx* c, const TmzDev* dev, const Task* tasks, int n, int warps, const Task* gtasks,
-                         int gn, int gwarps, const Sample2* srcs, int parity, long long n_top, cudaStream_t st_main,
-                         cudaStream_t st_aux) {
-    cudaError_t e = cudaSuccess;
-    if (gn > 0) {
-        const size_t sm = adj_smem(T, gwarps, true);
-        e = cudaFuncSetAttribute(k_adj<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        k_adj<T, true><<<gn / gwarps, gwarps * 32, sm, st_aux>>>(dev, gtasks, gn, srcs, parity, n_top);
-    }
-    if (n > 0) {
-        const size_t sm = adj_smem(T, warps, false);
-        e = cudaFuncSetAttribute(k_adj<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        k_adj<T, false><<<n / warps, warps * 32, sm, st_main>>>(dev, tasks, n, srcs, parity, n_top);
-    }
+template <int T, bool GEN, bool PMLV>
+cudaError_t launch_adj_v(const TmzDev* dev, const Task* tasks, int n, int warps, const Sample2* srcs, int parity,
+                         long long n_top, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const size_t sm = adj_smem(T, warps, GEN && PMLV);
+    cudaError_t e = cudaFuncSetAttribute(k_adj<T, GEN, PMLV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_adj<T, GEN, PMLV><<<n / warps, warps * 32, sm, st>>>(dev, tasks, n, srcs, parity, n_top);
     return cudaGetLastError();
+}
+
+struct AdjLists {
+    const Task *t0, *t1, *t2;   // interior, CPML, lite
+    int n0, n1, n2, w0, w1, w2;
+};
+
+template <int T>
+cudaError_t launch_adj_T(const TmzDev* dev, const AdjLists& L, const Sample2* srcs, int parity, long long n_top,
+                         cudaStream_t s0, cudaStream_t s1, cudaStream_t s2) {
+    cudaError_t e = launch_adj_v<T, true, true>(dev, L.t1, L.n1, L.w1, srcs, parity, n_top, s1);
+    if (e == cudaSuccess) e = launch_adj_v<T, true, false>(dev, L.t2, L.n2, L.w2, srcs, parity, n_top, s2);
+    if (e == cudaSuccess) e = launch_adj_v<T, false, false>(dev, L.t0, L.n0, L.w0, srcs, parity, n_top, s0);
+    return e;
+}
+
+// dL/deps_r += sum over the segment's steps of e (dCa E^n + dCb curlH^{n+1/2})
+__global__ void k_grad_reduce(const float* __restrict__ rec, const float* __restrict__ erec,
+                              const float2* __restrict__ dc, float* __restrict__ grad, int hw, int len) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= hw) return;
+    const float2 k2 = dc[c];
+    float g = 0.f;
+    for (int s = 0; s < len; s++)
+        g += erec[(size_t)s * hw + c] * (k2.x * rec[(size_t)s * 2 * hw + c] + k2.y * rec[(size_t)s * 2 * hw + hw + c]);
+    grad[c] += g;
 }
 
 }  // namespace
@@ -614,15 +633,18 @@ int fdtd_adjoint_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, f
         for (void* p : to_free) cudaFree(p);
     };
     std::vector<TmzDev> fwd(ns), adj(ns);
-    std::vector<Task> tasks, tasks_g;
+    std::vector<Task> tasks, tasks_g, tasks_l;   // interior, CPML, lite general
     std::vector<Sample2> tsrc;
-    const int T = c->opt_tblock, seg = c->opt_segment, warps = c->opt_warps, gwarps = 2;
+    std::vector<float*> rec_of(ns), erec_of(ns), grad_of(ns);
+    std::vector<const float2*> dc_of(ns);
+    const int T = c->opt_tblock, seg = c->opt_segment, warps = c->opt_warps, gwarps = 2, lwarps = 4;
     for (int k = 0; k < ns; k++) {
         Scene2* s = c->s2[k];
         const size_t fb = field_bytes(s), hw = (size_t)s->dsg_w * s->dsg_h;
-        float *aset = nullptr, *rec = nullptr, *gr = nullptr, *src = nullptr;
+        float *aset = nullptr, *rec = nullptr, *erec = nullptr, *gr = nullptr, *src = nullptr;
         float2* dc = nullptr;
         if (!dmalloc(F_COUNT2 * 2 * fb, (void**)&aset) || !dmalloc((size_t)every * 2 * hw * sizeof(float), (void**)&rec) ||
+            !dmalloc((size_t)every * hw * sizeof(float), (void**)&erec) ||
             !dmalloc(hw * sizeof(float), (void**)&gr) || !dmalloc(hw * sizeof(float2), (void**)&dc) ||
             !dmalloc(tab[k].size() * sizeof(float), (void**)&src)) {
             cleanup();
@@ -656,11 +678,16 @@ int fdtd_adjoint_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, f
         d.dsg_rec_len = every;
         d.dsg_dcoef = dc;
         d.grad = gr;
+        d.adj_rec = erec;
         d.adj_src = src;
         d.n_adj = std::max(1, n_adj[k]);
         d.rdx = (float)(1.0 / s->dx);
         d.rdy = (float)(1.0 / s->dy);
         fwd[k] = d;
+        rec_of[k] = rec;
+        erec_of[k] = erec;
+        grad_of[k] = gr;
+        dc_of[k] = dc;
         TmzDev a = d;
         for (int f = 0; f < F_COUNT2; f++)
             for (int p = 0; p < 2; p++) a.f[f][p] = abuf[(size_t)k * F_COUNT2 * 2 + f * 2 + p];
@@ -670,7 +697,7 @@ int fdtd_adjoint_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, f
         // adjoint tasks: general if a CPML slab, the design rectangle or an
         // adjoint source is within reach, or the strip is ragged
         const int wout = STRIP - 2 * HALO;
-        const size_t first = tasks.size(), first_g = tasks_g.size();
+        const size_t first = tasks.size(), first_g = tasks_g.size(), first_l = tasks_l.size();
         for (int ya = 0; ya < s->ny; ya += seg) {
             for (int x0 = 0; x0 < s->nx; x0 += wout) {
                 const int lx0 = x0 - HALO, lx1 = x0 - HALO + STRIP;
@@ -701,7 +728,7 @@ int fdtd_adjoint_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, f
                     for (int y = ya; y < yb; y += segg) {
                         bool g2;
                         Task t2 = make(y, std::min(y + segg, yb), &g2);
-                        tasks_g.push_back(t2);
+                        (t2.flags & TASK_PML ? tasks_g : tasks_l).push_back(t2);
                     }
                 }
             }
@@ -713,13 +740,15 @@ int fdtd_adjoint_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, f
             while ((tasks.size() - first) % warps) tasks.push_back(pad);
         if (tasks_g.size() > first_g)
             while ((tasks_g.size() - first_g) % gwarps) tasks_g.push_back(pad);
+        if (tasks_l.size() > first_l)
+            while ((tasks_l.size() - first_l) % lwarps) tasks_l.push_back(pad);
     }
     TmzDev *d_fwd = nullptr, *d_adj = nullptr;
-    Task *d_t = nullptr, *d_tg = nullptr;
+    Task *d_t = nullptr, *d_tg = nullptr, *d_tl = nullptr;
     Sample2* d_src = nullptr;
     if (!dmalloc(ns * sizeof(TmzDev), (void**)&d_fwd) || !dmalloc(ns * sizeof(TmzDev), (void**)&d_adj) ||
         !dmalloc(tasks.size() * sizeof(Task), (void**)&d_t) || !dmalloc(tasks_g.size() * sizeof(Task), (void**)&d_tg) ||
-        !dmalloc(tsrc.size() * sizeof(Sample2), (void**)&d_src)) {
+        !dmalloc(tasks_l.size() * sizeof(Task), (void**)&d_tl) || !dmalloc(tsrc.size() * sizeof(Sample2), (void**)&d_src)) {
         cleanup();
         c->err = "adjoint: out of device memory";
         return FDTD_ENOMEM;
@@ -727,6 +756,7 @@ int fdtd_adjoint_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, f
     cudaMemcpyAsync(d_adj, adj.data(), ns * sizeof(TmzDev), cudaMemcpyHostToDevice, st);
     if (!tasks.empty()) cudaMemcpyAsync(d_t, tasks.data(), tasks.size() * sizeof(Task), cudaMemcpyHostToDevice, st);
     if (!tasks_g.empty()) cudaMemcpyAsync(d_tg, tasks_g.data(), tasks_g.size() * sizeof(Task), cudaMemcpyHostToDevice, st);
+    if (!tasks_l.empty()) cudaMemcpyAsync(d_tl, tasks_l.data(), tasks_l.size() * sizeof(Task), cudaMemcpyHostToDevice, st);
     if (!tsrc.empty()) cudaMemcpyAsync(d_src, tsrc.data(), tsrc.size() * sizeof(Sample2), cudaMemcpyHostToDevice, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
@@ -766,31 +796,50 @@ int fdtd_adjoint_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, f
             q += done;
         }
         if (rc) break;
-        // reverse the segment, T reverse steps per launch
+        // reverse the segment, T reverse steps per launch; the CPML and lite
+        // variants run on their own streams beside the interior one
+        AdjLists L;
+        L.t0 = d_t; L.n0 = (int)tasks.size(); L.w0 = warps;
+        L.t1 = d_tg; L.n1 = (int)tasks_g.size(); L.w1 = gwarps;
+        L.t2 = d_tl; L.n2 = (int)tasks_l.size(); L.w2 = lwarps;
+        const bool fork1 = L.n1 > 0, fork2 = L.n2 > 0;
         for (int64_t q = len; q > 0 && rc == FDTD_OK;) {
             const int done = (int)std::min<int64_t>(T, q);
             const long long n_top = a0 + q - 1;
-            const bool both = !tasks.empty() && !tasks_g.empty();
-            if (both) {
+            if (fork1 || fork2) {
                 cudaEventRecord(c->ev_fork, st);
-                cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
+                if (fork1) cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
+                if (fork2) cudaStreamWaitEvent(c->aux2, c->ev_fork, 0);
             }
-            cudaStream_t sa = both ? c->aux : st;
+            cudaStream_t s1 = fork1 ? c->aux : st, s2 = fork2 ? c->aux2 : st;
             switch (done) {
-                case 1: e = launch_adj_T<1>(c, d_adj, d_t, (int)tasks.size(), warps, d_tg, (int)tasks_g.size(), gwarps, d_src, apar, n_top, st, sa); break;
-                case 2: e = launch_adj_T<2>(c, d_adj, d_t, (int)tasks.size(), warps, d_tg, (int)tasks_g.size(), gwarps, d_src, apar, n_top, st, sa); break;
-                case 3: e = launch_adj_T<3>(c, d_adj, d_t, (int)tasks.size(), warps, d_tg, (int)tasks_g.size(), gwarps, d_src, apar, n_top, st, sa); break;
-                default: e = launch_adj_T<4>(c, d_adj, d_t, (int)tasks.size(), warps, d_tg, (int)tasks_g.size(), gwarps, d_src, apar, n_top, st, sa); break;
+                case 1: e = launch_adj_T<1>(d_adj, L, d_src, apar, n_top, st, s1, s2); break;
+                case 2: e = launch_adj_T<2>(d_adj, L, d_src, apar, n_top, st, s1, s2); break;
+                case 3: e = launch_adj_T<3>(d_adj, L, d_src, apar, n_top, st, s1, s2); break;
+                default: e = launch_adj_T<4>(d_adj, L, d_src, apar, n_top, st, s1, s2); break;
             }
-            c->launches += (tasks.empty() ? 0 : 1) + (tasks_g.empty() ? 0 : 1);
-            if (both) {
+            c->launches += (L.n0 > 0) + (L.n1 > 0) + (L.n2 > 0);
+            if (fork1) {
                 cudaEventRecord(c->ev_join, c->aux);
                 cudaStreamWaitEvent(st, c->ev_join, 0);
+            }
+            if (fork2) {
+                cudaEventRecord(c->ev_join2, c->aux2);
+                cudaStreamWaitEvent(st, c->ev_join2, 0);
             }
             if (e != cudaSuccess) rc = cuda_err(e, "adjoint launch");
             apar ^= 1;
             q -= done;
         }
+        if (rc) break;
+        // fold the segment's e and forward recording into dL/deps_r
+        for (int k = 0; k < ns; k++) {
+            const int hw = c->s2[k]->dsg_w * c->s2[k]->dsg_h;
+            k_grad_reduce<<<(hw + 255) / 256, 256, 0, st>>>(rec_of[k], erec_of[k], dc_of[k], grad_of[k], hw, (int)len);
+            c->launches++;
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_err(e, "adjoint: gradient reduction");
     }
     c->d_scenes = saved_scenes;
     if (rc == FDTD_OK) {

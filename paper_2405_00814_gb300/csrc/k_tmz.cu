@@ -146,7 +146,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
                          S->f[F_PHXY][parity ^ 1], S->f[F_PHYX][parity ^ 1]};
 
     // design rectangle (continuous permittivity)
-    const bool dsg = PML && (tk.flags & TASK_DSG) != 0;
+    const bool dsg = (tk.flags & TASK_DSG) != 0;
     const bool has_samp = tk.samp_end > tk.samp_begin;
     // source
     const bool has_src = (tk.flags & TASK_SRC) != 0;
@@ -282,7 +282,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
             const uint32_t m = M[t];
             float4 c0 = coef_s[m & 255u], c1 = coef_s[(m >> 8) & 255u];
             float4 c2 = coef_s[(m >> 16) & 255u], c3 = coef_s[m >> 24];
-            if constexpr (PML) if (dsg) {
+            if (dsg) {
                 const int dj = a - S->dsg_j0;
                 if (dj >= 0 && dj < S->dsg_h) {
                     const float4* drow = S->dsg_coef + (size_t)dj * S->dsg_w;
@@ -801,55 +801,78 @@ __global__ void k_tmz_finite(const TmzDev* __restrict__ scenes, int parity, int*
 // ===========================================================================
 // launchers
 // ===========================================================================
-template <int T, bool PML>
+// variant 0: interior (clean) tasks; 1: CPML tasks; 2: lite tasks (design
+// rectangle, source, probes or ragged edge, no CPML)
+template <int T, int V>
 static cudaError_t launch_fused_T(const Task* tasks, int n_tasks, int warps, const fdtd_ctx* c, cudaStream_t st,
                                   long long n0, int parity) {
-    const size_t smem = tmz_fused_smem(T, warps, PML);
+    const size_t smem = tmz_fused_smem(T, warps, V == 1);
     const int blocks = n_tasks / warps;   // task lists are padded to whole CTAs
-    if (PML) {
-        cudaError_t e = cudaFuncSetAttribute(k_tmz_fused<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e;
+    if (V == 1) {
+        e = cudaFuncSetAttribute(k_tmz_fused<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k_tmz_fused<T, true><<<blocks, warps * 32, smem, st>>>(c->d_scenes, tasks, n_tasks, c->d_samp, parity, n0);
+    } else if (V == 2) {
+        e = cudaFuncSetAttribute(k_tmz_fused<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_tmz_fused<T, false><<<blocks, warps * 32, smem, st>>>(c->d_scenes, tasks, n_tasks, c->d_samp, parity, n0);
     } else {
-        cudaError_t e = cudaFuncSetAttribute(k_tmz_interior<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_tmz_interior<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k_tmz_interior<T><<<blocks, warps * 32, smem, st>>>(c->d_scenes, tasks, n_tasks, parity);
     }
     return cudaGetLastError();
 }
 
-template <bool PML>
+template <int V>
 static cudaError_t launch_fused(const Task* tasks, int n_tasks, int warps, const fdtd_ctx* c, cudaStream_t st, int T,
                                 long long n0, int parity) {
     switch (T) {
-        case 1: return launch_fused_T<1, PML>(tasks, n_tasks, warps, c, st, n0, parity);
-        case 2: return launch_fused_T<2, PML>(tasks, n_tasks, warps, c, st, n0, parity);
-        case 3: return launch_fused_T<3, PML>(tasks, n_tasks, warps, c, st, n0, parity);
-        case 4: return launch_fused_T<4, PML>(tasks, n_tasks, warps, c, st, n0, parity);
+        case 1: return launch_fused_T<1, V>(tasks, n_tasks, warps, c, st, n0, parity);
+        case 2: return launch_fused_T<2, V>(tasks, n_tasks, warps, c, st, n0, parity);
+        case 3: return launch_fused_T<3, V>(tasks, n_tasks, warps, c, st, n0, parity);
+        case 4: return launch_fused_T<4, V>(tasks, n_tasks, warps, c, st, n0, parity);
     }
     return cudaErrorInvalidValue;
 }
 
-// one T-step block: interior tasks on the context's stream, boundary tasks on
-// a forked stream, joined before the next block reads the new buffer
+// one T-step block: interior tasks on the context's stream, CPML and lite tasks
+// on two forked streams, joined before the next block reads the new buffer
 int tmz_fused_launch(fdtd_ctx* c, int T, int warps, long long n0, int parity) {
     cudaError_t e = cudaSuccess;
-    const bool both = c->n_tasks_b > 0 && c->n_tasks > 0;
-    if (both) {
+    const int nb = c->n_tasks_b, nl = c->n_tasks_l, ni = c->n_tasks;
+    cudaStream_t sb = c->stream, sl = c->stream;
+    if ((nb > 0) + (nl > 0) + (ni > 0) > 1) {
         e = cudaEventRecord(c->ev_fork, c->stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
+        if (e == cudaSuccess && nb > 0) {
+            e = cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
+            sb = c->aux;
+        }
+        if (e == cudaSuccess && nl > 0) {
+            e = cudaStreamWaitEvent(c->aux2, c->ev_fork, 0);
+            sl = c->aux2;
+        }
     }
-    if (e == cudaSuccess && c->n_tasks_b > 0) {
-        e = launch_fused<true>(c->d_tasks_b, c->n_tasks_b, c->warps_b, c, both ? c->aux : c->stream, T, n0, parity);
+    if (e == cudaSuccess && nb > 0) {
+        e = launch_fused<1>(c->d_tasks_b, nb, c->warps_b, c, sb, T, n0, parity);
         c->launches++;
     }
-    if (e == cudaSuccess && c->n_tasks > 0) {
-        e = launch_fused<false>(c->d_tasks, c->n_tasks, warps, c, c->stream, T, n0, parity);
+    if (e == cudaSuccess && nl > 0) {
+        e = launch_fused<2>(c->d_tasks_l, nl, c->warps_l, c, sl, T, n0, parity);
         c->launches++;
     }
-    if (both && e == cudaSuccess) {
-        e = cudaEventRecord(c->ev_join, c->aux);
+    if (e == cudaSuccess && ni > 0) {
+        e = launch_fused<0>(c->d_tasks, ni, warps, c, c->stream, T, n0, parity);
+        c->launches++;
+    }
+    if (e == cudaSuccess && sb != c->stream) {
+        e = cudaEventRecord(c->ev_join, sb);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+    }
+    if (e == cudaSuccess && sl != c->stream) {
+        e = cudaEventRecord(c->ev_join2, sl);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_join2, 0);
     }
     if (e != cudaSuccess) {
         c->err = std::string("fused launch: ") + cudaGetErrorString(e);
