@@ -138,6 +138,7 @@ void scene2_free(Scene2* s) {
     dfree(s->d_src);
     dfree(s->d_rec);
     dfree(s->d_dsg);
+    dfree(s->d_band);
     delete s;
 }
 
@@ -179,6 +180,7 @@ int scene2_init(fdtd_ctx* c, const fdtd_grid* g, double dx, double dt, double co
     memset((void*)s->fbuf, 0, sizeof(s->fbuf));
     s->d_mat = nullptr; s->d_coef = nullptr; s->d_prof = nullptr; s->d_src = nullptr; s->d_rec = nullptr;
     s->d_dsg = nullptr;
+    s->d_band = nullptr;
     s->nx = g->nx; s->ny = g->ny; s->npml = npml;
     s->dx = dx; s->dy = dy; s->dt = dt;
     s->pitch = ((PAD_X + g->nx + STRIP) + 31) / 32 * 32;
@@ -268,6 +270,8 @@ fdtd_ctx* ctx_new(void* stream) {
     c->graph = nullptr;
     c->adj = nullptr;
     c->d_tasks_all = nullptr;
+    c->d_dft = nullptr;
+    c->n_dft = 0;
     c->n_tasks_all = 0;
     c->d_ctl = nullptr;
     c->ctl_words = 0;
@@ -335,6 +339,12 @@ int ensure_capacity(fdtd_ctx* c, int64_t t_end) {
 
 // device scene descriptors, fused-kernel task list and sample lists
 int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
+    // a recorded graph holds the buffers about to be replaced
+    if (c->graph_exec) {
+        cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
+        c->graph_exec = nullptr;
+        c->graph_t = c->graph_n = -1;
+    }
     const int ns = (int)c->s2.size();
     std::vector<TmzDev> dev(ns);
     for (int k = 0; k < ns; k++) {
@@ -359,6 +369,7 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
         d.rec_cap = s->rec_cap;
         d.dsg_i0 = s->dsg_i0; d.dsg_j0 = s->dsg_j0; d.dsg_w = s->d_dsg ? s->dsg_w : 0; d.dsg_h = s->dsg_h;
         d.dsg_coef = s->d_dsg;
+        d.dsg_band = s->d_band;
     }
     // tasks: per scene, strips of 120 columns x segments of seg rows.  Tasks
     // with a CPML slab or the design rectangle within reach go to the boundary
@@ -444,7 +455,10 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     dfree(c->d_scenes); dfree(c->d_tasks); dfree(c->d_tasks_b); dfree(c->d_samp); dfree(c->d_samp_scene); dfree(c->d_samp_off);
     dfree(c->d_tasks_all);
     dfree(c->d_tasks_l);
+    dfree(c->d_dft);
     c->d_tasks_l = nullptr;
+    c->d_dft = nullptr;
+    c->n_dft = 0;
     c->d_scenes = nullptr; c->d_tasks = nullptr; c->d_tasks_b = nullptr; c->d_samp = nullptr; c->d_samp_scene = nullptr;
     c->d_samp_off = nullptr; c->d_tasks_all = nullptr;
     int rc;
@@ -470,7 +484,33 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     if (!ssamp.empty())
         CK(cudaMemcpyAsync(c->d_samp_scene, ssamp.data(), ssamp.size() * sizeof(Sample2), cudaMemcpyHostToDevice, c->stream), "upload");
     CK(cudaMemcpyAsync(c->d_samp_off, soff.data(), soff.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream), "upload");
+    // DFT accumulators of every cell monitor, for one launch per T-step block
+    std::vector<DftItem> items;
+    for (const DftMon& m : c->mons) {
+        if (m.plane_k >= 0) continue;
+        const Scene2* s = c->s2[m.scene];
+        for (int q = 0; q < m.n_cells; q++)
+            for (int f = 0; f < m.n_freq; f++) {
+                DftItem it;
+                it.rec = s->d_rec;
+                it.acc = m.d_acc + (size_t)q * m.n_freq + f;
+                double fr = m.freqs[f] * s->dt;
+                fr -= floor(fr);
+                const double v = ldexp(fr, 64);
+                it.inc = v >= 18446744073709551615.0 ? 0ull : (unsigned long long)v;
+                it.dt = (float)s->dt;
+                it.n_rec = (int)s->samples.size();
+                it.slot = m.slot0 + q;
+                it.pad = 0;
+                items.push_back(it);
+            }
+    }
+    if (!items.empty()) {
+        if ((rc = dalloc(c, &c->d_dft, items.size() * sizeof(DftItem), "dft items"))) return rc;
+        CK(cudaMemcpyAsync(c->d_dft, items.data(), items.size() * sizeof(DftItem), cudaMemcpyHostToDevice, c->stream), "upload");
+    }
     CK(cudaStreamSynchronize(c->stream), "upload task list");
+    c->n_dft = (int)items.size();
     c->n_tasks = (int)tasks.size();
     c->n_tasks_b = (int)tasks_b.size();
     c->n_tasks_all = (int)all.size();
@@ -578,6 +618,7 @@ void fdtd_destroy(fdtd_ctx* c) {
     dfree(c->d_scenes); dfree(c->d_tasks); dfree(c->d_tasks_b); dfree(c->d_samp); dfree(c->d_samp_scene);
     dfree(c->d_samp_off);
     dfree(c->d_tasks_all);
+    dfree(c->d_dft);
     dfree(c->d_ctl);
     if (c->h_err) cudaFreeHost(c->h_err);
     if (c->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
@@ -686,11 +727,18 @@ int fdtd_set_design(fdtd_ctx* c, int i0, int j0, int w, int h, const double* eps
     }
     if (!s->d_dsg || s->dsg_w != w || s->dsg_h != h) {
         dfree(s->d_dsg);
+        dfree(s->d_band);
         s->d_dsg = nullptr;
+        s->d_band = nullptr;
         int rc = dalloc(c, &s->d_dsg, n * sizeof(float4), "design coefficients");
+        if (rc) return rc;
+        rc = dalloc(c, &s->d_band, (size_t)3 * h * s->pitch * sizeof(float), "design band");
         if (rc) return rc;
     }
     CK(cudaMemcpyAsync(s->d_dsg, co.data(), n * sizeof(float4), cudaMemcpyHostToDevice, c->stream), "upload design");
+    s->dsg_i0 = i0; s->dsg_j0 = j0; s->dsg_w = w; s->dsg_h = h;
+    int brc = tmz_design_band(c, s);
+    if (brc) return brc;
     CK(cudaStreamSynchronize(c->stream), "upload design");
     s->dsg_eps.assign(eps_r, eps_r + n);
     if (sigma) s->dsg_sig.assign(sigma, sigma + n);
@@ -801,9 +849,8 @@ static int step_launches(fdtd_ctx* c, int64_t n_steps) {
             c->parity ^= 1;
         }
         if (rc) return rc;
-        for (const DftMon& m : c->mons) {
-            if (m.plane_k >= 0) continue;
-            rc = dft_cells_launch(c, m, c->t, done);
+        if (c->n_dft > 0) {
+            rc = dft_items_launch(c, c->t, done);
             if (rc) return rc;
         }
         c->t += done;

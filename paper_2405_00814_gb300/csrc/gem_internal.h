@@ -57,6 +57,7 @@ struct TmzDev {
     // continuous-permittivity design rectangle (overrides the table inside it)
     int dsg_i0, dsg_j0, dsg_w, dsg_h;   // dsg_w == 0: none
     const float4* dsg_coef;             // [dsg_h][dsg_w] (Ca, Cb/dx, Cb/dy, Cb)
+    const float* dsg_band;              // [3][dsg_h][pitch]: Ca, Cb/dx, Cb/dy of every cell of the design rows
     // reverse mode: forward recompute records E^n and curl H^{n+1/2} over the
     // design rectangle; the adjoint kernels read them, inject dL/dE^{n+1} at the
     // monitor cells and keep dL/dE^{n+1} over the design rectangle, which a
@@ -97,6 +98,17 @@ struct DftMon {
     int plane_k, comp_mask;
 };
 
+// one (cell, frequency) accumulator of a 2D cell monitor, for the single DFT
+// launch per T-step block.  The phase of step n is (n + 1) * inc modulo 2^64,
+// a 64-bit fixed-point fraction of a cycle (inc = frac(f dt) * 2^64).
+struct DftItem {
+    const float* rec;
+    float4* acc;
+    unsigned long long inc;
+    float dt;
+    int n_rec, slot, pad;
+};
+
 struct Probe {
     int scene, slot;
     int64_t t_start;
@@ -124,6 +136,7 @@ struct Scene2 {
     // design rectangle
     int dsg_i0, dsg_j0, dsg_w, dsg_h;
     float4* d_dsg;
+    float* d_band;                       // see TmzDev::dsg_band
     std::vector<double> dsg_eps, dsg_sig;
 };
 
@@ -166,6 +179,8 @@ struct fdtd_ctx {
     void* adj;
     // persistent kernel: all tasks in one list (general tasks first), control words
     gem::Task* d_tasks_all;
+    gem::DftItem* d_dft;           // every 2D cell-monitor accumulator
+    int n_dft;
     int n_tasks_all;
     unsigned* d_ctl;
     int ctl_words;
@@ -188,7 +203,9 @@ int tmz_naive_step(fdtd_ctx* c, long long n);
 int dft_cells_launch(fdtd_ctx* c, const DftMon& m, long long n0, int nsteps);
 int tmz_finite_check(fdtd_ctx* c, int* bad);
 int tmz_persistent_launch(fdtd_ctx* c, int T, long long n0, int n_blocks, int parity);
-size_t tmz_fused_smem(int T, int warps, bool pml);
+size_t tmz_fused_smem(int T, int warps, int V);
+int tmz_design_band(fdtd_ctx* c, Scene2* s);
+int dft_items_launch(fdtd_ctx* c, long long n0, int nsteps);   // V: 0 interior, 1 CPML, 2 lite
 }  // namespace gem
 
 namespace gem {

@@ -41,19 +41,23 @@
 namespace gem {
 
 int step_prepare(fdtd_ctx* c, int64_t n_steps);
-size_t tmz_fused_smem(int T, int warps, bool pml);
 
 namespace {
 
 constexpr int A_PF_G = 3;
 constexpr int A_Q_I = 8;
 
-__host__ __device__ constexpr int a_nslot(bool gen) { return gen ? 7 : 3; }
-__host__ __device__ constexpr int a_stage_f4(bool gen) { return a_nslot(gen) * 32 + 8; }
-__host__ __device__ constexpr int a_stages(int T, bool gen) { return gen ? T + A_PF_G : A_Q_I; }
-__host__ __device__ constexpr int a_pf(int T, bool gen) { return gen ? A_PF_G : A_Q_I - T; }
+// Stage slots per lane and row: interior e hx hy; lite adds the design band's
+// Ca, Cb/dx, Cb/dy; CPML adds the four psi and, after the material words, the
+// row's y-profile scalars.  pv = CPML variant.
+__host__ __device__ constexpr int a_nslot(bool gen, bool pv) { return pv ? 7 : (gen ? 6 : 3); }
+__host__ __device__ constexpr int a_stage_f4(bool gen, bool pv) { return a_nslot(gen, pv) * 32 + 8 + (pv ? 1 : 0); }
+__host__ __device__ constexpr int a_stages(int T, bool pv) { return pv ? T + A_PF_G : A_Q_I; }
+__host__ __device__ constexpr int a_pf(int T, bool pv) { return pv ? A_PF_G : A_Q_I - T; }
 
-size_t adj_smem(int T, int warps, bool gen) { return (size_t)warps * a_stages(T, gen) * a_stage_f4(gen) * sizeof(float4); }
+size_t adj_smem(int T, int warps, bool gen, bool pv) {
+    return (size_t)warps * a_stages(T, pv) * a_stage_f4(gen, pv) * sizeof(float4);
+}
 
 __device__ __forceinline__ void acp16(void* smem, const void* gmem) {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -82,10 +86,11 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
                                                           const Sample2* __restrict__ srcs, int parity,
                                                           long long n_top) {
     constexpr bool PV = GEN && PMLV;
+    constexpr bool SD = GEN && !PMLV;   // design band staged
     constexpr int Q = a_stages(T, PV);
     constexpr int PF = a_pf(T, PV);
-    constexpr int SF4 = a_stage_f4(PV);
-    constexpr int NS = a_nslot(PV);
+    constexpr int SF4 = a_stage_f4(GEN, PV);
+    constexpr int NS = a_nslot(GEN, PV);
     extern __shared__ float4 smem_f4[];
     __shared__ float4 coef_s[256];
 
@@ -119,6 +124,19 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
     const bool pml = PV && (tk.flags & TASK_PML) != 0;
     const bool dsg = GEN && (tk.flags & TASK_DSG) != 0;
     const bool has_src = GEN && tk.samp_end > tk.samp_begin;
+    const int dsg_i0 = S->dsg_i0, dsg_j0 = S->dsg_j0, dsg_w = S->dsg_w, dsg_h = S->dsg_h;
+    const float4* __restrict__ dsg_coef = S->dsg_coef;
+    const float* __restrict__ band = S->dsg_band;
+    const size_t band_plane = (size_t)dsg_h * pitch;
+    const long long rec_n0 = S->dsg_rec_n0, rec_len = S->dsg_rec_len;
+    float* const adj_rec = S->adj_rec;
+    const float* __restrict__ adj_src = S->adj_src;
+    const int n_adj = S->n_adj;
+    // the task's adjoint source cells: the first 32 ride in lane registers
+    const int n_samp = tk.samp_end - tk.samp_begin;
+    Sample2 my_samp;
+    my_samp.i = -1; my_samp.j = -1; my_samp.comp = 0; my_samp.slot = 0;
+    if (GEN && lane < n_samp) my_samp = srcs[tk.samp_begin + lane];
     const int npml = S->has_pml;
     const float* pr = S->prof;
     const int prow = S->rows;
@@ -148,8 +166,19 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
         acp16(st + 1 * 32 + lane, hx_in + g);
         acp16(st + 2 * 32 + lane, hy_in + g);
         acp4(reinterpret_cast<uint32_t*>(st + NS * 32) + lane, mat + g);
+        if constexpr (SD) {
+            if (dsg && row >= dsg_j0 && row < dsg_j0 + dsg_h) {
+                const float* b = band + (size_t)(row - dsg_j0) * pitch + cs;
+                acp16(st + 3 * 32 + lane, b);
+                acp16(st + 4 * 32 + lane, b + band_plane);
+                acp16(st + 5 * 32 + lane, b + 2 * band_plane);
+            }
+        }
         if constexpr (PV) {
             if (pml) {
+                // the row's bEy, cEy, bHy, cHy
+                if (yslab(row) && lane < 4)
+                    acp4(reinterpret_cast<float*>(st + NS * 32 + 8) + lane, pr + 4 * pitch + lane * prow + row + PAD_Y);
                 if (lane_px) {
                     acp16(st + 3 * 32 + lane, psi_in[0] + g);
                     acp16(st + 6 * 32 + lane, psi_in[3] + g);
@@ -169,22 +198,33 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
         c[3] = coef_s[m >> 24];
         if constexpr (GEN) {
             if (dsg) {
-                const int dj = row - S->dsg_j0;
-                if (dj >= 0 && dj < S->dsg_h) {
-                    const float4* drow = S->dsg_coef + (size_t)dj * S->dsg_w;
-                    const int di = cx - S->dsg_i0;
-                    for (int q = 0; q < 4; q++)
-                        if (di + q >= 0 && di + q < S->dsg_w) c[q] = drow[di + q];
+                const int dj = row - dsg_j0;
+                if (dj >= 0 && dj < dsg_h) {
+                    if constexpr (SD) {
+                        const float4* st = stage_of(row);
+                        const float4 ca = st[3 * 32 + lane], cbx = st[4 * 32 + lane], cby = st[5 * 32 + lane];
+                        c[0] = make_float4(ca.x, cbx.x, cby.x, 0.f);
+                        c[1] = make_float4(ca.y, cbx.y, cby.y, 0.f);
+                        c[2] = make_float4(ca.z, cbx.z, cby.z, 0.f);
+                        c[3] = make_float4(ca.w, cbx.w, cby.w, 0.f);
+                    } else {
+                        const float4* drow = dsg_coef + (size_t)dj * dsg_w;
+                        const int di = cx - dsg_i0;
+                        for (int q = 0; q < 4; q++)
+                            if (di + q >= 0 && di + q < dsg_w) c[q] = drow[di + q];
+                    }
                 }
             }
         }
     };
+    // y-profile scalar k (bEy, cEy, bHy, cHy) of a CPML row, from its stage
+    auto yp = [&](const float4* sta, int k) { return reinterpret_cast<const float*>(sta + NS * 32 + 8)[k]; };
     // gy of a row whose adjoint state is final for the level just finished
     auto gy_of = [&](const float4& e, const float4* c, int row, const float4* sta) {
         float4 g = make_float4(-c[0].z * e.x, -c[1].z * e.y, -c[2].z * e.z, -c[3].z * e.w);
         if constexpr (PV) {
             if (pml && yslab(row)) {
-                const float ce = pr[4 * pitch + prow + row + PAD_Y];
+                const float ce = yp(sta, 1);
                 const float4 p = sta[4 * 32 + lane];
                 g.x = g.x * (1.f + ce) + ce * p.x;
                 g.y = g.y * (1.f + ce) + ce * p.y;
@@ -200,12 +240,20 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
     // the gy the row below takes from it
     auto inject = [&](float4& e, int row, long long m) {
         if constexpr (GEN) {
-            if (has_src && m >= 0)
-                for (int q = tk.samp_begin; q < tk.samp_end; q++) {
+            if (has_src && m >= 0) {
+                const int nq = n_samp < 32 ? n_samp : 32;
+                for (int q = 0; q < nq; q++) {
+                    if (__shfl_sync(0xffffffffu, my_samp.j, q) != row) continue;   // warp-uniform
+                    const int d = __shfl_sync(0xffffffffu, my_samp.i, q) - cx;
+                    const int slot = __shfl_sync(0xffffffffu, my_samp.slot, q);
+                    if (d >= 0 && d < 4) cref(e, d) += adj_src[m * n_adj + slot];
+                }
+                for (int q = tk.samp_begin + 32; q < tk.samp_end; q++) {
                     const Sample2 sp = srcs[q];
                     const int d = sp.i - cx;
-                    if (sp.j == row && d >= 0 && d < 4) cref(e, d) += S->adj_src[m * S->n_adj + sp.slot];
+                    if (sp.j == row && d >= 0 && d < 4) cref(e, d) += adj_src[m * n_adj + sp.slot];
                 }
+            }
         }
     };
 
@@ -269,15 +317,15 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
                 if (dsg && a >= tk.ya && a < tk.yb && out_lane) {
                     // keep dL/dE^{n+1} of the owned design cells; a reduction after
                     // the segment forms dL/deps_r from it and the recorded E^n, curl H
-                    const int dj = a - S->dsg_j0;
-                    const long long nr = n - S->dsg_rec_n0;
-                    if (dj >= 0 && dj < S->dsg_h && nr >= 0 && nr < S->dsg_rec_len) {
-                        const size_t hw = (size_t)S->dsg_w * S->dsg_h;
-                        float* er = S->adj_rec + (size_t)nr * hw + (size_t)dj * S->dsg_w;
-                        const int di = cx - S->dsg_i0;
+                    const int dj = a - dsg_j0;
+                    const long long nr = n - rec_n0;
+                    if (dj >= 0 && dj < dsg_h && nr >= 0 && nr < rec_len) {
+                        const size_t hw = (size_t)dsg_w * dsg_h;
+                        float* er = adj_rec + (size_t)nr * hw + (size_t)dj * dsg_w;
+                        const int di = cx - dsg_i0;
                         for (int q = 0; q < 4; q++) {
                             const int d = di + q;
-                            if (d >= 0 && d < S->dsg_w) er[d] = cget(E[t], q);
+                            if (d >= 0 && d < dsg_w) er[d] = cget(E[t], q);
                         }
                     }
                 }
@@ -297,7 +345,7 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
                         gx.w = gx.w * (1.f + cex[3]) + cex[3] * p.w;
                     }
                     if (yslab(a)) {
-                        const float ce = pr[4 * pitch + prow + a + PAD_Y];
+                        const float ce = yp(sta, 1);
                         const float4 p = sta[4 * 32 + lane];
                         gya.x = gya.x * (1.f + ce) + ce * p.x;
                         gya.y = gya.y * (1.f + ce) + ce * p.y;
@@ -327,7 +375,7 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
                         sta[3 * 32 + lane] = p;
                     }
                     if (yslab(a)) {
-                        const float be = pr[4 * pitch + a + PAD_Y];
+                        const float be = yp(sta, 0);
                         float4 p = sta[4 * 32 + lane];
                         p.x = be * (p.x - uy.x);
                         p.y = be * (p.y - uy.y);
@@ -355,7 +403,7 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
                         fx.w = fx.w * (1.f + chx[3]) + chx[3] * p.w;
                     }
                     if (yslab(a)) {
-                        const float ch = pr[4 * pitch + 3 * prow + a + PAD_Y];
+                        const float ch = yp(sta, 3);
                         const float4 p = sta[5 * 32 + lane];
                         fya.x = fya.x * (1.f + ch) + ch * p.x;
                         fya.y = fya.y * (1.f + ch) + ch * p.y;
@@ -376,7 +424,7 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
             if constexpr (PV) {
                 if (pml) {
                     if (yslab(a)) {
-                        const float bh = pr[4 * pitch + 2 * prow + a + PAD_Y];
+                        const float bh = yp(sta, 2);
                         float4 p = sta[5 * 32 + lane];
                         p.x = bh * (p.x - dby * X[t].x);
                         p.y = bh * (p.y - dby * X[t].y);
@@ -445,7 +493,7 @@ template <int T, bool GEN, bool PMLV>
 cudaError_t launch_adj_v(const TmzDev* dev, const Task* tasks, int n, int warps, const Sample2* srcs, int parity,
                          long long n_top, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    const size_t sm = adj_smem(T, warps, GEN && PMLV);
+    const size_t sm = adj_smem(T, warps, GEN, GEN && PMLV);
     cudaError_t e = cudaFuncSetAttribute(k_adj<T, GEN, PMLV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k_adj<T, GEN, PMLV><<<n / warps, warps * 32, sm, st>>>(dev, tasks, n, srcs, parity, n_top);

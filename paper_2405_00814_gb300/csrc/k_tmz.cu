@@ -26,22 +26,30 @@
 
 namespace gem {
 
-// Two variants share one body.  Boundary tasks (a CPML slab or a design
-// rectangle in reach) stage 7 float4 slots per lane per row -- Ez Hx Hy and
-// psi_Ezx psi_Ezy psi_Hxy psi_Hyx -- and keep PF_B rows in flight.  Interior
-// tasks stage only Ez Hx Hy and keep PF_I rows in flight, with a register cap
-// that lets four warps share each SM sub-partition.
-// Interior warps always hold Q_I = 8 stages (a power of two, so the stage of a
-// row is a mask) with 8 - T rows in flight.
+// Three task kinds.  CPML tasks (general_task<T, true>) stage 7 float4 slots per
+// lane per row -- Ez Hx Hy and psi_Ezx psi_Ezy psi_Hxy psi_Hyx -- plus the row's
+// four y-profile scalars, and keep PF_B rows in flight.  Lite tasks (design
+// rectangle, source, probes, ragged edge; general_task<T, false>) stage Ez Hx Hy
+// and, inside the design band, the row's Ca, Cb/dx, Cb/dy, so that no level of
+// the wavefront waits on a global load.  Interior tasks (k_tmz_interior) stage
+// only Ez Hx Hy, with a register cap that lets four warps share each SM
+// sub-partition.  Lite and interior warps hold Q_I = 8 stages (a power of two,
+// so the stage of a row is a mask) with 8 - T rows in flight.
 constexpr int PF_B = 3;
 constexpr int Q_I = 8;
 __host__ __device__ constexpr int nslot_of(bool pml) { return pml ? 7 : 3; }
 __host__ __device__ constexpr int stage_f4(bool pml) { return nslot_of(pml) * 32 + 8; }   // + 32 uint32 material words
 __host__ __device__ constexpr int stages_for(int T, bool pml) { return pml ? T + PF_B : Q_I; }
 __host__ __device__ constexpr int pf_of(int T, bool pml) { return pml ? PF_B : Q_I - T; }
+// general tasks: CPML kind adds one float4 of y-profile scalars after the
+// material words; lite kind has three design-coefficient slots after the fields
+__host__ __device__ constexpr int gen_nslot(bool pml) { return pml ? 7 : 6; }
+__host__ __device__ constexpr int gen_stage_f4(bool pml) { return gen_nslot(pml) * 32 + 8 + (pml ? 1 : 0); }
 
-size_t tmz_fused_smem(int T, int warps, bool pml) {
-    return (size_t)warps * stages_for(T, pml) * stage_f4(pml) * sizeof(float4);
+// V: 0 interior, 1 CPML, 2 lite
+size_t tmz_fused_smem(int T, int warps, int V) {
+    if (V == 0) return (size_t)warps * stages_for(T, false) * stage_f4(false) * sizeof(float4);
+    return (size_t)warps * stages_for(T, V == 1) * gen_stage_f4(V == 1) * sizeof(float4);
 }
 
 __device__ __forceinline__ size_t sidx(int pitch, int i, int j) {
@@ -106,9 +114,10 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
                                              const Sample2* __restrict__ samps, int parity, long long n0,
                                              const float4* coef_s, float4* stage0, int lane) {
     constexpr int PF = pf_of(T, PML);
-    constexpr int NSLOT = nslot_of(PML);
-    constexpr int STAGE_F4 = stage_f4(PML);
+    constexpr int NSLOT = gen_nslot(PML);
+    constexpr int STAGE_F4 = gen_stage_f4(PML);
     constexpr int Q = stages_for(T, PML);
+    constexpr bool SD = !PML;   // design coefficients come staged (lite kind)
     const int pitch = S->pitch, nx = S->nx, ny = S->ny;
     const float* __restrict__ ez_in = S->f[F_EZ][parity];
     const float* __restrict__ hx_in = S->f[F_HX][parity];
@@ -145,12 +154,27 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
     float* psi_out[4] = {S->f[F_PEZX][parity ^ 1], S->f[F_PEZY][parity ^ 1],
                          S->f[F_PHXY][parity ^ 1], S->f[F_PHYX][parity ^ 1]};
 
-    // design rectangle (continuous permittivity)
+    // design rectangle (continuous permittivity); scene scalars live in registers
     const bool dsg = (tk.flags & TASK_DSG) != 0;
-    const bool has_samp = tk.samp_end > tk.samp_begin;
-    // source
+    const int dsg_i0 = S->dsg_i0, dsg_j0 = S->dsg_j0, dsg_w = S->dsg_w, dsg_h = S->dsg_h;
+    const float4* __restrict__ dsg_coef = S->dsg_coef;
+    const float* __restrict__ band = S->dsg_band;
+    const size_t band_plane = (size_t)dsg_h * pitch;
+    float* const dsg_rec = S->dsg_rec;
+    const long long rec_n0 = S->dsg_rec_n0, rec_len = S->dsg_rec_len;
+    const float rdx = S->rdx, rdy = S->rdy;
+    // probes and monitor cells of this task: the first 32 ride in lane registers
+    const int n_samp = tk.samp_end - tk.samp_begin;
+    const bool has_samp = n_samp > 0;
+    Sample2 my_samp;
+    my_samp.i = -1; my_samp.j = -1; my_samp.comp = 0; my_samp.slot = 0;
+    if (lane < n_samp) my_samp = samps[tk.samp_begin + lane];
+    // source: this launch's T waveform values ride in lanes 0..T-1
     const bool has_src = (tk.flags & TASK_SRC) != 0;
     const int src_j = S->src_j, src_d = S->src_i - cx;
+    const long long src_len = S->src_len;
+    float wv = 0.f;
+    if (has_src && lane < T && n0 + lane < src_len) wv = S->src_wave[n0 + lane];
 
 
     auto issue = [&](int row) {
@@ -161,8 +185,19 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
         cp_async16(st + 1 * 32 + lane, hx_in + g, true);
         cp_async16(st + 2 * 32 + lane, hy_in + g, true);
         cp_async4(reinterpret_cast<uint32_t*>(st + NSLOT * 32) + lane, mat + g);
+        if constexpr (SD) {
+            if (dsg && row >= dsg_j0 && row < dsg_j0 + dsg_h) {
+                const float* b = band + (size_t)(row - dsg_j0) * pitch + cs;
+                cp_async16(st + 3 * 32 + lane, b, true);
+                cp_async16(st + 4 * 32 + lane, b + band_plane, true);
+                cp_async16(st + 5 * 32 + lane, b + 2 * band_plane, true);
+            }
+        }
         if constexpr (PML) if (pml) {
             const bool yrow = (row < npml) || (row >= ny - npml);
+            // the row's bEy, cEy, bHy, cHy
+            if (yrow && lane < 4)
+                cp_async4(reinterpret_cast<float*>(st + NSLOT * 32 + 8) + lane, pr.p + 4 * pitch + lane * pr.rows + row + PAD_Y);
             if (lane_px) {
                 cp_async16(st + 3 * 32 + lane, psi_in[0] + g, true);
                 cp_async16(st + 6 * 32 + lane, psi_in[3] + g, true);
@@ -192,7 +227,6 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
         cp_commit();
     }
 
-    const float* wave = S->src_wave;
     float* rec = S->rec;
     const int n_rec = S->n_rec;
 
@@ -220,16 +254,16 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
         for (int t = 1; t <= T; t++) {
             const int a = r - t;
             if (a < s_row) continue;   // warp-uniform
-            float4* sta = PML ? stage0 + ((a - s_row) % Q) * STAGE_F4 : stage0;
+            float4* sta = stage0 + ((a - s_row) % Q) * STAGE_F4;
+            const float* yprof = reinterpret_cast<const float*>(sta + NSLOT * 32 + 8);
             // ---- layer 1: H at row a from Ez at level t-1 (rows a, a+1) ----
             const float4 e = E[t], eu = E[t - 1];
             const float er = __shfl_down_sync(0xffffffffu, e.x, 1);
             float4 dey = make_float4(eu.x - e.x, eu.y - e.y, eu.z - e.z, eu.w - e.w);
             float4 dex = make_float4(e.y - e.x, e.z - e.y, e.w - e.z, er - e.w);
             if constexpr (PML) if (pml) {
-                const int rs = a + PAD_Y;
                 if ((a < npml) || (a >= ny - npml)) {
-                    const float b = pr.bHy(rs), c = pr.cHy(rs);
+                    const float b = yprof[2], c = yprof[3];
                     float4 p = sta[5 * 32 + lane];
                     p.x = b * p.x + c * dey.x;
                     p.y = b * p.y + c * dey.y;
@@ -258,9 +292,8 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
             float4 dhx = make_float4(X[t].x - X[t + 1].x, X[t].y - X[t + 1].y, X[t].z - X[t + 1].z,
                                      X[t].w - X[t + 1].w);
             if constexpr (PML) if (pml) {
-                const int rs = a + PAD_Y;
                 if ((a < npml) || (a >= ny - npml)) {
-                    const float b = pr.bEy(rs), c = pr.cEy(rs);
+                    const float b = yprof[0], c = yprof[1];
                     float4 p = sta[4 * 32 + lane];
                     p.x = b * p.x + c * dhx.x;
                     p.y = b * p.y + c * dhx.y;
@@ -283,26 +316,35 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
             float4 c0 = coef_s[m & 255u], c1 = coef_s[(m >> 8) & 255u];
             float4 c2 = coef_s[(m >> 16) & 255u], c3 = coef_s[m >> 24];
             if (dsg) {
-                const int dj = a - S->dsg_j0;
-                if (dj >= 0 && dj < S->dsg_h) {
-                    const float4* drow = S->dsg_coef + (size_t)dj * S->dsg_w;
-                    const int di = cx - S->dsg_i0;
-                    if (di >= 0 && di < S->dsg_w) c0 = drow[di];
-                    if (di + 1 >= 0 && di + 1 < S->dsg_w) c1 = drow[di + 1];
-                    if (di + 2 >= 0 && di + 2 < S->dsg_w) c2 = drow[di + 2];
-                    if (di + 3 >= 0 && di + 3 < S->dsg_w) c3 = drow[di + 3];
+                const int dj = a - dsg_j0;
+                if (dj >= 0 && dj < dsg_h) {
+                    const int di = cx - dsg_i0;
+                    if constexpr (SD) {
+                        // the band holds the effective coefficients of every column
+                        const float4 ca = sta[3 * 32 + lane], cbx = sta[4 * 32 + lane], cby = sta[5 * 32 + lane];
+                        c0 = make_float4(ca.x, cbx.x, cby.x, 0.f);
+                        c1 = make_float4(ca.y, cbx.y, cby.y, 0.f);
+                        c2 = make_float4(ca.z, cbx.z, cby.z, 0.f);
+                        c3 = make_float4(ca.w, cbx.w, cby.w, 0.f);
+                    } else {
+                        const float4* drow = dsg_coef + (size_t)dj * dsg_w;
+                        if (di >= 0 && di < dsg_w) c0 = drow[di];
+                        if (di + 1 >= 0 && di + 1 < dsg_w) c1 = drow[di + 1];
+                        if (di + 2 >= 0 && di + 2 < dsg_w) c2 = drow[di + 2];
+                        if (di + 3 >= 0 && di + 3 < dsg_w) c3 = drow[di + 3];
+                    }
                     // reverse-mode recompute: E^n and curl H^{n+1/2} of the owned design cells
-                    const long long nr = n0 + (t - 1) - S->dsg_rec_n0;
-                    if (S->dsg_rec && nr >= 0 && nr < S->dsg_rec_len && a >= tk.ya && a < tk.yb && out_lane) {
-                        const size_t hw = (size_t)S->dsg_w * S->dsg_h;
-                        float* re = S->dsg_rec + (size_t)nr * 2 * hw + (size_t)dj * S->dsg_w;
+                    const long long nr = n0 + (t - 1) - rec_n0;
+                    if (dsg_rec && nr >= 0 && nr < rec_len && a >= tk.ya && a < tk.yb && out_lane) {
+                        const size_t hw = (size_t)dsg_w * dsg_h;
+                        float* re = dsg_rec + (size_t)nr * 2 * hw + (size_t)dj * dsg_w;
                         const float ev[4] = {E[t].x, E[t].y, E[t].z, E[t].w};
-                        const float kv[4] = {dhy.x * S->rdx - dhx.x * S->rdy, dhy.y * S->rdx - dhx.y * S->rdy,
-                                             dhy.z * S->rdx - dhx.z * S->rdy, dhy.w * S->rdx - dhx.w * S->rdy};
+                        const float kv[4] = {dhy.x * rdx - dhx.x * rdy, dhy.y * rdx - dhx.y * rdy,
+                                             dhy.z * rdx - dhx.z * rdy, dhy.w * rdx - dhx.w * rdy};
 #pragma unroll
                         for (int q = 0; q < 4; q++) {
                             const int d = di + q;
-                            if (d >= 0 && d < S->dsg_w && cx + q >= tk.x0 && cx + q < tk.x0 + (STRIP - 2 * HALO)) {
+                            if (d >= 0 && d < dsg_w && cx + q >= tk.x0 && cx + q < tk.x0 + (STRIP - 2 * HALO)) {
                                 re[d] = ev[q];
                                 re[hw + d] = kv[q];
                             }
@@ -316,14 +358,25 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
             E[t].w = e_upd(E[t].w, dhy.w, dhx.w, c3);
 
             const long long n = n0 + (t - 1);   // this level makes E^{n+1}
-            if (has_src && a == src_j && src_d >= 0 && src_d < 4 && n < S->src_len)
-                add4(E[t], src_d, wave[n]);
-            if (has_samp) for (int q = tk.samp_begin; q < tk.samp_end; q++) {
-                const Sample2 sp = samps[q];
-                const int d = sp.i - cx;
-                if (sp.j == a && d >= 0 && d < 4) {
-                    const float v = sp.comp == 0 ? comp4(E[t], d) : (sp.comp == 1 ? comp4(X[t], d) : comp4(Y[t], d));
-                    rec[n * n_rec + sp.slot] = v;
+            if (has_src && a == src_j) {
+                const float w = __shfl_sync(0xffffffffu, wv, t - 1);
+                if (src_d >= 0 && src_d < 4 && n < src_len) add4(E[t], src_d, w);
+            }
+            if (has_samp) {
+                const int nq = n_samp < 32 ? n_samp : 32;
+                for (int q = 0; q < nq; q++) {
+                    if (__shfl_sync(0xffffffffu, my_samp.j, q) != a) continue;   // warp-uniform
+                    const int d = __shfl_sync(0xffffffffu, my_samp.i, q) - cx;
+                    const int comp = __shfl_sync(0xffffffffu, my_samp.comp, q);
+                    const int slot = __shfl_sync(0xffffffffu, my_samp.slot, q);
+                    if (d >= 0 && d < 4)
+                        rec[n * n_rec + slot] = comp == 0 ? comp4(E[t], d) : (comp == 1 ? comp4(X[t], d) : comp4(Y[t], d));
+                }
+                for (int q = tk.samp_begin + 32; q < tk.samp_end; q++) {
+                    const Sample2 sp = samps[q];
+                    const int d = sp.i - cx;
+                    if (sp.j == a && d >= 0 && d < 4)
+                        rec[n * n_rec + sp.slot] = sp.comp == 0 ? comp4(E[t], d) : (sp.comp == 1 ? comp4(X[t], d) : comp4(Y[t], d));
                 }
             }
         }
@@ -380,12 +433,13 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
     cp_wait<0>();
 }
 
+// CPML blocks run 2 warps, lite blocks 4 (the lists are padded to that)
 template <int T, bool PML>
-__global__ void __launch_bounds__(256, PML ? 1 : 2) k_tmz_fused(const TmzDev* __restrict__ scenes,
+__global__ void __launch_bounds__(PML ? 256 : 128, PML ? 1 : 3) k_tmz_fused(const TmzDev* __restrict__ scenes,
                                                    const Task* __restrict__ tasks, int n_tasks,
                                                    const Sample2* __restrict__ samps, int parity,
                                                    long long n0) {
-    constexpr int STAGE_F4 = stage_f4(PML);
+    constexpr int STAGE_F4 = gen_stage_f4(PML);
     constexpr int Q = stages_for(T, PML);
     extern __shared__ float4 smem_f4[];
     __shared__ float4 coef_s[256];
@@ -456,7 +510,7 @@ __global__ void __launch_bounds__(256, 1) k_tmz_persistent(const TmzDev* __restr
                                                           const Sample2* __restrict__ samps, int parity0,
                                                           long long n0, int n_blocks, unsigned* ctl,
                                                           long long spin_limit, int skip_cta) {
-    constexpr int STAGE_F4 = stage_f4(true);
+    constexpr int STAGE_F4 = gen_stage_f4(true);
     constexpr int Q = stages_for(T, true);
     extern __shared__ float4 smem_f4[];
     const int lane = threadIdx.x & 31;
@@ -484,7 +538,7 @@ template <int T>
 static cudaError_t launch_persistent_T(const fdtd_ctx* c, cudaStream_t st, int parity, long long n0, int n_blocks,
                                        long long spin_limit, int* grid_out) {
     const int warps = 8;
-    const size_t smem = (size_t)warps * stages_for(T, true) * stage_f4(true) * sizeof(float4);
+    const size_t smem = tmz_fused_smem(T, warps, 1);
     cudaError_t e = cudaFuncSetAttribute(k_tmz_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0, dev = 0, sms = 0;
@@ -806,7 +860,7 @@ __global__ void k_tmz_finite(const TmzDev* __restrict__ scenes, int parity, int*
 template <int T, int V>
 static cudaError_t launch_fused_T(const Task* tasks, int n_tasks, int warps, const fdtd_ctx* c, cudaStream_t st,
                                   long long n0, int parity) {
-    const size_t smem = tmz_fused_smem(T, warps, V == 1);
+    const size_t smem = tmz_fused_smem(T, warps, V);
     const int blocks = n_tasks / warps;   // task lists are padded to whole CTAs
     cudaError_t e;
     if (V == 1) {
@@ -897,6 +951,68 @@ int tmz_naive_step(fdtd_ctx* c, long long n) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         c->err = std::string("naive step: ") + cudaGetErrorString(e);
+        return FDTD_ECUDA;
+    }
+    return FDTD_OK;
+}
+
+// effective (Ca, Cb/dx, Cb/dy) of every stored column of the design rows: the
+// design value inside the rectangle, the material table's elsewhere
+__global__ void k_design_band(const uint8_t* __restrict__ mat, const float4* __restrict__ coef,
+                              const float4* __restrict__ dsg, float* __restrict__ band, int pitch, int i0, int j0,
+                              int w, int h) {
+    const int cs = blockIdx.x * blockDim.x + threadIdx.x;
+    const int dj = blockIdx.y;
+    if (cs >= pitch || dj >= h) return;
+    const int i = cs - PAD_X;
+    float4 co = coef[mat[(size_t)(j0 + dj + PAD_Y) * pitch + cs]];
+    if (i >= i0 && i < i0 + w) co = dsg[(size_t)dj * w + (i - i0)];
+    const size_t plane = (size_t)h * pitch, o = (size_t)dj * pitch + cs;
+    band[o] = co.x;
+    band[plane + o] = co.y;
+    band[2 * plane + o] = co.z;
+}
+
+int tmz_design_band(fdtd_ctx* c, Scene2* s) {
+    const dim3 grd((unsigned)((s->pitch + 127) / 128), (unsigned)s->dsg_h);
+    k_design_band<<<grd, 128, 0, c->stream>>>(s->d_mat, s->d_coef, s->d_dsg, s->d_band, s->pitch, s->dsg_i0,
+                                             s->dsg_j0, s->dsg_w, s->dsg_h);
+    c->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        c->err = std::string("design band: ") + cudaGetErrorString(e);
+        return FDTD_ECUDA;
+    }
+    return FDTD_OK;
+}
+
+// every cell-monitor accumulator of the context, one thread each, over the
+// steps n0 .. n0 + nsteps - 1: F += E^{n+1} exp(-i 2 pi f (n+1) dt) dt.  The
+// phase is exact in 64-bit fixed point; its sine and cosine are taken in FP32.
+__global__ void k_dft_items(const DftItem* __restrict__ items, int n_items, long long n0, int nsteps) {
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n_items) return;
+    const DftItem it = items[id];
+    float4 a = *it.acc;
+    for (int k = 0; k < nsteps; k++) {
+        const long long n = n0 + k;
+        const float e = it.rec[n * it.n_rec + it.slot];
+        const unsigned long long ph = (unsigned long long)(n + 1) * it.inc;
+        const float x = (float)(long long)ph * 5.42101086242752217e-20f;   // 2^-64: cycles in [-1/2, 1/2)
+        float sn, cs;
+        sincospif(2.f * x, &sn, &cs);
+        kahan_add(a.x, a.z, e * (cs * it.dt));
+        kahan_add(a.y, a.w, -e * (sn * it.dt));
+    }
+    *it.acc = a;
+}
+
+int dft_items_launch(fdtd_ctx* c, long long n0, int nsteps) {
+    k_dft_items<<<(c->n_dft + 127) / 128, 128, 0, c->stream>>>(c->d_dft, c->n_dft, n0, nsteps);
+    c->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        c->err = std::string("dft: ") + cudaGetErrorString(e);
         return FDTD_ECUDA;
     }
     return FDTD_OK;

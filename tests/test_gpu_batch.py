@@ -115,3 +115,49 @@ def test_persistent_barrier_timeout_is_reported_and_recoverable():
     for k, s in enumerate(scs):
         assert_fields_close(got[k], oracle_run(s, 64))
     sim.close()
+
+
+def test_graph_rerecords_after_design_change():
+    """A recorded graph refers to the context's device buffers.  Changing a
+    design rebuilds them, so the next graph step must record afresh and give
+    what a plain run with the new design gives (fields and DFT monitors)."""
+    from paper_2405_00814_gb300 import fdtd
+    scs = scenes.adjoint_scenes(side=192, n_designs=2, nsteps=160, npml=8, design=48, n_monitors=3)
+    rng = np.random.default_rng(5)
+    eps2 = [1.0 + 3.0 * rng.random((48, 48)) for _ in scs]
+
+    def make(graph):
+        sim = fdtd.Simulation.batch(scs)
+        mids = []
+        for k, sc in enumerate(scs):
+            sim.select(k)
+            sim.set_scene_source(sc.source)
+            sim.set_design(sc.design[0], sc.design[1], sc.design_eps)
+            mids.append(sim.add_dft_monitor(sc.monitors, sc.freqs))
+        sim.set_option("graph", graph)
+        return sim, mids
+
+    def redesign(sim):
+        for k, sc in enumerate(scs):
+            sim.select(k)
+            sim.set_design(sc.design[0], sc.design[1], eps2[k])
+
+    sim, mids = make(1)
+    sim.step(160)          # records the graph for the first design
+    sim.reset()
+    redesign(sim)
+    sim.step(160)          # same start step and length: must not replay the old graph
+    sim.sync()
+    got, got_dft = _fields(sim, scs), [sim.read_dft(m) for m in mids]
+    sim.close()
+    ref, rmids = make(0)
+    redesign(ref)
+    ref.step(160)
+    ref.sync()
+    want, want_dft = _fields(ref, scs), [ref.read_dft(m) for m in rmids]
+    ref.close()
+    for a, b in zip(got, want):
+        for c in ("ez", "hx", "hy"):
+            assert np.array_equal(a[c], b[c])
+    for a, b in zip(got_dft, want_dft):
+        assert np.array_equal(a, b)
