@@ -251,6 +251,7 @@ def main():
     ap.add_argument("--nsteps", type=int, default=None, help="leapfrog steps per solve (default: the workload's 4000)")
     ap.add_argument("--size", type=int, default=4096, help="grid side (profiling runs use smaller sides)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--graph", action="store_true", help="replay each solve from a recorded CUDA graph")
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint-ratio measurement")
     args = ap.parse_args()
 
@@ -284,6 +285,8 @@ def main():
     sim.set_option("kernel", args.kernel)
     for k, v in tune.items():
         sim.set_option(k, v)
+    if args.graph:
+        sim.set_option("graph", 1)
 
     def solve():
         sim.reset()

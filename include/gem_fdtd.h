@@ -84,6 +84,10 @@ extern "C" {
 #define FDTD_OPT_SPIN_LIMIT 5     /* polls (about 0.25 us each) a persistent-kernel barrier wait makes before it gives up */
 #define FDTD_OPT_DEBUG_SKIP_CTA 6 /* test hook: this CTA of the persistent kernel never arrives at the barrier, so the
                                      others' waits run out (-1 = off); fdtd_sync then returns FDTD_ETIMEOUT */
+#define FDTD_OPT_ADJ_STORE 7 /* reverse mode, read by fdtd_set_checkpointing: 1 (default) = the forward pass keeps
+                                E^{n+1} - E^n over every design rectangle for every step in device memory
+                                (steps x design cells x 4 B) and fdtd_adjoint_grad needs no recompute;
+                                0 = keep field checkpoints only and recompute each segment (less memory) */
 
 typedef struct fdtd_ctx fdtd_ctx;
 
@@ -224,10 +228,12 @@ int fdtd_check_finite(fdtd_ctx* ctx);
  * differentiable (Sec. III-A); these calls compute the discrete adjoint of the
  * two layers of Prop. 2 -- the transposed layers in reverse time order.
  *
- * fdtd_set_checkpointing: from now on, fdtd_step saves the full state of every
- * scene (fields and CPML auxiliaries) whenever the step count is a multiple of
- * `every` (0 turns it off and frees the checkpoints).  Checkpoints live in
- * device memory owned by the context. */
+ * fdtd_set_checkpointing: from now on, fdtd_step works in segments of `every`
+ * steps (0 turns reverse mode off and frees its memory).  With FDTD_OPT_ADJ_STORE
+ * = 1 it records r^n = E^{n+1} - E^n (before the source) over every design
+ * rectangle for every step, one device block per segment; with 0 it saves the
+ * full state of every scene (fields and CPML auxiliaries) at each segment start
+ * instead.  All of it lives in device memory owned by the context. */
 int fdtd_set_checkpointing(fdtd_ctx* ctx, int every);
 
 /* Gradient of a real loss L(F) of the running DFTs with respect to eps_r over
@@ -236,11 +242,14 @@ int fdtd_set_checkpointing(fdtd_ctx* ctx, int every);
  * for every cell DFT monitor in creation order, [n_cells][n_freq] each,
  * concatenated (host).  The adjoint source at a monitor cell for step n is
  * sum_f (dL/dRe F cos(2 pi f (n+1) dt) - dL/dIm F sin(2 pi f (n+1) dt)) dt.
- * Segments between checkpoints are recomputed newest first (recording E^n and
- * curl H^{n+1/2} over the design cells), then reversed.  grad receives
- * dL/deps_r as [scene][h][w] floats (host, or device when on_device != 0).
- * The fields are left in an unspecified state: call fdtd_reset before the next
- * forward run. */
+ * Segments are reversed newest first (in checkpoint mode each is first
+ * recomputed from its checkpoint to record r^n).  With e^{n+1} = dL/dE^{n+1},
+ *   dL/deps_r = sum_n e^{n+1} (dCa/deps_r E^n + dCb/deps_r curlH^{n+1/2})
+ *             = -eps0 / (eps0 eps_r + sigma dt / 2) * sum_n e^{n+1} r^n,
+ * since dCa/deps_r = -sigma dCb/deps_r and Cb curlH = E^{n+1} - Ca E^n.  grad
+ * receives dL/deps_r as [scene][h][w] floats (host, or device when on_device !=
+ * 0).  The fields are left in an unspecified state: call fdtd_reset before the
+ * next forward run. */
 int fdtd_adjoint_grad(fdtd_ctx* ctx, const float* dLdF_re, const float* dLdF_im, float* grad, int on_device);
 
 /* Largest graph fdtd_mp_steps_noalloc accepts (nodes). */

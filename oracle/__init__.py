@@ -69,6 +69,11 @@ def num_threads() -> int:
     return lib().or_num_threads()
 
 
+def set_threads(n: int) -> None:
+    """OpenMP threads of later calls (the loop bodies and results are unchanged)."""
+    lib().or_set_threads(int(n))
+
+
 def _p(a):
     return a.ctypes.data_as(_dp) if a is not None else None
 

@@ -48,6 +48,15 @@ int or_num_threads(void) {
 #endif
 }
 
+/* thread count of later parallel loops (timing only; results do not depend on it) */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ---------------------------------------------------------------------------
  * eq. (7): E^{n+1} = (A_-/A_+) E^n + dt/(A_+ eps) curl H^{n+1/2},
  * A_-/+ = 1 -/+ sigma dt/(2 eps).

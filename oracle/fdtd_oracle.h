@@ -168,6 +168,7 @@ double or3_energy(const or3_problem* p, const double* eps_cell, const or3_state*
                   const double* hx_prev, const double* hy_prev, const double* hz_prev);
 
 int or_num_threads(void);
+void or_set_threads(int n);
 
 #ifdef __cplusplus
 }

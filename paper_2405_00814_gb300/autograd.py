@@ -19,7 +19,9 @@ class DesignBatch:
     Each scene needs a source, DFT monitor cells + frequencies and a design
     rectangle (paper_2405_00814_gb300.scenes.adjoint_scenes builds such scenes)."""
 
-    def __init__(self, scenes, *, ckpt_every=100, stream=None, tblock=4, segment=24, warps=8):
+    def __init__(self, scenes, *, ckpt_every=100, stream=None, tblock=4, segment=24, warps=8, store=True):
+        """store: keep the forward pass's design-region history in device memory
+        (no recompute in the gradient); False keeps field checkpoints only."""
         self.scenes = scenes
         self.nsteps = scenes[0].nsteps
         self.sim = fdtd.Simulation.batch(scenes, stream=stream)
@@ -33,6 +35,7 @@ class DesignBatch:
         self.sim.set_option("tblock", tblock)
         self.sim.set_option("segment", segment)
         self.sim.set_option("warps", warps)
+        self.sim.set_option("adj_store", int(bool(store)))
         self.sim.set_checkpointing(ckpt_every)
         self.design_shape = (len(scenes), scenes[0].design[3], scenes[0].design[2])
 

@@ -9,6 +9,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -284,6 +286,7 @@ fdtd_ctx* ctx_new(void* stream) {
     }
     c->spin_limit = 4000000;   // about one second of 256 ns polls
     c->opt_debug_skip = -1;
+    c->opt_adj_store = 1;
     c->opt_graph = 0;
     c->graph_exec = nullptr;
     c->graph_t = c->graph_n = -1;
@@ -379,6 +382,8 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     std::vector<Task> tasks, tasks_b, tasks_l;
     std::vector<Sample2> tsamp;
     const int warps_b = 2, warps_l = 4;
+    bool any_design = false;
+    for (const Scene2* s : c->s2) any_design = any_design || s->d_dsg != nullptr;
     for (int k = 0; k < ns; k++) {
         Scene2* s = c->s2[k];
         const size_t first = tasks.size(), first_b = tasks_b.size(), first_l = tasks_l.size();
@@ -412,7 +417,9 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
             for (const Sample2& sp : s->samples)
                 if (sp.i >= x0 && sp.i < x0 + wout && sp.j >= ya && sp.j < yb) tsamp.push_back(sp);
             t.samp_end = (int)tsamp.size();
-            if (t.flags & TASK_PML) tasks_b.push_back(t);
+            // the lite kernel pays for its own launch and stream fork only when a
+            // design rectangle gives it work; otherwise its tasks join the CPML list
+            if ((t.flags & TASK_PML) || (general && !any_design)) tasks_b.push_back(t);
             else if (general) tasks_l.push_back(t);
             else tasks.push_back(t);
         };
@@ -461,6 +468,8 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     c->n_dft = 0;
     c->d_scenes = nullptr; c->d_tasks = nullptr; c->d_tasks_b = nullptr; c->d_samp = nullptr; c->d_samp_scene = nullptr;
     c->d_samp_off = nullptr; c->d_tasks_all = nullptr;
+    adj_patch_descriptors(c, dev.data());   // the design history being recorded, if any
+    c->h_scenes = dev;
     int rc;
     if ((rc = dalloc(c, &c->d_scenes, dev.size() * sizeof(TmzDev), "scene descriptors"))) return rc;
     if ((rc = dalloc(c, &c->d_tasks, tasks.size() * sizeof(Task), "tasks"))) return rc;
@@ -533,6 +542,20 @@ int field_slot_2d(int comp) {
 }  // namespace
 
 namespace gem {
+cudaError_t ensure_dyn_smem(const void* kernel, size_t bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> done;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& have = done[std::make_pair(dev, kernel)];
+    if (bytes <= have) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) have = bytes;
+    return e;
+}
+
 // record/waveform capacity and device descriptors for the next n_steps
 int step_prepare(fdtd_ctx* c, int64_t n_steps) {
     if (c->s2.empty()) return fail(c, FDTD_ESTATE, "no scene");
@@ -653,6 +676,10 @@ int fdtd_set_option(fdtd_ctx* c, int option, int64_t v) {
             if (v < -1 || v > (1 << 20)) return fail(c, FDTD_EINVAL, "debug CTA index out of range");
             c->opt_debug_skip = (int)v;
             return FDTD_OK;
+        case FDTD_OPT_ADJ_STORE:
+            if (v < 0 || v > 1) return fail(c, FDTD_EINVAL, "adjoint store option must be 0 or 1");
+            c->opt_adj_store = (int)v;
+            return FDTD_OK;
         case FDTD_OPT_TBLOCK:
             if (v < 1 || v > MAX_TB) return fail(c, FDTD_EINVAL, "tblock %lld outside 1..%d", (long long)v, MAX_TB);
             c->opt_tblock = (int)v;
@@ -683,6 +710,7 @@ int64_t fdtd_get_option(const fdtd_ctx* c, int option) {
         case FDTD_OPT_GRAPH: return c->opt_graph;
         case FDTD_OPT_SPIN_LIMIT: return c->spin_limit;
         case FDTD_OPT_DEBUG_SKIP_CTA: return c->opt_debug_skip;
+        case FDTD_OPT_ADJ_STORE: return c->opt_adj_store;
     }
     return -1;
 }

@@ -58,18 +58,16 @@ struct TmzDev {
     int dsg_i0, dsg_j0, dsg_w, dsg_h;   // dsg_w == 0: none
     const float4* dsg_coef;             // [dsg_h][dsg_w] (Ca, Cb/dx, Cb/dy, Cb)
     const float* dsg_band;              // [3][dsg_h][pitch]: Ca, Cb/dx, Cb/dy of every cell of the design rows
-    // reverse mode: forward recompute records E^n and curl H^{n+1/2} over the
-    // design rectangle; the adjoint kernels read them, inject dL/dE^{n+1} at the
+    // reverse mode: the forward pass (or a recompute) records r^n = E^{n+1} - E^n
+    // over the design rectangle; the adjoint kernels inject dL/dE^{n+1} at the
     // monitor cells and keep dL/dE^{n+1} over the design rectangle, which a
     // reduction after each segment turns into dL/deps_r
-    float* dsg_rec;                     // [steps][2][dsg_h * dsg_w], step n at n - dsg_rec_n0
+    float* dsg_rec;                     // [steps][dsg_h * dsg_w], step n at n - dsg_rec_n0
     long long dsg_rec_n0, dsg_rec_len;
-    const float2* dsg_dcoef;            // [dsg_h][dsg_w] (dCa/deps_r, dCb/deps_r)
     float* grad;                        // [dsg_h][dsg_w]
     float* adj_rec;                     // [steps][dsg_h * dsg_w]: dL/dE^{n+1}, step n at n - dsg_rec_n0
     const float* adj_src;               // [steps][n_adj]: dL/dE^{n+1} at adjoint source cells
     int n_adj;
-    float rdx, rdy;                     // 1/dx, 1/dy
 };
 
 // one warp's work in the fused kernel: columns [x0, x0 + STRIP - 2 HALO) and
@@ -180,6 +178,7 @@ struct fdtd_ctx {
     // persistent kernel: all tasks in one list (general tasks first), control words
     gem::Task* d_tasks_all;
     gem::DftItem* d_dft;           // every 2D cell-monitor accumulator
+    std::vector<gem::TmzDev> h_scenes;   // host copy of d_scenes
     int n_dft;
     int n_tasks_all;
     unsigned* d_ctl;
@@ -187,6 +186,7 @@ struct fdtd_ctx {
     int* h_err;                  // pinned: error flag of the last persistent launch
     long long spin_limit;        // barrier polls before a CTA gives up
     int opt_debug_skip;          // CTA that skips its barrier arrivals (-1 none)
+    int opt_adj_store;           // FDTD_OPT_ADJ_STORE
     // CUDA graph of a step sequence
     int opt_graph;
     void* graph_exec;
@@ -205,7 +205,11 @@ int tmz_finite_check(fdtd_ctx* c, int* bad);
 int tmz_persistent_launch(fdtd_ctx* c, int T, long long n0, int n_blocks, int parity);
 size_t tmz_fused_smem(int T, int warps, int V);
 int tmz_design_band(fdtd_ctx* c, Scene2* s);
-int dft_items_launch(fdtd_ctx* c, long long n0, int nsteps);   // V: 0 interior, 1 CPML, 2 lite
+// raise a kernel's dynamic shared-memory limit to `bytes` on the current device,
+// once (the attribute call is a driver round trip; later launches reuse it)
+cudaError_t ensure_dyn_smem(const void* kernel, size_t bytes);
+int dft_items_launch(fdtd_ctx* c, long long n0, int nsteps);
+void adj_patch_descriptors(fdtd_ctx* c, TmzDev* dev);   // V: 0 interior, 1 CPML, 2 lite
 }  // namespace gem
 
 namespace gem {

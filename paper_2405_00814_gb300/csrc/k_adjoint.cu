@@ -494,7 +494,7 @@ cudaError_t launch_adj_v(const TmzDev* dev, const Task* tasks, int n, int warps,
                          long long n_top, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const size_t sm = adj_smem(T, warps, GEN, GEN && PMLV);
-    cudaError_t e = cudaFuncSetAttribute(k_adj<T, GEN, PMLV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = ensure_dyn_smem((const void*)k_adj<T, GEN, PMLV>, sm);
     if (e != cudaSuccess) return e;
     k_adj<T, GEN, PMLV><<<n / warps, warps * 32, sm, st>>>(dev, tasks, n, srcs, parity, n_top);
     return cudaGetLastError();
@@ -514,16 +514,14 @@ cudaError_t launch_adj_T(const TmzDev* dev, const AdjLists& L, const Sample2* sr
     return e;
 }
 
-// dL/deps_r += sum over the segment's steps of e (dCa E^n + dCb curlH^{n+1/2})
+// dL/deps_r += fac * sum over the segment's steps of e^{n+1} r^n
 __global__ void k_grad_reduce(const float* __restrict__ rec, const float* __restrict__ erec,
-                              const float2* __restrict__ dc, float* __restrict__ grad, int hw, int len) {
+                              const float* __restrict__ fac, float* __restrict__ grad, int hw, int len) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= hw) return;
-    const float2 k2 = dc[c];
     float g = 0.f;
-    for (int s = 0; s < len; s++)
-        g += erec[(size_t)s * hw + c] * (k2.x * rec[(size_t)s * 2 * hw + c] + k2.y * rec[(size_t)s * 2 * hw + hw + c]);
-    grad[c] += g;
+    for (int s = 0; s < len; s++) g += erec[(size_t)s * hw + c] * rec[(size_t)s * hw + c];
+    grad[c] += fac[c] * g;
 }
 
 }  // namespace
@@ -532,17 +530,62 @@ __global__ void k_grad_reduce(const float* __restrict__ rec, const float* __rest
 // host: checkpoints and the reverse sweep
 // ---------------------------------------------------------------------------
 struct AdjState {
-    std::vector<float*> ckpt;      // [slot * n_scenes + scene] -> F_COUNT2 padded arrays
     int every;
+    int store;                     // 1: design history (no recompute); 0: field checkpoints
+    std::vector<float*> ckpt;      // [slot * n_scenes + scene] -> F_COUNT2 padded arrays
+    std::vector<float*> hist;      // [slot * n_scenes + scene] -> every x design cells of r^n
 };
 
 static size_t field_bytes(const Scene2* s) { return (size_t)s->pitch * s->rows * sizeof(float); }
+static size_t design_cells(const Scene2* s) { return s->d_dsg ? (size_t)s->dsg_w * s->dsg_h : 0; }
+
+// store mode: point every scene's recording at the history block of the
+// segment that contains step t
+static void patch_for_step(const fdtd_ctx* c, const AdjState* A, TmzDev* dev, int64_t t) {
+    const int ns = (int)c->s2.size();
+    const int64_t slot = t / A->every;
+    for (int k = 0; k < ns; k++) {
+        const size_t q = (size_t)slot * ns + k;
+        float* h = q < A->hist.size() ? A->hist[q] : nullptr;
+        dev[k].dsg_rec = h;
+        dev[k].dsg_rec_n0 = slot * A->every;
+        dev[k].dsg_rec_len = h ? A->every : 0;
+    }
+}
+
+void adj_patch_descriptors(fdtd_ctx* c, TmzDev* dev) {
+    const AdjState* A = (const AdjState*)c->adj;
+    if (!A || A->every <= 0 || !A->store) return;
+    patch_for_step(c, A, dev, c->t);
+}
 
 int adj_checkpoint_if_due(fdtd_ctx* c) {
     AdjState* A = (AdjState*)c->adj;
     if (!A || A->every <= 0 || c->t % A->every) return FDTD_OK;
     const int slot = (int)(c->t / A->every);
     const int ns = (int)c->s2.size();
+    if (A->store) {
+        if ((int)A->hist.size() < (slot + 1) * ns) A->hist.resize((size_t)(slot + 1) * ns, nullptr);
+        for (int k = 0; k < ns; k++) {
+            const size_t hw = design_cells(c->s2[k]);
+            float*& p = A->hist[(size_t)slot * ns + k];
+            if (hw && !p && cudaMalloc(&p, (size_t)A->every * hw * sizeof(float)) != cudaSuccess) {
+                cudaGetLastError();
+                p = nullptr;
+                c->err = "design history: out of device memory (FDTD_OPT_ADJ_STORE = 0 recomputes instead)";
+                return FDTD_ENOMEM;
+            }
+        }
+        if ((int)c->h_scenes.size() != ns) return FDTD_OK;   // descriptors not built yet: rebuild patches them
+        patch_for_step(c, A, c->h_scenes.data(), c->t);
+        cudaError_t e = cudaMemcpyAsync(c->d_scenes, c->h_scenes.data(), ns * sizeof(TmzDev), cudaMemcpyHostToDevice,
+                                        c->stream);
+        if (e != cudaSuccess) {
+            c->err = std::string("design history descriptors: ") + cudaGetErrorString(e);
+            return FDTD_ECUDA;
+        }
+        return FDTD_OK;
+    }
     if ((int)A->ckpt.size() < (slot + 1) * ns) A->ckpt.resize((size_t)(slot + 1) * ns, nullptr);
     for (int k = 0; k < ns; k++) {
         Scene2* s = c->s2[k];
@@ -562,7 +605,6 @@ int adj_checkpoint_if_due(fdtd_ctx* c) {
             }
         }
     }
-    c->launches += 0;
     return FDTD_OK;
 }
 
@@ -575,10 +617,14 @@ int adj_next_boundary(const fdtd_ctx* c, int64_t t) {
 void adj_free(fdtd_ctx* c) {
     AdjState* A = (AdjState*)c->adj;
     if (!A) return;
+    cudaStreamSynchronize(c->stream);
     for (float* p : A->ckpt)
+        if (p) cudaFree(p);
+    for (float* p : A->hist)
         if (p) cudaFree(p);
     delete A;
     c->adj = nullptr;
+    c->dirty = true;   // descriptors drop the recording pointers
 }
 
 }  // namespace gem
@@ -601,6 +647,7 @@ int fdtd_set_checkpointing(fdtd_ctx* c, int every) {
     if (every > 0) {
         AdjState* A = new AdjState();
         A->every = every;
+        A->store = c->opt_adj_store;
         c->adj = A;
     }
     return FDTD_OK;
@@ -615,15 +662,21 @@ int fdtd_adjoint_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, f
     }
     const int64_t N = c->t;
     const int ns = (int)c->s2.size();
-    if (N < 1 || (int64_t)A->ckpt.size() < ((N - 1) / A->every + 1) * ns) {
-        c->err = "no checkpointed forward run to reverse";
-        return FDTD_ESTATE;
-    }
+    const int64_t nseg = N >= 1 ? (N - 1) / A->every + 1 : 0;
     for (Scene2* s : c->s2)
         if (!s->d_dsg) {
             c->err = "every scene needs a design rectangle (fdtd_set_design)";
             return FDTD_ESTATE;
         }
+    {
+        const std::vector<float*>& have = A->store ? A->hist : A->ckpt;
+        bool ok = N >= 1 && (int64_t)have.size() >= nseg * ns;
+        for (int64_t q = 0; ok && q < nseg * ns; q++) ok = have[(size_t)q] != nullptr;
+        if (!ok) {
+            c->err = "no recorded forward run to reverse";
+            return FDTD_ESTATE;
+        }
+    }
     cudaStream_t st = c->stream;
     auto cuda_err = [&](cudaError_t e, const char* what) {
         c->err = std::string(what) + ": " + cudaGetErrorString(e);
@@ -683,17 +736,16 @@ int fdtd_adjoint_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, f
     std::vector<TmzDev> fwd(ns), adj(ns);
     std::vector<Task> tasks, tasks_g, tasks_l;   // interior, CPML, lite general
     std::vector<Sample2> tsrc;
-    std::vector<float*> rec_of(ns), erec_of(ns), grad_of(ns);
-    std::vector<const float2*> dc_of(ns);
+    std::vector<float*> rec_of(ns), erec_of(ns), grad_of(ns), fac_of(ns);
     const int T = c->opt_tblock, seg = c->opt_segment, warps = c->opt_warps, gwarps = 2, lwarps = 4;
     for (int k = 0; k < ns; k++) {
         Scene2* s = c->s2[k];
-        const size_t fb = field_bytes(s), hw = (size_t)s->dsg_w * s->dsg_h;
-        float *aset = nullptr, *rec = nullptr, *erec = nullptr, *gr = nullptr, *src = nullptr;
-        float2* dc = nullptr;
-        if (!dmalloc(F_COUNT2 * 2 * fb, (void**)&aset) || !dmalloc((size_t)every * 2 * hw * sizeof(float), (void**)&rec) ||
+        const size_t fb = field_bytes(s), hw = design_cells(s);
+        float *aset = nullptr, *rec = nullptr, *erec = nullptr, *gr = nullptr, *src = nullptr, *fac = nullptr;
+        if (!dmalloc(F_COUNT2 * 2 * fb, (void**)&aset) ||
+            (!A->store && !dmalloc((size_t)every * hw * sizeof(float), (void**)&rec)) ||
             !dmalloc((size_t)every * hw * sizeof(float), (void**)&erec) ||
-            !dmalloc(hw * sizeof(float), (void**)&gr) || !dmalloc(hw * sizeof(float2), (void**)&dc) ||
+            !dmalloc(hw * sizeof(float), (void**)&gr) || !dmalloc(hw * sizeof(float), (void**)&fac) ||
             !dmalloc(tab[k].size() * sizeof(float), (void**)&src)) {
             cleanup();
             c->err = "adjoint: out of device memory";
@@ -702,17 +754,17 @@ int fdtd_adjoint_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, f
         cudaMemsetAsync(aset, 0, F_COUNT2 * 2 * fb, st);
         cudaMemsetAsync(gr, 0, hw * sizeof(float), st);
         cudaMemcpyAsync(src, tab[k].data(), tab[k].size() * sizeof(float), cudaMemcpyHostToDevice, st);
-        // dCa/deps_r and dCb/deps_r from eq. (7): with D = eps + sigma dt / 2,
-        // Cb = dt / D, Ca = (eps - sigma dt / 2) / D, dD/deps_r = eps0
-        std::vector<float2> dch(hw);
+        // eq. (7) with D = eps0 eps_r + sigma dt / 2: Ca = (eps0 eps_r - sigma dt / 2) / D,
+        // Cb = dt / D, so dCb/deps_r = -eps0 dt / D^2 = (-eps0 / D) Cb and
+        // dCa/deps_r = eps0 sigma dt / D^2 = -sigma dCb/deps_r; the per-cell factor
+        // of sum_n e^{n+1} r^n is -eps0 / D
+        std::vector<float> fach(hw);
         const double eps0 = 1.0 / (4.0e-7 * M_PI * 299792458.0 * 299792458.0);
         for (size_t q = 0; q < hw; q++) {
-            const double eps = eps0 * s->dsg_eps[q];
             const double sg = s->dsg_sig.empty() ? 0.0 : s->dsg_sig[q];
-            const double D = eps + sg * s->dt / 2.0;
-            dch[q] = make_float2((float)(eps0 * sg * s->dt / (D * D)), (float)(-eps0 * s->dt / (D * D)));
+            fach[q] = (float)(-eps0 / (eps0 * s->dsg_eps[q] + sg * s->dt / 2.0));
         }
-        cudaMemcpyAsync(dc, dch.data(), hw * sizeof(float2), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(fac, fach.data(), hw * sizeof(float), cudaMemcpyHostToDevice, st);
         for (int f = 0; f < F_COUNT2; f++)
             for (int p = 0; p < 2; p++) abuf.push_back((float*)((char*)aset + (f * 2 + p) * fb));
         // forward descriptor for the recompute, adjoint descriptor for the reverse sweep
@@ -724,18 +776,15 @@ int fdtd_adjoint_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, f
         }
         d.dsg_rec = rec;
         d.dsg_rec_len = every;
-        d.dsg_dcoef = dc;
         d.grad = gr;
         d.adj_rec = erec;
         d.adj_src = src;
         d.n_adj = std::max(1, n_adj[k]);
-        d.rdx = (float)(1.0 / s->dx);
-        d.rdy = (float)(1.0 / s->dy);
         fwd[k] = d;
         rec_of[k] = rec;
         erec_of[k] = erec;
         grad_of[k] = gr;
-        dc_of[k] = dc;
+        fac_of[k] = fac;
         TmzDev a = d;
         for (int f = 0; f < F_COUNT2; f++)
             for (int p = 0; p < 2; p++) a.f[f][p] = abuf[(size_t)k * F_COUNT2 * 2 + f * 2 + p];
@@ -812,38 +861,41 @@ int fdtd_adjoint_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, f
         return cuda_err(e, "adjoint: upload");
     }
 
-    // swap the forward descriptors in for the recompute (recording on)
+    // checkpoint mode: swap the forward descriptors in for the recompute (recording on)
     TmzDev* saved_scenes = c->d_scenes;
-    c->d_scenes = d_fwd;
+    if (!A->store) c->d_scenes = d_fwd;
     int apar = 0;
-    const int64_t nseg = (N - 1) / every + 1;
     int rc = FDTD_OK;
     for (int64_t sg = nseg - 1; sg >= 0 && rc == FDTD_OK; sg--) {
         const int64_t a0 = sg * every, len = std::min<int64_t>(every, N - a0);
-        // restore the checkpoint into buffer 0 and recompute the segment
-        for (int k = 0; k < ns && rc == FDTD_OK; k++) {
-            Scene2* s = c->s2[k];
-            const size_t fb = field_bytes(s);
-            const float* p = A->ckpt[(size_t)sg * ns + k];
-            for (int f = 0; f < F_COUNT2; f++) {
-                e = cudaMemcpyAsync(s->fbuf[f][0], (const char*)p + f * fb, fb, cudaMemcpyDeviceToDevice, st);
-                if (e != cudaSuccess) rc = cuda_err(e, "adjoint: restore");
-            }
+        for (int k = 0; k < ns; k++) {
             fwd[k].dsg_rec_n0 = a0;
             adj[k].dsg_rec_n0 = a0;
         }
-        if (rc) break;
-        // both descriptor sets see this segment's recording base step
-        cudaMemcpyAsync(d_fwd, fwd.data(), ns * sizeof(TmzDev), cudaMemcpyHostToDevice, st);
+        // the adjoint descriptors see this segment's base step
         cudaMemcpyAsync(d_adj, adj.data(), ns * sizeof(TmzDev), cudaMemcpyHostToDevice, st);
-        c->parity = 0;
-        for (int64_t q = 0; q < len && rc == FDTD_OK;) {
-            const int done = (int)std::min<int64_t>(T, len - q);
-            rc = tmz_fused_launch(c, done, warps, a0 + q, c->parity);
-            c->parity ^= 1;
-            q += done;
+        if (!A->store) {
+            // restore the checkpoint into buffer 0 and recompute the segment, recording r^n
+            for (int k = 0; k < ns && rc == FDTD_OK; k++) {
+                Scene2* s = c->s2[k];
+                const size_t fb = field_bytes(s);
+                const float* p = A->ckpt[(size_t)sg * ns + k];
+                for (int f = 0; f < F_COUNT2; f++) {
+                    e = cudaMemcpyAsync(s->fbuf[f][0], (const char*)p + f * fb, fb, cudaMemcpyDeviceToDevice, st);
+                    if (e != cudaSuccess) rc = cuda_err(e, "adjoint: restore");
+                }
+            }
+            if (rc) break;
+            cudaMemcpyAsync(d_fwd, fwd.data(), ns * sizeof(TmzDev), cudaMemcpyHostToDevice, st);
+            c->parity = 0;
+            for (int64_t q = 0; q < len && rc == FDTD_OK;) {
+                const int done = (int)std::min<int64_t>(T, len - q);
+                rc = tmz_fused_launch(c, done, warps, a0 + q, c->parity);
+                c->parity ^= 1;
+                q += done;
+            }
+            if (rc) break;
         }
-        if (rc) break;
         // reverse the segment, T reverse steps per launch; the CPML and lite
         // variants run on their own streams beside the interior one
         AdjLists L;
@@ -880,10 +932,11 @@ int fdtd_adjoint_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, f
             q -= done;
         }
         if (rc) break;
-        // fold the segment's e and forward recording into dL/deps_r
+        // fold the segment's e and recorded r^n into dL/deps_r
         for (int k = 0; k < ns; k++) {
-            const int hw = c->s2[k]->dsg_w * c->s2[k]->dsg_h;
-            k_grad_reduce<<<(hw + 255) / 256, 256, 0, st>>>(rec_of[k], erec_of[k], dc_of[k], grad_of[k], hw, (int)len);
+            const int hw = (int)design_cells(c->s2[k]);
+            const float* r = A->store ? A->hist[(size_t)sg * ns + k] : rec_of[k];
+            k_grad_reduce<<<(hw + 255) / 256, 256, 0, st>>>(r, erec_of[k], fac_of[k], grad_of[k], hw, (int)len);
             c->launches++;
         }
         e = cudaGetLastError();

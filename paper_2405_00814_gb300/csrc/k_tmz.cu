@@ -162,7 +162,6 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
     const size_t band_plane = (size_t)dsg_h * pitch;
     float* const dsg_rec = S->dsg_rec;
     const long long rec_n0 = S->dsg_rec_n0, rec_len = S->dsg_rec_len;
-    const float rdx = S->rdx, rdy = S->rdy;
     // probes and monitor cells of this task: the first 32 ride in lane registers
     const int n_samp = tk.samp_end - tk.samp_begin;
     const bool has_samp = n_samp > 0;
@@ -333,29 +332,29 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
                         if (di + 2 >= 0 && di + 2 < dsg_w) c2 = drow[di + 2];
                         if (di + 3 >= 0 && di + 3 < dsg_w) c3 = drow[di + 3];
                     }
-                    // reverse-mode recompute: E^n and curl H^{n+1/2} of the owned design cells
-                    const long long nr = n0 + (t - 1) - rec_n0;
-                    if (dsg_rec && nr >= 0 && nr < rec_len && a >= tk.ya && a < tk.yb && out_lane) {
-                        const size_t hw = (size_t)dsg_w * dsg_h;
-                        float* re = dsg_rec + (size_t)nr * 2 * hw + (size_t)dj * dsg_w;
-                        const float ev[4] = {E[t].x, E[t].y, E[t].z, E[t].w};
-                        const float kv[4] = {dhy.x * rdx - dhx.x * rdy, dhy.y * rdx - dhx.y * rdy,
-                                             dhy.z * rdx - dhx.z * rdy, dhy.w * rdx - dhx.w * rdy};
-#pragma unroll
-                        for (int q = 0; q < 4; q++) {
-                            const int d = di + q;
-                            if (d >= 0 && d < dsg_w && cx + q >= tk.x0 && cx + q < tk.x0 + (STRIP - 2 * HALO)) {
-                                re[d] = ev[q];
-                                re[hw + d] = kv[q];
-                            }
-                        }
-                    }
                 }
             }
+            const float4 e_old = E[t];
             E[t].x = e_upd(E[t].x, dhy.x, dhx.x, c0);
             E[t].y = e_upd(E[t].y, dhy.y, dhx.y, c1);
             E[t].z = e_upd(E[t].z, dhy.z, dhx.z, c2);
             E[t].w = e_upd(E[t].w, dhy.w, dhx.w, c3);
+            // reverse mode: E^{n+1} - E^n of the owned design cells (before the
+            // source), which carries dL/deps_r of step n up to a per-cell factor
+            if (dsg && dsg_rec) {
+                const int dj = a - dsg_j0;
+                const long long nr = n0 + (t - 1) - rec_n0;
+                if (dj >= 0 && dj < dsg_h && nr >= 0 && nr < rec_len && a >= tk.ya && a < tk.yb && out_lane) {
+                    const int di = cx - dsg_i0;
+                    float* re = dsg_rec + (size_t)nr * dsg_w * dsg_h + (size_t)dj * dsg_w;
+                    const float dv[4] = {E[t].x - e_old.x, E[t].y - e_old.y, E[t].z - e_old.z, E[t].w - e_old.w};
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const int d = di + q;
+                        if (d >= 0 && d < dsg_w && cx + q >= tk.x0 && cx + q < tk.x0 + (STRIP - 2 * HALO)) re[d] = dv[q];
+                    }
+                }
+            }
 
             const long long n = n0 + (t - 1);   // this level makes E^{n+1}
             if (has_src && a == src_j) {
@@ -539,7 +538,7 @@ static cudaError_t launch_persistent_T(const fdtd_ctx* c, cudaStream_t st, int p
                                        long long spin_limit, int* grid_out) {
     const int warps = 8;
     const size_t smem = tmz_fused_smem(T, warps, 1);
-    cudaError_t e = cudaFuncSetAttribute(k_tmz_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_dyn_smem((const void*)k_tmz_persistent<T>, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0, dev = 0, sms = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tmz_persistent<T>, warps * 32, smem);
@@ -864,15 +863,15 @@ static cudaError_t launch_fused_T(const Task* tasks, int n_tasks, int warps, con
     const int blocks = n_tasks / warps;   // task lists are padded to whole CTAs
     cudaError_t e;
     if (V == 1) {
-        e = cudaFuncSetAttribute(k_tmz_fused<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = ensure_dyn_smem((const void*)k_tmz_fused<T, true>, smem);
         if (e != cudaSuccess) return e;
         k_tmz_fused<T, true><<<blocks, warps * 32, smem, st>>>(c->d_scenes, tasks, n_tasks, c->d_samp, parity, n0);
     } else if (V == 2) {
-        e = cudaFuncSetAttribute(k_tmz_fused<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = ensure_dyn_smem((const void*)k_tmz_fused<T, false>, smem);
         if (e != cudaSuccess) return e;
         k_tmz_fused<T, false><<<blocks, warps * 32, smem, st>>>(c->d_scenes, tasks, n_tasks, c->d_samp, parity, n0);
     } else {
-        e = cudaFuncSetAttribute(k_tmz_interior<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = ensure_dyn_smem((const void*)k_tmz_interior<T>, smem);
         if (e != cudaSuccess) return e;
         k_tmz_interior<T><<<blocks, warps * 32, smem, st>>>(c->d_scenes, tasks, n_tasks, parity);
     }

@@ -1,5 +1,6 @@
-"""GPU reverse mode (checkpointed recompute + fused adjoint kernels) against the
-FP64 oracle's adjoint and central finite differences of the FP64 oracle."""
+"""GPU reverse mode (design history kept from the forward pass, or checkpointed
+recompute, + fused adjoint kernels) against the FP64 oracle's adjoint and central
+finite differences of the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -38,11 +39,12 @@ def _oracle_loss(sc, eps_design):
     return float(np.sum(sim.dft[0] ** 2 + sim.dft[1] ** 2))
 
 
+@pytest.mark.parametrize("store", [True, False])
 @pytest.mark.parametrize("side,npml,design,nsteps,ckpt,tblock", [(128, 10, 32, 900, 100, 4), (96, 8, 24, 700, 37, 3)])
-def test_adjoint_matches_oracle(side, npml, design, nsteps, ckpt, tblock):
+def test_adjoint_matches_oracle(side, npml, design, nsteps, ckpt, tblock, store):
     from paper_2405_00814_gb300 import autograd
     scs = scenes.adjoint_scenes(side=side, n_designs=2, nsteps=nsteps, npml=npml, design=design, n_monitors=4)
-    batch = autograd.DesignBatch(scs, ckpt_every=ckpt, tblock=tblock)
+    batch = autograd.DesignBatch(scs, ckpt_every=ckpt, tblock=tblock, store=store)
     eps = np.stack([s.design_eps for s in scs])
     F = batch.forward(eps)
     g = batch.gradient(2.0 * F)
@@ -75,6 +77,34 @@ def test_adjoint_matches_central_fd():
     err = np.abs(got - fd) / np.maximum(np.abs(fd), 1e-2 * gscale)
     assert np.max(err) <= TOL_GRAD, (got, fd)
     batch.close()
+
+
+@pytest.mark.parametrize("store", [True, False])
+def test_adjoint_lossy_design_matches_oracle(store):
+    """A design region with sigma > 0: dCa/deps_r no longer vanishes, and the
+    gradient still follows from E^{n+1} - E^n."""
+    from paper_2405_00814_gb300 import fdtd
+    import oracle
+    sc = scenes.adjoint_scenes(side=96, n_designs=1, nsteps=600, npml=8, design=24, n_monitors=3)[0]
+    i0, j0, w, h = sc.design
+    sig_d = 0.05 * np.random.default_rng(11).random((h, w))
+    sim = fdtd.Simulation.batch([sc])
+    sim.select(0)
+    sim.set_scene_source(sc.source)
+    sim.set_design(i0, j0, sc.design_eps, sig_d)
+    mid = sim.add_dft_monitor(sc.monitors, sc.freqs)
+    sim.set_option("adj_store", int(store))
+    sim.set_checkpointing(60)
+    sim.step(sc.nsteps)
+    F = sim.read_dft(mid)
+    g = sim.adjoint_grad([2.0 * F], (1, h, w))[0]
+    sim.close()
+    sig_cell = sc.sigma[sc.mat].astype(np.float64)
+    sig_cell[j0:j0 + h, i0:i0 + w] = sig_d
+    osim = oracle.TMz(sc, sigma_cell=sig_cell, nsteps_src=sc.nsteps)
+    _, fre, fim, gref = osim.adjoint_grad(sc.nsteps, 60, sc.monitors, sc.freqs, sc.design)
+    assert np.max(np.abs(F - (fre + 1j * fim))) <= 1e-4 * np.max(np.abs(fre + 1j * fim))
+    assert _grad_err(g, gref) <= TOL_GRAD, _grad_err(g, gref)
 
 
 def test_autograd_function_backward():
