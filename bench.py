@@ -107,21 +107,86 @@ def _traffic_record():
 
 def cpu_baseline(sc, budget_s=12.0):
     """The FP64 oracle as it stands, on the host cores, over a bounded prefix of
-    the same workload: chunks of 10 steps until the budget is used."""
+    the same workload: chunks of 10 steps until the budget is used, with every
+    core (OpenMP over rows) and then with one thread."""
     import oracle
-    sim = oracle.TMz(sc, nsteps_src=sc.nsteps)
-    sim.run(2)
-    t0 = time.perf_counter()
-    steps = 0
-    while time.perf_counter() - t0 < budget_s:
-        sim.run(10)
-        steps += 10
-    dt = time.perf_counter() - t0
-    return {"value": sc.cells * steps / dt, "unit": "cell-updates/s", "cores": oracle.num_threads(),
-            "kind": "oracle", "sample": f"{steps} leapfrog steps of the full {sc.nx}x{sc.ny} scene (FP64, OpenMP over rows)"}
+    cores = oracle.num_threads()
+
+    def timed(threads, budget):
+        oracle.set_threads(threads)
+        sim = oracle.TMz(sc, nsteps_src=sc.nsteps)
+        sim.run(2)
+        t0 = time.perf_counter()
+        steps = 0
+        while time.perf_counter() - t0 < budget:
+            sim.run(10)
+            steps += 10
+        return sc.cells * steps / (time.perf_counter() - t0), steps
+
+    try:
+        v_all, s_all = timed(cores, budget_s)
+        v_one, s_one = timed(1, budget_s / 3)
+    finally:
+        oracle.set_threads(cores)
+    return {"value": v_all, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"{s_all} leapfrog steps of the full {sc.nx}x{sc.ny} scene (FP64, OpenMP over rows)",
+            "single_thread": {"value": v_one, "sample": f"{s_one} leapfrog steps, 1 thread"},
+            "paper_sweep": oracle_sweep()}
 
 
-def adjoint_ratio(stream, reps=2):
+def oracle_sweep(sides=(250, 1000, 2000, 3000, 4000, 5000, 6400), budget_s=1.5):
+    """The paper's free-space sweep on the oracle (all cores): a bounded prefix
+    of each 1024-step solve, at least 2 steps, about budget_s seconds per side."""
+    import oracle
+    from paper_2405_00814_gb300 import scenes
+    out = {}
+    for side in sides:
+        sc = scenes.free_space(side)
+        sim = oracle.TMz(sc, nsteps_src=sc.nsteps)
+        sim.run(1)
+        t0 = time.perf_counter()
+        steps = 0
+        while steps < 2 or (time.perf_counter() - t0 < budget_s and steps < sc.nsteps):
+            sim.run(1)
+            steps += 1
+        out[str(side)] = {"cell_updates_per_s": sc.cells * steps / (time.perf_counter() - t0), "steps": steps}
+    return out
+
+
+def paper_sweep(stream, tune, sides=(250, 1000, 2000, 3000, 4000, 5000, 6400), nsteps=1024, runs=5):
+    """The paper's timing workload (Sec. IV, Fig. 5): free space with a 16-cell
+    absorbing boundary, square grids of the listed sides, 1024 steps, 5 runs per
+    side; mean and 95% confidence half-width (Student t, 4 dof) of the device
+    time per solve, and cell-updates/s."""
+    import torch
+    from paper_2405_00814_gb300 import fdtd, scenes
+    t95 = 2.776
+    out = {}
+    for side in sides:
+        sc = scenes.free_space(side, nsteps=nsteps)
+        sim = fdtd.from_scene(sc, stream=stream)
+        for k, v in tune.items():
+            sim.set_option(k, v)
+        sim.step(nsteps)            # warm-up solve
+        ms = []
+        for _ in range(runs):
+            sim.reset()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(nsteps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        sim.close()
+        mean = sum(ms) / runs
+        sd = (sum((x - mean) ** 2 for x in ms) / (runs - 1)) ** 0.5
+        out[str(side)] = {"ms_mean": mean, "ms_ci95": t95 * sd / runs ** 0.5,
+                          "cell_updates_per_s": sc.cells * nsteps / (mean / 1e3)}
+    return {"workload": "paper_sweep_free_space_cpml16_1024steps", "runs": runs, "sides": out,
+            "timing": "CUDA events around fdtd_step per solve after one warm-up solve"}
+
+
+def adjoint_ratio(stream, reps=2, nsteps=None):
     """Time of one adjoint gradient (forward with checkpoints every 100 steps +
     reverse sweep) over the time of one plain forward solve, on the 1024^2
     inverse-design workload (8 designs, 256^2 design regions, 8 monitors,
@@ -129,7 +194,7 @@ def adjoint_ratio(stream, reps=2):
     import numpy as np
     import torch
     from paper_2405_00814_gb300 import autograd, scenes
-    scs = scenes.adjoint_scenes()
+    scs = scenes.adjoint_scenes() if nsteps is None else scenes.adjoint_scenes(nsteps=nsteps)
     eps = np.stack([s.design_eps for s in scs])
     plain = autograd.DesignBatch(scs, ckpt_every=0, stream=stream)
     ckpt = autograd.DesignBatch(scs, ckpt_every=100, stream=stream)
@@ -149,7 +214,7 @@ def adjoint_ratio(stream, reps=2):
     plain.close()
     ckpt.close()
     cu = scs[0].cells * len(scs) * scs[0].nsteps
-    return {"workload": "adjoint_tmz2d_1024x1024_x8designs_3000steps_ckpt100", "forward_ms": 1e3 * t_fwd,
+    return {"workload": f"adjoint_tmz2d_1024x1024_x8designs_{scs[0].nsteps}steps_ckpt100", "forward_ms": 1e3 * t_fwd,
             "gradient_ms": 1e3 * t_grad, "ratio": t_grad / t_fwd, "forward_cups": cu / t_fwd,
             "timing": "host wall clock around synchronised calls, best of %d after one warm-up" % reps}
 
@@ -185,13 +250,15 @@ def batch_throughput(stream, reps=2):
             "timing": "CUDA events around one solve replayed from a CUDA graph, best of %d after one warm-up" % reps}
 
 
-def yee3d_throughput(stream, nsteps=200):
+def yee3d_throughput(stream, nsteps=200, side=512, kernel=None):
     """512^3 box workload (64 dielectric boxes, 10-cell CPML, Ez dipole, DFT plane
     at 3 frequencies): cell-updates/s over nsteps steps."""
     import torch
     from paper_2405_00814_gb300 import fdtd, scenes
-    sc = scenes.box_scene()
+    sc = scenes.box_scene() if side == 512 else scenes.box_scene(side=side)
     sim = fdtd.from_scene(sc, stream=stream)
+    if kernel is not None:
+        sim.set_option("kernel", kernel)
     sim.add_dft_plane(sc.dft_plane_k, ("ex", "ey", "ez"), sc.freqs)
     sim.step(10)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -203,7 +270,7 @@ def yee3d_throughput(stream, nsteps=200):
     sim.close()
     peak, _ = _peaks()
     cu = sc.cells * nsteps / (ms / 1e3)
-    return {"workload": "yee3d_512^3_boxes64_cpml10_dftplane", "cell_updates_per_s": cu, "ms_per_step": ms / nsteps,
+    return {"workload": f"yee3d_{side}^3_boxes64_cpml10_dftplane", "cell_updates_per_s": cu, "ms_per_step": ms / nsteps,
             "hbm_roofline_frac_at_49B_per_cell_update": cu * 49.0 / (peak * 1e9)}
 
 
@@ -244,7 +311,7 @@ def main():
     ap.add_argument("--tblock", type=int, default=None)
     ap.add_argument("--segment", type=int, default=None)
     ap.add_argument("--warps", type=int, default=None)
-    ap.add_argument("--kernel", type=int, default=0)
+    ap.add_argument("--kernel", type=int, default=None, help="FDTD_OPT_KERNEL (2D default 0; 3D default 1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-sample", type=int, default=20)
@@ -252,6 +319,9 @@ def main():
     ap.add_argument("--size", type=int, default=4096, help="grid side (profiling runs use smaller sides)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--graph", action="store_true", help="replay each solve from a recorded CUDA graph")
+    ap.add_argument("--workload", default="main", choices=["main", "adjoint", "batch", "yee3d", "sweep"],
+                    help="main: the JSON line of record; the others time one secondary workload alone "
+                         "(for profiling; --nsteps and, for yee3d, --size and --kernel apply)")
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint-ratio measurement")
     args = ap.parse_args()
 
@@ -274,14 +344,30 @@ def main():
     __graft_entry__.build()
     from paper_2405_00814_gb300 import fdtd, scenes
 
+    stream = torch.cuda.current_stream()
+    if args.workload != "main":
+        if args.workload == "adjoint":
+            res = adjoint_ratio(stream, nsteps=args.nsteps)
+        elif args.workload == "batch":
+            res = batch_throughput(stream)
+        elif args.workload == "yee3d":
+            res = yee3d_throughput(stream, nsteps=args.nsteps or 200, side=args.size if args.size != 4096 else 512,
+                                   kernel=args.kernel)
+        else:
+            res = paper_sweep(stream, {"tblock": 4, "segment": 24, "warps": 8})
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        return
+
     sc = scenes.ellipse_scene(side=args.size)
     nsteps = args.nsteps or sc.nsteps
-    stream = torch.cuda.current_stream()
     sim = fdtd.from_scene(sc, stream=stream)
     tune = {"tblock": 4, "segment": 24, "warps": 8}
     for k in ("tblock", "segment", "warps"):
         if getattr(args, k) is not None:
             tune[k] = getattr(args, k)
+    if args.kernel is None:
+        args.kernel = 0
     sim.set_option("kernel", args.kernel)
     for k, v in tune.items():
         sim.set_option(k, v)
@@ -380,6 +466,7 @@ def main():
         out["adjoint"] = adjoint_ratio(stream)
         out["batch"] = batch_throughput(stream)
         out["yee3d"] = yee3d_throughput(stream)
+        out["paper_sweep"] = paper_sweep(stream, tune)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sc, args.cpu_budget)
     if rank == 0:

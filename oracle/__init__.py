@@ -16,7 +16,6 @@ no closed form; it is checked by a reflection bound against an enlarged domain.
 from __future__ import annotations
 
 import ctypes as C
-import os
 
 import numpy as np
 
@@ -442,6 +441,3 @@ class Yee3D:
         return lib().or3_energy(C.byref(self._p), _p(self.eps_cell), C.byref(self._s),
                                 *[_p(x) for x in a])
 
-
-def set_threads(n: int):
-    os.environ["OMP_NUM_THREADS"] = str(n)

@@ -275,6 +275,7 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
         acommit();
     }
 
+#pragma unroll 1
     for (int r = s_row; r <= r_last; ++r) {
         await_<PF - 1>();
 #pragma unroll

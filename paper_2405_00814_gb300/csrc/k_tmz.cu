@@ -229,7 +229,9 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
     float* rec = S->rec;
     const int n_rec = S->n_rec;
 
-#pragma unroll 2
+    // not unrolled: the general body is large, and instruction fetch, not
+    // issue, limits these latency-bound warps
+#pragma unroll 1
     for (int r = s_row; r <= r_last; ++r) {
         cp_wait<PF - 1>();
         // shift the ring and take row r from its stage
