@@ -274,6 +274,34 @@ def yee3d_throughput(stream, nsteps=200, side=512, kernel=None):
             "hbm_roofline_frac_at_49B_per_cell_update": cu * 49.0 / (peak * 1e9)}
 
 
+def edgelist_throughput(stream, side=2048, nsteps=200):
+    """The literal message-passing form (Prop. 1/2: two CSR layers per step) on
+    the heterogeneous CPML scene scaled to side^2: cell-updates/s, and the
+    algorithmic bytes per cell-update of the two gathers (8 B per edge for
+    column index and weight, 12 B per node for row pointer, value and result)."""
+    import torch
+    from paper_2405_00814_gb300 import fdtd, scenes
+    sc = scenes.ellipse_scene(side=side)
+    sim = fdtd.from_scene(sc, stream=stream)
+    sim.step_edgelist(4)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step_edgelist(nsteps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    b = 0
+    for layer in (1, 2):
+        nn, ne = sim.graph_size(layer)
+        b += 8 * ne + 12 * nn
+    sim.close()
+    peak, _ = _peaks()
+    cu = sc.cells * nsteps / (ms / 1e3)
+    bpc = b / sc.cells
+    return {"workload": f"edgelist_tmz2d_{side}x{side}_ellipses_cpml16", "cell_updates_per_s": cu,
+            "bytes_per_cell_update": bpc, "hbm_frac": cu * bpc / (peak * 1e9), "ms_per_step": ms / nsteps}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -319,7 +347,7 @@ def main():
     ap.add_argument("--size", type=int, default=4096, help="grid side (profiling runs use smaller sides)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--graph", action="store_true", help="replay each solve from a recorded CUDA graph")
-    ap.add_argument("--workload", default="main", choices=["main", "adjoint", "batch", "yee3d", "sweep"],
+    ap.add_argument("--workload", default="main", choices=["main", "adjoint", "batch", "yee3d", "sweep", "edgelist"],
                     help="main: the JSON line of record; the others time one secondary workload alone "
                          "(for profiling; --nsteps and, for yee3d, --size and --kernel apply)")
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint-ratio measurement")
@@ -353,6 +381,8 @@ def main():
         elif args.workload == "yee3d":
             res = yee3d_throughput(stream, nsteps=args.nsteps or 200, side=args.size if args.size != 4096 else 512,
                                    kernel=args.kernel)
+        elif args.workload == "edgelist":
+            res = edgelist_throughput(stream, side=args.size if args.size != 4096 else 2048, nsteps=args.nsteps or 200)
         else:
             res = paper_sweep(stream, {"tblock": 4, "segment": 24, "warps": 8})
         if rank == 0:
@@ -467,6 +497,7 @@ def main():
         out["batch"] = batch_throughput(stream)
         out["yee3d"] = yee3d_throughput(stream)
         out["paper_sweep"] = paper_sweep(stream, tune)
+        out["edgelist"] = edgelist_throughput(stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sc, args.cpu_budget)
     if rank == 0:

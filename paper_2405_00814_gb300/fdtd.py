@@ -373,6 +373,12 @@ class Simulation:
         self._check(self._L.fdtd_adjoint_grad(self._h, re.ctypes.data, im.ctypes.data, res.ctypes.data, 0))
         return res
 
+    def graph_size(self, layer: int):
+        """(nodes, edges) of message-passing layer 1 or 2 of the current scene."""
+        nn, ne = C.c_int64(), C.c_int64()
+        self._check(self._L.fdtd_export_graph(self._h, layer, C.byref(nn), C.byref(ne), None, None, None))
+        return nn.value, ne.value
+
     def export_graph(self, layer: int):
         nn, ne = C.c_int64(), C.c_int64()
         self._check(self._L.fdtd_export_graph(self._h, layer, C.byref(nn), C.byref(ne), None, None, None))
