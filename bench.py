@@ -250,7 +250,7 @@ def batch_throughput(stream, reps=2):
             "timing": "CUDA events around one solve replayed from a CUDA graph, best of %d after one warm-up" % reps}
 
 
-def yee3d_throughput(stream, nsteps=200, side=512, kernel=None):
+def yee3d_throughput(stream, nsteps=200, side=512, kernel=None, segment=None):
     """512^3 box workload (64 dielectric boxes, 10-cell CPML, Ez dipole, DFT plane
     at 3 frequencies): cell-updates/s over nsteps steps."""
     import torch
@@ -259,6 +259,8 @@ def yee3d_throughput(stream, nsteps=200, side=512, kernel=None):
     sim = fdtd.from_scene(sc, stream=stream)
     if kernel is not None:
         sim.set_option("kernel", kernel)
+    if segment is not None:
+        sim.set_option("segment", segment)
     sim.add_dft_plane(sc.dft_plane_k, ("ex", "ey", "ez"), sc.freqs)
     sim.step(10)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -349,7 +351,7 @@ def main():
     ap.add_argument("--graph", action="store_true", help="replay each solve from a recorded CUDA graph")
     ap.add_argument("--workload", default="main", choices=["main", "adjoint", "batch", "yee3d", "sweep", "edgelist"],
                     help="main: the JSON line of record; the others time one secondary workload alone "
-                         "(for profiling; --nsteps and, for yee3d, --size and --kernel apply)")
+                         "(for profiling; --nsteps and, for yee3d, --size, --kernel and --segment apply)")
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint-ratio measurement")
     args = ap.parse_args()
 
@@ -380,7 +382,7 @@ def main():
             res = batch_throughput(stream)
         elif args.workload == "yee3d":
             res = yee3d_throughput(stream, nsteps=args.nsteps or 200, side=args.size if args.size != 4096 else 512,
-                                   kernel=args.kernel)
+                                   kernel=args.kernel, segment=args.segment)
         elif args.workload == "edgelist":
             res = edgelist_throughput(stream, side=args.size if args.size != 4096 else 2048, nsteps=args.nsteps or 200)
         else:

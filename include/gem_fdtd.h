@@ -74,10 +74,10 @@ extern "C" {
                                 1 = one H and one E launch per step;
                                 2 = persistent: one cooperative launch runs many T-step blocks of every scene,
                                     warps pulling tasks from a shared counter, a bounded grid barrier between blocks.
-                                3D: 0 = fused z-marching kernel, 1 = one H and one E launch per step (default) */
+                                3D: 0 = fused z-marching kernel (default), 1 = one H and one E launch per step */
 #define FDTD_OPT_TBLOCK 1    /* time steps per HBM pass of the fused kernel, 1..4 */
 #define FDTD_OPT_SEGMENT 2   /* 2D: rows per warp task of the fused kernel (multiple of 8, >= 8);
-                                3D: planes per z-segment of the fused z-marching kernel (>= 1) */
+                                3D: planes per z-segment of the fused z-marching kernel (>= 1, default 16) */
 #define FDTD_OPT_WARPS 3     /* warps per CTA of the fused kernel, 1..8 */
 #define FDTD_OPT_GRAPH 4     /* 1: fdtd_step records its launches into a CUDA graph and replays it when called
                                 again with the same start step, step count and buffer parity (e.g. after fdtd_reset) */
@@ -158,7 +158,8 @@ int fdtd_add_dft_monitor(fdtd_ctx* ctx, const int32_t* cells, int n_cells, const
                          int n_freq, int* mon_id);
 
 /* 3D only: running DFT of the E components in comp_mask (bit c = FDTD_EX+c) over
- * the whole plane z = k (cell index k), same convention as above. */
+ * the whole plane z = k (cell index k), same convention as above; 1..16
+ * frequencies (FDTD_EINVAL otherwise). */
 int fdtd_add_dft_plane(fdtd_ctx* ctx, int k, int comp_mask, const double* freqs_hz, int n_freq,
                        int* mon_id);
 

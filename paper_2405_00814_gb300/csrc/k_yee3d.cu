@@ -254,203 +254,340 @@ __global__ void k_e3(Dev3 S) {
 }
 
 // ---------------------------------------------------------------------------
-// fused z-marching step: one CTA owns a TX x TY tile of (i, j) and a z-segment
-// [kA, kB).  Per plane k it stages E^n(k+1) with a one-cell halo in shared
-// memory, updates H(k) on the tile plus its low halo (i0-1 column, j0-1 row,
-// recomputed from the read-only input so no other CTA is waited on), then E(k)
-// on the tile, with H(k-1) of its own column carried in registers.  Reads
-// buffer `in`, writes buffer `out`.  A segment starting above k = 0 first
+// fused z-marching step.  One CTA owns a tile of TXC = 128 cells in x by TYR
+// rows in y and a z-segment [kA, kB).  Warp w handles row j = j0 - 1 + w (warp 0
+// is the halo row j0 - 1, whose H the owned rows need), each lane 4 consecutive
+// cells as float4.  Per plane k:
+//   layer 1: H(k) of the warp's row from E(k) (rows j, j+1; the cell right of
+//            the lane), E(k+1) and H_old(k); lane 0 also forms Hy, Hz of the
+//            cell left of the tile (x0 - 1), recomputed so no other CTA is waited on;
+//   layer 2: E(k) of the owned rows from H(k) of the row (left neighbours by
+//            warp shuffle), of the row below (shared memory) and H(k-1) of the
+//            lane's own cells (registers).
+// E planes are staged by cp.async into a shared-memory ring D3 planes ahead of
+// use (136-float rows: cells x0-4 .. x0+131); H_old and the material bytes of
+// the next plane are prefetched into registers.  Two CTA barriers per plane.
+// Reads buffer `in`, writes buffer `out`.  A segment starting above k = 0 first
 // recomputes H(kA-1) (warm-up plane, nothing stored).
 // ---------------------------------------------------------------------------
-constexpr int TX3 = 32, TY3 = 8;
+constexpr int TXC = 128;           // cells per tile row (32 lanes x 4)
+constexpr int TYR = 7;             // owned rows per tile (8 warps with the halo row)
+constexpr int NW3 = TYR + 1;       // warps per CTA
+constexpr int D3 = 2;              // E planes staged ahead
+constexpr int NE3 = D3 + 2;        // E ring slots: planes k .. k + 1 + D3
+constexpr int ER3 = TYR + 2;       // staged E rows: j0 - 1 .. j0 + TYR
+constexpr int EW4 = (TXC + 8) / 4; // staged E row, float4s: cells x0 - 4 .. x0 + TXC + 3
 
 struct Bufs3 {
     const float* in[G_COUNT];
     float* out[G_COUNT];
 };
 
-__device__ __forceinline__ void cpa16(float* smem, const float* gmem, bool valid) {
+__device__ __forceinline__ void cpa16(void* smem, const void* gmem, bool valid) {
     unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(valid ? 16 : 0) : "memory");
 }
 
-constexpr int EW3 = 40;   // staged E row: storage columns [i0, i0 + 40) = cells i0 - 4 .. i0 + 35
-constexpr int HW3 = 36;   // staged H row: cells i0 - 4 .. i0 + 31
+size_t fused3_smem() {
+    return (size_t)NE3 * 3 * ER3 * EW4 * sizeof(float4)     // E ring
+           + (size_t)NW3 * 2 * TXC * sizeof(float)            // H(k) of each row: Hx, Hz
+           + 256 * sizeof(float4)                             // coefficient table
+           + 4 * TXC * sizeof(float);                         // CPML x-profiles of the tile: bHx cHx bEx cEx
+}
 
-__global__ void __launch_bounds__(TX3 * TY3) k_yee3d_fused(Dev3 S, Bufs3 B, int segz) {
-    __shared__ __align__(16) float Eb[3][3][TY3 + 2][EW3];   // E^n, planes k, k+1, k+2 (ring by plane % 3)
-    __shared__ __align__(16) float Hb[2][3][TY3 + 1][HW3];   // H^{n-1/2}, planes k, k+1 (ring by plane % 2)
-    __shared__ float Ht[3][TY3 + 1][TX3 + 1];                // H^{n+1/2}(k) on the tile and its low halo
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX3 + tx;
-    const int i0 = blockIdx.x * TX3, j0 = blockIdx.y * TY3;
-    const int kA = blockIdx.z * segz, kB = min(kA + segz, S.nz);
-    const size_t plane = (size_t)S.pitch * S.rows;
-    // storage index of (column s of the staged row, row jj, plane k); column 0 is cell i0 - 4
-    auto sidx = [&](int jj, int k) { return ((size_t)(k + 1) * S.rows + (jj + 1)) * S.pitch + i0; };
-    const P3 pr{S.prof, S.pitch, S.rows, S.planes};
-    const bool pml = S.has_pml != 0;
-    const int i = i0 + tx, j = j0 + ty;
-    const bool own = i < S.nx && j < S.ny;
+__device__ __forceinline__ float f4c(const float4& v, int q) { return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w)); }
+__device__ __forceinline__ void f4s(float4& v, int q, float a) {
+    if (q == 0) v.x = a; else if (q == 1) v.y = a; else if (q == 2) v.z = a; else v.w = a;
+}
 
-    // staging: 16-byte copies of whole aligned row pieces; rows beyond the
-    // padded array (jj > ny) and planes beyond nz read as zeros
-    auto issue_e = [&](int k) {
-        const int b = k % 3;
-        for (int q = tid; q < 3 * (TY3 + 2) * (EW3 / 4); q += TX3 * TY3) {
-            const int comp = q / ((TY3 + 2) * (EW3 / 4));
-            const int r = q % ((TY3 + 2) * (EW3 / 4));
-            const int qy = r / (EW3 / 4), v = r % (EW3 / 4);
-            const int jj = j0 - 1 + qy;
-            const bool in = jj <= S.ny && k <= S.nz;
-            cpa16(&Eb[b][comp][qy][4 * v], B.in[G_EX + comp] + (in ? sidx(jj, k) + 4 * v : 0), in);
+// CPML auxiliary of one cell: psi <- b psi + c d, returns d + psi
+__device__ __forceinline__ float psi_upd(const float* in, float* out, size_t c, float b, float cc, float d, bool store) {
+    if (b == 0.f && cc == 0.f) return d;
+    const float v = b * in[c] + cc * d;
+    if (store) out[c] = v;
+    return d + v;
+}
+
+// the same for a lane's four cells at g (16-byte aligned), with their old psi
+// p already loaded: cells whose bit in `upd` is clear keep psi (their field
+// component is not updated); `nval` cells lie inside the grid and are stored
+__device__ __forceinline__ float4 psi4p(const float4 p, float* out, size_t g, float4 b, float4 c, float4 d, bool store,
+                                        int nval, unsigned upd) {
+    float4 v;
+    v.x = (upd & 1u) ? b.x * p.x + c.x * d.x : p.x;
+    v.y = (upd & 2u) ? b.y * p.y + c.y * d.y : p.y;
+    v.z = (upd & 4u) ? b.z * p.z + c.z * d.z : p.z;
+    v.w = (upd & 8u) ? b.w * p.w + c.w * d.w : p.w;
+    if (store) {
+        if (nval >= 4) {
+            *reinterpret_cast<float4*>(out + g) = v;
+        } else {
+            for (int q = 0; q < nval; q++) out[g + q] = f4c(v, q);
         }
-    };
-    auto issue_h = [&](int k) {
-        const int b = k & 1;
-        for (int q = tid; q < 3 * (TY3 + 1) * (HW3 / 4); q += TX3 * TY3) {
-            const int comp = q / ((TY3 + 1) * (HW3 / 4));
-            const int r = q % ((TY3 + 1) * (HW3 / 4));
-            const int qy = r / (HW3 / 4), v = r % (HW3 / 4);
-            const int jj = j0 - 1 + qy;
-            const bool in = jj <= S.ny && k < S.nz;
-            cpa16(&Hb[b][comp][qy][4 * v], B.in[G_HX + comp] + (in ? sidx(jj, k) + 4 * v : 0), in);
-        }
-    };
-
-    // this thread's H cells (tile + low halo, (TY3+1) x (TX3+1) = 297 of them)
-    // and their x/y CPML profiles, fixed for the whole march
-    constexpr int NHC = ((TY3 + 1) * (TX3 + 1) + TX3 * TY3 - 1) / (TX3 * TY3);
-    int hq[NHC], hqy[NHC], hqx[NHC];
-    float hbx[NHC], hcx[NHC], hby[NHC], hcy[NHC];
-#pragma unroll
-    for (int u = 0; u < NHC; u++) {
-        hq[u] = tid + u * TX3 * TY3;
-        hqy[u] = hq[u] / (TX3 + 1);
-        hqx[u] = hq[u] % (TX3 + 1);
-        const int ii = i0 - 1 + hqx[u], jj = j0 - 1 + hqy[u];
-        const bool ok = hq[u] < (TY3 + 1) * (TX3 + 1) && ii >= 0 && jj >= 0 && ii < S.nx && jj < S.ny;
-        hbx[u] = ok && pml ? pr.bHx(ii + PX3) : 0.f;
-        hcx[u] = ok && pml ? pr.cHx(ii + PX3) : 0.f;
-        hby[u] = ok && pml ? pr.bHy(jj + 1) : 0.f;
-        hcy[u] = ok && pml ? pr.cHy(jj + 1) : 0.f;
     }
-    const float ebx = own && pml ? pr.bEx(i + PX3) : 0.f, ecx = own && pml ? pr.cEx(i + PX3) : 0.f;
-    const float eby = own && pml ? pr.bEy(j + 1) : 0.f, ecy = own && pml ? pr.cEy(j + 1) : 0.f;
+    return make_float4(d.x + v.x, d.y + v.y, d.z + v.z, d.w + v.w);
+}
+
+__device__ __forceinline__ float4 psi4(const float* in, float* out, size_t g, float4 b, float4 c, float4 d, bool store,
+                                       int nval, unsigned upd) {
+    return psi4p(*reinterpret_cast<const float4*>(in + g), out, g, b, c, d, store, nval, upd);
+}
+
+__global__ void __launch_bounds__(NW3 * 32, 2) k_yee3d_fused(Dev3 S, Bufs3 B, int segz) {
+    extern __shared__ float4 sm4[];
+    float4* Eb = sm4;                                                    // [NE3][3][ER3][EW4]
+    float* Ht = reinterpret_cast<float*>(sm4 + NE3 * 3 * ER3 * EW4);     // [NW3][2][TXC]
+    float4* coef_s = reinterpret_cast<float4*>(Ht + NW3 * 2 * TXC);      // [256]
+    float* Xp = reinterpret_cast<float*>(coef_s + 256);                  // [4][TXC]: bHx cHx bEx cEx
+    const float* Ef = reinterpret_cast<const float*>(Eb);
+
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, tid = threadIdx.x;
+    const int x0 = blockIdx.x * TXC, j0 = blockIdx.y * TYR;
+    const int kA = blockIdx.z * segz, kB = min(kA + segz, S.nz);
+    const int pitch = S.pitch, rows = S.rows;
+    const int j = j0 - 1 + w;                  // this warp's row
+    const int x = x0 + 4 * lane;               // first of this lane's cells
+    const bool own_row = w >= 1 && j < S.ny;
+    const P3 pr{S.prof, pitch, rows, S.planes};
+    const int npml = S.has_pml;
+    const bool pml = npml > 0;
+    for (int q = tid; q < 256; q += NW3 * 32) coef_s[q] = S.coef[q];
+    if (pml)
+        for (int q = tid; q < 4 * TXC; q += NW3 * 32) {
+            const int a = q / TXC, xc = x0 + q % TXC;
+            const bool in = xc < S.nx;
+            Xp[q] = !in ? 0.f : (a == 0 ? pr.bHx(xc + PX3) : a == 1 ? pr.cHx(xc + PX3) : a == 2 ? pr.bEx(xc + PX3) : pr.cEx(xc + PX3));
+        }
+
+    // CPML reach (conservative; the profiles decide cell by cell)
+    const bool lane_px = pml && (x - 1 < npml + 1 || x + 4 >= S.nx - npml - 1);
+    const bool row_py = pml && (j < npml + 1 || j >= S.ny - npml - 1);
+    const bool jin = j >= 0 && j < S.ny;
+    const float hby = row_py && jin ? pr.bHy(j + 1) : 0.f, hcy = row_py && jin ? pr.cHy(j + 1) : 0.f;
+    const float eby = row_py && jin ? pr.bEy(j + 1) : 0.f, ecy = row_py && jin ? pr.cEy(j + 1) : 0.f;
+    // lane 0's left-halo cell x0 - 1
+    const bool halo_x = lane == 0 && x0 > 0;
+
+    // E(p) rows j0-1 .. j0+TYR into ring slot p % NE3; rows past the padded array
+    // and planes past nz read as zeros
+    auto issue_e = [&](int p) {
+        float4* dst = Eb + (size_t)(p % NE3) * 3 * ER3 * EW4;
+        for (int q = tid; q < 3 * ER3 * EW4; q += NW3 * 32) {
+            const int comp = q / (ER3 * EW4), r = (q / EW4) % ER3, v = q % EW4;
+            const int jj = j0 - 1 + r;
+            const bool in = jj <= S.ny && p <= S.nz;
+            const size_t g = ((size_t)(p + 1) * rows + (jj + 1)) * pitch + x0 + 4 * v;   // cell x0 - 4 + 4v
+            cpa16(dst + q, B.in[G_EX + comp] + (in ? g : 0), in);
+        }
+    };
+    auto eidx = [&](int slot, int comp, int r) { return ((slot * 3 + comp) * ER3 + r) * EW4; };
+
+    // this lane's cells in plane p: storage index of cell x
+    auto gidx = [&](int p) { return ((size_t)(p + 1) * rows + (j + 1)) * pitch + x + PX3; };
+    const bool hrow_ok = j >= -1 && j <= S.ny;
+    float4 hxo, hyo, hzo, hxn, hyn, hzn;   // H_old of plane k (o) and k + 1 (n)
+    float hym_o = 0.f, hzm_o = 0.f, hym_n = 0.f, hzm_n = 0.f;   // lane 0: H_old at x0 - 1
+    uint32_t mo = 0, mn = 0;               // material bytes of the 4 cells
+    auto load_plane = [&](int p, float4& hx, float4& hy, float4& hz, float& hym, float& hzm, uint32_t& m) {
+        hx = hy = hz = make_float4(0.f, 0.f, 0.f, 0.f);
+        hym = hzm = 0.f;
+        m = 0;
+        if (!hrow_ok || p >= S.nz) return;
+        const size_t g = gidx(p);
+        hx = *reinterpret_cast<const float4*>(B.in[G_HX] + g);
+        hy = *reinterpret_cast<const float4*>(B.in[G_HY] + g);
+        hz = *reinterpret_cast<const float4*>(B.in[G_HZ] + g);
+        if (own_row) m = *reinterpret_cast<const uint32_t*>(S.mat + g);
+        if (halo_x) {
+            hym = B.in[G_HY][g - 1];
+            hzm = B.in[G_HZ][g - 1];
+        }
+    };
 
     const int kf = kA > 0 ? kA - 1 : 0;
     issue_e(kf);
-    issue_e(kf + 1);
-    issue_h(kf);
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    float hx_prev = 0.f, hy_prev = 0.f;   // H(k-1) of this thread's column (zero pad below k = 0)
-    const size_t own_row = ((size_t)(j + 1)) * S.pitch + (i + PX3);
-    uint8_t m_next = own ? S.mat[(size_t)((kf < kA ? kA : kf) + 1) * plane + own_row] : 0;
-    for (int k = kf; k < kB; k++) {
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        __syncthreads();
-        // prefetch plane k+1's inputs while plane k computes (their slots held plane k-1)
-        if (k + 1 < kB) {
-            issue_e(k + 2);
-            issue_h(k + 1);
-        }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-        const uint8_t m_cur = m_next;
-        if (own && k + 1 < kB) m_next = S.mat[(size_t)(k + 2) * plane + own_row];
-        const int ec = k % 3, en = (k + 1) % 3, hb = k & 1;
-        const float bz = pml ? pr.bHz(k + 1) : 0.f, cz = pml ? pr.cHz(k + 1) : 0.f;
-        // ---- layer 1 on the tile and its low halo ----
 #pragma unroll
-        for (int u = 0; u < NHC; u++) {
-            if (hq[u] >= (TY3 + 1) * (TX3 + 1)) break;
-            const int qy = hqy[u], qx = hqx[u];
-            const int ii = i0 - 1 + qx, jj = j0 - 1 + qy;
-            float hx = 0.f, hy = 0.f, hz = 0.f;
-            if (ii >= 0 && jj >= 0 && ii < S.nx && jj < S.ny) {
-                const int sx = qx + 3;   // staged column of cell ii
-                const size_t c = (size_t)(k + 1) * plane + (size_t)(jj + 1) * S.pitch + (ii + PX3);
-                const float exc = Eb[ec][0][qy][sx], eyc = Eb[ec][1][qy][sx], ezc = Eb[ec][2][qy][sx];
-                float dezy = Eb[ec][2][qy + 1][sx] - ezc;
-                float deyz = Eb[en][1][qy][sx] - eyc;
-                float dexz = Eb[en][0][qy][sx] - exc;
-                float dezx = Eb[ec][2][qy][sx + 1] - ezc;
-                float deyx = Eb[ec][1][qy][sx + 1] - eyc;
-                float dexy = Eb[ec][0][qy + 1][sx] - exc;
-                const bool owned = ii >= i0 && jj >= j0 && k >= kA;   // halo and warm-up values are not stored
-                auto ps = [&](int slot, float bb, float cc, float d) {
-                    if (bb == 0.f && cc == 0.f) return d;
-                    const float vv = bb * B.in[slot][c] + cc * d;
-                    if (owned) B.out[slot][c] = vv;
-                    return d + vv;
-                };
-                if (pml) {
-                    dezy = ps(P_HXY, hby[u], hcy[u], dezy);
-                    deyz = ps(P_HXZ, bz, cz, deyz);
-                    dexz = ps(P_HYZ, bz, cz, dexz);
-                    dezx = ps(P_HYX, hbx[u], hcx[u], dezx);
-                    deyx = ps(P_HZX, hbx[u], hcx[u], deyx);
-                    dexy = ps(P_HZY, hby[u], hcy[u], dexy);
-                }
-                const int hx_ = qx + 3;
-                hx = Hb[hb][0][qy][hx_] - (S.cdy * dezy - S.cdz * deyz);
-                hy = Hb[hb][1][qy][hx_] - (S.cdz * dexz - S.cdx * dezx);
-                hz = Hb[hb][2][qy][hx_] - (S.cdx * deyx - S.cdy * dexy);
-                if (owned) {
-                    B.out[G_HX][c] = hx;
-                    B.out[G_HY][c] = hy;
-                    B.out[G_HZ][c] = hz;
+    for (int d = 0; d < D3; d++) {
+        issue_e(kf + 1 + d);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    load_plane(kf, hxo, hyo, hzo, hym_o, hzm_o, mo);
+    float4 hxp = make_float4(0.f, 0.f, 0.f, 0.f), hyp = hxp;   // H(k-1) of the lane's cells
+    // one plane; H_old and material of plane k are in the (o) registers, plane
+    // k + 1's are loaded into the (n) ones.  The loop alternates the two sets,
+    // so no register copy waits on a load that is still in flight.
+    auto step = [&](const int k, const float4& hxo, const float4& hyo, const float4& hzo, const float hym_o,
+                    const float hzm_o, const uint32_t mo, float4& hxn, float4& hyn, float4& hzn, float& hym_n,
+                    float& hzm_n, uint32_t& mn) {
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(D3 - 1) : "memory");
+        __syncthreads();
+        issue_e(k + 1 + D3);   // into the slot plane k - 1 used
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        load_plane(k + 1, hxn, hyn, hzn, hym_n, hzm_n, mn);
+        // x-slab lanes: this plane's four x-axis psi, loaded before the H update so
+        // their latency overlaps it
+        float4 pyx = make_float4(0.f, 0.f, 0.f, 0.f), pzx = pyx, peyx = pyx, pezx = pyx;
+        if (lane_px && jin) {
+            const size_t g = gidx(k);
+            pyx = *reinterpret_cast<const float4*>(B.in[P_HYX] + g);
+            pzx = *reinterpret_cast<const float4*>(B.in[P_HZX] + g);
+            if (own_row) {
+                peyx = *reinterpret_cast<const float4*>(B.in[P_EYX] + g);
+                pezx = *reinterpret_cast<const float4*>(B.in[P_EZX] + g);
+            }
+        }
+        const int sc = k % NE3, sn = (k + 1) % NE3;
+        const bool kz = pml && (k < npml + 1 || k >= S.nz - npml - 1);
+        const bool any_h = lane_px || row_py || kz;
+        const bool store = k >= kA;
+
+        // ---- layer 1: H(k) of row j ----
+        const int o = 1 + lane;   // float4 slot of the lane's cells in a staged row
+        const float4 ex = Eb[eidx(sc, 0, w) + o], ey = Eb[eidx(sc, 1, w) + o], ez = Eb[eidx(sc, 2, w) + o];
+        const float4 ezu = Eb[eidx(sc, 2, w + 1) + o], exu = Eb[eidx(sc, 0, w + 1) + o];
+        const float4 eyk = Eb[eidx(sn, 1, w) + o], exk = Eb[eidx(sn, 0, w) + o];
+        const float ezr = Ef[eidx(sc, 2, w) * 4 + 8 + 4 * lane], eyr = Ef[eidx(sc, 1, w) * 4 + 8 + 4 * lane];
+        float4 dezy = make_float4(ezu.x - ez.x, ezu.y - ez.y, ezu.z - ez.z, ezu.w - ez.w);
+        float4 deyz = make_float4(eyk.x - ey.x, eyk.y - ey.y, eyk.z - ey.z, eyk.w - ey.w);
+        float4 dexz = make_float4(exk.x - ex.x, exk.y - ex.y, exk.z - ex.z, exk.w - ex.w);
+        float4 dezx = make_float4(ez.y - ez.x, ez.z - ez.y, ez.w - ez.z, ezr - ez.w);
+        float4 deyx = make_float4(ey.y - ey.x, ey.z - ey.y, ey.w - ey.z, eyr - ey.w);
+        float4 dexy = make_float4(exu.x - ex.x, exu.y - ex.y, exu.z - ex.z, exu.w - ex.w);
+        const int nval = S.nx - x;   // cells of the lane inside the grid (>= 4: all)
+        if (any_h && jin) {
+            // psi <- b psi + c dF for the lane's four cells, one group per slab axis
+            const size_t g = gidx(k);
+            const bool st = store && own_row;
+            if (row_py) {
+                const float4 b4 = make_float4(hby, hby, hby, hby), c4 = make_float4(hcy, hcy, hcy, hcy);
+                dezy = psi4(B.in[P_HXY], B.out[P_HXY], g, b4, c4, dezy, st, nval, 15u);
+                dexy = psi4(B.in[P_HZY], B.out[P_HZY], g, b4, c4, dexy, st, nval, 15u);
+            }
+            if (kz) {
+                const float bz = pr.bHz(k + 1), cz = pr.cHz(k + 1);
+                const float4 b4 = make_float4(bz, bz, bz, bz), c4 = make_float4(cz, cz, cz, cz);
+                deyz = psi4(B.in[P_HXZ], B.out[P_HXZ], g, b4, c4, deyz, st, nval, 15u);
+                dexz = psi4(B.in[P_HYZ], B.out[P_HYZ], g, b4, c4, dexz, st, nval, 15u);
+            }
+            if (lane_px) {
+                const float4 b4 = *reinterpret_cast<const float4*>(Xp + 0 * TXC + 4 * lane);
+                const float4 c4 = *reinterpret_cast<const float4*>(Xp + 1 * TXC + 4 * lane);
+                dezx = psi4p(pyx, B.out[P_HYX], g, b4, c4, dezx, st, nval, 15u);
+                deyx = psi4p(pzx, B.out[P_HZX], g, b4, c4, deyx, st, nval, 15u);
+            }
+        }
+        const float cdx = S.cdx, cdy = S.cdy, cdz = S.cdz;
+        float4 hx, hy, hz;
+        hx.x = hxo.x - (cdy * dezy.x - cdz * deyz.x); hx.y = hxo.y - (cdy * dezy.y - cdz * deyz.y);
+        hx.z = hxo.z - (cdy * dezy.z - cdz * deyz.z); hx.w = hxo.w - (cdy * dezy.w - cdz * deyz.w);
+        hy.x = hyo.x - (cdz * dexz.x - cdx * dezx.x); hy.y = hyo.y - (cdz * dexz.y - cdx * dezx.y);
+        hy.z = hyo.z - (cdz * dexz.z - cdx * dezx.z); hy.w = hyo.w - (cdz * dexz.w - cdx * dezx.w);
+        hz.x = hzo.x - (cdx * deyx.x - cdy * dexy.x); hz.y = hzo.y - (cdx * deyx.y - cdy * dexy.y);
+        hz.z = hzo.z - (cdx * deyx.z - cdy * dexy.z); hz.w = hzo.w - (cdx * deyx.w - cdy * dexy.w);
+        // lane 0: Hy, Hz of the cell left of the tile (x0 - 1)
+        float hym = 0.f, hzm = 0.f;
+        if (halo_x && jin) {
+            const int cl = 3;   // staged column of cell x0 - 1
+            const float exm = Ef[eidx(sc, 0, w) * 4 + cl], eym = Ef[eidx(sc, 1, w) * 4 + cl];
+            const float ezm = Ef[eidx(sc, 2, w) * 4 + cl];
+            float dexz_m = Ef[eidx(sn, 0, w) * 4 + cl] - exm;
+            float dezx_m = ez.x - ezm, deyx_m = ey.x - eym;
+            float dexy_m = Ef[eidx(sc, 0, w + 1) * 4 + cl] - exm;
+            if (pml) {
+                const size_t gm = gidx(k) - 1;
+                const float bz = kz ? pr.bHz(k + 1) : 0.f, cz = kz ? pr.cHz(k + 1) : 0.f;
+                dexz_m = psi_upd(B.in[P_HYZ], nullptr, gm, bz, cz, dexz_m, false);
+                const float mbx = pr.bHx(x0 - 1 + PX3), mcx = pr.cHx(x0 - 1 + PX3);
+                dezx_m = psi_upd(B.in[P_HYX], nullptr, gm, mbx, mcx, dezx_m, false);
+                deyx_m = psi_upd(B.in[P_HZX], nullptr, gm, mbx, mcx, deyx_m, false);
+                dexy_m = psi_upd(B.in[P_HZY], nullptr, gm, hby, hcy, dexy_m, false);
+            }
+            hym = hym_o - (cdz * dexz_m - cdx * dezx_m);
+            hzm = hzm_o - (cdx * deyx_m - cdy * dexy_m);
+        }
+        // the row's Hx, Hz for the row above; the owned rows' H is stored
+        *reinterpret_cast<float4*>(Ht + (w * 2 + 0) * TXC + 4 * lane) = hx;
+        *reinterpret_cast<float4*>(Ht + (w * 2 + 1) * TXC + 4 * lane) = hz;
+        if (store && own_row) {
+            const size_t g = gidx(k);
+            if (x + 3 < S.nx) {
+                *reinterpret_cast<float4*>(B.out[G_HX] + g) = hx;
+                *reinterpret_cast<float4*>(B.out[G_HY] + g) = hy;
+                *reinterpret_cast<float4*>(B.out[G_HZ] + g) = hz;
+            } else {
+                for (int q = 0; q < 4 && x + q < S.nx; q++) {
+                    B.out[G_HX][g + q] = f4c(hx, q);
+                    B.out[G_HY][g + q] = f4c(hy, q);
+                    B.out[G_HZ][g + q] = f4c(hz, q);
                 }
             }
-            Ht[0][qy][qx] = hx;
-            Ht[1][qy][qx] = hy;
-            Ht[2][qy][qx] = hz;
         }
         __syncthreads();
-        // ---- layer 2 on the tile ----
-        const float hxc = Ht[0][ty + 1][tx + 1], hyc = Ht[1][ty + 1][tx + 1], hzc = Ht[2][ty + 1][tx + 1];
-        if (own && k >= kA) {
-            const size_t c = (size_t)(k + 1) * plane + own_row;
-            const float4 co = S.coef[m_cur];
-            const float bez = pml ? pr.bEz(k + 1) : 0.f, cez = pml ? pr.cEz(k + 1) : 0.f;
-            float dhzy = hzc - Ht[2][ty][tx + 1], dhyz = hyc - hy_prev;
-            float dhxz = hxc - hx_prev, dhzx = hzc - Ht[2][ty + 1][tx];
-            float dhyx = hyc - Ht[1][ty + 1][tx], dhxy = hxc - Ht[0][ty][tx + 1];
-            const int sx = tx + 4;
-            const float exc = Eb[ec][0][ty + 1][sx], eyc = Eb[ec][1][ty + 1][sx], ezc = Eb[ec][2][ty + 1][sx];
-            auto ps = [&](int slot, float bb, float cc, float d) {
-                if (bb == 0.f && cc == 0.f) return d;
-                const float vv = bb * B.in[slot][c] + cc * d;
-                B.out[slot][c] = vv;
-                return d + vv;
-            };
-            float ex = exc, ey = eyc, ez = ezc;
-            if (j >= 1 && k >= 1) {
-                if (pml) {
-                    dhzy = ps(P_EXY, eby, ecy, dhzy);
-                    dhyz = ps(P_EXZ, bez, cez, dhyz);
+
+        // ---- layer 2: E(k) of the owned rows ----
+        const float hyl0 = __shfl_up_sync(0xffffffffu, hy.w, 1), hzl0 = __shfl_up_sync(0xffffffffu, hz.w, 1);
+        if (w >= 1) {
+            const float hyl = lane == 0 ? hym : hyl0, hzl = lane == 0 ? hzm : hzl0;
+            const float4 hxd = *reinterpret_cast<const float4*>(Ht + ((w - 1) * 2 + 0) * TXC + 4 * lane);
+            const float4 hzd = *reinterpret_cast<const float4*>(Ht + ((w - 1) * 2 + 1) * TXC + 4 * lane);
+            float4 dhzy = make_float4(hz.x - hzd.x, hz.y - hzd.y, hz.z - hzd.z, hz.w - hzd.w);
+            float4 dhyz = make_float4(hy.x - hyp.x, hy.y - hyp.y, hy.z - hyp.z, hy.w - hyp.w);
+            float4 dhxz = make_float4(hx.x - hxp.x, hx.y - hxp.y, hx.z - hxp.z, hx.w - hxp.w);
+            float4 dhzx = make_float4(hz.x - hzl, hz.y - hz.x, hz.z - hz.y, hz.w - hz.z);
+            float4 dhyx = make_float4(hy.x - hyl, hy.y - hy.x, hy.z - hy.y, hy.w - hy.z);
+            float4 dhxy = make_float4(hx.x - hxd.x, hx.y - hxd.y, hx.z - hxd.z, hx.w - hxd.w);
+            const bool wj = j >= 1, wk = k >= 1;   // Ex, Ez need j >= 1; Ex, Ey need k >= 1
+            const unsigned wi = x >= 1 ? 15u : 14u;   // Ey, Ez need i >= 1
+            const unsigned mex = (wj && wk) ? 15u : 0u, mey = wk ? wi : 0u, mez = wj ? wi : 0u;
+            const size_t g = gidx(k);
+            if ((lane_px || row_py || kz) && own_row) {
+                if (row_py) {
+                    const float4 b4 = make_float4(eby, eby, eby, eby), c4 = make_float4(ecy, ecy, ecy, ecy);
+                    dhzy = psi4(B.in[P_EXY], B.out[P_EXY], g, b4, c4, dhzy, store, nval, mex);
+                    dhxy = psi4(B.in[P_EZY], B.out[P_EZY], g, b4, c4, dhxy, store, nval, mez);
                 }
-                ex = co.x * exc + co.z * dhzy - co.w * dhyz;
-            }
-            if (i >= 1 && k >= 1) {
-                if (pml) {
-                    dhxz = ps(P_EYZ, bez, cez, dhxz);
-                    dhzx = ps(P_EYX, ebx, ecx, dhzx);
+                if (kz) {
+                    const float bz = pr.bEz(k + 1), cz = pr.cEz(k + 1);
+                    const float4 b4 = make_float4(bz, bz, bz, bz), c4 = make_float4(cz, cz, cz, cz);
+                    dhyz = psi4(B.in[P_EXZ], B.out[P_EXZ], g, b4, c4, dhyz, store, nval, mex);
+                    dhxz = psi4(B.in[P_EYZ], B.out[P_EYZ], g, b4, c4, dhxz, store, nval, mey);
                 }
-                ey = co.x * eyc + co.w * dhxz - co.y * dhzx;
-            }
-            if (i >= 1 && j >= 1) {
-                if (pml) {
-                    dhyx = ps(P_EZX, ebx, ecx, dhyx);
-                    dhxy = ps(P_EZY, eby, ecy, dhxy);
+                if (lane_px) {
+                    const float4 b4 = *reinterpret_cast<const float4*>(Xp + 2 * TXC + 4 * lane);
+                    const float4 c4 = *reinterpret_cast<const float4*>(Xp + 3 * TXC + 4 * lane);
+                    dhzx = psi4p(peyx, B.out[P_EYX], g, b4, c4, dhzx, store, nval, mey);
+                    dhyx = psi4p(pezx, B.out[P_EZX], g, b4, c4, dhyx, store, nval, mez);
                 }
-                ez = co.x * ezc + co.y * dhyx - co.z * dhxy;
             }
-            B.out[G_EX][c] = ex;
-            B.out[G_EY][c] = ey;
-            B.out[G_EZ][c] = ez;
+            float4 nex = ex, ney = ey, nez = ez;
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const float4 co = coef_s[(mo >> (8 * q)) & 255u];
+                if (mex & (1u << q)) f4s(nex, q, co.x * f4c(ex, q) + co.z * f4c(dhzy, q) - co.w * f4c(dhyz, q));
+                if (mey & (1u << q)) f4s(ney, q, co.x * f4c(ey, q) + co.w * f4c(dhxz, q) - co.y * f4c(dhzx, q));
+                if (mez & (1u << q)) f4s(nez, q, co.x * f4c(ez, q) + co.y * f4c(dhyx, q) - co.z * f4c(dhxy, q));
+            }
+            if (store && own_row) {
+                if (x + 3 < S.nx) {
+                    *reinterpret_cast<float4*>(B.out[G_EX] + g) = nex;
+                    *reinterpret_cast<float4*>(B.out[G_EY] + g) = ney;
+                    *reinterpret_cast<float4*>(B.out[G_EZ] + g) = nez;
+                } else {
+                    for (int q = 0; q < 4 && x + q < S.nx; q++) {
+                        B.out[G_EX][g + q] = f4c(nex, q);
+                        B.out[G_EY][g + q] = f4c(ney, q);
+                        B.out[G_EZ][g + q] = f4c(nez, q);
+                    }
+                }
+            }
         }
-        hx_prev = hxc;
-        hy_prev = hyc;
-        __syncthreads();
+        hxp = hx;
+        hyp = hy;
+    };
+    for (int k = kf; k < kB; k += 2) {
+        step(k, hxo, hyo, hzo, hym_o, hzm_o, mo, hxn, hyn, hzn, hym_n, hzm_n, mn);
+        if (k + 1 >= kB) break;
+        step(k + 1, hxn, hyn, hzn, hym_n, hzm_n, mn, hxo, hyo, hzo, hym_o, hzm_o, mo);
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
@@ -479,25 +616,31 @@ __device__ __forceinline__ void kahan3(float& s, float& c, float v) {
 // running DFT over a z plane: acc[pc][f][j][i] = (re, im, comp_re, comp_im)
 __global__ void k_dft_plane3(Dev3 S, int plane_k, int comp_mask, const double* freq, int n_freq, double dt,
                              float4* acc, long long n) {
+    // the step's twiddles dt e^{-i 2 pi f (n+1) dt}: FP64 phase, once per block
+    __shared__ float2 tw[16];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if (tid < n_freq && tid < 16) {
+        double ph = freq[tid] * dt * (double)(n + 1);
+        ph -= floor(ph);
+        double sn, cs;
+        sincospi(2.0 * ph, &sn, &cs);
+        tw[tid] = make_float2((float)cs * (float)dt, -(float)sn * (float)dt);
+    }
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= S.nx || j >= S.ny) return;
     const size_t c = ((size_t)(plane_k + 1) * S.rows + (j + 1)) * S.pitch + (i + PX3);
     const size_t plane = (size_t)S.nx * S.ny;
     const size_t cell = (size_t)j * S.nx + i;
-    const float fdt = (float)dt;
     int pc = 0;
     for (int comp = 0; comp < 3; comp++) {
         if (!(comp_mask & (1 << comp))) continue;
         const float e = S.f[comp][c];
         for (int f = 0; f < n_freq; f++) {
-            double ph = freq[f] * dt * (double)(n + 1);
-            ph -= floor(ph);
-            double sn, cs;
-            sincospi(2.0 * ph, &sn, &cs);
             float4 a = acc[((size_t)pc * n_freq + f) * plane + cell];
-            kahan3(a.x, a.z, e * ((float)cs * fdt));
-            kahan3(a.y, a.w, -e * ((float)sn * fdt));
+            kahan3(a.x, a.z, e * tw[f].x);
+            kahan3(a.y, a.w, e * tw[f].y);
             acc[((size_t)pc * n_freq + f) * plane + cell] = a;
         }
         pc++;
@@ -613,7 +756,7 @@ int fdtd_create3(const fdtd_grid* g, double dx, double dt, double courant, const
     c->stream = (cudaStream_t)stream;
     c->s3 = nullptr;
     c->cur = 0; c->t = 0; c->parity = 0; c->launches = 0;
-    c->opt_kernel = 1; c->opt_tblock = 1; c->opt_segment = 64; c->opt_warps = 8;
+    c->opt_kernel = 0; c->opt_tblock = 1; c->opt_segment = 16; c->opt_warps = 8;
     c->dirty = true;
     c->d_scenes = nullptr; c->d_tasks = nullptr; c->d_tasks_b = nullptr; c->n_tasks_b = 0; c->warps_b = 2; c->d_tasks_l = nullptr; c->n_tasks_l = 0; c->warps_l = 4;
     c->d_dft = nullptr; c->n_dft = 0; c->opt_adj_store = 1;
@@ -655,7 +798,9 @@ int fdtd_create3(const fdtd_grid* g, double dx, double dt, double courant, const
     s->d_rec = nullptr;
     s->nx = g->nx; s->ny = g->ny; s->nz = g->nz; s->npml = npml;
     s->dx = dx; s->dy = dy; s->dz = dz; s->dt = dt;
-    s->pitch = (g->nx + PX3 + 40 + 31) / 32 * 32;   // room for the last tile's 40-float staging rows
+    // room for the unfused kernels' neighbours and the fused kernel's last tile,
+    // whose staged rows reach storage column x0 + TXC + 7
+    s->pitch = (std::max(g->nx + PX3 + 40, (g->nx + TXC - 1) / TXC * TXC + 8) + 31) / 32 * 32;
     s->rows = g->ny + 2;
     s->planes = g->nz + 2;
     s->src_kind = -1; s->src_i = s->src_j = s->src_k = -1; s->src_comp = G_EZ; s->src_param = 0; s->src_cap = 0;
@@ -787,8 +932,8 @@ int fdtd_add_dft_plane3(fdtd_ctx* c, int k, int comp_mask, const double* freqs, 
     Scene3* s = S3(c);
     if (!s) return fail3(c, FDTD_ESTATE, "no 3D scene");
     if (c->t != 0) return fail3(c, FDTD_ESTATE, "monitors must be added before the first step");
-    if (k < 0 || k >= s->nz || (comp_mask & ~7) || !comp_mask || !freqs || n_freq < 1)
-        return fail3(c, FDTD_EINVAL, "plane monitor: k in 0..nz-1, comp_mask of Ex|Ey|Ez bits, frequencies");
+    if (k < 0 || k >= s->nz || (comp_mask & ~7) || !comp_mask || !freqs || n_freq < 1 || n_freq > 16)
+        return fail3(c, FDTD_EINVAL, "plane monitor: k in 0..nz-1, comp_mask of Ex|Ey|Ez bits, 1..16 frequencies");
     int ncomp = 0;
     for (int q = 0; q < 3; q++) ncomp += (comp_mask >> q) & 1;
     DftMon m;
@@ -819,7 +964,12 @@ int fdtd_step3(fdtd_ctx* c, int64_t n_steps) {
     const dim3 grp((s->nx + 31) / 32, (s->ny + 7) / 8, 1);
     const int si = s->src_kind >= 0 ? s->src_i : -1;
     const int segz = std::max(1, c->opt_segment);
-    const dim3 gfz((s->nx + TX3 - 1) / TX3, (s->ny + TY3 - 1) / TY3, (s->nz + segz - 1) / segz);
+    const dim3 gfz((s->nx + TXC - 1) / TXC, (s->ny + TYR - 1) / TYR, (s->nz + segz - 1) / segz);
+    const size_t smem3 = fused3_smem();
+    if (c->opt_kernel != 1) {
+        cudaError_t ea = ensure_dyn_smem((const void*)k_yee3d_fused, smem3);
+        if (ea != cudaSuccess) return fail3(c, FDTD_ECUDA, "fused 3D kernel: %s", cudaGetErrorString(ea));
+    }
     for (int64_t q = 0; q < n_steps; q++) {
         const long long n = c->t + q;
         if (c->opt_kernel == 1) {
@@ -832,7 +982,7 @@ int fdtd_step3(fdtd_ctx* c, int64_t n_steps) {
                 b.in[w] = s->f[w];
                 b.out[w] = s->g[w];
             }
-            k_yee3d_fused<<<gfz, dim3(TX3, TY3), 0, c->stream>>>(d, b, segz);
+            k_yee3d_fused<<<gfz, NW3 * 32, smem3, c->stream>>>(d, b, segz);
             c->launches++;
             for (int w = 0; w < G_COUNT; w++) std::swap(s->f[w], s->g[w]);
             d = dev_of(s);

@@ -71,10 +71,10 @@ def test_3d_cavity_mode_closed_form():
     sim.close()
 
 
-@pytest.mark.parametrize("kernel,segz", [(0, 64), (0, 7), (1, 64)])
-def test_3d_boxes_cpml_probes_plane_dft(kernel, segz):
+@pytest.mark.parametrize("kernel,segz,side", [(0, 64, 40), (0, 7, 40), (1, 64, 40), (0, 5, 37)])
+def test_3d_boxes_cpml_probes_plane_dft(kernel, segz, side):
     from paper_2405_00814_gb300 import fdtd
-    sc = scenes.box_scene(side=40, nsteps=150, npml=6, n_boxes=10)
+    sc = scenes.box_scene(side=side, nsteps=150, npml=6, n_boxes=10)
     sc.source = scenes.Source(20, 20, 20, component="ez", kind="ricker", params=(40e9,))
     sc.dft_plane_k = 28
     sc.freqs = np.array([10e9, 20e9, 30e9])
@@ -96,7 +96,8 @@ def test_3d_boxes_cpml_probes_plane_dft(kernel, segz):
     sim.close()
 
 
-def test_3d_full_size_512_light_cone():
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_3d_full_size_512_light_cone(kernel):
     """The 512^3 box workload (10-cell CPML, 64 boxes, Gaussian Ez dipole) as the
     benchmark runs it, 110 steps: every field equals the oracle on the crop that
     holds the dipole's dependency cone and is exactly zero outside it."""
@@ -104,7 +105,7 @@ def test_3d_full_size_512_light_cone():
     sc = scenes.box_scene()
     n = 110
     sim = fdtd.from_scene(sc)
-    sim.set_option("kernel", 1)
+    sim.set_option("kernel", kernel)
     sim.step(n)
     si, sj, sk = sc.source.i, sc.source.j, sc.source.k
     h = n + 2
