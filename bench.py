@@ -157,7 +157,8 @@ def paper_sweep(stream, tune, sides=(250, 1000, 2000, 3000, 4000, 5000, 6400), n
     """The paper's timing workload (Sec. IV, Fig. 5): free space with a 16-cell
     absorbing boundary, square grids of the listed sides, 1024 steps, 5 runs per
     side; mean and 95% confidence half-width (Student t, 4 dof) of the device
-    time per solve, and cell-updates/s."""
+    time per solve, and cell-updates/s.  tune None: the library's autotuner
+    picks the kernel options per side."""
     import torch
     from paper_2405_00814_gb300 import fdtd, scenes
     t95 = 2.776
@@ -165,8 +166,12 @@ def paper_sweep(stream, tune, sides=(250, 1000, 2000, 3000, 4000, 5000, 6400), n
     for side in sides:
         sc = scenes.free_space(side, nsteps=nsteps)
         sim = fdtd.from_scene(sc, stream=stream)
-        for k, v in tune.items():
-            sim.set_option(k, v)
+        if tune is None:
+            tune_used = sim.autotune(trial_steps=16)["options"]
+        else:
+            tune_used = dict(tune)
+            for k, v in tune.items():
+                sim.set_option(k, v)
         sim.step(nsteps)            # warm-up solve
         ms = []
         for _ in range(runs):
@@ -181,7 +186,7 @@ def paper_sweep(stream, tune, sides=(250, 1000, 2000, 3000, 4000, 5000, 6400), n
         mean = sum(ms) / runs
         sd = (sum((x - mean) ** 2 for x in ms) / (runs - 1)) ** 0.5
         out[str(side)] = {"ms_mean": mean, "ms_ci95": t95 * sd / runs ** 0.5,
-                          "cell_updates_per_s": sc.cells * nsteps / (mean / 1e3)}
+                          "cell_updates_per_s": sc.cells * nsteps / (mean / 1e3), "options": tune_used}
     return {"workload": "paper_sweep_free_space_cpml16_1024steps", "runs": runs, "sides": out,
             "timing": "CUDA events around fdtd_step per solve after one warm-up solve"}
 
@@ -386,7 +391,7 @@ def main():
         elif args.workload == "edgelist":
             res = edgelist_throughput(stream, side=args.size if args.size != 4096 else 2048, nsteps=args.nsteps or 200)
         else:
-            res = paper_sweep(stream, {"tblock": 4, "segment": 24, "warps": 8})
+            res = paper_sweep(stream, None)
         if rank == 0:
             print(json.dumps(res), flush=True)
         return
@@ -394,15 +399,22 @@ def main():
     sc = scenes.ellipse_scene(side=args.size)
     nsteps = args.nsteps or sc.nsteps
     sim = fdtd.from_scene(sc, stream=stream)
-    tune = {"tblock": 4, "segment": 24, "warps": 8}
-    for k in ("tblock", "segment", "warps"):
-        if getattr(args, k) is not None:
-            tune[k] = getattr(args, k)
-    if args.kernel is None:
-        args.kernel = 0
-    sim.set_option("kernel", args.kernel)
-    for k, v in tune.items():
-        sim.set_option(k, v)
+    # kernel options: the library's autotuner on this scene, unless given
+    manual = any(getattr(args, k) is not None for k in ("tblock", "segment", "warps", "kernel"))
+    if manual:
+        tune = {"tblock": 4, "segment": 24, "warps": 8}
+        for k in ("tblock", "segment", "warps"):
+            if getattr(args, k) is not None:
+                tune[k] = getattr(args, k)
+        if args.kernel is None:
+            args.kernel = 0
+        sim.set_option("kernel", args.kernel)
+        for k, v in tune.items():
+            sim.set_option(k, v)
+    else:
+        sim.autotune(trial_steps=32)
+        args.kernel = sim.get_option("kernel")
+        tune = {k: sim.get_option(k) for k in ("tblock", "segment", "warps")}
     if args.graph:
         sim.set_option("graph", 1)
 
@@ -445,7 +457,7 @@ def main():
     value = cell_updates * args.steps * world / (ms_total / 1e3)
 
     # dominant kernel: the fused stream, one launch per tblock steps
-    T = tune["tblock"] if args.kernel == 0 else 1
+    T = tune["tblock"] if args.kernel in (0, 2) else 1
     fused_launches = args.steps * math.ceil(nsteps / T)
     avg_launch_s = (ms_step_only / 1e3) / fused_launches
     peak, peak_kind = _peaks()
@@ -455,7 +467,9 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind,
                 "kernel": (f"k_tmz_interior<{T}> + k_tmz_fused<{T},1> (one T-step block, run concurrently)"
-                           if args.kernel == 0 else "k_tmz_h + k_tmz_e"),
+                           if args.kernel == 0 else
+                           f"k_tmz_persistent<{T}> (one T-step block between grid barriers)" if args.kernel == 2
+                           else "k_tmz_h + k_tmz_e"),
                 "unit_bytes": "25 B per grid cell per launch (each launch advances every cell T steps)"}
     hbm_frac_cu = value / world * BYTES_PER_CU / (peak * 1e9)
 
@@ -465,6 +479,7 @@ def main():
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": workload, "cells": sc.cells, "leapfrog_steps_per_bench_step": nsteps,
                       "tblock": T, "segment": tune["segment"], "warps_per_cta": tune["warps"],
+                      "kernel_options": "manual" if manual else "fdtd_autotune on this scene",
                       "l2": "inputs larger than L2 (fields 2x3x70 MB + material 17 MB)",
                       "parallelism": "replicas" if world > 1 else "single"},
            "roofline": roofline,
@@ -483,6 +498,7 @@ def main():
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             s2 = fdtd.from_scene(sc, stream=stream)
+            s2.set_option("kernel", args.kernel)
             for k, v in tune.items():
                 s2.set_option(k, v)
             s2.step(nsteps)
@@ -498,7 +514,7 @@ def main():
         out["adjoint"] = adjoint_ratio(stream)
         out["batch"] = batch_throughput(stream)
         out["yee3d"] = yee3d_throughput(stream)
-        out["paper_sweep"] = paper_sweep(stream, tune)
+        out["paper_sweep"] = paper_sweep(stream, None)
         out["edgelist"] = edgelist_throughput(stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sc, args.cpu_budget)

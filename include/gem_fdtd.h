@@ -216,10 +216,12 @@ int fdtd_load_state(fdtd_ctx* ctx, const void* buf, size_t bytes);
  * state of an incomplete step sequence. */
 int fdtd_sync(fdtd_ctx* ctx);
 
-/* Batched scenes (Sec. V-A runs many simulations of varying size): time each
- * candidate setting of (kernel 0 or 2, T 2..4, segment 16..48, warps 4 or 8) for
- * trial_steps steps on the current scenes and keep the fastest.  Leaves the
- * context reset (t = 0, zero fields).  *best_ms gets the best time per step. */
+/* Pick the 2D kernel options for the current scenes (one large scene, or a
+ * batch: Sec. V-A runs many simulations of varying size): time every candidate
+ * of (kernel 0: T 2..4, segment 16..96 in steps of 8, warps 4 or 8; kernel 2:
+ * T 2..4, segment 16, 24, 32 or 48) for trial_steps steps, time the four
+ * fastest twice more for 4 x trial_steps, and keep the best.  Leaves the context
+ * reset (t = 0, zero fields).  *best_ms gets the best time per step. */
 int fdtd_autotune(fdtd_ctx* ctx, int trial_steps, double* best_ms);
 
 /* Returns FDTD_EUNSTABLE if any field of any scene is not finite. Synchronises. */

@@ -984,8 +984,10 @@ int fdtd_autotune(fdtd_ctx* c, int trial_steps, double* best_ms) {
     if (c->adj) return fail(c, FDTD_EINVAL, "disable checkpointing before autotuning");
     struct Cand { int kernel, T, seg, warps; };
     std::vector<Cand> cand;
+    // the segment height sets how many CTAs a block launches, so the sweep is
+    // fine-grained: a list that fills whole waves of the 152 SMs wins
     for (int T = 2; T <= MAX_TB; T++)
-        for (int seg : {16, 24, 32, 48})
+        for (int seg = 16; seg <= 96; seg += 8)
             for (int w : {4, 8}) cand.push_back({0, T, seg, w});
     for (int T = 2; T <= MAX_TB; T++)
         for (int seg : {16, 24, 32, 48}) cand.push_back({2, T, seg, 8});
@@ -997,19 +999,36 @@ int fdtd_autotune(fdtd_ctx* c, int trial_steps, double* best_ms) {
     double best = 1e30;
     Cand win = {c->opt_kernel, c->opt_tblock, c->opt_segment, c->opt_warps};
     int rc = FDTD_OK;
-    for (const Cand& k : cand) {
+    auto time_of = [&](const Cand& k, int steps, double* per) {
         c->opt_kernel = k.kernel; c->opt_tblock = k.T; c->opt_segment = k.seg; c->opt_warps = k.warps;
         c->dirty = true;
-        if ((rc = fdtd_reset(c))) break;
-        if ((rc = fdtd_step(c, k.T))) break;   // warm-up (and build) outside the timing
+        int r = fdtd_reset(c);
+        if (!r) r = fdtd_step(c, k.T);   // warm-up (and build) outside the timing
+        if (r) return r;
         cudaEventRecord(e0, c->stream);
-        if ((rc = fdtd_step(c, trial_steps))) break;
+        if ((r = fdtd_step(c, steps))) return r;
         cudaEventRecord(e1, c->stream);
-        if ((rc = fdtd_sync(c))) break;
+        if ((r = fdtd_sync(c))) return r;
         float ms = 0;
         cudaEventElapsedTime(&ms, e0, e1);
-        const double per = ms / trial_steps;
-        if (per < best) {
+        *per = ms / steps;
+        return FDTD_OK;
+    };
+    // coarse pass over every candidate, then the four fastest again, longer
+    std::vector<std::pair<double, int>> coarse;
+    for (size_t q = 0; q < cand.size() && rc == FDTD_OK; q++) {
+        double per = 0;
+        rc = time_of(cand[q], trial_steps, &per);
+        coarse.push_back({per, (int)q});
+    }
+    std::sort(coarse.begin(), coarse.end());
+    for (size_t q = 0; q < coarse.size() && q < 4 && rc == FDTD_OK; q++) {
+        const Cand& k = cand[coarse[q].second];
+        double per = 0, per2 = 0;
+        rc = time_of(k, 4 * trial_steps, &per);
+        if (rc == FDTD_OK) rc = time_of(k, 4 * trial_steps, &per2);
+        per = std::min(per, per2);
+        if (rc == FDTD_OK && per < best) {
             best = per;
             win = k;
         }
