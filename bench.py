@@ -353,7 +353,8 @@ def main():
     ap.add_argument("--nsteps", type=int, default=None, help="leapfrog steps per solve (default: the workload's 4000)")
     ap.add_argument("--size", type=int, default=4096, help="grid side (profiling runs use smaller sides)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--graph", action="store_true", help="replay each solve from a recorded CUDA graph")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch every block from the host instead of replaying each solve from a CUDA graph")
     ap.add_argument("--workload", default="main", choices=["main", "adjoint", "batch", "yee3d", "sweep", "edgelist"],
                     help="main: the JSON line of record; the others time one secondary workload alone "
                          "(for profiling; --nsteps and, for yee3d, --size, --kernel and --segment apply)")
@@ -415,7 +416,10 @@ def main():
         sim.autotune(trial_steps=32)
         args.kernel = sim.get_option("kernel")
         tune = {k: sim.get_option(k) for k in ("tblock", "segment", "warps")}
-    if args.graph:
+    # each solve (reset + n steps from t = 0) is recorded once into a CUDA graph
+    # and replayed (FDTD_OPT_GRAPH); the warm-up solves record it
+    graph = not args.no_graph and args.kernel != 1
+    if graph:
         sim.set_option("graph", 1)
 
     def solve():
@@ -480,6 +484,7 @@ def main():
            "config": {"workload": workload, "cells": sc.cells, "leapfrog_steps_per_bench_step": nsteps,
                       "tblock": T, "segment": tune["segment"], "warps_per_cta": tune["warps"],
                       "kernel_options": "manual" if manual else "fdtd_autotune on this scene",
+                      "cuda_graph": graph,
                       "l2": "inputs larger than L2 (fields 2x3x70 MB + material 17 MB)",
                       "parallelism": "replicas" if world > 1 else "single"},
            "roofline": roofline,
