@@ -322,6 +322,134 @@ class TMz:
 
 
 # ---------------------------------------------------------------------------------
+# 2D TMz with the paper's split-field PML (split_pml.c)
+# ---------------------------------------------------------------------------------
+
+class _P2S(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("dx", C.c_double), ("dy", C.c_double),
+                ("dt", C.c_double), ("eps_cell", _dp), ("sig_cell", _dp), ("sxe", _dp), ("sxh", _dp),
+                ("sye", _dp), ("syh", _dp), ("src_i", C.c_int), ("src_j", C.c_int), ("src", _dp),
+                ("src_len", C.c_int64)]
+
+
+class _S2S(C.Structure):
+    _fields_ = [(n, _dp) for n in ("ezx", "ezy", "hx", "hy")]
+
+
+def split_axis(n, npml, delta, m=3.0):
+    """Berenger layer conductivity (S/m) at the E nodes and H nodes of one axis."""
+    sE = np.zeros(n)
+    sH = np.zeros(n)
+    lib().or_split_axis(int(n), int(npml), C.c_double(delta), C.c_double(m), _p(sE), _p(sH))
+    return sE, sH
+
+
+class TMzSplit:
+    """FP64 2D TMz run with the paper's split-field PML (Berenger, Sec. II-C):
+    the scene's npml cells on every side form the graded layer.  State: ezx,
+    ezy, hx, hy; self.ez() is their Ez = Ezx + Ezy."""
+
+    def __init__(self, scene, *, nsteps_src=None, eps_cell=None, sigma_cell=None, m=3.0):
+        self.nx, self.ny, self.dx, self.dy, self.dt = scene.nx, scene.ny, scene.dx, scene.dy, scene.dt
+        self.npml = scene.npml
+        if eps_cell is None:
+            eps_cell = scene.eps_r[scene.mat].astype(np.float64)
+            if scene.design is not None:
+                i0, j0, w, h = scene.design
+                eps_cell[j0:j0 + h, i0:i0 + w] = scene.design_eps
+        if sigma_cell is None:
+            sigma_cell = scene.sigma[scene.mat].astype(np.float64)
+        self.eps_cell = np.ascontiguousarray(eps_cell, np.float64)
+        self.sigma_cell = np.ascontiguousarray(sigma_cell, np.float64)
+        self.sxe, self.sxh = split_axis(self.nx, self.npml, self.dx, m)
+        self.sye, self.syh = split_axis(self.ny, self.npml, self.dy, m)
+        self.state = {k: np.zeros((self.ny, self.nx), np.float64) for k in ("ezx", "ezy", "hx", "hy")}
+        self.source = scene.source
+        self.src = source_samples(scene.source, self.dt, nsteps_src or scene.nsteps) if scene.source else None
+        self.n = 0
+        p = _P2S()
+        p.nx, p.ny, p.dx, p.dy, p.dt = self.nx, self.ny, self.dx, self.dy, self.dt
+        p.eps_cell, p.sig_cell = _p(self.eps_cell), _p(self.sigma_cell)
+        p.sxe, p.sxh, p.sye, p.syh = _p(self.sxe), _p(self.sxh), _p(self.sye), _p(self.syh)
+        if self.src is not None:
+            p.src_i, p.src_j, p.src, p.src_len = self.source.i, self.source.j, _p(self.src), len(self.src)
+        else:
+            p.src_i, p.src_j, p.src, p.src_len = -1, -1, None, 0
+        self._p = p
+        self._bind()
+
+    def _bind(self):
+        s = _S2S()
+        for k in ("ezx", "ezy", "hx", "hy"):
+            setattr(s, k, _p(self.state[k]))
+        self._s = s
+
+    def ez(self):
+        return self.state["ezx"] + self.state["ezy"]
+
+    def run(self, nsteps, samples=None, dft_cells=None, freqs=None):
+        """As TMz.run; samples and the DFT see Ez = Ezx + Ezy."""
+        m = _M2()
+        keep = []
+        out = {}
+        if samples is not None and len(samples):
+            si = np.array([q[0] for q in samples], np.int32)
+            sj = np.array([q[1] for q in samples], np.int32)
+            sc = np.array([_COMP2[q[2]] if isinstance(q[2], str) else q[2] for q in samples], np.int32)
+            buf = np.zeros((nsteps, len(samples)), np.float64)
+            keep += [si, sj, sc]
+            m.n_samp, m.si, m.sj, m.scomp, m.samp = len(samples), _ip_(si), _ip_(sj), _ip_(sc), _p(buf)
+            out["samples"] = buf
+        if dft_cells is not None and len(dft_cells):
+            di = np.ascontiguousarray(np.asarray(dft_cells)[:, 0], np.int32)
+            dj = np.ascontiguousarray(np.asarray(dft_cells)[:, 1], np.int32)
+            fr = np.ascontiguousarray(freqs, np.float64)
+            if not hasattr(self, "dft") or self.dft[0].shape != (len(di), len(fr)):
+                self.dft = (np.zeros((len(di), len(fr))), np.zeros((len(di), len(fr))))
+            keep += [di, dj, fr]
+            m.n_dft, m.di, m.dj, m.n_freq, m.freq = len(di), _ip_(di), _ip_(dj), len(fr), _p(fr)
+            m.dre, m.dim = _p(self.dft[0]), _p(self.dft[1])
+        lib().or2s_run(C.byref(self._p), C.byref(self._s), C.c_int64(self.n), C.c_int64(nsteps), C.byref(m))
+        self.n += nsteps
+        return out
+
+    def set_state(self, **fields):
+        for k, v in fields.items():
+            self.state[k][...] = v
+        self._bind()
+
+    def layer_h(self):
+        lib().or2s_layer_h(C.byref(self._p), C.byref(self._s))
+
+    def layer_e(self):
+        lib().or2s_layer_e(C.byref(self._p), C.byref(self._s))
+
+    # ---- literal 4-node graph (Sec. III-B) ----
+    def node_index(self, kind, i, j) -> int:
+        k = {"u": 0, "hx": 0, "q": 1, "hy": 1, "tx": 2, "ezx": 2, "tz": 3, "ezy": 3}[kind]
+        return lib().or2s_node_index(self.nx, k, i, j)
+
+    def graph_layer(self, layer):
+        n = 4 * self.nx * self.ny
+        nnz = lib().or2s_graph_layer(C.byref(self._p), layer, None, None, None)
+        rowptr = np.zeros(n + 1, np.int64)
+        col = np.zeros(nnz, np.int32)
+        w = np.zeros(nnz, np.float64)
+        lib().or2s_graph_layer(C.byref(self._p), layer, rowptr.ctypes.data_as(C.POINTER(C.c_int64)),
+                               col.ctypes.data_as(C.POINTER(C.c_int32)), _p(w))
+        return rowptr, col, w
+
+    def to_nodes(self) -> np.ndarray:
+        h = np.zeros(4 * self.nx * self.ny, np.float64)
+        lib().or2s_state_to_nodes(C.byref(self._p), C.byref(self._s), _p(h))
+        return h
+
+    def from_nodes(self, h):
+        h = np.ascontiguousarray(h, np.float64)
+        lib().or2s_nodes_to_state(C.byref(self._p), _p(h), C.byref(self._s))
+
+
+# ---------------------------------------------------------------------------------
 # 3D Yee
 # ---------------------------------------------------------------------------------
 

@@ -13,6 +13,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "fdtd_oracle.c")
+SRC2 = os.path.join(HERE, "split_pml.c")
 HDR = os.path.join(HERE, "fdtd_oracle.h")
 LIB = os.path.join(HERE, "liboracle.so")
 
@@ -21,14 +22,14 @@ def needs_build() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    return any(os.path.getmtime(f) > t for f in (SRC, HDR))
+    return any(os.path.getmtime(f) > t for f in (SRC, SRC2, HDR))
 
 
 def build(force: bool = False) -> str:
     if force or needs_build():
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
-               "-Wall", "-Wno-unused-function", SRC, "-o", tmp, "-lm"]
+               "-Wall", "-Wno-unused-function", SRC, SRC2, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, LIB)
     return LIB

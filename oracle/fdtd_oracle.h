@@ -93,6 +93,46 @@ void or2_layer_e(const or2_problem* p, or2_state* s);
 double or2_energy(const or2_problem* p, const double* eps_cell, const or2_state* s,
                   const double* hx_prev, const double* hy_prev);
 
+/* ---- 2D TMz with the paper's split-field PML (split_pml.c) -------------
+ * Berenger's split field (Sec. II-C, eqs. (10)-(13), rotated to TMz): Ez =
+ * Ezx + Ezy, each part damped by the conductivity of its derivative's axis,
+ * H damped by the matched sigma* = sigma mu0 / eps0; semi-implicit averaging
+ * of eq. (7) throughout.  Graded sigma(rho) = sigma_max (rho/d)^m,
+ * sigma_max = 0.8 (m+1) / (eta0 delta); E nodes at integer, H nodes at
+ * half-integer depth (sE, sH: [n]). */
+void or_split_axis(int n, int npml, double delta, double m, double* sE, double* sH);
+
+typedef struct {
+    int nx, ny;
+    double dx, dy, dt;
+    const double *eps_cell, *sig_cell;                     /* [ny*nx] eps_r, sigma (S/m) */
+    const double *sxe, *sxh;                               /* [nx] layer sigma at E nodes i, H nodes i+1/2 */
+    const double *sye, *syh;                               /* [ny] */
+    int src_i, src_j;                                      /* soft source added to Ezx; -1: none */
+    const double* src;
+    int64_t src_len;
+} or2s_problem;
+
+typedef struct {
+    double *ezx, *ezy, *hx, *hy;                           /* [ny*nx]; Ez = ezx + ezy */
+} or2s_state;
+
+/* layer 1 then layer 2 then the source, steps n0 .. n0+nsteps-1; monitors see
+ * Ez = Ezx + Ezy (component 0), Hx (1), Hy (2) */
+int or2s_run(const or2s_problem* p, or2s_state* s, int64_t n0, int64_t nsteps, or2_monitors* m);
+void or2s_layer_h(const or2s_problem* p, or2s_state* s);
+void or2s_layer_e(const or2s_problem* p, or2s_state* s);
+
+/* literal graph with absorbing boundaries (Sec. III-B): 4 nodes per cell,
+ * u(i,j) = i + 4 j nx (Hx), q(i,j) = 3 i + nx (4 j + 1) (Hy),
+ * tx(i,j) = 3 i + 1 + nx (4 j + 1) (Ezx), tz(i,j) = 3 i + 2 + nx (4 j + 1) (Ezy);
+ * kind 0 u, 1 q, 2 tx, 3 tz.  CSR by destination over all nodes (identity rows
+ * for nodes a layer does not update); returns nnz. */
+int64_t or2s_node_index(int nx, int kind, int i, int j);
+int64_t or2s_graph_layer(const or2s_problem* p, int layer, int64_t* rowptr, int32_t* col, double* w);
+void or2s_state_to_nodes(const or2s_problem* p, const or2s_state* s, double* h);
+void or2s_nodes_to_state(const or2s_problem* p, const double* h, or2s_state* s);
+
 /* ---- literal GEM graph (Prop. 1 and 2) ----------------------------------
  * Node numbering of Prop. 1 with k -> j:  u(i,j) = i + 3 j nx  (Hx),
  * q(i,j) = 2 i + nx (3 j + 1)  (Hy),  t(i,j) = 2 i + 1 + nx (3 j + 1)  (Ez),
