@@ -54,6 +54,12 @@ extern "C" {
 
 #define FDTD_PEC 0          /* plain PEC box */
 #define FDTD_CPML 1         /* CPML of pml_cells cells on every face, backed by PEC */
+#define FDTD_SPLIT_PML 2    /* 2D only: the paper's own absorber (Sec. II-C, eqs. (10)-(13)), Berenger's
+                               split-field PML of pml_cells cells on every face, backed by PEC: Ez = Ezx + Ezy
+                               in the layer, each part damped by the graded conductivity of its derivative's
+                               axis, H by the matched sigma* = sigma mu0/eps0, semi-implicit as eq. (7);
+                               sigma = sigma_max (depth/d)^3, sigma_max = 3.2 / (eta0 delta).  The layer's
+                               cells must be vacuum (eps_r 1, sigma 0).  Steps with the unfused kernels. */
 
 /* field components */
 #define FDTD_EX 0
@@ -94,8 +100,8 @@ typedef struct fdtd_ctx fdtd_ctx;
 typedef struct {
     int dims;       /* 2 (TMz) or 3 */
     int nx, ny, nz; /* cells per axis (nz ignored for dims == 2); each >= 4 */
-    int pml_cells;  /* CPML depth in cells when boundary == FDTD_CPML */
-    int boundary;   /* FDTD_PEC or FDTD_CPML */
+    int pml_cells;  /* absorbing layer depth in cells (FDTD_CPML, FDTD_SPLIT_PML) */
+    int boundary;   /* FDTD_PEC, FDTD_CPML or FDTD_SPLIT_PML */
     double dy, dz;  /* cell sizes in m for y and z; <= 0 means "same as dx" */
 } fdtd_grid;
 

@@ -107,6 +107,39 @@ void cpml_axis(int n, int npml, double delta, double dt, int pad, int len, float
     }
 }
 
+// Berenger split-field layer (Sec. II-C): conductivity sigma_max (depth/d)^3,
+// sigma_max = 0.8 (m+1) / (eta0 delta) with m = 3, E nodes at integer and H nodes
+// at half-integer depth.  Per node of one axis, in storage coordinates:
+// Ca, Cb/delta of the E part along this axis (vacuum, eq. (7) with sigma) and
+// Da, Db/delta of the H component damped by this axis (sigma* = sigma mu0/eps0).
+// Nodes outside the layer hold the vacuum values (sigma = 0).
+void split_axis(int n, int npml, double delta, double dt, int pad, int len, float* caE, float* cbE, float* daH,
+                float* dbH) {
+    for (int k = 0; k < len; k++) caE[k] = cbE[k] = daH[k] = dbH[k] = 0.f;
+    const double eta0 = sqrt(kMu0 / kEps0);
+    const double smax = 0.8 * (kPmlM + 1.0) / (eta0 * delta);
+    for (int i = 0; i < n; i++) {
+        const double xe = i, xh = i + 0.5, lo = npml, hi = n - npml;
+        double rE = 0, rH = 0;
+        if (xe < lo) rE = lo - xe;
+        if (xe > hi) rE = xe - hi;
+        if (xh < lo) rH = lo - xh;
+        if (xh > hi) rH = xh - hi;
+        const double sE = smax * pow(rE / npml, kPmlM), sH = smax * pow(rH / npml, kPmlM);
+        const double ae = 1.0 + sE * dt / (2.0 * kEps0);
+        caE[i + pad] = (float)((1.0 - sE * dt / (2.0 * kEps0)) / ae);
+        cbE[i + pad] = (float)(dt / (kEps0 * ae) / delta);
+        const double ah = 1.0 + sH * dt / (2.0 * kEps0);   // sigma* dt / (2 mu0) = sigma dt / (2 eps0)
+        daH[i + pad] = (float)((1.0 - sH * dt / (2.0 * kEps0)) / ah);
+        dbH[i + pad] = (float)(dt / (kMu0 * ah) / delta);
+    }
+}
+
+// an E node of the split layer (positive depth on either axis)
+bool split_layer_cell(int i, int j, int nx, int ny, int npml) {
+    return i < npml || i > nx - npml || j < npml || j > ny - npml;
+}
+
 // eq. (7): Ca = A_-/A_+, Cb = dt/(A_+ eps), A_-/+ = 1 -/+ sigma dt/(2 eps)
 float4 e_coeffs(double eps_r, double sigma, double dt, double dx, double dy) {
     const double eps = kEps0 * eps_r;
@@ -154,7 +187,8 @@ int scene2_init(fdtd_ctx* c, const fdtd_grid* g, double dx, double dt, double co
     if (!(dx > 0)) return fail(c, FDTD_EINVAL, "dx must be > 0");
     const double dy = g->dy > 0 ? g->dy : dx;
     int npml = 0;
-    if (g->boundary == FDTD_CPML) {
+    const bool split = g->boundary == FDTD_SPLIT_PML;
+    if (g->boundary == FDTD_CPML || split) {
         npml = g->pml_cells;
         if (npml < 1 || 2 * npml + 2 > std::min(g->nx, g->ny))
             return fail(c, FDTD_EINVAL, "pml_cells %d does not fit a %dx%d grid", npml, g->nx, g->ny);
@@ -177,13 +211,23 @@ int scene2_init(fdtd_ctx* c, const fdtd_grid* g, double dx, double dt, double co
     const int64_t ncell = (int64_t)g->nx * g->ny;
     for (int64_t k = 0; k < ncell; k++)
         if (mat[k] >= n_mat) return fail(c, FDTD_EINVAL, "material index %d at cell %lld >= n_mat %d", mat[k], (long long)k, n_mat);
+    if (split) {
+        // the split layer's coefficients are per-axis profiles of vacuum
+        for (int j = 0; j < g->ny; j++)
+            for (int i = 0; i < g->nx; i++) {
+                if (!split_layer_cell(i, j, g->nx, g->ny, npml)) continue;
+                const int m = mat[(size_t)j * g->nx + i];
+                if (table[m].eps_r != 1.0 || table[m].sigma != 0.0)
+                    return fail(c, FDTD_EINVAL, "split-field PML: cell (%d, %d) in the layer is not vacuum", i, j);
+            }
+    }
 
     Scene2* s = new Scene2();
     memset((void*)s->fbuf, 0, sizeof(s->fbuf));
     s->d_mat = nullptr; s->d_coef = nullptr; s->d_prof = nullptr; s->d_src = nullptr; s->d_rec = nullptr;
     s->d_dsg = nullptr;
     s->d_band = nullptr;
-    s->nx = g->nx; s->ny = g->ny; s->npml = npml;
+    s->nx = g->nx; s->ny = g->ny; s->npml = npml; s->split = split ? 1 : 0;
     s->dx = dx; s->dy = dy; s->dt = dt;
     s->pitch = ((PAD_X + g->nx + STRIP) + 31) / 32 * 32;
     s->rows = g->ny + 2 * PAD_Y;
@@ -222,8 +266,13 @@ int scene2_init(fdtd_ctx* c, const fdtd_grid* g, double dx, double dt, double co
     std::vector<float> prof(4 * (size_t)s->pitch + 4 * (size_t)s->rows, 0.f);
     float* px = prof.data();
     float* py = prof.data() + 4 * s->pitch;
-    cpml_axis(s->nx, npml, dx, dt, PAD_X, s->pitch, px, px + s->pitch, px + 2 * s->pitch, px + 3 * s->pitch);
-    cpml_axis(s->ny, npml, dy, dt, PAD_Y, s->rows, py, py + s->rows, py + 2 * s->rows, py + 3 * s->rows);
+    if (split) {
+        split_axis(s->nx, npml, dx, dt, PAD_X, s->pitch, px, px + s->pitch, px + 2 * s->pitch, px + 3 * s->pitch);
+        split_axis(s->ny, npml, dy, dt, PAD_Y, s->rows, py, py + s->rows, py + 2 * s->rows, py + 3 * s->rows);
+    } else {
+        cpml_axis(s->nx, npml, dx, dt, PAD_X, s->pitch, px, px + s->pitch, px + 2 * s->pitch, px + 3 * s->pitch);
+        cpml_axis(s->ny, npml, dy, dt, PAD_Y, s->rows, py, py + s->rows, py + 2 * s->rows, py + 3 * s->rows);
+    }
     rc = dalloc(c, &s->d_prof, prof.size() * sizeof(float), "profiles");
     if (rc) { scene2_free(s); return rc; }
     cudaError_t e = cudaMemcpyAsync(s->d_mat, pm.data(), pm.size(), cudaMemcpyHostToDevice, c->stream);
@@ -360,7 +409,8 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
         d.coef = s->d_coef;
         d.prof = s->d_prof;
         d.nx = s->nx; d.ny = s->ny; d.pitch = s->pitch; d.rows = s->rows;
-        d.has_pml = s->npml;
+        d.has_pml = s->split ? 0 : s->npml;
+        d.split = s->split ? s->npml : 0;
         d.dbx = (float)(s->dt / (kMu0 * s->dx));
         d.dby = (float)(s->dt / (kMu0 * s->dy));
         d.src_i = s->src_kind >= 0 ? s->src_i : -1;
@@ -746,6 +796,9 @@ int fdtd_set_design(fdtd_ctx* c, int i0, int j0, int w, int h, const double* eps
     if (!s) return fail(c, FDTD_EINVAL, "design regions are 2D only");
     if (!eps_r || w < 1 || h < 1 || i0 < 1 || j0 < 1 || i0 + w > s->nx || j0 + h > s->ny)
         return fail(c, FDTD_EINVAL, "design rectangle (%d, %d, %d, %d) must lie in 1..nx-1 x 1..ny-1", i0, j0, w, h);
+    if (s->split && (split_layer_cell(i0, j0, s->nx, s->ny, s->npml) ||
+                     split_layer_cell(i0 + w - 1, j0 + h - 1, s->nx, s->ny, s->npml)))
+        return fail(c, FDTD_EINVAL, "the design rectangle must lie inside the split-field PML");
     const size_t n = (size_t)w * h;
     std::vector<float4> co(n);
     for (size_t q = 0; q < n; q++) {
@@ -845,6 +898,12 @@ int fdtd_add_dft_plane(fdtd_ctx* c, int k, int comp_mask, const double* freqs, i
     return fdtd_add_dft_plane3(c, k, comp_mask, freqs, n_freq, mon_id);
 }
 
+static bool any_split(const fdtd_ctx* c) {
+    for (const Scene2* s : c->s2)
+        if (s->split) return true;
+    return false;
+}
+
 // the launches of n_steps steps (no allocation: step_prepare ran before)
 static int step_launches(fdtd_ctx* c, int64_t n_steps) {
     const int T = c->opt_tblock;
@@ -854,7 +913,8 @@ static int step_launches(fdtd_ctx* c, int64_t n_steps) {
         int done;
         rc = adj_checkpoint_if_due(c);
         if (rc) return rc;
-        if (c->opt_kernel == 1) {
+        if (c->opt_kernel == 1 || any_split(c)) {
+            // the split-field layer runs on the unfused pair only
             rc = tmz_naive_step(c, c->t);
             done = 1;
         } else if (c->opt_kernel == 2 && left >= T) {
@@ -982,6 +1042,7 @@ int fdtd_autotune(fdtd_ctx* c, int trial_steps, double* best_ms) {
     if (c->dims != 2) return fail(c, FDTD_EINVAL, "autotuning covers the 2D kernels");
     if (trial_steps < 4) return fail(c, FDTD_EINVAL, "trial_steps must be >= 4");
     if (c->adj) return fail(c, FDTD_EINVAL, "disable checkpointing before autotuning");
+    if (any_split(c)) return fail(c, FDTD_EINVAL, "a split-field PML steps with the unfused kernels only: nothing to tune");
     struct Cand { int kernel, T, seg, warps; };
     std::vector<Cand> cand;
     // the segment height sets how many CTAs a block launches, so the sweep is

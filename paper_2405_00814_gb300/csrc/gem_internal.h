@@ -47,6 +47,7 @@ struct TmzDev {
     const float* prof;          // 4 x-profiles [pitch] (bEx cEx bHx cHx), then 4 y-profiles [rows]
     int nx, ny, pitch, rows;
     int has_pml;
+    int split;                          // split-field PML depth (profiles hold Ca, Cb/d, Da, Db/d per axis)
     float dbx, dby;             // dt / (mu0 dx), dt / (mu0 dy)
     int src_i, src_j;           // soft source cell or -1
     const float* src_wave;      // src_wave[n] = s((n+1) dt)
@@ -114,6 +115,7 @@ struct Probe {
 
 struct Scene2 {
     int nx, ny, pitch, rows, npml;
+    int split;                           // 1: npml is a split-field PML, not a CPML
     double dx, dy, dt;
     std::vector<uint8_t> mat_host;       // [ny][nx] as given
     std::vector<double> eps_r, sigma;    // material table

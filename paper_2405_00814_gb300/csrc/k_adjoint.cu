@@ -640,6 +640,11 @@ int fdtd_set_checkpointing(fdtd_ctx* c, int every) {
         c->err = "checkpointed reverse mode is 2D only";
         return FDTD_EINVAL;
     }
+    for (const Scene2* s : c->s2)
+        if (s->split) {
+            c->err = "reverse mode covers the CPML and PEC boundaries, not the split-field PML";
+            return FDTD_EINVAL;
+        }
     if (every < 0) {
         c->err = "checkpoint interval must be >= 0";
         return FDTD_EINVAL;

@@ -411,6 +411,11 @@ int fdtd_step_edgelist(fdtd_ctx* c, int64_t n_steps) {
         return FDTD_EINVAL;
     }
     if (n_steps == 0) return FDTD_OK;
+    for (const Scene2* s : c->s2)
+        if (s->split) {
+            c->err = "the edge-list path builds the CPML graph; a split-field PML scene steps with fdtd_step";
+            return FDTD_EINVAL;
+        }
     int rc = step_prepare(c, n_steps);
     if (rc) return rc;
     // the graph's weights are frozen from the scene's coefficients when first needed
@@ -475,6 +480,10 @@ int fdtd_export_graph(fdtd_ctx* c, int layer, int64_t* n_nodes, int64_t* n_edges
         return FDTD_EINVAL;
     }
     const Scene2* s = c->s2[c->cur];
+    if (s->split) {
+        c->err = "graph export covers the CPML and PEC boundaries, not the split-field PML";
+        return FDTD_EINVAL;
+    }
     HostScene h;
     int rc = fetch(c, s, h);
     if (rc) return rc;

@@ -756,6 +756,19 @@ __global__ void k_tmz_h(const TmzDev* __restrict__ scenes, int parity) {
             dex += v;
         }
     }
+    if (S.split) {
+        // split-field layer (Sec. II-C): H damped by sigma* of the axis its
+        // derivative runs along, semi-implicit as eq. (7)
+        const Prof pr{S.prof, pitch, S.rows};
+        const int np = S.split;
+        float* hx = S.f[F_HX][parity];
+        float* hy = S.f[F_HY][parity];
+        if (j < np || j >= S.ny - np) hx[c] = pr.bHy(j + PAD_Y) * hx[c] - pr.cHy(j + PAD_Y) * dey;
+        else hx[c] -= S.dby * dey;
+        if (i < np || i >= S.nx - np) hy[c] = pr.bHx(i + PAD_X) * hy[c] + pr.cHx(i + PAD_X) * dex;
+        else hy[c] += S.dbx * dex;
+        return;
+    }
     S.f[F_HX][parity][c] -= S.dby * dey;
     S.f[F_HY][parity][c] += S.dbx * dex;
 }
@@ -795,6 +808,24 @@ __global__ void k_tmz_e(const TmzDev* __restrict__ scenes, int parity) {
         if (di >= 0 && di < S.dsg_w && dj >= 0 && dj < S.dsg_h) co = S.dsg_coef[(size_t)dj * S.dsg_w + di];
     }
     float* ez = S.f[F_EZ][parity];
+    if (S.split && i >= 1 && j >= 1) {
+        const int np = S.split;
+        const bool lx = i < np || i > S.nx - np, ly = j < np || j > S.ny - np;
+        if (lx || ly) {
+            // split-field layer (Sec. II-C): Ez = Ezx + Ezy, Ezy kept in the
+            // psi_Ezy array, each part damped along its own axis (vacuum cells)
+            const Prof pr{S.prof, pitch, S.rows};
+            float* pzy = S.f[F_PEZY][parity];
+            const float ezy0 = pzy[c], ezx0 = ez[c] - ezy0;
+            const float ax = lx ? pr.bEx(i + PAD_X) : co.x, bx = lx ? pr.cEx(i + PAD_X) : co.y;
+            const float ay = ly ? pr.bEy(j + PAD_Y) : co.x, by = ly ? pr.cEy(j + PAD_Y) : co.z;
+            const float ezx = ax * ezx0 + bx * dhy;
+            const float ezy = ay * ezy0 - by * dhx;
+            pzy[c] = ezy;
+            ez[c] = ezx + ezy;
+            return;
+        }
+    }
     ez[c] = e_upd(ez[c], dhy, dhx, co);
 }
 

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libgemfdtd.so")
 _LIB = None
 
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6
-PEC, CPML = 0, 1
+PEC, CPML, SPLIT_PML = 0, 1, 2
 COMP = {"ex": 0, "ey": 1, "ez": 2, "hx": 3, "hy": 4, "hz": 5}
 SRC = {"ricker": 0, "gauss_mod": 1, "gauss": 2, "sampled": 3}
 OPT = {"kernel": 0, "tblock": 1, "segment": 2, "warps": 3, "graph": 4, "spin_limit": 5, "debug_skip_cta": 6,
@@ -109,7 +109,9 @@ def _mat_table(eps_r, sigma):
     return tab
 
 
-def _grid_of(scene):
+def _grid_of(scene, boundary=None):
+    """boundary: None (CPML when the scene has a layer, else PEC), "cpml",
+    "split" (the paper's split-field PML) or "pec"."""
     g = Grid()
     if hasattr(scene, "nz"):
         g.dims, g.nx, g.ny, g.nz = 3, scene.nx, scene.ny, scene.nz
@@ -118,7 +120,10 @@ def _grid_of(scene):
         g.dims, g.nx, g.ny, g.nz = 2, scene.nx, scene.ny, 1
         g.dz = 0.0
     g.pml_cells = scene.npml
-    g.boundary = CPML if scene.npml > 0 else PEC
+    if boundary is None:
+        g.boundary = CPML if scene.npml > 0 else PEC
+    else:
+        g.boundary = {"pec": PEC, "cpml": CPML, "split": SPLIT_PML}[boundary]
     g.dy = scene.dy
     return g
 
@@ -126,14 +131,14 @@ def _grid_of(scene):
 class Simulation:
     """One context of the C ABI: one scene, or a batch of 2D scenes."""
 
-    def __init__(self, scene=None, *, stream=None, _handle=None):
+    def __init__(self, scene=None, *, stream=None, boundary=None, _handle=None):
         self._L = lib()
         self._h = None
         self.dims = 2
         if _handle is not None:
             self._h = _handle
             return
-        g = _grid_of(scene)
+        g = _grid_of(scene, boundary)
         self.dims = g.dims
         mat = np.ascontiguousarray(scene.mat, np.uint8)
         tab = _mat_table(scene.eps_r, scene.sigma)
@@ -409,10 +414,11 @@ def mp_steps_noalloc(layer1, layer2, h, n_steps, stream=None):
                         f" (n_nodes {h.numel()}, limit {MP_NOALLOC_MAX_NODES})")
 
 
-def from_scene(scene, *, stream=None, probes=True, monitors=True, source=True) -> Simulation:
+def from_scene(scene, *, stream=None, probes=True, monitors=True, source=True, boundary=None) -> Simulation:
     """A Simulation for a seeded scene: its source, its probes (Ez) and, if it
-    has monitor cells and frequencies, one DFT monitor over them."""
-    sim = Simulation(scene, stream=stream)
+    has monitor cells and frequencies, one DFT monitor over them.  boundary: see
+    _grid_of (default: CPML when the scene has a layer)."""
+    sim = Simulation(scene, stream=stream, boundary=boundary)
     if hasattr(scene, "nz"):
         sim._plane_ny, sim._plane_nx = scene.ny, scene.nx
     if source and scene.source is not None:

@@ -1,0 +1,85 @@
+"""GPU: the paper's split-field PML (Berenger, Sec. II-C) through the C ABI
+(FDTD_SPLIT_PML) against the FP64 split-field oracle, its absorption, and the
+inputs it refuses."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2405_00814_gb300 import scenes
+from tests._helpers import TOL_FIELD, rel_l2
+
+pytestmark = pytest.mark.gpu
+C0 = 299792458.0
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _gpu(sc, nsteps, probes):
+    from paper_2405_00814_gb300 import fdtd
+    sim = fdtd.from_scene(sc, boundary="split", probes=False)
+    pids = [sim.add_probe(int(i), int(j)) for i, j in probes]
+    sim.step(nsteps)
+    out = {c: sim.get_field(c, (sc.ny, sc.nx)) for c in ("ez", "hx", "hy")}
+    out["probes"] = np.stack([sim.read_probe(p, nsteps) for p in pids], 1) if pids else None
+    sim.close()
+    return out
+
+
+@pytest.mark.parametrize("side,nsteps", [(200, 700), (131, 500)])
+def test_split_pml_matches_oracle(oracle_mod, side, nsteps):
+    """Heterogeneous lossy interior, vacuum layer of 16 (12) cells, a probe."""
+    sc = scenes.ellipse_scene(side=side, nsteps=nsteps)
+    probes = [(side // 2 + 7, side // 3), (side - sc.npml - 3, side // 2)]
+    o = oracle_mod.TMzSplit(sc)
+    ref = o.run(nsteps, samples=[(i, j, "ez") for i, j in probes])["samples"]
+    g = _gpu(sc, nsteps, probes)
+    assert rel_l2(g["ez"], o.ez()) <= TOL_FIELD
+    assert rel_l2(g["hx"], o.state["hx"]) <= TOL_FIELD
+    assert rel_l2(g["hy"], o.state["hy"]) <= TOL_FIELD
+    assert rel_l2(g["probes"], ref) <= TOL_FIELD
+
+
+def test_split_pml_absorbs_on_the_gpu(oracle_mod):
+    """A probe next to a 16-cell layer against an FP64 domain so large that no
+    echo returns: the echo stays below -95 dB, as for the oracle."""
+    f0 = 2.4e9
+    dx = scenes._dx_for(2 * f0, 1.0, 20)
+    dt = 0.99 * dx / (C0 * math.sqrt(2))
+    nsteps = 900
+
+    def scene(n, npml, off):
+        s = scenes.Source(off + 30, off + 60, kind="gauss_mod", params=(f0,))
+        return scenes.Scene2D(nx=n, ny=n, dx=dx, dy=dx, dt=dt, npml=npml, mat=np.zeros((n, n), np.uint8),
+                              eps_r=np.array([1.0]), sigma=np.array([0.0]), nsteps=nsteps, source=s)
+
+    small = _gpu(scene(120, 16, 0), nsteps, [(24, 60)])["probes"][:, 0]
+    big = oracle_mod.TMz(scene(120 + 1800, 0, 900), nsteps_src=nsteps).run(
+        nsteps, samples=[(924, 960, "ez")])["samples"][:, 0]
+    refl = np.max(np.abs(small - big)) / np.max(np.abs(big))
+    assert 20 * math.log10(refl) < -95.0
+
+
+def test_split_pml_refusals():
+    from paper_2405_00814_gb300 import fdtd
+    sc = scenes.ellipse_scene(side=128, nsteps=10)
+    bad = scenes.ellipse_scene(side=128, nsteps=10)
+    bad.mat = bad.mat.copy()
+    bad.mat[3, 60] = 1                                    # a dielectric cell inside the layer
+    with pytest.raises(fdtd.FDTDError):
+        fdtd.Simulation(bad, boundary="split")
+    sim = fdtd.from_scene(sc, boundary="split")
+    with pytest.raises(fdtd.FDTDError):
+        sim.set_design(4, 40, np.full((8, 8), 2.0))       # overlaps the layer
+    with pytest.raises(fdtd.FDTDError):
+        sim.set_checkpointing(10)
+    with pytest.raises(fdtd.FDTDError):
+        sim.step_edgelist(1)
+    sim.step(8)
+    assert np.all(np.isfinite(sim.get_field("ez", (sc.ny, sc.nx))))
+    sim.close()
