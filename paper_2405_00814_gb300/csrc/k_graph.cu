@@ -11,6 +11,12 @@
 // kernel per layer, then the soft source.  The neighbourhood offsets follow the
 // update equations: E gathers from H at (i, j), (i-1, j), (i, j-1); H gathers
 // from E at (i, j), (i+1, j), (i, j+1).
+//
+// A scene with the split-field PML (Sec. II-C) uses the paper's graph with
+// absorbing boundaries instead (Sec. III-B): 4 nodes per cell, u(i,j) = i + 4 j nx
+// (Hx), q(i,j) = 3 i + nx (4 j + 1) (Hy), tx = q + 1 (Ezx), tz = q + 2 (Ezy); Ezx
+// gathers Hy at (i, j), (i-1, j), Ezy gathers Hx at (i, j), (i, j-1), and H gathers
+// both E parts at the forward neighbours.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -39,6 +45,7 @@ struct SceneGraph {
     int n_psi;
     int* d_psi;             // per psi node: (type << 29) | storage-free cell index j * nx + i
     int64_t psi_base;
+    int split;              // 4-node graph of the split-field layer
 };
 
 struct Graph {
@@ -48,6 +55,11 @@ struct Graph {
 static inline int64_t node_t(int nx, int i, int j) { return 2 * (int64_t)i + 1 + (int64_t)nx * (3 * (int64_t)j + 1); }
 static inline int64_t node_u(int nx, int i, int j) { return (int64_t)i + 3 * (int64_t)j * nx; }
 static inline int64_t node_q(int nx, int i, int j) { return 2 * (int64_t)i + (int64_t)nx * (3 * (int64_t)j + 1); }
+// split-field graph (Sec. III-B): kind 0 u (Hx), 1 q (Hy), 2 tx (Ezx), 3 tz (Ezy)
+static inline int64_t node4(int nx, int kind, int i, int j) {
+    if (kind == 0) return (int64_t)i + 4 * (int64_t)j * nx;
+    return 3 * (int64_t)i + (kind - 1) + (int64_t)nx * (4 * (int64_t)j + 1);
+}
 
 // host copies of the FP32 profiles and coefficients the kernels use
 struct HostScene {
@@ -57,6 +69,8 @@ struct HostScene {
     std::vector<uint8_t> mat;      // padded
     std::vector<float4> dsg;
     float dbx, dby;
+    int npml, split;
+    int dsg_i0, dsg_j0, dsg_w, dsg_h;
 };
 
 static int fetch(fdtd_ctx* c, const Scene2* s, HostScene& h) {
@@ -78,7 +92,76 @@ static int fetch(fdtd_ctx* c, const Scene2* s, HostScene& h) {
     }
     h.dbx = (float)(s->dt / (kMu0g * s->dx));
     h.dby = (float)(s->dt / (kMu0g * s->dy));
+    h.npml = s->npml;
+    h.split = s->split;
+    h.dsg_i0 = s->dsg_i0; h.dsg_j0 = s->dsg_j0; h.dsg_w = s->d_dsg ? s->dsg_w : 0; h.dsg_h = s->dsg_h;
     return FDTD_OK;
+}
+
+// the two layers of the split-field graph, rows in node order, weights from
+// the same FP32 profiles and coefficients the stencil kernels use
+static void build_layer_split(const HostScene& h, int layer, std::vector<int>& rowptr, std::vector<int>& col,
+                              std::vector<float>& w) {
+    const int nx = h.nx, ny = h.ny, np = h.npml;
+    const int64_t n_nodes = 4 * (int64_t)nx * ny;
+    const float* px = h.prof.data();
+    const float* py = h.prof.data() + 4 * h.pitch;
+    rowptr.assign(n_nodes + 1, 0);
+    col.clear();
+    w.clear();
+    col.reserve(n_nodes * 3);
+    w.reserve(n_nodes * 3);
+    auto put = [&](int64_t c, float v) {
+        col.push_back((int)c);
+        w.push_back(v);
+    };
+    for (int64_t v = 0; v < n_nodes; v++) {
+        rowptr[v] = (int)col.size();
+        const int j = (int)(v / (4 * (int64_t)nx));
+        const int64_t r = v % (4 * (int64_t)nx);
+        const int kind = r < nx ? 0 : 1 + (int)((r - nx) % 3);
+        const int i = r < nx ? (int)r : (int)((r - nx) / 3);
+        if (layer == 1 && kind == 0) {                 // Hx(i,j)
+            const bool ly = j < np || j >= ny - np;
+            const float da = ly ? py[2 * h.rows + j + PAD_Y] : 1.f, db = ly ? py[3 * h.rows + j + PAD_Y] : h.dby;
+            put(v, da);
+            if (j + 1 < ny) {
+                put(node4(nx, 2, i, j + 1), -db);
+                put(node4(nx, 3, i, j + 1), -db);
+            }
+            put(node4(nx, 2, i, j), db);
+            put(node4(nx, 3, i, j), db);
+        } else if (layer == 1 && kind == 1) {          // Hy(i,j)
+            const bool lx = i < np || i >= nx - np;
+            const float da = lx ? px[2 * h.pitch + i + PAD_X] : 1.f, db = lx ? px[3 * h.pitch + i + PAD_X] : h.dbx;
+            put(v, da);
+            if (i + 1 < nx) {
+                put(node4(nx, 2, i + 1, j), db);
+                put(node4(nx, 3, i + 1, j), db);
+            }
+            put(node4(nx, 2, i, j), -db);
+            put(node4(nx, 3, i, j), -db);
+        } else if (layer == 2 && kind >= 2 && i >= 1 && j >= 1) {
+            float4 co = h.coef[h.mat[(size_t)(j + PAD_Y) * h.pitch + i + PAD_X]];
+            const int di = i - h.dsg_i0, dj = j - h.dsg_j0;
+            if (h.dsg_w > 0 && di >= 0 && di < h.dsg_w && dj >= 0 && dj < h.dsg_h) co = h.dsg[(size_t)dj * h.dsg_w + di];
+            const bool lx = i < np || i > nx - np, ly = j < np || j > ny - np;
+            if (kind == 2) {                           // Ezx(i,j)
+                const float a = lx ? px[i + PAD_X] : co.x, b = lx ? px[h.pitch + i + PAD_X] : co.y;
+                put(v, a);
+                put(node4(nx, 1, i, j), b);
+                put(node4(nx, 1, i - 1, j), -b);
+            } else {                                   // Ezy(i,j)
+                const float a = ly ? py[j + PAD_Y] : co.x, b = ly ? py[h.rows + j + PAD_Y] : co.z;
+                put(v, a);
+                put(node4(nx, 0, i, j), -b);
+                put(node4(nx, 0, i, j - 1), b);
+            }
+        } else {
+            put(v, 1.f);                               // not updated by this layer
+        }
+    }
+    rowptr[n_nodes] = (int)col.size();
 }
 
 // psi node lists: type 0 psi_Hxy, 1 psi_Hyx, 2 psi_Ezx, 3 psi_Ezy (same storage slots F_PHXY, F_PHYX, F_PEZX, F_PEZY)
@@ -283,6 +366,47 @@ __global__ void k_psi_nodes(const TmzDev* __restrict__ sc, int scene, int parity
     else S.f[slot][parity][g] = h[base + k];
 }
 
+// split-field scenes: Ezx = Ez - Ezy where the layer keeps Ezy, Ez elsewhere
+__global__ void k_cells_nodes_split(const TmzDev* __restrict__ sc, int scene, int parity, float* h, int dir) {
+    const TmzDev& S = sc[scene];
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= (int64_t)S.nx * S.ny) return;
+    const int i = (int)(c % S.nx), j = (int)(c / S.nx);
+    const size_t g = gsidx(S.pitch, i, j);
+    const int np = S.split;
+    const bool layer = i < np || i > S.nx - np || j < np || j > S.ny - np;
+    const int64_t vu = (int64_t)i + 4 * (int64_t)j * S.nx;
+    const int64_t vq = 3 * (int64_t)i + (int64_t)S.nx * (4 * (int64_t)j + 1);
+    if (dir == 0) {
+        const float ezy = layer ? S.f[F_PEZY][parity][g] : 0.f;
+        h[vu] = S.f[F_HX][parity][g];
+        h[vq] = S.f[F_HY][parity][g];
+        h[vq + 1] = S.f[F_EZ][parity][g] - ezy;
+        h[vq + 2] = ezy;
+    } else {
+        S.f[F_HX][parity][g] = h[vu];
+        S.f[F_HY][parity][g] = h[vq];
+        S.f[F_EZ][parity][g] = h[vq + 1] + h[vq + 2];
+        S.f[F_PEZY][parity][g] = h[vq + 2];
+    }
+}
+
+__global__ void k_graph_src_rec_split(const TmzDev* __restrict__ sc, int scene, const Sample2* __restrict__ samps,
+                                      const int* __restrict__ samp_off, float* h, long long n) {
+    const TmzDev& S = sc[scene];
+    auto q_of = [&](int i, int j) { return 3 * (int64_t)i + (int64_t)S.nx * (4 * (int64_t)j + 1); };
+    if (threadIdx.x == 0 && S.src_i >= 0 && n < S.src_len) h[q_of(S.src_i, S.src_j) + 1] += S.src_wave[n];
+    __syncthreads();
+    for (int q = samp_off[scene] + threadIdx.x; q < samp_off[scene + 1]; q += blockDim.x) {
+        const Sample2 sp = samps[q];
+        float v;
+        if (sp.comp == F_EZ) v = h[q_of(sp.i, sp.j) + 1] + h[q_of(sp.i, sp.j) + 2];
+        else if (sp.comp == F_HX) v = h[(int64_t)sp.i + 4 * (int64_t)sp.j * S.nx];
+        else v = h[q_of(sp.i, sp.j)];
+        S.rec[n * S.n_rec + sp.slot] = v;
+    }
+}
+
 __global__ void k_graph_src_rec(const TmzDev* __restrict__ sc, int scene, const Sample2* __restrict__ samps,
                                 const int* __restrict__ samp_off, float* h, long long n) {
     const TmzDev& S = sc[scene];
@@ -325,8 +449,9 @@ static int upload_graph(fdtd_ctx* c, int scene, SceneGraph& g) {
     if (rc) return rc;
     std::vector<int> psi;
     std::vector<int64_t> idx4;
-    psi_lists(h, psi, idx4);
-    g.n_nodes = 3 * (int64_t)h.nx * h.ny + (int64_t)psi.size();
+    g.split = h.split;
+    if (!h.split) psi_lists(h, psi, idx4);
+    g.n_nodes = (h.split ? 4 : 3) * (int64_t)h.nx * h.ny + (int64_t)psi.size();
     g.n_psi = (int)psi.size();
     g.psi_base = 3 * (int64_t)h.nx * h.ny;
     if (g.n_nodes >= ((int64_t)1 << 31)) {
@@ -340,8 +465,12 @@ static int upload_graph(fdtd_ctx* c, int scene, SceneGraph& g) {
     for (int l = 0; l < 2; l++) {
         std::vector<int> rowptr, col;
         std::vector<float> w;
-        build_layer(h, l + 1, psi, idx4, rowptr, col, w);
-        if (l == 1) apply_design(h, s, rowptr, col, w, idx4);
+        if (h.split) {
+            build_layer_split(h, l + 1, rowptr, col, w);
+        } else {
+            build_layer(h, l + 1, psi, idx4, rowptr, col, w);
+            if (l == 1) apply_design(h, s, rowptr, col, w, idx4);
+        }
         g.nnz[l] = (int64_t)col.size();
         if (cudaMalloc(&g.d_rowptr[l], rowptr.size() * sizeof(int)) != cudaSuccess ||
             cudaMalloc(&g.d_col[l], col.size() * sizeof(int)) != cudaSuccess ||
@@ -411,11 +540,6 @@ int fdtd_step_edgelist(fdtd_ctx* c, int64_t n_steps) {
         return FDTD_EINVAL;
     }
     if (n_steps == 0) return FDTD_OK;
-    for (const Scene2* s : c->s2)
-        if (s->split) {
-            c->err = "the edge-list path builds the CPML graph; a split-field PML scene steps with fdtd_step";
-            return FDTD_EINVAL;
-        }
     int rc = step_prepare(c, n_steps);
     if (rc) return rc;
     // the graph's weights are frozen from the scene's coefficients when first needed
@@ -427,7 +551,11 @@ int fdtd_step_edgelist(fdtd_ctx* c, int64_t n_steps) {
         SceneGraph& g = G->g[k];
         const Scene2* s = c->s2[k];
         const int64_t ncell = (int64_t)s->nx * s->ny;
-        k_cells_nodes<<<(unsigned)((ncell + tb - 1) / tb), tb, 0, c->stream>>>(c->d_scenes, (int)k, c->parity, g.d_h[0], 0);
+        if (g.split)
+            k_cells_nodes_split<<<(unsigned)((ncell + tb - 1) / tb), tb, 0, c->stream>>>(c->d_scenes, (int)k, c->parity,
+                                                                                       g.d_h[0], 0);
+        else
+            k_cells_nodes<<<(unsigned)((ncell + tb - 1) / tb), tb, 0, c->stream>>>(c->d_scenes, (int)k, c->parity, g.d_h[0], 0);
         if (g.n_psi)
             k_psi_nodes<<<(g.n_psi + tb - 1) / tb, tb, 0, c->stream>>>(c->d_scenes, (int)k, c->parity, g.d_psi, g.n_psi,
                                                                       g.psi_base, g.d_h[0], 0);
@@ -440,7 +568,11 @@ int fdtd_step_edgelist(fdtd_ctx* c, int64_t n_steps) {
             const unsigned blocks = (unsigned)((g.n_nodes + tb - 1) / tb);
             k_mp_layer<<<blocks, tb, 0, c->stream>>>(g.d_rowptr[0], g.d_col[0], g.d_w[0], g.d_h[0], g.d_h[1], g.n_nodes);
             k_mp_layer<<<blocks, tb, 0, c->stream>>>(g.d_rowptr[1], g.d_col[1], g.d_w[1], g.d_h[1], g.d_h[0], g.n_nodes);
-            k_graph_src_rec<<<1, 128, 0, c->stream>>>(c->d_scenes, (int)k, c->d_samp_scene, c->d_samp_off, g.d_h[0], n);
+            if (g.split)
+                k_graph_src_rec_split<<<1, 128, 0, c->stream>>>(c->d_scenes, (int)k, c->d_samp_scene, c->d_samp_off,
+                                                                g.d_h[0], n);
+            else
+                k_graph_src_rec<<<1, 128, 0, c->stream>>>(c->d_scenes, (int)k, c->d_samp_scene, c->d_samp_off, g.d_h[0], n);
             c->launches += 3;
         }
         for (const DftMon& m : c->mons) {
@@ -453,7 +585,11 @@ int fdtd_step_edgelist(fdtd_ctx* c, int64_t n_steps) {
         SceneGraph& g = G->g[k];
         const Scene2* s = c->s2[k];
         const int64_t ncell = (int64_t)s->nx * s->ny;
-        k_cells_nodes<<<(unsigned)((ncell + tb - 1) / tb), tb, 0, c->stream>>>(c->d_scenes, (int)k, c->parity, g.d_h[0], 1);
+        if (g.split)
+            k_cells_nodes_split<<<(unsigned)((ncell + tb - 1) / tb), tb, 0, c->stream>>>(c->d_scenes, (int)k, c->parity,
+                                                                                       g.d_h[0], 1);
+        else
+            k_cells_nodes<<<(unsigned)((ncell + tb - 1) / tb), tb, 0, c->stream>>>(c->d_scenes, (int)k, c->parity, g.d_h[0], 1);
         if (g.n_psi)
             k_psi_nodes<<<(g.n_psi + tb - 1) / tb, tb, 0, c->stream>>>(c->d_scenes, (int)k, c->parity, g.d_psi, g.n_psi,
                                                                       g.psi_base, g.d_h[0], 1);
@@ -480,20 +616,20 @@ int fdtd_export_graph(fdtd_ctx* c, int layer, int64_t* n_nodes, int64_t* n_edges
         return FDTD_EINVAL;
     }
     const Scene2* s = c->s2[c->cur];
-    if (s->split) {
-        c->err = "graph export covers the CPML and PEC boundaries, not the split-field PML";
-        return FDTD_EINVAL;
-    }
     HostScene h;
     int rc = fetch(c, s, h);
     if (rc) return rc;
-    std::vector<int> psi;
-    std::vector<int64_t> idx4;
-    psi_lists(h, psi, idx4);
     std::vector<int> rowptr, col;
     std::vector<float> ww;
-    build_layer(h, layer, psi, idx4, rowptr, col, ww);
-    if (layer == 2) apply_design(h, s, rowptr, col, ww, idx4);
+    if (h.split) {
+        build_layer_split(h, layer, rowptr, col, ww);
+    } else {
+        std::vector<int> psi;
+        std::vector<int64_t> idx4;
+        psi_lists(h, psi, idx4);
+        build_layer(h, layer, psi, idx4, rowptr, col, ww);
+        if (layer == 2) apply_design(h, s, rowptr, col, ww, idx4);
+    }
     const int64_t nn = (int64_t)rowptr.size() - 1;
     *n_nodes = nn;
     *n_edges = (int64_t)col.size();

@@ -78,8 +78,40 @@ def test_split_pml_refusals():
         sim.set_design(4, 40, np.full((8, 8), 2.0))       # overlaps the layer
     with pytest.raises(fdtd.FDTDError):
         sim.set_checkpointing(10)
-    with pytest.raises(fdtd.FDTDError):
-        sim.step_edgelist(1)
     sim.step(8)
     assert np.all(np.isfinite(sim.get_field("ez", (sc.ny, sc.nx))))
+    sim.close()
+
+
+def test_split_pml_literal_graph_matches_oracle(oracle_mod):
+    """The 4-node graph of Sec. III-B through fdtd_step_edgelist: fields and a
+    probe against the FP64 split-field oracle."""
+    from paper_2405_00814_gb300 import fdtd
+    sc = scenes.ellipse_scene(side=150, nsteps=400)
+    probes = [(75, 40), (150 - sc.npml - 2, 75)]
+    o = oracle_mod.TMzSplit(sc)
+    ref = o.run(sc.nsteps, samples=[(i, j, "ez") for i, j in probes])["samples"]
+    sim = fdtd.from_scene(sc, boundary="split", probes=False)
+    pids = [sim.add_probe(i, j) for i, j in probes]
+    sim.step_edgelist(sc.nsteps)
+    assert rel_l2(sim.get_field("ez", (sc.ny, sc.nx)), o.ez()) <= TOL_FIELD
+    assert rel_l2(sim.get_field("hx", (sc.ny, sc.nx)), o.state["hx"]) <= TOL_FIELD
+    assert rel_l2(np.stack([sim.read_probe(p, sc.nsteps) for p in pids], 1), ref) <= TOL_FIELD
+    sim.close()
+
+
+def test_split_pml_exported_graph_is_the_oracle_graph(oracle_mod):
+    """Same nodes, same edges in the same order, weights equal to FP32 rounding."""
+    from paper_2405_00814_gb300 import fdtd
+    sc = scenes.ellipse_scene(side=64, nsteps=10, npml=8)
+    o = oracle_mod.TMzSplit(sc)
+    sim = fdtd.from_scene(sc, boundary="split")
+    for layer in (1, 2):
+        n, src, dst, w = sim.export_graph(layer)
+        r, c, wo = o.graph_layer(layer)
+        assert n == 4 * sc.nx * sc.ny
+        dst_o = np.repeat(np.arange(n), np.diff(r))
+        assert np.array_equal(dst, dst_o)
+        assert np.array_equal(src, c)
+        assert np.max(np.abs(w - wo) / np.maximum(np.abs(wo), 1e-30)) <= 2e-6
     sim.close()
