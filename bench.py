@@ -309,6 +309,43 @@ def edgelist_throughput(stream, side=2048, nsteps=200):
             "bytes_per_cell_update": bpc, "hbm_frac": cu * bpc / (peak * 1e9), "ms_per_step": ms / nsteps}
 
 
+def split_pml_throughput(stream, side=4096, nsteps=200, side_graph=2048):
+    """The paper's own absorber (split-field PML, FDTD_SPLIT_PML) on the
+    heterogeneous scene: the unfused stencil pair at side^2 (with the same pair
+    under CPML beside it), and the literal 4-node graph at side_graph^2."""
+    import torch
+    from paper_2405_00814_gb300 import fdtd, scenes
+    peak, _ = _peaks()
+
+    def timed(sim, fn, n):
+        fn(4)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn(n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    out = {"workload": f"split_pml_tmz2d_{side}_ellipses_layer16_{nsteps}steps"}
+    sc = scenes.ellipse_scene(side=side)
+    for name, boundary in (("split_stencil", "split"), ("cpml_unfused", "cpml")):
+        sim = fdtd.from_scene(sc, stream=stream, boundary=boundary)
+        sim.set_option("kernel", 1)
+        ms = timed(sim, sim.step, nsteps)
+        sim.close()
+        cu = sc.cells * nsteps / (ms / 1e3)
+        out[name] = {"cell_updates_per_s": cu, "hbm_frac_at_37B_per_cell_update": cu * 37.0 / (peak * 1e9)}
+    sg = scenes.ellipse_scene(side=side_graph)
+    sim = fdtd.from_scene(sg, stream=stream, boundary="split")
+    ms = timed(sim, sim.step_edgelist, nsteps)
+    b = sum(8 * ne + 12 * nn for nn, ne in (sim.graph_size(1), sim.graph_size(2)))
+    sim.close()
+    cu = sg.cells * nsteps / (ms / 1e3)
+    out["split_edgelist"] = {"side": side_graph, "cell_updates_per_s": cu, "bytes_per_cell_update": b / sg.cells,
+                             "hbm_frac": cu * (b / sg.cells) / (peak * 1e9)}
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -355,7 +392,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every block from the host instead of replaying each solve from a CUDA graph")
-    ap.add_argument("--workload", default="main", choices=["main", "adjoint", "batch", "yee3d", "sweep", "edgelist"],
+    ap.add_argument("--workload", default="main",
+                    choices=["main", "adjoint", "batch", "yee3d", "sweep", "edgelist", "split"],
                     help="main: the JSON line of record; the others time one secondary workload alone "
                          "(for profiling; --nsteps and, for yee3d, --size, --kernel and --segment apply)")
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint-ratio measurement")
@@ -389,6 +427,8 @@ def main():
         elif args.workload == "yee3d":
             res = yee3d_throughput(stream, nsteps=args.nsteps or 200, side=args.size if args.size != 4096 else 512,
                                    kernel=args.kernel, segment=args.segment)
+        elif args.workload == "split":
+            res = split_pml_throughput(stream, nsteps=args.nsteps or 200)
         elif args.workload == "edgelist":
             res = edgelist_throughput(stream, side=args.size if args.size != 4096 else 2048, nsteps=args.nsteps or 200)
         else:
@@ -521,6 +561,7 @@ def main():
         out["yee3d"] = yee3d_throughput(stream)
         out["paper_sweep"] = paper_sweep(stream, None)
         out["edgelist"] = edgelist_throughput(stream)
+        out["split_pml"] = split_pml_throughput(stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sc, args.cpu_budget)
     if rank == 0:
