@@ -346,6 +346,31 @@ def split_pml_throughput(stream, side=4096, nsteps=200, side_graph=2048):
     return out
 
 
+def phc_waveguide_time(stream, reps=3):
+    """The photonic-crystal example (Sec. V-B: 75 THz pulse from a line source in
+    an eps_r = 12 waveguide with two groups of 3 air holes) solved to the end of
+    its 3000 steps with both probes: milliseconds per solve (best of reps) on
+    the default temporally blocked path, one CUDA-graph replay per solve."""
+    import torch
+    from paper_2405_00814_gb300 import fdtd, scenes
+    sc = scenes.phc_waveguide()
+    sim = fdtd.from_scene(sc, stream=stream)
+    sim.set_option("graph", 1)
+    best = None
+    for _ in range(reps + 1):
+        sim.reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(sc.nsteps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    sim.close()
+    return {"workload": f"phc_waveguide_{sc.nx}x{sc.ny}_line_source_{sc.nsteps}steps", "ms_per_solve": best,
+            "cell_updates_per_s": sc.cells * sc.nsteps / (best / 1e3)}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -562,6 +587,7 @@ def main():
         out["paper_sweep"] = paper_sweep(stream, None)
         out["edgelist"] = edgelist_throughput(stream)
         out["split_pml"] = split_pml_throughput(stream)
+        out["phc_waveguide"] = phc_waveguide_time(stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sc, args.cpu_budget)
     if rank == 0:

@@ -74,6 +74,7 @@ extern "C" {
 #define FDTD_SRC_GAUSS_MOD 1 /* params[0] = f0: e^{-((t-t0)/tg)^2} sin(2 pi f0 (t-t0)), tg = 1/f0, t0 = 4 tg */
 #define FDTD_SRC_GAUSS 2     /* params[0] = f_max: e^{-((t-t0)/tg)^2}, tg = 1/f_max, t0 = 4 tg */
 #define FDTD_SRC_SAMPLED 3   /* samples[n] = s((n+1) dt), n < n_samples; 0 after */
+#define FDTD_SRC_SINE 4      /* params[0] = f: sin(2 pi f t), switched on at t = 0 (Sec. V-A's sinusoidal source) */
 
 /* options (fdtd_set_option) */
 #define FDTD_OPT_KERNEL 0    /* 2D: 0 = fused temporally blocked stream, two kernels per T-step block (default);
@@ -142,6 +143,14 @@ int64_t fdtd_get_option(const fdtd_ctx* ctx, int option);
  * samples/n_samples for FDTD_SRC_SAMPLED (copied).  Replaces any earlier source. */
 int fdtd_set_source(fdtd_ctx* ctx, int kind, int i, int j, int k, int component, const double* params,
                     const float* samples, int64_t n_samples);
+
+/* 2D only: a line source -- every cell (i, j) with j0 <= j < j1 of column i gets
+ * the same waveform added to Ez after each E update, as the photonic-crystal
+ * example excites every cell across its waveguide (Sec. V-B).  Same kinds and
+ * arguments as fdtd_set_source; 1 <= i < nx, 1 <= j0 < j1 <= ny.  Replaces any
+ * earlier source (a point source is the line j1 = j0 + 1). */
+int fdtd_set_line_source(fdtd_ctx* ctx, int kind, int i, int j0, int j1, const double* params, const float* samples,
+                         int64_t n_samples);
 
 /* Continuous permittivity over a rectangle of the selected 2D scene -- the
  * design region of inverse design, where every cell has its own eps_r.  Cells

@@ -96,7 +96,7 @@ def cpml_axis(n, npml, delta, dt, m=CPML_M, alpha_max=CPML_ALPHA_MAX, kappa_max=
     return dict(zip(["bE", "cE", "kE", "bH", "cH", "kH"], arrs))
 
 
-_WAVE_KIND = {"ricker": 0, "gauss_mod": 1, "gauss": 2}
+_WAVE_KIND = {"ricker": 0, "gauss_mod": 1, "gauss": 2, "sine": 3}
 
 
 def waveform(kind: str, param: float, dt: float, nsteps: int) -> np.ndarray:
@@ -123,7 +123,7 @@ class _P2(C.Structure):
                 ("dt", C.c_double), ("ca", _dp), ("cb", _dp)] + \
                [(n, _dp) for n in ("bex", "cex", "kex", "bhx", "chx", "khx",
                                    "bey", "cey", "key", "bhy", "chy", "khy")] + \
-               [("src_i", C.c_int), ("src_j", C.c_int), ("src", _dp), ("src_len", C.c_int64)]
+               [("src_i", C.c_int), ("src_j", C.c_int), ("src", _dp), ("src_len", C.c_int64), ("src_nj", C.c_int)]
 
 
 class _S2(C.Structure):
@@ -189,8 +189,9 @@ class TMz:
         if self.source is not None and self.src is not None:
             p.src_i, p.src_j = self.source.i, self.source.j
             p.src, p.src_len = _p(self.src), len(self.src)
+            p.src_nj = getattr(self.source, "length", 1)
         else:
-            p.src_i, p.src_j, p.src, p.src_len = -1, -1, None, 0
+            p.src_i, p.src_j, p.src, p.src_len, p.src_nj = -1, -1, None, 0, 0
         self._p = p
         self._bind_state()
 
@@ -329,7 +330,7 @@ class _P2S(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("dx", C.c_double), ("dy", C.c_double),
                 ("dt", C.c_double), ("eps_cell", _dp), ("sig_cell", _dp), ("sxe", _dp), ("sxh", _dp),
                 ("sye", _dp), ("syh", _dp), ("src_i", C.c_int), ("src_j", C.c_int), ("src", _dp),
-                ("src_len", C.c_int64)]
+                ("src_len", C.c_int64), ("src_nj", C.c_int)]
 
 
 class _S2S(C.Structure):
@@ -373,8 +374,9 @@ class TMzSplit:
         p.sxe, p.sxh, p.sye, p.syh = _p(self.sxe), _p(self.sxh), _p(self.sye), _p(self.syh)
         if self.src is not None:
             p.src_i, p.src_j, p.src, p.src_len = self.source.i, self.source.j, _p(self.src), len(self.src)
+            p.src_nj = getattr(self.source, "length", 1)
         else:
-            p.src_i, p.src_j, p.src, p.src_len = -1, -1, None, 0
+            p.src_i, p.src_j, p.src, p.src_len, p.src_nj = -1, -1, None, 0, 0
         self._p = p
         self._bind()
 

@@ -127,6 +127,8 @@ void or_waveform(int kind, double param, double dt, int64_t nsteps, double* out)
             const double tg = 1.0 / param, t0 = 4.0 * tg;
             const double u = (t - t0) / tg;
             s = exp(-u * u);
+        } else if (kind == 3) {
+            s = sin(2.0 * OR_PI * param * t);
         }
         out[n] = s;
     }
@@ -202,7 +204,10 @@ int or2_run(const or2_problem* p, or2_state* s, int64_t n0, int64_t nsteps, or2_
         const int64_t n = n0 + k;
         or2_layer_h(p, s);
         or2_layer_e(p, s);
-        if (p->src_i >= 0 && p->src && n < p->src_len) s->ez[IDX2(p->src_i, p->src_j)] += p->src[n];
+        if (p->src_i >= 0 && p->src && n < p->src_len) {
+            const int nj = p->src_nj > 0 ? p->src_nj : 1;
+            for (int q = 0; q < nj; q++) s->ez[IDX2(p->src_i, p->src_j + q)] += p->src[n];
+        }
         or2_record(p, s, n, k, m);
     }
     return 0;
@@ -614,7 +619,8 @@ int or2_adjoint_grad(const or2_problem* p, const double* eps_cell, const double*
                     eseg[k * nd + (int64_t)dj * dw + dI] = s.ez[c];
                 }
             or2_layer_e(p, &s);
-            if (p->src_i >= 0 && p->src && n < p->src_len) s.ez[IDX2(p->src_i, p->src_j)] += p->src[n];
+            if (p->src_i >= 0 && p->src && n < p->src_len)
+                for (int q = 0; q < (p->src_nj > 0 ? p->src_nj : 1); q++) s.ez[IDX2(p->src_i, p->src_j + q)] += p->src[n];
         }
         for (int64_t k = len - 1; k >= 0; k--) {
             const int64_t n = a0 + k; /* reversing step n: E^n -> E^{n+1} */

@@ -49,7 +49,8 @@ void or_cpml_axis(int n, int npml, double delta, double dt, double m, double alp
 /* Source waveforms s(t) at t = (n+1) dt, n = 0 .. nsteps-1.
  * kind 0 Ricker(f_peak): (1 - 2 pi^2 f^2 tau^2) exp(-pi^2 f^2 tau^2), tau = t - 1.5/f.
  * kind 1 Gaussian-modulated(f0): exp(-((t - t0)/tg)^2) sin(2 pi f0 (t - t0)), tg = 1/f0, t0 = 4 tg.
- * kind 2 Gaussian(f_max): exp(-((t - t0)/tg)^2), tg = 1/f_max, t0 = 4 tg. */
+ * kind 2 Gaussian(f_max): exp(-((t - t0)/tg)^2), tg = 1/f_max, t0 = 4 tg.
+ * kind 3 sinusoid(f): sin(2 pi f t). */
 void or_waveform(int kind, double param, double dt, int64_t nsteps, double* out);
 
 /* ---- 2D TMz ------------------------------------------------------------- */
@@ -62,6 +63,7 @@ typedef struct {
     int src_i, src_j;                                      /* -1: no source */
     const double* src;                                     /* src[n] = s((n+1) dt) */
     int64_t src_len;
+    int src_nj;                                            /* cells (src_i, src_j .. src_j + src_nj - 1); 0 = 1 */
 } or2_problem;
 
 typedef struct {
@@ -111,6 +113,7 @@ typedef struct {
     int src_i, src_j;                                      /* soft source added to Ezx; -1: none */
     const double* src;
     int64_t src_len;
+    int src_nj;                                            /* line of src_nj cells along j; 0 = 1 */
 } or2s_problem;
 
 typedef struct {

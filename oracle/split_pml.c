@@ -129,7 +129,10 @@ int or2s_run(const or2s_problem* p, or2s_state* s, int64_t n0, int64_t nsteps, o
         const int64_t n = n0 + k;
         or2s_layer_h(p, s);
         or2s_layer_e(p, s);
-        if (p->src_i >= 0 && p->src && n < p->src_len) s->ezx[IX(p->src_i, p->src_j)] += p->src[n];
+        if (p->src_i >= 0 && p->src && n < p->src_len) {
+            const int nj = p->src_nj > 0 ? p->src_nj : 1;
+            for (int q = 0; q < nj; q++) s->ezx[IX(p->src_i, p->src_j + q)] += p->src[n];
+        }
         split_record(p, s, n, k, m);
     }
     return 0;

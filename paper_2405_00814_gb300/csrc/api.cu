@@ -158,6 +158,7 @@ double waveform(int kind, double p, double t) {
     const double tg = 1.0 / p, t0 = 4.0 * tg, u = (t - t0) / tg;
     if (kind == FDTD_SRC_GAUSS_MOD) return exp(-u * u) * sin(2.0 * M_PI * p * (t - t0));
     if (kind == FDTD_SRC_GAUSS) return exp(-u * u);
+    if (kind == FDTD_SRC_SINE) return sin(2.0 * M_PI * p * t);
     return 0.0;
 }
 
@@ -238,7 +239,7 @@ int scene2_init(fdtd_ctx* c, const fdtd_grid* g, double dx, double dt, double co
         s->eps_r[m] = table[m].eps_r;
         s->sigma[m] = table[m].sigma;
     }
-    s->src_kind = -1; s->src_i = -1; s->src_j = -1; s->src_param = 0; s->src_cap = 0;
+    s->src_kind = -1; s->src_i = -1; s->src_j = -1; s->src_j1 = -1; s->src_param = 0; s->src_cap = 0;
     s->rec_cap = 0;
     s->dsg_i0 = s->dsg_j0 = s->dsg_w = s->dsg_h = 0;
 
@@ -415,6 +416,7 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
         d.dby = (float)(s->dt / (kMu0 * s->dy));
         d.src_i = s->src_kind >= 0 ? s->src_i : -1;
         d.src_j = s->src_kind >= 0 ? s->src_j : -1;
+        d.src_j1 = s->src_kind >= 0 ? s->src_j1 : -1;
         d.src_wave = s->d_src;
         d.src_len = s->src_kind >= 0 ? s->src_cap : 0;
         d.rec = s->d_rec;
@@ -448,7 +450,7 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
             const int ly0 = ya - MAX_TB, ly1 = yb + MAX_TB;        // widest streamed rows
             if (s->npml > 0 && (lx0 < s->npml || lx1 > s->nx - s->npml || ly0 < s->npml || ly1 > s->ny - s->npml))
                 f |= TASK_PML;
-            if (s->src_kind >= 0 && s->src_i >= lx0 && s->src_i < lx1 && s->src_j >= ly0 && s->src_j < ly1)
+            if (s->src_kind >= 0 && s->src_i >= lx0 && s->src_i < lx1 && s->src_j < ly1 && s->src_j1 > ly0)
                 f |= TASK_SRC;
             if (s->d_dsg && s->dsg_i0 < lx1 && s->dsg_i0 + s->dsg_w > lx0 && s->dsg_j0 < ly1 && s->dsg_j0 + s->dsg_h > ly0)
                 f |= TASK_DSG;
@@ -769,12 +771,20 @@ int fdtd_set_source(fdtd_ctx* c, int kind, int i, int j, int k, int component, c
                     const float* samples, int64_t n_samples) {
     if (!c) return FDTD_EINVAL;
     if (c->dims == 3) return fdtd_set_source3(c, kind, i, j, k, component, params, samples, n_samples);
+    if (component != FDTD_EZ) return fail(c, FDTD_EINVAL, "2D TMz sources drive Ez only");
+    return fdtd_set_line_source(c, kind, i, j, j + 1, params, samples, n_samples);
+}
+
+int fdtd_set_line_source(fdtd_ctx* c, int kind, int i, int j0, int j1, const double* params, const float* samples,
+                         int64_t n_samples) {
+    if (!c) return FDTD_EINVAL;
+    if (c->dims != 2) return fail(c, FDTD_EINVAL, "line sources are 2D only");
     Scene2* s = cur2(c);
     if (!s) return fail(c, FDTD_ESTATE, "no scene");
-    if (component != FDTD_EZ) return fail(c, FDTD_EINVAL, "2D TMz sources drive Ez only");
-    if (i < 1 || i >= s->nx || j < 1 || j >= s->ny)
-        return fail(c, FDTD_EINVAL, "source cell (%d, %d) outside 1..nx-1 x 1..ny-1", i, j);
-    if (kind < FDTD_SRC_RICKER || kind > FDTD_SRC_SAMPLED) return fail(c, FDTD_EINVAL, "unknown source kind %d", kind);
+    if (i < 1 || i >= s->nx || j0 < 1 || j1 > s->ny || j1 <= j0)
+        return fail(c, FDTD_EINVAL, "source cells (%d, %d..%d) outside 1..nx-1 x 1..ny-1", i, j0, j1 - 1);
+    const int j = j0;
+    if (kind < FDTD_SRC_RICKER || kind > FDTD_SRC_SINE) return fail(c, FDTD_EINVAL, "unknown source kind %d", kind);
     if (kind == FDTD_SRC_SAMPLED) {
         if (!samples || n_samples < 0) return fail(c, FDTD_EINVAL, "sampled source needs samples");
         s->src_samples.assign(samples, samples + n_samples);
@@ -785,6 +795,7 @@ int fdtd_set_source(fdtd_ctx* c, int kind, int i, int j, int k, int component, c
     s->src_kind = kind;
     s->src_i = i;
     s->src_j = j;
+    s->src_j1 = j1;
     s->src_cap = 0;   // regenerate the waveform table
     c->dirty = true;
     return FDTD_OK;

@@ -49,7 +49,8 @@ struct TmzDev {
     int has_pml;
     int split;                          // split-field PML depth (profiles hold Ca, Cb/d, Da, Db/d per axis)
     float dbx, dby;             // dt / (mu0 dx), dt / (mu0 dy)
-    int src_i, src_j;           // soft source cell or -1
+    int src_i, src_j;           // soft source cell or -1 (a line: cells (src_i, src_j .. src_j1 - 1))
+    int src_j1;
     const float* src_wave;      // src_wave[n] = s((n+1) dt)
     long long src_len;
     float* rec;                 // sample record [cap][n_rec]
@@ -124,7 +125,7 @@ struct Scene2 {
     float4* d_coef;
     float* d_prof;
     // source
-    int src_kind, src_i, src_j;
+    int src_kind, src_i, src_j, src_j1;
     double src_param;
     std::vector<float> src_samples;
     float* d_src;

@@ -395,7 +395,8 @@ __global__ void k_graph_src_rec_split(const TmzDev* __restrict__ sc, int scene, 
                                       const int* __restrict__ samp_off, float* h, long long n) {
     const TmzDev& S = sc[scene];
     auto q_of = [&](int i, int j) { return 3 * (int64_t)i + (int64_t)S.nx * (4 * (int64_t)j + 1); };
-    if (threadIdx.x == 0 && S.src_i >= 0 && n < S.src_len) h[q_of(S.src_i, S.src_j) + 1] += S.src_wave[n];
+    if (S.src_i >= 0 && n < S.src_len)
+        for (int j = S.src_j + (int)threadIdx.x; j < S.src_j1; j += blockDim.x) h[q_of(S.src_i, j) + 1] += S.src_wave[n];
     __syncthreads();
     for (int q = samp_off[scene] + threadIdx.x; q < samp_off[scene + 1]; q += blockDim.x) {
         const Sample2 sp = samps[q];
@@ -410,8 +411,9 @@ __global__ void k_graph_src_rec_split(const TmzDev* __restrict__ sc, int scene, 
 __global__ void k_graph_src_rec(const TmzDev* __restrict__ sc, int scene, const Sample2* __restrict__ samps,
                                 const int* __restrict__ samp_off, float* h, long long n) {
     const TmzDev& S = sc[scene];
-    if (threadIdx.x == 0 && S.src_i >= 0 && n < S.src_len)
-        h[2 * (int64_t)S.src_i + 1 + (int64_t)S.nx * (3 * (int64_t)S.src_j + 1)] += S.src_wave[n];
+    if (S.src_i >= 0 && n < S.src_len)
+        for (int j = S.src_j + (int)threadIdx.x; j < S.src_j1; j += blockDim.x)
+            h[2 * (int64_t)S.src_i + 1 + (int64_t)S.nx * (3 * (int64_t)j + 1)] += S.src_wave[n];
     __syncthreads();
     for (int q = samp_off[scene] + threadIdx.x; q < samp_off[scene + 1]; q += blockDim.x) {
         const Sample2 sp = samps[q];

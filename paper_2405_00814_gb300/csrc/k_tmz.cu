@@ -170,7 +170,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
     if (lane < n_samp) my_samp = samps[tk.samp_begin + lane];
     // source: this launch's T waveform values ride in lanes 0..T-1
     const bool has_src = (tk.flags & TASK_SRC) != 0;
-    const int src_j = S->src_j, src_d = S->src_i - cx;
+    const int src_j = S->src_j, src_j1 = S->src_j1, src_d = S->src_i - cx;
     const long long src_len = S->src_len;
     float wv = 0.f;
     if (has_src && lane < T && n0 + lane < src_len) wv = S->src_wave[n0 + lane];
@@ -359,7 +359,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
             }
 
             const long long n = n0 + (t - 1);   // this level makes E^{n+1}
-            if (has_src && a == src_j) {
+            if (has_src && a >= src_j && a < src_j1) {
                 const float w = __shfl_sync(0xffffffffu, wv, t - 1);
                 if (src_d >= 0 && src_d < 4 && n < src_len) add4(E[t], src_d, w);
             }
@@ -832,8 +832,9 @@ __global__ void k_tmz_e(const TmzDev* __restrict__ scenes, int parity) {
 __global__ void k_tmz_src_rec(const TmzDev* __restrict__ scenes, const Sample2* __restrict__ samps,
                               const int* __restrict__ samp_off, int parity, long long n) {
     const TmzDev& S = scenes[blockIdx.x];
-    if (threadIdx.x == 0 && S.src_i >= 0 && n < S.src_len)
-        S.f[F_EZ][parity][sidx(S.pitch, S.src_i, S.src_j)] += S.src_wave[n];
+    if (S.src_i >= 0 && n < S.src_len)
+        for (int j = S.src_j + (int)threadIdx.x; j < S.src_j1; j += blockDim.x)
+            S.f[F_EZ][parity][sidx(S.pitch, S.src_i, j)] += S.src_wave[n];
     __syncthreads();
     for (int q = samp_off[blockIdx.x] + threadIdx.x; q < samp_off[blockIdx.x + 1]; q += blockDim.x) {
         const Sample2 sp = samps[q];

@@ -135,6 +135,7 @@ double wave3(int kind, double p, double t) {
     const double tg = 1.0 / p, t0 = 4.0 * tg, u = (t - t0) / tg;
     if (kind == FDTD_SRC_GAUSS_MOD) return exp(-u * u) * sin(2.0 * M_PI * p * (t - t0));
     if (kind == FDTD_SRC_GAUSS) return exp(-u * u);
+    if (kind == FDTD_SRC_SINE) return sin(2.0 * M_PI * p * t);
     return 0.0;
 }
 
@@ -862,7 +863,7 @@ int fdtd_set_source3(fdtd_ctx* c, int kind, int i, int j, int k, int comp, const
                       (comp == FDTD_EZ && (i < 1 || j < 1));
     if (i < 0 || j < 0 || k < 0 || i >= s->nx || j >= s->ny || k >= s->nz || wall)
         return fail3(c, FDTD_EINVAL, "source (%d, %d, %d) outside the grid or on a PEC wall", i, j, k);
-    if (kind < FDTD_SRC_RICKER || kind > FDTD_SRC_SAMPLED) return fail3(c, FDTD_EINVAL, "unknown source kind");
+    if (kind < FDTD_SRC_RICKER || kind > FDTD_SRC_SINE) return fail3(c, FDTD_EINVAL, "unknown source kind");
     if (kind == FDTD_SRC_SAMPLED) {
         if (!samples || n_samples < 0) return fail3(c, FDTD_EINVAL, "sampled source needs samples");
         s->src_samples.assign(samples, samples + n_samples);

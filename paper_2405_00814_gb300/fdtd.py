@@ -20,7 +20,7 @@ _LIB = None
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6
 PEC, CPML, SPLIT_PML = 0, 1, 2
 COMP = {"ex": 0, "ey": 1, "ez": 2, "hx": 3, "hy": 4, "hz": 5}
-SRC = {"ricker": 0, "gauss_mod": 1, "gauss": 2, "sampled": 3}
+SRC = {"ricker": 0, "gauss_mod": 1, "gauss": 2, "sampled": 3, "sine": 4}
 OPT = {"kernel": 0, "tblock": 1, "segment": 2, "warps": 3, "graph": 4, "spin_limit": 5, "debug_skip_cta": 6,
        "adj_store": 7}
 
@@ -62,6 +62,7 @@ def lib():
         L.fdtd_get_option.argtypes = [vp, ip]
         L.fdtd_get_option.restype = i64
         L.fdtd_set_source.argtypes = [vp, ip, ip, ip, ip, ip, dp, vp, i64]
+        L.fdtd_set_line_source.argtypes = [vp, ip, ip, ip, ip, dp, vp, i64]
         L.fdtd_set_design.argtypes = [vp, ip, ip, ip, ip, dp, dp]
         L.fdtd_add_probe.argtypes = [vp, ip, ip, ip, ip, C.POINTER(C.c_int)]
         L.fdtd_add_dft_monitor.argtypes = [vp, vp, ip, dp, ip, C.POINTER(C.c_int)]
@@ -226,7 +227,23 @@ class Simulation:
             rc = self._L.fdtd_set_source(self._h, SRC[kind], i, j, k, COMP[component], par, None, 0)
         self._check(rc)
 
+    def set_line_source(self, kind, i, j0, j1, param=None, samples=None):
+        """Ez of cells (i, j0 .. j1-1) all get the same waveform (2D)."""
+        par = (C.c_double * 1)(float(param) if param is not None else 0.0)
+        if samples is not None:
+            smp = np.ascontiguousarray(samples, np.float32)
+            rc = self._L.fdtd_set_line_source(self._h, SRC[kind], i, j0, j1, par, smp.ctypes.data, len(smp))
+        else:
+            rc = self._L.fdtd_set_line_source(self._h, SRC[kind], i, j0, j1, par, None, 0)
+        self._check(rc)
+
     def set_scene_source(self, src):
+        if getattr(src, "length", 1) > 1:
+            if src.kind == "sampled":
+                self.set_line_source("sampled", src.i, src.j, src.j + src.length, samples=src.samples)
+            else:
+                self.set_line_source(src.kind, src.i, src.j, src.j + src.length, param=src.params[0])
+            return
         if src.kind == "sampled":
             self.set_source("sampled", src.i, src.j, src.k, src.component, samples=src.samples)
         else:
@@ -328,6 +345,17 @@ class Simulation:
         arr = np.empty(shape, np.float32) if out is None else out
         self._check(self._L.fdtd_get_field(self._h, COMP[component], arr.ctypes.data, 0))
         return arr
+
+    def get_field_te(self, component, shape):
+        """A 2D field under the paper's own TE naming (Sec. II-B: Ey, Hx, Hz in the
+        x-z plane, k the second index).  The library computes TMz; the rotation
+        x' = x, y' = z, z' = -y maps Ey = -Ez', Hx = Hx', Hz = Hy' with cell (i, j)
+        <-> (i, k), so "ey", "hx", "hz" are read from "ez" (negated), "hx", "hy".
+        The node numbering of the literal graph (t, u, q) is the paper's with
+        k -> j (fdtd_export_graph)."""
+        if component == "ey":
+            return -self.get_field("ez", shape)
+        return self.get_field({"hx": "hx", "hz": "hy"}[component], shape)
 
     def set_field(self, component, values):
         if hasattr(values, "data_ptr"):

@@ -41,14 +41,15 @@ def _u(rng, lo, hi, size=None):
 @dataclass
 class Source:
     """A soft point source: the field component at a cell gets s(t) added after
-    each E update.  kind is 'ricker', 'gauss_mod', 'gauss' or 'sampled'."""
+    each E update.  kind is 'ricker', 'gauss_mod', 'gauss', 'sine' or 'sampled'."""
     i: int
     j: int
     k: int = 0
     component: str = "ez"
     kind: str = "ricker"
-    params: tuple = ()            # ricker: (f_peak,); gauss_mod: (f0,); gauss: (f_max,)
+    params: tuple = ()            # ricker: (f_peak,); gauss_mod: (f0,); gauss: (f_max,); sine: (f,)
     samples: np.ndarray | None = None   # kind == 'sampled': s((n+1) dt) for n = 0..
+    length: int = 1               # 2D line source: cells (i, j .. j + length - 1)
 
 
 @dataclass
@@ -307,6 +308,43 @@ def box_scene(side: int = 512, nsteps: int = 2000, npml: int = 10, n_boxes: int 
                    source=Source(c, c, c, component="ez", kind="gauss", params=(f_max,)),
                    dft_plane_k=(3 * side) // 4, freqs=np.array([2.5e9, 5.0e9, 7.5e9]),
                    name=f"yee{side}_boxes_cpml{npml}")
+
+
+def phc_waveguide(nsteps: int = 3000, npml: int = 16, width_um: float = 1.2) -> Scene2D:
+    """The photonic-crystal example (Sec. V-B): a dielectric waveguide (eps_r = 12)
+    along x, periodic in one dimension by two groups of 3 round air holes of
+    radius 0.36 um, 1 um apart within a group, the groups 1.4 um apart; a line
+    source across the waveguide near its start driven by a 75 THz
+    Gaussian-modulated pulse.  The paper gives no waveguide width (1.2 um here),
+    domain size or probe position; dx is 20 points per the shortest wavelength
+    (f_max = 150 THz in eps_r = 12) and dt 0.99 of the Courant limit.  Probes: on
+    the axis in the gap between the groups and past the holes.  Deterministic:
+    no random draws."""
+    um = 1e-6
+    f0 = 75e12
+    dx = _dx_for(2 * f0, 12.0, 20)
+    dt = _dt_2d(dx, dx)
+    lx, ly = 12.0 * um, 5.0 * um
+    nx, ny = int(round(lx / dx)), int(round(ly / dx))
+    mat = np.zeros((ny, nx), np.uint8)
+    x = np.arange(nx)[None, :] * dx
+    y = np.arange(ny)[:, None] * dx
+    xc, yc = lx / 2, ly / 2
+    mat[np.broadcast_to(np.abs(y - yc) <= width_um * um / 2, (ny, nx))] = 1
+    for k in range(3):
+        for sgn in (-1.0, 1.0):
+            hx = xc + sgn * (0.7 + k * 1.0) * um
+            mat[(x - hx) ** 2 + (y - yc) ** 2 <= (0.36 * um) ** 2] = 0
+    mat[:npml, :] = 0
+    mat[-npml:, :] = 0
+    mat[:, :npml] = 0
+    mat[:, -npml:] = 0
+    jc = int(round(yc / dx))
+    half = int(width_um * um / 2 / dx)
+    src = Source(int(round(1.0 * um / dx)), jc - half, kind="gauss_mod", params=(f0,), length=2 * half + 1)
+    probes = np.array([[int(round(xc / dx)), jc], [int(round((lx - 1.0 * um) / dx)), jc]], np.int32)
+    return Scene2D(nx=nx, ny=ny, dx=dx, dy=dx, dt=dt, npml=npml, mat=mat, eps_r=np.array([1.0, 12.0]),
+                   sigma=np.array([0.0, 0.0]), nsteps=nsteps, source=src, probes=probes, name="phc_waveguide")
 
 
 def free_space(side: int, nsteps: int = 1024, npml: int = 16) -> Scene2D:

@@ -274,3 +274,36 @@ def test_cpml_reflection_bound(oracle_mod, npml, bound_db):
     refl = np.max(np.abs(small - big)) / np.max(np.abs(big))
     assert 20 * math.log10(refl) < bound_db
     del src
+
+
+def test_sine_source_closed_form_and_period(oracle_mod):
+    """The sinusoidal source (Sec. V-A) is s(t) = sin(2 pi f t) from t = 0: peaks
+    +1 / -1 a quarter and three quarters into each period, zero at half periods,
+    and periodic with 1/f."""
+    f = 3e9
+    for t, v in [(0.25 / f, 1.0), (0.75 / f, -1.0), (0.5 / f, 0.0), (7.25 / f, 1.0)]:
+        n = 29
+        s = oracle_mod.waveform("sine", f, t / (n + 1), n + 1)
+        assert abs(s[n] - v) < 1e-12
+    dt = 1 / (f * 40)           # exactly 40 steps per period
+    s = oracle_mod.waveform("sine", f, dt, 200)
+    assert np.max(np.abs(s[40:] - s[:-40])) < 1e-12
+
+
+def test_line_source_is_the_sum_of_point_sources(oracle_mod):
+    """The recurrence is linear, so a line source over cells (i, j0 .. j1-1) must
+    give the sum of the runs of point sources at those cells (heterogeneous lossy
+    medium with a CPML): a cell skipped, doubled or misplaced fails it."""
+    sc = scenes.ellipse_scene(side=80, nsteps=150)
+    i, j0, j1 = 23, 30, 37
+    line = scenes.Source(i, j0, kind="gauss_mod", params=(20e9,), length=j1 - j0)
+    sim = oracle_mod.TMz(sc, source=line, nsteps_src=sc.nsteps)
+    sim.run(sc.nsteps)
+    total = {k: np.zeros((sc.ny, sc.nx)) for k in ("ez", "hx", "hy")}
+    for j in range(j0, j1):
+        pt = oracle_mod.TMz(sc, source=scenes.Source(i, j, kind="gauss_mod", params=(20e9,)), nsteps_src=sc.nsteps)
+        pt.run(sc.nsteps)
+        for k in total:
+            total[k] += pt.state[k]
+    for k in total:
+        assert np.max(np.abs(sim.state[k] - total[k])) <= 1e-12 * np.max(np.abs(total[k])), k
