@@ -136,11 +136,15 @@ class Simulation:
         self._L = lib()
         self._h = None
         self.dims = 2
+        self.shape = None           # (nx, ny, nz) of a single-scene context
+        self.split = False
         if _handle is not None:
             self._h = _handle
             return
         g = _grid_of(scene, boundary)
         self.dims = g.dims
+        self.shape = (g.nx, g.ny, g.nz)
+        self.split = g.boundary == SPLIT_PML
         mat = np.ascontiguousarray(scene.mat, np.uint8)
         tab = _mat_table(scene.eps_r, scene.sigma)
         h = C.c_void_p()
@@ -412,7 +416,19 @@ class Simulation:
         self._check(self._L.fdtd_export_graph(self._h, layer, C.byref(nn), C.byref(ne), None, None, None))
         return nn.value, ne.value
 
-    def export_graph(self, layer: int):
+    def export_graph(self, layer: int, te: bool = False):
+        """(n_nodes, src, dst, w) of one message-passing layer (Prop. 1/2).  te:
+        weights for node values under the paper's TE naming (Ey = -Ez on the
+        electric nodes, te_node_signs); the numbering is the same."""
+        n, src, dst, w = self._export_graph(layer)
+        if te:
+            if self.shape is None:
+                raise ValueError("te=True needs a single-scene context")
+            sg = te_node_signs(self.shape[0], self.shape[1], n, self.split)
+            w = w * sg[src] * sg[dst]
+        return n, src, dst, w
+
+    def _export_graph(self, layer: int):
         nn, ne = C.c_int64(), C.c_int64()
         self._check(self._L.fdtd_export_graph(self._h, layer, C.byref(nn), C.byref(ne), None, None, None))
         src = np.empty(ne.value, np.int32)
@@ -421,6 +437,25 @@ class Simulation:
         self._check(self._L.fdtd_export_graph(self._h, layer, C.byref(nn), C.byref(ne), src.ctypes.data,
                                               dst.ctypes.data, w.ctypes.data))
         return nn.value, src, dst, w
+
+
+def te_node_signs(nx: int, ny: int, n_nodes: int, split: bool = False) -> np.ndarray:
+    """+1 or -1 per node of the exported graph: -1 on the electric nodes (t of
+    Prop. 1; tx and tz of the split-field graph, Sec. III-B), whose value is Ez
+    in the library's TMz and Ey = -Ez under the paper's TE naming.  Magnetic and
+    auxiliary (CPML) nodes keep their sign.  With S = diag(signs) the TE layer is
+    S W S, and S h maps node values between the two namings."""
+    idx = np.arange(n_nodes)
+    per = 4 if split else 3
+    r = idx % (per * nx)
+    grid = idx < per * nx * ny
+    if split:
+        e = grid & (r >= nx) & ((r - nx) % 3 != 0)      # (q, tx, tz) triples after the u block
+    else:
+        e = grid & (r >= nx) & ((r - nx) % 2 == 1)      # (q, t) pairs after the u block
+    sg = np.ones(n_nodes, np.float32)
+    sg[e] = -1.0
+    return sg
 
 
 MP_NOALLOC_MAX_NODES = 1 << 22

@@ -59,3 +59,39 @@ def test_sine_line_source_paths(path, opts):
     g = _run(sc, sc.nsteps, path, **opts)
     assert_fields_close(g, o)
     assert rel_l2(g["probes"], o["probes"]) <= TOL_FIELD
+
+
+def test_te_graph_export_steps_te_fields():
+    """The library's exported graph under the TE naming (export_graph(te=True))
+    advances TE node values built from get_field_te as the GPU step does."""
+    from paper_2405_00814_gb300 import fdtd
+    sc = scenes.ellipse_scene(side=64, nsteps=1, npml=0)
+    rng = np.random.default_rng(3)
+    sim = fdtd.from_scene(sc, source=False, probes=False, monitors=False)
+    ez = rng.standard_normal((sc.ny, sc.nx)).astype(np.float32)
+    ez[0, :] = 0.0
+    ez[:, 0] = 0.0
+    sim.set_field("ez", ez)
+    sim.set_field("hx", rng.standard_normal((sc.ny, sc.nx)).astype(np.float32))
+    sim.set_field("hy", rng.standard_normal((sc.ny, sc.nx)).astype(np.float32))
+    shp = (sc.ny, sc.nx)
+    te = {c: sim.get_field_te(c, shp).astype(np.float64) for c in ("ey", "hx", "hz")}
+    n, src, dst, w1 = sim.export_graph(1, te=True)
+    _, src2, dst2, w2 = sim.export_graph(2, te=True)
+    nx = sc.nx
+    h = np.zeros(n)
+    for j in range(sc.ny):
+        b = 3 * j * nx
+        h[b:b + nx] = te["hx"][j]                       # u = i + 3 k nx
+        h[b + nx:b + 3 * nx:2] = te["hz"][j]            # q = 2 i + nx (3 k + 1)
+        h[b + nx + 1:b + 3 * nx:2] = te["ey"][j]        # t = 2 i + 1 + nx (3 k + 1)
+    h1 = np.zeros(n)
+    np.add.at(h1, dst, w1 * h[src])
+    h2 = np.zeros(n)
+    np.add.at(h2, dst2, w2 * h1[src2])
+    sim.step(1)
+    for name, sl in (("ey", lambda b: slice(b + nx + 1, b + 3 * nx, 2)), ("hz", lambda b: slice(b + nx, b + 3 * nx, 2)),
+                     ("hx", lambda b: slice(b, b + nx))):
+        got = np.stack([h2[sl(3 * j * nx)] for j in range(sc.ny)])
+        assert rel_l2(got, sim.get_field_te(name, shp)) <= 1e-5, name
+    sim.close()
