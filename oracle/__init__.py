@@ -10,7 +10,8 @@ the seeded inputs from ``paper_2405_00814_gb300.scenes``.
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
 tests/test_oracle_*.py (closed-form cavity modes, the 2x2 lossy-mode recurrence,
 exact discrete energy, Courant blow-up, mirror symmetry, graph = stencil,
-adjoint dot-product and finite differences).  The CPML profile choice itself has
+adjoint dot-product and finite differences; the edge-weight reverse mode by
+finite differences in single weights and by its chain to the eps_r gradient).  The CPML profile choice itself has
 no closed form; it is checked by a reflection bound against an enlarged domain.
 """
 from __future__ import annotations
@@ -320,6 +321,110 @@ class TMz:
         if rc != 0:
             raise RuntimeError(f"or2_adjoint_grad failed ({rc})")
         return loss.value, fre, fim, grad
+
+
+    # ---- learnable edge weights: reverse mode over the literal graph ----
+    # The 11 weights a cell (i, j) owns as a destination (Prop. 1, TMz naming),
+    # as (layer, destination kind, source kind, di, dj of the source).
+    EDGE_CLASSES = (
+        (2, "t", "t", 0, 0),    # Ez <- Ez        Ca            (eq. 7)
+        (2, "t", "q", 0, 0),    # Ez <- Hy(i)     +Cb/dx
+        (2, "t", "q", -1, 0),   # Ez <- Hy(i-1)   -Cb/dx
+        (2, "t", "u", 0, 0),    # Ez <- Hx(j)     -Cb/dy
+        (2, "t", "u", 0, -1),   # Ez <- Hx(j-1)   +Cb/dy
+        (1, "u", "u", 0, 0),    # Hx <- Hx        1             (eq. 8)
+        (1, "u", "t", 0, 1),    # Hx <- Ez(j+1)   -Db/dy
+        (1, "u", "t", 0, 0),    # Hx <- Ez(j)     +Db/dy
+        (1, "q", "q", 0, 0),    # Hy <- Hy        1             (eq. 9)
+        (1, "q", "t", 1, 0),    # Hy <- Ez(i+1)   +Db/dx
+        (1, "q", "t", 0, 0),    # Hy <- Ez(i)     -Db/dx
+    )
+
+    def source_nodes(self):
+        """Electric nodes that receive the soft source (one per cell of a line)."""
+        if self.source is None or self.src is None:
+            return np.zeros(0, np.int64)
+        nj = max(1, getattr(self.source, "length", 1))
+        return np.array([self.node_index("t", self.source.i, self.source.j + q) for q in range(nj)], np.int64)
+
+    def graph_forward(self, nsteps, layers=None, monitors=None, freqs=None, keep=False):
+        """nsteps of Prop. 2 on node values, from the current state: h <- W2 (W1 h),
+        then the soft source s[n] on the source's electric nodes and the running
+        DFT F(f) += Ez^{n+1} exp(-i 2 pi f (n+1) dt) dt at the monitor cells.
+        layers: ((rowptr, col, w) of layer 1, of layer 2), default graph_layer.
+        Returns (h, F [n_mon, n_freq] complex, [h^n before each step] if keep).
+        Does not change self.state."""
+        W1, W2 = layers if layers is not None else (self.graph_layer(1), self.graph_layer(2))
+        h = self.to_nodes()
+        tm = np.array([self.node_index("t", int(i), int(j)) for i, j in monitors], np.int64) \
+            if monitors is not None else np.zeros(0, np.int64)
+        fr = np.asarray(freqs if freqs is not None else [], np.float64)
+        F = np.zeros((len(tm), len(fr)), np.complex128)
+        ts = self.source_nodes()
+        hist = []
+        for k in range(nsteps):
+            n = self.n + k
+            if keep:
+                hist.append(h)
+            h = TMz.csr_mv(*W2, TMz.csr_mv(*W1, h))
+            if len(ts) and n < len(self.src):
+                h[ts] += self.src[n]
+            if len(tm):
+                F += h[tm][:, None] * np.exp(-2j * np.pi * fr[None, :] * ((n + 1) * self.dt)) * self.dt
+        return h, F, hist
+
+    def graph_edge_grad(self, nsteps, monitors, freqs, dLdF_re, dLdF_im):
+        """Reverse mode of graph_forward for the linear loss
+        L = sum_{m,f} dLdF_re[m,f] Re F[m,f] + dLdF_im[m,f] Im F[m,f]:
+        dL/dw for every edge of both layers, in the CSR order of graph_layer.
+        With lam the adjoint of the node vector after step n, the layers are
+        reversed newest first: dL/dw2[e] += lam[dst] h1^n[src], lam1 = W2^T lam,
+        dL/dw1[e] += lam1[dst] h^n[src], lam = W1^T lam1; dL/dEz^n at the monitors
+        is dt sum_f (dLdF_re cos(2 pi f n dt) - dLdF_im sin(2 pi f n dt)).
+        Returns (g1, g2, F)."""
+        W1, W2 = self.graph_layer(1), self.graph_layer(2)
+        nn = len(W1[0]) - 1
+        dst1 = np.repeat(np.arange(nn), np.diff(W1[0]))
+        dst2 = np.repeat(np.arange(nn), np.diff(W2[0]))
+        _, F, hist = self.graph_forward(nsteps, (W1, W2), monitors, freqs, keep=True)
+        tm = np.array([self.node_index("t", int(i), int(j)) for i, j in monitors], np.int64)
+        fr = np.asarray(freqs, np.float64)
+        a = np.asarray(dLdF_re, np.float64).reshape(len(tm), len(fr))
+        b = np.asarray(dLdF_im, np.float64).reshape(len(tm), len(fr))
+        g1 = np.zeros(len(W1[2]))
+        g2 = np.zeros(len(W2[2]))
+        lam = np.zeros(nn)
+        for k in range(nsteps - 1, -1, -1):
+            ph = 2 * np.pi * fr * ((self.n + k + 1) * self.dt)
+            np.add.at(lam, tm, self.dt * (a @ np.cos(ph) - b @ np.sin(ph)))
+            h0 = hist[k]
+            h1 = TMz.csr_mv(*W1, h0)
+            g2 += lam[dst2] * h1[W2[1]]
+            lam1 = TMz.csr_mtv(*W2, lam)
+            g1 += lam1[dst1] * h0[W1[1]]
+            lam = TMz.csr_mtv(*W1, lam1)
+        return g1, g2, F
+
+    def edge_class_grad(self, g1, g2, design):
+        """The 11 per-cell edge classes (EDGE_CLASSES) of the cells of design =
+        (i0, j0, w, h), picked out of per-edge gradients in CSR order:
+        [11, h, w]."""
+        i0, j0, w, h = design
+        lay = {1: (self.graph_layer(1), g1), 2: (self.graph_layer(2), g2)}
+        out = np.zeros((len(self.EDGE_CLASSES), h, w))
+        for ci, (layer, kd, ks, di, dj) in enumerate(self.EDGE_CLASSES):
+            (rowptr, col, _), g = lay[layer]
+            for jj in range(h):
+                for ii in range(w):
+                    i, j = i0 + ii, j0 + jj
+                    d = self.node_index(kd, i, j)
+                    sidx = self.node_index(ks, i + di, j + dj)
+                    row = np.arange(rowptr[d], rowptr[d + 1])
+                    hit = row[col[row] == sidx]
+                    if len(hit) != 1:
+                        raise ValueError(f"edge class {ci} missing at ({i}, {j})")
+                    out[ci, jj, ii] = g[hit[0]]
+        return out
 
 
 # ---------------------------------------------------------------------------------
