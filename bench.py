@@ -195,7 +195,8 @@ def adjoint_ratio(stream, reps=2, nsteps=None):
     """Time of one adjoint gradient (forward with checkpoints every 100 steps +
     reverse sweep) over the time of one plain forward solve, on the 1024^2
     inverse-design workload (8 designs, 256^2 design regions, 8 monitors,
-    3000 steps)."""
+    3000 steps): dL/deps_r, and dL/dw of the 11 edge classes of every design
+    cell (fdtd_edge_grad)."""
     import numpy as np
     import torch
     from paper_2405_00814_gb300 import autograd, scenes
@@ -218,9 +219,13 @@ def adjoint_ratio(stream, reps=2, nsteps=None):
     t_grad = t_of(lambda: ckpt.gradient(2.0 * ckpt.forward(eps)))
     plain.close()
     ckpt.close()
+    edges = autograd.DesignBatch(scs, ckpt_every=100, stream=stream, edges=True)
+    t_edge = t_of(lambda: edges.edge_gradient(2.0 * edges.forward(eps)))
+    edges.close()
     cu = scs[0].cells * len(scs) * scs[0].nsteps
     return {"workload": f"adjoint_tmz2d_1024x1024_x8designs_{scs[0].nsteps}steps_ckpt100", "forward_ms": 1e3 * t_fwd,
             "gradient_ms": 1e3 * t_grad, "ratio": t_grad / t_fwd, "forward_cups": cu / t_fwd,
+            "edge_gradient_ms": 1e3 * t_edge, "edge_ratio": t_edge / t_fwd,
             "timing": "host wall clock around synchronised calls, best of %d after one warm-up" % reps}
 
 
@@ -350,11 +355,13 @@ def phc_waveguide_time(stream, reps=3):
     """The photonic-crystal example (Sec. V-B: 75 THz pulse from a line source in
     an eps_r = 12 waveguide with two groups of 3 air holes) solved to the end of
     its 3000 steps with both probes: milliseconds per solve (best of reps) on
-    the default temporally blocked path, one CUDA-graph replay per solve."""
+    the temporally blocked path with the autotuner's options, one CUDA-graph
+    replay per solve."""
     import torch
     from paper_2405_00814_gb300 import fdtd, scenes
     sc = scenes.phc_waveguide()
     sim = fdtd.from_scene(sc, stream=stream)
+    tune = sim.autotune()
     sim.set_option("graph", 1)
     best = None
     for _ in range(reps + 1):
@@ -368,6 +375,7 @@ def phc_waveguide_time(stream, reps=3):
         best = ms if best is None else min(best, ms)
     sim.close()
     return {"workload": f"phc_waveguide_{sc.nx}x{sc.ny}_line_source_{sc.nsteps}steps", "ms_per_solve": best,
+            "options": tune["options"],
             "cell_updates_per_s": sc.cells * sc.nsteps / (best / 1e3)}
 
 
@@ -418,7 +426,7 @@ def main():
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every block from the host instead of replaying each solve from a CUDA graph")
     ap.add_argument("--workload", default="main",
-                    choices=["main", "adjoint", "batch", "yee3d", "sweep", "edgelist", "split"],
+                    choices=["main", "adjoint", "batch", "yee3d", "sweep", "edgelist", "split", "phc"],
                     help="main: the JSON line of record; the others time one secondary workload alone "
                          "(for profiling; --nsteps and, for yee3d, --size, --kernel and --segment apply)")
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint-ratio measurement")
@@ -456,6 +464,8 @@ def main():
             res = split_pml_throughput(stream, nsteps=args.nsteps or 200)
         elif args.workload == "edgelist":
             res = edgelist_throughput(stream, side=args.size if args.size != 4096 else 2048, nsteps=args.nsteps or 200)
+        elif args.workload == "phc":
+            res = phc_waveguide_time(stream)
         else:
             res = paper_sweep(stream, None)
         if rank == 0:

@@ -94,7 +94,10 @@ extern "C" {
 #define FDTD_OPT_ADJ_STORE 7 /* reverse mode, read by fdtd_set_checkpointing: 1 (default) = the forward pass keeps
                                 E^{n+1} - E^n over every design rectangle for every step in device memory
                                 (steps x design cells x 4 B) and fdtd_adjoint_grad needs no recompute;
-                                0 = keep field checkpoints only and recompute each segment (less memory) */
+                                0 = keep field checkpoints only and recompute each segment (less memory);
+                                2 = for fdtd_edge_grad: the forward advances one step per launch and keeps
+                                Ez, Hx, Hy of the window one cell wider than each design rectangle after
+                                every step (steps x (w + 2)(h + 2) x 12 B) */
 
 typedef struct fdtd_ctx fdtd_ctx;
 
@@ -269,6 +272,32 @@ int fdtd_set_checkpointing(fdtd_ctx* ctx, int every);
  * 0).  The fields are left in an unspecified state: call fdtd_reset before the
  * next forward run. */
 int fdtd_adjoint_grad(fdtd_ctx* ctx, const float* dLdF_re, const float* dLdF_im, float* grad, int on_device);
+
+/* Learnable edge weights.  The paper's layers have fixed weights read off the
+ * update equations, and it notes that message-passing layers are differentiable
+ * (Sec. III-A); this is the gradient of the same loss as fdtd_adjoint_grad with
+ * respect to each weight of the graph of Prop. 1 whose destination node belongs
+ * to a design cell (i, j), treating every weight as an independent parameter.
+ * A cell owns FDTD_EDGE_CLASSES weights, in this order (destination <- source,
+ * TMz names, the weight's physical value in brackets, eqs. (7)-(9)):
+ *   layer 2:  0 Ez(i,j) <- Ez(i,j) [Ca]       1 Ez(i,j) <- Hy(i,j) [Cb/dx]
+ *             2 Ez(i,j) <- Hy(i-1,j) [-Cb/dx] 3 Ez(i,j) <- Hx(i,j) [-Cb/dy]
+ *             4 Ez(i,j) <- Hx(i,j-1) [Cb/dy]
+ *   layer 1:  5 Hx(i,j) <- Hx(i,j) [1]        6 Hx(i,j) <- Ez(i,j+1) [-Db/dy]
+ *             7 Hx(i,j) <- Ez(i,j) [Db/dy]    8 Hy(i,j) <- Hy(i,j) [1]
+ *             9 Hy(i,j) <- Ez(i+1,j) [Db/dx] 10 Hy(i,j) <- Ez(i,j) [-Db/dx]
+ * with Db = dt / mu0.  dL/dw = sum over steps n of (dL/d destination after the
+ * layer) x (source before the layer): dL/dE^{n+1} x (E^n or H^{n+1/2}) for layer 2,
+ * dL/dH^{n+1/2} x (E^n or H^{n-1/2}) for layer 1.
+ * Needs a forward run of N >= 1 steps from reset with FDTD_OPT_ADJ_STORE = 2 set
+ * before fdtd_set_checkpointing (FDTD_ESTATE otherwise), every scene with a
+ * design rectangle whose one-cell ring lies outside the CPML and inside the grid
+ * (the forward returns FDTD_EINVAL at its first step otherwise).  dLdF_re,
+ * dLdF_im: as for fdtd_adjoint_grad.  grad receives [scene][FDTD_EDGE_CLASSES][h][w]
+ * floats (host, or device when on_device != 0).  The fields are left in an
+ * unspecified state: call fdtd_reset before the next forward run. */
+#define FDTD_EDGE_CLASSES 11
+int fdtd_edge_grad(fdtd_ctx* ctx, const float* dLdF_re, const float* dLdF_im, float* grad, int on_device);
 
 /* Largest graph fdtd_mp_steps_noalloc accepts (nodes). */
 #define FDTD_MP_NOALLOC_MAX_NODES (1 << 22)

@@ -19,9 +19,12 @@ class DesignBatch:
     Each scene needs a source, DFT monitor cells + frequencies and a design
     rectangle (paper_2405_00814_gb300.scenes.adjoint_scenes builds such scenes)."""
 
-    def __init__(self, scenes, *, ckpt_every=100, stream=None, tblock=4, segment=24, warps=8, store=True):
+    def __init__(self, scenes, *, ckpt_every=100, stream=None, tblock=4, segment=24, warps=8, store=True,
+                 edges=False):
         """store: keep the forward pass's design-region history in device memory
-        (no recompute in the gradient); False keeps field checkpoints only."""
+        (no recompute in the gradient); False keeps field checkpoints only.
+        edges: record the forward for edge_gradient (dL/dw of the 11 weights each
+        design cell owns) instead of gradient."""
         self.scenes = scenes
         self.nsteps = scenes[0].nsteps
         self.sim = fdtd.Simulation.batch(scenes, stream=stream)
@@ -35,7 +38,7 @@ class DesignBatch:
         self.sim.set_option("tblock", tblock)
         self.sim.set_option("segment", segment)
         self.sim.set_option("warps", warps)
-        self.sim.set_option("adj_store", int(bool(store)))
+        self.sim.set_option("adj_store", 2 if edges else int(bool(store)))
         self.sim.set_checkpointing(ckpt_every)
         self.design_shape = (len(scenes), scenes[0].design[3], scenes[0].design[2])
 
@@ -53,6 +56,11 @@ class DesignBatch:
     def gradient(self, dLdF, out=None):
         """dL/deps_r [B, h, w] for dL/dF (complex, same shape as forward's F)."""
         return self.sim.adjoint_grad([dLdF[k] for k in range(len(self.scenes))], self.design_shape, out=out)
+
+    def edge_gradient(self, dLdF):
+        """dL/dw [B, 11, h, w] of the edge classes of fdtd_edge_grad (needs edges=True)."""
+        shapes = [(sc.design[3], sc.design[2]) for sc in self.scenes]
+        return np.stack(self.sim.edge_grad([dLdF[k] for k in range(len(self.scenes))], shapes))
 
     def close(self):
         self.sim.close()

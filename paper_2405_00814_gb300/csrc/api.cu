@@ -729,7 +729,7 @@ int fdtd_set_option(fdtd_ctx* c, int option, int64_t v) {
             c->opt_debug_skip = (int)v;
             return FDTD_OK;
         case FDTD_OPT_ADJ_STORE:
-            if (v < 0 || v > 1) return fail(c, FDTD_EINVAL, "adjoint store option must be 0 or 1");
+            if (v < 0 || v > 2) return fail(c, FDTD_EINVAL, "adjoint store option must be 0, 1 or 2");
             c->opt_adj_store = (int)v;
             return FDTD_OK;
         case FDTD_OPT_TBLOCK:
@@ -928,6 +928,12 @@ static int step_launches(fdtd_ctx* c, int64_t n_steps) {
             // the split-field layer runs on the unfused pair only
             rc = tmz_naive_step(c, c->t);
             done = 1;
+        } else if (adj_edge_mode(c)) {
+            // edge-weight reverse mode keeps the fields around the design after
+            // every step, so each launch advances one step
+            rc = tmz_fused_launch(c, 1, c->opt_warps, c->t, c->parity);
+            c->parity ^= 1;
+            done = 1;
         } else if (c->opt_kernel == 2 && left >= T) {
             // as many whole T-blocks as fit before the next checkpoint, in one launch
             const int64_t span = std::min<int64_t>(left, adj_next_boundary(c, c->t));
@@ -948,6 +954,10 @@ static int step_launches(fdtd_ctx* c, int64_t n_steps) {
             c->parity ^= 1;
         }
         if (rc) return rc;
+        if (adj_edge_mode(c)) {
+            rc = adj_edge_record(c, done);
+            if (rc) return rc;
+        }
         if (c->n_dft > 0) {
             rc = dft_items_launch(c, c->t, done);
             if (rc) return rc;

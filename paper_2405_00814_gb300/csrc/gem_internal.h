@@ -68,6 +68,8 @@ struct TmzDev {
     long long dsg_rec_n0, dsg_rec_len;
     float* grad;                        // [dsg_h][dsg_w]
     float* adj_rec;                     // [steps][dsg_h * dsg_w]: dL/dE^{n+1}, step n at n - dsg_rec_n0
+    int adj_edges;                      // 1: adj_rec is [steps][3][dsg_h * dsg_w]: dL/dE^{n+1},
+                                        //    dL/dHx^{n+1/2}, dL/dHy^{n+1/2} (edge-weight gradients)
     const float* adj_src;               // [steps][n_adj]: dL/dE^{n+1} at adjoint source cells
     int n_adj;
 };
@@ -206,13 +208,13 @@ int tmz_naive_step(fdtd_ctx* c, long long n);
 int dft_cells_launch(fdtd_ctx* c, const DftMon& m, long long n0, int nsteps);
 int tmz_finite_check(fdtd_ctx* c, int* bad);
 int tmz_persistent_launch(fdtd_ctx* c, int T, long long n0, int n_blocks, int parity);
-size_t tmz_fused_smem(int T, int warps, int V);
+size_t tmz_fused_smem(int T, int warps, int V);   // V: 0 interior, 1 CPML, 2 lite
 int tmz_design_band(fdtd_ctx* c, Scene2* s);
 // raise a kernel's dynamic shared-memory limit to `bytes` on the current device,
 // once (the attribute call is a driver round trip; later launches reuse it)
 cudaError_t ensure_dyn_smem(const void* kernel, size_t bytes);
 int dft_items_launch(fdtd_ctx* c, long long n0, int nsteps);
-void adj_patch_descriptors(fdtd_ctx* c, TmzDev* dev);   // V: 0 interior, 1 CPML, 2 lite
+void adj_patch_descriptors(fdtd_ctx* c, TmzDev* dev);
 }  // namespace gem
 
 namespace gem {
@@ -240,4 +242,8 @@ void graph_free(fdtd_ctx* c);
 int adj_checkpoint_if_due(fdtd_ctx* c);
 int adj_next_boundary(const fdtd_ctx* c, int64_t t);
 void adj_free(fdtd_ctx* c);
+// edge-weight reverse mode: the forward steps one step per launch and keeps the
+// fields of the window around each design rectangle after every step
+bool adj_edge_mode(const fdtd_ctx* c);
+int adj_edge_record(fdtd_ctx* c, int steps_done);
 }  // namespace gem

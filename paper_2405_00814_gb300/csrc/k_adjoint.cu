@@ -130,6 +130,7 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
     const size_t band_plane = (size_t)dsg_h * pitch;
     const long long rec_n0 = S->dsg_rec_n0, rec_len = S->dsg_rec_len;
     float* const adj_rec = S->adj_rec;
+    const int adj_edges = S->adj_edges;
     const float* __restrict__ adj_src = S->adj_src;
     const int n_adj = S->n_adj;
     // the task's adjoint source cells: the first 32 ride in lane registers
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
                     const long long nr = n - rec_n0;
                     if (dj >= 0 && dj < dsg_h && nr >= 0 && nr < rec_len) {
                         const size_t hw = (size_t)dsg_w * dsg_h;
-                        float* er = adj_rec + (size_t)nr * hw + (size_t)dj * dsg_w;
+                        float* er = adj_rec + (size_t)nr * hw * (adj_edges ? 3 : 1) + (size_t)dj * dsg_w;
                         const int di = cx - dsg_i0;
                         for (int q = 0; q < 4; q++) {
                             const int d = di + q;
@@ -365,6 +366,27 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
             X[t].y += gya.y - gyu.y;
             X[t].z += gya.z - gyu.z;
             X[t].w += gya.w - gyu.w;
+            if constexpr (GEN) {
+                // X[t], Y[t] now hold dL/dHx^{n+1/2}, dL/dHy^{n+1/2} of row a (the
+                // next step's self-loop plus layer 2 transposed): keep them over the
+                // owned design cells for the edge-weight gradients
+                if (adj_edges && dsg && a >= tk.ya && a < tk.yb && out_lane) {
+                    const int dj = a - dsg_j0;
+                    const long long nr = n - rec_n0;
+                    if (dj >= 0 && dj < dsg_h && nr >= 0 && nr < rec_len) {
+                        const size_t hw = (size_t)dsg_w * dsg_h;
+                        float* xr = adj_rec + ((size_t)nr * 3 + 1) * hw + (size_t)dj * dsg_w;
+                        const int di = cx - dsg_i0;
+                        for (int q = 0; q < 4; q++) {
+                            const int d = di + q;
+                            if (d >= 0 && d < dsg_w) {
+                                xr[d] = cget(X[t], q);
+                                xr[hw + d] = cget(Y[t], q);
+                            }
+                        }
+                    }
+                }
+            }
             if constexpr (PV) {
                 if (pml) {
                     if (lane_px) {
@@ -525,6 +547,70 @@ __global__ void k_grad_reduce(const float* __restrict__ rec, const float* __rest
     grad[c] += fac[c] * g;
 }
 
+// the fields of the window (i0 - 1 .. i0 + w) x (j0 - 1 .. j0 + h) around a design
+// rectangle after one step: out[3][H][W] = Ez^{n+1}, Hx^{n+1/2}, Hy^{n+1/2}
+__global__ void k_edge_record(const float* __restrict__ ez, const float* __restrict__ hx,
+                              const float* __restrict__ hy, int pitch, int i0, int j0, int W, int H,
+                              float* __restrict__ out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ww = W * H;
+    if (q >= ww) return;
+    const int i = i0 - 1 + q % W, j = j0 - 1 + q / W;
+    const size_t g = (size_t)(j + PAD_Y) * pitch + i + PAD_X;
+    out[q] = ez[g];
+    out[ww + q] = hx[g];
+    out[2 * ww + q] = hy[g];
+}
+
+// dL/dw of the 11 edge classes of every design cell (the order of
+// fdtd_edge_grad), summed over one segment: for layer 2 the destination's
+// dL/dE^{n+1} times the source's value in E^n or H^{n+1/2}, for layer 1 the
+// destination's dL/dH^{n+1/2} times the source's value in E^n or H^{n-1/2}.
+// win: the segment's windows [len][3][h+2][w+2] (k_edge_record after step n);
+// prev: the window after the step before the segment, NULL at step 0 (the
+// fields start at zero); erec: [len][3][h*w] = dL/dE^{n+1}, dL/dHx^{n+1/2},
+// dL/dHy^{n+1/2} kept by the adjoint kernels.
+__global__ void k_edge_reduce(const float* __restrict__ win, const float* __restrict__ prev,
+                              const float* __restrict__ erec, float* __restrict__ g, int w, int h, int len) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int hw = w * h;
+    if (c >= hw) return;
+    const int W = w + 2, ww = W * (h + 2);
+    const int x = (c / w + 1) * W + c % w + 1;
+    float a[11];
+#pragma unroll
+    for (int k = 0; k < 11; k++) a[k] = 0.f;
+    for (int s = 0; s < len; s++) {
+        const float* cur = win + (size_t)s * 3 * ww;
+        const float* pv = s > 0 ? cur - (size_t)3 * ww : prev;
+        float ez = 0.f, ez_n = 0.f, ez_e = 0.f, hx0 = 0.f, hy0 = 0.f;
+        if (pv) {
+            ez = pv[x];
+            ez_n = pv[x + W];
+            ez_e = pv[x + 1];
+            hx0 = pv[ww + x];
+            hy0 = pv[2 * ww + x];
+        }
+        const float hx1 = cur[ww + x], hx1_s = cur[ww + x - W];
+        const float hy1 = cur[2 * ww + x], hy1_w = cur[2 * ww + x - 1];
+        const float* lr = erec + (size_t)s * 3 * hw;
+        const float le = lr[c], lx = lr[hw + c], ly = lr[2 * hw + c];
+        a[0] += le * ez;
+        a[1] += le * hy1;
+        a[2] += le * hy1_w;
+        a[3] += le * hx1;
+        a[4] += le * hx1_s;
+        a[5] += lx * hx0;
+        a[6] += lx * ez_n;
+        a[7] += lx * ez;
+        a[8] += ly * hy0;
+        a[9] += ly * ez_e;
+        a[10] += ly * ez;
+    }
+#pragma unroll
+    for (int k = 0; k < 11; k++) g[(size_t)k * hw + c] += a[k];
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -532,13 +618,22 @@ __global__ void k_grad_reduce(const float* __restrict__ rec, const float* __rest
 // ---------------------------------------------------------------------------
 struct AdjState {
     int every;
-    int store;                     // 1: design history (no recompute); 0: field checkpoints
+    int store;                     // 1: history kept (no recompute); 0: field checkpoints
+    int edges;                     // 1: the history is the field window of each design (edge weights)
     std::vector<float*> ckpt;      // [slot * n_scenes + scene] -> F_COUNT2 padded arrays
     std::vector<float*> hist;      // [slot * n_scenes + scene] -> every x design cells of r^n
 };
 
 static size_t field_bytes(const Scene2* s) { return (size_t)s->pitch * s->rows * sizeof(float); }
 static size_t design_cells(const Scene2* s) { return s->d_dsg ? (size_t)s->dsg_w * s->dsg_h : 0; }
+static size_t window_cells(const Scene2* s) { return s->d_dsg ? (size_t)(s->dsg_w + 2) * (s->dsg_h + 2) : 0; }
+// every cell of the window around the design lies outside the CPML slabs and
+// inside the stored grid, so the 11 edges of each design cell are all its edges
+static bool window_inside(const Scene2* s) {
+    const int m = s->npml;
+    return s->dsg_i0 - 1 >= m && s->dsg_j0 - 1 >= m && s->dsg_i0 + s->dsg_w <= s->nx - 1 - m &&
+           s->dsg_j0 + s->dsg_h <= s->ny - 1 - m;
+}
 
 // store mode: point every scene's recording at the history block of the
 // segment that contains step t
@@ -547,7 +642,7 @@ static void patch_for_step(const fdtd_ctx* c, const AdjState* A, TmzDev* dev, in
     const int64_t slot = t / A->every;
     for (int k = 0; k < ns; k++) {
         const size_t q = (size_t)slot * ns + k;
-        float* h = q < A->hist.size() ? A->hist[q] : nullptr;
+        float* h = q < A->hist.size() && !A->edges ? A->hist[q] : nullptr;
         dev[k].dsg_rec = h;
         dev[k].dsg_rec_n0 = slot * A->every;
         dev[k].dsg_rec_len = h ? A->every : 0;
@@ -568,7 +663,13 @@ int adj_checkpoint_if_due(fdtd_ctx* c) {
     if (A->store) {
         if ((int)A->hist.size() < (slot + 1) * ns) A->hist.resize((size_t)(slot + 1) * ns, nullptr);
         for (int k = 0; k < ns; k++) {
-            const size_t hw = design_cells(c->s2[k]);
+            const Scene2* s = c->s2[k];
+            if (A->edges && s->d_dsg && !window_inside(s)) {
+                c->err = "edge-weight gradients need the design rectangle and a ring of one cell around it "
+                         "outside the CPML and inside the grid";
+                return FDTD_EINVAL;
+            }
+            const size_t hw = A->edges ? 3 * window_cells(s) : design_cells(s);
             float*& p = A->hist[(size_t)slot * ns + k];
             if (hw && !p && cudaMalloc(&p, (size_t)A->every * hw * sizeof(float)) != cudaSuccess) {
                 cudaGetLastError();
@@ -605,6 +706,36 @@ int adj_checkpoint_if_due(fdtd_ctx* c) {
                 return FDTD_ECUDA;
             }
         }
+    }
+    return FDTD_OK;
+}
+
+bool adj_edge_mode(const fdtd_ctx* c) {
+    const AdjState* A = (const AdjState*)c->adj;
+    return A && A->every > 0 && A->edges;
+}
+
+int adj_edge_record(fdtd_ctx* c, int steps_done) {
+    const AdjState* A = (const AdjState*)c->adj;
+    const int ns = (int)c->s2.size();
+    // the step just taken is c->t + steps_done - 1 (single steps in this mode)
+    const int64_t n = c->t + steps_done - 1;
+    const int64_t slot = n / A->every, step_in = n % A->every;
+    for (int k = 0; k < ns; k++) {
+        const Scene2* s = c->s2[k];
+        const size_t q = (size_t)slot * ns + k;
+        if (!s->d_dsg || q >= A->hist.size() || !A->hist[q]) continue;
+        const int W = s->dsg_w + 2, H = s->dsg_h + 2;
+        float* out = A->hist[q] + (size_t)step_in * 3 * W * H;
+        k_edge_record<<<(W * H + 255) / 256, 256, 0, c->stream>>>(
+            s->fbuf[F_EZ][c->parity], s->fbuf[F_HX][c->parity], s->fbuf[F_HY][c->parity], s->pitch, s->dsg_i0,
+            s->dsg_j0, W, H, out);
+        c->launches++;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        c->err = std::string("edge-weight record: ") + cudaGetErrorString(e);
+        return FDTD_ECUDA;
     }
     return FDTD_OK;
 }
@@ -653,19 +784,30 @@ int fdtd_set_checkpointing(fdtd_ctx* c, int every) {
     if (every > 0) {
         AdjState* A = new AdjState();
         A->every = every;
-        A->store = c->opt_adj_store;
+        A->store = c->opt_adj_store != 0;
+        A->edges = c->opt_adj_store == 2;
         c->adj = A;
     }
     return FDTD_OK;
 }
 
-int fdtd_adjoint_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, float* grad, int on_device) {
+// the reverse sweep shared by fdtd_adjoint_grad (edges = 0: dL/deps_r) and
+// fdtd_edge_grad (edges = 1: dL/dw of the 11 edge classes)
+static int reverse_run(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, float* grad, int on_device,
+                       int edges) {
     if (!c || !dLdF_re || !dLdF_im || !grad) return FDTD_EINVAL;
     AdjState* A = (AdjState*)c->adj;
     if (c->dims != 2 || !A || A->every <= 0) {
-        c->err = "fdtd_adjoint_grad needs a 2D forward run with checkpointing enabled";
+        c->err = "reverse mode needs a 2D forward run with checkpointing enabled";
         return FDTD_ESTATE;
     }
+    if (A->edges != edges) {
+        c->err = edges ? "fdtd_edge_grad needs a forward run recorded with FDTD_OPT_ADJ_STORE = 2"
+                       : "this forward run was recorded for edge-weight gradients (FDTD_OPT_ADJ_STORE = 2): "
+                         "call fdtd_edge_grad";
+        return FDTD_ESTATE;
+    }
+    const int planes = edges ? 3 : 1, n_out = edges ? FDTD_EDGE_CLASSES : 1;
     const int64_t N = c->t;
     const int ns = (int)c->s2.size();
     const int64_t nseg = N >= 1 ? (N - 1) / A->every + 1 : 0;
@@ -750,15 +892,15 @@ int fdtd_adjoint_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, f
         float *aset = nullptr, *rec = nullptr, *erec = nullptr, *gr = nullptr, *src = nullptr, *fac = nullptr;
         if (!dmalloc(F_COUNT2 * 2 * fb, (void**)&aset) ||
             (!A->store && !dmalloc((size_t)every * hw * sizeof(float), (void**)&rec)) ||
-            !dmalloc((size_t)every * hw * sizeof(float), (void**)&erec) ||
-            !dmalloc(hw * sizeof(float), (void**)&gr) || !dmalloc(hw * sizeof(float), (void**)&fac) ||
+            !dmalloc((size_t)every * planes * hw * sizeof(float), (void**)&erec) ||
+            !dmalloc(n_out * hw * sizeof(float), (void**)&gr) || !dmalloc(hw * sizeof(float), (void**)&fac) ||
             !dmalloc(tab[k].size() * sizeof(float), (void**)&src)) {
             cleanup();
             c->err = "adjoint: out of device memory";
             return FDTD_ENOMEM;
         }
         cudaMemsetAsync(aset, 0, F_COUNT2 * 2 * fb, st);
-        cudaMemsetAsync(gr, 0, hw * sizeof(float), st);
+        cudaMemsetAsync(gr, 0, n_out * hw * sizeof(float), st);
         cudaMemcpyAsync(src, tab[k].data(), tab[k].size() * sizeof(float), cudaMemcpyHostToDevice, st);
         // eq. (7) with D = eps0 eps_r + sigma dt / 2: Ca = (eps0 eps_r - sigma dt / 2) / D,
         // Cb = dt / D, so dCb/deps_r = -eps0 dt / D^2 = (-eps0 / D) Cb and
@@ -796,6 +938,7 @@ int fdtd_adjoint_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, f
             for (int p = 0; p < 2; p++) a.f[f][p] = abuf[(size_t)k * F_COUNT2 * 2 + f * 2 + p];
         a.rec = nullptr;
         a.n_rec = 0;
+        a.adj_edges = edges;
         adj[k] = a;
         // adjoint tasks: general if a CPML slab, the design rectangle or an
         // adjoint source is within reach, or the strip is ragged
@@ -940,9 +1083,17 @@ int fdtd_adjoint_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, f
         if (rc) break;
         // fold the segment's e and recorded r^n into dL/deps_r
         for (int k = 0; k < ns; k++) {
-            const int hw = (int)design_cells(c->s2[k]);
-            const float* r = A->store ? A->hist[(size_t)sg * ns + k] : rec_of[k];
-            k_grad_reduce<<<(hw + 255) / 256, 256, 0, st>>>(r, erec_of[k], fac_of[k], grad_of[k], hw, (int)len);
+            const Scene2* s = c->s2[k];
+            const int hw = (int)design_cells(s);
+            if (edges) {
+                const float* prev = sg > 0 ? A->hist[(size_t)(sg - 1) * ns + k] + (size_t)(every - 1) * 3 * window_cells(s)
+                                           : nullptr;
+                k_edge_reduce<<<(hw + 127) / 128, 128, 0, st>>>(A->hist[(size_t)sg * ns + k], prev, erec_of[k],
+                                                                grad_of[k], s->dsg_w, s->dsg_h, (int)len);
+            } else {
+                const float* r = A->store ? A->hist[(size_t)sg * ns + k] : rec_of[k];
+                k_grad_reduce<<<(hw + 255) / 256, 256, 0, st>>>(r, erec_of[k], fac_of[k], grad_of[k], hw, (int)len);
+            }
             c->launches++;
         }
         e = cudaGetLastError();
@@ -952,7 +1103,7 @@ int fdtd_adjoint_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, f
     if (rc == FDTD_OK) {
         size_t off = 0;
         for (int k = 0; k < ns; k++) {
-            const size_t hw = (size_t)c->s2[k]->dsg_w * c->s2[k]->dsg_h;
+            const size_t hw = (size_t)n_out * c->s2[k]->dsg_w * c->s2[k]->dsg_h;
             e = cudaMemcpyAsync(grad + off, adj[k].grad, hw * sizeof(float),
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
             if (e != cudaSuccess) {
@@ -964,6 +1115,14 @@ int fdtd_adjoint_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, f
     }
     cleanup();
     return rc;
+}
+
+int fdtd_adjoint_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, float* grad, int on_device) {
+    return reverse_run(c, dLdF_re, dLdF_im, grad, on_device, 0);
+}
+
+int fdtd_edge_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, float* grad, int on_device) {
+    return reverse_run(c, dLdF_re, dLdF_im, grad, on_device, 1);
 }
 
 }  // extern "C"

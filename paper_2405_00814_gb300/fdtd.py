@@ -86,6 +86,7 @@ def lib():
         L.fdtd_autotune.argtypes = [vp, ip, C.POINTER(C.c_double)]
         L.fdtd_set_checkpointing.argtypes = [vp, ip]
         L.fdtd_adjoint_grad.argtypes = [vp, vp, vp, vp, ip]
+        L.fdtd_edge_grad.argtypes = [vp, vp, vp, vp, ip]
         L.fdtd_mp_steps_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, i64, vp]
         _LIB = L
     return _LIB
@@ -410,6 +411,25 @@ class Simulation:
         self._check(self._L.fdtd_adjoint_grad(self._h, re.ctypes.data, im.ctypes.data, res.ctypes.data, 0))
         return res
 
+    def edge_grad(self, dLdF, design_shapes, out=None):
+        """dL/dw of the EDGE_CLASSES weights every design cell owns (fdtd_edge_grad)
+        after a forward run recorded with option adj_store = 2.  dLdF: as for
+        adjoint_grad; design_shapes: (h, w) of each scene's design rectangle.
+        Returns a list of [EDGE_CLASSES, h, w] host arrays, or fills the CUDA
+        tensor `out` (all scenes' blocks concatenated)."""
+        g = np.ascontiguousarray(np.concatenate([np.ravel(x) for x in dLdF]) if isinstance(dLdF, (list, tuple))
+                                 else np.ravel(dLdF))
+        re = np.ascontiguousarray(g.real, np.float32)
+        im = np.ascontiguousarray(g.imag, np.float32)
+        if out is not None and hasattr(out, "data_ptr"):
+            self._check(self._L.fdtd_edge_grad(self._h, re.ctypes.data, im.ctypes.data, out.data_ptr(), 1))
+            return out
+        sizes = [EDGE_CLASSES * h * w for h, w in design_shapes]
+        res = np.empty(sum(sizes), np.float32)
+        self._check(self._L.fdtd_edge_grad(self._h, re.ctypes.data, im.ctypes.data, res.ctypes.data, 0))
+        parts = np.split(res, np.cumsum(sizes)[:-1])
+        return [p.reshape(EDGE_CLASSES, h, w) for p, (h, w) in zip(parts, design_shapes)]
+
     def graph_size(self, layer: int):
         """(nodes, edges) of message-passing layer 1 or 2 of the current scene."""
         nn, ne = C.c_int64(), C.c_int64()
@@ -457,6 +477,8 @@ def te_node_signs(nx: int, ny: int, n_nodes: int, split: bool = False) -> np.nda
     sg[e] = -1.0
     return sg
 
+
+EDGE_CLASSES = 11   # FDTD_EDGE_CLASSES: weights a design cell owns as a destination
 
 MP_NOALLOC_MAX_NODES = 1 << 22
 
