@@ -98,6 +98,9 @@ extern "C" {
                                 2 = for fdtd_edge_grad: the forward advances one step per launch and keeps
                                 Ez, Hx, Hy of the window one cell wider than each design rectangle after
                                 every step (steps x (w + 2)(h + 2) x 12 B) */
+#define FDTD_OPT_SEGMENT_B 8 /* 2D: rows per warp task of the boundary kernels (CPML slabs, source, probes, design,
+                                ragged edge); 0 (default) = max(8, segment / 2).  Those warps carry a longer
+                                serial chain per row, so shorter tasks shorten the critical path */
 
 typedef struct fdtd_ctx fdtd_ctx;
 
@@ -154,6 +157,20 @@ int fdtd_set_source(fdtd_ctx* ctx, int kind, int i, int j, int k, int component,
  * earlier source (a point source is the line j1 = j0 + 1). */
 int fdtd_set_line_source(fdtd_ctx* ctx, int kind, int i, int j0, int j1, const double* params, const float* samples,
                          int64_t n_samples);
+
+/* Replace the material map and table of the selected 2D scene in place (same
+ * grid, boundary, dt), to solve a new geometry in an existing context without
+ * re-creating it.  mat_idx: [ny][nx] indices into table, host memory; table:
+ * n_mat (1..255) entries checked as for fdtd_create; eq. (7) gives the new
+ * coefficients.  The map is copied on the context's stream (asynchronously when
+ * mat_idx is page-locked: keep it unchanged until the next call that
+ * synchronises); its indices are not scanned, and a cell whose index is >= n_mat
+ * takes zero coefficients, i.e. acts as a PEC cell.  The walls i = 0 and j = 0
+ * stay PEC.  Fields, source, probes and monitors are kept (fdtd_reset starts a
+ * new solve); a design rectangle keeps its own values; a recorded CUDA graph
+ * stays valid.  FDTD_EINVAL: NULL pointers, n_mat outside 1..255, a rejected
+ * table entry, a non-vacuum cell in a split-field PML layer, a 3D context. */
+int fdtd_set_materials(fdtd_ctx* ctx, const uint8_t* mat_idx, const fdtd_material* table, int n_mat);
 
 /* Continuous permittivity over a rectangle of the selected 2D scene -- the
  * design region of inverse design, where every cell has its own eps_r.  Cells

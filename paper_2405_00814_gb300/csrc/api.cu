@@ -232,7 +232,6 @@ int scene2_init(fdtd_ctx* c, const fdtd_grid* g, double dx, double dt, double co
     s->dx = dx; s->dy = dy; s->dt = dt;
     s->pitch = ((PAD_X + g->nx + STRIP) + 31) / 32 * 32;
     s->rows = g->ny + 2 * PAD_Y;
-    s->mat_host.assign(mat, mat + ncell);
     s->eps_r.resize(n_mat);
     s->sigma.resize(n_mat);
     for (int m = 0; m < n_mat; m++) {
@@ -298,6 +297,7 @@ fdtd_ctx* ctx_new(void* stream) {
     c->opt_tblock = 4;
     c->opt_warps = 8;
     c->opt_segment = 64;
+    c->opt_segment_b = 0;
     c->dirty = true;
     c->d_scenes = nullptr;
     c->d_tasks = nullptr;
@@ -443,7 +443,7 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
         // reach, or a ragged right edge, run the general kernel ("boundary" list);
         // the rest run the lean interior kernel.  General warps are heavier per
         // row, so they get half-height segments.
-        const int seg_b = std::max(8, seg / 2);
+        const int seg_b = c->opt_segment_b > 0 ? c->opt_segment_b : std::max(8, seg / 2);
         auto flags_of = [&](int x0, int ya, int yb, bool* general) {
             int f = 0;
             const int lx0 = x0 - HALO, lx1 = x0 - HALO + STRIP;   // loaded columns
@@ -619,6 +619,22 @@ int step_prepare(fdtd_ctx* c, int64_t n_steps) {
     }
     return FDTD_OK;
 }
+
+// the PEC walls i = 0 and j = 0 of a padded material map take PEC_MAT
+__global__ void k_pec_walls(uint8_t* __restrict__ mat, int pitch, int nx, int ny) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nx) mat[(size_t)PAD_Y * pitch + PAD_X + q] = (uint8_t)PEC_MAT;
+    else if (q < nx + ny) mat[(size_t)(q - nx + PAD_Y) * pitch + PAD_X] = (uint8_t)PEC_MAT;
+}
+
+static int pec_walls(fdtd_ctx* c, Scene2* s) {
+    const int n = s->nx + s->ny;
+    k_pec_walls<<<(n + 255) / 256, 256, 0, c->stream>>>(s->d_mat, s->pitch, s->nx, s->ny);
+    c->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "PEC walls");
+    return FDTD_OK;
+}
 }  // namespace gem
 
 // ===========================================================================
@@ -743,6 +759,12 @@ int fdtd_set_option(fdtd_ctx* c, int option, int64_t v) {
             c->opt_segment = (int)v;
             c->dirty = true;
             return FDTD_OK;
+        case FDTD_OPT_SEGMENT_B:
+            if (v != 0 && (v < 4 || v > (1 << 20)))
+                return fail(c, FDTD_EINVAL, "boundary segment %lld: 0 (automatic) or >= 4 rows", (long long)v);
+            c->opt_segment_b = (int)v;
+            c->dirty = true;
+            return FDTD_OK;
         case FDTD_OPT_WARPS:
             if (v < 1 || v > 8) return fail(c, FDTD_EINVAL, "warps %lld outside 1..8", (long long)v);
             c->opt_warps = (int)v;
@@ -763,6 +785,7 @@ int64_t fdtd_get_option(const fdtd_ctx* c, int option) {
         case FDTD_OPT_SPIN_LIMIT: return c->spin_limit;
         case FDTD_OPT_DEBUG_SKIP_CTA: return c->opt_debug_skip;
         case FDTD_OPT_ADJ_STORE: return c->opt_adj_store;
+        case FDTD_OPT_SEGMENT_B: return c->opt_segment_b;
     }
     return -1;
 }
@@ -798,6 +821,55 @@ int fdtd_set_line_source(fdtd_ctx* c, int kind, int i, int j0, int j1, const dou
     s->src_j1 = j1;
     s->src_cap = 0;   // regenerate the waveform table
     c->dirty = true;
+    return FDTD_OK;
+}
+
+int fdtd_set_materials(fdtd_ctx* c, const uint8_t* mat, const fdtd_material* table, int n_mat) {
+    if (!c) return FDTD_EINVAL;
+    Scene2* s = cur2(c);
+    if (!s) return fail(c, FDTD_EINVAL, "fdtd_set_materials covers 2D scenes");
+    if (!mat || !table) return fail(c, FDTD_EINVAL, "NULL material map or table");
+    if (n_mat < 1 || n_mat > 255) return fail(c, FDTD_EINVAL, "n_mat %d outside 1..255", n_mat);
+    for (int m = 0; m < n_mat; m++) {
+        if (!(table[m].eps_r > 0)) return fail(c, FDTD_EINVAL, "material %d: eps_r must be > 0", m);
+        if (table[m].mu_r != 1.0) return fail(c, FDTD_EINVAL, "material %d: mu_r must be 1 (non-magnetic medium)", m);
+        if (!(table[m].sigma >= 0)) return fail(c, FDTD_EINVAL, "material %d: sigma must be >= 0", m);
+    }
+    if (s->split) {
+        // the split layer's coefficients are per-axis profiles of vacuum: scan the layer only
+        for (int j = 0; j < s->ny; j++) {
+            const bool yl = j < s->npml || j >= s->ny - s->npml;
+            for (int i = 0; i < s->nx; i++) {
+                if (!yl && i >= s->npml && i < s->nx - s->npml) {
+                    i = s->nx - s->npml - 1;
+                    continue;
+                }
+                const int m = mat[(size_t)j * s->nx + i];
+                if (m >= n_mat || table[m].eps_r != 1.0 || table[m].sigma != 0.0)
+                    return fail(c, FDTD_EINVAL, "split-field PML: cell (%d, %d) in the layer is not vacuum", i, j);
+            }
+        }
+    }
+    std::vector<float4> co(256, make_float4(0, 0, 0, 0));
+    for (int m = 0; m < n_mat; m++) co[m] = e_coeffs(table[m].eps_r, table[m].sigma, s->dt, s->dx, s->dy);
+    // the [ny][nx] map lands inside the padded layout; the walls are re-marked PEC
+    CK(cudaMemcpy2DAsync(s->d_mat + (size_t)PAD_Y * s->pitch + PAD_X, s->pitch, mat, s->nx, s->nx, s->ny,
+                         cudaMemcpyHostToDevice, c->stream), "upload material map");
+    CK(cudaMemcpyAsync(s->d_coef, co.data(), 256 * sizeof(float4), cudaMemcpyHostToDevice, c->stream),
+       "upload coefficients");
+    int rc = pec_walls(c, s);
+    if (rc) return rc;
+    if (s->d_dsg) {
+        rc = tmz_design_band(c, s);   // the band holds material coefficients outside the rectangle
+        if (rc) return rc;
+    }
+    s->eps_r.assign(n_mat, 0.0);
+    s->sigma.assign(n_mat, 0.0);
+    for (int m = 0; m < n_mat; m++) {
+        s->eps_r[m] = table[m].eps_r;
+        s->sigma[m] = table[m].sigma;
+    }
+    graph_free(c);   // the edge-list weights hold the old coefficients
     return FDTD_OK;
 }
 
@@ -1115,9 +1187,36 @@ int fdtd_autotune(fdtd_ctx* c, int trial_steps, double* best_ms) {
             win = k;
         }
     }
+    // then the boundary tasks' height for the winner (the automatic choice is
+    // the incumbent): their warps set the critical path beside the interior ones
+    int win_b = c->opt_segment_b;
+    if (rc == FDTD_OK && win.kernel == 0) {
+        const int saved_b = c->opt_segment_b;
+        c->opt_segment_b = 0;
+        double base = 0, base2 = 0;
+        rc = time_of(win, 4 * trial_steps, &base);
+        if (rc == FDTD_OK) rc = time_of(win, 4 * trial_steps, &base2);
+        base = std::min(base, base2);
+        win_b = 0;
+        for (int b : {8, 12, 16, 20, 24, 32, 40, win.seg}) {
+            if (rc != FDTD_OK) break;
+            c->opt_segment_b = b;
+            double per = 0, per2 = 0;
+            rc = time_of(win, 4 * trial_steps, &per);
+            if (rc == FDTD_OK) rc = time_of(win, 4 * trial_steps, &per2);
+            per = std::min(per, per2);
+            if (rc == FDTD_OK && per < 0.99 * base) {   // a clear gain over the incumbent
+                base = per;
+                win_b = b;
+            }
+        }
+        if (rc != FDTD_OK) win_b = saved_b;
+        best = std::min(best, base);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->opt_kernel = win.kernel; c->opt_tblock = win.T; c->opt_segment = win.seg; c->opt_warps = win.warps;
+    c->opt_segment_b = win_b;
     c->opt_graph = graph;
     c->dirty = true;
     int rc2 = fdtd_reset(c);

@@ -120,7 +120,6 @@ struct Scene2 {
     int nx, ny, pitch, rows, npml;
     int split;                           // 1: npml is a split-field PML, not a CPML
     double dx, dy, dt;
-    std::vector<uint8_t> mat_host;       // [ny][nx] as given
     std::vector<double> eps_r, sigma;    // material table
     float* fbuf[F_COUNT2][2];
     uint8_t* d_mat;
@@ -161,6 +160,7 @@ struct fdtd_ctx {
     int64_t launches;
     // options
     int opt_kernel, opt_tblock, opt_segment, opt_warps;
+    int opt_segment_b;           // FDTD_OPT_SEGMENT_B (0: max(8, opt_segment / 2))
     // device copies for the fused kernel, rebuilt when dirty
     bool dirty;
     gem::TmzDev* d_scenes;

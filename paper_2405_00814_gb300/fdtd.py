@@ -22,7 +22,7 @@ PEC, CPML, SPLIT_PML = 0, 1, 2
 COMP = {"ex": 0, "ey": 1, "ez": 2, "hx": 3, "hy": 4, "hz": 5}
 SRC = {"ricker": 0, "gauss_mod": 1, "gauss": 2, "sampled": 3, "sine": 4}
 OPT = {"kernel": 0, "tblock": 1, "segment": 2, "warps": 3, "graph": 4, "spin_limit": 5, "debug_skip_cta": 6,
-       "adj_store": 7}
+       "adj_store": 7, "segment_b": 8}
 
 
 class FDTDError(RuntimeError):
@@ -64,6 +64,7 @@ def lib():
         L.fdtd_set_source.argtypes = [vp, ip, ip, ip, ip, ip, dp, vp, i64]
         L.fdtd_set_line_source.argtypes = [vp, ip, ip, ip, ip, dp, vp, i64]
         L.fdtd_set_design.argtypes = [vp, ip, ip, ip, ip, dp, dp]
+        L.fdtd_set_materials.argtypes = [vp, vp, vp, ip]
         L.fdtd_add_probe.argtypes = [vp, ip, ip, ip, ip, C.POINTER(C.c_int)]
         L.fdtd_add_dft_monitor.argtypes = [vp, vp, ip, dp, ip, C.POINTER(C.c_int)]
         L.fdtd_add_dft_plane.argtypes = [vp, ip, ip, dp, ip, C.POINTER(C.c_int)]
@@ -254,6 +255,14 @@ class Simulation:
         else:
             self.set_source(src.kind, src.i, src.j, src.k, src.component, param=src.params[0])
 
+    def set_materials(self, mat, eps_r, sigma):
+        """New material map [ny][nx] (uint8; a page-locked array makes the upload
+        asynchronous) and table for the selected 2D scene (fdtd_set_materials)."""
+        m = mat if (isinstance(mat, np.ndarray) and mat.dtype == np.uint8 and mat.flags.c_contiguous) \
+            else np.ascontiguousarray(mat, np.uint8)
+        tab = _mat_table(eps_r, sigma)
+        self._check(self._L.fdtd_set_materials(self._h, m.ctypes.data, tab, len(eps_r)))
+
     def set_design(self, i0, j0, eps_r, sigma=None):
         eps = np.ascontiguousarray(eps_r, np.float64)
         h, w = eps.shape
@@ -327,7 +336,7 @@ class Simulation:
         best = C.c_double(0.0)
         self._check(self._L.fdtd_autotune(self._h, int(trial_steps), C.byref(best)))
         res = {"ms_per_step": best.value,
-               "options": {k: self.get_option(k) for k in ("kernel", "tblock", "segment", "warps")}}
+               "options": {k: self.get_option(k) for k in ("kernel", "tblock", "segment", "warps", "segment_b")}}
         if cache and key:
             data = json.load(open(cache)) if os.path.exists(cache) else {}
             data[ck] = res
