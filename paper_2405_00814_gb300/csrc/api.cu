@@ -307,6 +307,8 @@ fdtd_ctx* ctx_new(void* stream) {
     c->d_tasks_l = nullptr;
     c->n_tasks_l = 0;
     c->warps_l = 4;
+    c->d_tasks_s = nullptr;
+    c->n_tasks_s = 0;
     c->aux = c->aux2 = nullptr;
     c->ev_fork = c->ev_join = c->ev_join2 = nullptr;
     cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
@@ -431,14 +433,15 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     // list, the rest to the interior list; each list is padded to whole CTAs
     // per scene so that a CTA never mixes scenes.
     const int wout = STRIP - 2 * HALO;
-    std::vector<Task> tasks, tasks_b, tasks_l;
+    std::vector<Task> tasks, tasks_b, tasks_l, tasks_s;
     std::vector<Sample2> tsamp;
     const int warps_b = 2, warps_l = 4;
     bool any_design = false;
     for (const Scene2* s : c->s2) any_design = any_design || s->d_dsg != nullptr;
     for (int k = 0; k < ns; k++) {
         Scene2* s = c->s2[k];
-        const size_t first = tasks.size(), first_b = tasks_b.size(), first_l = tasks_l.size();
+        const size_t first = tasks.size(), first_b = tasks_b.size(), first_l = tasks_l.size(),
+                     first_s = tasks_s.size();
         // Tasks with a CPML slab, the design rectangle, the source or a probe in
         // reach, or a ragged right edge, run the general kernel ("boundary" list);
         // the rest run the lean interior kernel.  General warps are heavier per
@@ -471,7 +474,9 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
             t.samp_end = (int)tsamp.size();
             // the lite kernel pays for its own launch and stream fork only when a
             // design rectangle gives it work; otherwise its tasks join the CPML list
-            if ((t.flags & TASK_PML) || (general && !any_design)) tasks_b.push_back(t);
+            // tasks within reach of a split-field layer run the split variant
+            if ((t.flags & TASK_PML) && s->split) tasks_s.push_back(t);
+            else if ((t.flags & TASK_PML) || (general && !any_design)) tasks_b.push_back(t);
             else if (general) tasks_l.push_back(t);
             else tasks.push_back(t);
         };
@@ -496,6 +501,8 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
             while ((tasks_b.size() - first_b) % warps_b) tasks_b.push_back(pad);
         if (tasks_l.size() > first_l)
             while ((tasks_l.size() - first_l) % warps_l) tasks_l.push_back(pad);
+        if (tasks_s.size() > first_s)
+            while ((tasks_s.size() - first_s) % warps_b) tasks_s.push_back(pad);
     }
     std::vector<Sample2> ssamp;
     std::vector<int> soff(ns + 1, 0);
@@ -514,8 +521,10 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     dfree(c->d_scenes); dfree(c->d_tasks); dfree(c->d_tasks_b); dfree(c->d_samp); dfree(c->d_samp_scene); dfree(c->d_samp_off);
     dfree(c->d_tasks_all);
     dfree(c->d_tasks_l);
+    dfree(c->d_tasks_s);
     dfree(c->d_dft);
     c->d_tasks_l = nullptr;
+    c->d_tasks_s = nullptr;
     c->d_dft = nullptr;
     c->n_dft = 0;
     c->d_scenes = nullptr; c->d_tasks = nullptr; c->d_tasks_b = nullptr; c->d_samp = nullptr; c->d_samp_scene = nullptr;
@@ -528,6 +537,7 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     if ((rc = dalloc(c, &c->d_tasks_b, tasks_b.size() * sizeof(Task), "tasks"))) return rc;
     if ((rc = dalloc(c, &c->d_tasks_all, all.size() * sizeof(Task), "tasks"))) return rc;
     if ((rc = dalloc(c, &c->d_tasks_l, tasks_l.size() * sizeof(Task), "tasks"))) return rc;
+    if ((rc = dalloc(c, &c->d_tasks_s, tasks_s.size() * sizeof(Task), "tasks"))) return rc;
     if ((rc = dalloc(c, &c->d_samp, tsamp.size() * sizeof(Sample2), "samples"))) return rc;
     if ((rc = dalloc(c, &c->d_samp_scene, ssamp.size() * sizeof(Sample2), "samples"))) return rc;
     if ((rc = dalloc(c, &c->d_samp_off, soff.size() * sizeof(int), "sample offsets"))) return rc;
@@ -540,6 +550,8 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
         CK(cudaMemcpyAsync(c->d_tasks_all, all.data(), all.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
     if (!tasks_l.empty())
         CK(cudaMemcpyAsync(c->d_tasks_l, tasks_l.data(), tasks_l.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
+    if (!tasks_s.empty())
+        CK(cudaMemcpyAsync(c->d_tasks_s, tasks_s.data(), tasks_s.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
     if (!tsamp.empty())
         CK(cudaMemcpyAsync(c->d_samp, tsamp.data(), tsamp.size() * sizeof(Sample2), cudaMemcpyHostToDevice, c->stream), "upload");
     if (!ssamp.empty())
@@ -576,6 +588,7 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     c->n_tasks_b = (int)tasks_b.size();
     c->n_tasks_all = (int)all.size();
     c->n_tasks_l = (int)tasks_l.size();
+    c->n_tasks_s = (int)tasks_s.size();
     c->warps_l = warps_l;
     c->warps_b = warps_b;
     c->task_tb = T;
@@ -715,6 +728,7 @@ void fdtd_destroy(fdtd_ctx* c) {
     if (c->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     dfree(c->d_tasks_l);
+    dfree(c->d_tasks_s);
     if (c->aux) cudaStreamDestroy(c->aux);
     if (c->aux2) cudaStreamDestroy(c->aux2);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -996,8 +1010,8 @@ static int step_launches(fdtd_ctx* c, int64_t n_steps) {
         int done;
         rc = adj_checkpoint_if_due(c);
         if (rc) return rc;
-        if (c->opt_kernel == 1 || any_split(c)) {
-            // the split-field layer runs on the unfused pair only
+        if (c->opt_kernel == 1 || (c->opt_kernel == 2 && any_split(c))) {
+            // the persistent kernel has no split-field variant: unfused pair
             rc = tmz_naive_step(c, c->t);
             done = 1;
         } else if (adj_edge_mode(c)) {
@@ -1135,7 +1149,6 @@ int fdtd_autotune(fdtd_ctx* c, int trial_steps, double* best_ms) {
     if (c->dims != 2) return fail(c, FDTD_EINVAL, "autotuning covers the 2D kernels");
     if (trial_steps < 4) return fail(c, FDTD_EINVAL, "trial_steps must be >= 4");
     if (c->adj) return fail(c, FDTD_EINVAL, "disable checkpointing before autotuning");
-    if (any_split(c)) return fail(c, FDTD_EINVAL, "a split-field PML steps with the unfused kernels only: nothing to tune");
     struct Cand { int kernel, T, seg, warps; };
     std::vector<Cand> cand;
     // the segment height sets how many CTAs a block launches, so the sweep is
@@ -1143,8 +1156,9 @@ int fdtd_autotune(fdtd_ctx* c, int trial_steps, double* best_ms) {
     for (int T = 2; T <= MAX_TB; T++)
         for (int seg = 16; seg <= 96; seg += 8)
             for (int w : {4, 8}) cand.push_back({0, T, seg, w});
-    for (int T = 2; T <= MAX_TB; T++)
-        for (int seg : {16, 24, 32, 48}) cand.push_back({2, T, seg, 8});
+    if (!any_split(c))   // the persistent kernel has no split-field variant
+        for (int T = 2; T <= MAX_TB; T++)
+            for (int seg : {16, 24, 32, 48}) cand.push_back({2, T, seg, 8});
     const int graph = c->opt_graph;
     c->opt_graph = 0;
     cudaEvent_t e0, e1;

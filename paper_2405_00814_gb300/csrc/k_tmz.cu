@@ -46,10 +46,11 @@ __host__ __device__ constexpr int pf_of(int T, bool pml) { return pml ? PF_B : Q
 __host__ __device__ constexpr int gen_nslot(bool pml) { return pml ? 7 : 6; }
 __host__ __device__ constexpr int gen_stage_f4(bool pml) { return gen_nslot(pml) * 32 + 8 + (pml ? 1 : 0); }
 
-// V: 0 interior, 1 CPML, 2 lite
+// V: 0 interior, 1 CPML, 2 lite, 3 split-field layer
 size_t tmz_fused_smem(int T, int warps, int V) {
     if (V == 0) return (size_t)warps * stages_for(T, false) * stage_f4(false) * sizeof(float4);
-    return (size_t)warps * stages_for(T, V == 1) * gen_stage_f4(V == 1) * sizeof(float4);
+    const bool pml = V == 1 || V == 3;   // 3: split-field layer, same stages as CPML
+    return (size_t)warps * stages_for(T, pml) * gen_stage_f4(pml) * sizeof(float4);
 }
 
 __device__ __forceinline__ size_t sidx(int pitch, int i, int j) {
@@ -109,7 +110,7 @@ struct Prof {
 // One warp's task of the general kernel (any task: CPML slab, design rectangle,
 // source, probes, ragged edge).  coef_s is the scene's coefficient table (shared
 // or global memory); stage0 the warp's Q x STAGE_F4 float4 staging area.
-template <int T, bool PML>
+template <int T, bool PML, bool SPL = false>
 __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const Task& tk,
                                              const Sample2* __restrict__ samps, int parity, long long n0,
                                              const float4* coef_s, float4* stage0, int lane) {
@@ -140,7 +141,18 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
     const Prof pr{S->prof, pitch, S->rows};
     bool lane_px = false;
     float4 bex4 = make_float4(0, 0, 0, 0), cex4 = bex4, bhx4 = bex4, chx4 = bex4;
-    if (pml) {
+    // split-field layer (SPL): depth nsp; the profiles hold Ca, Cb/d of E and
+    // Da, Db/d of H per axis, and the stage's psi_Ezy slot carries Ezy
+    const int nsp = SPL ? S->split : 0;
+    const bool lane_sx = SPL && pml && ((cx < nsp) || (cx + 3 >= nx - nsp));
+    if (lane_sx) {
+        bex4 = make_float4(pr.bEx(cs), pr.bEx(cs + 1), pr.bEx(cs + 2), pr.bEx(cs + 3));
+        cex4 = make_float4(pr.cEx(cs), pr.cEx(cs + 1), pr.cEx(cs + 2), pr.cEx(cs + 3));
+        bhx4 = make_float4(pr.bHx(cs), pr.bHx(cs + 1), pr.bHx(cs + 2), pr.bHx(cs + 3));
+        chx4 = make_float4(pr.cHx(cs), pr.cHx(cs + 1), pr.cHx(cs + 2), pr.cHx(cs + 3));
+    }
+    auto srow = [&](int row) { return (row < nsp) || (row >= ny - nsp); };   // a split-layer row (E or H)
+    if (!SPL && pml) {
         lane_px = (cx < npml) || (cx + 3 >= nx - npml);
         if (lane_px) {
             bex4 = make_float4(pr.bEx(cs), pr.bEx(cs + 1), pr.bEx(cs + 2), pr.bEx(cs + 3));
@@ -192,7 +204,14 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
                 cp_async16(st + 5 * 32 + lane, b + 2 * band_plane, true);
             }
         }
-        if constexpr (PML) if (pml) {
+        if constexpr (SPL) if (pml) {
+            // the row's Ca, Cb/dy of E and Da, Db/dy of H, and Ezy
+            const bool yrow = srow(row);
+            if (yrow && lane < 4)
+                cp_async4(reinterpret_cast<float*>(st + NSLOT * 32 + 8) + lane, pr.p + 4 * pitch + lane * pr.rows + row + PAD_Y);
+            if (yrow || lane_sx) cp_async16(st + 4 * 32 + lane, psi_in[1] + g, true);
+        }
+        if constexpr (PML && !SPL) if (pml) {
             const bool yrow = (row < npml) || (row >= ny - npml);
             // the row's bEy, cEy, bHy, cHy
             if (yrow && lane < 4)
@@ -262,7 +281,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
             const float er = __shfl_down_sync(0xffffffffu, e.x, 1);
             float4 dey = make_float4(eu.x - e.x, eu.y - e.y, eu.z - e.z, eu.w - e.w);
             float4 dex = make_float4(e.y - e.x, e.z - e.y, e.w - e.z, er - e.w);
-            if constexpr (PML) if (pml) {
+            if constexpr (PML && !SPL) if (pml) {
                 if ((a < npml) || (a >= ny - npml)) {
                     const float b = yprof[2], c = yprof[3];
                     float4 p = sta[5 * 32 + lane];
@@ -283,8 +302,34 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
                     dex.x += p.x; dex.y += p.y; dex.z += p.z; dex.w += p.w;
                 }
             }
-            X[t].x -= dby * dey.x; X[t].y -= dby * dey.y; X[t].z -= dby * dey.z; X[t].w -= dby * dey.w;
-            Y[t].x += dbx * dex.x; Y[t].y += dbx * dex.y; Y[t].z += dbx * dex.z; Y[t].w += dbx * dex.w;
+            bool h_done = false;
+            if constexpr (SPL) if (pml) {
+                // split layer: H damped along the axis its derivative runs along
+                // (sigma*), semi-implicit as eq. (7); elsewhere the plain update
+                if (srow(a)) {
+                    const float da = yprof[2], db = yprof[3];
+                    X[t].x = da * X[t].x - db * dey.x; X[t].y = da * X[t].y - db * dey.y;
+                    X[t].z = da * X[t].z - db * dey.z; X[t].w = da * X[t].w - db * dey.w;
+                } else {
+                    X[t].x -= dby * dey.x; X[t].y -= dby * dey.y; X[t].z -= dby * dey.z; X[t].w -= dby * dey.w;
+                }
+                if (lane_sx) {
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const int i = cx + q;
+                        const float hy = comp4(Y[t], q), d = comp4(dex, q);
+                        const float v = (i < nsp || i >= nx - nsp) ? comp4(bhx4, q) * hy + comp4(chx4, q) * d : hy + dbx * d;
+                        if (q == 0) Y[t].x = v; else if (q == 1) Y[t].y = v; else if (q == 2) Y[t].z = v; else Y[t].w = v;
+                    }
+                } else {
+                    Y[t].x += dbx * dex.x; Y[t].y += dbx * dex.y; Y[t].z += dbx * dex.z; Y[t].w += dbx * dex.w;
+                }
+                h_done = true;
+            }
+            if (!h_done) {
+                X[t].x -= dby * dey.x; X[t].y -= dby * dey.y; X[t].z -= dby * dey.z; X[t].w -= dby * dey.w;
+                Y[t].x += dbx * dex.x; Y[t].y += dbx * dex.y; Y[t].z += dbx * dex.z; Y[t].w += dbx * dex.w;
+            }
 
             // ---- layer 2: Ez at row a from H at level t (rows a, a-1) ----
             const float4 y = Y[t];
@@ -292,7 +337,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
             float4 dhy = make_float4(y.x - yl, y.y - y.x, y.z - y.y, y.w - y.z);
             float4 dhx = make_float4(X[t].x - X[t + 1].x, X[t].y - X[t + 1].y, X[t].z - X[t + 1].z,
                                      X[t].w - X[t + 1].w);
-            if constexpr (PML) if (pml) {
+            if constexpr (PML && !SPL) if (pml) {
                 if ((a < npml) || (a >= ny - npml)) {
                     const float b = yprof[0], c = yprof[1];
                     float4 p = sta[4 * 32 + lane];
@@ -341,6 +386,31 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
             E[t].y = e_upd(E[t].y, dhy.y, dhx.y, c1);
             E[t].z = e_upd(E[t].z, dhy.z, dhx.z, c2);
             E[t].w = e_upd(E[t].w, dhy.w, dhx.w, c3);
+            if constexpr (SPL) if (pml) {
+                // split layer (Sec. II-C): Ez = Ezx + Ezy with Ezy in the stage,
+                // each part advanced with its own axis's coefficients (vacuum cells)
+                const bool ly = a < nsp || a > ny - nsp;
+                if ((ly || lane_sx) && a >= 1) {
+                    float4 zy = sta[4 * 32 + lane];
+                    const float4 cq[4] = {c0, c1, c2, c3};
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const int i = cx + q;
+                        const bool lx = i < nsp || i > nx - nsp;
+                        if (i < 1 || !(lx || ly)) continue;
+                        const float ezy0 = comp4(zy, q), ezx0 = comp4(e_old, q) - ezy0;
+                        const float ax = lx ? comp4(bex4, q) : cq[q].x, bx = lx ? comp4(cex4, q) : cq[q].y;
+                        const float ay = ly ? yprof[0] : cq[q].x, by = ly ? yprof[1] : cq[q].z;
+                        const float ezx = ax * ezx0 + bx * comp4(dhy, q);
+                        const float ezy = ay * ezy0 - by * comp4(dhx, q);
+                        if (q == 0) { zy.x = ezy; E[t].x = ezx + ezy; }
+                        else if (q == 1) { zy.y = ezy; E[t].y = ezx + ezy; }
+                        else if (q == 2) { zy.z = ezy; E[t].z = ezx + ezy; }
+                        else { zy.w = ezy; E[t].w = ezx + ezy; }
+                    }
+                    sta[4 * 32 + lane] = zy;
+                }
+            }
             // reverse mode: E^{n+1} - E^n of the owned design cells (before the
             // source), which carries dL/deps_r of step n up to a per-cell factor
             if (dsg && dsg_rec) {
@@ -393,7 +463,10 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
                     *reinterpret_cast<float4*>(ez_out + g) = E[T];
                     *reinterpret_cast<float4*>(hx_out + g) = X[T];
                     *reinterpret_cast<float4*>(hy_out + g) = Y[T];
-                    if constexpr (PML) if (pml) {
+                    if constexpr (SPL) if (pml) {
+                        if (srow(o) || lane_sx) *reinterpret_cast<float4*>(psi_out[1] + g) = sto[4 * 32 + lane];
+                    }
+                    if constexpr (PML && !SPL) if (pml) {
                         if ((o < npml) || (o >= ny - npml)) {
                             *reinterpret_cast<float4*>(psi_out[1] + g) = sto[4 * 32 + lane];
                             *reinterpret_cast<float4*>(psi_out[2] + g) = sto[5 * 32 + lane];
@@ -409,12 +482,14 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
                         p0 = sto[3 * 32 + lane]; p1 = sto[4 * 32 + lane];
                         p2 = sto[5 * 32 + lane]; p3 = sto[6 * 32 + lane];
                     }
-                    const bool yrow = pml && ((o < npml) || (o >= ny - npml));
+                    const bool yrow = !SPL && pml && ((o < npml) || (o >= ny - npml));
+                    const bool srw = SPL && pml && (srow(o) || lane_sx);
                     for (int c = 0; c < 4; c++) {
                         if (cx + c >= nx) break;
                         ez_out[g + c] = comp4(E[T], c);
                         hx_out[g + c] = comp4(X[T], c);
                         hy_out[g + c] = comp4(Y[T], c);
+                        if (srw) psi_out[1][g + c] = comp4(p1, c);
                         if (yrow) {
                             psi_out[1][g + c] = comp4(p1, c);
                             psi_out[2][g + c] = comp4(p2, c);
@@ -435,7 +510,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
 }
 
 // CPML blocks run 2 warps, lite blocks 4 (the lists are padded to that)
-template <int T, bool PML>
+template <int T, bool PML, bool SPL = false>
 __global__ void __launch_bounds__(PML ? 256 : 128, PML ? 1 : 3) k_tmz_fused(const TmzDev* __restrict__ scenes,
                                                    const Task* __restrict__ tasks, int n_tasks,
                                                    const Sample2* __restrict__ samps, int parity,
@@ -457,7 +532,7 @@ __global__ void __launch_bounds__(PML ? 256 : 128, PML ? 1 : 3) k_tmz_fused(cons
     if (tid >= n_tasks) return;
     const Task tk = tasks[tid];
     if (tk.scene < 0) return;
-    general_task<T, PML>(S, tk, samps, parity, n0, coef_s, smem_f4 + (size_t)wib * Q * STAGE_F4, lane);
+    general_task<T, PML, SPL>(S, tk, samps, parity, n0, coef_s, smem_f4 + (size_t)wib * Q * STAGE_F4, lane);
 }
 
 // ===========================================================================
@@ -900,6 +975,11 @@ static cudaError_t launch_fused_T(const Task* tasks, int n_tasks, int warps, con
         e = ensure_dyn_smem((const void*)k_tmz_fused<T, true>, smem);
         if (e != cudaSuccess) return e;
         k_tmz_fused<T, true><<<blocks, warps * 32, smem, st>>>(c->d_scenes, tasks, n_tasks, c->d_samp, parity, n0);
+    } else if (V == 3) {
+        e = ensure_dyn_smem((const void*)k_tmz_fused<T, true, true>, smem);
+        if (e != cudaSuccess) return e;
+        k_tmz_fused<T, true, true><<<blocks, warps * 32, smem, st>>>(c->d_scenes, tasks, n_tasks, c->d_samp, parity,
+                                                                      n0);
     } else if (V == 2) {
         e = ensure_dyn_smem((const void*)k_tmz_fused<T, false>, smem);
         if (e != cudaSuccess) return e;
@@ -928,7 +1008,7 @@ static cudaError_t launch_fused(const Task* tasks, int n_tasks, int warps, const
 // on two forked streams, joined before the next block reads the new buffer
 int tmz_fused_launch(fdtd_ctx* c, int T, int warps, long long n0, int parity) {
     cudaError_t e = cudaSuccess;
-    const int nb = c->n_tasks_b, nl = c->n_tasks_l, ni = c->n_tasks;
+    const int nb = c->n_tasks_b + c->n_tasks_s, nl = c->n_tasks_l, ni = c->n_tasks;
     cudaStream_t sb = c->stream, sl = c->stream;
     if ((nb > 0) + (nl > 0) + (ni > 0) > 1) {
         e = cudaEventRecord(c->ev_fork, c->stream);
@@ -941,8 +1021,13 @@ int tmz_fused_launch(fdtd_ctx* c, int T, int warps, long long n0, int parity) {
             sl = c->aux2;
         }
     }
-    if (e == cudaSuccess && nb > 0) {
-        e = launch_fused<1>(c->d_tasks_b, nb, c->warps_b, c, sb, T, n0, parity);
+    if (e == cudaSuccess && c->n_tasks_b > 0) {
+        e = launch_fused<1>(c->d_tasks_b, c->n_tasks_b, c->warps_b, c, sb, T, n0, parity);
+        c->launches++;
+    }
+    if (e == cudaSuccess && c->n_tasks_s > 0) {
+        // split-field layer tasks follow the CPML ones on the same stream
+        e = launch_fused<3>(c->d_tasks_s, c->n_tasks_s, c->warps_b, c, sb, T, n0, parity);
         c->launches++;
     }
     if (e == cudaSuccess && nl > 0) {

@@ -20,9 +20,12 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
-def _gpu(sc, nsteps, probes):
+def _gpu(sc, nsteps, probes, kernel=0, tblock=4, segment=24):
     from paper_2405_00814_gb300 import fdtd
     sim = fdtd.from_scene(sc, boundary="split", probes=False)
+    sim.set_option("kernel", kernel)
+    sim.set_option("tblock", tblock)
+    sim.set_option("segment", segment)
     pids = [sim.add_probe(int(i), int(j)) for i, j in probes]
     sim.step(nsteps)
     out = {c: sim.get_field(c, (sc.ny, sc.nx)) for c in ("ez", "hx", "hy")}
@@ -31,14 +34,16 @@ def _gpu(sc, nsteps, probes):
     return out
 
 
+@pytest.mark.parametrize("kernel,tblock,segment", [(1, 1, 64), (0, 4, 24), (0, 3, 16), (0, 2, 56), (0, 1, 8)])
 @pytest.mark.parametrize("side,nsteps", [(200, 700), (131, 500)])
-def test_split_pml_matches_oracle(oracle_mod, side, nsteps):
-    """Heterogeneous lossy interior, vacuum layer of 16 (12) cells, a probe."""
+def test_split_pml_matches_oracle(oracle_mod, side, nsteps, kernel, tblock, segment):
+    """Heterogeneous lossy interior, vacuum layer of 16 (12) cells, probes (one
+    in the layer); the unfused pair and the temporally blocked split variant."""
     sc = scenes.ellipse_scene(side=side, nsteps=nsteps)
-    probes = [(side // 2 + 7, side // 3), (side - sc.npml - 3, side // 2)]
+    probes = [(side // 2 + 7, side // 3), (side - sc.npml - 3, side // 2), (5, side - 4)]
     o = oracle_mod.TMzSplit(sc)
     ref = o.run(nsteps, samples=[(i, j, "ez") for i, j in probes])["samples"]
-    g = _gpu(sc, nsteps, probes)
+    g = _gpu(sc, nsteps, probes, kernel, tblock, segment)
     assert rel_l2(g["ez"], o.ez()) <= TOL_FIELD
     assert rel_l2(g["hx"], o.state["hx"]) <= TOL_FIELD
     assert rel_l2(g["hy"], o.state["hy"]) <= TOL_FIELD
@@ -114,4 +119,46 @@ def test_split_pml_exported_graph_is_the_oracle_graph(oracle_mod):
         assert np.array_equal(dst, dst_o)
         assert np.array_equal(src, c)
         assert np.max(np.abs(w - wo) / np.maximum(np.abs(wo), 1e-30)) <= 2e-6
+    sim.close()
+
+
+@pytest.mark.parametrize("tblock,segment", [(4, 24), (3, 40)])
+def test_split_pml_fused_design_and_line_source_in_layer(oracle_mod, tblock, segment):
+    """The temporally blocked split variant with a design rectangle (its own
+    coefficients) and a line source that starts inside the x-layer."""
+    from paper_2405_00814_gb300 import fdtd
+    sc = scenes.ellipse_scene(side=170, nsteps=600)
+    rng = np.random.default_rng(8)
+    sc.design = (40, 50, 33, 21)
+    sc.design_eps = 1 + 7 * rng.random((21, 33))
+    sc.source = scenes.Source(9, 60, kind="gauss_mod", params=(2.4e9,), length=20)
+    probes = [(9, 70), (60, 60), (150, 160)]
+    o = oracle_mod.TMzSplit(sc)
+    ref = o.run(sc.nsteps, samples=[(i, j, "ez") for i, j in probes])["samples"]
+    sim = fdtd.from_scene(sc, boundary="split", probes=False)
+    sim.set_option("tblock", tblock)
+    sim.set_option("segment", segment)
+    pids = [sim.add_probe(i, j) for i, j in probes]
+    sim.step(sc.nsteps)
+    assert rel_l2(sim.get_field("ez", (sc.ny, sc.nx)), o.ez()) <= TOL_FIELD
+    assert rel_l2(sim.get_field("hy", (sc.ny, sc.nx)), o.state["hy"]) <= TOL_FIELD
+    assert rel_l2(np.stack([sim.read_probe(p, sc.nsteps) for p in pids], 1), ref) <= TOL_FIELD
+    sim.close()
+
+
+def test_split_pml_autotune_and_graph(oracle_mod):
+    """The autotuner's pick (no persistent kernel for a split layer) and CUDA-graph
+    replay of the fused split solve."""
+    from paper_2405_00814_gb300 import fdtd
+    sc = scenes.ellipse_scene(side=160, nsteps=400)
+    o = oracle_mod.TMzSplit(sc)
+    o.run(sc.nsteps)
+    sim = fdtd.from_scene(sc, boundary="split")
+    tune = sim.autotune(trial_steps=8)
+    assert tune["options"]["kernel"] == 0
+    sim.set_option("graph", 1)
+    for _ in range(2):
+        sim.reset()
+        sim.step(sc.nsteps)
+    assert rel_l2(sim.get_field("ez", (sc.ny, sc.nx)), o.ez()) <= TOL_FIELD
     sim.close()
