@@ -84,7 +84,7 @@ extern "C" {
                                 3D: 0 = fused z-marching kernel (default), 1 = one H and one E launch per step */
 #define FDTD_OPT_TBLOCK 1    /* time steps per HBM pass of the fused kernel, 1..4 */
 #define FDTD_OPT_SEGMENT 2   /* 2D: rows per warp task of the fused kernel (multiple of 8, >= 8);
-                                3D: planes per z-segment of the fused z-marching kernel (>= 1, default 16) */
+                                3D: planes per z-segment of the fused z-marching kernel (>= 1, default 24) */
 #define FDTD_OPT_WARPS 3     /* warps per CTA of the fused kernel, 1..8 */
 #define FDTD_OPT_GRAPH 4     /* 1: fdtd_step records its launches into a CUDA graph and replays it when called
                                 again with the same start step, step count and buffer parity (e.g. after fdtd_reset) */
@@ -253,10 +253,12 @@ int fdtd_sync(fdtd_ctx* ctx);
 
 /* Pick the 2D kernel options for the current scenes (one large scene, or a
  * batch: Sec. V-A runs many simulations of varying size): time every candidate
- * of (kernel 0: T 2..4, segment 16..96 in steps of 8, warps 4 or 8; kernel 2:
- * T 2..4, segment 16, 24, 32 or 48) for trial_steps steps, time the four
- * fastest twice more for 4 x trial_steps, and keep the best.  Leaves the context
- * reset (t = 0, zero fields).  *best_ms gets the best time per step. */
+ * of (kernel 0: T 2..4, segment 16..96 in steps of 8, warps 4 or 8; kernel 2,
+ * not for a split-field PML: T 2..4, segment 16, 24, 32 or 48) for trial_steps
+ * steps, time the four fastest twice more for 4 x trial_steps, keep the best,
+ * then for kernel 0 try FDTD_OPT_SEGMENT_B values against the automatic one
+ * (kept only if 1 % faster).  Leaves the context reset (t = 0, zero fields).
+ * *best_ms gets the best time per step. */
 int fdtd_autotune(fdtd_ctx* ctx, int trial_steps, double* best_ms);
 
 /* Returns FDTD_EUNSTABLE if any field of any scene is not finite. Synchronises. */
