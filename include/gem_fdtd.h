@@ -95,9 +95,9 @@ extern "C" {
                                 E^{n+1} - E^n over every design rectangle for every step in device memory
                                 (steps x design cells x 4 B) and fdtd_adjoint_grad needs no recompute;
                                 0 = keep field checkpoints only and recompute each segment (less memory);
-                                2 = for fdtd_edge_grad: the forward advances one step per launch and keeps
-                                Ez, Hx, Hy of the window one cell wider than each design rectangle after
-                                every step (steps x (w + 2)(h + 2) x 12 B) */
+                                2 = for fdtd_edge_grad: the forward keeps Ez, Hx, Hy of the window one
+                                cell wider than each design rectangle after every step
+                                (steps x (w + 2)(h + 2) x 12 B) */
 #define FDTD_OPT_SEGMENT_B 8 /* 2D: rows per warp task of the boundary kernels (CPML slabs, source, probes, design,
                                 ragged edge); 0 (default) = max(8, segment / 2).  Those warps carry a longer
                                 serial chain per row, so shorter tasks shorten the critical path */
@@ -177,7 +177,9 @@ int fdtd_set_materials(fdtd_ctx* ctx, const uint8_t* mat_idx, const fdtd_materia
  * [i0, i0+w) x [j0, j0+h) take eps_r[dj*w + di] and sigma[dj*w + di] (sigma NULL
  * = 0) instead of their material-table entry; coefficients follow eq. (7).  The
  * rectangle must avoid the PEC walls: 1 <= i0, i0 + w <= nx, same for j.
- * Calling it again replaces the values (same rectangle) or the rectangle. */
+ * Calling it again replaces the values (same rectangle) or the rectangle; while
+ * checkpointing is on (fdtd_set_checkpointing) the rectangle may move but not
+ * change its size (FDTD_EINVAL). */
 int fdtd_set_design(fdtd_ctx* ctx, int i0, int j0, int w, int h, const double* eps_r, const double* sigma);
 
 /* Probe: records the component at (i, j[, k]) after every following step

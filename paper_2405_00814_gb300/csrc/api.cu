@@ -896,6 +896,9 @@ int fdtd_set_design(fdtd_ctx* c, int i0, int j0, int w, int h, const double* eps
     if (s->split && (split_layer_cell(i0, j0, s->nx, s->ny, s->npml) ||
                      split_layer_cell(i0 + w - 1, j0 + h - 1, s->nx, s->ny, s->npml)))
         return fail(c, FDTD_EINVAL, "the design rectangle must lie inside the split-field PML");
+    if (c->adj && s->d_dsg && (s->dsg_w != w || s->dsg_h != h))
+        return fail(c, FDTD_EINVAL, "the design rectangle's size is fixed while checkpointing is on "
+                                    "(its history blocks are sized for it)");
     const size_t n = (size_t)w * h;
     std::vector<float4> co(n);
     for (size_t q = 0; q < n; q++) {
@@ -1014,12 +1017,6 @@ static int step_launches(fdtd_ctx* c, int64_t n_steps) {
             // the persistent kernel has no split-field variant: unfused pair
             rc = tmz_naive_step(c, c->t);
             done = 1;
-        } else if (adj_edge_mode(c)) {
-            // edge-weight reverse mode keeps the fields around the design after
-            // every step, so each launch advances one step
-            rc = tmz_fused_launch(c, 1, c->opt_warps, c->t, c->parity);
-            c->parity ^= 1;
-            done = 1;
         } else if (c->opt_kernel == 2 && left >= T) {
             // as many whole T-blocks as fit before the next checkpoint, in one launch
             const int64_t span = std::min<int64_t>(left, adj_next_boundary(c, c->t));
@@ -1040,7 +1037,8 @@ static int step_launches(fdtd_ctx* c, int64_t n_steps) {
             c->parity ^= 1;
         }
         if (rc) return rc;
-        if (adj_edge_mode(c)) {
+        if (adj_edge_mode(c) && (c->opt_kernel == 1 || any_split(c))) {
+            // the unfused pair does not keep the design window itself
             rc = adj_edge_record(c, done);
             if (rc) return rc;
         }

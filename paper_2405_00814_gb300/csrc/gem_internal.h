@@ -66,6 +66,9 @@ struct TmzDev {
     // reduction after each segment turns into dL/deps_r
     float* dsg_rec;                     // [steps][dsg_h * dsg_w], step n at n - dsg_rec_n0
     long long dsg_rec_n0, dsg_rec_len;
+    int win_rec;                        // 1: dsg_rec instead keeps [steps][3][dsg_h + 2][dsg_w + 2]:
+                                        //    Ez^{n+1}, Hx^{n+1/2}, Hy^{n+1/2} of the window one cell
+                                        //    around the design (edge-weight gradients)
     float* grad;                        // [dsg_h][dsg_w]
     float* adj_rec;                     // [steps][dsg_h * dsg_w]: dL/dE^{n+1}, step n at n - dsg_rec_n0
     int adj_edges;                      // 1: adj_rec is [steps][3][dsg_h * dsg_w]: dL/dE^{n+1},
@@ -244,8 +247,9 @@ void graph_free(fdtd_ctx* c);
 int adj_checkpoint_if_due(fdtd_ctx* c);
 int adj_next_boundary(const fdtd_ctx* c, int64_t t);
 void adj_free(fdtd_ctx* c);
-// edge-weight reverse mode: the forward steps one step per launch and keeps the
-// fields of the window around each design rectangle after every step
+// edge-weight reverse mode: the forward keeps the fields of the window one cell
+// around each design rectangle after every step (the fused kernels in place,
+// the unfused pair through adj_edge_record)
 bool adj_edge_mode(const fdtd_ctx* c);
 int adj_edge_record(fdtd_ctx* c, int steps_done);
 }  // namespace gem

@@ -642,8 +642,9 @@ static void patch_for_step(const fdtd_ctx* c, const AdjState* A, TmzDev* dev, in
     const int64_t slot = t / A->every;
     for (int k = 0; k < ns; k++) {
         const size_t q = (size_t)slot * ns + k;
-        float* h = q < A->hist.size() && !A->edges ? A->hist[q] : nullptr;
+        float* h = q < A->hist.size() ? A->hist[q] : nullptr;
         dev[k].dsg_rec = h;
+        dev[k].win_rec = A->edges;
         dev[k].dsg_rec_n0 = slot * A->every;
         dev[k].dsg_rec_len = h ? A->every : 0;
     }
@@ -715,6 +716,8 @@ bool adj_edge_mode(const fdtd_ctx* c) {
     return A && A->every > 0 && A->edges;
 }
 
+// the fused kernels keep the window themselves; the unfused pair (one step per
+// call) has it copied out after each step
 int adj_edge_record(fdtd_ctx* c, int steps_done) {
     const AdjState* A = (const AdjState*)c->adj;
     const int ns = (int)c->s2.size();

@@ -174,6 +174,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
     const size_t band_plane = (size_t)dsg_h * pitch;
     float* const dsg_rec = S->dsg_rec;
     const long long rec_n0 = S->dsg_rec_n0, rec_len = S->dsg_rec_len;
+    const int win_rec = S->win_rec;
     // probes and monitor cells of this task: the first 32 ride in lane registers
     const int n_samp = tk.samp_end - tk.samp_begin;
     const bool has_samp = n_samp > 0;
@@ -413,7 +414,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
             }
             // reverse mode: E^{n+1} - E^n of the owned design cells (before the
             // source), which carries dL/deps_r of step n up to a per-cell factor
-            if (dsg && dsg_rec) {
+            if (dsg && dsg_rec && !win_rec) {
                 const int dj = a - dsg_j0;
                 const long long nr = n0 + (t - 1) - rec_n0;
                 if (dj >= 0 && dj < dsg_h && nr >= 0 && nr < rec_len && a >= tk.ya && a < tk.yb && out_lane) {
@@ -432,6 +433,26 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
             if (has_src && a >= src_j && a < src_j1) {
                 const float w = __shfl_sync(0xffffffffu, wv, t - 1);
                 if (src_d >= 0 && src_d < 4 && n < src_len) add4(E[t], src_d, w);
+            }
+            // edge-weight gradients: Ez^{n+1} (after the source), Hx^{n+1/2},
+            // Hy^{n+1/2} of the owned cells of the window one cell around the design
+            if (dsg && dsg_rec && win_rec) {
+                const int wr = a - (dsg_j0 - 1), W = dsg_w + 2, H = dsg_h + 2;
+                const long long nr = n - rec_n0;
+                if (wr >= 0 && wr < H && nr >= 0 && nr < rec_len && a >= tk.ya && a < tk.yb && out_lane) {
+                    const size_t ww = (size_t)W * H;
+                    float* re = dsg_rec + (size_t)nr * 3 * ww + (size_t)wr * W;
+                    const int wc = cx - (dsg_i0 - 1);
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const int d = wc + q;
+                        if (d >= 0 && d < W && cx + q >= tk.x0 && cx + q < tk.x0 + (STRIP - 2 * HALO)) {
+                            re[d] = comp4(E[t], q);
+                            re[ww + d] = comp4(X[t], q);
+                            re[2 * ww + d] = comp4(Y[t], q);
+                        }
+                    }
+                }
             }
             if (has_samp) {
                 const int nq = n_samp < 32 ? n_samp : 32;

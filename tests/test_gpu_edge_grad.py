@@ -28,7 +28,7 @@ def _grad_err(g, ref):
     return float(np.max(np.abs(g - ref) / den))
 
 
-def _gpu(sc, ckpt, dLdF, *, tblock=4, segment=16, mode=2, sig_d=None):
+def _gpu(sc, ckpt, dLdF, *, tblock=4, segment=16, mode=2, sig_d=None, kernel=0):
     from paper_2405_00814_gb300 import fdtd
     i0, j0, w, h = sc.design
     sim = fdtd.Simulation.batch([sc])
@@ -36,6 +36,7 @@ def _gpu(sc, ckpt, dLdF, *, tblock=4, segment=16, mode=2, sig_d=None):
     sim.set_scene_source(sc.source)
     sim.set_design(i0, j0, sc.design_eps, sig_d)
     mid = sim.add_dft_monitor(sc.monitors, sc.freqs)
+    sim.set_option("kernel", kernel)
     sim.set_option("tblock", tblock)
     sim.set_option("segment", segment)
     sim.set_option("adj_store", mode)
@@ -47,11 +48,14 @@ def _gpu(sc, ckpt, dLdF, *, tblock=4, segment=16, mode=2, sig_d=None):
     return F, g
 
 
-@pytest.mark.parametrize("side,npml,design,at,nsteps,ckpt,tblock,segment", [
-    (96, 8, 24, None, 600, 64, 4, 16),          # centred design, last segment partial
-    (150, 10, 37, (96, 30), 500, 100, 3, 24),   # two strips: the design crosses the strip boundary at x = 120
+@pytest.mark.parametrize("side,npml,design,at,nsteps,ckpt,tblock,segment,kernel", [
+    (96, 8, 24, None, 600, 64, 4, 16, 0),          # centred design, last segment partial
+    (150, 10, 37, (96, 30), 500, 100, 3, 24, 0),   # two strips: the design crosses the strip boundary at x = 120
+    (96, 8, 24, None, 300, 50, 2, 8, 0),           # short tasks: the window spans several task rows
+    (96, 8, 24, None, 300, 64, 1, 64, 1),          # unfused forward (window copied after each step)
+    (120, 8, 30, (20, 50), 300, 64, 4, 32, 2),     # persistent forward; the design's tasks reach the CPML
 ])
-def test_edge_grad_matches_oracle(side, npml, design, at, nsteps, ckpt, tblock, segment):
+def test_edge_grad_matches_oracle(side, npml, design, at, nsteps, ckpt, tblock, segment, kernel):
     import oracle
     sc = scenes.adjoint_scenes(side=side, n_designs=1, nsteps=nsteps, npml=npml, design=design, n_monitors=3)[0]
     if at is not None:
@@ -59,7 +63,7 @@ def test_edge_grad_matches_oracle(side, npml, design, at, nsteps, ckpt, tblock, 
     rng = np.random.default_rng(side)
     dLdF = (rng.standard_normal((len(sc.monitors), len(sc.freqs))) +
             1j * rng.standard_normal((len(sc.monitors), len(sc.freqs)))) * 1e9
-    F, g = _gpu(sc, ckpt, dLdF, tblock=tblock, segment=segment)
+    F, g = _gpu(sc, ckpt, dLdF, tblock=tblock, segment=segment, kernel=kernel)
     osim = oracle.TMz(sc, nsteps_src=sc.nsteps)
     g1, g2, Fo = osim.graph_edge_grad(sc.nsteps, sc.monitors, sc.freqs, dLdF.real, dLdF.imag)
     ref = osim.edge_class_grad(g1, g2, sc.design)
@@ -118,3 +122,9 @@ def test_edge_grad_refusals():
     with pytest.raises(fdtd.FDTDError):
         sim.step(5)
     sim.close()
+    for mode in (1, 2):                          # the recorded rectangle cannot change size
+        sim = _recorded(sc, mode, steps=10)
+        with pytest.raises(fdtd.FDTDError):
+            sim.set_design(i0, j0, np.full((h, w + 1), 2.0))
+        sim.set_design(i0 + 1, j0, np.full((h, w), 2.0))
+        sim.close()
