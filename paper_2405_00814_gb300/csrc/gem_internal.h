@@ -64,11 +64,10 @@ struct TmzDev {
     // over the design rectangle; the adjoint kernels inject dL/dE^{n+1} at the
     // monitor cells and keep dL/dE^{n+1} over the design rectangle, which a
     // reduction after each segment turns into dL/deps_r
-    float* dsg_rec;                     // [steps][dsg_h * dsg_w], step n at n - dsg_rec_n0
+    float* dsg_rec;                     // [steps][dsg_h * dsg_w], step n at n - dsg_rec_n0; in edge-weight
+                                        // mode [steps][3][dsg_h + 2][dsg_w + 2]: Ez^{n+1}, Hx^{n+1/2},
+                                        // Hy^{n+1/2} of the window one cell around the design
     long long dsg_rec_n0, dsg_rec_len;
-    int win_rec;                        // 1: dsg_rec instead keeps [steps][3][dsg_h + 2][dsg_w + 2]:
-                                        //    Ez^{n+1}, Hx^{n+1/2}, Hy^{n+1/2} of the window one cell
-                                        //    around the design (edge-weight gradients)
     float* grad;                        // [dsg_h][dsg_w]
     float* adj_rec;                     // [steps][dsg_h * dsg_w]: dL/dE^{n+1}, step n at n - dsg_rec_n0
     int adj_edges;                      // 1: adj_rec is [steps][3][dsg_h * dsg_w]: dL/dE^{n+1},

@@ -644,7 +644,6 @@ static void patch_for_step(const fdtd_ctx* c, const AdjState* A, TmzDev* dev, in
         const size_t q = (size_t)slot * ns + k;
         float* h = q < A->hist.size() ? A->hist[q] : nullptr;
         dev[k].dsg_rec = h;
-        dev[k].win_rec = A->edges;
         dev[k].dsg_rec_n0 = slot * A->every;
         dev[k].dsg_rec_len = h ? A->every : 0;
     }

@@ -46,10 +46,11 @@ __host__ __device__ constexpr int pf_of(int T, bool pml) { return pml ? PF_B : Q
 __host__ __device__ constexpr int gen_nslot(bool pml) { return pml ? 7 : 6; }
 __host__ __device__ constexpr int gen_stage_f4(bool pml) { return gen_nslot(pml) * 32 + 8 + (pml ? 1 : 0); }
 
-// V: 0 interior, 1 CPML, 2 lite, 3 split-field layer
+// V: 0 interior, 1 CPML, 2 lite, 3 split-field layer; 5, 6: CPML, lite keeping
+// the design window (edge-weight reverse mode)
 size_t tmz_fused_smem(int T, int warps, int V) {
     if (V == 0) return (size_t)warps * stages_for(T, false) * stage_f4(false) * sizeof(float4);
-    const bool pml = V == 1 || V == 3;   // 3: split-field layer, same stages as CPML
+    const bool pml = V == 1 || V == 3 || V == 5;   // 3: split-field layer, 5: CPML keeping the design window
     return (size_t)warps * stages_for(T, pml) * gen_stage_f4(pml) * sizeof(float4);
 }
 
@@ -110,7 +111,7 @@ struct Prof {
 // One warp's task of the general kernel (any task: CPML slab, design rectangle,
 // source, probes, ragged edge).  coef_s is the scene's coefficient table (shared
 // or global memory); stage0 the warp's Q x STAGE_F4 float4 staging area.
-template <int T, bool PML, bool SPL = false>
+template <int T, bool PML, bool SPL = false, bool WREC = false>
 __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const Task& tk,
                                              const Sample2* __restrict__ samps, int parity, long long n0,
                                              const float4* coef_s, float4* stage0, int lane) {
@@ -174,7 +175,6 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
     const size_t band_plane = (size_t)dsg_h * pitch;
     float* const dsg_rec = S->dsg_rec;
     const long long rec_n0 = S->dsg_rec_n0, rec_len = S->dsg_rec_len;
-    const int win_rec = S->win_rec;
     // probes and monitor cells of this task: the first 32 ride in lane registers
     const int n_samp = tk.samp_end - tk.samp_begin;
     const bool has_samp = n_samp > 0;
@@ -414,7 +414,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
             }
             // reverse mode: E^{n+1} - E^n of the owned design cells (before the
             // source), which carries dL/deps_r of step n up to a per-cell factor
-            if (dsg && dsg_rec && !win_rec) {
+            if (!WREC && dsg && dsg_rec) {
                 const int dj = a - dsg_j0;
                 const long long nr = n0 + (t - 1) - rec_n0;
                 if (dj >= 0 && dj < dsg_h && nr >= 0 && nr < rec_len && a >= tk.ya && a < tk.yb && out_lane) {
@@ -436,7 +436,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
             }
             // edge-weight gradients: Ez^{n+1} (after the source), Hx^{n+1/2},
             // Hy^{n+1/2} of the owned cells of the window one cell around the design
-            if (dsg && dsg_rec && win_rec) {
+            if (WREC && dsg && dsg_rec) {
                 const int wr = a - (dsg_j0 - 1), W = dsg_w + 2, H = dsg_h + 2;
                 const long long nr = n - rec_n0;
                 if (wr >= 0 && wr < H && nr >= 0 && nr < rec_len && a >= tk.ya && a < tk.yb && out_lane) {
@@ -531,7 +531,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
 }
 
 // CPML blocks run 2 warps, lite blocks 4 (the lists are padded to that)
-template <int T, bool PML, bool SPL = false>
+template <int T, bool PML, bool SPL = false, bool WREC = false>
 __global__ void __launch_bounds__(PML ? 256 : 128, PML ? 1 : 3) k_tmz_fused(const TmzDev* __restrict__ scenes,
                                                    const Task* __restrict__ tasks, int n_tasks,
                                                    const Sample2* __restrict__ samps, int parity,
@@ -553,7 +553,7 @@ __global__ void __launch_bounds__(PML ? 256 : 128, PML ? 1 : 3) k_tmz_fused(cons
     if (tid >= n_tasks) return;
     const Task tk = tasks[tid];
     if (tk.scene < 0) return;
-    general_task<T, PML, SPL>(S, tk, samps, parity, n0, coef_s, smem_f4 + (size_t)wib * Q * STAGE_F4, lane);
+    general_task<T, PML, SPL, WREC>(S, tk, samps, parity, n0, coef_s, smem_f4 + (size_t)wib * Q * STAGE_F4, lane);
 }
 
 // ===========================================================================
@@ -601,7 +601,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctl, long long spin_limit
     return ok_s != 0;
 }
 
-template <int T>
+template <int T, bool WREC>
 __global__ void __launch_bounds__(256, 1) k_tmz_persistent(const TmzDev* __restrict__ scenes,
                                                           const Task* __restrict__ tasks, int n_tasks,
                                                           const Sample2* __restrict__ samps, int parity0,
@@ -624,22 +624,22 @@ __global__ void __launch_bounds__(256, 1) k_tmz_persistent(const TmzDev* __restr
             const Task tk = tasks[idx];
             if (tk.scene >= 0) {
                 const TmzDev* S = scenes + tk.scene;
-                general_task<T, true>(S, tk, samps, parity, nb, S->coef, stage0, lane);
+                general_task<T, true, false, WREC>(S, tk, samps, parity, nb, S->coef, stage0, lane);
             }
         }
         if (!grid_barrier(ctl, spin_limit, skip_cta)) return;
     }
 }
 
-template <int T>
+template <int T, bool WREC>
 static cudaError_t launch_persistent_T(const fdtd_ctx* c, cudaStream_t st, int parity, long long n0, int n_blocks,
                                        long long spin_limit, int* grid_out) {
     const int warps = 8;
     const size_t smem = tmz_fused_smem(T, warps, 1);
-    cudaError_t e = ensure_dyn_smem((const void*)k_tmz_persistent<T>, smem);
+    cudaError_t e = ensure_dyn_smem((const void*)k_tmz_persistent<T, WREC>, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0, dev = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tmz_persistent<T>, warps * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tmz_persistent<T, WREC>, warps * 32, smem);
     if (e != cudaSuccess) return e;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -656,7 +656,7 @@ static cudaError_t launch_persistent_T(const fdtd_ctx* c, cudaStream_t st, int p
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_tmz_persistent<T>, (const TmzDev*)c->d_scenes, (const Task*)c->d_tasks_all,
+    return cudaLaunchKernelEx(&cfg, k_tmz_persistent<T, WREC>, (const TmzDev*)c->d_scenes, (const Task*)c->d_tasks_all,
                               c->n_tasks_all, (const Sample2*)c->d_samp, parity, n0, n_blocks, c->d_ctl, spin_limit,
                               c->opt_debug_skip);
 }
@@ -665,12 +665,21 @@ static cudaError_t launch_persistent_T(const fdtd_ctx* c, cudaStream_t st, int p
 int tmz_persistent_launch(fdtd_ctx* c, int T, long long n0, int n_blocks, int parity) {
     cudaError_t e = cudaMemsetAsync(c->d_ctl, 0, (size_t)(4 + n_blocks) * sizeof(unsigned), c->stream);
     int grid = 0;
+    const bool wrec = adj_edge_mode(c);   // edge-weight reverse mode: keep the design window
     if (e == cudaSuccess) {
         switch (T) {
-            case 1: e = launch_persistent_T<1>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid); break;
-            case 2: e = launch_persistent_T<2>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid); break;
-            case 3: e = launch_persistent_T<3>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid); break;
-            default: e = launch_persistent_T<4>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid); break;
+            case 1: e = wrec ? launch_persistent_T<1, true>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid)
+                             : launch_persistent_T<1, false>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid);
+                break;
+            case 2: e = wrec ? launch_persistent_T<2, true>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid)
+                             : launch_persistent_T<2, false>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid);
+                break;
+            case 3: e = wrec ? launch_persistent_T<3, true>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid)
+                             : launch_persistent_T<3, false>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid);
+                break;
+            default: e = wrec ? launch_persistent_T<4, true>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid)
+                              : launch_persistent_T<4, false>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid);
+                break;
         }
     }
     c->launches++;
@@ -985,7 +994,8 @@ __global__ void k_tmz_finite(const TmzDev* __restrict__ scenes, int parity, int*
 // launchers
 // ===========================================================================
 // variant 0: interior (clean) tasks; 1: CPML tasks; 2: lite tasks (design
-// rectangle, source, probes or ragged edge, no CPML)
+// rectangle, source, probes or ragged edge, no CPML); 3: split-field layer
+// tasks; 5, 6: variants 1, 2 keeping the design window (edge-weight mode)
 template <int T, int V>
 static cudaError_t launch_fused_T(const Task* tasks, int n_tasks, int warps, const fdtd_ctx* c, cudaStream_t st,
                                   long long n0, int parity) {
@@ -996,6 +1006,16 @@ static cudaError_t launch_fused_T(const Task* tasks, int n_tasks, int warps, con
         e = ensure_dyn_smem((const void*)k_tmz_fused<T, true>, smem);
         if (e != cudaSuccess) return e;
         k_tmz_fused<T, true><<<blocks, warps * 32, smem, st>>>(c->d_scenes, tasks, n_tasks, c->d_samp, parity, n0);
+    } else if (V == 5) {
+        e = ensure_dyn_smem((const void*)k_tmz_fused<T, true, false, true>, smem);
+        if (e != cudaSuccess) return e;
+        k_tmz_fused<T, true, false, true><<<blocks, warps * 32, smem, st>>>(c->d_scenes, tasks, n_tasks, c->d_samp,
+                                                                             parity, n0);
+    } else if (V == 6) {
+        e = ensure_dyn_smem((const void*)k_tmz_fused<T, false, false, true>, smem);
+        if (e != cudaSuccess) return e;
+        k_tmz_fused<T, false, false, true><<<blocks, warps * 32, smem, st>>>(c->d_scenes, tasks, n_tasks, c->d_samp,
+                                                                              parity, n0);
     } else if (V == 3) {
         e = ensure_dyn_smem((const void*)k_tmz_fused<T, true, true>, smem);
         if (e != cudaSuccess) return e;
@@ -1042,8 +1062,11 @@ int tmz_fused_launch(fdtd_ctx* c, int T, int warps, long long n0, int parity) {
             sl = c->aux2;
         }
     }
+    // edge-weight reverse mode: the variants that keep the design window
+    const bool wrec = adj_edge_mode(c);
     if (e == cudaSuccess && c->n_tasks_b > 0) {
-        e = launch_fused<1>(c->d_tasks_b, c->n_tasks_b, c->warps_b, c, sb, T, n0, parity);
+        e = wrec ? launch_fused<5>(c->d_tasks_b, c->n_tasks_b, c->warps_b, c, sb, T, n0, parity)
+                 : launch_fused<1>(c->d_tasks_b, c->n_tasks_b, c->warps_b, c, sb, T, n0, parity);
         c->launches++;
     }
     if (e == cudaSuccess && c->n_tasks_s > 0) {
@@ -1052,7 +1075,8 @@ int tmz_fused_launch(fdtd_ctx* c, int T, int warps, long long n0, int parity) {
         c->launches++;
     }
     if (e == cudaSuccess && nl > 0) {
-        e = launch_fused<2>(c->d_tasks_l, nl, c->warps_l, c, sl, T, n0, parity);
+        e = wrec ? launch_fused<6>(c->d_tasks_l, nl, c->warps_l, c, sl, T, n0, parity)
+                 : launch_fused<2>(c->d_tasks_l, nl, c->warps_l, c, sl, T, n0, parity);
         c->launches++;
     }
     if (e == cudaSuccess && ni > 0) {
