@@ -309,6 +309,7 @@ fdtd_ctx* ctx_new(void* stream) {
     c->warps_l = 4;
     c->d_tasks_s = nullptr;
     c->n_tasks_s = 0;
+    c->any_design = false;
     c->aux = c->aux2 = nullptr;
     c->ev_fork = c->ev_join = c->ev_join2 = nullptr;
     cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
@@ -435,9 +436,10 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     const int wout = STRIP - 2 * HALO;
     std::vector<Task> tasks, tasks_b, tasks_l, tasks_s;
     std::vector<Sample2> tsamp;
-    const int warps_b = 2, warps_l = 4;
+    const int warps_b = 2;
     bool any_design = false;
     for (const Scene2* s : c->s2) any_design = any_design || s->d_dsg != nullptr;
+    const int warps_l = 4;   // lite CTAs; each list is padded to its launch's CTA width
     for (int k = 0; k < ns; k++) {
         Scene2* s = c->s2[k];
         const size_t first = tasks.size(), first_b = tasks_b.size(), first_l = tasks_l.size(),
@@ -589,6 +591,7 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     c->n_tasks_all = (int)all.size();
     c->n_tasks_l = (int)tasks_l.size();
     c->n_tasks_s = (int)tasks_s.size();
+    c->any_design = any_design;
     c->warps_l = warps_l;
     c->warps_b = warps_b;
     c->task_tb = T;

@@ -47,10 +47,10 @@ __host__ __device__ constexpr int gen_nslot(bool pml) { return pml ? 7 : 6; }
 __host__ __device__ constexpr int gen_stage_f4(bool pml) { return gen_nslot(pml) * 32 + 8 + (pml ? 1 : 0); }
 
 // V: 0 interior, 1 CPML, 2 lite, 3 split-field layer; 5, 6: CPML, lite keeping
-// the design window (edge-weight reverse mode)
+// the design window (edge-weight reverse mode); 7: CPML without design code
 size_t tmz_fused_smem(int T, int warps, int V) {
     if (V == 0) return (size_t)warps * stages_for(T, false) * stage_f4(false) * sizeof(float4);
-    const bool pml = V == 1 || V == 3 || V == 5;   // 3: split-field layer, 5: CPML keeping the design window
+    const bool pml = V == 1 || V == 3 || V == 5 || V == 7;   // 3 split layer, 5 window-keeping, 7 design-free CPML
     return (size_t)warps * stages_for(T, pml) * gen_stage_f4(pml) * sizeof(float4);
 }
 
@@ -111,7 +111,7 @@ struct Prof {
 // One warp's task of the general kernel (any task: CPML slab, design rectangle,
 // source, probes, ragged edge).  coef_s is the scene's coefficient table (shared
 // or global memory); stage0 the warp's Q x STAGE_F4 float4 staging area.
-template <int T, bool PML, bool SPL = false, bool WREC = false>
+template <int T, bool PML, bool SPL = false, bool WREC = false, bool DSG = true>
 __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const Task& tk,
                                              const Sample2* __restrict__ samps, int parity, long long n0,
                                              const float4* coef_s, float4* stage0, int lane) {
@@ -168,7 +168,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
                          S->f[F_PHXY][parity ^ 1], S->f[F_PHYX][parity ^ 1]};
 
     // design rectangle (continuous permittivity); scene scalars live in registers
-    const bool dsg = (tk.flags & TASK_DSG) != 0;
+    const bool dsg = DSG && (tk.flags & TASK_DSG) != 0;   // DSG = false: compiled without design code
     const int dsg_i0 = S->dsg_i0, dsg_j0 = S->dsg_j0, dsg_w = S->dsg_w, dsg_h = S->dsg_h;
     const float4* __restrict__ dsg_coef = S->dsg_coef;
     const float* __restrict__ band = S->dsg_band;
@@ -531,7 +531,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
 }
 
 // CPML blocks run 2 warps, lite blocks 4 (the lists are padded to that)
-template <int T, bool PML, bool SPL = false, bool WREC = false>
+template <int T, bool PML, bool SPL = false, bool WREC = false, bool DSG = true>
 __global__ void __launch_bounds__(PML ? 256 : 128, PML ? 1 : 3) k_tmz_fused(const TmzDev* __restrict__ scenes,
                                                    const Task* __restrict__ tasks, int n_tasks,
                                                    const Sample2* __restrict__ samps, int parity,
@@ -546,14 +546,17 @@ __global__ void __launch_bounds__(PML ? 256 : 128, PML ? 1 : 3) k_tmz_fused(cons
     const int warps = blockDim.x >> 5;
     const int tid = blockIdx.x * warps + wib;
 
-    // every block holds tasks of one scene: stage its coefficient table
+    // every block holds tasks of one scene: stage its coefficient table (a
+    // block of padding only returns)
+    if (tasks[blockIdx.x * warps].scene < 0) return;
     const TmzDev* S = scenes + tasks[blockIdx.x * warps].scene;
     for (int k = threadIdx.x; k < 256; k += blockDim.x) coef_s[k] = S->coef[k];
     __syncthreads();
     if (tid >= n_tasks) return;
     const Task tk = tasks[tid];
     if (tk.scene < 0) return;
-    general_task<T, PML, SPL, WREC>(S, tk, samps, parity, n0, coef_s, smem_f4 + (size_t)wib * Q * STAGE_F4, lane);
+    general_task<T, PML, SPL, WREC, DSG>(S, tk, samps, parity, n0, coef_s, smem_f4 + (size_t)wib * Q * STAGE_F4,
+                                         lane);
 }
 
 // ===========================================================================
@@ -995,7 +998,8 @@ __global__ void k_tmz_finite(const TmzDev* __restrict__ scenes, int parity, int*
 // ===========================================================================
 // variant 0: interior (clean) tasks; 1: CPML tasks; 2: lite tasks (design
 // rectangle, source, probes or ragged edge, no CPML); 3: split-field layer
-// tasks; 5, 6: variants 1, 2 keeping the design window (edge-weight mode)
+// tasks; 5, 6: variants 1, 2 keeping the design window (edge-weight mode);
+// 7: variant 1 compiled without the design paths (contexts with no design)
 template <int T, int V>
 static cudaError_t launch_fused_T(const Task* tasks, int n_tasks, int warps, const fdtd_ctx* c, cudaStream_t st,
                                   long long n0, int parity) {
@@ -1006,6 +1010,11 @@ static cudaError_t launch_fused_T(const Task* tasks, int n_tasks, int warps, con
         e = ensure_dyn_smem((const void*)k_tmz_fused<T, true>, smem);
         if (e != cudaSuccess) return e;
         k_tmz_fused<T, true><<<blocks, warps * 32, smem, st>>>(c->d_scenes, tasks, n_tasks, c->d_samp, parity, n0);
+    } else if (V == 7) {
+        e = ensure_dyn_smem((const void*)k_tmz_fused<T, true, false, false, false>, smem);
+        if (e != cudaSuccess) return e;
+        k_tmz_fused<T, true, false, false, false><<<blocks, warps * 32, smem, st>>>(c->d_scenes, tasks, n_tasks,
+                                                                                     c->d_samp, parity, n0);
     } else if (V == 5) {
         e = ensure_dyn_smem((const void*)k_tmz_fused<T, true, false, true>, smem);
         if (e != cudaSuccess) return e;
@@ -1065,8 +1074,10 @@ int tmz_fused_launch(fdtd_ctx* c, int T, int warps, long long n0, int parity) {
     // edge-weight reverse mode: the variants that keep the design window
     const bool wrec = adj_edge_mode(c);
     if (e == cudaSuccess && c->n_tasks_b > 0) {
-        e = wrec ? launch_fused<5>(c->d_tasks_b, c->n_tasks_b, c->warps_b, c, sb, T, n0, parity)
-                 : launch_fused<1>(c->d_tasks_b, c->n_tasks_b, c->warps_b, c, sb, T, n0, parity);
+        // without a design rectangle the CPML tasks run a build with no design code
+        e = wrec             ? launch_fused<5>(c->d_tasks_b, c->n_tasks_b, c->warps_b, c, sb, T, n0, parity)
+            : c->any_design  ? launch_fused<1>(c->d_tasks_b, c->n_tasks_b, c->warps_b, c, sb, T, n0, parity)
+                             : launch_fused<7>(c->d_tasks_b, c->n_tasks_b, c->warps_b, c, sb, T, n0, parity);
         c->launches++;
     }
     if (e == cudaSuccess && c->n_tasks_s > 0) {
