@@ -309,7 +309,8 @@ fdtd_ctx* ctx_new(void* stream) {
     c->warps_l = 4;
     c->d_tasks_s = nullptr;
     c->n_tasks_s = 0;
-    c->any_design = false;
+    c->d_tasks_bd = nullptr;
+    c->n_tasks_bd = 0;
     c->aux = c->aux2 = nullptr;
     c->ev_fork = c->ev_join = c->ev_join2 = nullptr;
     cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
@@ -434,7 +435,7 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     // list, the rest to the interior list; each list is padded to whole CTAs
     // per scene so that a CTA never mixes scenes.
     const int wout = STRIP - 2 * HALO;
-    std::vector<Task> tasks, tasks_b, tasks_l, tasks_s;
+    std::vector<Task> tasks, tasks_b, tasks_l, tasks_s, tasks_bd;
     std::vector<Sample2> tsamp;
     const int warps_b = 2;
     bool any_design = false;
@@ -443,7 +444,7 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     for (int k = 0; k < ns; k++) {
         Scene2* s = c->s2[k];
         const size_t first = tasks.size(), first_b = tasks_b.size(), first_l = tasks_l.size(),
-                     first_s = tasks_s.size();
+                     first_s = tasks_s.size(), first_bd = tasks_bd.size();
         // Tasks with a CPML slab, the design rectangle, the source or a probe in
         // reach, or a ragged right edge, run the general kernel ("boundary" list);
         // the rest run the lean interior kernel.  General warps are heavier per
@@ -477,7 +478,10 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
             // the lite kernel pays for its own launch and stream fork only when a
             // design rectangle gives it work; otherwise its tasks join the CPML list
             // tasks within reach of a split-field layer run the split variant
+            // CPML tasks with the design in reach run the build with design code,
+            // all other CPML tasks the design-free one
             if ((t.flags & TASK_PML) && s->split) tasks_s.push_back(t);
+            else if ((t.flags & TASK_PML) && (t.flags & TASK_DSG)) tasks_bd.push_back(t);
             else if ((t.flags & TASK_PML) || (general && !any_design)) tasks_b.push_back(t);
             else if (general) tasks_l.push_back(t);
             else tasks.push_back(t);
@@ -505,6 +509,8 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
             while ((tasks_l.size() - first_l) % warps_l) tasks_l.push_back(pad);
         if (tasks_s.size() > first_s)
             while ((tasks_s.size() - first_s) % warps_b) tasks_s.push_back(pad);
+        if (tasks_bd.size() > first_bd)
+            while ((tasks_bd.size() - first_bd) % warps_b) tasks_bd.push_back(pad);
     }
     std::vector<Sample2> ssamp;
     std::vector<int> soff(ns + 1, 0);
@@ -516,6 +522,8 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     std::vector<Task> all;
     for (const Task& t : tasks_b)
         if (t.scene >= 0) all.push_back(t);
+    for (const Task& t : tasks_bd)
+        if (t.scene >= 0) all.push_back(t);
     for (const Task& t : tasks_l)
         if (t.scene >= 0) all.push_back(t);
     for (const Task& t : tasks)
@@ -524,9 +532,11 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     dfree(c->d_tasks_all);
     dfree(c->d_tasks_l);
     dfree(c->d_tasks_s);
+    dfree(c->d_tasks_bd);
     dfree(c->d_dft);
     c->d_tasks_l = nullptr;
     c->d_tasks_s = nullptr;
+    c->d_tasks_bd = nullptr;
     c->d_dft = nullptr;
     c->n_dft = 0;
     c->d_scenes = nullptr; c->d_tasks = nullptr; c->d_tasks_b = nullptr; c->d_samp = nullptr; c->d_samp_scene = nullptr;
@@ -540,6 +550,7 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     if ((rc = dalloc(c, &c->d_tasks_all, all.size() * sizeof(Task), "tasks"))) return rc;
     if ((rc = dalloc(c, &c->d_tasks_l, tasks_l.size() * sizeof(Task), "tasks"))) return rc;
     if ((rc = dalloc(c, &c->d_tasks_s, tasks_s.size() * sizeof(Task), "tasks"))) return rc;
+    if ((rc = dalloc(c, &c->d_tasks_bd, tasks_bd.size() * sizeof(Task), "tasks"))) return rc;
     if ((rc = dalloc(c, &c->d_samp, tsamp.size() * sizeof(Sample2), "samples"))) return rc;
     if ((rc = dalloc(c, &c->d_samp_scene, ssamp.size() * sizeof(Sample2), "samples"))) return rc;
     if ((rc = dalloc(c, &c->d_samp_off, soff.size() * sizeof(int), "sample offsets"))) return rc;
@@ -554,6 +565,8 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
         CK(cudaMemcpyAsync(c->d_tasks_l, tasks_l.data(), tasks_l.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
     if (!tasks_s.empty())
         CK(cudaMemcpyAsync(c->d_tasks_s, tasks_s.data(), tasks_s.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
+    if (!tasks_bd.empty())
+        CK(cudaMemcpyAsync(c->d_tasks_bd, tasks_bd.data(), tasks_bd.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
     if (!tsamp.empty())
         CK(cudaMemcpyAsync(c->d_samp, tsamp.data(), tsamp.size() * sizeof(Sample2), cudaMemcpyHostToDevice, c->stream), "upload");
     if (!ssamp.empty())
@@ -591,7 +604,7 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     c->n_tasks_all = (int)all.size();
     c->n_tasks_l = (int)tasks_l.size();
     c->n_tasks_s = (int)tasks_s.size();
-    c->any_design = any_design;
+    c->n_tasks_bd = (int)tasks_bd.size();
     c->warps_l = warps_l;
     c->warps_b = warps_b;
     c->task_tb = T;
@@ -732,6 +745,7 @@ void fdtd_destroy(fdtd_ctx* c) {
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     dfree(c->d_tasks_l);
     dfree(c->d_tasks_s);
+    dfree(c->d_tasks_bd);
     if (c->aux) cudaStreamDestroy(c->aux);
     if (c->aux2) cudaStreamDestroy(c->aux2);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);

@@ -171,7 +171,8 @@ struct fdtd_ctx {
     int n_tasks_b, warps_b;
     gem::Task* d_tasks_s;          // tasks within reach of a split-field PML layer
     int n_tasks_s;
-    bool any_design;               // some scene has a design rectangle (set by rebuild)
+    gem::Task* d_tasks_bd;         // CPML tasks with a design rectangle in reach
+    int n_tasks_bd;
     gem::Task* d_tasks_l;          // lite tasks: design, source, probes or ragged edge, no CPML
     int n_tasks_l, warps_l;
     cudaStream_t aux, aux2;        // forked streams for the CPML and lite tasks

@@ -80,7 +80,7 @@ __device__ __forceinline__ float cget(const float4& v, int c) { return c == 0 ? 
 // Reuses Sample2 {i, j, comp (unused), slot}.
 
 // GEN: design rectangle, adjoint sources, ragged edge; PMLV: CPML auxiliaries
-template <int T, bool GEN, bool PMLV>
+template <int T, bool GEN, bool PMLV, bool DSGV = true>
 __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 : (GEN ? 3 : 2)) k_adj(const TmzDev* __restrict__ scenes,
                                                           const Task* __restrict__ tasks, int n_tasks,
                                                           const Sample2* __restrict__ srcs, int parity,
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
     const int r_last = tk.yb + T - 1;
 
     const bool pml = PV && (tk.flags & TASK_PML) != 0;
-    const bool dsg = GEN && (tk.flags & TASK_DSG) != 0;
+    const bool dsg = GEN && DSGV && (tk.flags & TASK_DSG) != 0;   // DSGV = false: built without design code
     const bool has_src = GEN && tk.samp_end > tk.samp_begin;
     const int dsg_i0 = S->dsg_i0, dsg_j0 = S->dsg_j0, dsg_w = S->dsg_w, dsg_h = S->dsg_h;
     const float4* __restrict__ dsg_coef = S->dsg_coef;
@@ -512,26 +512,27 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
     await_<0>();
 }
 
-template <int T, bool GEN, bool PMLV>
+template <int T, bool GEN, bool PMLV, bool DSGV = true>
 cudaError_t launch_adj_v(const TmzDev* dev, const Task* tasks, int n, int warps, const Sample2* srcs, int parity,
                          long long n_top, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const size_t sm = adj_smem(T, warps, GEN, GEN && PMLV);
-    cudaError_t e = ensure_dyn_smem((const void*)k_adj<T, GEN, PMLV>, sm);
+    cudaError_t e = ensure_dyn_smem((const void*)k_adj<T, GEN, PMLV, DSGV>, sm);
     if (e != cudaSuccess) return e;
-    k_adj<T, GEN, PMLV><<<n / warps, warps * 32, sm, st>>>(dev, tasks, n, srcs, parity, n_top);
+    k_adj<T, GEN, PMLV, DSGV><<<n / warps, warps * 32, sm, st>>>(dev, tasks, n, srcs, parity, n_top);
     return cudaGetLastError();
 }
 
 struct AdjLists {
-    const Task *t0, *t1, *t2;   // interior, CPML, lite
-    int n0, n1, n2, w0, w1, w2;
+    const Task *t0, *t1, *t2, *t3;   // interior, CPML without a design in reach, lite, CPML with one
+    int n0, n1, n2, n3, w0, w1, w2;
 };
 
 template <int T>
 cudaError_t launch_adj_T(const TmzDev* dev, const AdjLists& L, const Sample2* srcs, int parity, long long n_top,
                          cudaStream_t s0, cudaStream_t s1, cudaStream_t s2) {
-    cudaError_t e = launch_adj_v<T, true, true>(dev, L.t1, L.n1, L.w1, srcs, parity, n_top, s1);
+    cudaError_t e = launch_adj_v<T, true, true, false>(dev, L.t1, L.n1, L.w1, srcs, parity, n_top, s1);
+    if (e == cudaSuccess) e = launch_adj_v<T, true, true>(dev, L.t3, L.n3, L.w1, srcs, parity, n_top, s1);
     if (e == cudaSuccess) e = launch_adj_v<T, true, false>(dev, L.t2, L.n2, L.w2, srcs, parity, n_top, s2);
     if (e == cudaSuccess) e = launch_adj_v<T, false, false>(dev, L.t0, L.n0, L.w0, srcs, parity, n_top, s0);
     return e;
@@ -884,7 +885,7 @@ static int reverse_run(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, 
         for (void* p : to_free) cudaFree(p);
     };
     std::vector<TmzDev> fwd(ns), adj(ns);
-    std::vector<Task> tasks, tasks_g, tasks_l;   // interior, CPML, lite general
+    std::vector<Task> tasks, tasks_g, tasks_l, tasks_gd;   // interior, CPML, lite general, CPML + design
     std::vector<Sample2> tsrc;
     std::vector<float*> rec_of(ns), erec_of(ns), grad_of(ns), fac_of(ns);
     const int T = c->opt_tblock, seg = c->opt_segment, warps = c->opt_warps, gwarps = 2, lwarps = 4;
@@ -945,7 +946,8 @@ static int reverse_run(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, 
         // adjoint tasks: general if a CPML slab, the design rectangle or an
         // adjoint source is within reach, or the strip is ragged
         const int wout = STRIP - 2 * HALO;
-        const size_t first = tasks.size(), first_g = tasks_g.size(), first_l = tasks_l.size();
+        const size_t first = tasks.size(), first_g = tasks_g.size(), first_l = tasks_l.size(),
+                     first_gd = tasks_gd.size();
         for (int ya = 0; ya < s->ny; ya += seg) {
             for (int x0 = 0; x0 < s->nx; x0 += wout) {
                 const int lx0 = x0 - HALO, lx1 = x0 - HALO + STRIP;
@@ -976,7 +978,7 @@ static int reverse_run(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, 
                     for (int y = ya; y < yb; y += segg) {
                         bool g2;
                         Task t2 = make(y, std::min(y + segg, yb), &g2);
-                        (t2.flags & TASK_PML ? tasks_g : tasks_l).push_back(t2);
+                        (t2.flags & TASK_PML ? (t2.flags & TASK_DSG ? tasks_gd : tasks_g) : tasks_l).push_back(t2);
                     }
                 }
             }
@@ -990,13 +992,16 @@ static int reverse_run(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, 
             while ((tasks_g.size() - first_g) % gwarps) tasks_g.push_back(pad);
         if (tasks_l.size() > first_l)
             while ((tasks_l.size() - first_l) % lwarps) tasks_l.push_back(pad);
+        if (tasks_gd.size() > first_gd)
+            while ((tasks_gd.size() - first_gd) % gwarps) tasks_gd.push_back(pad);
     }
     TmzDev *d_fwd = nullptr, *d_adj = nullptr;
-    Task *d_t = nullptr, *d_tg = nullptr, *d_tl = nullptr;
+    Task *d_t = nullptr, *d_tg = nullptr, *d_tl = nullptr, *d_tgd = nullptr;
     Sample2* d_src = nullptr;
     if (!dmalloc(ns * sizeof(TmzDev), (void**)&d_fwd) || !dmalloc(ns * sizeof(TmzDev), (void**)&d_adj) ||
         !dmalloc(tasks.size() * sizeof(Task), (void**)&d_t) || !dmalloc(tasks_g.size() * sizeof(Task), (void**)&d_tg) ||
-        !dmalloc(tasks_l.size() * sizeof(Task), (void**)&d_tl) || !dmalloc(tsrc.size() * sizeof(Sample2), (void**)&d_src)) {
+        !dmalloc(tasks_l.size() * sizeof(Task), (void**)&d_tl) || !dmalloc(tasks_gd.size() * sizeof(Task), (void**)&d_tgd) ||
+        !dmalloc(tsrc.size() * sizeof(Sample2), (void**)&d_src)) {
         cleanup();
         c->err = "adjoint: out of device memory";
         return FDTD_ENOMEM;
@@ -1005,6 +1010,8 @@ static int reverse_run(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, 
     if (!tasks.empty()) cudaMemcpyAsync(d_t, tasks.data(), tasks.size() * sizeof(Task), cudaMemcpyHostToDevice, st);
     if (!tasks_g.empty()) cudaMemcpyAsync(d_tg, tasks_g.data(), tasks_g.size() * sizeof(Task), cudaMemcpyHostToDevice, st);
     if (!tasks_l.empty()) cudaMemcpyAsync(d_tl, tasks_l.data(), tasks_l.size() * sizeof(Task), cudaMemcpyHostToDevice, st);
+    if (!tasks_gd.empty())
+        cudaMemcpyAsync(d_tgd, tasks_gd.data(), tasks_gd.size() * sizeof(Task), cudaMemcpyHostToDevice, st);
     if (!tsrc.empty()) cudaMemcpyAsync(d_src, tsrc.data(), tsrc.size() * sizeof(Sample2), cudaMemcpyHostToDevice, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
@@ -1053,7 +1060,8 @@ static int reverse_run(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, 
         L.t0 = d_t; L.n0 = (int)tasks.size(); L.w0 = warps;
         L.t1 = d_tg; L.n1 = (int)tasks_g.size(); L.w1 = gwarps;
         L.t2 = d_tl; L.n2 = (int)tasks_l.size(); L.w2 = lwarps;
-        const bool fork1 = L.n1 > 0, fork2 = L.n2 > 0;
+        L.t3 = d_tgd; L.n3 = (int)tasks_gd.size();
+        const bool fork1 = L.n1 > 0 || L.n3 > 0, fork2 = L.n2 > 0;
         for (int64_t q = len; q > 0 && rc == FDTD_OK;) {
             const int done = (int)std::min<int64_t>(T, q);
             const long long n_top = a0 + q - 1;
@@ -1069,7 +1077,7 @@ static int reverse_run(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, 
                 case 3: e = launch_adj_T<3>(d_adj, L, d_src, apar, n_top, st, s1, s2); break;
                 default: e = launch_adj_T<4>(d_adj, L, d_src, apar, n_top, st, s1, s2); break;
             }
-            c->launches += (L.n0 > 0) + (L.n1 > 0) + (L.n2 > 0);
+            c->launches += (L.n0 > 0) + (L.n1 > 0) + (L.n2 > 0) + (L.n3 > 0);
             if (fork1) {
                 cudaEventRecord(c->ev_join, c->aux);
                 cudaStreamWaitEvent(st, c->ev_join, 0);

@@ -999,7 +999,8 @@ __global__ void k_tmz_finite(const TmzDev* __restrict__ scenes, int parity, int*
 // variant 0: interior (clean) tasks; 1: CPML tasks; 2: lite tasks (design
 // rectangle, source, probes or ragged edge, no CPML); 3: split-field layer
 // tasks; 5, 6: variants 1, 2 keeping the design window (edge-weight mode);
-// 7: variant 1 compiled without the design paths (contexts with no design)
+// 7: variant 1 compiled without the design paths (CPML tasks with no design in
+// reach; those with one run variant 1 or 5)
 template <int T, int V>
 static cudaError_t launch_fused_T(const Task* tasks, int n_tasks, int warps, const fdtd_ctx* c, cudaStream_t st,
                                   long long n0, int parity) {
@@ -1058,7 +1059,7 @@ static cudaError_t launch_fused(const Task* tasks, int n_tasks, int warps, const
 // on two forked streams, joined before the next block reads the new buffer
 int tmz_fused_launch(fdtd_ctx* c, int T, int warps, long long n0, int parity) {
     cudaError_t e = cudaSuccess;
-    const int nb = c->n_tasks_b + c->n_tasks_s, nl = c->n_tasks_l, ni = c->n_tasks;
+    const int nb = c->n_tasks_b + c->n_tasks_s + c->n_tasks_bd, nl = c->n_tasks_l, ni = c->n_tasks;
     cudaStream_t sb = c->stream, sl = c->stream;
     if ((nb > 0) + (nl > 0) + (ni > 0) > 1) {
         e = cudaEventRecord(c->ev_fork, c->stream);
@@ -1074,10 +1075,14 @@ int tmz_fused_launch(fdtd_ctx* c, int T, int warps, long long n0, int parity) {
     // edge-weight reverse mode: the variants that keep the design window
     const bool wrec = adj_edge_mode(c);
     if (e == cudaSuccess && c->n_tasks_b > 0) {
-        // without a design rectangle the CPML tasks run a build with no design code
-        e = wrec             ? launch_fused<5>(c->d_tasks_b, c->n_tasks_b, c->warps_b, c, sb, T, n0, parity)
-            : c->any_design  ? launch_fused<1>(c->d_tasks_b, c->n_tasks_b, c->warps_b, c, sb, T, n0, parity)
-                             : launch_fused<7>(c->d_tasks_b, c->n_tasks_b, c->warps_b, c, sb, T, n0, parity);
+        // CPML tasks with no design rectangle in reach: the build without design code
+        e = launch_fused<7>(c->d_tasks_b, c->n_tasks_b, c->warps_b, c, sb, T, n0, parity);
+        c->launches++;
+    }
+    if (e == cudaSuccess && c->n_tasks_bd > 0) {
+        // CPML tasks with the design in reach follow on the same stream
+        e = wrec ? launch_fused<5>(c->d_tasks_bd, c->n_tasks_bd, c->warps_b, c, sb, T, n0, parity)
+                 : launch_fused<1>(c->d_tasks_bd, c->n_tasks_bd, c->warps_b, c, sb, T, n0, parity);
         c->launches++;
     }
     if (e == cudaSuccess && c->n_tasks_s > 0) {

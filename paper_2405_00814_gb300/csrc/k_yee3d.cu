@@ -759,7 +759,7 @@ int fdtd_create3(const fdtd_grid* g, double dx, double dt, double courant, const
     c->cur = 0; c->t = 0; c->parity = 0; c->launches = 0;
     c->opt_kernel = 0; c->opt_tblock = 1; c->opt_segment = 24; c->opt_warps = 8; c->opt_segment_b = 0;
     c->dirty = true;
-    c->d_scenes = nullptr; c->d_tasks = nullptr; c->d_tasks_b = nullptr; c->n_tasks_b = 0; c->warps_b = 2; c->d_tasks_l = nullptr; c->n_tasks_l = 0; c->warps_l = 4; c->d_tasks_s = nullptr; c->n_tasks_s = 0; c->any_design = false;
+    c->d_scenes = nullptr; c->d_tasks = nullptr; c->d_tasks_b = nullptr; c->n_tasks_b = 0; c->warps_b = 2; c->d_tasks_l = nullptr; c->n_tasks_l = 0; c->warps_l = 4; c->d_tasks_s = nullptr; c->n_tasks_s = 0; c->d_tasks_bd = nullptr; c->n_tasks_bd = 0;
     c->d_dft = nullptr; c->n_dft = 0; c->opt_adj_store = 1;
     c->aux = c->aux2 = nullptr; c->ev_fork = c->ev_join = c->ev_join2 = nullptr;
     c->d_samp = nullptr; c->d_samp_scene = nullptr; c->d_samp_off = nullptr;
