@@ -99,8 +99,8 @@ extern "C" {
                                 cell wider than each design rectangle after every step
                                 (steps x (w + 2)(h + 2) x 12 B) */
 #define FDTD_OPT_SEGMENT_B 8 /* 2D: rows per warp task of the boundary kernels (CPML slabs, source, probes, design,
-                                ragged edge); 0 (default) = max(8, segment / 2).  Those warps carry a longer
-                                serial chain per row, so shorter tasks shorten the critical path */
+                                ragged edge), forward and reverse sweep; 0 (default) = max(8, segment / 2).
+                                Those warps carry a longer serial chain per row than interior ones */
 
 typedef struct fdtd_ctx fdtd_ctx;
 

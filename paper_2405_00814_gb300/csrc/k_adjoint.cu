@@ -974,7 +974,7 @@ static int reverse_run(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, 
                     tasks.push_back(t);
                 } else {
                     tsrc.resize(mark);
-                    const int segg = std::max(8, seg / 2);
+                    const int segg = c->opt_segment_b > 0 ? c->opt_segment_b : std::max(8, seg / 2);
                     for (int y = ya; y < yb; y += segg) {
                         bool g2;
                         Task t2 = make(y, std::min(y + segg, yb), &g2);
