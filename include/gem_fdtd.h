@@ -59,7 +59,8 @@ extern "C" {
                                in the layer, each part damped by the graded conductivity of its derivative's
                                axis, H by the matched sigma* = sigma mu0/eps0, semi-implicit as eq. (7);
                                sigma = sigma_max (depth/d)^3, sigma_max = 3.2 / (eta0 delta).  The layer's
-                               cells must be vacuum (eps_r 1, sigma 0).  Steps with the unfused kernels. */
+                               cells must be vacuum (eps_r 1, sigma 0).  Steps with the temporally blocked
+                               kernels (FDTD_OPT_KERNEL 0) or the unfused pair (1; also used in place of 2). */
 
 /* field components */
 #define FDTD_EX 0
@@ -80,7 +81,8 @@ extern "C" {
 #define FDTD_OPT_KERNEL 0    /* 2D: 0 = fused temporally blocked stream, two kernels per T-step block (default);
                                 1 = one H and one E launch per step;
                                 2 = persistent: one cooperative launch runs many T-step blocks of every scene,
-                                    warps pulling tasks from a shared counter, a bounded grid barrier between blocks.
+                                    warps pulling tasks from a shared counter, a bounded grid barrier between blocks
+                                    (a context with a split-field PML steps with the unfused pair instead).
                                 3D: 0 = fused z-marching kernel (default), 1 = one H and one E launch per step */
 #define FDTD_OPT_TBLOCK 1    /* time steps per HBM pass of the fused kernel, 1..4 */
 #define FDTD_OPT_SEGMENT 2   /* 2D: rows per warp task of the fused kernel (multiple of 8, >= 8);
