@@ -128,3 +128,50 @@ def test_edge_grad_refusals():
             sim.set_design(i0, j0, np.full((h, w + 1), 2.0))
         sim.set_design(i0 + 1, j0, np.full((h, w), 2.0))
         sim.close()
+
+
+def test_edge_grad_two_scenes_and_device_output():
+    """A batch of two designs: each scene's [11, h, w] block equals the one its
+    own single-scene context gives, on host and in a CUDA tensor."""
+    import torch
+    from paper_2405_00814_gb300 import fdtd
+    scs = scenes.adjoint_scenes(side=96, n_designs=2, nsteps=300, npml=8, design=24, n_monitors=3)
+    rng = np.random.default_rng(21)
+    dLdF = [(rng.standard_normal((3, 1)) + 1j * rng.standard_normal((3, 1))) * 1e9 for _ in scs]
+    singles = [_gpu(sc, 60, d)[1] for sc, d in zip(scs, dLdF)]
+    sim = fdtd.Simulation.batch(scs)
+    for k, sc in enumerate(scs):
+        sim.select(k)
+        sim.set_scene_source(sc.source)
+        i0, j0, w, h = sc.design
+        sim.set_design(i0, j0, sc.design_eps)
+        sim.add_dft_monitor(sc.monitors, sc.freqs)
+    sim.set_option("tblock", 4)
+    sim.set_option("segment", 16)
+    sim.set_option("adj_store", 2)
+    sim.set_checkpointing(60)
+    sim.step(scs[0].nsteps)
+    shapes = [(sc.design[3], sc.design[2]) for sc in scs]
+    g = sim.edge_grad(dLdF, shapes)
+    for k in range(2):
+        assert _grad_err(g[k], singles[k]) <= 1e-5, k
+    sim.close()
+    # the same run with the result written into a device tensor
+    sim = fdtd.Simulation.batch(scs)
+    for k, sc in enumerate(scs):
+        sim.select(k)
+        sim.set_scene_source(sc.source)
+        i0, j0, w, h = sc.design
+        sim.set_design(i0, j0, sc.design_eps)
+        sim.add_dft_monitor(sc.monitors, sc.freqs)
+    sim.set_option("tblock", 4)
+    sim.set_option("segment", 16)
+    sim.set_option("adj_store", 2)
+    sim.set_checkpointing(60)
+    sim.step(scs[0].nsteps)
+    out = torch.empty(2 * 11 * 24 * 24, dtype=torch.float32, device="cuda")
+    sim.edge_grad(dLdF, shapes, out=out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().reshape(2, 11, 24, 24)
+    assert np.array_equal(got, np.stack(g))
+    sim.close()

@@ -123,3 +123,30 @@ def test_set_materials_refusals():
     with pytest.raises(fdtd.FDTDError):
         sim3.set_materials(np.zeros((n, n), np.uint8), np.array([1.0]), np.array([0.0]))
     sim3.close()
+
+
+def test_set_materials_in_a_batch_touches_only_the_selected_scene():
+    from paper_2405_00814_gb300 import fdtd
+    a, b = _pair(side=160, nsteps=150)
+    c = scenes.ellipse_scene(side=200, nsteps=150, seed_id=4)
+    ref = fdtd.Simulation.batch([b, c])
+    for k, s in enumerate((b, c)):
+        ref.select(k)
+        ref.set_scene_source(s.source)
+    ref.step(150)
+    want = []
+    for k, s in enumerate((b, c)):
+        ref.select(k)
+        want.append(ref.get_field("ez", (s.ny, s.nx)))
+    ref.close()
+    sim = fdtd.Simulation.batch([a, c])
+    for k, s in enumerate((a, c)):
+        sim.select(k)
+        sim.set_scene_source(s.source)
+    sim.select(0)
+    sim.set_materials(b.mat, b.eps_r, b.sigma)
+    sim.step(150)
+    for k, s in enumerate((b, c)):
+        sim.select(k)
+        assert np.array_equal(sim.get_field("ez", (s.ny, s.nx)), want[k]), k
+    sim.close()
