@@ -1227,7 +1227,7 @@ int fdtd_autotune(fdtd_ctx* c, int trial_steps, double* best_ms) {
         if (rc == FDTD_OK) rc = time_of(win, 4 * trial_steps, &base2);
         base = std::min(base, base2);
         win_b = 0;
-        for (int b : {8, 12, 16, 20, 24, 32, 40, win.seg}) {
+        for (int b : {4, 8, 12, 16, 20, 24, 32, 40, win.seg}) {
             if (rc != FDTD_OK) break;
             c->opt_segment_b = b;
             double per = 0, per2 = 0;
