@@ -140,12 +140,15 @@ class Simulation:
         self.dims = 2
         self.shape = None           # (nx, ny, nz) of a single-scene context
         self.split = False
+        self._cells = []            # cells of each scene, for the buffer-size checks
+        self._sel = 0
         if _handle is not None:
             self._h = _handle
             return
         g = _grid_of(scene, boundary)
         self.dims = g.dims
         self.shape = (g.nx, g.ny, g.nz)
+        self._cells = [g.nx * g.ny * g.nz]
         self.split = g.boundary == SPLIT_PML
         mat = np.ascontiguousarray(scene.mat, np.uint8)
         tab = _mat_table(scene.eps_r, scene.sigma)
@@ -171,6 +174,7 @@ class Simulation:
         rc = L.fdtd_create_batch(n, grids, dx, dt, mp, tp, nm, _stream_handle(stream), C.byref(h))
         sim = cls(_handle=h)
         sim._check(rc)
+        sim._cells = [s.nx * s.ny for s in scenes]
         return sim
 
     # ---------------------------------------------------------------- basics
@@ -206,7 +210,20 @@ class Simulation:
 
     def select(self, scene: int):
         self._check(self._L.fdtd_select_scene(self._h, scene))
+        self._sel = scene
         return self
+
+    def _need(self, buf, n, what):
+        """The library writes or reads exactly n float32 (or uint8) elements of buf:
+        refuse a buffer of another size before it can overrun."""
+        size = buf.numel() if hasattr(buf, "numel") else np.asarray(buf).size
+        if size != n:
+            raise ValueError(f"{what}: buffer holds {size} elements, the library uses {n}")
+        if hasattr(buf, "is_contiguous") and not buf.is_contiguous():
+            raise ValueError(f"{what}: the tensor must be contiguous")
+
+    def _field_cells(self):
+        return self._cells[self._sel] if self._sel < len(self._cells) else None
 
     def set_option(self, name: str, value: int):
         self._check(self._L.fdtd_set_option(self._h, OPT[name], int(value)))
@@ -260,6 +277,9 @@ class Simulation:
         asynchronous) and table for the selected 2D scene (fdtd_set_materials)."""
         m = mat if (isinstance(mat, np.ndarray) and mat.dtype == np.uint8 and mat.flags.c_contiguous) \
             else np.ascontiguousarray(mat, np.uint8)
+        n = self._field_cells()
+        if n is not None:
+            self._need(m, n, "set_materials")
         tab = _mat_table(eps_r, sigma)
         self._check(self._L.fdtd_set_materials(self._h, m.ctypes.data, tab, len(eps_r)))
 
@@ -353,10 +373,17 @@ class Simulation:
     def get_field(self, component, shape=None, out=None):
         """Copy a field out.  out: a CUDA torch tensor (device copy) or None (host
         numpy array of the given shape)."""
+        n = self._field_cells()
         if out is not None and hasattr(out, "data_ptr"):
+            if n is not None:
+                self._need(out, n, "get_field")
             self._check(self._L.fdtd_get_field(self._h, COMP[component], out.data_ptr(), 1))
             return out
         arr = np.empty(shape, np.float32) if out is None else out
+        if n is not None:
+            self._need(arr, n, "get_field")
+        if arr.dtype != np.float32 or not arr.flags.c_contiguous:
+            raise ValueError("get_field: out must be a C-contiguous float32 array")
         self._check(self._L.fdtd_get_field(self._h, COMP[component], arr.ctypes.data, 0))
         return arr
 
@@ -372,10 +399,15 @@ class Simulation:
         return self.get_field({"hx": "hx", "hz": "hy"}[component], shape)
 
     def set_field(self, component, values):
+        n = self._field_cells()
         if hasattr(values, "data_ptr"):
+            if n is not None:
+                self._need(values, n, "set_field")
             self._check(self._L.fdtd_set_field(self._h, COMP[component], values.data_ptr(), 1))
             return
         arr = np.ascontiguousarray(values, np.float32)
+        if n is not None:
+            self._need(arr, n, "set_field")
         self._check(self._L.fdtd_set_field(self._h, COMP[component], arr.ctypes.data, 0))
 
     def read_probe(self, pid, n=None) -> np.ndarray:
@@ -414,6 +446,7 @@ class Simulation:
         re = np.ascontiguousarray(g.real, np.float32)
         im = np.ascontiguousarray(g.imag, np.float32)
         if out is not None and hasattr(out, "data_ptr"):
+            self._need(out, int(np.prod(grad_shape)), "adjoint_grad")
             self._check(self._L.fdtd_adjoint_grad(self._h, re.ctypes.data, im.ctypes.data, out.data_ptr(), 1))
             return out
         res = np.empty(grad_shape, np.float32)
@@ -430,10 +463,11 @@ class Simulation:
                                  else np.ravel(dLdF))
         re = np.ascontiguousarray(g.real, np.float32)
         im = np.ascontiguousarray(g.imag, np.float32)
+        sizes = [EDGE_CLASSES * h * w for h, w in design_shapes]
         if out is not None and hasattr(out, "data_ptr"):
+            self._need(out, sum(sizes), "edge_grad")
             self._check(self._L.fdtd_edge_grad(self._h, re.ctypes.data, im.ctypes.data, out.data_ptr(), 1))
             return out
-        sizes = [EDGE_CLASSES * h * w for h, w in design_shapes]
         res = np.empty(sum(sizes), np.float32)
         self._check(self._L.fdtd_edge_grad(self._h, re.ctypes.data, im.ctypes.data, res.ctypes.data, 0))
         parts = np.split(res, np.cumsum(sizes)[:-1])

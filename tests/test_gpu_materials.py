@@ -121,7 +121,7 @@ def test_set_materials_refusals():
                         mat=np.zeros((n, n, n), np.uint8), eps_r=np.array([1.0]), sigma=np.array([0.0]), nsteps=1)
     sim3 = fdtd.from_scene(s3, source=False)
     with pytest.raises(fdtd.FDTDError):
-        sim3.set_materials(np.zeros((n, n), np.uint8), np.array([1.0]), np.array([0.0]))
+        sim3.set_materials(np.zeros((n * n, n), np.uint8), np.array([1.0]), np.array([0.0]))
     sim3.close()
 
 
@@ -149,4 +149,27 @@ def test_set_materials_in_a_batch_touches_only_the_selected_scene():
     for k, s in enumerate((b, c)):
         sim.select(k)
         assert np.array_equal(sim.get_field("ez", (s.ny, s.nx)), want[k]), k
+    sim.close()
+
+
+def test_buffers_of_the_wrong_size_are_refused():
+    """The binding checks every buffer the library reads or writes against the
+    selected scene's size before the call (a short buffer would be overrun)."""
+    import torch
+    from paper_2405_00814_gb300 import fdtd
+    a, _ = _pair(side=64, nsteps=10)
+    c = scenes.ellipse_scene(side=80, nsteps=10, seed_id=4)
+    sim = fdtd.Simulation.batch([a, c])
+    with pytest.raises(ValueError):
+        sim.get_field("ez", (64, 63))
+    with pytest.raises(ValueError):
+        sim.get_field("ez", out=torch.empty(64 * 64 - 1, device="cuda"))
+    with pytest.raises(ValueError):
+        sim.set_field("hx", np.zeros((64, 65), np.float32))
+    with pytest.raises(ValueError):
+        sim.set_materials(np.zeros((80, 80), np.uint8), a.eps_r, a.sigma)
+    sim.select(1)
+    assert sim.get_field("ez", (80, 80)).shape == (80, 80)
+    with pytest.raises(ValueError):
+        sim.get_field("ez", (64, 64))
     sim.close()
