@@ -24,8 +24,18 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
-def _report(config, result, err, tol):
+def r2(x, ref):
+    """Coefficient of determination of x against ref (the agreement statistic the
+    paper quotes over its validation scenes, Sec. V-A)."""
+    x = np.asarray(x, np.float64).ravel()
+    ref = np.asarray(ref, np.float64).ravel()
+    return 1.0 - float(np.sum((x - ref) ** 2)) / float(np.sum((ref - ref.mean()) ** 2))
+
+
+def _report(config, result, err, tol, r2v=None):
     line = {"config": config, "result": result, "error": float(err), "tol": tol}
+    if r2v is not None:
+        line["r2"] = r2v
     print("PARITY " + json.dumps(line))
     path = os.environ.get("PARITY_REPORT")
     if path:
@@ -43,8 +53,9 @@ def test_cavity_128():
     o = oracle_run(sc, sc.nsteps, probes=sc.probes)
     g = gpu_run(sc, sc.nsteps, tblock=4, segment=32)
     for c in ("ez", "hx", "hy"):
-        _report("cavity128_pec_ricker_500", c, rel_l2(g[c], o[c]), TOL_FIELD)
-    _report("cavity128_pec_ricker_500", "probes", rel_l2(g["probes"], o["probes"]), TOL_FIELD)
+        _report("cavity128_pec_ricker_500", c, rel_l2(g[c], o[c]), TOL_FIELD, r2(g[c], o[c]))
+    _report("cavity128_pec_ricker_500", "probes", rel_l2(g["probes"], o["probes"]), TOL_FIELD,
+            r2(g["probes"], o["probes"]))
 
 
 def test_heterogeneous_cpml_with_dft():
@@ -56,8 +67,8 @@ def test_heterogeneous_cpml_with_dft():
     g = gpu_run(sc, sc.nsteps, tblock=4, segment=56, warps=4)
     name = "ellipses512_cpml16_gaussmod_1200"
     for c in ("ez", "hx", "hy"):
-        _report(name, c, rel_l2(g[c], o[c]), TOL_FIELD)
-    _report(name, "probes", rel_l2(g["probes"], o["probes"]), TOL_FIELD)
+        _report(name, c, rel_l2(g[c], o[c]), TOL_FIELD, r2(g[c], o[c]))
+    _report(name, "probes", rel_l2(g["probes"], o["probes"]), TOL_FIELD, r2(g["probes"], o["probes"]))
     _report(name, "dft", _dft_err(g["dft"], o["dft"]), TOL_DFT)
 
 
@@ -82,7 +93,8 @@ def test_3d_boxes_plane_dft():
     for c in ("ex", "ey", "ez", "hx", "hy", "hz"):
         got = sim.get_field(c, (sc.nz, sc.ny, sc.nx))
         share = float(np.linalg.norm(osim.state[c])) / vec[c]
-        _report(name, c + " (vs its vector field)", rel_l2(got, osim.state[c], floor=vec[c]), TOL_FIELD)
+        _report(name, c + " (vs its vector field)", rel_l2(got, osim.state[c], floor=vec[c]), TOL_FIELD,
+                r2(got, osim.state[c]))
         own = rel_l2(got, osim.state[c])
         if share >= 0.1:
             _report(name, c, own, TOL_FIELD)
