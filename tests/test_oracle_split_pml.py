@@ -95,3 +95,22 @@ def test_split_profile_grading(oracle_mod):
     assert math.isclose(sE[3], smax * (5 / 8) ** 3, rel_tol=1e-14)
     assert math.isclose(sH[0], smax * (7.5 / 8) ** 3, rel_tol=1e-14)
     assert math.isclose(sH[n - 1], smax * (7.5 / 8) ** 3, rel_tol=1e-14)
+
+
+def test_split_line_source_is_the_sum_of_point_sources(oracle_mod):
+    """Linearity of the split recurrence: a line source over cells (i, j0 .. j1-1)
+    gives the sum of the point-source runs, also where the line enters the layer."""
+    sc = scenes.ellipse_scene(side=72, nsteps=140, npml=8)
+    i, j0, j1 = 5, 30, 36          # i = 5 lies inside the 8-cell layer
+    sc.source = scenes.Source(i, j0, kind="gauss_mod", params=(20e9,), length=j1 - j0)
+    line = oracle_mod.TMzSplit(sc)
+    line.run(sc.nsteps)
+    total = {k: np.zeros((sc.ny, sc.nx)) for k in ("ezx", "ezy", "hx", "hy")}
+    for j in range(j0, j1):
+        sc.source = scenes.Source(i, j, kind="gauss_mod", params=(20e9,))
+        pt = oracle_mod.TMzSplit(sc)
+        pt.run(sc.nsteps)
+        for k in total:
+            total[k] += pt.state[k]
+    for k in total:
+        assert np.max(np.abs(line.state[k] - total[k])) <= 1e-12 * max(np.max(np.abs(total[k])), 1e-300), k
