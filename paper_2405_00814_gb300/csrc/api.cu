@@ -512,6 +512,31 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
         if (tasks_bd.size() > first_bd)
             while ((tasks_bd.size() - first_bd) % warps_b) tasks_bd.push_back(pad);
     }
+    // every list is launched in blocks of its own width: a block holds tasks of one
+    // scene and starts with a real task, and every task lies inside its scene
+    auto valid = [&](const std::vector<Task>& L, int width, const char* what) {
+        if (L.size() % width) return fail(c, FDTD_ESTATE, "internal: %s list not padded to %d", what, width);
+        for (size_t b = 0; b < L.size(); b += width) {
+            const int sc = L[b].scene;
+            if (sc < 0 || sc >= ns) return fail(c, FDTD_ESTATE, "internal: %s block %zu starts with padding", what, b);
+            for (int q = 0; q < width; q++) {
+                const Task& t = L[b + q];
+                if (t.scene < 0) continue;
+                const Scene2* s = c->s2[t.scene];
+                if (t.scene != sc || t.x0 < 0 || t.x0 >= s->nx || t.ya < 0 || t.ya >= t.yb || t.yb > s->ny)
+                    return fail(c, FDTD_ESTATE, "internal: %s task %zu out of its scene", what, b + q);
+            }
+        }
+        return (int)FDTD_OK;
+    };
+    {
+        int vr = valid(tasks, warps, "interior");
+        if (!vr) vr = valid(tasks_b, warps_b, "CPML");
+        if (!vr) vr = valid(tasks_bd, warps_b, "CPML design");
+        if (!vr) vr = valid(tasks_s, warps_b, "split");
+        if (!vr) vr = valid(tasks_l, warps_l, "lite");
+        if (vr) return vr;
+    }
     std::vector<Sample2> ssamp;
     std::vector<int> soff(ns + 1, 0);
     for (int k = 0; k < ns; k++) {
