@@ -178,6 +178,22 @@ void scene2_free(Scene2* s) {
     delete s;
 }
 
+// the PEC walls i = 0 and j = 0 of a padded material map take PEC_MAT
+__global__ void k_pec_walls(uint8_t* __restrict__ mat, int pitch, int nx, int ny) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nx) mat[(size_t)PAD_Y * pitch + PAD_X + q] = (uint8_t)PEC_MAT;
+    else if (q < nx + ny) mat[(size_t)(q - nx + PAD_Y) * pitch + PAD_X] = (uint8_t)PEC_MAT;
+}
+
+static int pec_walls(fdtd_ctx* c, Scene2* s) {
+    const int n = s->nx + s->ny;
+    k_pec_walls<<<(n + 255) / 256, 256, 0, c->stream>>>(s->d_mat, s->pitch, s->nx, s->ny);
+    c->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "PEC walls");
+    return FDTD_OK;
+}
+
 int scene2_init(fdtd_ctx* c, const fdtd_grid* g, double dx, double dt, double courant, const uint8_t* mat,
                 const fdtd_material* table, int n_mat, Scene2** out) {
     *out = nullptr;
@@ -210,8 +226,14 @@ int scene2_init(fdtd_ctx* c, const fdtd_grid* g, double dx, double dt, double co
         if (!(table[m].sigma >= 0)) return fail(c, FDTD_EINVAL, "material %d: sigma must be >= 0", m);
     }
     const int64_t ncell = (int64_t)g->nx * g->ny;
-    for (int64_t k = 0; k < ncell; k++)
-        if (mat[k] >= n_mat) return fail(c, FDTD_EINVAL, "material index %d at cell %lld >= n_mat %d", mat[k], (long long)k, n_mat);
+    {
+        uint8_t mx = 0;   // a branch-free pass first; the offending cell is looked up only on failure
+        for (int64_t k = 0; k < ncell; k++) mx = mat[k] > mx ? mat[k] : mx;
+        if (mx >= n_mat)
+            for (int64_t k = 0; k < ncell; k++)
+                if (mat[k] >= n_mat)
+                    return fail(c, FDTD_EINVAL, "material index %d at cell %lld >= n_mat %d", mat[k], (long long)k, n_mat);
+    }
     if (split) {
         // the split layer's coefficients are per-axis profiles of vacuum
         for (int j = 0; j < g->ny; j++)
@@ -249,13 +271,10 @@ int scene2_init(fdtd_ctx* c, const fdtd_grid* g, double dx, double dt, double co
             if (rc) { scene2_free(s); return rc; }
             cudaMemsetAsync(s->fbuf[f][p], 0, fbytes, c->stream);
         }
-    // padded material map: pads and the PEC walls i = 0, j = 0 get PEC_MAT
-    std::vector<uint8_t> pm((size_t)s->pitch * s->rows, (uint8_t)PEC_MAT);
-    for (int j = 0; j < s->ny; j++)
-        for (int i = 0; i < s->nx; i++)
-            pm[(size_t)(j + PAD_Y) * s->pitch + i + PAD_X] =
-                (i == 0 || j == 0) ? (uint8_t)PEC_MAT : mat[(size_t)j * s->nx + i];
-    int rc = dalloc(c, &s->d_mat, pm.size(), "material map");
+    // padded material map: pads and the PEC walls i = 0, j = 0 get PEC_MAT (the
+    // map is copied into the padded layout on the device, walls marked after)
+    const size_t mat_bytes = (size_t)s->pitch * s->rows;
+    int rc = dalloc(c, &s->d_mat, mat_bytes, "material map");
     if (rc) { scene2_free(s); return rc; }
     // coefficient table
     std::vector<float4> co(256, make_float4(0, 0, 0, 0));
@@ -275,7 +294,11 @@ int scene2_init(fdtd_ctx* c, const fdtd_grid* g, double dx, double dt, double co
     }
     rc = dalloc(c, &s->d_prof, prof.size() * sizeof(float), "profiles");
     if (rc) { scene2_free(s); return rc; }
-    cudaError_t e = cudaMemcpyAsync(s->d_mat, pm.data(), pm.size(), cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e = cudaMemsetAsync(s->d_mat, PEC_MAT, mat_bytes, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(s->d_mat + (size_t)PAD_Y * s->pitch + PAD_X, s->pitch, mat, s->nx, s->nx, s->ny,
+                              cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && pec_walls(c, s) != FDTD_OK) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_coef, co.data(), 256 * sizeof(float4), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_prof, prof.data(), prof.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -674,21 +697,6 @@ int step_prepare(fdtd_ctx* c, int64_t n_steps) {
     return FDTD_OK;
 }
 
-// the PEC walls i = 0 and j = 0 of a padded material map take PEC_MAT
-__global__ void k_pec_walls(uint8_t* __restrict__ mat, int pitch, int nx, int ny) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < nx) mat[(size_t)PAD_Y * pitch + PAD_X + q] = (uint8_t)PEC_MAT;
-    else if (q < nx + ny) mat[(size_t)(q - nx + PAD_Y) * pitch + PAD_X] = (uint8_t)PEC_MAT;
-}
-
-static int pec_walls(fdtd_ctx* c, Scene2* s) {
-    const int n = s->nx + s->ny;
-    k_pec_walls<<<(n + 255) / 256, 256, 0, c->stream>>>(s->d_mat, s->pitch, s->nx, s->ny);
-    c->launches++;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(c, e, "PEC walls");
-    return FDTD_OK;
-}
 }  // namespace gem
 
 // ===========================================================================
