@@ -156,7 +156,7 @@ def oracle_sweep(sides=(250, 1000, 2000, 3000, 4000, 5000, 6400), budget_s=1.5):
 
 
 def paper_sweep(stream, tune, sides=(250, 1000, 2000, 3000, 4000, 5000, 6400), nsteps=1024, runs=5):
-    """The paper's timing workload (Sec. IV, Fig. 5): free space with a 16-cell
+    """The paper's timing workload (Sec. V-C, Fig. 5): free space with a 16-cell
     absorbing boundary, square grids of the listed sides, 1024 steps, 5 runs per
     side; mean and 95% confidence half-width (Student t, 4 dof) of the device
     time per solve, and cell-updates/s.  tune None: the library's autotuner

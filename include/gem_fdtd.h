@@ -7,12 +7,12 @@
  *   layer 1 (H from curl E), eqs. (8)(9), Prop. 2 first message-passing step;
  *   layer 2 (E from curl H), eq. (7),      Prop. 2 second step,
  * with per-cell update coefficients Ca = A_-/A_+, Cb = dt/(A_+ eps),
- * A_-/+ = 1 -/+ sigma dt/(2 eps) (Sec. II-B, eq. (7)); Da = 1 and Db = dt/(mu0 d)
- * because the medium is non-magnetic outside the absorber (Sec. II-A).
+ * A_-/+ = 1 -/+ sigma dt/(2 eps) (Sec. III-B, eq. (7)); Da = 1 and Db = dt/(mu0 d)
+ * because the medium is non-magnetic outside the absorber (Sec. III-A).
  *
  * 2D runs are TMz (Ez, Hx, Hy): the paper's TE formulation (Ey, Hx, Hz in the
  * x-z plane, eqs. (3)-(5)) under the rotation x'=x, y'=z, z'=-y.  3D runs use
- * the six-component Yee cell the paper says follows directly (Sec. II-B).
+ * the six-component Yee cell the paper says follows directly (Sec. III-B).
  *
  * Grid conventions.  Cell (i, j[, k]) owns Ez(i, j) at (i dx, j dy), Hx(i, j) at
  * (i, j+1/2), Hy(i, j) at (i+1/2, j) (3D: Ex (i+1/2, j, k), Ey (i, j+1/2, k),
@@ -20,7 +20,7 @@
  * Host arrays are row-major with x fastest: [ny][nx] or [nz][ny][nx].
  * PEC walls sit at index 0 (stored zeros) and at index N (ghost zeros).
  * The absorber is a convolutional PML (Roden & Gedney) backed by that PEC; the
- * paper's own absorber is Berenger's split field (Sec. II-C, eqs. (10)-(13)).
+ * paper's own absorber is Berenger's split field (Sec. III-C, eqs. (10)-(13)).
  *
  * Ownership.  The library copies every input at call time and keeps no caller
  * pointer.  It owns all device memory of a context.  Output buffers are
@@ -54,7 +54,7 @@ extern "C" {
 
 #define FDTD_PEC 0          /* plain PEC box */
 #define FDTD_CPML 1         /* CPML of pml_cells cells on every face, backed by PEC */
-#define FDTD_SPLIT_PML 2    /* 2D only: the paper's own absorber (Sec. II-C, eqs. (10)-(13)), Berenger's
+#define FDTD_SPLIT_PML 2    /* 2D only: the paper's own absorber (Sec. III-C, eqs. (10)-(13)), Berenger's
                                split-field PML of pml_cells cells on every face, backed by PEC: Ez = Ezx + Ezy
                                in the layer, each part damped by the graded conductivity of its derivative's
                                axis, H by the matched sigma* = sigma mu0/eps0, semi-implicit as eq. (7);
@@ -116,11 +116,11 @@ typedef struct {
 
 typedef struct {
     double eps_r; /* relative permittivity, > 0 */
-    double mu_r;  /* must be 1: the method assumes a non-magnetic medium (Sec. II-A) */
+    double mu_r;  /* must be 1: the method assumes a non-magnetic medium (Sec. III-A) */
     double sigma; /* electric conductivity, S/m, >= 0 */
 } fdtd_material;
 
-/* Create a context for one scene (Sec. II-B: grid, dx, dt, material map).
+/* Create a context for one scene (Sec. III-B: grid, dx, dt, material map).
  * dx: cell size in m (> 0).  dt: time step in s; if dt <= 0 the step is
  * courant * (Courant limit), courant in (0, 1].  A dt above the limit returns
  * FDTD_EUNSTABLE.  mat_idx: host uint8 map [ny][nx] (2D) or [nz][ny][nx] (3D) of
@@ -269,7 +269,7 @@ int fdtd_autotune(fdtd_ctx* ctx, int trial_steps, double* best_ms);
 int fdtd_check_finite(fdtd_ctx* ctx);
 
 /* Reverse mode (2D).  The paper notes that message-passing layers are
- * differentiable (Sec. III-A); these calls compute the discrete adjoint of the
+ * differentiable (Sec. IV-A); these calls compute the discrete adjoint of the
  * two layers of Prop. 2 -- the transposed layers in reverse time order.
  *
  * fdtd_set_checkpointing: from now on, fdtd_step works in segments of `every`
@@ -298,7 +298,7 @@ int fdtd_adjoint_grad(fdtd_ctx* ctx, const float* dLdF_re, const float* dLdF_im,
 
 /* Learnable edge weights.  The paper's layers have fixed weights read off the
  * update equations, and it notes that message-passing layers are differentiable
- * (Sec. III-A); this is the gradient of the same loss as fdtd_adjoint_grad with
+ * (Sec. IV-A); this is the gradient of the same loss as fdtd_adjoint_grad with
  * respect to each weight of the graph of Prop. 1 whose destination node belongs
  * to a design cell (i, j), treating every weight as an independent parameter.
  * A cell owns FDTD_EDGE_CLASSES weights, in this order (destination <- source,

@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE.  Only tests/, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of bench.py may import this package.
 It computes the discrete Yee leapfrog recurrence of arXiv 2405.00814 plainly in
-double precision (Sec. II-B eqs. (7)-(9) rotated to TMz, Prop. 1/2 for the
+double precision (Sec. III-B eqs. (7)-(9) rotated to TMz, Prop. 1/2 for the
 literal graph form) and shares no code with the CUDA path; the two meet only at
 the seeded inputs from ``paper_2405_00814_gb300.scenes``.
 
@@ -451,7 +451,7 @@ def split_axis(n, npml, delta, m=3.0):
 
 
 class TMzSplit:
-    """FP64 2D TMz run with the paper's split-field PML (Berenger, Sec. II-C):
+    """FP64 2D TMz run with the paper's split-field PML (Berenger, Sec. III-C):
     the scene's npml cells on every side form the graded layer.  State: ezx,
     ezy, hx, hy; self.ez() is their Ez = Ezx + Ezy."""
 
@@ -531,7 +531,7 @@ class TMzSplit:
     def layer_e(self):
         lib().or2s_layer_e(C.byref(self._p), C.byref(self._s))
 
-    # ---- literal 4-node graph (Sec. III-B) ----
+    # ---- literal 4-node graph (Sec. IV-B) ----
     def node_index(self, kind, i, j) -> int:
         k = {"u": 0, "hx": 0, "q": 1, "hy": 1, "tx": 2, "ezx": 2, "tz": 3, "ezy": 3}[kind]
         return lib().or2s_node_index(self.nx, k, i, j)

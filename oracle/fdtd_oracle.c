@@ -6,21 +6,21 @@
  * leg may load this library; it shares no code with the CUDA path.
  *
  * What each part follows:
- *   or_coeffs_e         Sec. II-B, eq. (7): Ca = A_-/A_+, Cb = dt/(A_+ eps).
+ *   or_coeffs_e         Sec. III-B, eq. (7): Ca = A_-/A_+, Cb = dt/(A_+ eps).
  *   or2_layer_h         eqs. (8)(9) rotated to TMz (Hx, Hy from curl Ez);
  *                       Prop. 2, first message-passing step.
  *   or2_layer_e         eq. (7) rotated to TMz (Ez from curl H);
- *                       Prop. 2, second step; ordering per Sec. II-B.
+ *                       Prop. 2, second step; ordering per Sec. III-B.
  *   or_cpml_axis        CPML of Roden & Gedney (2000) (the paper's own absorber
- *                       is Berenger's split field, Sec. II-C; the CPML is the
+ *                       is Berenger's split field, Sec. III-C; the CPML is the
  *                       published replacement used by these workloads).
  *   or2_graph_*         the literal graph of Prop. 1 and the two layers of
  *                       Prop. 2, with CPML auxiliaries appended as extra nodes.
  *   or2_adjoint_*       reverse mode of the same linear recurrence (the paper
  *                       only notes the message functions are differentiable,
- *                       Sec. III-A); transposed layers in reverse order.
+ *                       Sec. IV-A); transposed layers in reverse order.
  *   or3_*               the 3D Yee extension the paper says follows directly
- *                       (Sec. II-B, Sec. III-A).
+ *                       (Sec. III-B, Sec. IV-A).
  * Parallel loops (OpenMP over rows) do not change any per-cell arithmetic.
  */
 #include "fdtd_oracle.h"

@@ -96,7 +96,7 @@ double or2_energy(const or2_problem* p, const double* eps_cell, const or2_state*
                   const double* hx_prev, const double* hy_prev);
 
 /* ---- 2D TMz with the paper's split-field PML (split_pml.c) -------------
- * Berenger's split field (Sec. II-C, eqs. (10)-(13), rotated to TMz): Ez =
+ * Berenger's split field (Sec. III-C, eqs. (10)-(13), rotated to TMz): Ez =
  * Ezx + Ezy, each part damped by the conductivity of its derivative's axis,
  * H damped by the matched sigma* = sigma mu0 / eps0; semi-implicit averaging
  * of eq. (7) throughout.  Graded sigma(rho) = sigma_max (rho/d)^m,
@@ -126,7 +126,7 @@ int or2s_run(const or2s_problem* p, or2s_state* s, int64_t n0, int64_t nsteps, o
 void or2s_layer_h(const or2s_problem* p, or2s_state* s);
 void or2s_layer_e(const or2s_problem* p, or2s_state* s);
 
-/* literal graph with absorbing boundaries (Sec. III-B): 4 nodes per cell,
+/* literal graph with absorbing boundaries (Sec. IV-B): 4 nodes per cell,
  * u(i,j) = i + 4 j nx (Hx), q(i,j) = 3 i + nx (4 j + 1) (Hy),
  * tx(i,j) = 3 i + 1 + nx (4 j + 1) (Ezx), tz(i,j) = 3 i + 2 + nx (4 j + 1) (Ezy);
  * kind 0 u, 1 q, 2 tx, 3 tz.  CSR by destination over all nodes (identity rows

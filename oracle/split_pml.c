@@ -1,7 +1,7 @@
 /*
  * FP64 oracle, part 2: the paper's own absorbing boundary, Berenger's
- * split-field PML (Sec. II-C, eqs. (10)-(13)), in TMz and as the literal
- * 4-node-per-cell graph (Sec. III-B).
+ * split-field PML (Sec. III-C, eqs. (10)-(13)), in TMz and as the literal
+ * 4-node-per-cell graph (Sec. IV-B).
  *
  * TEST INFRASTRUCTURE, like fdtd_oracle.c: only the tests, the smoke check and
  * the benchmark's CPU baseline load it.
@@ -139,7 +139,7 @@ int or2s_run(const or2s_problem* p, or2s_state* s, int64_t n0, int64_t nsteps, o
 }
 
 /* ---------------------------------------------------------------------------
- * literal graph with absorbing boundaries (Sec. III-B): 4 nx ny nodes,
+ * literal graph with absorbing boundaries (Sec. IV-B): 4 nx ny nodes,
  * u(i,j) = i + 4 j nx (Hx), q(i,j) = 3 i + nx (4 j + 1) (Hy),
  * tx(i,j) = 3 i + 1 + nx (4 j + 1) (Ezx), tz(i,j) = 3 i + 2 + nx (4 j + 1) (Ezy).
  * The Ezy neighbourhood takes u(i,j-1) (the printed u(i-1,k) is a typo: Ezy

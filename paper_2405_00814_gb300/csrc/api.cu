@@ -107,7 +107,7 @@ void cpml_axis(int n, int npml, double delta, double dt, int pad, int len, float
     }
 }
 
-// Berenger split-field layer (Sec. II-C): conductivity sigma_max (depth/d)^3,
+// Berenger split-field layer (Sec. III-C): conductivity sigma_max (depth/d)^3,
 // sigma_max = 0.8 (m+1) / (eta0 delta) with m = 3, E nodes at integer and H nodes
 // at half-integer depth.  Per node of one axis, in storage coordinates:
 // Ca, Cb/delta of the E part along this axis (vacuum, eq. (7) with sigma) and

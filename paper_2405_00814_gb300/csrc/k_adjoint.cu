@@ -2,7 +2,7 @@
 // rectangle for losses of the running DFT at monitor cells.
 //
 // The paper only remarks that message-passing layers are differentiable
-// (Sec. III-A); this is the discrete adjoint of Prop. 2's two layers: the
+// (Sec. IV-A); this is the discrete adjoint of Prop. 2's two layers: the
 // transposed layers in reverse order.  With the adjoint state (e, hx, hy, psi)
 // holding dL/d(state) after a step, one reverse step is
 //   layer 2 transposed:  gx = (Cb/dx)(1 + cEx) e + cEx psi_ezx,

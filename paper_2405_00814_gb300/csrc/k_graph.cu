@@ -12,8 +12,8 @@
 // update equations: E gathers from H at (i, j), (i-1, j), (i, j-1); H gathers
 // from E at (i, j), (i+1, j), (i, j+1).
 //
-// A scene with the split-field PML (Sec. II-C) uses the paper's graph with
-// absorbing boundaries instead (Sec. III-B): 4 nodes per cell, u(i,j) = i + 4 j nx
+// A scene with the split-field PML (Sec. III-C) uses the paper's graph with
+// absorbing boundaries instead (Sec. IV-B): 4 nodes per cell, u(i,j) = i + 4 j nx
 // (Hx), q(i,j) = 3 i + nx (4 j + 1) (Hy), tx = q + 1 (Ezx), tz = q + 2 (Ezy); Ezx
 // gathers Hy at (i, j), (i-1, j), Ezy gathers Hx at (i, j), (i, j-1), and H gathers
 // both E parts at the forward neighbours.
@@ -55,7 +55,7 @@ struct Graph {
 static inline int64_t node_t(int nx, int i, int j) { return 2 * (int64_t)i + 1 + (int64_t)nx * (3 * (int64_t)j + 1); }
 static inline int64_t node_u(int nx, int i, int j) { return (int64_t)i + 3 * (int64_t)j * nx; }
 static inline int64_t node_q(int nx, int i, int j) { return 2 * (int64_t)i + (int64_t)nx * (3 * (int64_t)j + 1); }
-// split-field graph (Sec. III-B): kind 0 u (Hx), 1 q (Hy), 2 tx (Ezx), 3 tz (Ezy)
+// split-field graph (Sec. IV-B): kind 0 u (Hx), 1 q (Hy), 2 tx (Ezx), 3 tz (Ezy)
 static inline int64_t node4(int nx, int kind, int i, int j) {
     if (kind == 0) return (int64_t)i + 4 * (int64_t)j * nx;
     return 3 * (int64_t)i + (kind - 1) + (int64_t)nx * (4 * (int64_t)j + 1);

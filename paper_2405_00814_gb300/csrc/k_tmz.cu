@@ -1,6 +1,6 @@
 // 2D TMz kernels for sm_103a.
 //
-// The leapfrog step of Sec. II-B (eqs. (7)-(9), rotated to TMz) is the two
+// The leapfrog step of Sec. III-B (eqs. (7)-(9), rotated to TMz) is the two
 // message-passing layers of Prop. 2 with the graph kept implicit in the grid:
 //   layer 1:  Hx -= Db_y (dEz/dy + psi_Hxy),  Hy += Db_x (dEz/dx + psi_Hyx)
 //   layer 2:  Ez  = Ca Ez + Cb/dx (dHy + psi_Ezx) - Cb/dy (dHx + psi_Ezy)
@@ -388,7 +388,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
             E[t].z = e_upd(E[t].z, dhy.z, dhx.z, c2);
             E[t].w = e_upd(E[t].w, dhy.w, dhx.w, c3);
             if constexpr (SPL) if (pml) {
-                // split layer (Sec. II-C): Ez = Ezx + Ezy with Ezy in the stage,
+                // split layer (Sec. III-C): Ez = Ezx + Ezy with Ezy in the stage,
                 // each part advanced with its own axis's coefficients (vacuum cells)
                 const bool ly = a < nsp || a > ny - nsp;
                 if ((ly || lane_sx) && a >= 1) {
@@ -865,7 +865,7 @@ __global__ void k_tmz_h(const TmzDev* __restrict__ scenes, int parity) {
         }
     }
     if (S.split) {
-        // split-field layer (Sec. II-C): H damped by sigma* of the axis its
+        // split-field layer (Sec. III-C): H damped by sigma* of the axis its
         // derivative runs along, semi-implicit as eq. (7)
         const Prof pr{S.prof, pitch, S.rows};
         const int np = S.split;
@@ -920,7 +920,7 @@ __global__ void k_tmz_e(const TmzDev* __restrict__ scenes, int parity) {
         const int np = S.split;
         const bool lx = i < np || i > S.nx - np, ly = j < np || j > S.ny - np;
         if (lx || ly) {
-            // split-field layer (Sec. II-C): Ez = Ezx + Ezy, Ezy kept in the
+            // split-field layer (Sec. III-C): Ez = Ezx + Ezy, Ezy kept in the
             // psi_Ezy array, each part damped along its own axis (vacuum cells)
             const Prof pr{S.prof, pitch, S.rows};
             float* pzy = S.f[F_PEZY][parity];

@@ -1,5 +1,5 @@
 // 3D Yee path: the six-component extension of the leapfrog step that the paper
-// says follows directly from the 2D scheme (Sec. II-B; Sec. III-A), with the same
+// says follows directly from the 2D scheme (Sec. III-B; Sec. IV-A), with the same
 // two layers (H from curl E, then E from curl H), per-cell Ca and Cb from eq. (7)
 // for all three E components of a cell, and a CPML of twelve auxiliaries.
 //

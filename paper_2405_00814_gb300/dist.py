@@ -7,7 +7,7 @@
 * A single grid larger than one GPU splits into y-slabs; every step needs one
   row of Ez from the +y neighbour before layer 1 and one row of Hx from the -y
   neighbour before layer 2 (the H update reads Ez(j+1), the E update reads
-  Hx(j-1); Sec. II-B eqs. (7)-(9)).  ``SlabExchange`` does that exchange with
+  Hx(j-1); Sec. III-B eqs. (7)-(9)).  ``SlabExchange`` does that exchange with
   point-to-point messages into the receiver's own buffers.  Each box in this
   build has one GPU, so the slab path is exercised on CPU ranks.
 """

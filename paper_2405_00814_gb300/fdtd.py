@@ -388,7 +388,7 @@ class Simulation:
         return arr
 
     def get_field_te(self, component, shape):
-        """A 2D field under the paper's own TE naming (Sec. II-B: Ey, Hx, Hz in the
+        """A 2D field under the paper's own TE naming (Sec. III-B: Ey, Hx, Hz in the
         x-z plane, k the second index).  The library computes TMz; the rotation
         x' = x, y' = z, z' = -y maps Ey = -Ez', Hx = Hx', Hz = Hy' with cell (i, j)
         <-> (i, k), so "ey", "hx", "hz" are read from "ez" (negated), "hx", "hy".
@@ -504,7 +504,7 @@ class Simulation:
 
 def te_node_signs(nx: int, ny: int, n_nodes: int, split: bool = False) -> np.ndarray:
     """+1 or -1 per node of the exported graph: -1 on the electric nodes (t of
-    Prop. 1; tx and tz of the split-field graph, Sec. III-B), whose value is Ez
+    Prop. 1; tx and tz of the split-field graph, Sec. IV-B), whose value is Ez
     in the library's TMz and Ey = -Ez under the paper's TE naming.  Magnetic and
     auxiliary (CPML) nodes keep their sign.  With S = diag(signs) the TE layer is
     S W S, and S h maps node values between the two namings."""

@@ -1,5 +1,5 @@
 """GPU edge-weight gradients (fdtd_edge_grad: dL/dw of the 11 weights every
-design cell owns, Sec. III-A's layers taken as learnable) against the FP64
+design cell owns, Sec. IV-A's layers taken as learnable) against the FP64
 oracle's reverse mode over the literal graph, their chain to the eps_r
 gradient, and the inputs the mode refuses."""
 import math

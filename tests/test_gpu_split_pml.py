@@ -1,4 +1,4 @@
-"""GPU: the paper's split-field PML (Berenger, Sec. II-C) through the C ABI
+"""GPU: the paper's split-field PML (Berenger, Sec. III-C) through the C ABI
 (FDTD_SPLIT_PML) against the FP64 split-field oracle, its absorption, and the
 inputs it refuses."""
 import math
@@ -89,7 +89,7 @@ def test_split_pml_refusals():
 
 
 def test_split_pml_literal_graph_matches_oracle(oracle_mod):
-    """The 4-node graph of Sec. III-B through fdtd_step_edgelist: fields and a
+    """The 4-node graph of Sec. IV-B through fdtd_step_edgelist: fields and a
     probe against the FP64 split-field oracle."""
     from paper_2405_00814_gb300 import fdtd
     sc = scenes.ellipse_scene(side=150, nsteps=400)

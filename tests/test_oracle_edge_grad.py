@@ -1,5 +1,5 @@
 """Pins of the edge-weight reverse mode of the FP64 oracle (the paper's layers
-as learnable message passing, Sec. III-A: dL/dw for every edge of both layers).
+as learnable message passing, Sec. IV-A: dL/dw for every edge of both layers).
 
 (i) The graph forward with the source and the running DFT reproduces the
 stencil run (fields and F).  (ii) dL/dw equals central finite differences of

@@ -1,5 +1,5 @@
 """Pins of the split-field PML oracle (Berenger; the paper's own absorbing
-boundary, Sec. II-C, eqs. (10)-(13), and its 4-node graph, Sec. III-B).
+boundary, Sec. III-C, eqs. (10)-(13), and its 4-node graph, Sec. IV-B).
 
 * Without a layer the split recurrence is the plain Yee recurrence: Ezx + Ezy
   evolves exactly as Ez (the split only separates the two halves of curl H).

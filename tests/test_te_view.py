@@ -1,4 +1,4 @@
-"""The paper's TE naming (Sec. II-B, Prop. 1) as a view of the library's TMz
+"""The paper's TE naming (Sec. III-B, Prop. 1) as a view of the library's TMz
 graph: with S = diag(te_node_signs), S W S applied to S h reproduces the step,
 and its interior edge weights carry the signs and magnitudes of the TE update
 equations (7)-(9) written out directly (no GPU: the graph is the oracle's)."""
