@@ -307,3 +307,85 @@ def test_line_source_is_the_sum_of_point_sources(oracle_mod):
             total[k] += pt.state[k]
     for k in total:
         assert np.max(np.abs(sim.state[k] - total[k])) <= 1e-12 * np.max(np.abs(total[k])), k
+
+
+def _cpml_recover(b, c, dt):
+    """Invert the one-step recursive-convolution coefficients of a CPML node
+    with kappa = 1: b = exp(-(sigma + alpha) dt / eps0) gives sigma + alpha, and
+    c = sigma (b - 1) / (sigma + alpha) then gives sigma; alpha is the rest."""
+    eps0 = 1.0 / (MU0 * C0 ** 2)
+    s_plus_a = -np.log(b) * eps0 / dt
+    sigma = c * s_plus_a / (b - 1.0)
+    return sigma, s_plus_a - sigma
+
+
+def test_cpml_profile_values_at_fixed_depths(oracle_mod):
+    """The absorber's profiles (Sec. III-C; Roden-Gedney CPML with the grading
+    chosen for these workloads): polynomial sigma of order 3 up to
+    sigma_max = 0.8 (m + 1) / (eta0 delta) at the PEC, kappa = 1, and alpha
+    falling linearly from alpha_max = 0.05 S/m at the inner interface to 0 at the
+    PEC.  E nodes sit at integer depths rho = npml - i, H nodes half a cell
+    further in.  sigma and alpha are recovered from (b, c) at every node and
+    compared with the profile written out at each depth, with hand values at
+    rho = 1/2, 1, npml - 1/2 and npml; a reversed alpha ramp or a half-cell
+    shift of the H nodes fails."""
+    n, npml, d = 40, 8, 1e-3
+    dt = 0.99 * d / (C0 * math.sqrt(2))
+    eps0 = 1.0 / (MU0 * C0 ** 2)
+    p = oracle_mod.cpml_axis(n, npml, d, dt)
+    eta0 = math.sqrt(MU0 / eps0)
+    smax, amax = 0.8 * 4 / (eta0 * d), 0.05
+    assert np.all(p["kE"] == 1.0) and np.all(p["kH"] == 1.0)
+    # outside the layer the node is a plain Yee node: b = c = 0 (psi stays zero)
+    assert np.all(p["bE"][npml:n - npml + 1] == 0.0) and np.all(p["cE"][npml:n - npml + 1] == 0.0)
+    assert np.all(p["bH"][npml:n - npml] == 0.0) and np.all(p["cH"][npml:n - npml] == 0.0)
+    # depth of every node inside the layer, both faces
+    nodes = [("E", i, npml - i) for i in range(npml)] + [("E", i, i - (n - npml)) for i in range(n - npml + 1, n)]
+    nodes += [("H", i, npml - i - 0.5) for i in range(npml)] + \
+             [("H", i, i + 0.5 - (n - npml)) for i in range(n - npml, n)]
+    for kind, i, rho in nodes:
+        b, c = p["b" + kind][i], p["c" + kind][i]
+        sig, alp = _cpml_recover(b, c, dt)
+        x = rho / npml
+        assert math.isclose(sig, smax * x ** 3, rel_tol=1e-9), (kind, i, rho)
+        assert math.isclose(alp, amax * (1.0 - x), rel_tol=1e-7, abs_tol=1e-9 * amax), (kind, i, rho)
+    # hand values: rho = 1/2 (H node next to the interface, both faces)
+    for i in (npml - 1, n - npml):
+        sig, alp = _cpml_recover(p["bH"][i], p["cH"][i], dt)
+        assert math.isclose(sig, smax / 4096.0, rel_tol=1e-9)          # (1/16)^3
+        assert math.isclose(alp, amax * 15.0 / 16.0, rel_tol=1e-9)
+    # rho = 1 (E node one cell in)
+    sig, alp = _cpml_recover(p["bE"][npml - 1], p["cE"][npml - 1], dt)
+    assert math.isclose(sig, smax / 512.0, rel_tol=1e-9) and math.isclose(alp, amax * 7.0 / 8.0, rel_tol=1e-9)
+    # rho = npml - 1/2 (outermost H node, both faces)
+    for i in (0, n - 1):
+        sig, alp = _cpml_recover(p["bH"][i], p["cH"][i], dt)
+        assert math.isclose(sig, smax * (15.0 / 16.0) ** 3, rel_tol=1e-9)
+        assert math.isclose(alp, amax / 16.0, rel_tol=1e-6)
+    # rho = npml: the E node on the PEC wall has alpha = 0, so c = b - 1 and
+    # b = exp(-sigma_max dt / eps0)
+    assert math.isclose(p["bE"][0], math.exp(-smax * dt / eps0), rel_tol=1e-13)
+    assert math.isclose(p["cE"][0], p["bE"][0] - 1.0, rel_tol=1e-13)
+
+
+def test_cpml_coefficients_integrate_the_kernel(oracle_mod):
+    """c is the CPML's causal kernel -(sigma / eps0) exp(-(sigma + alpha) tau / eps0)
+    (kappa = 1) integrated over one step, and b its decay over one step, so that
+    psi^{n+1} = b psi^n + c dF is the exact recursive convolution for a
+    piecewise-constant dF.  The integral is taken numerically (Gauss-Legendre),
+    with sigma and alpha written out from the grading at each depth."""
+    n, npml, d = 30, 6, 2e-3
+    dt = 0.99 * d / (C0 * math.sqrt(2))
+    eps0 = 1.0 / (MU0 * C0 ** 2)
+    p = oracle_mod.cpml_axis(n, npml, d, dt)
+    smax = 0.8 * 4 / (math.sqrt(MU0 / eps0) * d)
+    xg, wg = np.polynomial.legendre.leggauss(40)
+    tau = 0.5 * dt * (xg + 1.0)
+    for kind, i, rho in [("E", i, npml - i) for i in range(npml)] + [("H", i, npml - i - 0.5) for i in range(npml)]:
+        sig = smax * (rho / npml) ** 3
+        alp = 0.05 * (1.0 - rho / npml)
+        kern = -(sig / eps0) * np.exp(-(sig + alp) * tau / eps0)
+        c_int = 0.5 * dt * float(np.dot(wg, kern))
+        b_dec = math.exp(-(sig + alp) * dt / eps0)
+        assert math.isclose(p["c" + kind][i], c_int, rel_tol=1e-12), (kind, i)
+        assert math.isclose(p["b" + kind][i], b_dec, rel_tol=1e-13), (kind, i)

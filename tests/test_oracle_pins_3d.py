@@ -162,3 +162,32 @@ def test_cpml_reflection_bound_3d(oracle_mod, comp):
             continue  # zero by the dipole's symmetry, up to rounding
         refl = np.max(np.abs(small[:, c] - big[:, c])) / amp[c]
         assert 20 * math.log10(refl) < -70.0, c  # this grading reaches -81 .. -104 dB
+
+
+def test_plane_dft_equals_direct_sum_3d(oracle_mod):
+    """The running DFT of a plane (Sec. I: frequency responses from sampled
+    waveforms): F(f) = sum_{n>=1} E^n exp(-i 2 pi f n dt) dt over every cell of
+    the plane and every E component, against a direct FP64 sum of the stored
+    samples.  The run is split in two calls, so the step count carried between
+    calls enters the phase as well."""
+    sc = scenes.box_scene(side=20, nsteps=90, npml=4, n_boxes=3)
+    sc.source = scenes.Source(9, 8, 10, component="ez", kind="ricker", params=(20e9,))
+    kp = 11
+    freqs = np.array([2.5e9, 6.0e9, 9.5e9])
+    comps = ("ex", "ey", "ez")
+    sim = oracle_mod.Yee3D(sc)
+    samples = [(i, j, kp, c) for c in comps for j in range(sc.ny) for i in range(sc.nx)]
+    a = sim.run(50, samples=samples, plane_k=kp, plane_comps=comps, freqs=freqs)["samples"]
+    b = sim.run(40, samples=samples, plane_k=kp, plane_comps=comps, freqs=freqs)["samples"]
+    series = np.concatenate([a, b])                       # row q holds E^{q+1}
+    t = (np.arange(series.shape[0]) + 1) * sc.dt
+    direct = (series.T @ np.exp(-2j * math.pi * freqs[None, :] * t[:, None])) * sc.dt
+    direct = direct.reshape(len(comps), sc.ny, sc.nx, len(freqs)).transpose(0, 3, 1, 2)
+    re, im = sim.plane
+    scale = np.max(np.abs(direct))
+    assert scale > 0
+    assert np.max(np.abs(re - direct.real)) <= 1e-12 * scale
+    assert np.max(np.abs(im - direct.imag)) <= 1e-12 * scale
+    # the plane is not trivially zero: the dipole reaches every component
+    for c in range(3):
+        assert np.max(np.abs(direct[c])) > 1e-3 * scale
