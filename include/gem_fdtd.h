@@ -91,8 +91,10 @@ extern "C" {
 #define FDTD_OPT_GRAPH 4     /* 1: fdtd_step records its launches into a CUDA graph and replays it when called
                                 again with the same start step, step count and buffer parity (e.g. after fdtd_reset) */
 #define FDTD_OPT_SPIN_LIMIT 5     /* polls (about 0.25 us each) a persistent-kernel barrier wait makes before it gives up */
-#define FDTD_OPT_DEBUG_SKIP_CTA 6 /* test hook: this CTA of the persistent kernel never arrives at the barrier, so the
-                                     others' waits run out (-1 = off); fdtd_sync then returns FDTD_ETIMEOUT */
+#define FDTD_OPT_DEBUG_SKIP_CTA 6 /* test hook: in the next persistent launch only, this CTA never arrives at the
+                                     barrier, so the others' waits run out (-1 = off; reset to -1 by that launch);
+                                     fdtd_sync then returns FDTD_ETIMEOUT.  The timeout is sticky: later persistent
+                                     launches return without stepping until fdtd_sync has reported it */
 #define FDTD_OPT_ADJ_STORE 7 /* reverse mode, read by fdtd_set_checkpointing: 1 (default) = the forward pass keeps
                                 E^{n+1} - E^n over every design rectangle for every step in device memory
                                 (steps x design cells x 4 B) and fdtd_adjoint_grad needs no recompute;
@@ -103,6 +105,10 @@ extern "C" {
 #define FDTD_OPT_SEGMENT_B 8 /* 2D: rows per warp task of the boundary kernels (CPML slabs, source, probes, design,
                                 ragged edge), forward and reverse sweep; 0 (default) = max(8, segment / 2).
                                 Those warps carry a longer serial chain per row than interior ones */
+#define FDTD_OPT_CHECK_EVERY 9 /* 2D: N > 0 = fdtd_step scans every field for NaN/Inf each time the step count
+                                  passes a multiple of N (at the end of that T-step block; one extra launch over
+                                  Ez, Hx, Hy), into a sticky device flag that fdtd_sync reports as FDTD_EUNSTABLE
+                                  -- a blow-up found without synchronising the time loop; 0 (default) = off */
 
 typedef struct fdtd_ctx fdtd_ctx;
 
@@ -137,6 +143,47 @@ int fdtd_create_batch(int n_scenes, const fdtd_grid* grids, const double* dx, co
                       const uint8_t* const* mat_idx, const fdtd_material* const* tables,
                       const int* n_mat, void* cuda_stream, fdtd_ctx** out);
 int fdtd_select_scene(fdtd_ctx* ctx, int scene);
+
+/* y-slab sub-domain of a 2D grid: the domain decomposition the paper's related
+ * work describes (Sec. II: the grid split into sub-domains, each advanced by its
+ * own processing unit, the solutions combined), for grids larger than one GPU.
+ * The context owns rows [j0, j1) of the whole grid `grid` (nx x ny, boundary
+ * FDTD_PEC or FDTD_CPML) and holds `ghost` (1..64) extra rows on each side that
+ * has a neighbour: local row r is grid row r + j0 - ghost_lo, where ghost_lo =
+ * ghost if j0 > 0 else 0 (likewise ghost_hi above j1 < ny).  Every local-index
+ * call (sources, probes, monitors, fields) uses those local rows.
+ * mat_idx: host uint8 map of the local rows, [j1 - j0 + ghost_lo + ghost_hi][nx];
+ * the CPML profile is the whole grid's, and only the grid's real walls are PEC.
+ * Layer 1 reads Ez one row up and layer 2 reads Hx one row down (eqs. (7)-(9)),
+ * so a step spoils one more ghost row at each cut: fdtd_step takes at most
+ * `ghost` steps per call (FDTD_EINVAL otherwise), after which the caller must
+ * refresh the ghost rows from the neighbours with fdtd_halo_export /
+ * fdtd_halo_import before the next step.  A source cell within `ghost` rows of
+ * a cut must be set in both slabs that hold it.  Requires j1 - j0 >= ghost.
+ * Not available on a slab: design rectangles, reverse mode, the edge-list path
+ * and graph export, autotuning, the split-field PML, batches. */
+int fdtd_create_slab(const fdtd_grid* grid, int j0, int j1, int ghost, double dx, double dt, double courant,
+                     const uint8_t* mat_idx, const fdtd_material* table, int n_mat, void* cuda_stream,
+                     fdtd_ctx** out);
+/* Floats in one side's halo: n_arrays x ghost x nx, n_arrays = 7 with a CPML
+ * (Ez, Hx, Hy, psi_Ezx, psi_Ezy, psi_Hxy, psi_Hyx), 3 without; 0 if not a slab. */
+int64_t fdtd_halo_count(const fdtd_ctx* ctx);
+/* Copy the `ghost` owned rows next to a cut (side 0: rows j0 .. j0 + ghost - 1;
+ * side 1: rows j1 - ghost .. j1 - 1) of every halo array, packed as
+ * [array][row][nx] floats, into buf (host, or device when on_device != 0).
+ * This is what the neighbour across that cut imports.  Ordered on the
+ * context's stream; synchronises for a host buffer.  FDTD_EINVAL: not a slab,
+ * side not 0/1, no neighbour on that side, NULL buf. */
+int fdtd_halo_export(fdtd_ctx* ctx, int side, float* buf, int on_device);
+/* Overwrite the ghost rows below the slab (side 0) or above it (side 1) from a
+ * buffer the neighbour exported from its opposite side (the rows land in this
+ * context's own memory; the library reads no other context's memory).  Ordered
+ * on this context's stream: when the neighbour uses another stream, order its
+ * export before this import (an event, or a synchronise).  Same errors. */
+int fdtd_halo_import(fdtd_ctx* ctx, int side, const float* buf, int on_device);
+/* Owned rows [*j0, *j1) of the whole grid and the grid row of local row 0
+ * (0, ny, 0 for a whole grid).  NULL outputs are skipped. */
+int fdtd_slab_rows(const fdtd_ctx* ctx, int* j0, int* j1, int* row_offset);
 int fdtd_num_scenes(const fdtd_ctx* ctx);
 
 void fdtd_destroy(fdtd_ctx* ctx);
@@ -177,12 +224,17 @@ int fdtd_set_materials(fdtd_ctx* ctx, const uint8_t* mat_idx, const fdtd_materia
 /* Continuous permittivity over a rectangle of the selected 2D scene -- the
  * design region of inverse design, where every cell has its own eps_r.  Cells
  * [i0, i0+w) x [j0, j0+h) take eps_r[dj*w + di] and sigma[dj*w + di] (sigma NULL
- * = 0) instead of their material-table entry; coefficients follow eq. (7).  The
- * rectangle must avoid the PEC walls: 1 <= i0, i0 + w <= nx, same for j.
+ * = 0) instead of their material-table entry; coefficients follow eq. (7).
+ * eps_r and sigma are host arrays, or device arrays when on_device != 0 (then
+ * the coefficients are formed by a kernel and no value crosses to the host).
+ * The rectangle must avoid the PEC walls: 1 <= i0, i0 + w <= nx, same for j.
  * Calling it again replaces the values (same rectangle) or the rectangle; while
  * checkpointing is on (fdtd_set_checkpointing) the rectangle may move but not
- * change its size (FDTD_EINVAL). */
-int fdtd_set_design(fdtd_ctx* ctx, int i0, int j0, int w, int h, const double* eps_r, const double* sigma);
+ * change its size (FDTD_EINVAL).  Synchronises.  FDTD_EINVAL also for an
+ * eps_r <= 0 or sigma < 0 (found on the device for device arrays, after which
+ * the scene has no design rectangle). */
+int fdtd_set_design(fdtd_ctx* ctx, int i0, int j0, int w, int h, const double* eps_r, const double* sigma,
+                    int on_device);
 
 /* Probe: records the component at (i, j[, k]) after every following step
  * (after the source) -- the waveforms of Fig. 2d.  *probe_id gets its index.
@@ -252,7 +304,9 @@ int fdtd_load_state(fdtd_ctx* ctx, const void* buf, size_t bytes);
 /* Wait for the context's stream.  Returns FDTD_ETIMEOUT if a bounded device
  * wait (the persistent kernel's grid barrier) gave up since the last call: the
  * kernel then stopped early, the context stays usable, and the fields hold the
- * state of an incomplete step sequence. */
+ * state of an incomplete step sequence.  Otherwise returns FDTD_EUNSTABLE if the
+ * periodic finite check (FDTD_OPT_CHECK_EVERY) found a non-finite value since
+ * the last call.  Each condition is reported once, then cleared. */
 int fdtd_sync(fdtd_ctx* ctx);
 
 /* Pick the 2D kernel options for the current scenes (one large scene, or a
@@ -327,9 +381,9 @@ int fdtd_edge_grad(fdtd_ctx* ctx, const float* dLdF_re, const float* dLdF_im, fl
 
 /* Allocation-free message passing.  The paper has no counterpart to this
  * entry point; it exists for callers that cannot allocate device memory -- a
- * stream being captured into a CUDA graph, a host whose own allocator owns all
- * device memory, or a real-time loop that cannot absorb the synchronisation of
- * cudaMalloc/cudaFree.  It runs n_steps applications of h <- W2 (W1 h) for two
+ * host application whose own allocator owns all device memory and allows no
+ * allocation behind its back, or a real-time loop that cannot absorb the
+ * device-wide synchronisation of cudaMalloc/cudaFree.  It runs n_steps applications of h <- W2 (W1 h) for two
  * layers given as CSR by destination (rowptr[n_nodes + 1], col and w per edge,
  * as fdtd_export_graph lists them after sorting by destination), with every
  * pointer a caller-allocated device pointer; h (n_nodes floats) is read and
@@ -338,8 +392,10 @@ int fdtd_edge_grad(fdtd_ctx* ctx, const float* dLdF_re, const float* dLdF_im, fl
  * every GPU loading the library keeps until the process exits; it never calls
  * cudaMalloc, cudaFree or any allocating routine.  The first call on a device
  * looks that array's address up (cudaGetSymbolAddress with the device
- * current), so make the first call before any stream capture begins.  All
- * calls share the array: calls that overlap on the GPU (different streams, or
+ * current), so make the first call before any stream capture begins.  The
+ * address is kept for the life of the device's primary context: after
+ * cudaDeviceReset (or anything else that destroys that context) in this
+ * process, do not call this entry point again.  All calls share the array: calls that overlap on the GPU (different streams, or
  * different host threads on one device) race and corrupt each other's results.
  * Returns FDTD_EINVAL for NULL pointers, n_nodes < 1 or n_nodes larger than
  * FDTD_MP_NOALLOC_MAX_NODES, n_steps < 0; FDTD_ECUDA if a launch fails.

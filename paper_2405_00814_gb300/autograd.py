@@ -1,10 +1,12 @@
 """torch.autograd.Function for running-DFT losses of a batch of 2D designs.
 
 The forward pass runs the sm_103a leapfrog kernels on a batch context (one scene
-per design) with checkpoints; the backward pass calls the reverse-mode kernels
-(fdtd_adjoint_grad), which recompute each segment and run the transposed layers
-backwards in time.  PyTorch only carries the tensors: every step runs in
-libgemfdtd.so.
+per design) in segments; by default it keeps E^{n+1} - E^n over every design
+cell in device memory, so the backward pass (fdtd_adjoint_grad) runs only the
+transposed layers backwards in time (store=False keeps field checkpoints
+instead and recomputes each segment first).  A CUDA design tensor stays on the
+device: its coefficients are formed by a kernel.  PyTorch only carries the
+tensors: every step runs in libgemfdtd.so.
 """
 from __future__ import annotations
 
@@ -43,8 +45,15 @@ class DesignBatch:
         self.design_shape = (len(scenes), scenes[0].design[3], scenes[0].design[2])
 
     def forward(self, eps):
-        """Run the forward solve for eps [B, h, w]; returns F [B, n_cells, n_freq]."""
-        eps = np.asarray(eps, np.float64)
+        """Run the forward solve for eps [B, h, w] (numpy array or torch tensor; a
+        CUDA tensor is read on the device); returns F [B, n_cells, n_freq]."""
+        if hasattr(eps, "is_cuda") and eps.is_cuda:
+            import torch
+            torch.cuda.current_stream(eps.device).synchronize()   # eps is complete before the library reads it
+        elif hasattr(eps, "detach"):
+            eps = eps.detach().cpu().numpy().astype(np.float64)
+        else:
+            eps = np.asarray(eps, np.float64)
         for k, sc in enumerate(self.scenes):
             i0, j0, _, _ = sc.design
             self.sim.select(k)
@@ -73,7 +82,7 @@ def dft_intensity_loss():
     class DFTIntensityLoss(torch.autograd.Function):
         @staticmethod
         def forward(ctx, eps, batch):
-            F = batch.forward(eps.detach().cpu().numpy())
+            F = batch.forward(eps.detach())   # a CUDA tensor stays on the device
             ctx.batch = batch
             ctx.F = F
             ctx.device = eps.device

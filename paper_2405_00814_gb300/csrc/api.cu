@@ -175,31 +175,58 @@ void scene2_free(Scene2* s) {
     dfree(s->d_rec);
     dfree(s->d_dsg);
     dfree(s->d_band);
+    dfree(s->d_dsg_fac);
     delete s;
 }
 
-// the PEC walls i = 0 and j = 0 of a padded material map take PEC_MAT
-__global__ void k_pec_walls(uint8_t* __restrict__ mat, int pitch, int nx, int ny) {
+// the PEC walls i = 0 and j = 0 of a padded material map take PEC_MAT (row 0
+// only when it is the wall: a slab above the grid's first row has none)
+__global__ void k_pec_walls(uint8_t* __restrict__ mat, int pitch, int nx, int ny, int wall_row0) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < nx) mat[(size_t)PAD_Y * pitch + PAD_X + q] = (uint8_t)PEC_MAT;
-    else if (q < nx + ny) mat[(size_t)(q - nx + PAD_Y) * pitch + PAD_X] = (uint8_t)PEC_MAT;
+    if (q < nx) {
+        if (wall_row0) mat[(size_t)PAD_Y * pitch + PAD_X + q] = (uint8_t)PEC_MAT;
+    } else if (q < nx + ny) {
+        mat[(size_t)(q - nx + PAD_Y) * pitch + PAD_X] = (uint8_t)PEC_MAT;
+    }
 }
 
 static int pec_walls(fdtd_ctx* c, Scene2* s) {
     const int n = s->nx + s->ny;
-    k_pec_walls<<<(n + 255) / 256, 256, 0, c->stream>>>(s->d_mat, s->pitch, s->nx, s->ny);
+    k_pec_walls<<<(n + 255) / 256, 256, 0, c->stream>>>(s->d_mat, s->pitch, s->nx, s->ny, s->yoff == 0 ? 1 : 0);
     c->launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "PEC walls");
     return FDTD_OK;
 }
 
+// owned rows [j0, j1) of a y-slab sub-domain and its halo depth
+struct SlabSpec {
+    int j0, j1, ghost;
+};
+
 int scene2_init(fdtd_ctx* c, const fdtd_grid* g, double dx, double dt, double courant, const uint8_t* mat,
-                const fdtd_material* table, int n_mat, Scene2** out) {
+                const fdtd_material* table, int n_mat, Scene2** out, const SlabSpec* slab = nullptr) {
     *out = nullptr;
     if (!g || !mat || !table) return fail(c, FDTD_EINVAL, "NULL grid, material map or table");
     if (g->dims != 2) return fail(c, FDTD_EINVAL, "scene dims %d: this entry handles 2D", g->dims);
     if (g->nx < 4 || g->ny < 4) return fail(c, FDTD_EINVAL, "grid %dx%d too small (>= 4 cells per axis)", g->nx, g->ny);
+    // a slab holds rows [j0 - ghost_lo, j1 + ghost_hi) of the grid
+    int yoff = 0, ny_loc = g->ny, ghost = 0, ghost_lo = 0, ghost_hi = 0;
+    if (slab) {
+        ghost = slab->ghost;
+        if (ghost < 1 || ghost > 64) return fail(c, FDTD_EINVAL, "ghost depth %d outside 1..64", ghost);
+        if (slab->j0 < 0 || slab->j1 > g->ny || slab->j1 - slab->j0 < ghost)
+            return fail(c, FDTD_EINVAL, "slab rows [%d, %d) of %d: need 0 <= j0, j1 <= ny and at least %d owned rows",
+                        slab->j0, slab->j1, g->ny, ghost);
+        ghost_lo = slab->j0 > 0 ? ghost : 0;
+        ghost_hi = slab->j1 < g->ny ? ghost : 0;
+        if (slab->j0 - ghost_lo < 0 || slab->j1 + ghost_hi > g->ny)
+            return fail(c, FDTD_EINVAL, "slab [%d, %d): its %d ghost rows leave the grid", slab->j0, slab->j1, ghost);
+        if (g->boundary == FDTD_SPLIT_PML) return fail(c, FDTD_EINVAL, "slab sub-domains cover PEC and CPML grids");
+        yoff = slab->j0 - ghost_lo;
+        ny_loc = slab->j1 - slab->j0 + ghost_lo + ghost_hi;
+        if (ny_loc < 4) return fail(c, FDTD_EINVAL, "slab of %d rows too small (>= 4)", ny_loc);
+    }
     if ((int64_t)g->nx * g->ny > (int64_t)1 << 31) return fail(c, FDTD_EINVAL, "grid too large");
     if (!(dx > 0)) return fail(c, FDTD_EINVAL, "dx must be > 0");
     const double dy = g->dy > 0 ? g->dy : dx;
@@ -225,7 +252,7 @@ int scene2_init(fdtd_ctx* c, const fdtd_grid* g, double dx, double dt, double co
         if (table[m].mu_r != 1.0) return fail(c, FDTD_EINVAL, "material %d: mu_r must be 1 (non-magnetic medium)", m);
         if (!(table[m].sigma >= 0)) return fail(c, FDTD_EINVAL, "material %d: sigma must be >= 0", m);
     }
-    const int64_t ncell = (int64_t)g->nx * g->ny;
+    const int64_t ncell = (int64_t)g->nx * ny_loc;
     {
         uint8_t mx = 0;   // a branch-free pass first; the offending cell is looked up only on failure
         for (int64_t k = 0; k < ncell; k++) mx = mat[k] > mx ? mat[k] : mx;
@@ -250,10 +277,12 @@ int scene2_init(fdtd_ctx* c, const fdtd_grid* g, double dx, double dt, double co
     s->d_mat = nullptr; s->d_coef = nullptr; s->d_prof = nullptr; s->d_src = nullptr; s->d_rec = nullptr;
     s->d_dsg = nullptr;
     s->d_band = nullptr;
-    s->nx = g->nx; s->ny = g->ny; s->npml = npml; s->split = split ? 1 : 0;
+    s->d_dsg_fac = nullptr;
+    s->nx = g->nx; s->ny = ny_loc; s->npml = npml; s->split = split ? 1 : 0;
+    s->yoff = yoff; s->ny_glob = g->ny; s->ghost = ghost; s->ghost_lo = ghost_lo; s->ghost_hi = ghost_hi;
     s->dx = dx; s->dy = dy; s->dt = dt;
     s->pitch = ((PAD_X + g->nx + STRIP) + 31) / 32 * 32;
-    s->rows = g->ny + 2 * PAD_Y;
+    s->rows = ny_loc + 2 * PAD_Y;
     s->eps_r.resize(n_mat);
     s->sigma.resize(n_mat);
     for (int m = 0; m < n_mat; m++) {
@@ -290,7 +319,13 @@ int scene2_init(fdtd_ctx* c, const fdtd_grid* g, double dx, double dt, double co
         split_axis(s->ny, npml, dy, dt, PAD_Y, s->rows, py, py + s->rows, py + 2 * s->rows, py + 3 * s->rows);
     } else {
         cpml_axis(s->nx, npml, dx, dt, PAD_X, s->pitch, px, px + s->pitch, px + 2 * s->pitch, px + 3 * s->pitch);
-        cpml_axis(s->ny, npml, dy, dt, PAD_Y, s->rows, py, py + s->rows, py + 2 * s->rows, py + 3 * s->rows);
+        // y: the whole grid's profile, then the slab's window of it
+        const int rows_g = g->ny + 2 * PAD_Y;
+        std::vector<float> pg(4 * (size_t)rows_g);
+        cpml_axis(g->ny, npml, dy, dt, PAD_Y, rows_g, pg.data(), pg.data() + rows_g, pg.data() + 2 * rows_g,
+                  pg.data() + 3 * rows_g);
+        for (int q = 0; q < 4; q++)
+            for (int r = 0; r < s->rows; r++) py[(size_t)q * s->rows + r] = pg[(size_t)q * rows_g + r + yoff];
     }
     rc = dalloc(c, &s->d_prof, prof.size() * sizeof(float), "profiles");
     if (rc) { scene2_free(s); return rc; }
@@ -364,6 +399,15 @@ fdtd_ctx* ctx_new(void* stream) {
     c->spin_limit = 4000000;   // about one second of 256 ns polls
     c->opt_debug_skip = -1;
     c->opt_adj_store = 1;
+    c->opt_check_every = 0;
+    c->d_bad = nullptr;
+    c->h_bad = nullptr;
+    if (cudaMallocHost(&c->h_bad, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        c->h_bad = nullptr;
+    } else {
+        *c->h_bad = 0;
+    }
     c->opt_graph = 0;
     c->graph_exec = nullptr;
     c->graph_t = c->graph_n = -1;
@@ -452,6 +496,8 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
         d.dsg_i0 = s->dsg_i0; d.dsg_j0 = s->dsg_j0; d.dsg_w = s->d_dsg ? s->dsg_w : 0; d.dsg_h = s->dsg_h;
         d.dsg_coef = s->d_dsg;
         d.dsg_band = s->d_band;
+        d.pml_ylo = s->npml - s->yoff;
+        d.pml_yhi = s->ny_glob - s->npml - s->yoff;
     }
     // tasks: per scene, strips of 120 columns x segments of seg rows.  Tasks
     // with a CPML slab or the design rectangle within reach go to the boundary
@@ -477,7 +523,8 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
             int f = 0;
             const int lx0 = x0 - HALO, lx1 = x0 - HALO + STRIP;   // loaded columns
             const int ly0 = ya - MAX_TB, ly1 = yb + MAX_TB;        // widest streamed rows
-            if (s->npml > 0 && (lx0 < s->npml || lx1 > s->nx - s->npml || ly0 < s->npml || ly1 > s->ny - s->npml))
+            if (s->npml > 0 && (lx0 < s->npml || lx1 > s->nx - s->npml || ly0 < s->npml - s->yoff ||
+                                ly1 > s->ny_glob - s->npml - s->yoff))
                 f |= TASK_PML;
             if (s->src_kind >= 0 && s->src_i >= lx0 && s->src_i < lx1 && s->src_j < ly1 && s->src_j1 > ly0)
                 f |= TASK_SRC;
@@ -697,6 +744,58 @@ int step_prepare(fdtd_ctx* c, int64_t n_steps) {
     return FDTD_OK;
 }
 
+bool ctx_has_slab(const fdtd_ctx* c) {
+    for (const Scene2* s : c->s2)
+        if (s->ghost) return true;
+    return false;
+}
+
+// the arrays a halo carries: Ez, Hx, Hy, and with a CPML the four psi arrays
+// (the x-slab ones run along every row; the y-slab ones matter where a cut
+// lies within the layer)
+static int halo_slots(const Scene2* s) { return s->npml > 0 ? F_COUNT2 : 3; }
+
+// copy `ghost` whole rows starting at local row r0 of every halo array between
+// the context's current buffers and a packed [slot][ghost][nx] buffer
+static int halo_copy(fdtd_ctx* c, Scene2* s, int r0, float* packed, const float* in, int on_device) {
+    const int ns = halo_slots(s);
+    const size_t plane = (size_t)s->ghost * s->nx;
+    for (int f = 0; f < ns; f++) {
+        float* dev = s->fbuf[f][c->parity] + (size_t)(r0 + PAD_Y) * s->pitch + PAD_X;
+        cudaError_t e;
+        if (packed)
+            e = cudaMemcpy2DAsync(packed + f * plane, (size_t)s->nx * sizeof(float), dev, (size_t)s->pitch * sizeof(float),
+                                  (size_t)s->nx * sizeof(float), s->ghost,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
+        else
+            e = cudaMemcpy2DAsync(dev, (size_t)s->pitch * sizeof(float), in + f * plane, (size_t)s->nx * sizeof(float),
+                                  (size_t)s->nx * sizeof(float), s->ghost,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "halo copy");
+    }
+    if (!on_device) CK(cudaStreamSynchronize(c->stream), "halo copy");
+    return FDTD_OK;
+}
+
+// the slab of a single-scene slab context, or NULL with the error set
+static Scene2* slab_of(fdtd_ctx* c, int side) {
+    Scene2* s = cur2(c);
+    if (!s || !s->ghost) {
+        fail(c, FDTD_EINVAL, "not a slab sub-domain (fdtd_create_slab)");
+        return nullptr;
+    }
+    if (side != 0 && side != 1) {
+        fail(c, FDTD_EINVAL, "side must be 0 (lower cut) or 1 (upper cut)");
+        return nullptr;
+    }
+    if ((side == 0 ? s->ghost_lo : s->ghost_hi) == 0) {
+        fail(c, FDTD_EINVAL, "the slab has no neighbour on side %d (it holds the grid's %s row)", side,
+             side == 0 ? "first" : "last");
+        return nullptr;
+    }
+    return s;
+}
+
 }  // namespace gem
 
 // ===========================================================================
@@ -706,6 +805,7 @@ extern "C" {
 
 int fdtd_create(const fdtd_grid* grid, double dx, double dt, double courant, const uint8_t* mat_idx,
                 const fdtd_material* table, int n_mat, void* cuda_stream, fdtd_ctx** out) {
+    NvtxRange nvtx("fdtd_create");
     if (!out) return FDTD_EINVAL;
     *out = nullptr;
     if (!grid) return FDTD_EINVAL;
@@ -726,6 +826,7 @@ int fdtd_create(const fdtd_grid* grid, double dx, double dt, double courant, con
 int fdtd_create_batch(int n_scenes, const fdtd_grid* grids, const double* dx, const double* dt,
                       const uint8_t* const* mat_idx, const fdtd_material* const* tables, const int* n_mat,
                       void* cuda_stream, fdtd_ctx** out) {
+    NvtxRange nvtx("fdtd_create_batch");
     if (!out) return FDTD_EINVAL;
     *out = nullptr;
     fdtd_ctx* c = ctx_new(cuda_stream);
@@ -741,6 +842,60 @@ int fdtd_create_batch(int n_scenes, const fdtd_grid* grids, const double* dx, co
         }
         c->s2.push_back(s);
     }
+    return FDTD_OK;
+}
+
+int fdtd_create_slab(const fdtd_grid* grid, int j0, int j1, int ghost, double dx, double dt, double courant,
+                     const uint8_t* mat_idx, const fdtd_material* table, int n_mat, void* cuda_stream,
+                     fdtd_ctx** out) {
+    NvtxRange nvtx("fdtd_create_slab");
+    if (!out) return FDTD_EINVAL;
+    *out = nullptr;
+    if (!grid) return FDTD_EINVAL;
+    fdtd_ctx* c = ctx_new(cuda_stream);
+    *out = c;
+    if (grid->dims != 2) return fail(c, FDTD_EINVAL, "slab sub-domains are 2D");
+    SlabSpec sp{j0, j1, ghost};
+    Scene2* s = nullptr;
+    int rc = scene2_init(c, grid, dx, dt, courant, mat_idx, table, n_mat, &s, &sp);
+    if (rc) return rc;
+    c->s2.push_back(s);
+    return FDTD_OK;
+}
+
+int64_t fdtd_halo_count(const fdtd_ctx* c) {
+    if (!c || c->dims != 2 || c->s2.empty()) return 0;
+    const Scene2* s = c->s2[c->cur];
+    return s->ghost ? (int64_t)halo_slots(s) * s->ghost * s->nx : 0;
+}
+
+int fdtd_halo_export(fdtd_ctx* c, int side, float* buf, int on_device) {
+    NvtxRange nvtx("fdtd_halo_export");
+    if (!c) return FDTD_EINVAL;
+    Scene2* s = slab_of(c, side);
+    if (!s) return FDTD_EINVAL;
+    if (!buf) return fail(c, FDTD_EINVAL, "NULL halo buffer");
+    // the owned rows next to the cut: the neighbour's ghost rows
+    const int r0 = side == 0 ? s->ghost_lo : s->ny - s->ghost_hi - s->ghost;
+    return halo_copy(c, s, r0, buf, nullptr, on_device);
+}
+
+int fdtd_halo_import(fdtd_ctx* c, int side, const float* buf, int on_device) {
+    NvtxRange nvtx("fdtd_halo_import");
+    if (!c) return FDTD_EINVAL;
+    Scene2* s = slab_of(c, side);
+    if (!s) return FDTD_EINVAL;
+    if (!buf) return fail(c, FDTD_EINVAL, "NULL halo buffer");
+    const int r0 = side == 0 ? 0 : s->ny - s->ghost_hi;
+    return halo_copy(c, s, r0, nullptr, buf, on_device);
+}
+
+int fdtd_slab_rows(const fdtd_ctx* c, int* j0, int* j1, int* row_offset) {
+    if (!c || c->dims != 2 || c->s2.empty()) return FDTD_EINVAL;
+    const Scene2* s = c->s2[c->cur];
+    if (j0) *j0 = s->yoff + s->ghost_lo;
+    if (j1) *j1 = s->yoff + s->ny - s->ghost_hi;
+    if (row_offset) *row_offset = s->yoff;
     return FDTD_OK;
 }
 
@@ -774,6 +929,8 @@ void fdtd_destroy(fdtd_ctx* c) {
     dfree(c->d_dft);
     dfree(c->d_ctl);
     if (c->h_err) cudaFreeHost(c->h_err);
+    dfree(c->d_bad);
+    if (c->h_bad) cudaFreeHost(c->h_bad);
     if (c->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     dfree(c->d_tasks_l);
@@ -823,6 +980,21 @@ int fdtd_set_option(fdtd_ctx* c, int option, int64_t v) {
             c->opt_segment = (int)v;
             c->dirty = true;
             return FDTD_OK;
+        case FDTD_OPT_CHECK_EVERY:
+            if (c->dims != 2) return fail(c, FDTD_EINVAL, "the periodic finite check covers 2D contexts");
+            if (v < 0 || v > (1 << 30)) return fail(c, FDTD_EINVAL, "check interval %lld outside 0..2^30", (long long)v);
+            if (v > 0 && !c->d_bad) {
+                if (!c->h_bad) return fail(c, FDTD_ENOMEM, "no pinned host word for the finite check");
+                int rc = dalloc(c, &c->d_bad, sizeof(int), "finite-check flag");
+                if (rc) return rc;
+                CK(cudaMemsetAsync(c->d_bad, 0, sizeof(int), c->stream), "finite-check flag");
+            }
+            c->opt_check_every = (int)v;
+            if (c->graph_exec) {   // a recorded step sequence lacks (or has) the checks
+                cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
+                c->graph_exec = nullptr;
+            }
+            return FDTD_OK;
         case FDTD_OPT_SEGMENT_B:
             if (v != 0 && (v < 4 || v > (1 << 20)))
                 return fail(c, FDTD_EINVAL, "boundary segment %lld: 0 (automatic) or >= 4 rows", (long long)v);
@@ -850,6 +1022,7 @@ int64_t fdtd_get_option(const fdtd_ctx* c, int option) {
         case FDTD_OPT_DEBUG_SKIP_CTA: return c->opt_debug_skip;
         case FDTD_OPT_ADJ_STORE: return c->opt_adj_store;
         case FDTD_OPT_SEGMENT_B: return c->opt_segment_b;
+        case FDTD_OPT_CHECK_EVERY: return c->opt_check_every;
     }
     return -1;
 }
@@ -868,8 +1041,9 @@ int fdtd_set_line_source(fdtd_ctx* c, int kind, int i, int j0, int j1, const dou
     if (c->dims != 2) return fail(c, FDTD_EINVAL, "line sources are 2D only");
     Scene2* s = cur2(c);
     if (!s) return fail(c, FDTD_ESTATE, "no scene");
-    if (i < 1 || i >= s->nx || j0 < 1 || j1 > s->ny || j1 <= j0)
-        return fail(c, FDTD_EINVAL, "source cells (%d, %d..%d) outside 1..nx-1 x 1..ny-1", i, j0, j1 - 1);
+    const int jmin = s->yoff == 0 ? 1 : 0;   // row 0 of a slab above the grid's first row is not a wall
+    if (i < 1 || i >= s->nx || j0 < jmin || j1 > s->ny || j1 <= j0)
+        return fail(c, FDTD_EINVAL, "source cells (%d, %d..%d) outside 1..nx-1 x %d..ny-1", i, j0, j1 - 1, jmin);
     const int j = j0;
     if (kind < FDTD_SRC_RICKER || kind > FDTD_SRC_SINE) return fail(c, FDTD_EINVAL, "unknown source kind %d", kind);
     if (kind == FDTD_SRC_SAMPLED) {
@@ -937,10 +1111,12 @@ int fdtd_set_materials(fdtd_ctx* c, const uint8_t* mat, const fdtd_material* tab
     return FDTD_OK;
 }
 
-int fdtd_set_design(fdtd_ctx* c, int i0, int j0, int w, int h, const double* eps_r, const double* sigma) {
+int fdtd_set_design(fdtd_ctx* c, int i0, int j0, int w, int h, const double* eps_r, const double* sigma,
+                    int on_device) {
     if (!c) return FDTD_EINVAL;
     Scene2* s = cur2(c);
     if (!s) return fail(c, FDTD_EINVAL, "design regions are 2D only");
+    if (s->ghost) return fail(c, FDTD_EINVAL, "design regions cover whole grids, not slab sub-domains");
     if (!eps_r || w < 1 || h < 1 || i0 < 1 || j0 < 1 || i0 + w > s->nx || j0 + h > s->ny)
         return fail(c, FDTD_EINVAL, "design rectangle (%d, %d, %d, %d) must lie in 1..nx-1 x 1..ny-1", i0, j0, w, h);
     if (s->split && (split_layer_cell(i0, j0, s->nx, s->ny, s->npml) ||
@@ -950,31 +1126,63 @@ int fdtd_set_design(fdtd_ctx* c, int i0, int j0, int w, int h, const double* eps
         return fail(c, FDTD_EINVAL, "the design rectangle's size is fixed while checkpointing is on "
                                     "(its history blocks are sized for it)");
     const size_t n = (size_t)w * h;
-    std::vector<float4> co(n);
-    for (size_t q = 0; q < n; q++) {
-        const double sg = sigma ? sigma[q] : 0.0;
-        if (!(eps_r[q] > 0) || !(sg >= 0)) return fail(c, FDTD_EINVAL, "design cell %zu: eps_r must be > 0, sigma >= 0", q);
-        co[q] = e_coeffs(eps_r[q], sg, s->dt, s->dx, s->dy);
+    std::vector<float4> co;
+    std::vector<float> fac;
+    if (!on_device) {
+        co.resize(n);
+        fac.resize(n);
+        for (size_t q = 0; q < n; q++) {
+            const double sg = sigma ? sigma[q] : 0.0;
+            if (!(eps_r[q] > 0) || !(sg >= 0))
+                return fail(c, FDTD_EINVAL, "design cell %zu: eps_r must be > 0, sigma >= 0", q);
+            co[q] = e_coeffs(eps_r[q], sg, s->dt, s->dx, s->dy);
+            fac[q] = (float)(-kEps0 / (kEps0 * eps_r[q] + sg * s->dt / 2.0));
+        }
     }
     if (!s->d_dsg || s->dsg_w != w || s->dsg_h != h) {
         dfree(s->d_dsg);
         dfree(s->d_band);
+        dfree(s->d_dsg_fac);
         s->d_dsg = nullptr;
         s->d_band = nullptr;
+        s->d_dsg_fac = nullptr;
         int rc = dalloc(c, &s->d_dsg, n * sizeof(float4), "design coefficients");
         if (rc) return rc;
         rc = dalloc(c, &s->d_band, (size_t)3 * h * s->pitch * sizeof(float), "design band");
         if (rc) return rc;
+        rc = dalloc(c, &s->d_dsg_fac, n * sizeof(float), "design gradient factor");
+        if (rc) return rc;
+        s->dsg_w = s->dsg_h = 0;   // sized, not yet valid
     }
-    CK(cudaMemcpyAsync(s->d_dsg, co.data(), n * sizeof(float4), cudaMemcpyHostToDevice, c->stream), "upload design");
+    if (on_device) {
+        // eq. (7) per cell on the device, straight from the caller's device arrays
+        int bad = 0;
+        int rc = tmz_design_coeffs(c, s, eps_r, sigma, n, &bad);
+        if (rc) return rc;
+        if (bad) {
+            // the coefficients were partly overwritten: drop the rectangle
+            dfree(s->d_dsg);
+            dfree(s->d_band);
+            dfree(s->d_dsg_fac);
+            s->d_dsg = nullptr;
+            s->d_band = nullptr;
+            s->d_dsg_fac = nullptr;
+            s->dsg_w = s->dsg_h = 0;
+            c->dirty = true;
+            graph_free(c);
+            return fail(c, FDTD_EINVAL, "design: every eps_r must be > 0 and every sigma >= 0 "
+                                        "(the design rectangle is removed)");
+        }
+    } else {
+        CK(cudaMemcpyAsync(s->d_dsg, co.data(), n * sizeof(float4), cudaMemcpyHostToDevice, c->stream),
+           "upload design");
+        CK(cudaMemcpyAsync(s->d_dsg_fac, fac.data(), n * sizeof(float), cudaMemcpyHostToDevice, c->stream),
+           "upload design");
+    }
     s->dsg_i0 = i0; s->dsg_j0 = j0; s->dsg_w = w; s->dsg_h = h;
     int brc = tmz_design_band(c, s);
     if (brc) return brc;
     CK(cudaStreamSynchronize(c->stream), "upload design");
-    s->dsg_eps.assign(eps_r, eps_r + n);
-    if (sigma) s->dsg_sig.assign(sigma, sigma + n);
-    else s->dsg_sig.clear();
-    s->dsg_i0 = i0; s->dsg_j0 = j0; s->dsg_w = w; s->dsg_h = h;
     c->dirty = true;
     graph_free(c);   // the edge-list weights hold the old coefficients
     return FDTD_OK;
@@ -1096,6 +1304,14 @@ static int step_launches(fdtd_ctx* c, int64_t n_steps) {
             rc = dft_items_launch(c, c->t, done);
             if (rc) return rc;
         }
+        if (c->opt_check_every > 0 && (c->t + done) / c->opt_check_every > c->t / c->opt_check_every) {
+            // a step count divisible by the interval ended inside this block: scan the
+            // fields into the sticky flag, which fdtd_sync reports
+            cudaError_t e = tmz_finite_launch(c, c->d_bad);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(c->h_bad, c->d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "periodic finite check");
+        }
         c->t += done;
         left -= done;
     }
@@ -1103,22 +1319,34 @@ static int step_launches(fdtd_ctx* c, int64_t n_steps) {
 }
 
 int fdtd_step(fdtd_ctx* c, int64_t n_steps) {
+    NvtxRange nvtx("fdtd_step");
     if (!c) return FDTD_EINVAL;
     if (n_steps < 0) return fail(c, FDTD_EINVAL, "n_steps < 0");
     if (n_steps == 0) return FDTD_OK;
     if (c->dims == 3) return fdtd_step3(c, n_steps);
+    for (const Scene2* s : c->s2)
+        if (s->ghost && n_steps > s->ghost)
+            return fail(c, FDTD_EINVAL, "a slab sub-domain advances at most %d steps (its ghost depth) between "
+                                        "halo exchanges; asked for %lld", s->ghost, (long long)n_steps);
     int rc = step_prepare(c, n_steps);
     if (rc) return rc;
     if (c->opt_kernel == 2) {
         // control words: 4 + one work counter per T-block of the longest launch
         const int need = 4 + (int)std::min<int64_t>(n_steps / std::max(1, c->opt_tblock) + 1, 1 << 20);
         if (c->ctl_words < need) {
+            // the error word (ctl[2]) is sticky until fdtd_sync reports it: carry a
+            // timeout of an earlier launch over into the new words
+            CK(cudaStreamSynchronize(c->stream), "sync before growing the control words");
             dfree(c->d_ctl);
             c->d_ctl = nullptr;
             c->ctl_words = 0;
             rc = dalloc(c, &c->d_ctl, (size_t)need * sizeof(unsigned), "persistent control words");
             if (rc) return rc;
             c->ctl_words = need;
+            CK(cudaMemsetAsync(c->d_ctl, 0, (size_t)need * sizeof(unsigned), c->stream), "control words");
+            if (c->h_err && *c->h_err)
+                CK(cudaMemcpyAsync(c->d_ctl + 2, c->h_err, sizeof(int), cudaMemcpyHostToDevice, c->stream),
+                   "control words");
         }
         if (!c->h_err) return fail(c, FDTD_ENOMEM, "no pinned host word for the persistent kernel");
     }
@@ -1184,19 +1412,32 @@ int fdtd_sync(fdtd_ctx* c) {
     if (!c) return FDTD_EINVAL;
     CK(cudaStreamSynchronize(c->stream), "sync");
     if (c->h_err && *c->h_err) {
+        // report once: clear the sticky device word and its host copy
+        if (c->d_ctl) CK(cudaMemsetAsync(c->d_ctl + 2, 0, sizeof(unsigned), c->stream), "clear the error word");
+        CK(cudaStreamSynchronize(c->stream), "sync");
         *c->h_err = 0;
+        if (c->h_bad) *c->h_bad = 0;   // fields of a cut-short run: a timeout is the first thing to report
+        if (c->d_bad) CK(cudaMemset(c->d_bad, 0, sizeof(int)), "clear the finite-check flag");
         return fail(c, FDTD_ETIMEOUT, "a grid-barrier wait of the persistent kernel gave up (spin limit %lld)",
                     (long long)c->spin_limit);
+    }
+    if (c->h_bad && *c->h_bad) {
+        if (c->d_bad) CK(cudaMemset(c->d_bad, 0, sizeof(int)), "clear the finite-check flag");
+        *c->h_bad = 0;
+        return fail(c, FDTD_EUNSTABLE, "the periodic finite check found non-finite field values "
+                                       "(FDTD_OPT_CHECK_EVERY %d)", c->opt_check_every);
     }
     return FDTD_OK;
 }
 
 // time candidate settings on the current scenes; keep the fastest
 int fdtd_autotune(fdtd_ctx* c, int trial_steps, double* best_ms) {
+    NvtxRange nvtx("fdtd_autotune");
     if (!c) return FDTD_EINVAL;
     if (c->dims != 2) return fail(c, FDTD_EINVAL, "autotuning covers the 2D kernels");
     if (trial_steps < 4) return fail(c, FDTD_EINVAL, "trial_steps must be >= 4");
     if (c->adj) return fail(c, FDTD_EINVAL, "disable checkpointing before autotuning");
+    if (ctx_has_slab(c)) return fail(c, FDTD_EINVAL, "autotuning covers whole grids, not slab sub-domains");
     struct Cand { int kernel, T, seg, warps; };
     std::vector<Cand> cand;
     // the segment height sets how many CTAs a block launches, so the sweep is
@@ -1370,6 +1611,7 @@ int64_t fdtd_time_step(const fdtd_ctx* c) { return c ? c->t : -1; }
 int64_t fdtd_launch_count(const fdtd_ctx* c) { return c ? c->launches : -1; }
 
 int fdtd_save_state(fdtd_ctx* c, void* buf, size_t* bytes) {
+    NvtxRange nvtx("fdtd_save_state");
     if (!c || !bytes) return FDTD_EINVAL;
     if (c->dims == 3) return fdtd_save_state3(c, buf, bytes);
     size_t need = 2 * sizeof(int64_t);
@@ -1409,6 +1651,7 @@ int fdtd_save_state(fdtd_ctx* c, void* buf, size_t* bytes) {
 }
 
 int fdtd_load_state(fdtd_ctx* c, const void* buf, size_t bytes) {
+    NvtxRange nvtx("fdtd_load_state");
     if (!c || !buf) return FDTD_EINVAL;
     if (c->dims == 3) return fdtd_load_state3(c, buf, bytes);
     if (bytes < 2 * sizeof(int64_t)) return fail(c, FDTD_EINVAL, "state buffer too small");

@@ -15,6 +15,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -23,6 +24,15 @@
 #include "gem_fdtd.h"
 
 namespace gem {
+
+// a named range on the host timeline for profilers (creation, stepping,
+// reverse mode, checkpoints); costs a function call when no tool listens
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr int PAD_X = 8;
 constexpr int PAD_Y = 8;
@@ -74,6 +84,10 @@ struct TmzDev {
                                         //    dL/dHx^{n+1/2}, dL/dHy^{n+1/2} (edge-weight gradients)
     const float* adj_src;               // [steps][n_adj]: dL/dE^{n+1} at adjoint source cells
     int n_adj;
+    // rows a with a < pml_ylo or a >= pml_yhi may lie in a y-slab of the CPML
+    // (npml and ny - npml for a whole grid; shifted by the row offset of a slab
+    // sub-domain, whose CPML profile is the whole grid's)
+    int pml_ylo, pml_yhi;
 };
 
 // one warp's work in the fused kernel: columns [x0, x0 + STRIP - 2 HALO) and
@@ -141,7 +155,13 @@ struct Scene2 {
     int dsg_i0, dsg_j0, dsg_w, dsg_h;
     float4* d_dsg;
     float* d_band;                       // see TmzDev::dsg_band
-    std::vector<double> dsg_eps, dsg_sig;
+    float* d_dsg_fac;                    // [dsg_h][dsg_w]: -eps0 / (eps0 eps_r + sigma dt / 2), the
+                                         // per-cell factor of the eps_r gradient (reverse mode)
+    // y-slab sub-domain of a larger grid (fdtd_create_slab): local row r is row
+    // r + yoff of the whole grid (ny_glob rows); ghost_lo / ghost_hi rows below /
+    // above the owned rows are copies of the neighbours' rows, refreshed by
+    // fdtd_halo_import; ghost is the depth of a halo (0: a whole grid)
+    int yoff, ny_glob, ghost, ghost_lo, ghost_hi;
 };
 
 }  // namespace gem
@@ -194,10 +214,13 @@ struct fdtd_ctx {
     int n_tasks_all;
     unsigned* d_ctl;
     int ctl_words;
-    int* h_err;                  // pinned: error flag of the last persistent launch
+    int* h_err;                  // pinned: copy of the sticky error word ctl[2] (cleared by fdtd_sync)
     long long spin_limit;        // barrier polls before a CTA gives up
     int opt_debug_skip;          // CTA that skips its barrier arrivals (-1 none)
     int opt_adj_store;           // FDTD_OPT_ADJ_STORE
+    int opt_check_every;         // FDTD_OPT_CHECK_EVERY (0: off)
+    int* d_bad;                  // sticky device word of the periodic finite check
+    int* h_bad;                  // pinned copy of it (cleared by fdtd_sync)
     // CUDA graph of a step sequence
     int opt_graph;
     void* graph_exec;
@@ -213,9 +236,11 @@ int tmz_fused_launch(fdtd_ctx* c, int T, int warps, long long n0, int parity);
 int tmz_naive_step(fdtd_ctx* c, long long n);
 int dft_cells_launch(fdtd_ctx* c, const DftMon& m, long long n0, int nsteps);
 int tmz_finite_check(fdtd_ctx* c, int* bad);
+cudaError_t tmz_finite_launch(fdtd_ctx* c, int* d_flag);
 int tmz_persistent_launch(fdtd_ctx* c, int T, long long n0, int n_blocks, int parity);
 size_t tmz_fused_smem(int T, int warps, int V);   // V: 0 interior, 1 CPML, 2 lite
 int tmz_design_band(fdtd_ctx* c, Scene2* s);
+int tmz_design_coeffs(fdtd_ctx* c, Scene2* s, const double* eps_r, const double* sigma, size_t n, int* bad);
 // raise a kernel's dynamic shared-memory limit to `bytes` on the current device,
 // once (the attribute call is a driver round trip; later launches reuse it)
 cudaError_t ensure_dyn_smem(const void* kernel, size_t bytes);
@@ -244,6 +269,8 @@ int fdtd_load_state3(fdtd_ctx* c, const void* buf, size_t bytes);
 int fdtd_check_finite3(fdtd_ctx* c);
 // literal edge-list path (k_graph.cu)
 void graph_free(fdtd_ctx* c);
+// a scene of the context is a y-slab sub-domain (fdtd_create_slab)
+bool ctx_has_slab(const fdtd_ctx* c);
 // reverse mode (k_adjoint.cu)
 int adj_checkpoint_if_due(fdtd_ctx* c);
 int adj_next_boundary(const fdtd_ctx* c, int64_t t);

@@ -659,6 +659,7 @@ void adj_patch_descriptors(fdtd_ctx* c, TmzDev* dev) {
 int adj_checkpoint_if_due(fdtd_ctx* c) {
     AdjState* A = (AdjState*)c->adj;
     if (!A || A->every <= 0 || c->t % A->every) return FDTD_OK;
+    NvtxRange nvtx("checkpoint");
     const int slot = (int)(c->t / A->every);
     const int ns = (int)c->s2.size();
     if (A->store) {
@@ -779,6 +780,10 @@ int fdtd_set_checkpointing(fdtd_ctx* c, int every) {
             c->err = "reverse mode covers the CPML and PEC boundaries, not the split-field PML";
             return FDTD_EINVAL;
         }
+    if (ctx_has_slab(c)) {
+        c->err = "reverse mode covers whole grids, not slab sub-domains";
+        return FDTD_EINVAL;
+    }
     if (every < 0) {
         c->err = "checkpoint interval must be >= 0";
         return FDTD_EINVAL;
@@ -908,14 +913,8 @@ static int reverse_run(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, 
         // eq. (7) with D = eps0 eps_r + sigma dt / 2: Ca = (eps0 eps_r - sigma dt / 2) / D,
         // Cb = dt / D, so dCb/deps_r = -eps0 dt / D^2 = (-eps0 / D) Cb and
         // dCa/deps_r = eps0 sigma dt / D^2 = -sigma dCb/deps_r; the per-cell factor
-        // of sum_n e^{n+1} r^n is -eps0 / D
-        std::vector<float> fach(hw);
-        const double eps0 = 1.0 / (4.0e-7 * M_PI * 299792458.0 * 299792458.0);
-        for (size_t q = 0; q < hw; q++) {
-            const double sg = s->dsg_sig.empty() ? 0.0 : s->dsg_sig[q];
-            fach[q] = (float)(-eps0 / (eps0 * s->dsg_eps[q] + sg * s->dt / 2.0));
-        }
-        cudaMemcpyAsync(fac, fach.data(), hw * sizeof(float), cudaMemcpyHostToDevice, st);
+        // of sum_n e^{n+1} r^n is -eps0 / D, formed when the design was set
+        cudaMemcpyAsync(fac, s->d_dsg_fac, hw * sizeof(float), cudaMemcpyDeviceToDevice, st);
         for (int f = 0; f < F_COUNT2; f++)
             for (int p = 0; p < 2; p++) abuf.push_back((float*)((char*)aset + (f * 2 + p) * fb));
         // forward descriptor for the recompute, adjoint descriptor for the reverse sweep
@@ -1128,10 +1127,12 @@ static int reverse_run(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, 
 }
 
 int fdtd_adjoint_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, float* grad, int on_device) {
+    NvtxRange nvtx("fdtd_adjoint_grad");
     return reverse_run(c, dLdF_re, dLdF_im, grad, on_device, 0);
 }
 
 int fdtd_edge_grad(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, float* grad, int on_device) {
+    NvtxRange nvtx("fdtd_edge_grad");
     return reverse_run(c, dLdF_re, dLdF_im, grad, on_device, 1);
 }
 

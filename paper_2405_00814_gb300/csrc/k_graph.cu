@@ -532,9 +532,14 @@ int step_prepare(fdtd_ctx* c, int64_t n_steps);
 extern "C" {
 
 int fdtd_step_edgelist(fdtd_ctx* c, int64_t n_steps) {
+    NvtxRange nvtx("fdtd_step_edgelist");
     if (!c) return FDTD_EINVAL;
     if (c->dims != 2 || c->s2.empty()) {
         c->err = "the edge-list path is 2D only";
+        return FDTD_EINVAL;
+    }
+    if (ctx_has_slab(c)) {
+        c->err = "slab sub-domains step with the implicit-stencil kernels only";
         return FDTD_EINVAL;
     }
     if (n_steps < 0) {
@@ -611,6 +616,10 @@ int fdtd_export_graph(fdtd_ctx* c, int layer, int64_t* n_nodes, int64_t* n_edges
     if (!c || !n_nodes || !n_edges) return FDTD_EINVAL;
     if (c->dims != 2 || c->s2.empty()) {
         c->err = "graph export is 2D only";
+        return FDTD_EINVAL;
+    }
+    if (ctx_has_slab(c)) {
+        c->err = "graph export covers whole grids, not slab sub-domains";
         return FDTD_EINVAL;
     }
     if (layer != 1 && layer != 2) {

@@ -1,11 +1,10 @@
 // Allocation-free message passing over a caller-supplied graph.
 //
 // fdtd_step_edgelist keeps the hidden state between the two layers in device
-// memory the context allocated.  Some callers cannot allocate at all: a stream
-// that is being captured into a CUDA graph (cudaMalloc is not allowed while a
-// capture is in progress), a host application whose allocator owns every byte
-// of device memory and forbids outside allocations, or a real-time loop that
-// cannot afford the device-wide synchronisation cudaMalloc/cudaFree imply.
+// memory the context allocated.  Some callers cannot allocate at all: a host
+// application whose allocator owns every byte of device memory and forbids
+// outside allocations, or a real-time loop that cannot afford the device-wide
+// synchronisation cudaMalloc/cudaFree imply.
 // fdtd_mp_steps_noalloc serves them: the caller passes the two layers (CSR by
 // destination, as fdtd_export_graph produces them) and the node state, and the
 // intermediate state after layer 1 lives in the fixed array below instead of in
@@ -29,6 +28,8 @@ float* g_scratch_ptr[kMaxDevices] = {};
 
 // The array's name is a host-side stand-in in host code, not a device address:
 // ask the runtime for the address once per device, with that device current.
+// The cached address belongs to the device's primary context; a context that
+// cudaDeviceReset destroyed and a new one recreated may hold the array elsewhere.
 int scratch_for_current_device(float** out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {

@@ -139,6 +139,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
     // CPML: lanes whose columns touch an x-slab carry psi_Ezx / psi_Hyx
     const bool pml = PML && (tk.flags & TASK_PML) != 0;
     const int npml = S->has_pml;
+    const int ylo = S->pml_ylo, yhi = S->pml_yhi;   // rows outside [ylo, yhi) may lie in a y-slab
     const Prof pr{S->prof, pitch, S->rows};
     bool lane_px = false;
     float4 bex4 = make_float4(0, 0, 0, 0), cex4 = bex4, bhx4 = bex4, chx4 = bex4;
@@ -213,7 +214,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
             if (yrow || lane_sx) cp_async16(st + 4 * 32 + lane, psi_in[1] + g, true);
         }
         if constexpr (PML && !SPL) if (pml) {
-            const bool yrow = (row < npml) || (row >= ny - npml);
+            const bool yrow = (row < ylo) || (row >= yhi);
             // the row's bEy, cEy, bHy, cHy
             if (yrow && lane < 4)
                 cp_async4(reinterpret_cast<float*>(st + NSLOT * 32 + 8) + lane, pr.p + 4 * pitch + lane * pr.rows + row + PAD_Y);
@@ -283,7 +284,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
             float4 dey = make_float4(eu.x - e.x, eu.y - e.y, eu.z - e.z, eu.w - e.w);
             float4 dex = make_float4(e.y - e.x, e.z - e.y, e.w - e.z, er - e.w);
             if constexpr (PML && !SPL) if (pml) {
-                if ((a < npml) || (a >= ny - npml)) {
+                if ((a < ylo) || (a >= yhi)) {
                     const float b = yprof[2], c = yprof[3];
                     float4 p = sta[5 * 32 + lane];
                     p.x = b * p.x + c * dey.x;
@@ -339,7 +340,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
             float4 dhx = make_float4(X[t].x - X[t + 1].x, X[t].y - X[t + 1].y, X[t].z - X[t + 1].z,
                                      X[t].w - X[t + 1].w);
             if constexpr (PML && !SPL) if (pml) {
-                if ((a < npml) || (a >= ny - npml)) {
+                if ((a < ylo) || (a >= yhi)) {
                     const float b = yprof[0], c = yprof[1];
                     float4 p = sta[4 * 32 + lane];
                     p.x = b * p.x + c * dhx.x;
@@ -488,7 +489,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
                         if (srow(o) || lane_sx) *reinterpret_cast<float4*>(psi_out[1] + g) = sto[4 * 32 + lane];
                     }
                     if constexpr (PML && !SPL) if (pml) {
-                        if ((o < npml) || (o >= ny - npml)) {
+                        if ((o < ylo) || (o >= yhi)) {
                             *reinterpret_cast<float4*>(psi_out[1] + g) = sto[4 * 32 + lane];
                             *reinterpret_cast<float4*>(psi_out[2] + g) = sto[5 * 32 + lane];
                         }
@@ -503,7 +504,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
                         p0 = sto[3 * 32 + lane]; p1 = sto[4 * 32 + lane];
                         p2 = sto[5 * 32 + lane]; p3 = sto[6 * 32 + lane];
                     }
-                    const bool yrow = !SPL && pml && ((o < npml) || (o >= ny - npml));
+                    const bool yrow = !SPL && pml && ((o < ylo) || (o >= yhi));
                     const bool srw = SPL && pml && (srow(o) || lane_sx);
                     for (int c = 0; c < 4; c++) {
                         if (cx + c >= nx) break;
@@ -616,6 +617,8 @@ __global__ void __launch_bounds__(256, 1) k_tmz_persistent(const TmzDev* __restr
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     float4* stage0 = smem_f4 + (size_t)wib * Q * STAGE_F4;
+    // an earlier launch of this context timed out and nobody has read the flag yet
+    if (*reinterpret_cast<volatile int*>(ctl + 2)) return;
     for (int b = 0; b < n_blocks; b++) {
         const int parity = parity0 ^ (b & 1);
         const long long nb = n0 + (long long)b * T;
@@ -664,9 +667,14 @@ static cudaError_t launch_persistent_T(const fdtd_ctx* c, cudaStream_t st, int p
                               c->opt_debug_skip);
 }
 
-// n_blocks T-step blocks in one cooperative launch (control words zeroed first)
+// n_blocks T-step blocks in one cooperative launch.  The arrival, generation and
+// work-counter words are zeroed first; the error word ctl[2] is not: it stays set
+// from a timed-out launch until fdtd_sync reports it, so a later launch of the
+// same step call neither advances the fields nor overwrites the flag.
 int tmz_persistent_launch(fdtd_ctx* c, int T, long long n0, int n_blocks, int parity) {
-    cudaError_t e = cudaMemsetAsync(c->d_ctl, 0, (size_t)(4 + n_blocks) * sizeof(unsigned), c->stream);
+    cudaError_t e = cudaMemsetAsync(c->d_ctl, 0, 2 * sizeof(unsigned), c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->d_ctl + 3, 0, (size_t)(1 + n_blocks) * sizeof(unsigned), c->stream);
     int grid = 0;
     const bool wrec = adj_edge_mode(c);   // edge-weight reverse mode: keep the design window
     if (e == cudaSuccess) {
@@ -686,6 +694,7 @@ int tmz_persistent_launch(fdtd_ctx* c, int T, long long n0, int n_blocks, int pa
         }
     }
     c->launches++;
+    c->opt_debug_skip = -1;   // the test hook covers one launch
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_err, c->d_ctl + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) {
         c->err = std::string("persistent launch: ") + cudaGetErrorString(e);
@@ -1152,6 +1161,46 @@ __global__ void k_design_band(const uint8_t* __restrict__ mat, const float4* __r
     band[2 * plane + o] = co.z;
 }
 
+// eq. (7) for every design cell from device arrays (FP64, as the host path):
+// co = (Ca, Cb/dx, Cb/dy, Cb) and the gradient factor -eps0 / (eps0 eps_r + sigma dt / 2);
+// *bad = 1 if some eps_r <= 0 or sigma < 0 (or either is NaN)
+__global__ void k_design_coeffs(const double* __restrict__ eps_r, const double* __restrict__ sigma, int n, double dt,
+                                double dx, double dy, double eps0, float4* __restrict__ co, float* __restrict__ fac,
+                                int* bad) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const double er = eps_r[q], sg = sigma ? sigma[q] : 0.0;
+    if (!(er > 0.0) || !(sg >= 0.0)) {
+        atomicOr(bad, 1);
+        return;
+    }
+    const double eps = __dmul_rn(eps0, er);
+    const double half = __ddiv_rn(__dmul_rn(sg, dt), __dmul_rn(2.0, eps));
+    const double am = __dsub_rn(1.0, half), ap = __dadd_rn(1.0, half);
+    const double ca = __ddiv_rn(am, ap), cb = __ddiv_rn(dt, __dmul_rn(ap, eps));
+    co[q] = make_float4((float)ca, (float)__ddiv_rn(cb, dx), (float)__ddiv_rn(cb, dy), (float)cb);
+    fac[q] = (float)__ddiv_rn(-eps0, __dadd_rn(eps, __ddiv_rn(__dmul_rn(sg, dt), 2.0)));
+}
+
+int tmz_design_coeffs(fdtd_ctx* c, Scene2* s, const double* eps_r, const double* sigma, size_t n, int* bad) {
+    int* d_bad = nullptr;
+    if (cudaMallocAsync(&d_bad, sizeof(int), c->stream) != cudaSuccess) return FDTD_ENOMEM;
+    cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream);
+    const double eps0 = 1.0 / (4.0e-7 * M_PI * 299792458.0 * 299792458.0);
+    k_design_coeffs<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(eps_r, sigma, (int)n, s->dt, s->dx, s->dy,
+                                                                         eps0, s->d_dsg, s->d_dsg_fac, d_bad);
+    c->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    cudaFreeAsync(d_bad, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->err = std::string("design coefficients: ") + cudaGetErrorString(e);
+        return FDTD_ECUDA;
+    }
+    return FDTD_OK;
+}
+
 int tmz_design_band(fdtd_ctx* c, Scene2* s) {
     const dim3 grd((unsigned)((s->pitch + 127) / 128), (unsigned)s->dsg_h);
     k_design_band<<<grd, 128, 0, c->stream>>>(s->d_mat, s->d_coef, s->d_dsg, s->d_band, s->pitch, s->dsg_i0,
@@ -1211,19 +1260,26 @@ int dft_cells_launch(fdtd_ctx* c, const DftMon& m, long long n0, int nsteps) {
     return FDTD_OK;
 }
 
-int tmz_finite_check(fdtd_ctx* c, int* bad) {
+// one scan of every scene's current Ez, Hx, Hy: sets *d_flag (device word) to 1
+// if any value is not finite; never clears it
+cudaError_t tmz_finite_launch(fdtd_ctx* c, int* d_flag) {
     int mx = 0, my = 0;
     for (auto* s : c->s2) {
         mx = s->nx > mx ? s->nx : mx;
         my = s->ny > my ? s->ny : my;
     }
+    const dim3 blk(32, 8);
+    const dim3 grd((mx + 31) / 32, (my + 7) / 8, (unsigned)c->s2.size());
+    k_tmz_finite<<<grd, blk, 0, c->stream>>>(c->d_scenes, c->parity, d_flag);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+int tmz_finite_check(fdtd_ctx* c, int* bad) {
     int* d_bad = nullptr;
     if (cudaMallocAsync(&d_bad, sizeof(int), c->stream) != cudaSuccess) return FDTD_ENOMEM;
     cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream);
-    const dim3 blk(32, 8);
-    const dim3 grd((mx + 31) / 32, (my + 7) / 8, (unsigned)c->s2.size());
-    k_tmz_finite<<<grd, blk, 0, c->stream>>>(c->d_scenes, c->parity, d_bad);
-    c->launches++;
+    tmz_finite_launch(c, d_bad);
     cudaMemcpyAsync(bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     cudaFreeAsync(d_bad, c->stream);
     cudaError_t e = cudaStreamSynchronize(c->stream);

@@ -4,12 +4,17 @@
   with no data-path collective: ``shard_scenes`` balances cells greedily.
 * Whole-job throughput is the units all ranks processed over the slowest rank's
   time (``job_throughput``).
-* A single grid larger than one GPU splits into y-slabs; every step needs one
-  row of Ez from the +y neighbour before layer 1 and one row of Hx from the -y
-  neighbour before layer 2 (the H update reads Ez(j+1), the E update reads
-  Hx(j-1); Sec. III-B eqs. (7)-(9)).  ``SlabExchange`` does that exchange with
-  point-to-point messages into the receiver's own buffers.  Each box in this
-  build has one GPU, so the slab path is exercised on CPU ranks.
+* A single grid larger than one GPU splits into y-slabs (the domain
+  decomposition of Sec. II); every step needs one row of Ez from the +y
+  neighbour before layer 1 and one row of Hx from the -y neighbour before
+  layer 2 (the H update reads Ez(j+1), the E update reads Hx(j-1); Sec. III-B
+  eqs. (7)-(9)).  ``SlabExchange`` does that exchange per step for host
+  arrays.  ``HaloExchange`` does it for slabs with ``ghost`` rows per cut,
+  which advance up to ``ghost`` steps between exchanges (the library's slab
+  contexts, fdtd_create_slab, with CUDA tensors over NCCL; host slabs with CPU
+  tensors over gloo); ``exchange_local`` refreshes slabs held by one process
+  (several slabs on one GPU).  Every exchange is point-to-point into the
+  receiver's own memory: no peer loads.
 """
 from __future__ import annotations
 
@@ -78,7 +83,7 @@ class SlabExchange:
         if to is not None:
             reqs.append(dist.isend(torch.from_numpy(np.ascontiguousarray(send_row)), to, group=self.group, tag=tag))
         if frm is not None:
-            buf = torch.empty(recv_row.shape, dtype=torch.float64)
+            buf = torch.from_numpy(np.empty_like(recv_row))   # the row's own dtype (float32 or float64)
             dist.recv(buf, frm, group=self.group, tag=tag)
             recv_row[...] = buf.numpy()
         for r in reqs:
@@ -100,3 +105,70 @@ class SlabExchange:
             send = h[self.g0 + (self.j1 - self.j0) - 1] if up is not None else None
             recv = h[0] if dn is not None else np.empty(h.shape[1])
             self._swap(send, recv, up, dn, tag=2 + k)
+
+
+def exchange_local(slabs, bufs=None):
+    """Refresh the ghost rows of slabs held by one process (ordered bottom to
+    top, each holding the rows above the previous one's): at every cut the lower
+    slab's top owned rows go to the upper slab's lower ghost rows and the upper
+    slab's bottom owned rows to the lower slab's upper ghost rows, through
+    buffers allocated once (CUDA tensors for the library's slabs, so each copy is
+    a device-to-device copy into the receiver's own memory).  The exports of a
+    cut read owned rows and the imports write ghost rows, so their order does
+    not matter.  Returns the buffers for reuse."""
+    import torch
+    if bufs is None:
+        bufs = []
+        for a in slabs[:-1]:
+            n = a.halo_count()
+            dev = "cuda" if getattr(a, "on_device", True) else "cpu"
+            bufs.append((torch.empty(n, dtype=torch.float32, device=dev),
+                         torch.empty(n, dtype=torch.float32, device=dev)))
+    for (a, b), (up, down) in zip(zip(slabs[:-1], slabs[1:]), bufs):
+        a.halo_export(1, up)
+        b.halo_export(0, down)
+        b.halo_import(0, up)
+        a.halo_import(1, down)
+    return bufs
+
+
+class HaloExchange:
+    """Ghost-row exchange of a y-slab decomposition across ranks, for any slab
+    with ``halo_count()``, ``halo_export(side, buf)`` and ``halo_import(side,
+    buf)`` (side 0: the cut below the owned rows, 1: above).  Each exchange
+    exports the owned rows next to every cut, sends them to the neighbour across
+    it, receives that neighbour's rows and imports them into the ghost rows:
+    point-to-point messages into the receiver's own buffers.  Tags tell the two
+    directions apart (gloo; NCCL ignores tags but keeps the order of the one
+    message per direction between a pair of ranks)."""
+
+    def __init__(self, slab, rank, world, device="cpu", dtype=None, group=None):
+        import torch
+        self.slab, self.rank, self.world, self.group = slab, rank, world, group
+        self.device = torch.device(device)
+        n = slab.halo_count()
+        dt = dtype or torch.float32
+        self.nbr = {}
+        if rank > 0:
+            self.nbr[0] = rank - 1
+        if rank + 1 < world:
+            self.nbr[1] = rank + 1
+        self.send = {s: torch.empty(n, dtype=dt, device=self.device) for s in self.nbr}
+        self.recv = {s: torch.empty(n, dtype=dt, device=self.device) for s in self.nbr}
+
+    def exchange(self):
+        import torch
+        import torch.distributed as dist
+        for side in self.nbr:
+            self.slab.halo_export(side, self.send[side])
+        if self.device.type == "cuda":
+            torch.cuda.synchronize(self.device)   # the exports ran on the slab's stream
+        reqs = []
+        for side, peer in self.nbr.items():
+            # tag 1: rows travelling up (sent across the upper cut), tag 2: down
+            reqs.append(dist.isend(self.send[side], peer, group=self.group, tag=1 if side == 1 else 2))
+            reqs.append(dist.irecv(self.recv[side], peer, group=self.group, tag=2 if side == 1 else 1))
+        for r in reqs:
+            r.wait()
+        for side in self.nbr:
+            self.slab.halo_import(side, self.recv[side])

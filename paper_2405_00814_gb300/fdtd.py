@@ -22,7 +22,7 @@ PEC, CPML, SPLIT_PML = 0, 1, 2
 COMP = {"ex": 0, "ey": 1, "ez": 2, "hx": 3, "hy": 4, "hz": 5}
 SRC = {"ricker": 0, "gauss_mod": 1, "gauss": 2, "sampled": 3, "sine": 4}
 OPT = {"kernel": 0, "tblock": 1, "segment": 2, "warps": 3, "graph": 4, "spin_limit": 5, "debug_skip_cta": 6,
-       "adj_store": 7, "segment_b": 8}
+       "adj_store": 7, "segment_b": 8, "check_every": 9}
 
 
 class FDTDError(RuntimeError):
@@ -63,7 +63,7 @@ def lib():
         L.fdtd_get_option.restype = i64
         L.fdtd_set_source.argtypes = [vp, ip, ip, ip, ip, ip, dp, vp, i64]
         L.fdtd_set_line_source.argtypes = [vp, ip, ip, ip, ip, dp, vp, i64]
-        L.fdtd_set_design.argtypes = [vp, ip, ip, ip, ip, dp, dp]
+        L.fdtd_set_design.argtypes = [vp, ip, ip, ip, ip, vp, vp, ip]
         L.fdtd_set_materials.argtypes = [vp, vp, vp, ip]
         L.fdtd_add_probe.argtypes = [vp, ip, ip, ip, ip, C.POINTER(C.c_int)]
         L.fdtd_add_dft_monitor.argtypes = [vp, vp, ip, dp, ip, C.POINTER(C.c_int)]
@@ -89,6 +89,13 @@ def lib():
         L.fdtd_adjoint_grad.argtypes = [vp, vp, vp, vp, ip]
         L.fdtd_edge_grad.argtypes = [vp, vp, vp, vp, ip]
         L.fdtd_mp_steps_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, i64, vp]
+        L.fdtd_create_slab.argtypes = [C.POINTER(Grid), ip, ip, ip, C.c_double, C.c_double, C.c_double, vp,
+                                       C.POINTER(Material), ip, vp, C.POINTER(vp)]
+        L.fdtd_halo_count.argtypes = [vp]
+        L.fdtd_halo_count.restype = i64
+        L.fdtd_halo_export.argtypes = [vp, ip, vp, ip]
+        L.fdtd_halo_import.argtypes = [vp, ip, vp, ip]
+        L.fdtd_slab_rows.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
         _LIB = L
     return _LIB
 
@@ -176,6 +183,64 @@ class Simulation:
         sim._check(rc)
         sim._cells = [s.nx * s.ny for s in scenes]
         return sim
+
+    @classmethod
+    def slab(cls, scene, j0, j1, ghost, *, stream=None, boundary=None):
+        """A y-slab sub-domain owning rows [j0, j1) of a 2D scene plus `ghost`
+        rows on each side with a neighbour (fdtd_create_slab).  Local row r is
+        scene row r + row_offset.  The scene's source is set when its cells fall
+        in the local rows (in local coordinates); probes and monitors are left to
+        the caller (on the slab that owns the cell)."""
+        L = lib()
+        g = _grid_of(scene, boundary)
+        glo = ghost if j0 > 0 else 0
+        ghi = ghost if j1 < scene.ny else 0
+        lo, hi = max(0, j0 - glo), min(scene.ny, j1 + ghi)
+        mat = np.ascontiguousarray(scene.mat[lo:hi], np.uint8)
+        tab = _mat_table(scene.eps_r, scene.sigma)
+        h = C.c_void_p()
+        rc = L.fdtd_create_slab(C.byref(g), int(j0), int(j1), int(ghost), scene.dx, scene.dt, 0.0, mat.ctypes.data,
+                                tab, len(scene.eps_r), _stream_handle(stream), C.byref(h))
+        sim = cls(_handle=h)
+        sim._check(rc)
+        sim.shape = (scene.nx, hi - lo, 1)
+        sim._cells = [scene.nx * (hi - lo)]
+        sim.slab_rows = (j0, j1, lo)
+        src = getattr(scene, "source", None)
+        if src is not None:
+            n = getattr(src, "length", 1)
+            a, b = max(src.j, lo), min(src.j + n, hi)
+            if a < b and not (a == 0 and lo == 0):
+                if src.kind == "sampled":
+                    sim.set_line_source("sampled", src.i, a - lo, b - lo, samples=src.samples)
+                else:
+                    sim.set_line_source(src.kind, src.i, a - lo, b - lo, param=src.params[0])
+        return sim
+
+    def halo_count(self) -> int:
+        return int(self._L.fdtd_halo_count(self._h))
+
+    def _halo_buf(self, buf):
+        self._need(buf, self.halo_count(), "halo")
+        if hasattr(buf, "data_ptr"):
+            if buf.dtype.__str__() != "torch.float32":
+                raise ValueError("halo buffers are float32")
+            return buf.data_ptr(), 1 if buf.is_cuda else 0
+        if not (isinstance(buf, np.ndarray) and buf.dtype == np.float32 and buf.flags.c_contiguous):
+            raise ValueError("halo buffers are contiguous float32")
+        return buf.ctypes.data, 0
+
+    def halo_export(self, side: int, out):
+        """The owned rows next to cut `side` (0 lower, 1 upper), packed
+        [array][ghost][nx], into out (CUDA tensor, CPU tensor or numpy array)."""
+        ptr, dev = self._halo_buf(out)
+        self._check(self._L.fdtd_halo_export(self._h, int(side), ptr, dev))
+        return out
+
+    def halo_import(self, side: int, buf):
+        """Overwrite the ghost rows beyond cut `side` from the neighbour's export."""
+        ptr, dev = self._halo_buf(buf)
+        self._check(self._L.fdtd_halo_import(self._h, int(side), ptr, dev))
 
     # ---------------------------------------------------------------- basics
     def _check(self, rc):
@@ -284,10 +349,24 @@ class Simulation:
         self._check(self._L.fdtd_set_materials(self._h, m.ctypes.data, tab, len(eps_r)))
 
     def set_design(self, i0, j0, eps_r, sigma=None):
+        """Design rectangle at (i0, j0) with per-cell eps_r [h][w] (and sigma).
+        A CUDA float64 tensor goes to the library as a device pointer (the
+        coefficients are formed on the GPU, no host copy); anything else is taken
+        as host values."""
+        if hasattr(eps_r, "data_ptr") and eps_r.is_cuda:
+            import torch
+            eps = eps_r.detach().to(torch.float64).contiguous()
+            sg = None if sigma is None else sigma.detach().to(device=eps.device, dtype=torch.float64).contiguous()
+            h, w = eps.shape
+            with torch.cuda.device(eps.device):
+                self._check(self._L.fdtd_set_design(self._h, i0, j0, w, h, eps.data_ptr(),
+                                                    None if sg is None else sg.data_ptr(), 1))
+            return
         eps = np.ascontiguousarray(eps_r, np.float64)
         h, w = eps.shape
-        sg = None if sigma is None else np.ascontiguousarray(sigma, np.float64).ctypes.data_as(C.POINTER(C.c_double))
-        self._check(self._L.fdtd_set_design(self._h, i0, j0, w, h, eps.ctypes.data_as(C.POINTER(C.c_double)), sg))
+        sg = None if sigma is None else np.ascontiguousarray(sigma, np.float64)
+        self._check(self._L.fdtd_set_design(self._h, i0, j0, w, h, eps.ctypes.data,
+                                            None if sg is None else sg.ctypes.data, 0))
 
     def add_probe(self, i, j, k=0, component="ez") -> int:
         pid = C.c_int()
@@ -331,7 +410,8 @@ class Simulation:
 
     def sync(self):
         """Wait for the stream; raises FDTDError(ETIMEOUT) if a bounded device
-        wait gave up since the last call."""
+        wait gave up since the last call, else FDTDError(EUNSTABLE) if the
+        periodic finite check (option "check_every") found a NaN or Inf."""
         self._check(self._L.fdtd_sync(self._h))
 
     def autotune(self, trial_steps=32, cache=None, key=None):
@@ -526,20 +606,58 @@ EDGE_CLASSES = 11   # FDTD_EDGE_CLASSES: weights a design cell owns as a destina
 MP_NOALLOC_MAX_NODES = 1 << 22
 
 
+def check_noalloc_args(layer1, layer2, h, require_cuda=True):
+    """Reject, before anything is launched, arguments fdtd_mp_steps_noalloc's
+    kernel would read out of bounds or across devices: tensors that are not
+    torch tensors, not on CUDA (when require_cuda), of the wrong dtype
+    (int32 rowptr/col, float32 w/h), not contiguous, not all on h's device;
+    a rowptr without n_nodes + 1 entries; w and col of different lengths.
+    Returns n_nodes."""
+    import torch
+    r1, c1, w1 = layer1
+    r2, c2, w2 = layer2
+    named = (("h", h, torch.float32), ("rowptr1", r1, torch.int32), ("col1", c1, torch.int32),
+             ("w1", w1, torch.float32), ("rowptr2", r2, torch.int32), ("col2", c2, torch.int32),
+             ("w2", w2, torch.float32))
+    for name, t, dt in named:
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name}: expected a torch tensor")
+        if require_cuda and not t.is_cuda:
+            raise ValueError(f"{name}: must be a CUDA tensor")
+        if t.dtype != dt:
+            raise ValueError(f"{name}: dtype {t.dtype}, expected {dt}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name}: must be contiguous")
+        if t.device != h.device:
+            raise ValueError(f"{name}: on {t.device}, h on {h.device}")
+    n = int(h.numel())
+    for k, (rp, col, w) in enumerate(((r1, c1, w1), (r2, c2, w2)), 1):
+        if rp.dim() != 1 or rp.numel() != n + 1:
+            raise ValueError(f"rowptr{k}: {rp.numel()} entries, expected n_nodes + 1 = {n + 1}")
+        if w.numel() != col.numel():
+            raise ValueError(f"w{k}: {w.numel()} entries, col{k} has {col.numel()}")
+    return n
+
+
 def mp_steps_noalloc(layer1, layer2, h, n_steps, stream=None):
     """Allocation-free two-layer message passing (fdtd_mp_steps_noalloc).
 
     layer1/layer2: (rowptr, col, w) CUDA tensors (int32, int32, float32); h:
     CUDA float32 tensor of node values, updated in place.  For callers that
-    cannot allocate device memory (see the C header)."""
+    cannot allocate device memory (see the C header).  The kernel trusts the
+    graph's shape, so check_noalloc_args vets every tensor first; the call runs
+    with h's device current (the scratch array is per device)."""
+    import torch
+    n = check_noalloc_args(layer1, layer2, h)
     L = lib()
     r1, c1, w1 = layer1
     r2, c2, w2 = layer2
-    rc = L.fdtd_mp_steps_noalloc(r1.data_ptr(), c1.data_ptr(), w1.data_ptr(), r2.data_ptr(), c2.data_ptr(),
-                                 w2.data_ptr(), h.data_ptr(), int(h.numel()), int(n_steps), _stream_handle(stream))
+    with torch.cuda.device(h.device):
+        rc = L.fdtd_mp_steps_noalloc(r1.data_ptr(), c1.data_ptr(), w1.data_ptr(), r2.data_ptr(), c2.data_ptr(),
+                                     w2.data_ptr(), h.data_ptr(), n, int(n_steps), _stream_handle(stream))
     if rc != OK:
         raise FDTDError(rc, "fdtd_mp_steps_noalloc rejected its arguments or failed to launch"
-                        f" (n_nodes {h.numel()}, limit {MP_NOALLOC_MAX_NODES})")
+                        f" (n_nodes {n}, limit {MP_NOALLOC_MAX_NODES})")
 
 
 def from_scene(scene, *, stream=None, probes=True, monitors=True, source=True, boundary=None) -> Simulation:

@@ -152,3 +152,32 @@ def _onehot(n, dj, di):
     z = np.zeros((n, n))
     z[dj, di] = 1.0
     return z
+
+
+def test_design_set_from_device_memory_equals_host_values():
+    """fdtd_set_design with on_device: the coefficients formed by the kernel
+    from a CUDA tensor give the same run as the host path, and an invalid value
+    found on the device is refused and drops the rectangle."""
+    import torch
+    from paper_2405_00814_gb300 import fdtd
+    sc = scenes.adjoint_scenes(side=96, n_designs=1, nsteps=200, npml=8, design=24, n_monitors=3)[0]
+    i0, j0, w, h = sc.design
+    sig = np.full((h, w), 0.02)
+    out = []
+    for dev in (False, True):
+        sim = fdtd.from_scene(sc)
+        if dev:
+            sim.set_design(i0, j0, torch.tensor(sc.design_eps, device="cuda"), torch.tensor(sig, device="cuda"))
+        else:
+            sim.set_design(i0, j0, sc.design_eps, sig)
+        sim.step(200)
+        out.append({c: sim.get_field(c, (sc.ny, sc.nx)) for c in ("ez", "hx", "hy")})
+        if dev:
+            bad = torch.tensor(sc.design_eps, device="cuda")
+            bad[3, 4] = 0.0
+            with pytest.raises(fdtd.FDTDError) as ei:
+                sim.set_design(i0, j0, bad)
+            assert ei.value.code == fdtd.EINVAL
+        sim.close()
+    for c in ("ez", "hx", "hy"):
+        assert rel_l2(out[1][c], out[0][c]) <= 1e-7, c

@@ -117,6 +117,37 @@ def test_persistent_barrier_timeout_is_reported_and_recoverable():
     sim.close()
 
 
+def test_persistent_timeout_in_an_early_launch_is_not_lost():
+    """Checkpoints every 16 steps split one step call into four persistent
+    launches; only the first has a CTA that never arrives.  The later launches
+    must neither clear the error word nor advance the fields, and fdtd_sync must
+    report FDTD_ETIMEOUT once."""
+    from paper_2405_00814_gb300 import fdtd
+    scs, sim, _ = _batch(n=2, nsteps=64, lo=96, hi=160)
+    sim.set_option("kernel", 2)
+    sim.set_option("tblock", 4)
+    sim.set_option("spin_limit", 20000)
+    sim.set_checkpointing(16)
+    sim.set_option("debug_skip_cta", 0)
+    n0 = sim.launch_count
+    sim.step(64)
+    assert sim.launch_count - n0 >= 4
+    assert sim.get_option("debug_skip_cta") == -1
+    with pytest.raises(fdtd.FDTDError) as ei:
+        sim.sync()
+    assert ei.value.code == fdtd.ETIMEOUT
+    sim.sync()                     # reported once
+    sim.set_checkpointing(0)
+    sim.set_option("spin_limit", 4000000)
+    sim.reset()
+    sim.step(64)
+    sim.sync()
+    got = _fields(sim, scs)
+    for k, s in enumerate(scs):
+        assert_fields_close(got[k], oracle_run(s, 64))
+    sim.close()
+
+
 def test_graph_rerecords_after_design_change():
     """A recorded graph refers to the context's device buffers.  Changing a
     design rebuilds them, so the next graph step must record afresh and give

@@ -1,8 +1,8 @@
 """The allocation-free message-passing entry point against the context path.
 
 fdtd_mp_steps_noalloc is for callers that cannot allocate device memory (a
-stream under graph capture, a host allocator that owns all device memory, a
-real-time loop that cannot take cudaMalloc's synchronisation).  It must give the
+host allocator that owns all device memory, a real-time loop that cannot take
+cudaMalloc's synchronisation).  It must give the
 same node values as fdtd_step_edgelist, the existing literal message-passing
 entry point, on the same graph and initial state -- checked on two calls in a
 row, since every call reuses the same fixed scratch array.  This file is named
@@ -85,7 +85,7 @@ def test_noalloc_rejects_oversized_graph(torch_cuda):
     torch = torch_cuda
     from paper_2405_00814_gb300 import fdtd
     n = fdtd.MP_NOALLOC_MAX_NODES + 1
-    rp = torch.zeros(2, dtype=torch.int32, device="cuda")
+    rp = torch.zeros(n + 1, dtype=torch.int32, device="cuda")   # well-formed, only too large
     col = torch.zeros(1, dtype=torch.int32, device="cuda")
     w = torch.zeros(1, dtype=torch.float32, device="cuda")
     h = torch.zeros(n, dtype=torch.float32, device="cuda")
