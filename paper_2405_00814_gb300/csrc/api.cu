@@ -369,6 +369,9 @@ fdtd_ctx* ctx_new(void* stream) {
     c->n_tasks_s = 0;
     c->d_tasks_bd = nullptr;
     c->n_tasks_bd = 0;
+    c->d_tasks_n = nullptr;
+    c->n_tasks_n = 0;
+    c->task_narrow = -1;
     c->aux = c->aux2 = nullptr;
     c->ev_fork = c->ev_join = c->ev_join2 = nullptr;
     cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
@@ -504,9 +507,10 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     // list, the rest to the interior list; each list is padded to whole CTAs
     // per scene so that a CTA never mixes scenes.
     const int wout = STRIP - 2 * HALO;
-    std::vector<Task> tasks, tasks_b, tasks_l, tasks_s, tasks_bd;
+    std::vector<Task> tasks, tasks_b, tasks_l, tasks_s, tasks_bd, tasks_n;
     std::vector<Sample2> tsamp;
     const int warps_b = 2;
+    const bool want_narrow = c->opt_kernel == 0;   // the persistent kernel takes whole-warp tasks only
     bool any_design = false;
     for (const Scene2* s : c->s2) any_design = any_design || s->d_dsg != nullptr;
     const int warps_l = 4;   // lite CTAs; each list is padded to its launch's CTA width
@@ -519,12 +523,26 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
         // the rest run the lean interior kernel.  General warps are heavier per
         // row, so they get half-height segments.
         const int seg_b = c->opt_segment_b > 0 ? c->opt_segment_b : std::max(8, seg / 2);
+        // Narrow x-slab tasks: the columns [0, NG_OWN) and [xr, nx) holding the
+        // x-slabs of a CPML go to lane-group tasks (4 per warp) instead of whole
+        // 120-column strips, and the strips cover [NG_OWN, xr) with a column
+        // limit.  A strip computes the slab cells in its reach without the CPML,
+        // which spoils one more column per step: its owned columns end at
+        // xr <= nx - npml - MAX_TB, and its first loaded column NG_OWN - HALO is
+        // outside the left slab.  The design rectangle must stay clear of the
+        // narrow columns (those tasks are built without design code).
+        const int xr = (s->nx - NG_OWN + 3) / 4 * 4;
+        const bool nar = want_narrow && s->npml > 0 && !s->split && s->nx >= 2 * NG_OWN + 8 &&
+                         NG_OWN - HALO >= s->npml && xr <= s->nx - s->npml - MAX_TB &&
+                         !(s->d_dsg && (s->dsg_i0 < NG_OWN + HALO || s->dsg_i0 + s->dsg_w > xr - HALO));
+        const int xl = nar ? NG_OWN : 0;
+        auto owned_end = [&](int x0) { return nar ? std::min(x0 + wout, xr) : x0 + wout; };
         auto flags_of = [&](int x0, int ya, int yb, bool* general) {
             int f = 0;
             const int lx0 = x0 - HALO, lx1 = x0 - HALO + STRIP;   // loaded columns
             const int ly0 = ya - MAX_TB, ly1 = yb + MAX_TB;        // widest streamed rows
-            if (s->npml > 0 && (lx0 < s->npml || lx1 > s->nx - s->npml || ly0 < s->npml - s->yoff ||
-                                ly1 > s->ny_glob - s->npml - s->yoff))
+            const bool xslab = !nar && (lx0 < s->npml || lx1 > s->nx - s->npml);
+            if (s->npml > 0 && (xslab || ly0 < s->npml - s->yoff || ly1 > s->ny_glob - s->npml - s->yoff))
                 f |= TASK_PML;
             if (s->src_kind >= 0 && s->src_i >= lx0 && s->src_i < lx1 && s->src_j < ly1 && s->src_j1 > ly0)
                 f |= TASK_SRC;
@@ -532,18 +550,18 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
                 f |= TASK_DSG;
             bool samp = false;
             for (const Sample2& sp : s->samples)
-                if (sp.i >= x0 && sp.i < x0 + wout && sp.j >= ya && sp.j < yb) samp = true;
-            *general = f != 0 || samp || x0 + wout > s->nx;
+                if (sp.i >= x0 && sp.i < owned_end(x0) && sp.j >= ya && sp.j < yb) samp = true;
+            *general = f != 0 || samp || (!nar && x0 + wout > s->nx);
             return f;
         };
         auto add_task = [&](int x0, int ya, int yb) {
             Task t;
             bool general;
-            t.scene = k; t.x0 = x0; t.ya = ya; t.yb = yb; t.pad = 0;
+            t.scene = k; t.x0 = x0; t.ya = ya; t.yb = yb; t.xe = nar ? owned_end(x0) : 0;
             t.flags = flags_of(x0, ya, yb, &general);
             t.samp_begin = (int)tsamp.size();
             for (const Sample2& sp : s->samples)
-                if (sp.i >= x0 && sp.i < x0 + wout && sp.j >= ya && sp.j < yb) tsamp.push_back(sp);
+                if (sp.i >= x0 && sp.i < owned_end(x0) && sp.j >= ya && sp.j < yb) tsamp.push_back(sp);
             t.samp_end = (int)tsamp.size();
             // the lite kernel pays for its own launch and stream fork only when a
             // design rectangle gives it work; otherwise its tasks join the CPML list
@@ -556,9 +574,37 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
             else if (general) tasks_l.push_back(t);
             else tasks.push_back(t);
         };
+        // the narrow tasks: both sides, segments of seg_b rows, the first task of
+        // each warp repeated (TASK_NOSTORE) to fill the warp's four lane groups
+        const size_t first_n = tasks_n.size();
+        if (nar) {
+            for (int side = 0; side < 2; side++) {
+                const int x0 = side == 0 ? 0 : xr, xe = side == 0 ? NG_OWN : s->nx;
+                for (int y = 0; y < s->ny; y += seg_b) {
+                    Task t;
+                    t.scene = k; t.x0 = x0; t.ya = y; t.yb = std::min(y + seg_b, s->ny); t.xe = xe;
+                    t.flags = TASK_PML;
+                    const int ly0 = t.ya - MAX_TB, ly1 = t.yb + MAX_TB;
+                    if (s->src_kind >= 0 && s->src_i >= x0 - HALO && s->src_i < x0 - HALO + 4 * NG_LANES &&
+                        s->src_j < ly1 && s->src_j1 > ly0)
+                        t.flags |= TASK_SRC;
+                    t.samp_begin = (int)tsamp.size();
+                    for (const Sample2& sp : s->samples)
+                        if (sp.i >= x0 && sp.i < xe && sp.j >= t.ya && sp.j < t.yb) tsamp.push_back(sp);
+                    t.samp_end = (int)tsamp.size();
+                    tasks_n.push_back(t);
+                }
+            }
+            const int per_warp = 32 / NG_LANES;
+            while ((tasks_n.size() - first_n) % per_warp) {
+                Task t = tasks_n[first_n + (tasks_n.size() - first_n) / per_warp * per_warp];
+                t.flags |= TASK_NOSTORE;
+                tasks_n.push_back(t);
+            }
+        }
         for (int ya = 0; ya < s->ny; ya += seg) {
             const int yb = std::min(ya + seg, s->ny);
-            for (int x0 = 0; x0 < s->nx; x0 += wout) {
+            for (int x0 = xl; x0 < (nar ? xr : s->nx); x0 += wout) {
                 bool general;
                 flags_of(x0, ya, yb, &general);
                 if (!general) {
@@ -581,6 +627,8 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
             while ((tasks_s.size() - first_s) % warps_b) tasks_s.push_back(pad);
         if (tasks_bd.size() > first_bd)
             while ((tasks_bd.size() - first_bd) % warps_b) tasks_bd.push_back(pad);
+        if (tasks_n.size() > first_n)   // whole CTAs of warps_b warps; a padding warp returns
+            while ((tasks_n.size() - first_n) % (warps_b * 32 / NG_LANES)) tasks_n.push_back(pad);
     }
     // every list is launched in blocks of its own width: a block holds tasks of one
     // scene and starts with a real task, and every task lies inside its scene
@@ -605,6 +653,7 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
         if (!vr) vr = valid(tasks_bd, warps_b, "CPML design");
         if (!vr) vr = valid(tasks_s, warps_b, "split");
         if (!vr) vr = valid(tasks_l, warps_l, "lite");
+        if (!vr) vr = valid(tasks_n, warps_b * 32 / NG_LANES, "narrow CPML");
         if (vr) return vr;
     }
     std::vector<Sample2> ssamp;
@@ -628,7 +677,9 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     dfree(c->d_tasks_l);
     dfree(c->d_tasks_s);
     dfree(c->d_tasks_bd);
+    dfree(c->d_tasks_n);
     dfree(c->d_dft);
+    c->d_tasks_n = nullptr;
     c->d_tasks_l = nullptr;
     c->d_tasks_s = nullptr;
     c->d_tasks_bd = nullptr;
@@ -646,6 +697,7 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     if ((rc = dalloc(c, &c->d_tasks_l, tasks_l.size() * sizeof(Task), "tasks"))) return rc;
     if ((rc = dalloc(c, &c->d_tasks_s, tasks_s.size() * sizeof(Task), "tasks"))) return rc;
     if ((rc = dalloc(c, &c->d_tasks_bd, tasks_bd.size() * sizeof(Task), "tasks"))) return rc;
+    if ((rc = dalloc(c, &c->d_tasks_n, tasks_n.size() * sizeof(Task), "tasks"))) return rc;
     if ((rc = dalloc(c, &c->d_samp, tsamp.size() * sizeof(Sample2), "samples"))) return rc;
     if ((rc = dalloc(c, &c->d_samp_scene, ssamp.size() * sizeof(Sample2), "samples"))) return rc;
     if ((rc = dalloc(c, &c->d_samp_off, soff.size() * sizeof(int), "sample offsets"))) return rc;
@@ -662,6 +714,8 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
         CK(cudaMemcpyAsync(c->d_tasks_s, tasks_s.data(), tasks_s.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
     if (!tasks_bd.empty())
         CK(cudaMemcpyAsync(c->d_tasks_bd, tasks_bd.data(), tasks_bd.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
+    if (!tasks_n.empty())
+        CK(cudaMemcpyAsync(c->d_tasks_n, tasks_n.data(), tasks_n.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
     if (!tsamp.empty())
         CK(cudaMemcpyAsync(c->d_samp, tsamp.data(), tsamp.size() * sizeof(Sample2), cudaMemcpyHostToDevice, c->stream), "upload");
     if (!ssamp.empty())
@@ -700,6 +754,8 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     c->n_tasks_l = (int)tasks_l.size();
     c->n_tasks_s = (int)tasks_s.size();
     c->n_tasks_bd = (int)tasks_bd.size();
+    c->n_tasks_n = (int)tasks_n.size();
+    c->task_narrow = want_narrow ? 1 : 0;
     c->warps_l = warps_l;
     c->warps_b = warps_b;
     c->task_tb = T;
@@ -737,7 +793,7 @@ int step_prepare(fdtd_ctx* c, int64_t n_steps) {
     if (c->s2.empty()) return fail(c, FDTD_ESTATE, "no scene");
     int rc = ensure_capacity(c, c->t + n_steps);
     if (rc) return rc;
-    if (c->dirty || c->task_seg != c->opt_segment) {
+    if (c->dirty || c->task_seg != c->opt_segment || c->task_narrow != (c->opt_kernel == 0 ? 1 : 0)) {
         rc = rebuild(c, c->opt_tblock, c->opt_segment, c->opt_warps);
         if (rc) return rc;
     }
@@ -936,6 +992,7 @@ void fdtd_destroy(fdtd_ctx* c) {
     dfree(c->d_tasks_l);
     dfree(c->d_tasks_s);
     dfree(c->d_tasks_bd);
+    dfree(c->d_tasks_n);
     if (c->aux) cudaStreamDestroy(c->aux);
     if (c->aux2) cudaStreamDestroy(c->aux2);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);

@@ -92,14 +92,22 @@ struct TmzDev {
 
 // one warp's work in the fused kernel: columns [x0, x0 + STRIP - 2 HALO) and
 // rows [ya, yb) of one scene, plus the samples that fall in that output region
+// (a narrow task of a lane group owns columns [x0, x0 + (NG_LANES - 2) 4))
 struct Task {
     int scene;
     int x0, ya, yb;
     int samp_begin, samp_end;   // into the launch's Sample2 list
     int flags;                  // TASK_* bits
-    int pad;
+    int xe;                     // > 0: no column at or past xe is owned (0: none)
 };
-enum { TASK_PML = 1, TASK_SRC = 2, TASK_DSG = 4 };
+// TASK_NOSTORE: a copy that only fills a lane group of a warp (computes, stores nothing)
+enum { TASK_PML = 1, TASK_SRC = 2, TASK_DSG = 4, TASK_NOSTORE = 8 };
+// lanes per task of the narrow CPML kernel (4 tasks per warp); each owns
+// NG_OWN columns at one side of the grid, the columns of an x-slab of the CPML
+// and its reach (rebuild uses them when the layer is at most NG_OWN - HALO -
+// MAX_TB cells deep, so that no interior strip computes a CPML cell it owns)
+constexpr int NG_LANES = 8;
+constexpr int NG_OWN = (NG_LANES - 2) * 4;
 
 // ---------------------------------------------------------------------------
 // host side
@@ -193,6 +201,9 @@ struct fdtd_ctx {
     int n_tasks_s;
     gem::Task* d_tasks_bd;         // CPML tasks with a design rectangle in reach
     int n_tasks_bd;
+    gem::Task* d_tasks_n;          // narrow x-slab CPML tasks, NG_LANES lanes each (4 per warp)
+    int n_tasks_n;
+    int task_narrow;               // the lists were built with narrow x-slab tasks (kernel 0)
     gem::Task* d_tasks_l;          // lite tasks: design, source, probes or ragged edge, no CPML
     int n_tasks_l, warps_l;
     cudaStream_t aux, aux2;        // forked streams for the CPML and lite tasks

@@ -952,7 +952,7 @@ static int reverse_run(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, 
                 const int lx0 = x0 - HALO, lx1 = x0 - HALO + STRIP;
                 auto make = [&](int y0, int y1, bool* gen) {
                     Task t;
-                    t.scene = k; t.x0 = x0; t.ya = y0; t.yb = y1; t.flags = 0; t.pad = 0;
+                    t.scene = k; t.x0 = x0; t.ya = y0; t.yb = y1; t.flags = 0; t.xe = 0;
                     const int ly0 = y0 - MAX_TB, ly1 = y1 + MAX_TB;
                     if (s->npml > 0 && (lx0 < s->npml || lx1 > s->nx - s->npml || ly0 < s->npml || ly1 > s->ny - s->npml))
                         t.flags |= TASK_PML;

@@ -44,12 +44,16 @@ __host__ __device__ constexpr int pf_of(int T, bool pml) { return pml ? PF_B : Q
 // general tasks: CPML kind adds one float4 of y-profile scalars after the
 // material words; lite kind has three design-coefficient slots after the fields
 __host__ __device__ constexpr int gen_nslot(bool pml) { return pml ? 7 : 6; }
-__host__ __device__ constexpr int gen_stage_f4(bool pml) { return gen_nslot(pml) * 32 + 8 + (pml ? 1 : 0); }
+__host__ __device__ constexpr int gen_stage_f4(bool pml, int groups = 1) {
+    return gen_nslot(pml) * 32 + 8 + (pml ? groups : 0);
+}
 
 // V: 0 interior, 1 CPML, 2 lite, 3 split-field layer; 5, 6: CPML, lite keeping
-// the design window (edge-weight reverse mode); 7: CPML without design code
+// the design window (edge-weight reverse mode); 7: CPML without design code;
+// 8: CPML without design code in narrow lane groups (NG_LANES lanes per task)
 size_t tmz_fused_smem(int T, int warps, int V) {
     if (V == 0) return (size_t)warps * stages_for(T, false) * stage_f4(false) * sizeof(float4);
+    if (V == 8) return (size_t)warps * stages_for(T, true) * gen_stage_f4(true, 32 / NG_LANES) * sizeof(float4);
     const bool pml = V == 1 || V == 3 || V == 5 || V == 7;   // 3 split layer, 5 window-keeping, 7 design-free CPML
     return (size_t)warps * stages_for(T, pml) * gen_stage_f4(pml) * sizeof(float4);
 }
@@ -111,13 +115,21 @@ struct Prof {
 // One warp's task of the general kernel (any task: CPML slab, design rectangle,
 // source, probes, ragged edge).  coef_s is the scene's coefficient table (shared
 // or global memory); stage0 the warp's Q x STAGE_F4 float4 staging area.
-template <int T, bool PML, bool SPL = false, bool WREC = false, bool DSG = true>
+//
+// G < 32: the warp runs 32 / G independent tasks, one per group of G lanes (a
+// narrow strip of (G - 2) * 4 owned columns each, e.g. the columns of an x-slab
+// of the CPML): x-neighbours come from width-G shuffles, every group streams as
+// many rows as the longest task of the warp (a shorter one re-reads its last
+// row and stores nothing past it), and the source and the samples are read
+// from memory, not shuffled, since the groups' rows differ.
+template <int T, bool PML, bool SPL = false, bool WREC = false, bool DSG = true, int G = 32>
 __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const Task& tk,
                                              const Sample2* __restrict__ samps, int parity, long long n0,
                                              const float4* coef_s, float4* stage0, int lane) {
+    static_assert(G == 32 || (G >= 4 && G < 32 && (G & (G - 1)) == 0), "lane groups of 4, 8 or 16 lanes");
     constexpr int PF = pf_of(T, PML);
     constexpr int NSLOT = gen_nslot(PML);
-    constexpr int STAGE_F4 = gen_stage_f4(PML);
+    constexpr int STAGE_F4 = gen_stage_f4(PML, 32 / G);
     constexpr int Q = stages_for(T, PML);
     constexpr bool SD = !PML;   // design coefficients come staged (lite kind)
     const int pitch = S->pitch, nx = S->nx, ny = S->ny;
@@ -130,11 +142,18 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
     const uint8_t* __restrict__ mat = S->mat;
     const float dbx = S->dbx, dby = S->dby;
 
-    const int cx = tk.x0 - HALO + 4 * lane;     // first of this lane's 4 columns
+    const int gl = lane & (G - 1);             // lane within the task's group
+    const int grp = lane / G;                  // the group (0 for whole-warp tasks)
+    const int cx = tk.x0 - HALO + 4 * gl;      // first of this lane's 4 columns
     const int cs = cx + PAD_X;                 // its storage column (>= 4)
-    const bool out_lane = (lane >= HALO / 4) && (lane < 32 - HALO / 4) && (cx < nx);
+    // owned: not a halo lane, inside the grid and before the task's column limit
+    const bool out_lane = (gl >= HALO / 4) && (gl < G - HALO / 4) && (cx < nx) && (tk.xe == 0 || cx < tk.xe) &&
+                          !(tk.flags & TASK_NOSTORE);
     const int s_row = tk.ya - T;               // first row streamed
     const int r_last = tk.yb + T - 1;          // last row streamed
+    // iterations of the row loop: the longest stream of the warp's tasks
+    int n_iter = r_last - s_row + 1;
+    if constexpr (G < 32) n_iter = (int)__reduce_max_sync(0xffffffffu, (unsigned)n_iter);
 
     // CPML: lanes whose columns touch an x-slab carry psi_Ezx / psi_Hyx
     const bool pml = PML && (tk.flags & TASK_PML) != 0;
@@ -181,17 +200,19 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
     const bool has_samp = n_samp > 0;
     Sample2 my_samp;
     my_samp.i = -1; my_samp.j = -1; my_samp.comp = 0; my_samp.slot = 0;
-    if (lane < n_samp) my_samp = samps[tk.samp_begin + lane];
+    if (G == 32 && lane < n_samp) my_samp = samps[tk.samp_begin + lane];
     // source: this launch's T waveform values ride in lanes 0..T-1
     const bool has_src = (tk.flags & TASK_SRC) != 0;
     const int src_j = S->src_j, src_j1 = S->src_j1, src_d = S->src_i - cx;
     const long long src_len = S->src_len;
     float wv = 0.f;
-    if (has_src && lane < T && n0 + lane < src_len) wv = S->src_wave[n0 + lane];
+    if (G == 32 && has_src && lane < T && n0 + lane < src_len) wv = S->src_wave[n0 + lane];
 
 
-    auto issue = [&](int row) {
-        const int q = (row - s_row) % Q;
+    // stage the row of iteration i (past its last row, a group re-reads that row)
+    auto issue = [&](int i) {
+        const int row = G < 32 ? min(s_row + i, r_last) : s_row + i;
+        const int q = i % Q;
         float4* st = stage0 + q * STAGE_F4;
         const size_t g = (size_t)(row + PAD_Y) * pitch + cs;
         cp_async16(st + 0 * 32 + lane, ez_in + g, true);
@@ -209,15 +230,15 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
         if constexpr (SPL) if (pml) {
             // the row's Ca, Cb/dy of E and Da, Db/dy of H, and Ezy
             const bool yrow = srow(row);
-            if (yrow && lane < 4)
-                cp_async4(reinterpret_cast<float*>(st + NSLOT * 32 + 8) + lane, pr.p + 4 * pitch + lane * pr.rows + row + PAD_Y);
+            if (yrow && gl < 4)
+                cp_async4(reinterpret_cast<float*>(st + NSLOT * 32 + 8 + grp) + gl, pr.p + 4 * pitch + gl * pr.rows + row + PAD_Y);
             if (yrow || lane_sx) cp_async16(st + 4 * 32 + lane, psi_in[1] + g, true);
         }
         if constexpr (PML && !SPL) if (pml) {
             const bool yrow = (row < ylo) || (row >= yhi);
             // the row's bEy, cEy, bHy, cHy
-            if (yrow && lane < 4)
-                cp_async4(reinterpret_cast<float*>(st + NSLOT * 32 + 8) + lane, pr.p + 4 * pitch + lane * pr.rows + row + PAD_Y);
+            if (yrow && gl < 4)
+                cp_async4(reinterpret_cast<float*>(st + NSLOT * 32 + 8 + grp) + gl, pr.p + 4 * pitch + gl * pr.rows + row + PAD_Y);
             if (lane_px) {
                 cp_async16(st + 3 * 32 + lane, psi_in[0] + g, true);
                 cp_async16(st + 6 * 32 + lane, psi_in[3] + g, true);
@@ -243,7 +264,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
 
 #pragma unroll
     for (int k = 0; k < PF; k++) {
-        if (s_row + k <= r_last) issue(s_row + k);
+        if (k < n_iter) issue(k);
         cp_commit();
     }
 
@@ -253,7 +274,8 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
     // not unrolled: the general body is large, and instruction fetch, not
     // issue, limits these latency-bound warps
 #pragma unroll 1
-    for (int r = s_row; r <= r_last; ++r) {
+    for (int it = 0; it < n_iter; ++it) {
+        const int r = s_row + it;
         cp_wait<PF - 1>();
         // shift the ring and take row r from its stage
 #pragma unroll
@@ -265,7 +287,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
             M[k] = M[k - 1];
         }
         {
-            const float4* st = stage0 + ((r - s_row) % Q) * STAGE_F4;
+            const float4* st = stage0 + (it % Q) * STAGE_F4;
             E[0] = st[0 * 32 + lane];
             X[0] = st[1 * 32 + lane];
             Y[0] = st[2 * 32 + lane];
@@ -277,10 +299,10 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
             const int a = r - t;
             if (a < s_row) continue;   // warp-uniform
             float4* sta = stage0 + ((a - s_row) % Q) * STAGE_F4;
-            const float* yprof = reinterpret_cast<const float*>(sta + NSLOT * 32 + 8);
+            const float* yprof = reinterpret_cast<const float*>(sta + NSLOT * 32 + 8 + grp);
             // ---- layer 1: H at row a from Ez at level t-1 (rows a, a+1) ----
             const float4 e = E[t], eu = E[t - 1];
-            const float er = __shfl_down_sync(0xffffffffu, e.x, 1);
+            const float er = __shfl_down_sync(0xffffffffu, e.x, 1, G);
             float4 dey = make_float4(eu.x - e.x, eu.y - e.y, eu.z - e.z, eu.w - e.w);
             float4 dex = make_float4(e.y - e.x, e.z - e.y, e.w - e.z, er - e.w);
             if constexpr (PML && !SPL) if (pml) {
@@ -335,7 +357,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
 
             // ---- layer 2: Ez at row a from H at level t (rows a, a-1) ----
             const float4 y = Y[t];
-            const float yl = __shfl_up_sync(0xffffffffu, y.w, 1);
+            const float yl = __shfl_up_sync(0xffffffffu, y.w, 1, G);
             float4 dhy = make_float4(y.x - yl, y.y - y.x, y.z - y.y, y.w - y.z);
             float4 dhx = make_float4(X[t].x - X[t + 1].x, X[t].y - X[t + 1].y, X[t].z - X[t + 1].z,
                                      X[t].w - X[t + 1].w);
@@ -432,8 +454,12 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
 
             const long long n = n0 + (t - 1);   // this level makes E^{n+1}
             if (has_src && a >= src_j && a < src_j1) {
-                const float w = __shfl_sync(0xffffffffu, wv, t - 1);
-                if (src_d >= 0 && src_d < 4 && n < src_len) add4(E[t], src_d, w);
+                if constexpr (G == 32) {
+                    const float w = __shfl_sync(0xffffffffu, wv, t - 1);
+                    if (src_d >= 0 && src_d < 4 && n < src_len) add4(E[t], src_d, w);
+                } else {
+                    if (src_d >= 0 && src_d < 4 && n < src_len) add4(E[t], src_d, S->src_wave[n]);
+                }
             }
             // edge-weight gradients: Ez^{n+1} (after the source), Hx^{n+1/2},
             // Hy^{n+1/2} of the owned cells of the window one cell around the design
@@ -455,8 +481,8 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
                     }
                 }
             }
-            if (has_samp) {
-                const int nq = n_samp < 32 ? n_samp : 32;
+            if (has_samp && a >= tk.ya && a < tk.yb && !(tk.flags & TASK_NOSTORE)) {
+                const int nq = G == 32 ? (n_samp < 32 ? n_samp : 32) : 0;   // groups read their samples from memory
                 for (int q = 0; q < nq; q++) {
                     if (__shfl_sync(0xffffffffu, my_samp.j, q) != a) continue;   // warp-uniform
                     const int d = __shfl_sync(0xffffffffu, my_samp.i, q) - cx;
@@ -465,7 +491,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
                     if (d >= 0 && d < 4)
                         rec[n * n_rec + slot] = comp == 0 ? comp4(E[t], d) : (comp == 1 ? comp4(X[t], d) : comp4(Y[t], d));
                 }
-                for (int q = tk.samp_begin + 32; q < tk.samp_end; q++) {
+                for (int q = tk.samp_begin + (G == 32 ? 32 : 0); q < tk.samp_end; q++) {
                     const Sample2 sp = samps[q];
                     const int d = sp.i - cx;
                     if (sp.j == a && d >= 0 && d < 4)
@@ -476,7 +502,7 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
 
         // ---- row r - T is T steps newer: write it out ----
         const int o = r - T;
-        if (o >= tk.ya) {
+        if (o >= tk.ya && o < tk.yb) {
             const float4* sto = stage0 + ((o - s_row) % Q) * STAGE_F4;
             (void)sto;
             if (out_lane) {
@@ -524,8 +550,8 @@ __device__ __forceinline__ void general_task(const TmzDev* __restrict__ S, const
                 }
             }
         }
-        // the stage of row r - T is free: prefetch row r + PF into it
-        if (r + PF <= r_last) issue(r + PF);
+        // the stage of row r - T is free: prefetch the row of iteration it + PF into it
+        if (it + PF < n_iter) issue(it + PF);
         cp_commit();
     }
     cp_wait<0>();
@@ -558,6 +584,45 @@ __global__ void __launch_bounds__(PML ? 256 : 128, PML ? 1 : 3) k_tmz_fused(cons
     if (tk.scene < 0) return;
     general_task<T, PML, SPL, WREC, DSG>(S, tk, samps, parity, n0, coef_s, smem_f4 + (size_t)wib * Q * STAGE_F4,
                                          lane);
+}
+
+// CPML tasks of one T-step block in one launch: the first nw_blocks CTAs run
+// whole-warp tasks (y-slab segments, sources, probes; the build without design
+// code), the rest run the narrow x-slab tasks, 32 / NG_LANES per warp.  Both
+// lists are padded to whole CTAs of one scene.
+template <int T>
+__global__ void __launch_bounds__(256, 1) k_tmz_cpml_mixed(const TmzDev* __restrict__ scenes,
+                                                          const Task* __restrict__ tasks_w, int nw_blocks,
+                                                          const Task* __restrict__ tasks_n,
+                                                          const Sample2* __restrict__ samps, int parity,
+                                                          long long n0) {
+    constexpr int Q = stages_for(T, true);
+    constexpr int STAGE_W = gen_stage_f4(true), STAGE_N = gen_stage_f4(true, 32 / NG_LANES);
+    extern __shared__ float4 smem_f4[];
+    __shared__ float4 coef_s[256];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int warps = blockDim.x >> 5;
+    const bool narrow = (int)blockIdx.x >= nw_blocks;
+    constexpr int PER_WARP = 32 / NG_LANES;
+    const Task* first = narrow ? tasks_n + (size_t)(blockIdx.x - nw_blocks) * warps * PER_WARP
+                               : tasks_w + (size_t)blockIdx.x * warps;
+    if (first->scene < 0) return;
+    const TmzDev* S = scenes + first->scene;
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) coef_s[k] = S->coef[k];
+    __syncthreads();
+    if (!narrow) {
+        const Task tk = tasks_w[(size_t)blockIdx.x * warps + wib];
+        if (tk.scene < 0) return;
+        general_task<T, true, false, false, false>(S, tk, samps, parity, n0, coef_s,
+                                                   smem_f4 + (size_t)wib * Q * STAGE_W, lane);
+    } else {
+        const Task* tw = first + (size_t)wib * PER_WARP;
+        if (tw[0].scene < 0) return;   // a padding warp (whole warps only)
+        const Task tk = tw[lane / NG_LANES];
+        general_task<T, true, false, false, false, NG_LANES>(S, tk, samps, parity, n0, coef_s,
+                                                             smem_f4 + (size_t)wib * Q * STAGE_N, lane);
+    }
 }
 
 // ===========================================================================
@@ -789,7 +854,7 @@ __global__ void __launch_bounds__(256, 2) k_tmz_interior(const TmzDev* __restric
 
     const int cx = tk.x0 - HALO + 4 * lane;
     const int cs = cx + PAD_X;
-    const bool out_lane = (lane >= HALO / 4) && (lane < 32 - HALO / 4);
+    const bool out_lane = (lane >= HALO / 4) && (lane < 32 - HALO / 4) && (tk.xe == 0 || cx < tk.xe);
     const int s_row = tk.ya - T;
     const int r_last = tk.yb + T - 1;
     float4* stage0 = smem_f4 + (size_t)wib * Q * SF4;
@@ -1052,6 +1117,28 @@ static cudaError_t launch_fused_T(const Task* tasks, int n_tasks, int warps, con
     return cudaGetLastError();
 }
 
+template <int T>
+static cudaError_t launch_cpml_mixed_T(const fdtd_ctx* c, cudaStream_t st, long long n0, int parity) {
+    const int warps = c->warps_b;
+    const size_t smem = tmz_fused_smem(T, warps, 8);   // the larger stage of the two task kinds
+    const int nw = c->n_tasks_b / warps, nn = c->n_tasks_n / (warps * 32 / NG_LANES);
+    cudaError_t e = ensure_dyn_smem((const void*)k_tmz_cpml_mixed<T>, smem);
+    if (e != cudaSuccess) return e;
+    k_tmz_cpml_mixed<T><<<nw + nn, warps * 32, smem, st>>>(c->d_scenes, c->d_tasks_b, nw, c->d_tasks_n, c->d_samp,
+                                                           parity, n0);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_cpml_mixed(const fdtd_ctx* c, cudaStream_t st, int T, long long n0, int parity) {
+    switch (T) {
+        case 1: return launch_cpml_mixed_T<1>(c, st, n0, parity);
+        case 2: return launch_cpml_mixed_T<2>(c, st, n0, parity);
+        case 3: return launch_cpml_mixed_T<3>(c, st, n0, parity);
+        case 4: return launch_cpml_mixed_T<4>(c, st, n0, parity);
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <int V>
 static cudaError_t launch_fused(const Task* tasks, int n_tasks, int warps, const fdtd_ctx* c, cudaStream_t st, int T,
                                 long long n0, int parity) {
@@ -1068,7 +1155,7 @@ static cudaError_t launch_fused(const Task* tasks, int n_tasks, int warps, const
 // on two forked streams, joined before the next block reads the new buffer
 int tmz_fused_launch(fdtd_ctx* c, int T, int warps, long long n0, int parity) {
     cudaError_t e = cudaSuccess;
-    const int nb = c->n_tasks_b + c->n_tasks_s + c->n_tasks_bd, nl = c->n_tasks_l, ni = c->n_tasks;
+    const int nb = c->n_tasks_b + c->n_tasks_s + c->n_tasks_bd + c->n_tasks_n, nl = c->n_tasks_l, ni = c->n_tasks;
     cudaStream_t sb = c->stream, sl = c->stream;
     if ((nb > 0) + (nl > 0) + (ni > 0) > 1) {
         e = cudaEventRecord(c->ev_fork, c->stream);
@@ -1083,7 +1170,12 @@ int tmz_fused_launch(fdtd_ctx* c, int T, int warps, long long n0, int parity) {
     }
     // edge-weight reverse mode: the variants that keep the design window
     const bool wrec = adj_edge_mode(c);
-    if (e == cudaSuccess && c->n_tasks_b > 0) {
+    if (e == cudaSuccess && c->n_tasks_n > 0) {
+        // whole-warp CPML tasks without the design in reach and the narrow x-slab
+        // tasks, in one launch
+        e = launch_cpml_mixed(c, sb, T, n0, parity);
+        c->launches++;
+    } else if (e == cudaSuccess && c->n_tasks_b > 0) {
         // CPML tasks with no design rectangle in reach: the build without design code
         e = launch_fused<7>(c->d_tasks_b, c->n_tasks_b, c->warps_b, c, sb, T, n0, parity);
         c->launches++;
