@@ -311,7 +311,7 @@ int fdtd_sync(fdtd_ctx* ctx);
 
 /* Pick the 2D kernel options for the current scenes (one large scene, or a
  * batch: Sec. V-A runs many simulations of varying size): time every candidate
- * of (kernel 0: T 2..4, segment 16..96 in steps of 8, warps 4 or 8; kernel 2,
+ * of (kernel 0: T 2..4, segment 16..96 in steps of 8, warps 2, 4 or 8; kernel 2,
  * not for a split-field PML: T 2..4, segment 16, 24, 32 or 48) for trial_steps
  * steps, time the four fastest twice more for 4 x trial_steps, keep the best,
  * then for kernel 0 try FDTD_OPT_SEGMENT_B values against the automatic one

@@ -602,8 +602,22 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
                 tasks_n.push_back(t);
             }
         }
-        for (int ya = 0; ya < s->ny; ya += seg) {
-            const int yb = std::min(ya + seg, s->ny);
+        // row segments: the rows within reach of a y-slab of the CPML, [0, y_lo)
+        // and [y_hi, ny), in boundary-task heights, the rows between in
+        // segments of seg rows, so that no segment reaches a slab by a few rows
+        std::vector<std::pair<int, int>> segs;
+        {
+            int y_lo = 0, y_hi = s->ny;
+            if (s->npml > 0) {
+                y_lo = std::min(s->ny, std::max(0, s->npml - s->yoff + MAX_TB));
+                y_hi = std::max(y_lo, std::min(s->ny, s->ny_glob - s->npml - s->yoff - MAX_TB));
+            }
+            for (int y = 0; y < y_lo; y += seg_b) segs.emplace_back(y, std::min(y + seg_b, y_lo));
+            for (int y = y_lo; y < y_hi; y += seg) segs.emplace_back(y, std::min(y + seg, y_hi));
+            for (int y = y_hi; y < s->ny; y += seg_b) segs.emplace_back(y, std::min(y + seg_b, s->ny));
+        }
+        for (const auto& sg : segs) {
+            const int ya = sg.first, yb = sg.second;
             for (int x0 = xl; x0 < (nar ? xr : s->nx); x0 += wout) {
                 bool general;
                 flags_of(x0, ya, yb, &general);
@@ -1501,7 +1515,7 @@ int fdtd_autotune(fdtd_ctx* c, int trial_steps, double* best_ms) {
     // fine-grained: a list that fills whole waves of the 152 SMs wins
     for (int T = 2; T <= MAX_TB; T++)
         for (int seg = 16; seg <= 96; seg += 8)
-            for (int w : {4, 8}) cand.push_back({0, T, seg, w});
+            for (int w : {2, 4, 8}) cand.push_back({0, T, seg, w});
     if (!any_split(c))   // the persistent kernel has no split-field variant
         for (int T = 2; T <= MAX_TB; T++)
             for (int seg : {16, 24, 32, 48}) cand.push_back({2, T, seg, 8});

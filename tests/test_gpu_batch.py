@@ -192,3 +192,72 @@ def test_graph_rerecords_after_design_change():
             assert np.array_equal(a[c], b[c])
     for a, b in zip(got_dft, want_dft):
         assert np.array_equal(a, b)
+
+
+_CFG4_SUBSET = (44, 36, 17, 8)   # the largest scene of the 64-scene batch (2004^2), the two smallest, a 1700^2 one
+
+
+def _oracle_with_peak(s, n, every=50):
+    """The oracle run of scene s for n steps, in chunks, keeping the largest norm
+    each field component reached (sampled every `every` steps): by the last step
+    of a long run most of the wave has left through the CPML, and the relative
+    L2 error is then taken against max(|x|, 1e-3 max_n |x^n|)."""
+    import oracle
+    sim = oracle.TMz(s, nsteps_src=n)
+    peak = {c: 0.0 for c in ("ez", "hx", "hy")}
+    probe = (s.nx // 3, s.ny // 2)
+    series = []
+    done = 0
+    while done < n:
+        k = min(every, n - done)
+        series.append(sim.run(k, samples=[(probe[0], probe[1], "ez")])["samples"])
+        done += k
+        for c in peak:
+            peak[c] = max(peak[c], float(np.linalg.norm(sim.state[c])))
+    out = {c: sim.state[c].copy() for c in ("ez", "hx", "hy")}
+    out["probes"] = np.concatenate(series)
+    out["peak"] = peak
+    return out
+
+
+@pytest.fixture(scope="module")
+def cfg4_subset():
+    """Four scenes of the 64-scene batch workload (sides log-uniform 256..2048,
+    CPML 12, 2000 steps) and their full-length FP64 oracle runs."""
+    allsc = scenes.batch_scenes()
+    scs = [allsc[k] for k in _CFG4_SUBSET]
+    refs = [_oracle_with_peak(s, s.nsteps) for s in scs]
+    return scs, refs
+
+
+@pytest.mark.parametrize("kernel,tblock,segment,warps", [(0, 4, 48, 4), (2, 4, 32, 8)])
+def test_batch_workload_scenes_at_full_length(cfg4_subset, kernel, tblock, segment, warps):
+    """The batch workload's scenes at its full 2000 steps, in one context as the
+    benchmark runs them: the per-block kernels (the options the autotuner
+    picks) and the single persistent launch, each replayed from a CUDA graph,
+    against the oracle scene by scene."""
+    from paper_2405_00814_gb300 import fdtd
+    scs, refs = cfg4_subset
+    sim = fdtd.Simulation.batch(scs)
+    pids = []
+    for k, s in enumerate(scs):
+        sim.select(k)
+        sim.set_scene_source(s.source)
+        pids.append(sim.add_probe(s.nx // 3, s.ny // 2))
+    sim.set_option("kernel", kernel)
+    sim.set_option("tblock", tblock)
+    sim.set_option("segment", segment)
+    sim.set_option("warps", warps)
+    sim.set_option("graph", 1)
+    n = scs[0].nsteps
+    sim.step(n)                 # records the graph and runs it
+    sim.reset()
+    sim.step(n)                 # replays it
+    sim.sync()
+    for k, (s, o) in enumerate(zip(scs, refs)):
+        sim.select(k)
+        for c in ("ez", "hx", "hy"):
+            e = rel_l2(sim.get_field(c, (s.ny, s.nx)), o[c], floor=1e-3 * o["peak"][c])
+            assert e <= TOL_FIELD, (s.nx, c, e)
+        assert rel_l2(sim.read_probe(pids[k], n), o["probes"][:, 0]) <= TOL_FIELD
+    sim.close()
