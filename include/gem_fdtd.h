@@ -81,8 +81,10 @@ extern "C" {
 #define FDTD_OPT_KERNEL 0    /* 2D: 0 = fused temporally blocked stream, two kernels per T-step block (default);
                                 1 = one H and one E launch per step;
                                 2 = persistent: one cooperative launch runs many T-step blocks of every scene,
-                                    warps pulling tasks from a shared counter, a bounded grid barrier between blocks
-                                    (a context with a split-field PML steps with the unfused pair instead).
+                                    warps pulling (block, work item) pairs in order from a shared counter; an item
+                                    waits (bounded) only for the items of the previous block whose regions meet its
+                                    own, so there is no barrier between blocks (a context with a split-field PML
+                                    steps with the unfused pair instead).
                                 3D: 0 = fused z-marching kernel (default), 1 = one H and one E launch per step */
 #define FDTD_OPT_TBLOCK 1    /* time steps per HBM pass of the fused kernel, 1..4 */
 #define FDTD_OPT_SEGMENT 2   /* 2D: rows per warp task of the fused kernel (multiple of 8, >= 8);
@@ -90,11 +92,14 @@ extern "C" {
 #define FDTD_OPT_WARPS 3     /* warps per CTA of the fused kernel, 1..8 */
 #define FDTD_OPT_GRAPH 4     /* 1: fdtd_step records its launches into a CUDA graph and replays it when called
                                 again with the same start step, step count and buffer parity (e.g. after fdtd_reset) */
-#define FDTD_OPT_SPIN_LIMIT 5     /* polls (about 0.25 us each) a persistent-kernel barrier wait makes before it gives up */
-#define FDTD_OPT_DEBUG_SKIP_CTA 6 /* test hook: in the next persistent launch only, this CTA never arrives at the
-                                     barrier, so the others' waits run out (-1 = off; reset to -1 by that launch);
-                                     fdtd_sync then returns FDTD_ETIMEOUT.  The timeout is sticky: later persistent
-                                     launches return without stepping until fdtd_sync has reported it */
+#define FDTD_OPT_SPIN_LIMIT 5     /* polls (about 0.1 us each) a persistent-kernel wait for another work item makes
+                                     before it gives up */
+#define FDTD_OPT_DEBUG_STALL_ITEM 6 /* test hook: in the next persistent launch only, the work item of this index
+                                       (0 <= v < the launch's items per block) never reports its first block done, so
+                                       the items that wait on it give up after FDTD_OPT_SPIN_LIMIT polls (-1 = off; reset
+                                       to -1 by that launch); fdtd_sync then returns FDTD_ETIMEOUT.  The timeout is
+                                       sticky: later persistent launches return without stepping until fdtd_sync has
+                                       reported it */
 #define FDTD_OPT_ADJ_STORE 7 /* reverse mode, read by fdtd_set_checkpointing: 1 (default) = the forward pass keeps
                                 E^{n+1} - E^n over every design rectangle for every step in device memory
                                 (steps x design cells x 4 B) and fdtd_adjoint_grad needs no recompute;
@@ -109,6 +114,8 @@ extern "C" {
                                   passes a multiple of N (at the end of that T-step block; one extra launch over
                                   Ez, Hx, Hy), into a sticky device flag that fdtd_sync reports as FDTD_EUNSTABLE
                                   -- a blow-up found without synchronising the time loop; 0 (default) = off */
+#define FDTD_OPT_CLUSTER 10  /* 3D fused kernel: 1 (default) plain launch; 2, 4 or 8 = thread-block clusters of that many
+                                y-adjacent tiles, scheduled together on one GPC */
 
 typedef struct fdtd_ctx fdtd_ctx;
 
@@ -302,7 +309,7 @@ int fdtd_save_state(fdtd_ctx* ctx, void* buf, size_t* bytes);
 int fdtd_load_state(fdtd_ctx* ctx, const void* buf, size_t bytes);
 
 /* Wait for the context's stream.  Returns FDTD_ETIMEOUT if a bounded device
- * wait (the persistent kernel's grid barrier) gave up since the last call: the
+ * wait (the persistent kernel's wait for another work item) gave up since the last call: the
  * kernel then stopped early, the context stays usable, and the fields hold the
  * state of an incomplete step sequence.  Otherwise returns FDTD_EUNSTABLE if the
  * periodic finite check (FDTD_OPT_CHECK_EVERY) found a non-finite value since

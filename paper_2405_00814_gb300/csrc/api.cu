@@ -386,10 +386,10 @@ fdtd_ctx* ctx_new(void* stream) {
     c->task_tb = c->task_seg = -1;
     c->graph = nullptr;
     c->adj = nullptr;
-    c->d_tasks_all = nullptr;
+    c->d_ptasks = nullptr; c->d_pitems = nullptr; c->d_dep_off = nullptr; c->d_dep_idx = nullptr; c->d_done = nullptr;
     c->d_dft = nullptr;
     c->n_dft = 0;
-    c->n_tasks_all = 0;
+    c->n_pitems = 0;
     c->d_ctl = nullptr;
     c->ctl_words = 0;
     c->h_err = nullptr;
@@ -399,7 +399,7 @@ fdtd_ctx* ctx_new(void* stream) {
     } else {
         *c->h_err = 0;
     }
-    c->spin_limit = 4000000;   // about one second of 256 ns polls
+    c->spin_limit = 4000000;   // about half a second of polls
     c->opt_debug_skip = -1;
     c->opt_adj_store = 1;
     c->opt_check_every = 0;
@@ -510,7 +510,7 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     std::vector<Task> tasks, tasks_b, tasks_l, tasks_s, tasks_bd, tasks_n;
     std::vector<Sample2> tsamp;
     const int warps_b = 2;
-    const bool want_narrow = c->opt_kernel == 0;   // the persistent kernel takes whole-warp tasks only
+    const bool want_narrow = c->opt_kernel == 0 || c->opt_kernel == 2;   // not the unfused pair
     bool any_design = false;
     for (const Scene2* s : c->s2) any_design = any_design || s->d_dsg != nullptr;
     const int warps_l = 4;   // lite CTAs; each list is padded to its launch's CTA width
@@ -676,18 +676,78 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
         for (const Sample2& sp : c->s2[k]->samples) ssamp.push_back(sp);
         soff[k + 1] = (int)ssamp.size();
     }
-    // the persistent kernel takes every task from one list, heavy ones first
-    std::vector<Task> all;
-    for (const Task& t : tasks_b)
-        if (t.scene >= 0) all.push_back(t);
-    for (const Task& t : tasks_bd)
-        if (t.scene >= 0) all.push_back(t);
-    for (const Task& t : tasks_l)
-        if (t.scene >= 0) all.push_back(t);
-    for (const Task& t : tasks)
-        if (t.scene >= 0) all.push_back(t);
+    // the persistent kernel's items, the long chains first: narrow groups, general
+    // tasks, interior tasks; each waits for the items of the previous block
+    // whose regions meet its own
+    std::vector<Task> ptasks;
+    std::vector<int2> pitems;
+    const int per_warp_n = 32 / NG_LANES;
+    for (size_t q = 0; q + per_warp_n <= tasks_n.size(); q += per_warp_n) {
+        if (tasks_n[q].scene < 0) continue;
+        pitems.push_back(make_int2(PITEM_NARROW, (int)ptasks.size()));
+        for (int g = 0; g < per_warp_n; g++) ptasks.push_back(tasks_n[q + g]);
+    }
+    for (const std::vector<Task>* L : {&tasks_b, &tasks_bd, &tasks_l, &tasks})
+        for (const Task& t : *L) {
+            if (t.scene < 0) continue;
+            pitems.push_back(make_int2(L == &tasks ? PITEM_INTERIOR : PITEM_GENERAL, (int)ptasks.size()));
+            ptasks.push_back(t);
+        }
+    std::vector<int> dep_off(pitems.size() + 1, 0), dep_idx;
+    {
+        // a task reads columns [x0 - HALO, x0 - HALO + 4 lanes) and rows
+        // [ya - MAX_TB, yb + MAX_TB); it owns [x0, xe) x [ya, yb) (nothing for a
+        // lane-group filler copy).  Two items depend on each other when one's
+        // read box meets the other's owned box.
+        struct Box { int scene, item, rx0, rx1, ry0, ry1, ox0, ox1, oy0, oy1; };
+        std::vector<Box> bx;
+        for (size_t i = 0; i < pitems.size(); i++) {
+            const int n = pitems[i].x == PITEM_NARROW ? per_warp_n : 1;
+            const int lanes = pitems[i].x == PITEM_NARROW ? NG_LANES : 32;
+            for (int g = 0; g < n; g++) {
+                const Task& t = ptasks[(size_t)pitems[i].y + g];
+                const Scene2* s = c->s2[t.scene];
+                Box b;
+                b.scene = t.scene; b.item = (int)i;
+                b.rx0 = t.x0 - HALO; b.rx1 = t.x0 - HALO + 4 * lanes;
+                b.ry0 = t.ya - MAX_TB; b.ry1 = t.yb + MAX_TB;
+                b.ox0 = t.x0;
+                b.ox1 = std::min(s->nx, t.xe > 0 ? t.xe : t.x0 + 4 * (lanes - 2));
+                b.oy0 = t.ya; b.oy1 = t.yb;
+                if (t.flags & TASK_NOSTORE) b.ox1 = b.ox0;   // owns nothing
+                bx.push_back(b);
+            }
+        }
+        // boxes by (scene, first read column): a box can only meet boxes whose
+        // columns start within one strip of its own
+        std::map<std::pair<int, int>, std::vector<int>> by_col;
+        for (size_t q = 0; q < bx.size(); q++) by_col[{bx[q].scene, bx[q].rx0}].push_back((int)q);
+        auto meets = [](int a0, int a1, int b0, int b1) { return a0 < b1 && b0 < a1; };
+        std::vector<std::vector<int>> deps(pitems.size());
+        for (const Box& a : bx) {
+            auto lo = by_col.lower_bound({a.scene, a.rx0 - STRIP});
+            auto hi = by_col.upper_bound({a.scene, a.rx1});
+            for (auto itr = lo; itr != hi; ++itr)
+                for (int q : itr->second) {
+                    const Box& b = bx[q];
+                    if ((meets(a.rx0, a.rx1, b.ox0, b.ox1) && meets(a.ry0, a.ry1, b.oy0, b.oy1)) ||
+                        (meets(a.ox0, a.ox1, b.rx0, b.rx1) && meets(a.oy0, a.oy1, b.ry0, b.ry1)))
+                        deps[a.item].push_back(b.item);
+                }
+        }
+        for (size_t i = 0; i < pitems.size(); i++) {
+            std::vector<int>& d = deps[i];
+            d.push_back((int)i);   // its own previous block
+            std::sort(d.begin(), d.end());
+            d.erase(std::unique(d.begin(), d.end()), d.end());
+            dep_idx.insert(dep_idx.end(), d.begin(), d.end());
+            dep_off[i + 1] = (int)dep_idx.size();
+        }
+    }
     dfree(c->d_scenes); dfree(c->d_tasks); dfree(c->d_tasks_b); dfree(c->d_samp); dfree(c->d_samp_scene); dfree(c->d_samp_off);
-    dfree(c->d_tasks_all);
+    dfree(c->d_ptasks); dfree(c->d_pitems); dfree(c->d_dep_off); dfree(c->d_dep_idx); dfree(c->d_done);
+    c->d_ptasks = nullptr; c->d_pitems = nullptr; c->d_dep_off = nullptr; c->d_dep_idx = nullptr; c->d_done = nullptr;
+    c->n_pitems = 0;
     dfree(c->d_tasks_l);
     dfree(c->d_tasks_s);
     dfree(c->d_tasks_bd);
@@ -700,14 +760,18 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     c->d_dft = nullptr;
     c->n_dft = 0;
     c->d_scenes = nullptr; c->d_tasks = nullptr; c->d_tasks_b = nullptr; c->d_samp = nullptr; c->d_samp_scene = nullptr;
-    c->d_samp_off = nullptr; c->d_tasks_all = nullptr;
+    c->d_samp_off = nullptr;
     adj_patch_descriptors(c, dev.data());   // the design history being recorded, if any
     c->h_scenes = dev;
     int rc;
     if ((rc = dalloc(c, &c->d_scenes, dev.size() * sizeof(TmzDev), "scene descriptors"))) return rc;
     if ((rc = dalloc(c, &c->d_tasks, tasks.size() * sizeof(Task), "tasks"))) return rc;
     if ((rc = dalloc(c, &c->d_tasks_b, tasks_b.size() * sizeof(Task), "tasks"))) return rc;
-    if ((rc = dalloc(c, &c->d_tasks_all, all.size() * sizeof(Task), "tasks"))) return rc;
+    if ((rc = dalloc(c, &c->d_ptasks, ptasks.size() * sizeof(Task), "persistent tasks"))) return rc;
+    if ((rc = dalloc(c, &c->d_pitems, pitems.size() * sizeof(int2), "persistent items"))) return rc;
+    if ((rc = dalloc(c, &c->d_dep_off, dep_off.size() * sizeof(int), "persistent dependencies"))) return rc;
+    if ((rc = dalloc(c, &c->d_dep_idx, dep_idx.size() * sizeof(int), "persistent dependencies"))) return rc;
+    if ((rc = dalloc(c, &c->d_done, pitems.size() * sizeof(unsigned), "persistent completion counts"))) return rc;
     if ((rc = dalloc(c, &c->d_tasks_l, tasks_l.size() * sizeof(Task), "tasks"))) return rc;
     if ((rc = dalloc(c, &c->d_tasks_s, tasks_s.size() * sizeof(Task), "tasks"))) return rc;
     if ((rc = dalloc(c, &c->d_tasks_bd, tasks_bd.size() * sizeof(Task), "tasks"))) return rc;
@@ -720,8 +784,12 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
         CK(cudaMemcpyAsync(c->d_tasks, tasks.data(), tasks.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
     if (!tasks_b.empty())
         CK(cudaMemcpyAsync(c->d_tasks_b, tasks_b.data(), tasks_b.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
-    if (!all.empty())
-        CK(cudaMemcpyAsync(c->d_tasks_all, all.data(), all.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
+    if (!ptasks.empty()) {
+        CK(cudaMemcpyAsync(c->d_ptasks, ptasks.data(), ptasks.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
+        CK(cudaMemcpyAsync(c->d_pitems, pitems.data(), pitems.size() * sizeof(int2), cudaMemcpyHostToDevice, c->stream), "upload");
+        CK(cudaMemcpyAsync(c->d_dep_idx, dep_idx.data(), dep_idx.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream), "upload");
+    }
+    CK(cudaMemcpyAsync(c->d_dep_off, dep_off.data(), dep_off.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream), "upload");
     if (!tasks_l.empty())
         CK(cudaMemcpyAsync(c->d_tasks_l, tasks_l.data(), tasks_l.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream), "upload");
     if (!tasks_s.empty())
@@ -764,7 +832,7 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     c->n_dft = (int)items.size();
     c->n_tasks = (int)tasks.size();
     c->n_tasks_b = (int)tasks_b.size();
-    c->n_tasks_all = (int)all.size();
+    c->n_pitems = (int)pitems.size();
     c->n_tasks_l = (int)tasks_l.size();
     c->n_tasks_s = (int)tasks_s.size();
     c->n_tasks_bd = (int)tasks_bd.size();
@@ -807,7 +875,7 @@ int step_prepare(fdtd_ctx* c, int64_t n_steps) {
     if (c->s2.empty()) return fail(c, FDTD_ESTATE, "no scene");
     int rc = ensure_capacity(c, c->t + n_steps);
     if (rc) return rc;
-    if (c->dirty || c->task_seg != c->opt_segment || c->task_narrow != (c->opt_kernel == 0 ? 1 : 0)) {
+    if (c->dirty || c->task_seg != c->opt_segment || c->task_narrow != (c->opt_kernel != 1 ? 1 : 0)) {
         rc = rebuild(c, c->opt_tblock, c->opt_segment, c->opt_warps);
         if (rc) return rc;
     }
@@ -995,7 +1063,7 @@ void fdtd_destroy(fdtd_ctx* c) {
     adj_free(c);
     dfree(c->d_scenes); dfree(c->d_tasks); dfree(c->d_tasks_b); dfree(c->d_samp); dfree(c->d_samp_scene);
     dfree(c->d_samp_off);
-    dfree(c->d_tasks_all);
+    dfree(c->d_ptasks); dfree(c->d_pitems); dfree(c->d_dep_off); dfree(c->d_dep_idx); dfree(c->d_done);
     dfree(c->d_dft);
     dfree(c->d_ctl);
     if (c->h_err) cudaFreeHost(c->h_err);
@@ -1032,8 +1100,8 @@ int fdtd_set_option(fdtd_ctx* c, int option, int64_t v) {
             if (v < 1) return fail(c, FDTD_EINVAL, "spin limit must be >= 1");
             c->spin_limit = v;
             return FDTD_OK;
-        case FDTD_OPT_DEBUG_SKIP_CTA:
-            if (v < -1 || v > (1 << 20)) return fail(c, FDTD_EINVAL, "debug CTA index out of range");
+        case FDTD_OPT_DEBUG_STALL_ITEM:
+            if (v < -1 || v > (1 << 20)) return fail(c, FDTD_EINVAL, "debug item index out of range");
             c->opt_debug_skip = (int)v;
             return FDTD_OK;
         case FDTD_OPT_ADJ_STORE:
@@ -1050,6 +1118,11 @@ int fdtd_set_option(fdtd_ctx* c, int option, int64_t v) {
                 return fail(c, FDTD_EINVAL, "segment %lld: 2D needs a multiple of 8 >= 8, 3D >= 1", (long long)v);
             c->opt_segment = (int)v;
             c->dirty = true;
+            return FDTD_OK;
+        case FDTD_OPT_CLUSTER:
+            if (c->dims != 3) return fail(c, FDTD_EINVAL, "thread-block clusters apply to the 3D fused kernel");
+            if (v != 1 && v != 2 && v != 4 && v != 8) return fail(c, FDTD_EINVAL, "cluster size %lld: 1, 2, 4 or 8", (long long)v);
+            c->opt_cluster = (int)v;
             return FDTD_OK;
         case FDTD_OPT_CHECK_EVERY:
             if (c->dims != 2) return fail(c, FDTD_EINVAL, "the periodic finite check covers 2D contexts");
@@ -1090,10 +1163,11 @@ int64_t fdtd_get_option(const fdtd_ctx* c, int option) {
         case FDTD_OPT_WARPS: return c->opt_warps;
         case FDTD_OPT_GRAPH: return c->opt_graph;
         case FDTD_OPT_SPIN_LIMIT: return c->spin_limit;
-        case FDTD_OPT_DEBUG_SKIP_CTA: return c->opt_debug_skip;
+        case FDTD_OPT_DEBUG_STALL_ITEM: return c->opt_debug_skip;
         case FDTD_OPT_ADJ_STORE: return c->opt_adj_store;
         case FDTD_OPT_SEGMENT_B: return c->opt_segment_b;
         case FDTD_OPT_CHECK_EVERY: return c->opt_check_every;
+        case FDTD_OPT_CLUSTER: return c->opt_cluster;
     }
     return -1;
 }
@@ -1489,7 +1563,7 @@ int fdtd_sync(fdtd_ctx* c) {
         *c->h_err = 0;
         if (c->h_bad) *c->h_bad = 0;   // fields of a cut-short run: a timeout is the first thing to report
         if (c->d_bad) CK(cudaMemset(c->d_bad, 0, sizeof(int)), "clear the finite-check flag");
-        return fail(c, FDTD_ETIMEOUT, "a grid-barrier wait of the persistent kernel gave up (spin limit %lld)",
+        return fail(c, FDTD_ETIMEOUT, "a wait of the persistent kernel for another work item gave up (spin limit %lld)",
                     (long long)c->spin_limit);
     }
     if (c->h_bad && *c->h_bad) {

@@ -108,6 +108,8 @@ enum { TASK_PML = 1, TASK_SRC = 2, TASK_DSG = 4, TASK_NOSTORE = 8 };
 // MAX_TB cells deep, so that no interior strip computes a CPML cell it owns)
 constexpr int NG_LANES = 8;
 constexpr int NG_OWN = (NG_LANES - 2) * 4;
+// kinds of persistent-kernel items
+enum { PITEM_INTERIOR = 0, PITEM_GENERAL = 1, PITEM_NARROW = 2 };
 
 // ---------------------------------------------------------------------------
 // host side
@@ -217,19 +219,26 @@ struct fdtd_ctx {
     void* graph;
     // reverse mode (k_adjoint.cu): checkpoints of the forward run
     void* adj;
-    // persistent kernel: all tasks in one list (general tasks first), control words
-    gem::Task* d_tasks_all;
+    // persistent kernel: the items of one T-step block (an interior task, a
+    // general task, or four narrow tasks: (kind, first task in d_ptasks)), the
+    // items each must wait for (CSR), their completion counts, control words
+    gem::Task* d_ptasks;
+    int2* d_pitems;
+    int* d_dep_off;
+    int* d_dep_idx;
+    unsigned* d_done;
+    int n_pitems;
     gem::DftItem* d_dft;           // every 2D cell-monitor accumulator
     std::vector<gem::TmzDev> h_scenes;   // host copy of d_scenes
     int n_dft;
-    int n_tasks_all;
     unsigned* d_ctl;
     int ctl_words;
     int* h_err;                  // pinned: copy of the sticky error word ctl[2] (cleared by fdtd_sync)
-    long long spin_limit;        // barrier polls before a CTA gives up
-    int opt_debug_skip;          // CTA that skips its barrier arrivals (-1 none)
+    long long spin_limit;        // polls a persistent-kernel wait makes before it gives up
+    int opt_debug_skip;          // work item that never reports its first block done (-1 none)
     int opt_adj_store;           // FDTD_OPT_ADJ_STORE
     int opt_check_every;         // FDTD_OPT_CHECK_EVERY (0: off)
+    int opt_cluster;             // FDTD_OPT_CLUSTER (3D: y tiles per thread-block cluster)
     int* d_bad;                  // sticky device word of the periodic finite check
     int* h_bad;                  // pinned copy of it (cleared by fdtd_sync)
     // CUDA graph of a step sequence

@@ -626,149 +626,6 @@ __global__ void __launch_bounds__(256, 1) k_tmz_cpml_mixed(const TmzDev* __restr
 }
 
 // ===========================================================================
-// persistent kernel: one cooperative launch advances every scene of a batch
-// by n_blocks * T steps.  Warps pull (scene, strip, segment) tasks of all scenes
-// from a per-block work counter, so uneven scene sizes balance themselves; a
-// grid-wide barrier separates T-step blocks (each block reads buffer p and
-// writes 1 - p).  Every wait is bounded: after spin_limit polls a CTA sets the
-// error flag and returns, and the others stop waiting when they see the flag.
-//
-// ctl layout (unsigned): [0] arrivals, [1] generation, [2] error flag,
-// [3] unused, [4 + b] work counter of block b.  skip_cta >= 0 names a CTA
-// that never arrives (a test of the timeout path); -1 in normal runs.
-// ===========================================================================
-__device__ __forceinline__ bool grid_barrier(unsigned* ctl, long long spin_limit, int skip_cta) {
-    __shared__ int ok_s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned* vgen = ctl + 1;
-        volatile int* verr = reinterpret_cast<volatile int*>(ctl + 2);
-        const unsigned gen = *vgen;
-        __threadfence();
-        bool ok = true;
-        const bool skip = skip_cta == (int)blockIdx.x;
-        const unsigned arrived = skip ? 0u : atomicAdd(ctl, 1u) + 1u;
-        if (!skip && arrived == gridDim.x) {
-            ctl[0] = 0;
-            __threadfence();
-            atomicAdd(ctl + 1, 1u);
-        } else {
-            long long it = 0;
-            while (*vgen == gen) {
-                if (*verr || ++it > spin_limit) {
-                    atomicExch(reinterpret_cast<int*>(ctl + 2), 1);
-                    ok = false;
-                    break;
-                }
-                __nanosleep(256);
-            }
-        }
-        __threadfence();
-        ok_s = ok && !*verr;
-    }
-    __syncthreads();
-    return ok_s != 0;
-}
-
-template <int T, bool WREC>
-__global__ void __launch_bounds__(256, 1) k_tmz_persistent(const TmzDev* __restrict__ scenes,
-                                                          const Task* __restrict__ tasks, int n_tasks,
-                                                          const Sample2* __restrict__ samps, int parity0,
-                                                          long long n0, int n_blocks, unsigned* ctl,
-                                                          long long spin_limit, int skip_cta) {
-    constexpr int STAGE_F4 = gen_stage_f4(true);
-    constexpr int Q = stages_for(T, true);
-    extern __shared__ float4 smem_f4[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    float4* stage0 = smem_f4 + (size_t)wib * Q * STAGE_F4;
-    // an earlier launch of this context timed out and nobody has read the flag yet
-    if (*reinterpret_cast<volatile int*>(ctl + 2)) return;
-    for (int b = 0; b < n_blocks; b++) {
-        const int parity = parity0 ^ (b & 1);
-        const long long nb = n0 + (long long)b * T;
-        for (;;) {
-            int idx = 0;
-            if (lane == 0) idx = (int)atomicAdd(ctl + 4 + b, 1u);
-            idx = __shfl_sync(0xffffffffu, idx, 0);
-            if (idx >= n_tasks) break;
-            const Task tk = tasks[idx];
-            if (tk.scene >= 0) {
-                const TmzDev* S = scenes + tk.scene;
-                general_task<T, true, false, WREC>(S, tk, samps, parity, nb, S->coef, stage0, lane);
-            }
-        }
-        if (!grid_barrier(ctl, spin_limit, skip_cta)) return;
-    }
-}
-
-template <int T, bool WREC>
-static cudaError_t launch_persistent_T(const fdtd_ctx* c, cudaStream_t st, int parity, long long n0, int n_blocks,
-                                       long long spin_limit, int* grid_out) {
-    const int warps = 8;
-    const size_t smem = tmz_fused_smem(T, warps, 1);
-    cudaError_t e = ensure_dyn_smem((const void*)k_tmz_persistent<T, WREC>, smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0, dev = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tmz_persistent<T, WREC>, warps * 32, smem);
-    if (e != cudaSuccess) return e;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int grid = per_sm * sms;
-    *grid_out = grid;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(warps * 32);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_tmz_persistent<T, WREC>, (const TmzDev*)c->d_scenes, (const Task*)c->d_tasks_all,
-                              c->n_tasks_all, (const Sample2*)c->d_samp, parity, n0, n_blocks, c->d_ctl, spin_limit,
-                              c->opt_debug_skip);
-}
-
-// n_blocks T-step blocks in one cooperative launch.  The arrival, generation and
-// work-counter words are zeroed first; the error word ctl[2] is not: it stays set
-// from a timed-out launch until fdtd_sync reports it, so a later launch of the
-// same step call neither advances the fields nor overwrites the flag.
-int tmz_persistent_launch(fdtd_ctx* c, int T, long long n0, int n_blocks, int parity) {
-    cudaError_t e = cudaMemsetAsync(c->d_ctl, 0, 2 * sizeof(unsigned), c->stream);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(c->d_ctl + 3, 0, (size_t)(1 + n_blocks) * sizeof(unsigned), c->stream);
-    int grid = 0;
-    const bool wrec = adj_edge_mode(c);   // edge-weight reverse mode: keep the design window
-    if (e == cudaSuccess) {
-        switch (T) {
-            case 1: e = wrec ? launch_persistent_T<1, true>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid)
-                             : launch_persistent_T<1, false>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid);
-                break;
-            case 2: e = wrec ? launch_persistent_T<2, true>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid)
-                             : launch_persistent_T<2, false>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid);
-                break;
-            case 3: e = wrec ? launch_persistent_T<3, true>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid)
-                             : launch_persistent_T<3, false>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid);
-                break;
-            default: e = wrec ? launch_persistent_T<4, true>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid)
-                              : launch_persistent_T<4, false>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid);
-                break;
-        }
-    }
-    c->launches++;
-    c->opt_debug_skip = -1;   // the test hook covers one launch
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_err, c->d_ctl + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
-    if (e != cudaSuccess) {
-        c->err = std::string("persistent launch: ") + cudaGetErrorString(e);
-        return FDTD_ECUDA;
-    }
-    return FDTD_OK;
-}
-
-// ===========================================================================
 // interior kernel: tasks with no CPML slab, design rectangle, source or probe in
 // reach and all 120 output columns inside the grid (every other task runs the
 // general kernel above).  Same wavefront; the steady-state loop body has no
@@ -820,28 +677,16 @@ __device__ __forceinline__ void level(Ring<T>& R, int t, float dbx, float dby, c
     R.E[t].w = e_upd(e.w, y.w - y.z, R.X[t].w - R.X[t + 1].w, c3);
 }
 
+// One warp's interior task: T levels of the wavefront over the strip's rows,
+// no boundary work.  coef_s is the scene's coefficient table (shared or global
+// memory), stage0 the warp's Q_I x stage_f4(false) float4 staging area.
 template <int T>
-__global__ void __launch_bounds__(256, 2) k_tmz_interior(const TmzDev* __restrict__ scenes,
-                                                        const Task* __restrict__ tasks, int n_tasks,
-                                                        int parity) {
+__device__ __forceinline__ void interior_task(const TmzDev* __restrict__ S, const Task& tk, int parity,
+                                              const float4* coef_s, float4* stage0, int lane) {
     constexpr int PF = pf_of(T, false);
     constexpr int SF4 = stage_f4(false);
     constexpr int Q = stages_for(T, false);
     static_assert((Q & (Q - 1)) == 0, "interior stage count must be a power of two");
-    extern __shared__ float4 smem_f4[];
-    __shared__ float4 coef_s[256];
-
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int warps = blockDim.x >> 5;
-    const int tid = blockIdx.x * warps + wib;
-    const TmzDev* S = scenes + tasks[blockIdx.x * warps].scene;
-    for (int k = threadIdx.x; k < 256; k += blockDim.x) coef_s[k] = S->coef[k];
-    __syncthreads();
-    if (tid >= n_tasks) return;
-    const Task tk = tasks[tid];
-    if (tk.scene < 0) return;
-
     const int pitch = S->pitch;
     const float* __restrict__ ez_in = S->f[F_EZ][parity];
     const float* __restrict__ hx_in = S->f[F_HX][parity];
@@ -857,7 +702,6 @@ __global__ void __launch_bounds__(256, 2) k_tmz_interior(const TmzDev* __restric
     const bool out_lane = (lane >= HALO / 4) && (lane < 32 - HALO / 4) && (tk.xe == 0 || cx < tk.xe);
     const int s_row = tk.ya - T;
     const int r_last = tk.yb + T - 1;
-    float4* stage0 = smem_f4 + (size_t)wib * Q * SF4;
     // rows past r_last are still inside the pad rows: the prefetch never needs a guard
     auto issue = [&](int row) {
         float4* st = stage0 + ((row - s_row) & (Q - 1)) * SF4;
@@ -904,6 +748,194 @@ __global__ void __launch_bounds__(256, 2) k_tmz_interior(const TmzDev* __restric
         cp_commit();
     }
     cp_wait<0>();
+}
+
+
+template <int T>
+__global__ void __launch_bounds__(256, 2) k_tmz_interior(const TmzDev* __restrict__ scenes,
+                                                        const Task* __restrict__ tasks, int n_tasks,
+                                                        int parity) {
+    constexpr int SF4 = stage_f4(false);
+    constexpr int Q = stages_for(T, false);
+    extern __shared__ float4 smem_f4[];
+    __shared__ float4 coef_s[256];
+
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int warps = blockDim.x >> 5;
+    const int tid = blockIdx.x * warps + wib;
+    const TmzDev* S = scenes + tasks[blockIdx.x * warps].scene;
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) coef_s[k] = S->coef[k];
+    __syncthreads();
+    if (tid >= n_tasks) return;
+    const Task tk = tasks[tid];
+    if (tk.scene < 0) return;
+    interior_task<T>(S, tk, parity, coef_s, smem_f4 + (size_t)wib * Q * SF4, lane);
+}
+
+// ===========================================================================
+// persistent kernel: one cooperative launch advances every scene of a batch
+// by n_blocks * T steps.  The work is a list of items per T-step block -- an
+// interior task, a whole-warp general task (CPML, design, source, probes) or
+// four narrow x-slab tasks -- and warps pull (block, item) pairs in order from
+// one counter, so uneven scene sizes balance themselves.  There is no barrier
+// between blocks: an item of block b waits only until every item whose region
+// it reads or overwrites (its neighbours, itself included) has finished block
+// b - 1, as counted in done[] (block b reads buffer p and writes 1 - p, so these
+// are the only items whose data it touches).  Items are claimed in order and
+// wait only on items of the previous block, which were claimed earlier by
+// resident warps, so the lowest unfinished block always progresses.  Every
+// wait is bounded: after spin_limit polls the warp sets the error flag and
+// returns, and the others stop waiting when they see it.
+//
+// ctl layout (unsigned): [0] next (block, item) index, [2] error flag (kept by
+// the host until fdtd_sync reports it).  stall_item >= 0 names an item that never
+// reports block 0 done (a test of the timeout path); -1 in normal runs.
+// ===========================================================================
+template <int T, bool WREC>
+__global__ void __launch_bounds__(256, 1) k_tmz_persistent(const TmzDev* __restrict__ scenes,
+                                                          const Task* __restrict__ ptasks,
+                                                          const int2* __restrict__ items, int n_items,
+                                                          const int* __restrict__ dep_off,
+                                                          const int* __restrict__ dep_idx,
+                                                          const Sample2* __restrict__ samps, int parity0,
+                                                          long long n0, int n_blocks, unsigned* ctl,
+                                                          unsigned* done, long long spin_limit, int stall_item) {
+    constexpr int STAGE_W = (stages_for(T, true) * gen_stage_f4(true, 32 / NG_LANES) >
+                             stages_for(T, false) * stage_f4(false))
+                                ? stages_for(T, true) * gen_stage_f4(true, 32 / NG_LANES)
+                                : stages_for(T, false) * stage_f4(false);
+    extern __shared__ float4 smem_f4[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    float4* stage0 = smem_f4 + (size_t)wib * STAGE_W;
+    volatile int* verr = reinterpret_cast<volatile int*>(ctl + 2);
+    // an earlier launch of this context timed out and nobody has read the flag yet
+    if (*verr) return;
+    const long long total = (long long)n_blocks * n_items;
+    for (;;) {
+        long long idx = 0;
+        if (lane == 0) idx = (long long)atomicAdd(ctl, 1u);
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+        if (idx >= total) return;
+        const int b = (int)(idx / n_items), it = (int)(idx % n_items);
+        // wait for the neighbours' block b - 1
+        int ok = 1;
+        if (lane == 0 && b > 0) {
+            long long spins = 0;
+            for (int q = dep_off[it]; q < dep_off[it + 1] && ok; q++) {
+                const unsigned* d = done + dep_idx[q];
+                unsigned v;
+                for (;;) {
+                    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(d) : "memory");
+                    if (v >= (unsigned)b) break;
+                    if (*verr || ++spins > spin_limit) {
+                        atomicExch(reinterpret_cast<int*>(ctl + 2), 1);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(100);
+                }
+            }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) return;
+        __syncwarp();
+        const int parity = parity0 ^ (b & 1);
+        const long long nb = n0 + (long long)b * T;
+        const int2 item = items[it];
+        if (item.x == PITEM_NARROW) {
+            const Task tk = ptasks[item.y + lane / NG_LANES];
+            const TmzDev* S = scenes + tk.scene;
+            general_task<T, true, false, false, false, NG_LANES>(S, tk, samps, parity, nb, S->coef, stage0, lane);
+        } else {
+            const Task tk = ptasks[item.y];
+            const TmzDev* S = scenes + tk.scene;
+            if (item.x == PITEM_INTERIOR) interior_task<T>(S, tk, parity, S->coef, stage0, lane);
+            else general_task<T, true, false, WREC>(S, tk, samps, parity, nb, S->coef, stage0, lane);
+        }
+        // publish: every lane's stores of this item, then the count
+        __syncwarp();
+        if (lane == 0 && !(b == 0 && it == stall_item)) {
+            __threadfence();
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(done + it), "r"((unsigned)(b + 1)) : "memory");
+        }
+    }
+}
+
+// dynamic shared memory of the persistent kernel: per warp, the larger of the
+// general (narrow) and interior staging areas
+static size_t persistent_smem(int T, int warps) {
+    const size_t g = (size_t)stages_for(T, true) * gen_stage_f4(true, 32 / NG_LANES);
+    const size_t i = (size_t)stages_for(T, false) * stage_f4(false);
+    return (size_t)warps * (g > i ? g : i) * sizeof(float4);
+}
+
+template <int T, bool WREC>
+static cudaError_t launch_persistent_T(const fdtd_ctx* c, cudaStream_t st, int parity, long long n0, int n_blocks,
+                                       long long spin_limit, int* grid_out) {
+    const int warps = 8;
+    const size_t smem = persistent_smem(T, warps);
+    cudaError_t e = ensure_dyn_smem((const void*)k_tmz_persistent<T, WREC>, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tmz_persistent<T, WREC>, warps * 32, smem);
+    if (e != cudaSuccess) return e;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int grid = per_sm * sms;
+    *grid_out = grid;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(warps * 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;   // every CTA resident: a waited-on item is always being worked
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_tmz_persistent<T, WREC>, (const TmzDev*)c->d_scenes, (const Task*)c->d_ptasks,
+                              (const int2*)c->d_pitems, c->n_pitems, (const int*)c->d_dep_off, (const int*)c->d_dep_idx,
+                              (const Sample2*)c->d_samp, parity, n0, n_blocks, c->d_ctl, c->d_done, spin_limit,
+                              c->opt_debug_skip);
+}
+
+// n_blocks T-step blocks in one cooperative launch.  The work counter and the
+// completion counts are zeroed first; the error word ctl[2] is not: it stays set
+// from a timed-out launch until fdtd_sync reports it, so a later launch of the
+// same step call neither advances the fields nor overwrites the flag.
+int tmz_persistent_launch(fdtd_ctx* c, int T, long long n0, int n_blocks, int parity) {
+    cudaError_t e = cudaMemsetAsync(c->d_ctl, 0, 2 * sizeof(unsigned), c->stream);
+    if (e == cudaSuccess && c->n_pitems > 0)
+        e = cudaMemsetAsync(c->d_done, 0, (size_t)c->n_pitems * sizeof(unsigned), c->stream);
+    int grid = 0;
+    const bool wrec = adj_edge_mode(c);   // edge-weight reverse mode: keep the design window
+    if (e == cudaSuccess && c->n_pitems > 0) {
+        switch (T) {
+            case 1: e = wrec ? launch_persistent_T<1, true>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid)
+                             : launch_persistent_T<1, false>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid);
+                break;
+            case 2: e = wrec ? launch_persistent_T<2, true>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid)
+                             : launch_persistent_T<2, false>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid);
+                break;
+            case 3: e = wrec ? launch_persistent_T<3, true>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid)
+                             : launch_persistent_T<3, false>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid);
+                break;
+            default: e = wrec ? launch_persistent_T<4, true>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid)
+                              : launch_persistent_T<4, false>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid);
+                break;
+        }
+    }
+    c->launches++;
+    c->opt_debug_skip = -1;   // the test hook covers one launch
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_err, c->d_ctl + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) {
+        c->err = std::string("persistent launch: ") + cudaGetErrorString(e);
+        return FDTD_ECUDA;
+    }
+    return FDTD_OK;
 }
 
 // ===========================================================================

@@ -762,7 +762,7 @@ int fdtd_create3(const fdtd_grid* g, double dx, double dt, double courant, const
     c->d_scenes = nullptr; c->d_tasks = nullptr; c->d_tasks_b = nullptr; c->n_tasks_b = 0; c->warps_b = 2; c->d_tasks_l = nullptr; c->n_tasks_l = 0; c->warps_l = 4; c->d_tasks_s = nullptr; c->n_tasks_s = 0; c->d_tasks_bd = nullptr; c->n_tasks_bd = 0;
     c->d_dft = nullptr; c->n_dft = 0; c->opt_adj_store = 1;
     c->d_tasks_n = nullptr; c->n_tasks_n = 0; c->task_narrow = -1;
-    c->opt_check_every = 0; c->d_bad = nullptr; c->h_bad = nullptr;
+    c->opt_check_every = 0; c->d_bad = nullptr; c->h_bad = nullptr; c->opt_cluster = 1;
     c->aux = c->aux2 = nullptr; c->ev_fork = c->ev_join = c->ev_join2 = nullptr;
     c->d_samp = nullptr; c->d_samp_scene = nullptr; c->d_samp_off = nullptr;
     c->n_tasks = 0; c->task_tb = c->task_seg = -1; c->graph = nullptr; c->adj = nullptr;
@@ -967,7 +967,10 @@ int fdtd_step3(fdtd_ctx* c, int64_t n_steps) {
     const dim3 grp((s->nx + 31) / 32, (s->ny + 7) / 8, 1);
     const int si = s->src_kind >= 0 ? s->src_i : -1;
     const int segz = std::max(1, c->opt_segment);
-    const dim3 gfz((s->nx + TXC - 1) / TXC, (s->ny + TYR - 1) / TYR, (s->nz + segz - 1) / segz);
+    // y tiles, padded to whole clusters (a tile past the grid stores nothing)
+    const int cy = std::max(1, c->opt_cluster);
+    const int ty = ((s->ny + TYR - 1) / TYR + cy - 1) / cy * cy;
+    const dim3 gfz((s->nx + TXC - 1) / TXC, ty, (s->nz + segz - 1) / segz);
     const size_t smem3 = fused3_smem();
     if (c->opt_kernel != 1) {
         cudaError_t ea = ensure_dyn_smem((const void*)k_yee3d_fused, smem3);
@@ -985,7 +988,26 @@ int fdtd_step3(fdtd_ctx* c, int64_t n_steps) {
                 b.in[w] = s->f[w];
                 b.out[w] = s->g[w];
             }
-            k_yee3d_fused<<<gfz, NW3 * 32, smem3, c->stream>>>(d, b, segz);
+            if (cy > 1) {
+                // clusters of cy y-adjacent tiles run at once on one GPC, so the
+                // E and H halo rows one tile re-reads are in the L2 its neighbour filled
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = gfz;
+                cfg.blockDim = dim3(NW3 * 32);
+                cfg.dynamicSmemBytes = smem3;
+                cfg.stream = c->stream;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeClusterDimension;
+                attr[0].val.clusterDim.x = 1;
+                attr[0].val.clusterDim.y = cy;
+                attr[0].val.clusterDim.z = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                cudaError_t el = cudaLaunchKernelEx(&cfg, k_yee3d_fused, d, b, segz);
+                if (el != cudaSuccess) return fail3(c, FDTD_ECUDA, "clustered 3D launch: %s", cudaGetErrorString(el));
+            } else {
+                k_yee3d_fused<<<gfz, NW3 * 32, smem3, c->stream>>>(d, b, segz);
+            }
             c->launches++;
             for (int w = 0; w < G_COUNT; w++) std::swap(s->f[w], s->g[w]);
             d = dev_of(s);
