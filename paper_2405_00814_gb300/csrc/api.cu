@@ -676,23 +676,34 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
         for (const Sample2& sp : c->s2[k]->samples) ssamp.push_back(sp);
         soff[k + 1] = (int)ssamp.size();
     }
-    // the persistent kernel's items, the long chains first: narrow groups, general
-    // tasks, interior tasks; each waits for the items of the previous block
-    // whose regions meet its own
+    // the persistent kernel's items, in space order (scene, strip, row): an item
+    // of block b then waits for items of block b - 1 that were claimed about one
+    // block's worth of work earlier, so blocks overlap instead of draining; each
+    // item waits for the items of the previous block whose regions meet its own
     std::vector<Task> ptasks;
     std::vector<int2> pitems;
     const int per_warp_n = 32 / NG_LANES;
-    for (size_t q = 0; q + per_warp_n <= tasks_n.size(); q += per_warp_n) {
-        if (tasks_n[q].scene < 0) continue;
-        pitems.push_back(make_int2(PITEM_NARROW, (int)ptasks.size()));
-        for (int g = 0; g < per_warp_n; g++) ptasks.push_back(tasks_n[q + g]);
-    }
-    for (const std::vector<Task>* L : {&tasks_b, &tasks_bd, &tasks_l, &tasks})
-        for (const Task& t : *L) {
-            if (t.scene < 0) continue;
-            pitems.push_back(make_int2(L == &tasks ? PITEM_INTERIOR : PITEM_GENERAL, (int)ptasks.size()));
-            ptasks.push_back(t);
+    {
+        struct It { int kind; std::vector<Task> t; };
+        std::vector<It> its;
+        for (size_t q = 0; q + per_warp_n <= tasks_n.size(); q += per_warp_n) {
+            if (tasks_n[q].scene < 0) continue;
+            its.push_back({PITEM_NARROW, std::vector<Task>(tasks_n.begin() + q, tasks_n.begin() + q + per_warp_n)});
         }
+        for (const std::vector<Task>* L : {&tasks_b, &tasks_bd, &tasks_l, &tasks})
+            for (const Task& t : *L)
+                if (t.scene >= 0) its.push_back({L == &tasks ? PITEM_INTERIOR : PITEM_GENERAL, {t}});
+        std::stable_sort(its.begin(), its.end(), [](const It& a, const It& b) {
+            const Task &p = a.t[0], &q = b.t[0];
+            if (p.scene != q.scene) return p.scene < q.scene;
+            if (p.x0 != q.x0) return p.x0 < q.x0;
+            return p.ya < q.ya;
+        });
+        for (const It& it : its) {
+            pitems.push_back(make_int2(it.kind, (int)ptasks.size()));
+            ptasks.insert(ptasks.end(), it.t.begin(), it.t.end());
+        }
+    }
     std::vector<int> dep_off(pitems.size() + 1, 0), dep_idx;
     {
         // a task reads columns [x0 - HALO, x0 - HALO + 4 lanes) and rows
@@ -1119,11 +1130,6 @@ int fdtd_set_option(fdtd_ctx* c, int option, int64_t v) {
             c->opt_segment = (int)v;
             c->dirty = true;
             return FDTD_OK;
-        case FDTD_OPT_CLUSTER:
-            if (c->dims != 3) return fail(c, FDTD_EINVAL, "thread-block clusters apply to the 3D fused kernel");
-            if (v != 1 && v != 2 && v != 4 && v != 8) return fail(c, FDTD_EINVAL, "cluster size %lld: 1, 2, 4 or 8", (long long)v);
-            c->opt_cluster = (int)v;
-            return FDTD_OK;
         case FDTD_OPT_CHECK_EVERY:
             if (c->dims != 2) return fail(c, FDTD_EINVAL, "the periodic finite check covers 2D contexts");
             if (v < 0 || v > (1 << 30)) return fail(c, FDTD_EINVAL, "check interval %lld outside 0..2^30", (long long)v);
@@ -1167,7 +1173,6 @@ int64_t fdtd_get_option(const fdtd_ctx* c, int option) {
         case FDTD_OPT_ADJ_STORE: return c->opt_adj_store;
         case FDTD_OPT_SEGMENT_B: return c->opt_segment_b;
         case FDTD_OPT_CHECK_EVERY: return c->opt_check_every;
-        case FDTD_OPT_CLUSTER: return c->opt_cluster;
     }
     return -1;
 }
@@ -1592,7 +1597,7 @@ int fdtd_autotune(fdtd_ctx* c, int trial_steps, double* best_ms) {
             for (int w : {2, 4, 8}) cand.push_back({0, T, seg, w});
     if (!any_split(c))   // the persistent kernel has no split-field variant
         for (int T = 2; T <= MAX_TB; T++)
-            for (int seg : {16, 24, 32, 48}) cand.push_back({2, T, seg, 8});
+            for (int seg : {16, 32, 48, 64}) cand.push_back({2, T, seg, 8});
     const int graph = c->opt_graph;
     c->opt_graph = 0;
     cudaEvent_t e0, e1;

@@ -238,7 +238,6 @@ struct fdtd_ctx {
     int opt_debug_skip;          // work item that never reports its first block done (-1 none)
     int opt_adj_store;           // FDTD_OPT_ADJ_STORE
     int opt_check_every;         // FDTD_OPT_CHECK_EVERY (0: off)
-    int opt_cluster;             // FDTD_OPT_CLUSTER (3D: y tiles per thread-block cluster)
     int* d_bad;                  // sticky device word of the periodic finite check
     int* h_bad;                  // pinned copy of it (cleared by fdtd_sync)
     // CUDA graph of a step sequence

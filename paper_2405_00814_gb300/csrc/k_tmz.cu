@@ -819,27 +819,31 @@ __global__ void __launch_bounds__(256, 1) k_tmz_persistent(const TmzDev* __restr
         idx = __shfl_sync(0xffffffffu, idx, 0);
         if (idx >= total) return;
         const int b = (int)(idx / n_items), it = (int)(idx % n_items);
-        // wait for the neighbours' block b - 1
-        int ok = 1;
-        if (lane == 0 && b > 0) {
+        // wait for the neighbours' block b - 1: the lanes poll up to 32 counts at
+        // once (relaxed loads), then one fence orders the item's reads after them
+        if (b > 0) {
+            const int d0 = dep_off[it], nd = dep_off[it + 1] - d0;
             long long spins = 0;
-            for (int q = dep_off[it]; q < dep_off[it + 1] && ok; q++) {
-                const unsigned* d = done + dep_idx[q];
-                unsigned v;
+            for (int base = 0; base < nd; base += 32) {
+                const int q = base + lane;
+                const unsigned* d = q < nd ? done + dep_idx[d0 + q] : nullptr;
                 for (;;) {
-                    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(d) : "memory");
-                    if (v >= (unsigned)b) break;
-                    if (*verr || ++spins > spin_limit) {
-                        atomicExch(reinterpret_cast<int*>(ctl + 2), 1);
-                        ok = 0;
-                        break;
+                    int ready = 1;
+                    if (d) {
+                        unsigned v;
+                        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(d) : "memory");
+                        ready = v >= (unsigned)b;
+                    }
+                    if (__all_sync(0xffffffffu, ready)) break;
+                    if (__any_sync(0xffffffffu, *verr != 0) || ++spins > spin_limit) {
+                        if (lane == 0) atomicExch(reinterpret_cast<int*>(ctl + 2), 1);
+                        return;
                     }
                     __nanosleep(100);
                 }
             }
+            __threadfence();
         }
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (!ok) return;
         __syncwarp();
         const int parity = parity0 ^ (b & 1);
         const long long nb = n0 + (long long)b * T;
@@ -857,8 +861,8 @@ __global__ void __launch_bounds__(256, 1) k_tmz_persistent(const TmzDev* __restr
         // publish: every lane's stores of this item, then the count
         __syncwarp();
         if (lane == 0 && !(b == 0 && it == stall_item)) {
-            __threadfence();
-            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(done + it), "r"((unsigned)(b + 1)) : "memory");
+            __threadfence();   // release: the fence, then a plain store of the count
+            asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(done + it), "r"((unsigned)(b + 1)) : "memory");
         }
     }
 }

@@ -23,9 +23,12 @@
 
 using namespace gem;
 
-// x offset of cell i = 0 in a row: a 4-float left pad keeps every 32-cell tile
-// row 16-byte aligned for the fused kernel's staging
-constexpr int PX3 = 4;
+// x offset of cell i = 0 in a row: a 32-float (128-byte) left pad puts every
+// 128-cell tile row of the fused kernel on a 128-byte line, so a warp's float4
+// loads and stores of its row cover whole 32-byte sectors (a partly written
+// sector costs the DRAM a read-modify-write), and the staged rows, which start
+// 4 cells left of the tile, stay 16-byte aligned
+constexpr int PX3 = 32;
 
 enum { G_EX = 0, G_EY, G_EZ, G_HX, G_HY, G_HZ,
        P_EXY, P_EXZ, P_EYZ, P_EYX, P_EZX, P_EZY, P_HXY, P_HXZ, P_HYZ, P_HYX, P_HZX, P_HZY, G_COUNT };
@@ -377,7 +380,7 @@ __global__ void __launch_bounds__(NW3 * 32, 2) k_yee3d_fused(Dev3 S, Bufs3 B, in
             const int comp = q / (ER3 * EW4), r = (q / EW4) % ER3, v = q % EW4;
             const int jj = j0 - 1 + r;
             const bool in = jj <= S.ny && p <= S.nz;
-            const size_t g = ((size_t)(p + 1) * rows + (jj + 1)) * pitch + x0 + 4 * v;   // cell x0 - 4 + 4v
+            const size_t g = ((size_t)(p + 1) * rows + (jj + 1)) * pitch + x0 - 4 + PX3 + 4 * v;   // cell x0 - 4 + 4v
             cpa16(dst + q, B.in[G_EX + comp] + (in ? g : 0), in);
         }
     };
@@ -762,7 +765,7 @@ int fdtd_create3(const fdtd_grid* g, double dx, double dt, double courant, const
     c->d_scenes = nullptr; c->d_tasks = nullptr; c->d_tasks_b = nullptr; c->n_tasks_b = 0; c->warps_b = 2; c->d_tasks_l = nullptr; c->n_tasks_l = 0; c->warps_l = 4; c->d_tasks_s = nullptr; c->n_tasks_s = 0; c->d_tasks_bd = nullptr; c->n_tasks_bd = 0;
     c->d_dft = nullptr; c->n_dft = 0; c->opt_adj_store = 1;
     c->d_tasks_n = nullptr; c->n_tasks_n = 0; c->task_narrow = -1;
-    c->opt_check_every = 0; c->d_bad = nullptr; c->h_bad = nullptr; c->opt_cluster = 1;
+    c->opt_check_every = 0; c->d_bad = nullptr; c->h_bad = nullptr;
     c->aux = c->aux2 = nullptr; c->ev_fork = c->ev_join = c->ev_join2 = nullptr;
     c->d_samp = nullptr; c->d_samp_scene = nullptr; c->d_samp_off = nullptr;
     c->n_tasks = 0; c->task_tb = c->task_seg = -1; c->graph = nullptr; c->adj = nullptr;
@@ -802,8 +805,8 @@ int fdtd_create3(const fdtd_grid* g, double dx, double dt, double courant, const
     s->nx = g->nx; s->ny = g->ny; s->nz = g->nz; s->npml = npml;
     s->dx = dx; s->dy = dy; s->dz = dz; s->dt = dt;
     // room for the unfused kernels' neighbours and the fused kernel's last tile,
-    // whose staged rows reach storage column x0 + TXC + 7
-    s->pitch = (std::max(g->nx + PX3 + 40, (g->nx + TXC - 1) / TXC * TXC + 8) + 31) / 32 * 32;
+    // whose staged rows reach cell x0 + TXC + 3 (storage column x0 + TXC + 3 + PX3)
+    s->pitch = (std::max(g->nx + PX3 + 40, (g->nx + TXC - 1) / TXC * TXC + PX3 + 8) + 31) / 32 * 32;
     s->rows = g->ny + 2;
     s->planes = g->nz + 2;
     s->src_kind = -1; s->src_i = s->src_j = s->src_k = -1; s->src_comp = G_EZ; s->src_param = 0; s->src_cap = 0;
@@ -967,10 +970,7 @@ int fdtd_step3(fdtd_ctx* c, int64_t n_steps) {
     const dim3 grp((s->nx + 31) / 32, (s->ny + 7) / 8, 1);
     const int si = s->src_kind >= 0 ? s->src_i : -1;
     const int segz = std::max(1, c->opt_segment);
-    // y tiles, padded to whole clusters (a tile past the grid stores nothing)
-    const int cy = std::max(1, c->opt_cluster);
-    const int ty = ((s->ny + TYR - 1) / TYR + cy - 1) / cy * cy;
-    const dim3 gfz((s->nx + TXC - 1) / TXC, ty, (s->nz + segz - 1) / segz);
+    const dim3 gfz((s->nx + TXC - 1) / TXC, (s->ny + TYR - 1) / TYR, (s->nz + segz - 1) / segz);
     const size_t smem3 = fused3_smem();
     if (c->opt_kernel != 1) {
         cudaError_t ea = ensure_dyn_smem((const void*)k_yee3d_fused, smem3);
@@ -988,26 +988,7 @@ int fdtd_step3(fdtd_ctx* c, int64_t n_steps) {
                 b.in[w] = s->f[w];
                 b.out[w] = s->g[w];
             }
-            if (cy > 1) {
-                // clusters of cy y-adjacent tiles run at once on one GPC, so the
-                // E and H halo rows one tile re-reads are in the L2 its neighbour filled
-                cudaLaunchConfig_t cfg = {};
-                cfg.gridDim = gfz;
-                cfg.blockDim = dim3(NW3 * 32);
-                cfg.dynamicSmemBytes = smem3;
-                cfg.stream = c->stream;
-                cudaLaunchAttribute attr[1];
-                attr[0].id = cudaLaunchAttributeClusterDimension;
-                attr[0].val.clusterDim.x = 1;
-                attr[0].val.clusterDim.y = cy;
-                attr[0].val.clusterDim.z = 1;
-                cfg.attrs = attr;
-                cfg.numAttrs = 1;
-                cudaError_t el = cudaLaunchKernelEx(&cfg, k_yee3d_fused, d, b, segz);
-                if (el != cudaSuccess) return fail3(c, FDTD_ECUDA, "clustered 3D launch: %s", cudaGetErrorString(el));
-            } else {
-                k_yee3d_fused<<<gfz, NW3 * 32, smem3, c->stream>>>(d, b, segz);
-            }
+            k_yee3d_fused<<<gfz, NW3 * 32, smem3, c->stream>>>(d, b, segz);
             c->launches++;
             for (int w = 0; w < G_COUNT; w++) std::swap(s->f[w], s->g[w]);
             d = dev_of(s);

@@ -22,8 +22,7 @@ PEC, CPML, SPLIT_PML = 0, 1, 2
 COMP = {"ex": 0, "ey": 1, "ez": 2, "hx": 3, "hy": 4, "hz": 5}
 SRC = {"ricker": 0, "gauss_mod": 1, "gauss": 2, "sampled": 3, "sine": 4}
 OPT = {"kernel": 0, "tblock": 1, "segment": 2, "warps": 3, "graph": 4, "spin_limit": 5, "debug_stall_item": 6,
-       "adj_store": 7, "segment_b": 8, "check_every": 9,
-       "cluster": 10}
+       "adj_store": 7, "segment_b": 8, "check_every": 9}
 
 
 class FDTDError(RuntimeError):
