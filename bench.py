@@ -261,7 +261,7 @@ def batch_throughput(stream, reps=2):
     # segment heights
     opts = tune["options"]
     sim.set_option("kernel", 2)
-    segs = [opts["segment"]] if opts["kernel"] == 2 else [32, 64]
+    segs = [opts["segment"]] if opts["kernel"] == 2 else [64, 96, 128]
     pbest, pseg = None, None
     for seg in segs:
         if opts["kernel"] != 2:

@@ -317,7 +317,7 @@ int fdtd_sync(fdtd_ctx* ctx);
 /* Pick the 2D kernel options for the current scenes (one large scene, or a
  * batch: Sec. V-A runs many simulations of varying size): time every candidate
  * of (kernel 0: T 2..4, segment 16..96 in steps of 8, warps 2, 4 or 8; kernel 2,
- * not for a split-field PML: T 2..4, segment 16, 32, 48 or 64) for trial_steps
+ * not for a split-field PML: T 2..4, segment 32, 64, 96 or 128) for trial_steps
  * steps, time the four fastest twice more for 4 x trial_steps, keep the best,
  * then for kernel 0 try FDTD_OPT_SEGMENT_B values against the automatic one
  * (kept only if 1 % faster).  Leaves the context reset (t = 0, zero fields).

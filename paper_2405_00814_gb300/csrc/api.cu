@@ -1597,7 +1597,7 @@ int fdtd_autotune(fdtd_ctx* c, int trial_steps, double* best_ms) {
             for (int w : {2, 4, 8}) cand.push_back({0, T, seg, w});
     if (!any_split(c))   // the persistent kernel has no split-field variant
         for (int T = 2; T <= MAX_TB; T++)
-            for (int seg : {16, 32, 48, 64}) cand.push_back({2, T, seg, 8});
+            for (int seg : {32, 64, 96, 128}) cand.push_back({2, T, seg, 8});
     const int graph = c->opt_graph;
     c->opt_graph = 0;
     cudaEvent_t e0, e1;
