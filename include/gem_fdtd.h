@@ -87,7 +87,7 @@ extern "C" {
                                     steps with the unfused pair instead).
                                 3D: 0 = fused z-marching kernel (default), 1 = one H and one E launch per step */
 #define FDTD_OPT_TBLOCK 1    /* time steps per HBM pass of the fused kernel, 1..4 */
-#define FDTD_OPT_SEGMENT 2   /* 2D: rows per warp task of the fused kernel (multiple of 8, >= 8);
+#define FDTD_OPT_SEGMENT 2   /* 2D: rows per warp task of the fused kernel (>= 8);
                                 3D: planes per z-segment of the fused z-marching kernel (>= 1, default 24) */
 #define FDTD_OPT_WARPS 3     /* warps per CTA of the fused kernel, 1..8 */
 #define FDTD_OPT_GRAPH 4     /* 1: fdtd_step records its launches into a CUDA graph and replays it when called
@@ -316,7 +316,7 @@ int fdtd_sync(fdtd_ctx* ctx);
 
 /* Pick the 2D kernel options for the current scenes (one large scene, or a
  * batch: Sec. V-A runs many simulations of varying size): time every candidate
- * of (kernel 0: T 2..4, segment 16..96 in steps of 8, warps 2, 4 or 8; kernel 2,
+ * of (kernel 0: T 2..4, segment 16..96 in steps of 4, warps 2, 4 or 8; kernel 2,
  * not for a split-field PML: T 2..4, segment 32, 64, 96 or 128) for trial_steps
  * steps, time the four fastest twice more for 4 x trial_steps, keep the best,
  * then for kernel 0 try FDTD_OPT_SEGMENT_B values against the automatic one

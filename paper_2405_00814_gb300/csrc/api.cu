@@ -372,6 +372,7 @@ fdtd_ctx* ctx_new(void* stream) {
     c->d_tasks_n = nullptr;
     c->n_tasks_n = 0;
     c->task_narrow = -1;
+    c->task_pers = -1;
     c->aux = c->aux2 = nullptr;
     c->ev_fork = c->ev_join = c->ev_join2 = nullptr;
     cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
@@ -683,7 +684,7 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     std::vector<Task> ptasks;
     std::vector<int2> pitems;
     const int per_warp_n = 32 / NG_LANES;
-    {
+    if (c->opt_kernel == 2) {
         struct It { int kind; std::vector<Task> t; };
         std::vector<It> its;
         for (size_t q = 0; q + per_warp_n <= tasks_n.size(); q += per_warp_n) {
@@ -849,6 +850,7 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     c->n_tasks_bd = (int)tasks_bd.size();
     c->n_tasks_n = (int)tasks_n.size();
     c->task_narrow = want_narrow ? 1 : 0;
+    c->task_pers = c->opt_kernel == 2 ? 1 : 0;
     c->warps_l = warps_l;
     c->warps_b = warps_b;
     c->task_tb = T;
@@ -886,7 +888,8 @@ int step_prepare(fdtd_ctx* c, int64_t n_steps) {
     if (c->s2.empty()) return fail(c, FDTD_ESTATE, "no scene");
     int rc = ensure_capacity(c, c->t + n_steps);
     if (rc) return rc;
-    if (c->dirty || c->task_seg != c->opt_segment || c->task_narrow != (c->opt_kernel != 1 ? 1 : 0)) {
+    if (c->dirty || c->task_seg != c->opt_segment || c->task_narrow != (c->opt_kernel != 1 ? 1 : 0) ||
+        c->task_pers != (c->opt_kernel == 2 ? 1 : 0)) {
         rc = rebuild(c, c->opt_tblock, c->opt_segment, c->opt_warps);
         if (rc) return rc;
     }
@@ -1124,9 +1127,9 @@ int fdtd_set_option(fdtd_ctx* c, int option, int64_t v) {
             c->opt_tblock = (int)v;
             return FDTD_OK;
         case FDTD_OPT_SEGMENT:
-            // 2D: rows per warp task (multiple of 8); 3D: planes per z-segment (>= 1)
-            if (c->dims == 3 ? (v < 1 || v > (1 << 20)) : (v < 8 || v > (1 << 20) || v % 8))
-                return fail(c, FDTD_EINVAL, "segment %lld: 2D needs a multiple of 8 >= 8, 3D >= 1", (long long)v);
+            // 2D: rows per warp task (>= 8); 3D: planes per z-segment (>= 1)
+            if (c->dims == 3 ? (v < 1 || v > (1 << 20)) : (v < 8 || v > (1 << 20)))
+                return fail(c, FDTD_EINVAL, "segment %lld: 2D needs >= 8, 3D >= 1", (long long)v);
             c->opt_segment = (int)v;
             c->dirty = true;
             return FDTD_OK;
@@ -1593,7 +1596,7 @@ int fdtd_autotune(fdtd_ctx* c, int trial_steps, double* best_ms) {
     // the segment height sets how many CTAs a block launches, so the sweep is
     // fine-grained: a list that fills whole waves of the 152 SMs wins
     for (int T = 2; T <= MAX_TB; T++)
-        for (int seg = 16; seg <= 96; seg += 8)
+        for (int seg = 16; seg <= 96; seg += 4)
             for (int w : {2, 4, 8}) cand.push_back({0, T, seg, w});
     if (!any_split(c))   // the persistent kernel has no split-field variant
         for (int T = 2; T <= MAX_TB; T++)

@@ -205,7 +205,8 @@ struct fdtd_ctx {
     int n_tasks_bd;
     gem::Task* d_tasks_n;          // narrow x-slab CPML tasks, NG_LANES lanes each (4 per warp)
     int n_tasks_n;
-    int task_narrow;               // the lists were built with narrow x-slab tasks (kernel 0)
+    int task_narrow;               // the lists were built with narrow x-slab tasks (kernels 0, 2)
+    int task_pers;                 // the persistent kernel's items were built (kernel 2)
     gem::Task* d_tasks_l;          // lite tasks: design, source, probes or ragged edge, no CPML
     int n_tasks_l, warps_l;
     cudaStream_t aux, aux2;        // forked streams for the CPML and lite tasks

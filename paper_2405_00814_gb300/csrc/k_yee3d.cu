@@ -764,7 +764,7 @@ int fdtd_create3(const fdtd_grid* g, double dx, double dt, double courant, const
     c->dirty = true;
     c->d_scenes = nullptr; c->d_tasks = nullptr; c->d_tasks_b = nullptr; c->n_tasks_b = 0; c->warps_b = 2; c->d_tasks_l = nullptr; c->n_tasks_l = 0; c->warps_l = 4; c->d_tasks_s = nullptr; c->n_tasks_s = 0; c->d_tasks_bd = nullptr; c->n_tasks_bd = 0;
     c->d_dft = nullptr; c->n_dft = 0; c->opt_adj_store = 1;
-    c->d_tasks_n = nullptr; c->n_tasks_n = 0; c->task_narrow = -1;
+    c->d_tasks_n = nullptr; c->n_tasks_n = 0; c->task_narrow = -1; c->task_pers = -1;
     c->opt_check_every = 0; c->d_bad = nullptr; c->h_bad = nullptr;
     c->aux = c->aux2 = nullptr; c->ev_fork = c->ev_join = c->ev_join2 = nullptr;
     c->d_samp = nullptr; c->d_samp_scene = nullptr; c->d_samp_off = nullptr;
