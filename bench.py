@@ -593,9 +593,9 @@ def main():
     traffic = _traffic_record()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": (f"k_tmz_interior<{T}> + k_tmz_fused<{T},1> (one T-step block, run concurrently)"
+                "kernel": (f"k_tmz_interior<{T}> + k_tmz_cpml_mixed<{T}> (one T-step block, run concurrently)"
                            if args.kernel == 0 else
-                           f"k_tmz_persistent<{T}> (one T-step block between grid barriers)" if args.kernel == 2
+                           f"k_tmz_persistent<{T}> (T-step blocks of dependency-ordered work items)" if args.kernel == 2
                            else "k_tmz_h + k_tmz_e"),
                 "unit_bytes": "25 B per grid cell per launch (each launch advances every cell T steps)"}
     hbm_frac_cu = value / world * BYTES_PER_CU / (peak * 1e9)
