@@ -51,12 +51,14 @@ constexpr int A_Q_I = 8;
 // Ca, Cb/dx, Cb/dy; CPML adds the four psi and, after the material words, the
 // row's y-profile scalars.  pv = CPML variant.
 __host__ __device__ constexpr int a_nslot(bool gen, bool pv) { return pv ? 7 : (gen ? 6 : 3); }
-__host__ __device__ constexpr int a_stage_f4(bool gen, bool pv) { return a_nslot(gen, pv) * 32 + 8 + (pv ? 1 : 0); }
+__host__ __device__ constexpr int a_stage_f4(bool gen, bool pv, int groups = 1) {
+    return a_nslot(gen, pv) * 32 + 8 + (pv ? groups : 0);
+}
 __host__ __device__ constexpr int a_stages(int T, bool pv) { return pv ? T + A_PF_G : A_Q_I; }
 __host__ __device__ constexpr int a_pf(int T, bool pv) { return pv ? A_PF_G : A_Q_I - T; }
 
-size_t adj_smem(int T, int warps, bool gen, bool pv) {
-    return (size_t)warps * a_stages(T, pv) * a_stage_f4(gen, pv) * sizeof(float4);
+size_t adj_smem(int T, int warps, bool gen, bool pv, int groups = 1) {
+    return (size_t)warps * a_stages(T, pv) * a_stage_f4(gen, pv, groups) * sizeof(float4);
 }
 
 __device__ __forceinline__ void acp16(void* smem, const void* gmem) {
@@ -80,31 +82,22 @@ __device__ __forceinline__ float cget(const float4& v, int c) { return c == 0 ? 
 // Reuses Sample2 {i, j, comp (unused), slot}.
 
 // GEN: design rectangle, adjoint sources, ragged edge; PMLV: CPML auxiliaries
-template <int T, bool GEN, bool PMLV, bool DSGV = true>
-__global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 : (GEN ? 3 : 2)) k_adj(const TmzDev* __restrict__ scenes,
-                                                          const Task* __restrict__ tasks, int n_tasks,
-                                                          const Sample2* __restrict__ srcs, int parity,
-                                                          long long n_top) {
+// One warp's reverse task (or, G < 32, 32 / G narrow tasks of G lanes each, one
+// per lane group, as in the forward general task: width-G shuffles, every group
+// streams as many rows as the warp's longest task and stores nothing past its
+// own, adjoint sources read from memory).  coef_s: the scene's coefficient
+// table; stage0: the warp's staging area.
+template <int T, bool GEN, bool PMLV, bool DSGV = true, int G = 32>
+__device__ __forceinline__ void adj_task(const TmzDev* __restrict__ S, const Task& tk,
+                                         const Sample2* __restrict__ srcs, int parity, long long n_top,
+                                         const float4* coef_s, float4* stage0, int lane) {
+    static_assert(G == 32 || (GEN && PMLV && G >= 4 && G < 32 && (G & (G - 1)) == 0), "narrow groups are CPML tasks");
     constexpr bool PV = GEN && PMLV;
     constexpr bool SD = GEN && !PMLV;   // design band staged
     constexpr int Q = a_stages(T, PV);
     constexpr int PF = a_pf(T, PV);
-    constexpr int SF4 = a_stage_f4(GEN, PV);
+    constexpr int SF4 = a_stage_f4(GEN, PV, 32 / G);
     constexpr int NS = a_nslot(GEN, PV);
-    extern __shared__ float4 smem_f4[];
-    __shared__ float4 coef_s[256];
-
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int warps = blockDim.x >> 5;
-    const int tid = blockIdx.x * warps + wib;
-    const TmzDev* S = scenes + tasks[blockIdx.x * warps].scene;
-    for (int k = threadIdx.x; k < 256; k += blockDim.x) coef_s[k] = S->coef[k];
-    __syncthreads();
-    if (tid >= n_tasks) return;
-    const Task tk = tasks[tid];
-    if (tk.scene < 0) return;
-
     const int pitch = S->pitch, nx = S->nx, ny = S->ny;
     const float* __restrict__ e_in = S->f[F_EZ][parity];
     const float* __restrict__ hx_in = S->f[F_HX][parity];
@@ -115,11 +108,16 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
     const uint8_t* __restrict__ mat = S->mat;
     const float dbx = S->dbx, dby = S->dby;
 
-    const int cx = tk.x0 - HALO + 4 * lane;
+    const int gl = lane & (G - 1);             // lane within the task's group
+    const int grp = lane / G;
+    const int cx = tk.x0 - HALO + 4 * gl;
     const int cs = cx + PAD_X;
-    const bool out_lane = (lane >= HALO / 4) && (lane < 32 - HALO / 4) && (cx < nx);
+    const bool out_lane = (gl >= HALO / 4) && (gl < G - HALO / 4) && (cx < nx) && (tk.xe == 0 || cx < tk.xe) &&
+                          !(tk.flags & TASK_NOSTORE);
     const int s_row = tk.ya - T;
     const int r_last = tk.yb + T - 1;
+    int n_iter = r_last - s_row + 1;
+    if constexpr (G < 32) n_iter = (int)__reduce_max_sync(0xffffffffu, (unsigned)n_iter);
 
     const bool pml = PV && (tk.flags & TASK_PML) != 0;
     const bool dsg = GEN && DSGV && (tk.flags & TASK_DSG) != 0;   // DSGV = false: built without design code
@@ -137,7 +135,7 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
     const int n_samp = tk.samp_end - tk.samp_begin;
     Sample2 my_samp;
     my_samp.i = -1; my_samp.j = -1; my_samp.comp = 0; my_samp.slot = 0;
-    if (GEN && lane < n_samp) my_samp = srcs[tk.samp_begin + lane];
+    if (GEN && G == 32 && lane < n_samp) my_samp = srcs[tk.samp_begin + lane];
     const int npml = S->has_pml;
     const float* pr = S->prof;
     const int prow = S->rows;
@@ -157,11 +155,12 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
     float* psi_out[4] = {S->f[F_PEZX][parity ^ 1], S->f[F_PEZY][parity ^ 1], S->f[F_PHXY][parity ^ 1],
                          S->f[F_PHYX][parity ^ 1]};
 
-    float4* stage0 = smem_f4 + (size_t)wib * Q * SF4;
     auto stage_of = [&](int row) { return stage0 + ((row - s_row) % Q) * SF4; };
     auto yslab = [&](int row) { return (row < npml) || (row >= ny - npml); };
-    auto issue = [&](int row) {
-        float4* st = stage_of(row);
+    // stage the row of iteration i (past its last row, a group re-reads that row)
+    auto issue = [&](int i) {
+        const int row = G < 32 ? min(s_row + i, r_last) : s_row + i;
+        float4* st = stage0 + (i % Q) * SF4;
         const size_t g = (size_t)(row + PAD_Y) * pitch + cs;
         acp16(st + 0 * 32 + lane, e_in + g);
         acp16(st + 1 * 32 + lane, hx_in + g);
@@ -178,8 +177,8 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
         if constexpr (PV) {
             if (pml) {
                 // the row's bEy, cEy, bHy, cHy
-                if (yslab(row) && lane < 4)
-                    acp4(reinterpret_cast<float*>(st + NS * 32 + 8) + lane, pr + 4 * pitch + lane * prow + row + PAD_Y);
+                if (yslab(row) && gl < 4)
+                    acp4(reinterpret_cast<float*>(st + NS * 32 + 8 + grp) + gl, pr + 4 * pitch + gl * prow + row + PAD_Y);
                 if (lane_px) {
                     acp16(st + 3 * 32 + lane, psi_in[0] + g);
                     acp16(st + 6 * 32 + lane, psi_in[3] + g);
@@ -219,7 +218,7 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
         }
     };
     // y-profile scalar k (bEy, cEy, bHy, cHy) of a CPML row, from its stage
-    auto yp = [&](const float4* sta, int k) { return reinterpret_cast<const float*>(sta + NS * 32 + 8)[k]; };
+    auto yp = [&](const float4* sta, int k) { return reinterpret_cast<const float*>(sta + NS * 32 + 8 + grp)[k]; };
     // gy of a row whose adjoint state is final for the level just finished
     auto gy_of = [&](const float4& e, const float4* c, int row, const float4* sta) {
         float4 g = make_float4(-c[0].z * e.x, -c[1].z * e.y, -c[2].z * e.z, -c[3].z * e.w);
@@ -242,14 +241,14 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
     auto inject = [&](float4& e, int row, long long m) {
         if constexpr (GEN) {
             if (has_src && m >= 0) {
-                const int nq = n_samp < 32 ? n_samp : 32;
+                const int nq = G == 32 ? (n_samp < 32 ? n_samp : 32) : 0;   // groups read sources from memory
                 for (int q = 0; q < nq; q++) {
                     if (__shfl_sync(0xffffffffu, my_samp.j, q) != row) continue;   // warp-uniform
                     const int d = __shfl_sync(0xffffffffu, my_samp.i, q) - cx;
                     const int slot = __shfl_sync(0xffffffffu, my_samp.slot, q);
                     if (d >= 0 && d < 4) cref(e, d) += adj_src[m * n_adj + slot];
                 }
-                for (int q = tk.samp_begin + 32; q < tk.samp_end; q++) {
+                for (int q = tk.samp_begin + (G == 32 ? 32 : 0); q < tk.samp_end; q++) {
                     const Sample2 sp = srcs[q];
                     const int d = sp.i - cx;
                     if (sp.j == row && d >= 0 && d < 4) cref(e, d) += adj_src[m * n_adj + sp.slot];
@@ -272,12 +271,13 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
     for (int k = 0; k < T + 2; k++) X[k] = make_float4(0, 0, 0, 0);
 #pragma unroll
     for (int k = 0; k < PF; k++) {
-        issue(s_row + k);
+        issue(k);
         acommit();
     }
 
 #pragma unroll 1
-    for (int r = s_row; r <= r_last; ++r) {
+    for (int it = 0; it < n_iter; ++it) {
+        const int r = s_row + it;
         await_<PF - 1>();
 #pragma unroll
         for (int k = T + 1; k >= 1; k--) X[k] = X[k - 1];
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
                     }
                 }
             }
-            const float gxr = __shfl_down_sync(0xffffffffu, gx.x, 1);
+            const float gxr = __shfl_down_sync(0xffffffffu, gx.x, 1, G);
             Y[t].x += gx.x - gx.y;
             Y[t].y += gx.y - gx.z;
             Y[t].z += gx.z - gx.w;
@@ -439,7 +439,7 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
             } else {
                 fyd = make_float4(-dby * X[t + 1].x, -dby * X[t + 1].y, -dby * X[t + 1].z, -dby * X[t + 1].w);
             }
-            const float fxl = __shfl_up_sync(0xffffffffu, fx.w, 1);
+            const float fxl = __shfl_up_sync(0xffffffffu, fx.w, 1, G);
             E[t].x += fyd.x - fya.x + fxl - fx.x;
             E[t].y += fyd.y - fya.y + fx.x - fx.y;
             E[t].z += fyd.z - fya.z + fx.y - fx.z;
@@ -474,7 +474,7 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
         }
 
         const int o = r - T;
-        if (o >= tk.ya) {
+        if (o >= tk.ya && o < tk.yb) {
             const size_t g = (size_t)(o + PAD_Y) * pitch + cs;
             if (out_lane) {
                 if (cx + 3 < nx) {
@@ -506,10 +506,70 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
             }
         }
         // rows past r_last stay inside the pad rows
-        issue(r + PF);
+        issue(it + PF);
         acommit();
     }
     await_<0>();
+}
+
+template <int T, bool GEN, bool PMLV, bool DSGV = true>
+__global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 : (GEN ? 3 : 2)) k_adj(const TmzDev* __restrict__ scenes,
+                                                          const Task* __restrict__ tasks, int n_tasks,
+                                                          const Sample2* __restrict__ srcs, int parity,
+                                                          long long n_top) {
+    constexpr bool PV = GEN && PMLV;
+    constexpr int Q = a_stages(T, PV);
+    constexpr int SF4 = a_stage_f4(GEN, PV);
+    extern __shared__ float4 smem_f4[];
+    __shared__ float4 coef_s[256];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int warps = blockDim.x >> 5;
+    const int tid = blockIdx.x * warps + wib;
+    const TmzDev* S = scenes + tasks[blockIdx.x * warps].scene;
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) coef_s[k] = S->coef[k];
+    __syncthreads();
+    if (tid >= n_tasks) return;
+    const Task tk = tasks[tid];
+    if (tk.scene < 0) return;
+    adj_task<T, GEN, PMLV, DSGV>(S, tk, srcs, parity, n_top, coef_s, smem_f4 + (size_t)wib * Q * SF4, lane);
+}
+
+// the reverse sweep's CPML tasks without a design in reach, in one launch: the
+// first nw_blocks CTAs run whole-warp tasks, the rest the narrow x-slab tasks,
+// 32 / NG_LANES per warp (both lists padded to whole CTAs of one scene)
+template <int T>
+__global__ void __launch_bounds__(256, 1) k_adj_cpml_mixed(const TmzDev* __restrict__ scenes,
+                                                          const Task* __restrict__ tasks_w, int nw_blocks,
+                                                          const Task* __restrict__ tasks_n,
+                                                          const Sample2* __restrict__ srcs, int parity,
+                                                          long long n_top) {
+    constexpr int Q = a_stages(T, true);
+    constexpr int SF_W = a_stage_f4(true, true), SF_N = a_stage_f4(true, true, 32 / NG_LANES);
+    constexpr int PER_WARP = 32 / NG_LANES;
+    extern __shared__ float4 smem_f4[];
+    __shared__ float4 coef_s[256];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int warps = blockDim.x >> 5;
+    const bool narrow = (int)blockIdx.x >= nw_blocks;
+    const Task* first = narrow ? tasks_n + (size_t)(blockIdx.x - nw_blocks) * warps * PER_WARP
+                               : tasks_w + (size_t)blockIdx.x * warps;
+    if (first->scene < 0) return;
+    const TmzDev* S = scenes + first->scene;
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) coef_s[k] = S->coef[k];
+    __syncthreads();
+    if (!narrow) {
+        const Task tk = tasks_w[(size_t)blockIdx.x * warps + wib];
+        if (tk.scene < 0) return;
+        adj_task<T, true, true, false>(S, tk, srcs, parity, n_top, coef_s, smem_f4 + (size_t)wib * Q * SF_W, lane);
+    } else {
+        const Task* tw = first + (size_t)wib * PER_WARP;
+        if (tw[0].scene < 0) return;   // a padding warp (whole warps only)
+        const Task tk = tw[lane / NG_LANES];
+        adj_task<T, true, true, false, NG_LANES>(S, tk, srcs, parity, n_top, coef_s,
+                                                 smem_f4 + (size_t)wib * Q * SF_N, lane);
+    }
 }
 
 template <int T, bool GEN, bool PMLV, bool DSGV = true>
@@ -525,13 +585,27 @@ cudaError_t launch_adj_v(const TmzDev* dev, const Task* tasks, int n, int warps,
 
 struct AdjLists {
     const Task *t0, *t1, *t2, *t3;   // interior, CPML without a design in reach, lite, CPML with one
-    int n0, n1, n2, n3, w0, w1, w2;
+    const Task* tn;                  // narrow x-slab CPML tasks (32 / NG_LANES per warp)
+    int n0, n1, n2, n3, nn, w0, w1, w2;
 };
+
+template <int T>
+cudaError_t launch_adj_mixed(const TmzDev* dev, const AdjLists& L, const Sample2* srcs, int parity, long long n_top,
+                             cudaStream_t st) {
+    const int warps = L.w1;
+    const size_t sm = adj_smem(T, warps, true, true, 32 / NG_LANES);
+    cudaError_t e = ensure_dyn_smem((const void*)k_adj_cpml_mixed<T>, sm);
+    if (e != cudaSuccess) return e;
+    const int nw = L.n1 / warps, nb = L.nn / (warps * 32 / NG_LANES);
+    k_adj_cpml_mixed<T><<<nw + nb, warps * 32, sm, st>>>(dev, L.t1, nw, L.tn, srcs, parity, n_top);
+    return cudaGetLastError();
+}
 
 template <int T>
 cudaError_t launch_adj_T(const TmzDev* dev, const AdjLists& L, const Sample2* srcs, int parity, long long n_top,
                          cudaStream_t s0, cudaStream_t s1, cudaStream_t s2) {
-    cudaError_t e = launch_adj_v<T, true, true, false>(dev, L.t1, L.n1, L.w1, srcs, parity, n_top, s1);
+    cudaError_t e = L.nn > 0 ? launch_adj_mixed<T>(dev, L, srcs, parity, n_top, s1)
+                             : launch_adj_v<T, true, true, false>(dev, L.t1, L.n1, L.w1, srcs, parity, n_top, s1);
     if (e == cudaSuccess) e = launch_adj_v<T, true, true>(dev, L.t3, L.n3, L.w1, srcs, parity, n_top, s1);
     if (e == cudaSuccess) e = launch_adj_v<T, true, false>(dev, L.t2, L.n2, L.w2, srcs, parity, n_top, s2);
     if (e == cudaSuccess) e = launch_adj_v<T, false, false>(dev, L.t0, L.n0, L.w0, srcs, parity, n_top, s0);
@@ -890,7 +964,7 @@ static int reverse_run(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, 
         for (void* p : to_free) cudaFree(p);
     };
     std::vector<TmzDev> fwd(ns), adj(ns);
-    std::vector<Task> tasks, tasks_g, tasks_l, tasks_gd;   // interior, CPML, lite general, CPML + design
+    std::vector<Task> tasks, tasks_g, tasks_l, tasks_gd, tasks_n;   // interior, CPML, lite, CPML + design, narrow
     std::vector<Sample2> tsrc;
     std::vector<float*> rec_of(ns), erec_of(ns), grad_of(ns), fac_of(ns);
     const int T = c->opt_tblock, seg = c->opt_segment, warps = c->opt_warps, gwarps = 2, lwarps = 4;
@@ -943,29 +1017,69 @@ static int reverse_run(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, 
         a.adj_edges = edges;
         adj[k] = a;
         // adjoint tasks: general if a CPML slab, the design rectangle or an
-        // adjoint source is within reach, or the strip is ragged
+        // adjoint source is within reach, or the strip is ragged.  As in the
+        // forward, the columns holding the CPML x-slabs go to narrow lane-group
+        // tasks when the layer is shallow enough and the design clear of them,
+        // the strips between them carrying a column limit, and the row segments
+        // start and end at the y-slab's reach.
         const int wout = STRIP - 2 * HALO;
         const size_t first = tasks.size(), first_g = tasks_g.size(), first_l = tasks_l.size(),
-                     first_gd = tasks_gd.size();
-        for (int ya = 0; ya < s->ny; ya += seg) {
-            for (int x0 = 0; x0 < s->nx; x0 += wout) {
+                     first_gd = tasks_gd.size(), first_n = tasks_n.size();
+        const int segg = c->opt_segment_b > 0 ? c->opt_segment_b : std::max(8, seg / 2);
+        const int xr = (s->nx - NG_OWN + 3) / 4 * 4;
+        const bool nar = s->npml > 0 && s->nx >= 2 * NG_OWN + 8 && NG_OWN - HALO >= s->npml &&
+                         xr <= s->nx - s->npml - MAX_TB &&
+                         !(s->dsg_i0 < NG_OWN + HALO || s->dsg_i0 + s->dsg_w > xr - HALO);
+        auto owned_end = [&](int x0) { return nar ? std::min(x0 + wout, xr) : x0 + wout; };
+        auto add_srcs = [&](Task& t, int lx0, int lx1, int ly0, int ly1) {
+            t.samp_begin = (int)tsrc.size();
+            for (const Sample2& sp : srcs[k])
+                if (sp.i >= lx0 && sp.i < lx1 && sp.j >= ly0 && sp.j < ly1) tsrc.push_back(sp);
+            t.samp_end = (int)tsrc.size();
+        };
+        if (nar) {
+            for (int side = 0; side < 2; side++) {
+                const int x0 = side == 0 ? 0 : xr, xe = side == 0 ? NG_OWN : s->nx;
+                for (int y = 0; y < s->ny; y += segg) {
+                    Task t;
+                    t.scene = k; t.x0 = x0; t.ya = y; t.yb = std::min(y + segg, s->ny); t.flags = TASK_PML; t.xe = xe;
+                    add_srcs(t, x0 - HALO, x0 - HALO + 4 * NG_LANES, t.ya - MAX_TB, t.yb + MAX_TB);
+                    tasks_n.push_back(t);
+                }
+            }
+            const int per_warp = 32 / NG_LANES;
+            while ((tasks_n.size() - first_n) % per_warp) {
+                Task t = tasks_n[first_n + (tasks_n.size() - first_n) / per_warp * per_warp];
+                t.flags |= TASK_NOSTORE;
+                tasks_n.push_back(t);
+            }
+        }
+        std::vector<std::pair<int, int>> segs;
+        {
+            const int y_lo = s->npml > 0 ? std::min(s->ny, s->npml + MAX_TB) : 0;
+            const int y_hi = s->npml > 0 ? std::max(y_lo, s->ny - s->npml - MAX_TB) : s->ny;
+            for (int y = 0; y < y_lo; y += segg) segs.emplace_back(y, std::min(y + segg, y_lo));
+            for (int y = y_lo; y < y_hi; y += seg) segs.emplace_back(y, std::min(y + seg, y_hi));
+            for (int y = y_hi; y < s->ny; y += segg) segs.emplace_back(y, std::min(y + segg, s->ny));
+        }
+        for (const auto& sgm : segs) {
+            const int ya = sgm.first;
+            for (int x0 = nar ? NG_OWN : 0; x0 < (nar ? xr : s->nx); x0 += wout) {
                 const int lx0 = x0 - HALO, lx1 = x0 - HALO + STRIP;
                 auto make = [&](int y0, int y1, bool* gen) {
                     Task t;
-                    t.scene = k; t.x0 = x0; t.ya = y0; t.yb = y1; t.flags = 0; t.xe = 0;
+                    t.scene = k; t.x0 = x0; t.ya = y0; t.yb = y1; t.flags = 0; t.xe = nar ? owned_end(x0) : 0;
                     const int ly0 = y0 - MAX_TB, ly1 = y1 + MAX_TB;
-                    if (s->npml > 0 && (lx0 < s->npml || lx1 > s->nx - s->npml || ly0 < s->npml || ly1 > s->ny - s->npml))
+                    const bool xslab = !nar && (lx0 < s->npml || lx1 > s->nx - s->npml);
+                    if (s->npml > 0 && (xslab || ly0 < s->npml || ly1 > s->ny - s->npml))
                         t.flags |= TASK_PML;
                     if (s->dsg_i0 < lx1 && s->dsg_i0 + s->dsg_w > lx0 && s->dsg_j0 < ly1 && s->dsg_j0 + s->dsg_h > ly0)
                         t.flags |= TASK_DSG;
-                    t.samp_begin = (int)tsrc.size();
-                    for (const Sample2& sp : srcs[k])
-                        if (sp.i >= lx0 && sp.i < lx1 && sp.j >= ly0 && sp.j < ly1) tsrc.push_back(sp);
-                    t.samp_end = (int)tsrc.size();
-                    *gen = t.flags != 0 || t.samp_end > t.samp_begin || x0 + wout > s->nx;
+                    add_srcs(t, lx0, lx1, ly0, ly1);
+                    *gen = t.flags != 0 || t.samp_end > t.samp_begin || (!nar && x0 + wout > s->nx);
                     return t;
                 };
-                const int yb = std::min(ya + seg, s->ny);
+                const int yb = sgm.second;
                 bool gen;
                 const size_t mark = tsrc.size();
                 Task t = make(ya, yb, &gen);
@@ -973,7 +1087,6 @@ static int reverse_run(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, 
                     tasks.push_back(t);
                 } else {
                     tsrc.resize(mark);
-                    const int segg = c->opt_segment_b > 0 ? c->opt_segment_b : std::max(8, seg / 2);
                     for (int y = ya; y < yb; y += segg) {
                         bool g2;
                         Task t2 = make(y, std::min(y + segg, yb), &g2);
@@ -993,13 +1106,16 @@ static int reverse_run(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, 
             while ((tasks_l.size() - first_l) % lwarps) tasks_l.push_back(pad);
         if (tasks_gd.size() > first_gd)
             while ((tasks_gd.size() - first_gd) % gwarps) tasks_gd.push_back(pad);
+        if (tasks_n.size() > first_n)   // whole CTAs of gwarps warps; a padding warp returns
+            while ((tasks_n.size() - first_n) % (gwarps * 32 / NG_LANES)) tasks_n.push_back(pad);
     }
     TmzDev *d_fwd = nullptr, *d_adj = nullptr;
-    Task *d_t = nullptr, *d_tg = nullptr, *d_tl = nullptr, *d_tgd = nullptr;
+    Task *d_t = nullptr, *d_tg = nullptr, *d_tl = nullptr, *d_tgd = nullptr, *d_tn = nullptr;
     Sample2* d_src = nullptr;
     if (!dmalloc(ns * sizeof(TmzDev), (void**)&d_fwd) || !dmalloc(ns * sizeof(TmzDev), (void**)&d_adj) ||
         !dmalloc(tasks.size() * sizeof(Task), (void**)&d_t) || !dmalloc(tasks_g.size() * sizeof(Task), (void**)&d_tg) ||
         !dmalloc(tasks_l.size() * sizeof(Task), (void**)&d_tl) || !dmalloc(tasks_gd.size() * sizeof(Task), (void**)&d_tgd) ||
+        !dmalloc(tasks_n.size() * sizeof(Task), (void**)&d_tn) ||
         !dmalloc(tsrc.size() * sizeof(Sample2), (void**)&d_src)) {
         cleanup();
         c->err = "adjoint: out of device memory";
@@ -1011,6 +1127,7 @@ static int reverse_run(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, 
     if (!tasks_l.empty()) cudaMemcpyAsync(d_tl, tasks_l.data(), tasks_l.size() * sizeof(Task), cudaMemcpyHostToDevice, st);
     if (!tasks_gd.empty())
         cudaMemcpyAsync(d_tgd, tasks_gd.data(), tasks_gd.size() * sizeof(Task), cudaMemcpyHostToDevice, st);
+    if (!tasks_n.empty()) cudaMemcpyAsync(d_tn, tasks_n.data(), tasks_n.size() * sizeof(Task), cudaMemcpyHostToDevice, st);
     if (!tsrc.empty()) cudaMemcpyAsync(d_src, tsrc.data(), tsrc.size() * sizeof(Sample2), cudaMemcpyHostToDevice, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
@@ -1060,7 +1177,8 @@ static int reverse_run(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, 
         L.t1 = d_tg; L.n1 = (int)tasks_g.size(); L.w1 = gwarps;
         L.t2 = d_tl; L.n2 = (int)tasks_l.size(); L.w2 = lwarps;
         L.t3 = d_tgd; L.n3 = (int)tasks_gd.size();
-        const bool fork1 = L.n1 > 0 || L.n3 > 0, fork2 = L.n2 > 0;
+        L.tn = d_tn; L.nn = (int)tasks_n.size();
+        const bool fork1 = L.n1 > 0 || L.n3 > 0 || L.nn > 0, fork2 = L.n2 > 0;
         for (int64_t q = len; q > 0 && rc == FDTD_OK;) {
             const int done = (int)std::min<int64_t>(T, q);
             const long long n_top = a0 + q - 1;
