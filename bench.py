@@ -288,9 +288,11 @@ def batch_throughput(stream, reps=2):
             "timing": "CUDA events around one solve replayed from a CUDA graph, best of %d after one warm-up" % reps}
 
 
-def yee3d_throughput(stream, nsteps=200, side=512, kernel=None, segment=None):
+def yee3d_throughput(stream, nsteps=200, side=512, kernel=None, segment=None, tblock=None):
     """512^3 box workload (64 dielectric boxes, 10-cell CPML, Ez dipole, DFT plane
-    at 3 frequencies): cell-updates/s over nsteps steps."""
+    at 3 frequencies): cell-updates/s over nsteps steps.  Roofline: 49 B per cell
+    per HBM pass (E, H, material read; E, H written), one pass per `tblock`
+    steps."""
     import torch
     from paper_2405_00814_gb300 import fdtd, scenes
     sc = scenes.box_scene() if side == 512 else scenes.box_scene(side=side)
@@ -299,6 +301,9 @@ def yee3d_throughput(stream, nsteps=200, side=512, kernel=None, segment=None):
         sim.set_option("kernel", kernel)
     if segment is not None:
         sim.set_option("segment", segment)
+    if tblock is not None:
+        sim.set_option("tblock", tblock)
+    tb, seg = sim.get_option("tblock"), sim.get_option("segment")
     sim.add_dft_plane(sc.dft_plane_k, ("ex", "ey", "ez"), sc.freqs)
     sim.step(10)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -311,6 +316,10 @@ def yee3d_throughput(stream, nsteps=200, side=512, kernel=None, segment=None):
     peak, _ = _peaks()
     cu = sc.cells * nsteps / (ms / 1e3)
     return {"workload": f"yee3d_{side}^3_boxes64_cpml10_dftplane", "cell_updates_per_s": cu, "ms_per_step": ms / nsteps,
+            "tblock": tb, "segment": seg,
+            # against the kernel's own bound (49 B per cell per pass of tblock steps)
+            "hbm_roofline_frac": cu * 49.0 / tb / (peak * 1e9),
+            # against the bound of any one-step-per-pass kernel (49 B per cell-update)
             "hbm_roofline_frac_at_49B_per_cell_update": cu * 49.0 / (peak * 1e9)}
 
 
@@ -476,7 +485,7 @@ def main():
     ap.add_argument("--workload", default="main",
                     choices=["main", "adjoint", "batch", "yee3d", "sweep", "edgelist", "split", "phc"],
                     help="main: the JSON line of record; the others time one secondary workload alone "
-                         "(for profiling; --nsteps and, for yee3d, --size, --kernel and --segment apply)")
+                         "(for profiling; --nsteps and, for yee3d, --size, --kernel, --segment and --tblock apply)")
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint-ratio measurement")
     args = ap.parse_args()
 
@@ -507,7 +516,7 @@ def main():
             res = batch_throughput(stream)
         elif args.workload == "yee3d":
             res = yee3d_throughput(stream, nsteps=args.nsteps or 200, side=args.size if args.size != 4096 else 512,
-                                   kernel=args.kernel, segment=args.segment)
+                                   kernel=args.kernel, segment=args.segment, tblock=args.tblock)
         elif args.workload == "split":
             res = split_pml_throughput(stream, nsteps=args.nsteps or 200)
         elif args.workload == "edgelist":

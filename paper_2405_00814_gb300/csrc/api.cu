@@ -1123,7 +1123,8 @@ int fdtd_set_option(fdtd_ctx* c, int option, int64_t v) {
             c->opt_adj_store = (int)v;
             return FDTD_OK;
         case FDTD_OPT_TBLOCK:
-            if (v < 1 || v > MAX_TB) return fail(c, FDTD_EINVAL, "tblock %lld outside 1..%d", (long long)v, MAX_TB);
+            if (v < 1 || v > (c->dims == 3 ? 2 : MAX_TB))
+                return fail(c, FDTD_EINVAL, "tblock %lld outside 1..%d", (long long)v, c->dims == 3 ? 2 : MAX_TB);
             c->opt_tblock = (int)v;
             return FDTD_OK;
         case FDTD_OPT_SEGMENT:

@@ -56,6 +56,15 @@ struct Scene3 {
     long long rec_cap;
     bool samp_dirty;
     int kernel;            // 0 fused z-marching (default), 1 one H and one E launch per step
+    // the two-step kernel's tiling (built for s2_seg): samples by owning tile,
+    // and the tiles without CPML reach (d_s2tiles[0, n_int)) and with it (the rest)
+    int* d_s2off;
+    int* d_s2idx;
+    int* d_s2tiles;
+    int n_s2int, n_s2pml;
+    int s2_seg;
+    cudaStream_t aux;      // second stream: the tiles without CPML run beside the others
+    cudaEvent_t ev_fork, ev_join;
 };
 
 namespace {
@@ -667,6 +676,541 @@ __global__ void k_dft_cells3(const float* rec, int n_rec, int slot0, int n_cells
     acc[id] = a;
 }
 
+// ---------------------------------------------------------------------------
+// two-step z-marching kernel (FDTD_OPT_TBLOCK = 2): one HBM pass advances the
+// state by two leapfrog steps, n -> n + 2.  A CTA owns TX2 = 120 cells in x by
+// TY rows in y and a z-segment [kA, kB).  It computes the first step over the
+// owned box grown by two cells on every side in x and y (lanes 0 and 31, warps
+// 0, 1 and TY + 2 carry the overlap), so the second step needs nothing that
+// another CTA computes.  Warp w handles row r = yo - 2 + w, each lane the four
+// cells xo - 4 + 4 lane .. + 3 as float4.  Iteration q (planes kA - 2 .. kB):
+//   step 1 at plane q:     H1(q) from E0(q), E0(q + 1) (staged by cp.async)
+//                          and H0(q); E1(q) from H1(q) of the row and the row
+//                          below (shared memory) and H1(q - 1) (registers);
+//                          then the step's source, probe cells and plane DFT;
+//   step 2 at plane q - 1: H2(q - 1) from E1(q - 1), E1(q) and E1(q - 1) of the
+//                          row above (shared memory, by plane parity); E2(q - 1)
+//                          from H2(q - 1) of the row and the row below and
+//                          H2(q - 2).
+// Values outside the grid are forced to zero at both steps (they are the PEC
+// ghost walls).  The first step's CPML auxiliaries wait in thread-local memory,
+// by plane parity, for the second step.  Reads buffer `in`, writes buffer `out`;
+// only the owned cells of the second step are stored.
+// ---------------------------------------------------------------------------
+constexpr int TX2 = 120;           // owned cells per tile row (lanes 1 .. 30)
+constexpr int NE2 = 4;             // E ring slots: planes q .. q + 3
+constexpr int MAXP2 = 4;           // plane monitors the kernel updates itself
+constexpr int T2_ROWS = 9;         // owned rows per tile (12 warps)
+
+struct Extra2 {
+    const float* wave;             // source waveform: step n adds wave[n] (n < wlen)
+    long long wlen;
+    int si, sj, sk, scomp;         // source cell and component 0..2 (si < 0: none)
+    const Sample3* samp;           // probe and monitor cells
+    int n_samp;
+    const int* s_off;              // per CTA: [s_off[b], s_off[b + 1]) of s_idx
+    const int* s_idx;              // samples each CTA owns, by CTA
+    float* rec;                    // rec[n * n_samp + slot]
+    int n_mon;                     // plane monitors (<= MAXP2)
+    int mon_k[MAXP2], mon_mask[MAXP2], mon_nf[MAXP2];
+    const double* mon_f[MAXP2];
+    float4* mon_acc[MAXP2];
+    double dt;
+    long long n;                   // index of the first of the two steps
+};
+
+template <int TY, bool PML>
+constexpr size_t t2_smem() {
+    return ((size_t)NE2 * 3 * (TY + 4) * 32      // E ring [NE2][3][TY + 4][32]
+            + (size_t)4 * (TY + 3) * 2 * 32      // H1 rows, E1 rows (two parities), H2 rows
+            + 256                                // coefficient table
+            + 128                                // x-profiles of the 128 columns
+            + MAXP2 * 8                          // twiddles [MAXP2][16] float2
+            + (PML ? (size_t)12 * (TY + 3) * 32 : 0)) * sizeof(float4);   // x-slab psi, per thread
+}
+
+__device__ __forceinline__ float4 f4sub(const float4 a, const float4 b) {
+    return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
+__device__ __forceinline__ float4 f4add(const float4 a, const float4 b) {
+    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ float4 f4keep(const float4 v, unsigned m) {
+    return make_float4((m & 1u) ? v.x : 0.f, (m & 2u) ? v.y : 0.f, (m & 4u) ? v.z : 0.f, (m & 8u) ? v.w : 0.f);
+}
+__device__ __forceinline__ float4 f4bc(float a) { return make_float4(a, a, a, a); }
+// psi <- b psi + c d for the cells whose bit is set in `upd` (the others keep psi)
+__device__ __forceinline__ float4 psi_next(const float4 p, const float4 b, const float4 c, const float4 d, unsigned upd) {
+    float4 v;
+    v.x = (upd & 1u) ? b.x * p.x + c.x * d.x : p.x;
+    v.y = (upd & 2u) ? b.y * p.y + c.y * d.y : p.y;
+    v.z = (upd & 4u) ? b.z * p.z + c.z * d.z : p.z;
+    v.w = (upd & 8u) ? b.w * p.w + c.w * d.w : p.w;
+    return v;
+}
+// stores the cells of v whose bit is set in m (all four: one 16-byte store)
+__device__ __forceinline__ void st4m(float* base, size_t g, const float4 v, unsigned m) {
+    if (m == 15u) {
+        *reinterpret_cast<float4*>(base + g) = v;
+    } else if (m) {
+        if (m & 1u) base[g] = v.x;
+        if (m & 2u) base[g + 1] = v.y;
+        if (m & 4u) base[g + 2] = v.z;
+        if (m & 8u) base[g + 3] = v.w;
+    }
+}
+__device__ __forceinline__ float4 ld4(const float* base, size_t g) { return *reinterpret_cast<const float4*>(base + g); }
+
+template <int TY, bool PML>
+__global__ void __launch_bounds__((TY + 3) * 32, 1) k_yee3d_t2(Dev3 S, Bufs3 B, Extra2 X, int segz, const int* tiles,
+                                                                  int gx, int gy) {
+    constexpr int NW = TY + 3, ER = TY + 4, NT = NW * 32;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ float4 sm4[];
+    float4* ring = sm4;                                      // [NE2][3][ER][32]
+    float4* bH1 = ring + NE2 * 3 * ER * 32;                  // [NW][2][32]: Hx, Hz of step 1
+    float4* bE1 = bH1 + NW * 2 * 32;                         // [2][NW][2][32]: Ez, Ex of step 1 by plane parity
+    float4* bH2 = bE1 + 2 * NW * 2 * 32;                     // [NW][2][32]: Hx, Hz of step 2
+    float4* coef_s = bH2 + NW * 2 * 32;                      // [256]
+    float* Xp = reinterpret_cast<float*>(coef_s + 256);      // [4][128]: bHx cHx bEx cEx
+    float2* tw = reinterpret_cast<float2*>(Xp + 4 * 128);    // [MAXP2][16]
+    // x-slab lanes' CPML auxiliaries (HYX HZX EYX EZX), each thread its own
+    // column: the next plane's stored values (cp.async, one plane ahead) and the
+    // first step's values by plane parity
+    float4* px0 = reinterpret_cast<float4*>(tw + MAXP2 * 16);   // [4][NT]
+    float4* px1 = px0 + 4 * NT;                                 // [2][4][NT]
+
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, tid = threadIdx.x;
+    // this CTA's tile of the (gx, gy, planes / segz) tiling, from the list
+    const int tile = tiles[blockIdx.x];
+    const int bx = tile % gx, by = (tile / gx) % gy, bz = tile / (gx * gy);
+    const int xo = bx * TX2, yo = by * TY;
+    const int kA = bz * segz, kB = min(kA + segz, S.nz);
+    const int pitch = S.pitch, rows = S.rows, nx = S.nx, ny = S.ny, nz = S.nz;
+    const int r = yo - 2 + w;                  // this warp's row
+    const int xc = xo - 4 + 4 * lane;          // first of this lane's cells
+    const bool jin = r >= 0 && r < ny;
+    unsigned xm = 0, xi1 = 0;                  // cells inside the grid; and with i >= 1
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        xm |= (xc + c >= 0 && xc + c < nx) ? (1u << c) : 0u;
+        xi1 |= (xc + c >= 1 && xc + c < nx) ? (1u << c) : 0u;
+    }
+    const bool own_row = w >= 2 && w <= TY + 1 && r < ny;
+    const unsigned own_x = (lane >= 1 && lane <= 30) ? xm : 0u;
+    const int npml = S.has_pml;
+    const bool pml = PML && npml > 0;
+    const P3 pr{S.prof, pitch, rows, S.planes};
+    for (int q = tid; q < 256; q += NT) coef_s[q] = S.coef[q];
+    if (pml)
+        for (int q = tid; q < 4 * 128; q += NT) {
+            const int a = q >> 7, c = xo - 4 + (q & 127);
+            const bool in = c >= 0 && c < nx;
+            Xp[q] = !in ? 0.f : (a == 0 ? pr.bHx(c + PX3) : a == 1 ? pr.cHx(c + PX3) : a == 2 ? pr.bEx(c + PX3) : pr.cEx(c + PX3));
+        }
+    if (tid < MAXP2 * 16) {
+        const int m = tid >> 4, f = tid & 15;
+        if (m < X.n_mon && f < X.mon_nf[m]) {
+            // the first step's twiddle dt e^{-i 2 pi f (n + 1) dt}, FP64 phase
+            double ph = X.mon_f[m][f] * X.dt * (double)(X.n + 1);
+            ph -= floor(ph);
+            double sn, cs;
+            sincospi(2.0 * ph, &sn, &cs);
+            tw[tid] = make_float2((float)cs * (float)X.dt, -(float)sn * (float)X.dt);
+        }
+    }
+    const int sb0 = X.s_off ? X.s_off[tile] : 0, sb1 = X.s_off ? X.s_off[tile + 1] : 0;
+
+    // CPML reach (conservative; the profiles decide cell by cell)
+    const bool lane_px = pml && xm != 0 && (xc - 1 < npml + 1 || xc + 4 >= nx - npml - 1);
+    const bool row_py = pml && jin && (r < npml + 1 || r >= ny - npml - 1);
+    const float hby = row_py ? pr.bHy(r + 1) : 0.f, hcy = row_py ? pr.cHy(r + 1) : 0.f;
+    const float eby = row_py ? pr.bEy(r + 1) : 0.f, ecy = row_py ? pr.cEy(r + 1) : 0.f;
+
+    const int kf = kA - 2;
+    auto gidx = [&](int p) { return ((size_t)(p + 1) * rows + (r + 1)) * pitch + xc + PX3; };
+    // E0(p), rows yo-2 .. yo+TY+1, columns xo-4 .. xo+123, into ring slot
+    // (p - kf) % NE2; rows and planes outside the padded array and columns past
+    // the right pad read as zeros
+    auto issue = [&](int p) {
+        if (p > kB + 1) return;
+        float4* dst = ring + (size_t)((p - kf) & (NE2 - 1)) * 3 * ER * 32;
+        const bool pin = p >= -1 && p <= nz;
+        for (int e = tid; e < 3 * ER * 32; e += NT) {
+            const int v = e & 31, cr = e >> 5;
+            const int comp = cr / ER, jj = yo - 2 + (cr - comp * ER);
+            const bool in = pin && jj >= -1 && jj <= ny && xo - 4 + 4 * v <= nx;
+            const float* src = in ? B.in[G_EX + comp] + ((size_t)(p + 1) * rows + (jj + 1)) * pitch + xo - 4 + 4 * v + PX3
+                                  : B.in[G_EX];
+            cpa16(dst + e, src, in);
+        }
+    };
+    auto load_h = [&](int p, float4& hx, float4& hy, float4& hz, uint32_t& m) {
+        hx = hy = hz = make_float4(0.f, 0.f, 0.f, 0.f);
+        m = 0;
+        if (!jin || p < 0 || p >= nz || p > kB || xm == 0) return;
+        const size_t g = gidx(p);
+        hx = ld4(B.in[G_HX], g);
+        hy = ld4(B.in[G_HY], g);
+        hz = ld4(B.in[G_HZ], g);
+        m = *reinterpret_cast<const uint32_t*>(S.mat + g);
+    };
+    auto issue_pxh = [&](int p) {   // HYX, HZX of plane p (x-slab lanes)
+        if (!PML || !lane_px || !jin || p < 0 || p >= nz || p > kB) return;
+        const size_t g = gidx(p);
+        cpa16(px0 + 0 * NT + tid, B.in[P_HYX] + g, true);
+        cpa16(px0 + 1 * NT + tid, B.in[P_HZX] + g, true);
+    };
+    auto issue_pxe = [&](int p) {   // EYX, EZX of plane p (x-slab lanes)
+        if (!PML || !lane_px || !jin || p < 0 || p >= nz || p > kB) return;
+        const size_t g = gidx(p);
+        cpa16(px0 + 2 * NT + tid, B.in[P_EYX] + g, true);
+        cpa16(px0 + 3 * NT + tid, B.in[P_EZX] + g, true);
+    };
+
+    // cp.async groups, oldest first, as every iteration q leaves them:
+    //   CPML build:  E0(q + 2) | x-psi H(q) | x-psi E(q) | E0(q + 3) | x-psi H(q + 1)
+    //   otherwise:   E0(q + 2) | E0(q + 3)
+    // (the prologue starts the same sequence with E0 planes kf and kf + 1 first)
+    issue(kf);
+    issue(kf + 1);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    issue(kf + 2);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    if constexpr (PML) {
+        issue_pxh(kf);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        issue_pxe(kf);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    issue(kf + 3);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    // the state one iteration hands the next: H0 and material of plane q, the
+    // material of plane q - 1, H1(q - 1), E1(q - 1) and H2(q - 2)
+    struct St2 {
+        float4 hx, hy, hz;
+        uint32_t m, mp;
+        float4 h1x, h1y, h1z, e1x, e1y, e1z, h2x, h2y;
+    };
+    St2 s0, s1;
+    load_h(kf, s0.hx, s0.hy, s0.hz, s0.m);
+    s0.mp = 0;
+    s0.h1x = s0.h1y = s0.h1z = s0.e1x = s0.e1y = s0.e1z = s0.h2x = s0.h2y = z4;
+    float4 pm[PML ? 2 : 1][PML ? 8 : 1];       // step-1 y and z CPML auxiliaries by plane parity
+    asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+    __syncthreads();
+    const float cdx = S.cdx, cdy = S.cdy, cdz = S.cdz;
+
+    auto body = [&](const int q, const St2& A, St2& Bn) {
+        load_h(q + 1, Bn.hx, Bn.hy, Bn.hz, Bn.m);
+        const float4* Ec = ring + (size_t)((q - kf) & (NE2 - 1)) * 3 * ER * 32;
+        const float4* En = ring + (size_t)((q + 1 - kf) & (NE2 - 1)) * 3 * ER * 32;
+        const bool kin1 = q >= 0 && q < nz;
+        const unsigned dom1 = (jin && kin1) ? xm : 0u;
+        const bool kz1 = pml && kin1 && (q < npml + 1 || q >= nz - npml - 1);
+        const bool psi1 = pml && dom1 && (lane_px || row_py || kz1);
+        float4* pm1 = pm[PML ? (q & 1) : 0];
+
+        float4* px1q = px1 + (size_t)(q & 1) * 4 * NT + tid;
+        if constexpr (PML) asm volatile("cp.async.wait_group 2;\n" ::: "memory");   // x-psi H(q)
+
+        // ---- step 1, layer 1: H1(q) of row r ----
+        const float4 ex = Ec[(0 * ER + w) * 32 + lane], ey = Ec[(1 * ER + w) * 32 + lane];
+        const float4 ez = Ec[(2 * ER + w) * 32 + lane];
+        float4 h1x, h1y, h1z;
+        {
+            const float4 ezu = Ec[(2 * ER + w + 1) * 32 + lane], exu = Ec[(0 * ER + w + 1) * 32 + lane];
+            const float4 eyk = En[(1 * ER + w) * 32 + lane], exk = En[(0 * ER + w) * 32 + lane];
+            const float ezr = __shfl_down_sync(FULL, ez.x, 1), eyr = __shfl_down_sync(FULL, ey.x, 1);
+            float4 dezy = f4sub(ezu, ez), deyz = f4sub(eyk, ey), dexz = f4sub(exk, ex), dexy = f4sub(exu, ex);
+            float4 dezx = make_float4(ez.y - ez.x, ez.z - ez.y, ez.w - ez.z, ezr - ez.w);
+            float4 deyx = make_float4(ey.y - ey.x, ey.z - ey.y, ey.w - ey.z, eyr - ey.w);
+            if (psi1) {
+                const size_t g = gidx(q);
+                if (row_py) {
+                    const float4 b4 = f4bc(hby), c4 = f4bc(hcy);
+                    pm1[0] = psi_next(ld4(B.in[P_HXY], g), b4, c4, dezy, 15u);
+                    pm1[1] = psi_next(ld4(B.in[P_HZY], g), b4, c4, dexy, 15u);
+                    dezy = f4add(dezy, pm1[0]);
+                    dexy = f4add(dexy, pm1[1]);
+                }
+                if (kz1) {
+                    const float4 b4 = f4bc(pr.bHz(q + 1)), c4 = f4bc(pr.cHz(q + 1));
+                    pm1[2] = psi_next(ld4(B.in[P_HXZ], g), b4, c4, deyz, 15u);
+                    pm1[3] = psi_next(ld4(B.in[P_HYZ], g), b4, c4, dexz, 15u);
+                    deyz = f4add(deyz, pm1[2]);
+                    dexz = f4add(dexz, pm1[3]);
+                }
+                if (lane_px) {
+                    const float4 b4 = *reinterpret_cast<const float4*>(Xp + 0 * 128 + 4 * lane);
+                    const float4 c4 = *reinterpret_cast<const float4*>(Xp + 1 * 128 + 4 * lane);
+                    const float4 v4 = psi_next(px0[0 * NT + tid], b4, c4, dezx, 15u);
+                    const float4 v5 = psi_next(px0[1 * NT + tid], b4, c4, deyx, 15u);
+                    px1q[0 * NT] = v4;
+                    px1q[1 * NT] = v5;
+                    dezx = f4add(dezx, v4);
+                    deyx = f4add(deyx, v5);
+                }
+            }
+            h1x = make_float4(A.hx.x - (cdy * dezy.x - cdz * deyz.x), A.hx.y - (cdy * dezy.y - cdz * deyz.y),
+                              A.hx.z - (cdy * dezy.z - cdz * deyz.z), A.hx.w - (cdy * dezy.w - cdz * deyz.w));
+            h1y = make_float4(A.hy.x - (cdz * dexz.x - cdx * dezx.x), A.hy.y - (cdz * dexz.y - cdx * dezx.y),
+                              A.hy.z - (cdz * dexz.z - cdx * dezx.z), A.hy.w - (cdz * dexz.w - cdx * dezx.w));
+            h1z = make_float4(A.hz.x - (cdx * deyx.x - cdy * dexy.x), A.hz.y - (cdx * deyx.y - cdy * dexy.y),
+                              A.hz.z - (cdx * deyx.z - cdy * dexy.z), A.hz.w - (cdx * deyx.w - cdy * dexy.w));
+            h1x = f4keep(h1x, dom1);
+            h1y = f4keep(h1y, dom1);
+            h1z = f4keep(h1z, dom1);
+        }
+        bH1[(w * 2 + 0) * 32 + lane] = h1x;
+        bH1[(w * 2 + 1) * 32 + lane] = h1z;
+        if constexpr (PML) {
+            issue_pxh(q + 1);
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+        }
+        __syncthreads();
+        if constexpr (PML) asm volatile("cp.async.wait_group 2;\n" ::: "memory");   // x-psi E(q)
+
+        // ---- step 1, layer 2: E1(q) of rows yo-1 .. yo+TY ----
+        float4 e1x = ex, e1y = ey, e1z = ez;
+        if (w >= 1) {
+            const float4 hxd = bH1[((w - 1) * 2 + 0) * 32 + lane], hzd = bH1[((w - 1) * 2 + 1) * 32 + lane];
+            const float hyl = __shfl_up_sync(FULL, h1y.w, 1), hzl = __shfl_up_sync(FULL, h1z.w, 1);
+            float4 dhzy = f4sub(h1z, hzd), dhyz = f4sub(h1y, A.h1y), dhxz = f4sub(h1x, A.h1x), dhxy = f4sub(h1x, hxd);
+            float4 dhzx = make_float4(h1z.x - hzl, h1z.y - h1z.x, h1z.z - h1z.y, h1z.w - h1z.z);
+            float4 dhyx = make_float4(h1y.x - hyl, h1y.y - h1y.x, h1y.z - h1y.y, h1y.w - h1y.z);
+            // Ex needs j, k >= 1; Ey i, k >= 1; Ez i, j >= 1 (the rest are PEC walls)
+            const unsigned mex = (r >= 1 && q >= 1) ? dom1 : 0u, mey = q >= 1 ? (dom1 ? xi1 : 0u) : 0u;
+            const unsigned mez = r >= 1 ? (dom1 ? xi1 : 0u) : 0u;
+            if (psi1) {
+                const size_t g = gidx(q);
+                if (row_py) {
+                    const float4 b4 = f4bc(eby), c4 = f4bc(ecy);
+                    pm1[4] = psi_next(ld4(B.in[P_EXY], g), b4, c4, dhzy, mex);
+                    pm1[5] = psi_next(ld4(B.in[P_EZY], g), b4, c4, dhxy, mez);
+                    dhzy = f4add(dhzy, pm1[4]);
+                    dhxy = f4add(dhxy, pm1[5]);
+                }
+                if (kz1) {
+                    const float4 b4 = f4bc(pr.bEz(q + 1)), c4 = f4bc(pr.cEz(q + 1));
+                    pm1[6] = psi_next(ld4(B.in[P_EXZ], g), b4, c4, dhyz, mex);
+                    pm1[7] = psi_next(ld4(B.in[P_EYZ], g), b4, c4, dhxz, mey);
+                    dhyz = f4add(dhyz, pm1[6]);
+                    dhxz = f4add(dhxz, pm1[7]);
+                }
+                if (lane_px) {
+                    const float4 b4 = *reinterpret_cast<const float4*>(Xp + 2 * 128 + 4 * lane);
+                    const float4 c4 = *reinterpret_cast<const float4*>(Xp + 3 * 128 + 4 * lane);
+                    const float4 va = psi_next(px0[2 * NT + tid], b4, c4, dhzx, mey);
+                    const float4 vb = psi_next(px0[3 * NT + tid], b4, c4, dhyx, mez);
+                    px1q[2 * NT] = va;
+                    px1q[3 * NT] = vb;
+                    dhzx = f4add(dhzx, va);
+                    dhyx = f4add(dhyx, vb);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const float4 co = coef_s[(A.m >> (8 * c)) & 255u];
+                if (mex & (1u << c)) f4s(e1x, c, co.x * f4c(ex, c) + co.z * f4c(dhzy, c) - co.w * f4c(dhyz, c));
+                if (mey & (1u << c)) f4s(e1y, c, co.x * f4c(ey, c) + co.w * f4c(dhxz, c) - co.y * f4c(dhzx, c));
+                if (mez & (1u << c)) f4s(e1z, c, co.x * f4c(ez, c) + co.y * f4c(dhyx, c) - co.z * f4c(dhxy, c));
+            }
+            // the first step's source, in every CTA that computes its cell
+            if (X.si >= xc && X.si < xc + 4 && r == X.sj && q == X.sk && X.n < X.wlen) {
+                const float s = X.wave[X.n];
+                const int c = X.si - xc;
+                if (X.scomp == 0) f4s(e1x, c, f4c(e1x, c) + s);
+                else if (X.scomp == 1) f4s(e1y, c, f4c(e1y, c) + s);
+                else f4s(e1z, c, f4c(e1z, c) + s);
+            }
+            float4* be = bE1 + (size_t)(((q - kf) & 1) * NW + w) * 2 * 32;
+            be[lane] = e1z;
+            be[32 + lane] = e1x;
+        }
+        // the first step's probe and monitor cells this CTA owns
+        for (int s = sb0; s < sb1; s++) {
+            const Sample3 sp = X.samp[X.s_idx[s]];
+            if (sp.k == q && sp.j == r && sp.i >= xc && sp.i < xc + 4) {
+                const int c = sp.i - xc;
+                const float4 v = sp.comp == G_EX ? e1x : sp.comp == G_EY ? e1y : sp.comp == G_EZ ? e1z
+                               : sp.comp == G_HX ? h1x : sp.comp == G_HY ? h1y : h1z;
+                X.rec[X.n * X.n_samp + sp.slot] = f4c(v, c);
+            }
+        }
+        // the first step's plane DFT over the owned cells
+        if (X.n_mon > 0 && own_row && own_x && q >= kA && q < kB) {
+            const size_t plane = (size_t)nx * ny;
+            for (int m = 0; m < X.n_mon; m++) {
+                if (X.mon_k[m] != q) continue;
+                const int nf = X.mon_nf[m];
+                int pc = 0;
+                for (int comp = 0; comp < 3; comp++) {
+                    if (!(X.mon_mask[m] & (1 << comp))) continue;
+                    const float4 v = comp == 0 ? e1x : comp == 1 ? e1y : e1z;
+                    for (int c = 0; c < 4; c++) {
+                        if (!(own_x & (1u << c))) continue;
+                        const float e = f4c(v, c);
+                        const size_t cell = (size_t)r * nx + xc + c;
+                        for (int f = 0; f < nf; f++) {
+                            float4* ap = X.mon_acc[m] + ((size_t)pc * nf + f) * plane + cell;
+                            float4 a = *ap;
+                            const float2 t = tw[m * 16 + f];
+                            kahan3(a.x, a.z, e * t.x);
+                            kahan3(a.y, a.w, e * t.y);
+                            *ap = a;
+                        }
+                    }
+                    pc++;
+                }
+            }
+        }
+
+        // ---- step 2, layer 1: H2(q - 1) of rows yo-1 .. yo+TY-1 ----
+        const int p2 = q - 1;
+        const bool kin2 = p2 >= 0 && p2 < nz;
+        const unsigned dom2 = (jin && kin2) ? xm : 0u;
+        const bool kz2 = pml && kin2 && (p2 < npml + 1 || p2 >= nz - npml - 1);
+        const bool psi2 = pml && dom2 && (lane_px || row_py || kz2);
+        const unsigned om = (own_row && p2 >= kA) ? own_x : 0u;   // cells of plane p2 this CTA stores
+        const float4* pm2 = pm[PML ? (p2 & 1) : 0];
+        const float4* px2 = px1 + (size_t)(p2 & 1) * 4 * NT + tid;   // x-slab psi of step 1 at plane p2
+        float4 h2x = z4, h2y = z4, h2z = z4;
+        const bool do_h2 = w >= 1 && w <= TY + 1 && q >= kA;
+        if (do_h2) {
+            const float4* be = bE1 + (size_t)(((p2 - kf) & 1) * NW + w + 1) * 2 * 32;
+            const float4 ezu = be[lane], exu = be[32 + lane];
+            const float ezr = __shfl_down_sync(FULL, A.e1z.x, 1), eyr = __shfl_down_sync(FULL, A.e1y.x, 1);
+            float4 dezy = f4sub(ezu, A.e1z), deyz = f4sub(e1y, A.e1y), dexz = f4sub(e1x, A.e1x), dexy = f4sub(exu, A.e1x);
+            float4 dezx = make_float4(A.e1z.y - A.e1z.x, A.e1z.z - A.e1z.y, A.e1z.w - A.e1z.z, ezr - A.e1z.w);
+            float4 deyx = make_float4(A.e1y.y - A.e1y.x, A.e1y.z - A.e1y.y, A.e1y.w - A.e1y.z, eyr - A.e1y.w);
+            if (psi2) {
+                const size_t g = gidx(p2);
+                if (row_py) {
+                    const float4 b4 = f4bc(hby), c4 = f4bc(hcy);
+                    const float4 v0 = psi_next(pm2[0], b4, c4, dezy, 15u), v1 = psi_next(pm2[1], b4, c4, dexy, 15u);
+                    st4m(B.out[P_HXY], g, v0, om);
+                    st4m(B.out[P_HZY], g, v1, om);
+                    dezy = f4add(dezy, v0);
+                    dexy = f4add(dexy, v1);
+                }
+                if (kz2) {
+                    const float4 b4 = f4bc(pr.bHz(p2 + 1)), c4 = f4bc(pr.cHz(p2 + 1));
+                    const float4 v2 = psi_next(pm2[2], b4, c4, deyz, 15u), v3 = psi_next(pm2[3], b4, c4, dexz, 15u);
+                    st4m(B.out[P_HXZ], g, v2, om);
+                    st4m(B.out[P_HYZ], g, v3, om);
+                    deyz = f4add(deyz, v2);
+                    dexz = f4add(dexz, v3);
+                }
+                if (lane_px) {
+                    const float4 b4 = *reinterpret_cast<const float4*>(Xp + 0 * 128 + 4 * lane);
+                    const float4 c4 = *reinterpret_cast<const float4*>(Xp + 1 * 128 + 4 * lane);
+                    const float4 v4 = psi_next(px2[0 * NT], b4, c4, dezx, 15u), v5 = psi_next(px2[1 * NT], b4, c4, deyx, 15u);
+                    st4m(B.out[P_HYX], g, v4, om);
+                    st4m(B.out[P_HZX], g, v5, om);
+                    dezx = f4add(dezx, v4);
+                    deyx = f4add(deyx, v5);
+                }
+            }
+            h2x = make_float4(A.h1x.x - (cdy * dezy.x - cdz * deyz.x), A.h1x.y - (cdy * dezy.y - cdz * deyz.y),
+                              A.h1x.z - (cdy * dezy.z - cdz * deyz.z), A.h1x.w - (cdy * dezy.w - cdz * deyz.w));
+            h2y = make_float4(A.h1y.x - (cdz * dexz.x - cdx * dezx.x), A.h1y.y - (cdz * dexz.y - cdx * dezx.y),
+                              A.h1y.z - (cdz * dexz.z - cdx * dezx.z), A.h1y.w - (cdz * dexz.w - cdx * dezx.w));
+            h2z = make_float4(A.h1z.x - (cdx * deyx.x - cdy * dexy.x), A.h1z.y - (cdx * deyx.y - cdy * dexy.y),
+                              A.h1z.z - (cdx * deyx.z - cdy * dexy.z), A.h1z.w - (cdx * deyx.w - cdy * dexy.w));
+            h2x = f4keep(h2x, dom2);
+            h2y = f4keep(h2y, dom2);
+            h2z = f4keep(h2z, dom2);
+            bH2[(w * 2 + 0) * 32 + lane] = h2x;
+            bH2[(w * 2 + 1) * 32 + lane] = h2z;
+            if (om) {
+                const size_t g = gidx(p2);
+                st4m(B.out[G_HX], g, h2x, om);
+                st4m(B.out[G_HY], g, h2y, om);
+                st4m(B.out[G_HZ], g, h2z, om);
+            }
+        }
+        // planes q + 1 and q + 2 staged (four newer groups, one without the
+        // CPML, may still be in flight); then plane q's slot takes plane q + NE2
+        if constexpr (PML)
+            asm volatile("cp.async.wait_group 4;\n" ::: "memory");
+        else
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        __syncthreads();
+        if constexpr (PML) {
+            issue_pxe(q + 1);
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+        }
+        issue(q + NE2);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+
+        // ---- step 2, layer 2: E2(q - 1) of the owned rows ----
+        if (w >= 2 && w <= TY + 1 && p2 >= kA) {
+            const float4 hxd = bH2[((w - 1) * 2 + 0) * 32 + lane], hzd = bH2[((w - 1) * 2 + 1) * 32 + lane];
+            const float hyl = __shfl_up_sync(FULL, h2y.w, 1), hzl = __shfl_up_sync(FULL, h2z.w, 1);
+            float4 dhzy = f4sub(h2z, hzd), dhyz = f4sub(h2y, A.h2y), dhxz = f4sub(h2x, A.h2x), dhxy = f4sub(h2x, hxd);
+            float4 dhzx = make_float4(h2z.x - hzl, h2z.y - h2z.x, h2z.z - h2z.y, h2z.w - h2z.z);
+            float4 dhyx = make_float4(h2y.x - hyl, h2y.y - h2y.x, h2y.z - h2y.y, h2y.w - h2y.z);
+            const unsigned mex = (r >= 1 && p2 >= 1) ? dom2 : 0u, mey = p2 >= 1 ? (dom2 ? xi1 : 0u) : 0u;
+            const unsigned mez = r >= 1 ? (dom2 ? xi1 : 0u) : 0u;
+            if (psi2) {
+                const size_t g = gidx(p2);
+                if (row_py) {
+                    const float4 b4 = f4bc(eby), c4 = f4bc(ecy);
+                    const float4 v6 = psi_next(pm2[4], b4, c4, dhzy, mex), v7 = psi_next(pm2[5], b4, c4, dhxy, mez);
+                    st4m(B.out[P_EXY], g, v6, om);
+                    st4m(B.out[P_EZY], g, v7, om);
+                    dhzy = f4add(dhzy, v6);
+                    dhxy = f4add(dhxy, v7);
+                }
+                if (kz2) {
+                    const float4 b4 = f4bc(pr.bEz(p2 + 1)), c4 = f4bc(pr.cEz(p2 + 1));
+                    const float4 v8 = psi_next(pm2[6], b4, c4, dhyz, mex), v9 = psi_next(pm2[7], b4, c4, dhxz, mey);
+                    st4m(B.out[P_EXZ], g, v8, om);
+                    st4m(B.out[P_EYZ], g, v9, om);
+                    dhyz = f4add(dhyz, v8);
+                    dhxz = f4add(dhxz, v9);
+                }
+                if (lane_px) {
+                    const float4 b4 = *reinterpret_cast<const float4*>(Xp + 2 * 128 + 4 * lane);
+                    const float4 c4 = *reinterpret_cast<const float4*>(Xp + 3 * 128 + 4 * lane);
+                    const float4 va = psi_next(px2[2 * NT], b4, c4, dhzx, mey), vb = psi_next(px2[3 * NT], b4, c4, dhyx, mez);
+                    st4m(B.out[P_EYX], g, va, om);
+                    st4m(B.out[P_EZX], g, vb, om);
+                    dhzx = f4add(dhzx, va);
+                    dhyx = f4add(dhyx, vb);
+                }
+            }
+            float4 e2x = A.e1x, e2y = A.e1y, e2z = A.e1z;
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const float4 co = coef_s[(A.mp >> (8 * c)) & 255u];
+                if (mex & (1u << c)) f4s(e2x, c, co.x * f4c(A.e1x, c) + co.z * f4c(dhzy, c) - co.w * f4c(dhyz, c));
+                if (mey & (1u << c)) f4s(e2y, c, co.x * f4c(A.e1y, c) + co.w * f4c(dhxz, c) - co.y * f4c(dhzx, c));
+                if (mez & (1u << c)) f4s(e2z, c, co.x * f4c(A.e1z, c) + co.y * f4c(dhyx, c) - co.z * f4c(dhxy, c));
+            }
+            if (om) {
+                const size_t g = gidx(p2);
+                st4m(B.out[G_EX], g, e2x, om);
+                st4m(B.out[G_EY], g, e2y, om);
+                st4m(B.out[G_EZ], g, e2z, om);
+            }
+        }
+        Bn.h2x = h2x;
+        Bn.h2y = h2y;
+        Bn.h1x = h1x; Bn.h1y = h1y; Bn.h1z = h1z;
+        Bn.e1x = e1x; Bn.e1y = e1y; Bn.e1z = e1z;
+        Bn.mp = A.m;
+    };
+    for (int q = kf; q <= kB; q++) {
+        body(q, s0, s1);
+        s0 = s1;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+
 __global__ void k_finite3(Dev3 S, int* bad) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -690,6 +1234,12 @@ void scene3_free(Scene3* s) {
     if (s->d_src) cudaFree(s->d_src);
     if (s->d_samp) cudaFree(s->d_samp);
     if (s->d_rec) cudaFree(s->d_rec);
+    if (s->d_s2off) cudaFree(s->d_s2off);
+    if (s->d_s2idx) cudaFree(s->d_s2idx);
+    if (s->d_s2tiles) cudaFree(s->d_s2tiles);
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
+    if (s->aux) cudaStreamDestroy(s->aux);
     delete s;
 }
 
@@ -743,6 +1293,7 @@ int ensure3(fdtd_ctx* c, int64_t t_end) {
                                 cudaMemcpyHostToDevice, c->stream), "samples");
         CK3(cudaStreamSynchronize(c->stream), "samples");
         s->samp_dirty = false;
+        s->s2_seg = -1;
     }
     return FDTD_OK;
 }
@@ -802,11 +1353,15 @@ int fdtd_create3(const fdtd_grid* g, double dx, double dt, double courant, const
     for (int q = 0; q < G_COUNT; q++) s->f[q] = s->g[q] = nullptr;
     s->d_mat = nullptr; s->d_coef = nullptr; s->d_prof = nullptr; s->d_src = nullptr; s->d_samp = nullptr;
     s->d_rec = nullptr;
+    s->d_s2off = nullptr; s->d_s2idx = nullptr; s->d_s2tiles = nullptr; s->n_s2int = s->n_s2pml = 0; s->s2_seg = -1;
+    s->aux = nullptr; s->ev_fork = s->ev_join = nullptr;
     s->nx = g->nx; s->ny = g->ny; s->nz = g->nz; s->npml = npml;
     s->dx = dx; s->dy = dy; s->dz = dz; s->dt = dt;
     // room for the unfused kernels' neighbours and the fused kernel's last tile,
     // whose staged rows reach cell x0 + TXC + 3 (storage column x0 + TXC + 3 + PX3)
-    s->pitch = (std::max(g->nx + PX3 + 40, (g->nx + TXC - 1) / TXC * TXC + PX3 + 8) + 31) / 32 * 32;
+    // and the two-step kernel's last tile, whose lanes reach cell 120 ntx + 3
+    s->pitch = (std::max(std::max(g->nx + PX3 + 40, (g->nx + TXC - 1) / TXC * TXC + PX3 + 8),
+                         (g->nx + TX2 - 1) / TX2 * TX2 + PX3 + 8) + 31) / 32 * 32;
     s->rows = g->ny + 2;
     s->planes = g->nz + 2;
     s->src_kind = -1; s->src_i = s->src_j = s->src_k = -1; s->src_comp = G_EZ; s->src_param = 0; s->src_cap = 0;
@@ -959,6 +1514,66 @@ int fdtd_add_dft_plane3(fdtd_ctx* c, int k, int comp_mask, const double* freqs, 
     return FDTD_OK;
 }
 
+// samples by owning CTA of the two-step kernel's tiling (TX2 x T2_ROWS x segz)
+static int build_s2(fdtd_ctx* c, Scene3* s, int segz, const dim3& g2) {
+    if (s->s2_seg == segz) return FDTD_OK;
+    const int ncta = (int)(g2.x * g2.y * g2.z);
+    std::vector<int> cnt((size_t)ncta + 1, 0), idx(std::max<size_t>(1, s->samples.size()));
+    auto cta_of = [&](const Sample3& sp) {
+        return (int)(sp.i / TX2 + g2.x * (sp.j / T2_ROWS + g2.y * (sp.k / segz)));
+    };
+    for (const Sample3& sp : s->samples) cnt[cta_of(sp) + 1]++;
+    for (int b = 0; b < ncta; b++) cnt[b + 1] += cnt[b];
+    std::vector<int> pos(cnt.begin(), cnt.end() - 1);
+    for (size_t q = 0; q < s->samples.size(); q++) idx[pos[cta_of(s->samples[q])]++] = (int)q;
+    // a tile needs the CPML build when a lane, row or plane of its two-step
+    // footprint meets the kernel's (conservative) CPML reach
+    const int np = s->npml;
+    auto reach = [&](int v, int n) { return v >= 0 && v < n && (v < np + 1 || v >= n - np - 1); };
+    std::vector<int> tint, tpml;
+    for (int t = 0; t < ncta; t++) {
+        const int bx = t % (int)g2.x, by = (t / (int)g2.x) % (int)g2.y, bz = t / (int)(g2.x * g2.y);
+        bool p = false;
+        if (np > 0) {
+            for (int l = 0; l < 32 && !p; l++) {
+                const int xc = bx * TX2 - 4 + 4 * l;
+                p = xc + 3 >= 0 && xc < s->nx && (xc - 1 < np + 1 || xc + 4 >= s->nx - np - 1);
+            }
+            for (int r = by * T2_ROWS - 2; r <= by * T2_ROWS + T2_ROWS && !p; r++) p = reach(r, s->ny);
+            for (int k = bz * segz - 2; k <= std::min(bz * segz + segz, s->nz) && !p; k++) p = reach(k, s->nz);
+        }
+        (p ? tpml : tint).push_back(t);
+    }
+    s->n_s2int = (int)tint.size();
+    s->n_s2pml = (int)tpml.size();
+    tint.insert(tint.end(), tpml.begin(), tpml.end());
+    if (s->d_s2off) cudaFree(s->d_s2off);
+    if (s->d_s2idx) cudaFree(s->d_s2idx);
+    if (s->d_s2tiles) cudaFree(s->d_s2tiles);
+    s->d_s2off = s->d_s2idx = s->d_s2tiles = nullptr;
+    s->s2_seg = -1;
+    if (cudaMalloc(&s->d_s2off, cnt.size() * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&s->d_s2idx, idx.size() * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&s->d_s2tiles, tint.size() * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail3(c, FDTD_ENOMEM, "tables of the two-step kernel");
+    }
+    if (!s->aux) {
+        if (cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return fail3(c, FDTD_ECUDA, "second stream of the two-step kernel");
+        }
+    }
+    CK3(cudaMemcpyAsync(s->d_s2off, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream), "samples");
+    CK3(cudaMemcpyAsync(s->d_s2idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream), "samples");
+    CK3(cudaMemcpyAsync(s->d_s2tiles, tint.data(), tint.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream), "tiles");
+    CK3(cudaStreamSynchronize(c->stream), "samples");
+    s->s2_seg = segz;
+    return FDTD_OK;
+}
+
 int fdtd_step3(fdtd_ctx* c, int64_t n_steps) {
     Scene3* s = S3(c);
     if (!s) return fail3(c, FDTD_ESTATE, "no 3D scene");
@@ -972,41 +1587,118 @@ int fdtd_step3(fdtd_ctx* c, int64_t n_steps) {
     const int segz = std::max(1, c->opt_segment);
     const dim3 gfz((s->nx + TXC - 1) / TXC, (s->ny + TYR - 1) / TYR, (s->nz + segz - 1) / segz);
     const size_t smem3 = fused3_smem();
+    // the two-step kernel (FDTD_OPT_TBLOCK = 2) takes steps in pairs; it updates
+    // at most MAXP2 plane monitors itself
+    int n_plane = 0;
+    for (const DftMon& m : c->mons) n_plane += m.plane_k >= 0 ? 1 : 0;
+    const bool two = c->opt_kernel != 1 && c->opt_tblock == 2 && n_plane <= MAXP2 && n_steps >= 2;
+    const dim3 g2((s->nx + TX2 - 1) / TX2, (s->ny + T2_ROWS - 1) / T2_ROWS, (s->nz + segz - 1) / segz);
+    const size_t smem2i = t2_smem<T2_ROWS, false>(), smem2p = t2_smem<T2_ROWS, true>();
     if (c->opt_kernel != 1) {
         cudaError_t ea = ensure_dyn_smem((const void*)k_yee3d_fused, smem3);
+        if (ea == cudaSuccess && two) ea = ensure_dyn_smem((const void*)k_yee3d_t2<T2_ROWS, false>, smem2i);
+        if (ea == cudaSuccess && two && s->npml)
+            ea = ensure_dyn_smem((const void*)k_yee3d_t2<T2_ROWS, true>, smem2p);
         if (ea != cudaSuccess) return fail3(c, FDTD_ECUDA, "fused 3D kernel: %s", cudaGetErrorString(ea));
     }
-    for (int64_t q = 0; q < n_steps; q++) {
+    if (two) {
+        rc = build_s2(c, s, segz, g2);
+        if (rc) return rc;
+    }
+    auto swap_bufs = [&]() {
+        for (int w = 0; w < G_COUNT; w++) std::swap(s->f[w], s->g[w]);
+        d = dev_of(s);
+    };
+    auto bufs = [&]() {
+        Bufs3 b;
+        for (int w = 0; w < G_COUNT; w++) {
+            b.in[w] = s->f[w];
+            b.out[w] = s->g[w];
+        }
+        return b;
+    };
+    // after step n: the source, probes and plane DFT (src_rec: the kernel has
+    // not done them), then the cell monitors from the record
+    auto after = [&](long long n, bool src_rec) {
+        if (src_rec) {
+            if (si >= 0 || !s->samples.empty()) {
+                k_src_rec3<<<1, 128, 0, c->stream>>>(d, si, s->src_j, s->src_k, s->src_comp, s->d_src,
+                                                     s->src_kind >= 0 ? s->src_cap : 0, s->d_samp,
+                                                     (int)s->samples.size(), s->d_rec, n);
+                c->launches++;
+            }
+        }
+        for (const DftMon& m : c->mons) {
+            if (m.plane_k >= 0) {
+                if (!src_rec) continue;
+                k_dft_plane3<<<grp, blk, 0, c->stream>>>(d, m.plane_k, m.comp_mask, m.d_freq, m.n_freq, s->dt, m.d_acc, n);
+            } else {
+                k_dft_cells3<<<(m.n_cells * m.n_freq + 127) / 128, 128, 0, c->stream>>>(
+                    s->d_rec, (int)s->samples.size(), m.slot0, m.n_cells, m.d_freq, m.n_freq, s->dt, m.d_acc, n);
+            }
+            c->launches++;
+        }
+    };
+    for (int64_t q = 0; q < n_steps;) {
         const long long n = c->t + q;
+        if (two && q + 1 < n_steps) {
+            Extra2 x;
+            memset(&x, 0, sizeof(x));
+            x.wave = s->d_src;
+            x.wlen = s->src_kind >= 0 ? s->src_cap : 0;
+            x.si = si; x.sj = s->src_j; x.sk = s->src_k; x.scomp = s->src_comp - G_EX;
+            x.samp = s->d_samp;
+            x.n_samp = (int)s->samples.size();
+            x.s_off = s->samples.empty() ? nullptr : s->d_s2off;
+            x.s_idx = s->d_s2idx;
+            x.rec = s->d_rec;
+            for (const DftMon& m : c->mons)
+                if (m.plane_k >= 0) {
+                    x.mon_k[x.n_mon] = m.plane_k; x.mon_mask[x.n_mon] = m.comp_mask; x.mon_nf[x.n_mon] = m.n_freq;
+                    x.mon_f[x.n_mon] = m.d_freq; x.mon_acc[x.n_mon] = m.d_acc;
+                    x.n_mon++;
+                }
+            x.dt = s->dt;
+            x.n = n;
+            // tiles without CPML reach on the second stream, the others here
+            const Bufs3 b2 = bufs();
+            const int nthr = (T2_ROWS + 3) * 32;
+            const bool fork = s->n_s2int > 0 && s->n_s2pml > 0;
+            if (fork) {
+                CK3(cudaEventRecord(s->ev_fork, c->stream), "fork");
+                CK3(cudaStreamWaitEvent(s->aux, s->ev_fork, 0), "fork");
+            }
+            if (s->n_s2int > 0) {
+                k_yee3d_t2<T2_ROWS, false><<<s->n_s2int, nthr, smem2i, fork ? s->aux : c->stream>>>(
+                    d, b2, x, segz, s->d_s2tiles, (int)g2.x, (int)g2.y);
+                c->launches++;
+            }
+            if (s->n_s2pml > 0) {
+                k_yee3d_t2<T2_ROWS, true><<<s->n_s2pml, nthr, smem2p, c->stream>>>(
+                    d, b2, x, segz, s->d_s2tiles + s->n_s2int, (int)g2.x, (int)g2.y);
+                c->launches++;
+            }
+            if (fork) {
+                CK3(cudaEventRecord(s->ev_join, s->aux), "join");
+                CK3(cudaStreamWaitEvent(c->stream, s->ev_join, 0), "join");
+            }
+            swap_bufs();
+            after(n, false);
+            after(n + 1, true);
+            q += 2;
+            continue;
+        }
         if (c->opt_kernel == 1) {
             k_h3<<<grd, blk, 0, c->stream>>>(d);
             k_e3<<<grd, blk, 0, c->stream>>>(d);
             c->launches += 2;
         } else {
-            Bufs3 b;
-            for (int w = 0; w < G_COUNT; w++) {
-                b.in[w] = s->f[w];
-                b.out[w] = s->g[w];
-            }
-            k_yee3d_fused<<<gfz, NW3 * 32, smem3, c->stream>>>(d, b, segz);
+            k_yee3d_fused<<<gfz, NW3 * 32, smem3, c->stream>>>(d, bufs(), segz);
             c->launches++;
-            for (int w = 0; w < G_COUNT; w++) std::swap(s->f[w], s->g[w]);
-            d = dev_of(s);
+            swap_bufs();
         }
-        if (si >= 0 || !s->samples.empty()) {
-            k_src_rec3<<<1, 128, 0, c->stream>>>(d, si, s->src_j, s->src_k, s->src_comp, s->d_src,
-                                                 s->src_kind >= 0 ? s->src_cap : 0, s->d_samp, (int)s->samples.size(),
-                                                 s->d_rec, n);
-            c->launches++;
-        }
-        for (const DftMon& m : c->mons) {
-            if (m.plane_k >= 0)
-                k_dft_plane3<<<grp, blk, 0, c->stream>>>(d, m.plane_k, m.comp_mask, m.d_freq, m.n_freq, s->dt, m.d_acc, n);
-            else
-                k_dft_cells3<<<(m.n_cells * m.n_freq + 127) / 128, 128, 0, c->stream>>>(
-                    s->d_rec, (int)s->samples.size(), m.slot0, m.n_cells, m.d_freq, m.n_freq, s->dt, m.d_acc, n);
-            c->launches++;
-        }
+        after(n, true);
+        q += 1;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail3(c, FDTD_ECUDA, "3D step: %s", cudaGetErrorString(e));

@@ -32,7 +32,8 @@ def _oracle3(sc, n, samples=None, plane=False):
     return res
 
 
-def test_3d_cavity_mode_closed_form():
+@pytest.mark.parametrize("tblock", [1, 2])
+def test_3d_cavity_mode_closed_form(tblock):
     from paper_2405_00814_gb300 import fdtd
     nx, ny, nz = 24, 20, 16
     d = (1e-3, 1.1e-3, 0.9e-3)
@@ -60,6 +61,7 @@ def test_3d_cavity_mode_closed_form():
     hy = f * (fwd(ex, 0) / d[2] - fwd(ez, 2) / d[0])
     hz = f * (fwd(ey, 2) / d[0] - fwd(ex, 1) / d[1])
     sim = fdtd.Simulation(sc)
+    sim.set_option("tblock", tblock)
     for name, v in (("ex", ex), ("ey", ey), ("ez", ez), ("hx", hx), ("hy", hy), ("hz", hz)):
         sim.set_field(name, v)
     sim.step(200)
@@ -71,24 +73,29 @@ def test_3d_cavity_mode_closed_form():
     sim.close()
 
 
-@pytest.mark.parametrize("kernel,segz,side", [(0, 64, 40), (0, 7, 40), (1, 64, 40), (0, 5, 37)])
-def test_3d_boxes_cpml_probes_plane_dft(kernel, segz, side):
+@pytest.mark.parametrize("kernel,segz,side,tblock,n", [
+    (0, 64, 40, 1, 150), (0, 7, 40, 1, 150), (1, 64, 40, 1, 150), (0, 5, 37, 1, 150),
+    # the two-step kernel: segments of 1 .. 64 planes, a ragged last tile row,
+    # an odd step count (the last step runs the one-step kernel)
+    (0, 64, 40, 2, 150), (0, 7, 40, 2, 150), (0, 1, 37, 2, 150), (0, 2, 37, 2, 150), (0, 5, 37, 2, 151)])
+def test_3d_boxes_cpml_probes_plane_dft(kernel, segz, side, tblock, n):
     from paper_2405_00814_gb300 import fdtd
-    sc = scenes.box_scene(side=side, nsteps=150, npml=6, n_boxes=10)
+    sc = scenes.box_scene(side=side, nsteps=n, npml=6, n_boxes=10)
     sc.source = scenes.Source(20, 20, 20, component="ez", kind="ricker", params=(40e9,))
     sc.dft_plane_k = 28
     sc.freqs = np.array([10e9, 20e9, 30e9])
     probes = [(12, 14, 22, "ez"), (25, 9, 30, "hx"), (30, 30, 10, "ey")]
-    o = _oracle3(sc, 150, samples=probes, plane=True)
+    o = _oracle3(sc, n, samples=probes, plane=True)
     sim = fdtd.from_scene(sc)
     sim.set_option("kernel", kernel)
     sim.set_option("segment", segz)
+    sim.set_option("tblock", tblock)
     pids = [sim.add_probe(i, j, k, c) for i, j, k, c in probes]
     mid = sim.add_dft_plane(sc.dft_plane_k, ("ex", "ey", "ez"), sc.freqs)
-    sim.step(150)
+    sim.step(n)
     for c in COMPS:
         assert rel_l2(sim.get_field(c, (sc.nz, sc.ny, sc.nx)), o[c]) <= TOL_FIELD, c
-    got = np.stack([sim.read_probe(p, 150) for p in pids], 1)
+    got = np.stack([sim.read_probe(p, n) for p in pids], 1)
     for q in range(len(probes)):
         assert rel_l2(got[:, q], o["samples"][:, q]) <= TOL_FIELD, probes[q]
     dft = sim.read_dft(mid)
@@ -96,8 +103,93 @@ def test_3d_boxes_cpml_probes_plane_dft(kernel, segz, side):
     sim.close()
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
-def test_3d_full_size_512_light_cone(kernel):
+def _random_state3(nx, ny, nz, seed):
+    """Random E and H over the whole grid; the tangential E on the PEC walls
+    (Ex at j|k = 0, Ey at i|k = 0, Ez at i|j = 0) is zero."""
+    rng = np.random.default_rng(seed)
+    st = {c: rng.standard_normal((nz, ny, nx)) * (1.0 if c[0] == "e" else 2.6e-3) for c in COMPS}
+    st["ex"][:, 0, :] = 0
+    st["ex"][0, :, :] = 0
+    st["ey"][:, :, 0] = 0
+    st["ey"][0, :, :] = 0
+    st["ez"][:, :, 0] = 0
+    st["ez"][:, 0, :] = 0
+    return st
+
+
+@pytest.mark.parametrize("tblock,segz,n,npml,shape", [
+    (2, 4, 41, 5, (250, 23, 19)), (2, 19, 40, 5, (250, 23, 19)), (2, 3, 23, 0, (250, 23, 19)),
+    (1, 4, 41, 5, (250, 23, 19)),
+    # tiles clear of the CPML (the build without it, on the second stream) beside tiles in its reach
+    (2, 8, 30, 4, (370, 40, 40))])
+def test_3d_rectangular_three_x_tiles(tblock, segz, n, npml, shape):
+    """A 250 x 23 x 19 grid (three 120-cell x-tiles of the two-step kernel, the
+    last one 10 cells wide; or 370 x 40 x 40, where some tiles are clear of the
+    CPML), a CPML (or PEC walls), a lossy and two dielectric materials, random
+    initial E and H everywhere plus a source on a tile seam, probes of all six
+    components on both sides of the seams and a plane DFT: fields, probe
+    records and the DFT equal the oracle."""
+    import oracle
+    from paper_2405_00814_gb300 import fdtd
+    nx, ny, nz = shape
+    mat = np.zeros((nz, ny, nx), np.uint8)
+    mat[3:15, 4:20, 100:140] = 1
+    mat[6:12, 2:9, 200:247] = 2
+    mat[8:17, 10:21, 30:70] = 3
+    dx = 1e-3
+    dt = 0.99 / (C0 * math.sqrt(3.0) / dx)
+    sc = scenes.Scene3D(nx=nx, ny=ny, nz=nz, dx=dx, dy=dx, dz=dx, dt=dt, npml=npml, mat=mat,
+                        eps_r=np.array([1.0, 4.0, 2.5, 6.0]), sigma=np.array([0.0, 0.0, 0.02, 0.0]), nsteps=n,
+                        source=scenes.Source(120, 11, 9, component="ey", kind="ricker", params=(60e9,)))
+    freqs = np.array([20e9, 45e9])
+    probes = [(119, 11, 9, "ez"), (120, 12, 9, "hx"), (239, 11, 8, "hy"), (240, 11, 10, "ex"),
+              (118, 9, 11, "hz"), (120, 11, 9, "ey"), (0, 0, 0, "hz"), (249, 22, 18, "hx")]
+    st = _random_state3(nx, ny, nz, 11)
+    osim = oracle.Yee3D(sc, nsteps_src=n)
+    osim.set_state(**st)
+    out = osim.run(n, samples=probes, plane_k=9, freqs=freqs)
+    plane = osim.plane[0] + 1j * osim.plane[1]
+    sim = fdtd.from_scene(sc)
+    sim.set_option("segment", segz)
+    sim.set_option("tblock", tblock)
+    for c in COMPS:
+        sim.set_field(c, st[c].astype(np.float32))
+    pids = [sim.add_probe(i, j, k, c) for i, j, k, c in probes]
+    mid = sim.add_dft_plane(9, ("ex", "ey", "ez"), freqs)
+    sim.step(n)
+    for c in COMPS:
+        assert rel_l2(sim.get_field(c, (nz, ny, nx)), osim.state[c]) <= TOL_FIELD, c
+    got = np.stack([sim.read_probe(p, n) for p in pids], 1)
+    for q in range(len(probes)):
+        assert rel_l2(got[:, q], out["samples"][:, q]) <= TOL_FIELD, probes[q]
+    dft = sim.read_dft(mid)
+    assert np.max(np.abs(dft - plane)) <= 1e-4 * np.max(np.abs(plane))
+    sim.close()
+
+
+def test_3d_two_step_equals_one_step():
+    """The two-step kernel and the one-step kernel give the same fields on the
+    40^3 box scene (both FP32; only the rounding of the same sums differs).
+    Hz, which the z-directed dipole leaves near zero, is measured against the
+    norm of the whole H field."""
+    from paper_2405_00814_gb300 import fdtd
+    sc = scenes.box_scene(side=40, nsteps=60, npml=6, n_boxes=10)
+    out = []
+    for tb in (1, 2):
+        sim = fdtd.from_scene(sc)
+        sim.set_option("tblock", tb)
+        sim.step(60)
+        out.append({c: sim.get_field(c, (sc.nz, sc.ny, sc.nx)) for c in COMPS})
+        sim.close()
+    norm = {k: math.sqrt(sum(float(np.sum(out[0][c].astype(np.float64) ** 2)) for c in COMPS if c[0] == k))
+            for k in "eh"}
+    for c in COMPS:
+        floor = norm[c[0]] if float(np.linalg.norm(out[0][c])) < 1e-2 * norm[c[0]] else 0.0
+        assert rel_l2(out[1][c], out[0][c], floor=floor) <= 1e-5, c
+
+
+@pytest.mark.parametrize("kernel,tblock", [(0, 1), (1, 1), (0, 2)])
+def test_3d_full_size_512_light_cone(kernel, tblock):
     """The 512^3 box workload (10-cell CPML, 64 boxes, Gaussian Ez dipole) as the
     benchmark runs it, 110 steps: every field equals the oracle on the crop that
     holds the dipole's dependency cone and is exactly zero outside it."""
@@ -106,6 +198,7 @@ def test_3d_full_size_512_light_cone(kernel):
     n = 110
     sim = fdtd.from_scene(sc)
     sim.set_option("kernel", kernel)
+    sim.set_option("tblock", tblock)
     sim.step(n)
     si, sj, sk = sc.source.i, sc.source.j, sc.source.k
     h = n + 2
