@@ -304,6 +304,8 @@ def yee3d_throughput(stream, nsteps=200, side=512, kernel=None, segment=None, tb
     if tblock is not None:
         sim.set_option("tblock", tblock)
     tb, seg = sim.get_option("tblock"), sim.get_option("segment")
+    if seg == 0:   # automatic: 24 planes for the one-step kernel, 48 for the two-step one
+        seg = 48 if tb == 2 else 24
     sim.add_dft_plane(sc.dft_plane_k, ("ex", "ey", "ez"), sc.freqs)
     sim.step(10)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -473,7 +475,7 @@ def main():
     ap.add_argument("--segment", type=int, default=None)
     ap.add_argument("--warps", type=int, default=None)
     ap.add_argument("--segment-b", type=int, default=None, help="FDTD_OPT_SEGMENT_B (boundary task rows; 0 = automatic)")
-    ap.add_argument("--kernel", type=int, default=None, help="FDTD_OPT_KERNEL (2D default 0; 3D default 1)")
+    ap.add_argument("--kernel", type=int, default=None, help="FDTD_OPT_KERNEL (default 0)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-sample", type=int, default=20)

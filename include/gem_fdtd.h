@@ -86,11 +86,12 @@ extern "C" {
                                     own, so there is no barrier between blocks (a context with a split-field PML
                                     steps with the unfused pair instead).
                                 3D: 0 = fused z-marching kernel (default), 1 = one H and one E launch per step */
-#define FDTD_OPT_TBLOCK 1    /* time steps per HBM pass of the fused kernel: 2D 1..4; 3D 1 or 2 (2: the
-                                two-step z-marching kernel takes the steps in pairs, an odd last step runs
-                                the one-step kernel; with more than 4 plane monitors every step does) */
+#define FDTD_OPT_TBLOCK 1    /* time steps per HBM pass of the fused kernel: 2D 1..4; 3D 1 or 2 (2, the 3D
+                                default: the two-step z-marching kernel takes the steps in pairs, an odd last
+                                step runs the one-step kernel; with more than 4 plane monitors every step does) */
 #define FDTD_OPT_SEGMENT 2   /* 2D: rows per warp task of the fused kernel (>= 8);
-                                3D: planes per z-segment of the fused z-marching kernel (>= 1, default 24) */
+                                3D: planes per z-segment of the fused z-marching kernels (>= 1; 0, the
+                                default = 24 for the one-step kernel, 48 for the two-step one) */
 #define FDTD_OPT_WARPS 3     /* warps per CTA of the fused kernel, 1..8 */
 #define FDTD_OPT_GRAPH 4     /* 1: fdtd_step records its launches into a CUDA graph and replays it when called
                                 again with the same start step, step count and buffer parity (e.g. after fdtd_reset) */

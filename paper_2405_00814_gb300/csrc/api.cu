@@ -1071,6 +1071,7 @@ void fdtd_destroy(fdtd_ctx* c) {
     for (DftMon& m : c->mons) {
         dfree(m.d_freq);
         dfree(m.d_acc);
+        dfree(m.d_e1);
     }
     fdtd_destroy3(c);
     graph_free(c);
@@ -1128,9 +1129,9 @@ int fdtd_set_option(fdtd_ctx* c, int option, int64_t v) {
             c->opt_tblock = (int)v;
             return FDTD_OK;
         case FDTD_OPT_SEGMENT:
-            // 2D: rows per warp task (>= 8); 3D: planes per z-segment (>= 1)
-            if (c->dims == 3 ? (v < 1 || v > (1 << 20)) : (v < 8 || v > (1 << 20)))
-                return fail(c, FDTD_EINVAL, "segment %lld: 2D needs >= 8, 3D >= 1", (long long)v);
+            // 2D: rows per warp task (>= 8); 3D: planes per z-segment (>= 1; 0 = automatic)
+            if (c->dims == 3 ? (v < 0 || v > (1 << 20)) : (v < 8 || v > (1 << 20)))
+                return fail(c, FDTD_EINVAL, "segment %lld: 2D needs >= 8, 3D >= 1 (or 0, automatic)", (long long)v);
             c->opt_segment = (int)v;
             c->dirty = true;
             return FDTD_OK;

@@ -124,6 +124,7 @@ struct DftMon {
     int64_t t_start;            // first step accumulated
     // 3D plane monitor
     int plane_k, comp_mask;
+    float* d_e1 = nullptr;      // 3D two-step kernel: the plane's E after the first step, [3][rows][pitch]
 };
 
 // one (cell, frequency) accumulator of a 2D cell monitor, for the single DFT

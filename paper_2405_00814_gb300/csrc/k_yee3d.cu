@@ -660,6 +660,47 @@ __global__ void k_dft_plane3(Dev3 S, int plane_k, int comp_mask, const double* f
     }
 }
 
+// the running plane DFT of two steps n and n + 1 in one pass over the
+// accumulators: E of step n from the two-step kernel's copy e1 of the plane
+// ([3][rows][pitch]), E of step n + 1 from the fields
+__global__ void k_dft_plane3_pair(Dev3 S, int plane_k, int comp_mask, const double* freq, int n_freq, double dt,
+                                  float4* acc, long long n, const float* e1) {
+    __shared__ float2 tw[2][16];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if (tid < 2 * 16) {
+        const int s = tid >> 4, f = tid & 15;
+        if (f < n_freq) {
+            double ph = freq[f] * dt * (double)(n + 1 + s);
+            ph -= floor(ph);
+            double sn, cs;
+            sincospi(2.0 * ph, &sn, &cs);
+            tw[s][f] = make_float2((float)cs * (float)dt, -(float)sn * (float)dt);
+        }
+    }
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= S.nx || j >= S.ny) return;
+    const size_t c = ((size_t)(plane_k + 1) * S.rows + (j + 1)) * S.pitch + (i + PX3);
+    const size_t c1 = (size_t)(j + 1) * S.pitch + (i + PX3), cs = (size_t)S.rows * S.pitch;
+    const size_t plane = (size_t)S.nx * S.ny;
+    const size_t cell = (size_t)j * S.nx + i;
+    int pc = 0;
+    for (int comp = 0; comp < 3; comp++) {
+        if (!(comp_mask & (1 << comp))) continue;
+        const float ea = e1[comp * cs + c1], eb = S.f[comp][c];
+        for (int f = 0; f < n_freq; f++) {
+            float4 a = acc[((size_t)pc * n_freq + f) * plane + cell];
+            kahan3(a.x, a.z, ea * tw[0][f].x);
+            kahan3(a.y, a.w, ea * tw[0][f].y);
+            kahan3(a.x, a.z, eb * tw[1][f].x);
+            kahan3(a.y, a.w, eb * tw[1][f].y);
+            acc[((size_t)pc * n_freq + f) * plane + cell] = a;
+        }
+        pc++;
+    }
+}
+
 __global__ void k_dft_cells3(const float* rec, int n_rec, int slot0, int n_cells, const double* freq, int n_freq,
                              double dt, float4* acc, long long n) {
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
@@ -712,10 +753,8 @@ struct Extra2 {
     const int* s_idx;              // samples each CTA owns, by CTA
     float* rec;                    // rec[n * n_samp + slot]
     int n_mon;                     // plane monitors (<= MAXP2)
-    int mon_k[MAXP2], mon_mask[MAXP2], mon_nf[MAXP2];
-    const double* mon_f[MAXP2];
-    float4* mon_acc[MAXP2];
-    double dt;
+    int mon_k[MAXP2], mon_mask[MAXP2];
+    float* mon_e1[MAXP2];          // the plane's E after the first step, [3][rows][pitch]
     long long n;                   // index of the first of the two steps
 };
 
@@ -725,7 +764,6 @@ constexpr size_t t2_smem() {
             + (size_t)4 * (TY + 3) * 2 * 32      // H1 rows, E1 rows (two parities), H2 rows
             + 256                                // coefficient table
             + 128                                // x-profiles of the 128 columns
-            + MAXP2 * 8                          // twiddles [MAXP2][16] float2
             + (PML ? (size_t)12 * (TY + 3) * 32 : 0)) * sizeof(float4);   // x-slab psi, per thread
 }
 
@@ -773,11 +811,10 @@ __global__ void __launch_bounds__((TY + 3) * 32, 1) k_yee3d_t2(Dev3 S, Bufs3 B, 
     float4* bH2 = bE1 + 2 * NW * 2 * 32;                     // [NW][2][32]: Hx, Hz of step 2
     float4* coef_s = bH2 + NW * 2 * 32;                      // [256]
     float* Xp = reinterpret_cast<float*>(coef_s + 256);      // [4][128]: bHx cHx bEx cEx
-    float2* tw = reinterpret_cast<float2*>(Xp + 4 * 128);    // [MAXP2][16]
     // x-slab lanes' CPML auxiliaries (HYX HZX EYX EZX), each thread its own
     // column: the next plane's stored values (cp.async, one plane ahead) and the
     // first step's values by plane parity
-    float4* px0 = reinterpret_cast<float4*>(tw + MAXP2 * 16);   // [4][NT]
+    float4* px0 = reinterpret_cast<float4*>(Xp + 4 * 128);      // [4][NT]
     float4* px1 = px0 + 4 * NT;                                 // [2][4][NT]
 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, tid = threadIdx.x;
@@ -808,17 +845,6 @@ __global__ void __launch_bounds__((TY + 3) * 32, 1) k_yee3d_t2(Dev3 S, Bufs3 B, 
             const bool in = c >= 0 && c < nx;
             Xp[q] = !in ? 0.f : (a == 0 ? pr.bHx(c + PX3) : a == 1 ? pr.cHx(c + PX3) : a == 2 ? pr.bEx(c + PX3) : pr.cEx(c + PX3));
         }
-    if (tid < MAXP2 * 16) {
-        const int m = tid >> 4, f = tid & 15;
-        if (m < X.n_mon && f < X.mon_nf[m]) {
-            // the first step's twiddle dt e^{-i 2 pi f (n + 1) dt}, FP64 phase
-            double ph = X.mon_f[m][f] * X.dt * (double)(X.n + 1);
-            ph -= floor(ph);
-            double sn, cs;
-            sincospi(2.0 * ph, &sn, &cs);
-            tw[tid] = make_float2((float)cs * (float)X.dt, -(float)sn * (float)X.dt);
-        }
-    }
     const int sb0 = X.s_off ? X.s_off[tile] : 0, sb1 = X.s_off ? X.s_off[tile + 1] : 0;
 
     // CPML reach (conservative; the profiles decide cell by cell)
@@ -1039,33 +1065,16 @@ __global__ void __launch_bounds__((TY + 3) * 32, 1) k_yee3d_t2(Dev3 S, Bufs3 B, 
                 X.rec[X.n * X.n_samp + sp.slot] = f4c(v, c);
             }
         }
-        // the first step's plane DFT over the owned cells
-        if (X.n_mon > 0 && own_row && own_x && q >= kA && q < kB) {
-            const size_t plane = (size_t)nx * ny;
+        // a monitored plane's E after the first step, for the DFT launch that
+        // accumulates both steps after this kernel
+        if (X.n_mon > 0 && own_row && own_x && q >= kA && q < kB)
             for (int m = 0; m < X.n_mon; m++) {
                 if (X.mon_k[m] != q) continue;
-                const int nf = X.mon_nf[m];
-                int pc = 0;
-                for (int comp = 0; comp < 3; comp++) {
-                    if (!(X.mon_mask[m] & (1 << comp))) continue;
-                    const float4 v = comp == 0 ? e1x : comp == 1 ? e1y : e1z;
-                    for (int c = 0; c < 4; c++) {
-                        if (!(own_x & (1u << c))) continue;
-                        const float e = f4c(v, c);
-                        const size_t cell = (size_t)r * nx + xc + c;
-                        for (int f = 0; f < nf; f++) {
-                            float4* ap = X.mon_acc[m] + ((size_t)pc * nf + f) * plane + cell;
-                            float4 a = *ap;
-                            const float2 t = tw[m * 16 + f];
-                            kahan3(a.x, a.z, e * t.x);
-                            kahan3(a.y, a.w, e * t.y);
-                            *ap = a;
-                        }
-                    }
-                    pc++;
-                }
+                const size_t g = (size_t)(r + 1) * pitch + xc + PX3, cs = (size_t)rows * pitch;
+                if (X.mon_mask[m] & 1) st4m(X.mon_e1[m], g, e1x, own_x);
+                if (X.mon_mask[m] & 2) st4m(X.mon_e1[m] + cs, g, e1y, own_x);
+                if (X.mon_mask[m] & 4) st4m(X.mon_e1[m] + 2 * cs, g, e1z, own_x);
             }
-        }
 
         // ---- step 2, layer 1: H2(q - 1) of rows yo-1 .. yo+TY-1 ----
         const int p2 = q - 1;
@@ -1311,7 +1320,7 @@ int fdtd_create3(const fdtd_grid* g, double dx, double dt, double courant, const
     c->stream = (cudaStream_t)stream;
     c->s3 = nullptr;
     c->cur = 0; c->t = 0; c->parity = 0; c->launches = 0;
-    c->opt_kernel = 0; c->opt_tblock = 1; c->opt_segment = 24; c->opt_warps = 8; c->opt_segment_b = 0;
+    c->opt_kernel = 0; c->opt_tblock = 2; c->opt_segment = 0; c->opt_warps = 8; c->opt_segment_b = 0;
     c->dirty = true;
     c->d_scenes = nullptr; c->d_tasks = nullptr; c->d_tasks_b = nullptr; c->n_tasks_b = 0; c->warps_b = 2; c->d_tasks_l = nullptr; c->n_tasks_l = 0; c->warps_l = 4; c->d_tasks_s = nullptr; c->n_tasks_s = 0; c->d_tasks_bd = nullptr; c->n_tasks_bd = 0;
     c->d_dft = nullptr; c->n_dft = 0; c->opt_adj_store = 1;
@@ -1584,7 +1593,9 @@ int fdtd_step3(fdtd_ctx* c, int64_t n_steps) {
     const dim3 grd((s->nx + 31) / 32, (s->ny + 7) / 8, s->nz);
     const dim3 grp((s->nx + 31) / 32, (s->ny + 7) / 8, 1);
     const int si = s->src_kind >= 0 ? s->src_i : -1;
-    const int segz = std::max(1, c->opt_segment);
+    // z-segment planes: the option, else 24 for the one-step kernel, 48 for the two-step one
+    const int segz = c->opt_segment > 0 ? c->opt_segment : 24;
+    const int seg2 = c->opt_segment > 0 ? c->opt_segment : 48;
     const dim3 gfz((s->nx + TXC - 1) / TXC, (s->ny + TYR - 1) / TYR, (s->nz + segz - 1) / segz);
     const size_t smem3 = fused3_smem();
     // the two-step kernel (FDTD_OPT_TBLOCK = 2) takes steps in pairs; it updates
@@ -1592,7 +1603,7 @@ int fdtd_step3(fdtd_ctx* c, int64_t n_steps) {
     int n_plane = 0;
     for (const DftMon& m : c->mons) n_plane += m.plane_k >= 0 ? 1 : 0;
     const bool two = c->opt_kernel != 1 && c->opt_tblock == 2 && n_plane <= MAXP2 && n_steps >= 2;
-    const dim3 g2((s->nx + TX2 - 1) / TX2, (s->ny + T2_ROWS - 1) / T2_ROWS, (s->nz + segz - 1) / segz);
+    const dim3 g2((s->nx + TX2 - 1) / TX2, (s->ny + T2_ROWS - 1) / T2_ROWS, (s->nz + seg2 - 1) / seg2);
     const size_t smem2i = t2_smem<T2_ROWS, false>(), smem2p = t2_smem<T2_ROWS, true>();
     if (c->opt_kernel != 1) {
         cudaError_t ea = ensure_dyn_smem((const void*)k_yee3d_fused, smem3);
@@ -1602,8 +1613,17 @@ int fdtd_step3(fdtd_ctx* c, int64_t n_steps) {
         if (ea != cudaSuccess) return fail3(c, FDTD_ECUDA, "fused 3D kernel: %s", cudaGetErrorString(ea));
     }
     if (two) {
-        rc = build_s2(c, s, segz, g2);
+        rc = build_s2(c, s, seg2, g2);
         if (rc) return rc;
+        for (DftMon& m : c->mons)
+            if (m.plane_k >= 0 && !m.d_e1) {
+                const size_t b = (size_t)3 * s->rows * s->pitch * sizeof(float);
+                if (cudaMalloc(&m.d_e1, b) != cudaSuccess) {
+                    cudaGetLastError();
+                    m.d_e1 = nullptr;
+                    return fail3(c, FDTD_ENOMEM, "plane copy of the two-step kernel");
+                }
+            }
     }
     auto swap_bufs = [&]() {
         for (int w = 0; w < G_COUNT; w++) std::swap(s->f[w], s->g[w]);
@@ -1618,8 +1638,10 @@ int fdtd_step3(fdtd_ctx* c, int64_t n_steps) {
         return b;
     };
     // after step n: the source, probes and plane DFT (src_rec: the kernel has
-    // not done them), then the cell monitors from the record
-    auto after = [&](long long n, bool src_rec) {
+    // not done them; pair: the plane DFT takes steps n - 1 and n, the first
+    // from the two-step kernel's copy of the plane), then the cell monitors
+    // from the record
+    auto after = [&](long long n, bool src_rec, bool pair) {
         if (src_rec) {
             if (si >= 0 || !s->samples.empty()) {
                 k_src_rec3<<<1, 128, 0, c->stream>>>(d, si, s->src_j, s->src_k, s->src_comp, s->d_src,
@@ -1631,7 +1653,12 @@ int fdtd_step3(fdtd_ctx* c, int64_t n_steps) {
         for (const DftMon& m : c->mons) {
             if (m.plane_k >= 0) {
                 if (!src_rec) continue;
-                k_dft_plane3<<<grp, blk, 0, c->stream>>>(d, m.plane_k, m.comp_mask, m.d_freq, m.n_freq, s->dt, m.d_acc, n);
+                if (pair)
+                    k_dft_plane3_pair<<<grp, blk, 0, c->stream>>>(d, m.plane_k, m.comp_mask, m.d_freq, m.n_freq, s->dt,
+                                                                  m.d_acc, n - 1, m.d_e1);
+                else
+                    k_dft_plane3<<<grp, blk, 0, c->stream>>>(d, m.plane_k, m.comp_mask, m.d_freq, m.n_freq, s->dt,
+                                                             m.d_acc, n);
             } else {
                 k_dft_cells3<<<(m.n_cells * m.n_freq + 127) / 128, 128, 0, c->stream>>>(
                     s->d_rec, (int)s->samples.size(), m.slot0, m.n_cells, m.d_freq, m.n_freq, s->dt, m.d_acc, n);
@@ -1654,11 +1681,9 @@ int fdtd_step3(fdtd_ctx* c, int64_t n_steps) {
             x.rec = s->d_rec;
             for (const DftMon& m : c->mons)
                 if (m.plane_k >= 0) {
-                    x.mon_k[x.n_mon] = m.plane_k; x.mon_mask[x.n_mon] = m.comp_mask; x.mon_nf[x.n_mon] = m.n_freq;
-                    x.mon_f[x.n_mon] = m.d_freq; x.mon_acc[x.n_mon] = m.d_acc;
+                    x.mon_k[x.n_mon] = m.plane_k; x.mon_mask[x.n_mon] = m.comp_mask; x.mon_e1[x.n_mon] = m.d_e1;
                     x.n_mon++;
                 }
-            x.dt = s->dt;
             x.n = n;
             // tiles without CPML reach on the second stream, the others here
             const Bufs3 b2 = bufs();
@@ -1670,12 +1695,12 @@ int fdtd_step3(fdtd_ctx* c, int64_t n_steps) {
             }
             if (s->n_s2int > 0) {
                 k_yee3d_t2<T2_ROWS, false><<<s->n_s2int, nthr, smem2i, fork ? s->aux : c->stream>>>(
-                    d, b2, x, segz, s->d_s2tiles, (int)g2.x, (int)g2.y);
+                    d, b2, x, seg2, s->d_s2tiles, (int)g2.x, (int)g2.y);
                 c->launches++;
             }
             if (s->n_s2pml > 0) {
                 k_yee3d_t2<T2_ROWS, true><<<s->n_s2pml, nthr, smem2p, c->stream>>>(
-                    d, b2, x, segz, s->d_s2tiles + s->n_s2int, (int)g2.x, (int)g2.y);
+                    d, b2, x, seg2, s->d_s2tiles + s->n_s2int, (int)g2.x, (int)g2.y);
                 c->launches++;
             }
             if (fork) {
@@ -1683,8 +1708,8 @@ int fdtd_step3(fdtd_ctx* c, int64_t n_steps) {
                 CK3(cudaStreamWaitEvent(c->stream, s->ev_join, 0), "join");
             }
             swap_bufs();
-            after(n, false);
-            after(n + 1, true);
+            after(n, false, false);
+            after(n + 1, true, true);
             q += 2;
             continue;
         }
@@ -1697,7 +1722,7 @@ int fdtd_step3(fdtd_ctx* c, int64_t n_steps) {
             c->launches++;
             swap_bufs();
         }
-        after(n, true);
+        after(n, true, false);
         q += 1;
     }
     cudaError_t e = cudaGetLastError();

@@ -98,9 +98,9 @@ def test_zero_steps_is_a_no_op():
     sim.close()
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel,tblock", [(0, 1), (1, 1), (0, 2)])
 @pytest.mark.parametrize("n", [4, 9])
-def test_3d_tiny_grids(kernel, n):
+def test_3d_tiny_grids(kernel, tblock, n):
     """3D grids of a few cells (every tile mostly pad), random materials."""
     from paper_2405_00814_gb300 import fdtd
     import oracle
@@ -116,6 +116,7 @@ def test_3d_tiny_grids(kernel, n):
     osim.run(sc.nsteps)
     sim = fdtd.from_scene(sc)
     sim.set_option("kernel", kernel)
+    sim.set_option("tblock", tblock)
     sim.set_option("segment", 3)
     sim.step(sc.nsteps)
     for comp in ("ex", "ey", "ez", "hx", "hy", "hz"):
