@@ -81,10 +81,11 @@ extern "C" {
 #define FDTD_OPT_KERNEL 0    /* 2D: 0 = fused temporally blocked stream, two kernels per T-step block (default);
                                 1 = one H and one E launch per step;
                                 2 = persistent: one cooperative launch runs many T-step blocks of every scene,
-                                    warps pulling (block, work item) pairs in order from a shared counter; an item
-                                    waits (bounded) only for the items of the previous block whose regions meet its
-                                    own, so there is no barrier between blocks (a context with a split-field PML
-                                    steps with the unfused pair instead).
+                                    warps pulling (block, work item) pairs in order from two shared counters, one
+                                    for interior items and one for the rest (CPML, design, sources, probes), served
+                                    by warps with 128 and 248 registers; an item waits (bounded) only for the items
+                                    of the previous block whose regions meet its own, so there is no barrier between
+                                    blocks (a context with a split-field PML steps with the unfused pair instead).
                                 3D: 0 = fused z-marching kernel (default), 1 = one H and one E launch per step */
 #define FDTD_OPT_TBLOCK 1    /* time steps per HBM pass of the fused kernel: 2D 1..4; 3D 1 or 2 (2, the 3D
                                 default: the two-step z-marching kernel takes the steps in pairs, an odd last

@@ -758,8 +758,11 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     }
     dfree(c->d_scenes); dfree(c->d_tasks); dfree(c->d_tasks_b); dfree(c->d_samp); dfree(c->d_samp_scene); dfree(c->d_samp_off);
     dfree(c->d_ptasks); dfree(c->d_pitems); dfree(c->d_dep_off); dfree(c->d_dep_idx); dfree(c->d_done);
+    dfree(c->d_pq);
     c->d_ptasks = nullptr; c->d_pitems = nullptr; c->d_dep_off = nullptr; c->d_dep_idx = nullptr; c->d_done = nullptr;
+    c->d_pq = nullptr;
     c->n_pitems = 0;
+    c->n_pint = c->n_pgen = 0;
     dfree(c->d_tasks_l);
     dfree(c->d_tasks_s);
     dfree(c->d_tasks_bd);
@@ -784,6 +787,17 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     if ((rc = dalloc(c, &c->d_dep_off, dep_off.size() * sizeof(int), "persistent dependencies"))) return rc;
     if ((rc = dalloc(c, &c->d_dep_idx, dep_idx.size() * sizeof(int), "persistent dependencies"))) return rc;
     if ((rc = dalloc(c, &c->d_done, pitems.size() * sizeof(unsigned), "persistent completion counts"))) return rc;
+    // the two queues: interior items (interior warps), then the rest (general warps)
+    std::vector<int> pq;
+    for (size_t i = 0; i < pitems.size(); i++)
+        if (pitems[i].x == PITEM_INTERIOR) pq.push_back((int)i);
+    c->n_pint = (int)pq.size();
+    for (size_t i = 0; i < pitems.size(); i++)
+        if (pitems[i].x != PITEM_INTERIOR) pq.push_back((int)i);
+    c->n_pgen = (int)pq.size() - c->n_pint;
+    if ((rc = dalloc(c, &c->d_pq, std::max<size_t>(1, pq.size()) * sizeof(int), "persistent queues"))) return rc;
+    if (!pq.empty())
+        CK(cudaMemcpyAsync(c->d_pq, pq.data(), pq.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream), "upload");
     if ((rc = dalloc(c, &c->d_tasks_l, tasks_l.size() * sizeof(Task), "tasks"))) return rc;
     if ((rc = dalloc(c, &c->d_tasks_s, tasks_s.size() * sizeof(Task), "tasks"))) return rc;
     if ((rc = dalloc(c, &c->d_tasks_bd, tasks_bd.size() * sizeof(Task), "tasks"))) return rc;
@@ -1079,6 +1093,7 @@ void fdtd_destroy(fdtd_ctx* c) {
     dfree(c->d_scenes); dfree(c->d_tasks); dfree(c->d_tasks_b); dfree(c->d_samp); dfree(c->d_samp_scene);
     dfree(c->d_samp_off);
     dfree(c->d_ptasks); dfree(c->d_pitems); dfree(c->d_dep_off); dfree(c->d_dep_idx); dfree(c->d_done);
+    dfree(c->d_pq);
     dfree(c->d_dft);
     dfree(c->d_ctl);
     if (c->h_err) cudaFreeHost(c->h_err);

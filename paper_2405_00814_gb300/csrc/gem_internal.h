@@ -230,6 +230,10 @@ struct fdtd_ctx {
     int* d_dep_idx;
     unsigned* d_done;
     int n_pitems;
+    // the items by warp class: interior items first, then general and narrow
+    // ones, each in space order (the two queues of the persistent kernel)
+    int* d_pq = nullptr;
+    int n_pint = 0, n_pgen = 0;
     gem::DftItem* d_dft;           // every 2D cell-monitor accumulator
     std::vector<gem::TmzDev> h_scenes;   // host copy of d_scenes
     int n_dft;

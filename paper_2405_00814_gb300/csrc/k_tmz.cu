@@ -778,47 +778,63 @@ __global__ void __launch_bounds__(256, 2) k_tmz_interior(const TmzDev* __restric
 // by n_blocks * T steps.  The work is a list of items per T-step block -- an
 // interior task, a whole-warp general task (CPML, design, source, probes) or
 // four narrow x-slab tasks -- and warps pull (block, item) pairs in order from
-// one counter, so uneven scene sizes balance themselves.  There is no barrier
+// a counter, so uneven scene sizes balance themselves.  There is no barrier
 // between blocks: an item of block b waits only until every item whose region
 // it reads or overwrites (its neighbours, itself included) has finished block
 // b - 1, as counted in done[] (block b reads buffer p and writes 1 - p, so these
-// are the only items whose data it touches).  Items are claimed in order and
-// wait only on items of the previous block, which were claimed earlier by
-// resident warps, so the lowest unfinished block always progresses.  Every
-// wait is bounded: after spin_limit polls the warp sets the error flag and
-// returns, and the others stop waiting when they see it.
+// are the only items whose data it touches).  Every wait is bounded: after
+// spin_limit polls the warp sets the error flag and returns, and the others
+// stop waiting when they see it.
 //
-// ctl layout (unsigned): [0] next (block, item) index, [2] error flag (kept by
-// the host until fdtd_sync reports it).  stall_item >= 0 names an item that never
-// reports block 0 done (a test of the timeout path); -1 in normal runs.
+// The CTA is 12 warps in two classes, as the items need registers: warps 0-7
+// take interior items and give registers back (setmaxnreg down to 128, what
+// the interior wavefront needs), warps 8-11 take general and narrow items and
+// get them (up to 248).  The split spends exactly the 384 x 168 registers the
+// CTA is launched with (the host checks the kernel's count before launching,
+// since a larger split would wait forever).  Each class pulls from its own
+// queue in (block, space) order; both are served in block order and every item
+// waits only for the previous block, so the lowest unfinished block always
+// progresses.
+//
+// ctl layout (unsigned): [0] next interior (block, item) index, [1] next
+// general one, [2] error flag (kept by the host until fdtd_sync reports it).
+// stall_item >= 0 names an item that never reports block 0 done (a test of the
+// timeout path); -1 in normal runs.
 // ===========================================================================
-template <int T, bool WREC>
-__global__ void __launch_bounds__(256, 1) k_tmz_persistent(const TmzDev* __restrict__ scenes,
-                                                          const Task* __restrict__ ptasks,
-                                                          const int2* __restrict__ items, int n_items,
-                                                          const int* __restrict__ dep_off,
-                                                          const int* __restrict__ dep_idx,
-                                                          const Sample2* __restrict__ samps, int parity0,
-                                                          long long n0, int n_blocks, unsigned* ctl,
-                                                          unsigned* done, long long spin_limit, int stall_item) {
-    constexpr int STAGE_W = (stages_for(T, true) * gen_stage_f4(true, 32 / NG_LANES) >
-                             stages_for(T, false) * stage_f4(false))
-                                ? stages_for(T, true) * gen_stage_f4(true, 32 / NG_LANES)
-                                : stages_for(T, false) * stage_f4(false);
-    extern __shared__ float4 smem_f4[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    float4* stage0 = smem_f4 + (size_t)wib * STAGE_W;
+constexpr int PW_INT = 8, PW_GEN = 4;                 // warps per class
+constexpr int PREG_LAUNCH = 168, PREG_INT = 128, PREG_GEN = 248;
+static_assert(PW_INT * PREG_INT + PW_GEN * PREG_GEN <= (PW_INT + PW_GEN) * PREG_LAUNCH,
+              "the register split must fit the CTA's launch allocation");
+
+template <int T>
+__host__ __device__ constexpr int pstage_int() { return stages_for(T, false) * stage_f4(false); }
+template <int T>
+__host__ __device__ constexpr int pstage_gen() { return stages_for(T, true) * gen_stage_f4(true, 32 / NG_LANES); }
+
+// one warp's loop over its class's queue: claim, wait for the neighbours'
+// previous block, run, publish (general warps lending a hand with interior
+// items measured no faster on the 64-scene batch: 539 vs 545 G)
+template <int T, bool WREC, bool GEN>
+__device__ __forceinline__ void persistent_loop(const TmzDev* __restrict__ scenes, const Task* __restrict__ ptasks,
+                                                const int2* __restrict__ items, const int* __restrict__ queue,
+                                                int n_int, int n_gen, const int* __restrict__ dep_off,
+                                                const int* __restrict__ dep_idx, const Sample2* __restrict__ samps,
+                                                int parity0, long long n0, int n_blocks, unsigned* ctl,
+                                                unsigned* done, long long spin_limit, int stall_item, float4* stage0,
+                                                int lane) {
     volatile int* verr = reinterpret_cast<volatile int*>(ctl + 2);
     // an earlier launch of this context timed out and nobody has read the flag yet
     if (*verr) return;
-    const long long total = (long long)n_blocks * n_items;
+    const long long tot_i = (long long)n_blocks * n_int, tot_g = (long long)n_blocks * n_gen;
     for (;;) {
+        constexpr int sel = GEN ? 1 : 0;   // the general queue follows the interior one
+        const long long tot = GEN ? tot_g : tot_i;
         long long idx = 0;
-        if (lane == 0) idx = (long long)atomicAdd(ctl, 1u);
+        if (lane == 0) idx = (long long)atomicAdd(ctl + sel, 1u);
         idx = __shfl_sync(0xffffffffu, idx, 0);
-        if (idx >= total) return;
-        const int b = (int)(idx / n_items), it = (int)(idx % n_items);
+        if (idx >= tot) return;
+        const int nq = GEN ? n_gen : n_int;
+        const int b = (int)(idx / nq), it = queue[(GEN ? n_int : 0) + (int)(idx % nq)];
         // wait for the neighbours' block b - 1: the lanes poll up to 32 counts at
         // once (relaxed loads), then one fence orders the item's reads after them
         if (b > 0) {
@@ -848,15 +864,20 @@ __global__ void __launch_bounds__(256, 1) k_tmz_persistent(const TmzDev* __restr
         const int parity = parity0 ^ (b & 1);
         const long long nb = n0 + (long long)b * T;
         const int2 item = items[it];
-        if (item.x == PITEM_NARROW) {
-            const Task tk = ptasks[item.y + lane / NG_LANES];
-            const TmzDev* S = scenes + tk.scene;
-            general_task<T, true, false, false, false, NG_LANES>(S, tk, samps, parity, nb, S->coef, stage0, lane);
+        if constexpr (GEN) {
+            if (item.x == PITEM_NARROW) {
+                const Task tk = ptasks[item.y + lane / NG_LANES];
+                const TmzDev* S = scenes + tk.scene;
+                general_task<T, true, false, false, false, NG_LANES>(S, tk, samps, parity, nb, S->coef, stage0, lane);
+            } else {
+                const Task tk = ptasks[item.y];
+                const TmzDev* S = scenes + tk.scene;
+                general_task<T, true, false, WREC>(S, tk, samps, parity, nb, S->coef, stage0, lane);
+            }
         } else {
             const Task tk = ptasks[item.y];
             const TmzDev* S = scenes + tk.scene;
-            if (item.x == PITEM_INTERIOR) interior_task<T>(S, tk, parity, S->coef, stage0, lane);
-            else general_task<T, true, false, WREC>(S, tk, samps, parity, nb, S->coef, stage0, lane);
+            interior_task<T>(S, tk, parity, S->coef, stage0, lane);
         }
         // publish: every lane's stores of this item, then the count
         __syncwarp();
@@ -867,23 +888,51 @@ __global__ void __launch_bounds__(256, 1) k_tmz_persistent(const TmzDev* __restr
     }
 }
 
-// dynamic shared memory of the persistent kernel: per warp, the larger of the
-// general (narrow) and interior staging areas
-static size_t persistent_smem(int T, int warps) {
-    const size_t g = (size_t)stages_for(T, true) * gen_stage_f4(true, 32 / NG_LANES);
+template <int T, bool WREC>
+__global__ void __launch_bounds__((PW_INT + PW_GEN) * 32, 1) k_tmz_persistent(
+    const TmzDev* __restrict__ scenes, const Task* __restrict__ ptasks, const int2* __restrict__ items,
+    const int* __restrict__ queue, int n_int, int n_gen, const int* __restrict__ dep_off,
+    const int* __restrict__ dep_idx, const Sample2* __restrict__ samps, int parity0, long long n0, int n_blocks,
+    unsigned* ctl, unsigned* done, long long spin_limit, int stall_item) {
+    extern __shared__ float4 smem_f4[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    if (wib >= PW_INT) {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(PREG_GEN) : "memory");
+        float4* stage0 = smem_f4 + (size_t)PW_INT * pstage_int<T>() + (size_t)(wib - PW_INT) * pstage_gen<T>();
+        persistent_loop<T, WREC, true>(scenes, ptasks, items, queue, n_int, n_gen, dep_off, dep_idx, samps, parity0,
+                                       n0, n_blocks, ctl, done, spin_limit, stall_item, stage0, lane);
+    } else {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(PREG_INT) : "memory");
+        float4* stage0 = smem_f4 + (size_t)wib * pstage_int<T>();
+        persistent_loop<T, WREC, false>(scenes, ptasks, items, queue, n_int, n_gen, dep_off, dep_idx, samps, parity0,
+                                        n0, n_blocks, ctl, done, spin_limit, stall_item, stage0, lane);
+    }
+}
+
+// dynamic shared memory of the persistent kernel: the interior warps' staging,
+// then the general warps'
+static size_t persistent_smem(int T) {
     const size_t i = (size_t)stages_for(T, false) * stage_f4(false);
-    return (size_t)warps * (g > i ? g : i) * sizeof(float4);
+    const size_t g = (size_t)stages_for(T, true) * gen_stage_f4(true, 32 / NG_LANES);
+    return ((size_t)PW_INT * i + (size_t)PW_GEN * g) * sizeof(float4);
 }
 
 template <int T, bool WREC>
 static cudaError_t launch_persistent_T(const fdtd_ctx* c, cudaStream_t st, int parity, long long n0, int n_blocks,
                                        long long spin_limit, int* grid_out) {
-    const int warps = 8;
-    const size_t smem = persistent_smem(T, warps);
+    const int threads = (PW_INT + PW_GEN) * 32;
+    const size_t smem = persistent_smem(T);
     cudaError_t e = ensure_dyn_smem((const void*)k_tmz_persistent<T, WREC>, smem);
     if (e != cudaSuccess) return e;
+    // the register split is exact only for a kernel built at PREG_LAUNCH
+    // registers; any other count could leave setmaxnreg.inc waiting forever
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, (const void*)k_tmz_persistent<T, WREC>);
+    if (e != cudaSuccess) return e;
+    if (fa.numRegs != PREG_LAUNCH) return cudaErrorInvalidConfiguration;
     int per_sm = 0, dev = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tmz_persistent<T, WREC>, warps * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tmz_persistent<T, WREC>, threads, smem);
     if (e != cudaSuccess) return e;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -892,7 +941,7 @@ static cudaError_t launch_persistent_T(const fdtd_ctx* c, cudaStream_t st, int p
     *grid_out = grid;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(warps * 32);
+    cfg.blockDim = dim3(threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -901,15 +950,11 @@ static cudaError_t launch_persistent_T(const fdtd_ctx* c, cudaStream_t st, int p
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_tmz_persistent<T, WREC>, (const TmzDev*)c->d_scenes, (const Task*)c->d_ptasks,
-                              (const int2*)c->d_pitems, c->n_pitems, (const int*)c->d_dep_off, (const int*)c->d_dep_idx,
-                              (const Sample2*)c->d_samp, parity, n0, n_blocks, c->d_ctl, c->d_done, spin_limit,
-                              c->opt_debug_skip);
+                              (const int2*)c->d_pitems, (const int*)c->d_pq, c->n_pint, c->n_pgen,
+                              (const int*)c->d_dep_off, (const int*)c->d_dep_idx, (const Sample2*)c->d_samp, parity,
+                              n0, n_blocks, c->d_ctl, c->d_done, spin_limit, c->opt_debug_skip);
 }
 
-// n_blocks T-step blocks in one cooperative launch.  The work counter and the
-// completion counts are zeroed first; the error word ctl[2] is not: it stays set
-// from a timed-out launch until fdtd_sync reports it, so a later launch of the
-// same step call neither advances the fields nor overwrites the flag.
 int tmz_persistent_launch(fdtd_ctx* c, int T, long long n0, int n_blocks, int parity) {
     cudaError_t e = cudaMemsetAsync(c->d_ctl, 0, 2 * sizeof(unsigned), c->stream);
     if (e == cudaSuccess && c->n_pitems > 0)
