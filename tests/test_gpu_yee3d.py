@@ -221,3 +221,27 @@ def test_3d_full_size_512_light_cone(kernel, tblock):
         assert np.count_nonzero(g) == 0, c
         del g
     sim.close()
+
+
+def test_3d_options():
+    """3D contexts default to the two-step kernel with automatic segments;
+    FDTD_OPT_TBLOCK takes 1 or 2 there, FDTD_OPT_SEGMENT 0 (automatic) or >= 1."""
+    from paper_2405_00814_gb300 import fdtd
+    sc = scenes.box_scene(side=24, nsteps=8, npml=4, n_boxes=3)
+    sim = fdtd.from_scene(sc)
+    assert sim.get_option("tblock") == 2
+    assert sim.get_option("segment") == 0
+    for bad in (0, 3, 4):
+        with pytest.raises(fdtd.FDTDError) as ei:
+            sim.set_option("tblock", bad)
+        assert ei.value.code == fdtd.EINVAL
+    with pytest.raises(fdtd.FDTDError):
+        sim.set_option("segment", -1)
+    sim.set_option("segment", 5)
+    sim.step(3)                       # a pair, then a one-step launch
+    sim.set_option("segment", 0)
+    sim.set_option("tblock", 1)
+    sim.step(2)
+    sim.sync()
+    assert sim.time_step == 5
+    sim.close()
