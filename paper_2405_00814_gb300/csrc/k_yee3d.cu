@@ -3,12 +3,16 @@
 // two layers (H from curl E, then E from curl H), per-cell Ca and Cb from eq. (7)
 // for all three E components of a cell, and a CPML of twelve auxiliaries.
 //
-// Layout: every array is [nz + 2][ny + 2][pitch] FP32 with one zero pad cell on
-// each side; cell (i, j, k) sits at ((k + 1)(ny + 2) + j + 1) pitch + i + 1, pitch
-// = round_up(nx + 2, 32).  Tangential E on the walls i|j|k = 0 is never updated
-// (stays zero); the pads are the ghost walls at N.  Fields are updated in place:
-// one H launch and one E launch per step, then a small source/probe launch and
-// the plane DFT.
+// Layout: every array is [nz + 2][ny + 2][pitch] FP32 with one zero pad row and
+// plane on each side and a 32-cell left pad; cell (i, j, k) sits at
+// ((k + 1)(ny + 2) + j + 1) pitch + i + 32, the pitch a multiple of 32 wide
+// enough for every kernel's last tile.  Tangential E on the walls i|j|k = 0 is
+// never updated (stays zero); the pads are the ghost walls at N.  Three step
+// paths: the two-step z-marching kernel (default: two steps per HBM pass), the
+// one-step z-marching kernel, and an unfused H launch plus E launch per step
+// updating in place.  The z-marching kernels read one copy of every array and
+// write the other.  After each step a small launch adds the source and records
+// the probes, and the plane DFT accumulates.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
