@@ -66,6 +66,7 @@ struct Scene3 {
     int* d_s2idx;
     int* d_s2tiles;
     int n_s2int, n_s2pml;
+    int s2_xs;             // x-slab lanes per warp of the widest tile (the CPML build's slots)
     int s2_seg;
     cudaStream_t aux;      // second stream: the tiles without CPML run beside the others
     cudaEvent_t ev_fork, ev_join;
@@ -745,7 +746,7 @@ __global__ void k_dft_cells3(const float* rec, int n_rec, int slot0, int n_cells
 constexpr int TX2 = 120;           // owned cells per tile row (lanes 1 .. 30)
 constexpr int NE2 = 4;             // E ring slots: planes q .. q + 3
 constexpr int MAXP2 = 4;           // plane monitors the kernel updates itself
-constexpr int T2_ROWS = 9;         // owned rows per tile (12 warps)
+constexpr int T2_ROWS = 13;        // owned rows per tile (16 warps)
 
 struct Extra2 {
     const float* wave;             // source waveform: step n adds wave[n] (n < wlen)
@@ -762,13 +763,14 @@ struct Extra2 {
     long long n;                   // index of the first of the two steps
 };
 
+// xs: x-slab lanes per warp the CPML build keeps auxiliaries for
 template <int TY, bool PML>
-constexpr size_t t2_smem() {
+constexpr size_t t2_smem(int xs) {
     return ((size_t)NE2 * 3 * (TY + 4) * 32      // E ring [NE2][3][TY + 4][32]
             + (size_t)4 * (TY + 3) * 2 * 32      // H1 rows, E1 rows (two parities), H2 rows
             + 256                                // coefficient table
             + 128                                // x-profiles of the 128 columns
-            + (PML ? (size_t)12 * (TY + 3) * 32 : 0)) * sizeof(float4);   // x-slab psi, per thread
+            + (PML ? (size_t)12 * (TY + 3) * xs : 0)) * sizeof(float4);   // x-slab psi, per slab lane
 }
 
 __device__ __forceinline__ float4 f4sub(const float4 a, const float4 b) {
@@ -805,7 +807,7 @@ __device__ __forceinline__ float4 ld4(const float* base, size_t g) { return *rei
 
 template <int TY, bool PML>
 __global__ void __launch_bounds__((TY + 3) * 32, 1) k_yee3d_t2(Dev3 S, Bufs3 B, Extra2 X, int segz, const int* tiles,
-                                                                  int gx, int gy) {
+                                                                  int gx, int gy, int xs) {
     constexpr int NW = TY + 3, ER = TY + 4, NT = NW * 32;
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ float4 sm4[];
@@ -815,11 +817,12 @@ __global__ void __launch_bounds__((TY + 3) * 32, 1) k_yee3d_t2(Dev3 S, Bufs3 B, 
     float4* bH2 = bE1 + 2 * NW * 2 * 32;                     // [NW][2][32]: Hx, Hz of step 2
     float4* coef_s = bH2 + NW * 2 * 32;                      // [256]
     float* Xp = reinterpret_cast<float*>(coef_s + 256);      // [4][128]: bHx cHx bEx cEx
-    // x-slab lanes' CPML auxiliaries (HYX HZX EYX EZX), each thread its own
-    // column: the next plane's stored values (cp.async, one plane ahead) and the
-    // first step's values by plane parity
-    float4* px0 = reinterpret_cast<float4*>(Xp + 4 * 128);      // [4][NT]
-    float4* px1 = px0 + 4 * NT;                                 // [2][4][NT]
+    // x-slab lanes' CPML auxiliaries (HYX HZX EYX EZX), a slot per slab lane of
+    // each warp (xs per warp): the next plane's stored values (cp.async, one
+    // plane ahead) and the first step's values by plane parity
+    const int PS = NW * xs;                                      // slots per auxiliary
+    float4* px0 = reinterpret_cast<float4*>(Xp + 4 * 128);      // [4][PS]
+    float4* px1 = px0 + 4 * PS;                                 // [2][4][PS]
 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, tid = threadIdx.x;
     // this CTA's tile of the (gx, gy, planes / segz) tiling, from the list
@@ -852,7 +855,11 @@ __global__ void __launch_bounds__((TY + 3) * 32, 1) k_yee3d_t2(Dev3 S, Bufs3 B, 
     const int sb0 = X.s_off ? X.s_off[tile] : 0, sb1 = X.s_off ? X.s_off[tile + 1] : 0;
 
     // CPML reach (conservative; the profiles decide cell by cell)
-    const bool lane_px = pml && xm != 0 && (xc - 1 < npml + 1 || xc + 4 >= nx - npml - 1);
+    bool lane_px = pml && xm != 0 && (xc - 1 < npml + 1 || xc + 4 >= nx - npml - 1);
+    // this lane's slot among the warp's slab lanes (the host sizes xs for the
+    // widest tile; a lane past it would only skip its auxiliaries)
+    const int sid = w * xs + __popc(__ballot_sync(FULL, lane_px) & ((1u << lane) - 1u));
+    lane_px = lane_px && sid < (w + 1) * xs;
     const bool row_py = pml && jin && (r < npml + 1 || r >= ny - npml - 1);
     const float hby = row_py ? pr.bHy(r + 1) : 0.f, hcy = row_py ? pr.cHy(r + 1) : 0.f;
     const float eby = row_py ? pr.bEy(r + 1) : 0.f, ecy = row_py ? pr.cEy(r + 1) : 0.f;
@@ -888,14 +895,14 @@ __global__ void __launch_bounds__((TY + 3) * 32, 1) k_yee3d_t2(Dev3 S, Bufs3 B, 
     auto issue_pxh = [&](int p) {   // HYX, HZX of plane p (x-slab lanes)
         if (!PML || !lane_px || !jin || p < 0 || p >= nz || p > kB) return;
         const size_t g = gidx(p);
-        cpa16(px0 + 0 * NT + tid, B.in[P_HYX] + g, true);
-        cpa16(px0 + 1 * NT + tid, B.in[P_HZX] + g, true);
+        cpa16(px0 + 0 * PS + sid, B.in[P_HYX] + g, true);
+        cpa16(px0 + 1 * PS + sid, B.in[P_HZX] + g, true);
     };
     auto issue_pxe = [&](int p) {   // EYX, EZX of plane p (x-slab lanes)
         if (!PML || !lane_px || !jin || p < 0 || p >= nz || p > kB) return;
         const size_t g = gidx(p);
-        cpa16(px0 + 2 * NT + tid, B.in[P_EYX] + g, true);
-        cpa16(px0 + 3 * NT + tid, B.in[P_EZX] + g, true);
+        cpa16(px0 + 2 * PS + sid, B.in[P_EYX] + g, true);
+        cpa16(px0 + 3 * PS + sid, B.in[P_EZX] + g, true);
     };
 
     // cp.async groups, oldest first, as every iteration q leaves them:
@@ -942,7 +949,7 @@ __global__ void __launch_bounds__((TY + 3) * 32, 1) k_yee3d_t2(Dev3 S, Bufs3 B, 
         const bool psi1 = pml && dom1 && (lane_px || row_py || kz1);
         float4* pm1 = pm[PML ? (q & 1) : 0];
 
-        float4* px1q = px1 + (size_t)(q & 1) * 4 * NT + tid;
+        float4* px1q = px1 + (size_t)(q & 1) * 4 * PS + sid;
         if constexpr (PML) asm volatile("cp.async.wait_group 2;\n" ::: "memory");   // x-psi H(q)
 
         // ---- step 1, layer 1: H1(q) of row r ----
@@ -975,10 +982,10 @@ __global__ void __launch_bounds__((TY + 3) * 32, 1) k_yee3d_t2(Dev3 S, Bufs3 B, 
                 if (lane_px) {
                     const float4 b4 = *reinterpret_cast<const float4*>(Xp + 0 * 128 + 4 * lane);
                     const float4 c4 = *reinterpret_cast<const float4*>(Xp + 1 * 128 + 4 * lane);
-                    const float4 v4 = psi_next(px0[0 * NT + tid], b4, c4, dezx, 15u);
-                    const float4 v5 = psi_next(px0[1 * NT + tid], b4, c4, deyx, 15u);
-                    px1q[0 * NT] = v4;
-                    px1q[1 * NT] = v5;
+                    const float4 v4 = psi_next(px0[0 * PS + sid], b4, c4, dezx, 15u);
+                    const float4 v5 = psi_next(px0[1 * PS + sid], b4, c4, deyx, 15u);
+                    px1q[0 * PS] = v4;
+                    px1q[1 * PS] = v5;
                     dezx = f4add(dezx, v4);
                     deyx = f4add(deyx, v5);
                 }
@@ -1032,10 +1039,10 @@ __global__ void __launch_bounds__((TY + 3) * 32, 1) k_yee3d_t2(Dev3 S, Bufs3 B, 
                 if (lane_px) {
                     const float4 b4 = *reinterpret_cast<const float4*>(Xp + 2 * 128 + 4 * lane);
                     const float4 c4 = *reinterpret_cast<const float4*>(Xp + 3 * 128 + 4 * lane);
-                    const float4 va = psi_next(px0[2 * NT + tid], b4, c4, dhzx, mey);
-                    const float4 vb = psi_next(px0[3 * NT + tid], b4, c4, dhyx, mez);
-                    px1q[2 * NT] = va;
-                    px1q[3 * NT] = vb;
+                    const float4 va = psi_next(px0[2 * PS + sid], b4, c4, dhzx, mey);
+                    const float4 vb = psi_next(px0[3 * PS + sid], b4, c4, dhyx, mez);
+                    px1q[2 * PS] = va;
+                    px1q[3 * PS] = vb;
                     dhzx = f4add(dhzx, va);
                     dhyx = f4add(dhyx, vb);
                 }
@@ -1088,7 +1095,7 @@ __global__ void __launch_bounds__((TY + 3) * 32, 1) k_yee3d_t2(Dev3 S, Bufs3 B, 
         const bool psi2 = pml && dom2 && (lane_px || row_py || kz2);
         const unsigned om = (own_row && p2 >= kA) ? own_x : 0u;   // cells of plane p2 this CTA stores
         const float4* pm2 = pm[PML ? (p2 & 1) : 0];
-        const float4* px2 = px1 + (size_t)(p2 & 1) * 4 * NT + tid;   // x-slab psi of step 1 at plane p2
+        const float4* px2 = px1 + (size_t)(p2 & 1) * 4 * PS + sid;   // x-slab psi of step 1 at plane p2
         float4 h2x = z4, h2y = z4, h2z = z4;
         const bool do_h2 = w >= 1 && w <= TY + 1 && q >= kA;
         if (do_h2) {
@@ -1119,7 +1126,7 @@ __global__ void __launch_bounds__((TY + 3) * 32, 1) k_yee3d_t2(Dev3 S, Bufs3 B, 
                 if (lane_px) {
                     const float4 b4 = *reinterpret_cast<const float4*>(Xp + 0 * 128 + 4 * lane);
                     const float4 c4 = *reinterpret_cast<const float4*>(Xp + 1 * 128 + 4 * lane);
-                    const float4 v4 = psi_next(px2[0 * NT], b4, c4, dezx, 15u), v5 = psi_next(px2[1 * NT], b4, c4, deyx, 15u);
+                    const float4 v4 = psi_next(px2[0 * PS], b4, c4, dezx, 15u), v5 = psi_next(px2[1 * PS], b4, c4, deyx, 15u);
                     st4m(B.out[P_HYX], g, v4, om);
                     st4m(B.out[P_HZX], g, v5, om);
                     dezx = f4add(dezx, v4);
@@ -1188,7 +1195,7 @@ __global__ void __launch_bounds__((TY + 3) * 32, 1) k_yee3d_t2(Dev3 S, Bufs3 B, 
                 if (lane_px) {
                     const float4 b4 = *reinterpret_cast<const float4*>(Xp + 2 * 128 + 4 * lane);
                     const float4 c4 = *reinterpret_cast<const float4*>(Xp + 3 * 128 + 4 * lane);
-                    const float4 va = psi_next(px2[2 * NT], b4, c4, dhzx, mey), vb = psi_next(px2[3 * NT], b4, c4, dhyx, mez);
+                    const float4 va = psi_next(px2[2 * PS], b4, c4, dhzx, mey), vb = psi_next(px2[3 * PS], b4, c4, dhyx, mez);
                     st4m(B.out[P_EYX], g, va, om);
                     st4m(B.out[P_EZX], g, vb, om);
                     dhzx = f4add(dhzx, va);
@@ -1367,6 +1374,7 @@ int fdtd_create3(const fdtd_grid* g, double dx, double dt, double courant, const
     s->d_mat = nullptr; s->d_coef = nullptr; s->d_prof = nullptr; s->d_src = nullptr; s->d_samp = nullptr;
     s->d_rec = nullptr;
     s->d_s2off = nullptr; s->d_s2idx = nullptr; s->d_s2tiles = nullptr; s->n_s2int = s->n_s2pml = 0; s->s2_seg = -1;
+    s->s2_xs = 1;
     s->aux = nullptr; s->ev_fork = s->ev_join = nullptr;
     s->nx = g->nx; s->ny = g->ny; s->nz = g->nz; s->npml = npml;
     s->dx = dx; s->dy = dy; s->dz = dz; s->dt = dt;
@@ -1544,6 +1552,18 @@ static int build_s2(fdtd_ctx* c, Scene3* s, int segz, const dim3& g2) {
     const int np = s->npml;
     auto reach = [&](int v, int n) { return v >= 0 && v < n && (v < np + 1 || v >= n - np - 1); };
     std::vector<int> tint, tpml;
+    // the CPML build's x-slab lanes per warp: the most any x-tile has (the
+    // kernel's own lane predicate)
+    s->s2_xs = 1;
+    if (np > 0)
+        for (int bx = 0; bx < (int)g2.x; bx++) {
+            int n = 0;
+            for (int l = 0; l < 32; l++) {
+                const int xc = bx * TX2 - 4 + 4 * l;
+                n += (xc + 3 >= 0 && xc < s->nx && (xc - 1 < np + 1 || xc + 4 >= s->nx - np - 1)) ? 1 : 0;
+            }
+            s->s2_xs = std::max(s->s2_xs, n);
+        }
     for (int t = 0; t < ncta; t++) {
         const int bx = t % (int)g2.x, by = (t / (int)g2.x) % (int)g2.y, bz = t / (int)(g2.x * g2.y);
         bool p = false;
@@ -1606,19 +1626,33 @@ int fdtd_step3(fdtd_ctx* c, int64_t n_steps) {
     // at most MAXP2 plane monitors itself
     int n_plane = 0;
     for (const DftMon& m : c->mons) n_plane += m.plane_k >= 0 ? 1 : 0;
-    const bool two = c->opt_kernel != 1 && c->opt_tblock == 2 && n_plane <= MAXP2 && n_steps >= 2;
+    bool two = c->opt_kernel != 1 && c->opt_tblock == 2 && n_plane <= MAXP2 && n_steps >= 2;
     const dim3 g2((s->nx + TX2 - 1) / TX2, (s->ny + T2_ROWS - 1) / T2_ROWS, (s->nz + seg2 - 1) / seg2);
-    const size_t smem2i = t2_smem<T2_ROWS, false>(), smem2p = t2_smem<T2_ROWS, true>();
+    const size_t smem2i = t2_smem<T2_ROWS, false>(0);
     if (c->opt_kernel != 1) {
         cudaError_t ea = ensure_dyn_smem((const void*)k_yee3d_fused, smem3);
         if (ea == cudaSuccess && two) ea = ensure_dyn_smem((const void*)k_yee3d_t2<T2_ROWS, false>, smem2i);
-        if (ea == cudaSuccess && two && s->npml)
-            ea = ensure_dyn_smem((const void*)k_yee3d_t2<T2_ROWS, true>, smem2p);
         if (ea != cudaSuccess) return fail3(c, FDTD_ECUDA, "fused 3D kernel: %s", cudaGetErrorString(ea));
     }
+    size_t smem2p = 0;
     if (two) {
         rc = build_s2(c, s, seg2, g2);
         if (rc) return rc;
+        smem2p = t2_smem<T2_ROWS, true>(s->s2_xs);
+        // a CPML so thick that a tile's slab lanes overflow shared memory: steps
+        // run the one-step kernel
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (s->npml && smem2p > (size_t)optin) two = false;
+    }
+    if (two) {
+        if (s->npml) {
+            cudaError_t ea = ensure_dyn_smem((const void*)k_yee3d_t2<T2_ROWS, true>, smem2p);
+            if (ea != cudaSuccess)
+                return fail3(c, FDTD_ECUDA, "two-step 3D kernel, %zu B of shared memory (%d x-slab lanes per warp): %s",
+                             smem2p, s->s2_xs, cudaGetErrorString(ea));
+        }
         for (DftMon& m : c->mons)
             if (m.plane_k >= 0 && !m.d_e1) {
                 const size_t b = (size_t)3 * s->rows * s->pitch * sizeof(float);
@@ -1699,12 +1733,12 @@ int fdtd_step3(fdtd_ctx* c, int64_t n_steps) {
             }
             if (s->n_s2int > 0) {
                 k_yee3d_t2<T2_ROWS, false><<<s->n_s2int, nthr, smem2i, fork ? s->aux : c->stream>>>(
-                    d, b2, x, seg2, s->d_s2tiles, (int)g2.x, (int)g2.y);
+                    d, b2, x, seg2, s->d_s2tiles, (int)g2.x, (int)g2.y, 0);
                 c->launches++;
             }
             if (s->n_s2pml > 0) {
                 k_yee3d_t2<T2_ROWS, true><<<s->n_s2pml, nthr, smem2p, c->stream>>>(
-                    d, b2, x, seg2, s->d_s2tiles + s->n_s2int, (int)g2.x, (int)g2.y);
+                    d, b2, x, seg2, s->d_s2tiles + s->n_s2int, (int)g2.x, (int)g2.y, s->s2_xs);
                 c->launches++;
             }
             if (fork) {

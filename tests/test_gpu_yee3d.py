@@ -245,3 +245,19 @@ def test_3d_options():
     sim.sync()
     assert sim.time_step == 5
     sim.close()
+
+
+def test_3d_thick_cpml_falls_back_to_one_step():
+    """A 62-cell CPML on a 128^3 grid puts every lane of a tile in the x-slab,
+    more auxiliary slots than the two-step kernel's shared memory holds; the
+    steps run the one-step kernel and still equal the oracle."""
+    from paper_2405_00814_gb300 import fdtd
+    sc = scenes.box_scene(side=128, nsteps=20, npml=62, n_boxes=4)
+    sc.source = scenes.Source(64, 64, 64, component="ez", kind="ricker", params=(60e9,))
+    o = _oracle3(sc, 20)
+    sim = fdtd.from_scene(sc)
+    assert sim.get_option("tblock") == 2
+    sim.step(20)
+    for c in COMPS:
+        assert rel_l2(sim.get_field(c, (sc.nz, sc.ny, sc.nx)), o[c]) <= TOL_FIELD, c
+    sim.close()
