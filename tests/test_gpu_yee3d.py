@@ -261,3 +261,40 @@ def test_3d_thick_cpml_falls_back_to_one_step():
     for c in COMPS:
         assert rel_l2(sim.get_field(c, (sc.nz, sc.ny, sc.nx)), o[c]) <= TOL_FIELD, c
     sim.close()
+
+
+@pytest.mark.parametrize("n_planes", [2, 5])
+def test_3d_two_step_several_monitors(n_planes):
+    """Plane monitors on both sides of a z-segment boundary (the two-step kernel
+    copies each plane's E after the first step; more than four planes send every
+    step through the one-step kernel) and a cell monitor whose first-step
+    samples the kernel records: each plane DFT equals the oracle's, and the cell
+    DFT equals the direct FP64 sum dt Σ_n E^n e^{-i 2π f (n+1) dt} over the
+    oracle's samples, over an odd number of steps."""
+    import oracle
+    from paper_2405_00814_gb300 import fdtd
+    n = 61
+    sc = scenes.box_scene(side=40, nsteps=n, npml=6, n_boxes=10)
+    sc.source = scenes.Source(20, 20, 20, component="ez", kind="ricker", params=(40e9,))
+    freqs = np.array([15e9, 35e9])
+    planes = [5, 23, 24, 28, 31][:n_planes]
+    cells = np.array([(12, 14, 22), (25, 9, 30), (30, 30, 10)], np.int32)
+    sim = fdtd.from_scene(sc)
+    sim.set_option("segment", 24)
+    mids = [sim.add_dft_plane(k, ("ex", "ey", "ez"), freqs) for k in planes]
+    cmid = sim.add_dft_monitor(cells, freqs)
+    sim.step(n)
+    for k, mid in zip(planes, mids):
+        osim = oracle.Yee3D(sc, nsteps_src=n)
+        osim.run(n, plane_k=k, freqs=freqs)
+        ref = osim.plane[0] + 1j * osim.plane[1]
+        got = sim.read_dft(mid)
+        assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref)), k
+    osim = oracle.Yee3D(sc, nsteps_src=n)
+    out = osim.run(n, samples=[(int(i), int(j), int(k), "ez") for i, j, k in cells])
+    e = out["samples"]                                   # [n, cells]
+    ph = np.exp(-2j * np.pi * np.outer(np.arange(1, n + 1) * sc.dt, freqs))   # [n, f]
+    ref = sc.dt * np.einsum("nc,nf->cf", e, ph)
+    got = sim.read_dft(cmid)
+    assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
+    sim.close()
