@@ -733,19 +733,22 @@ __global__ void k_dft_cells3(const float* rec, int n_rec, int slot0, int n_cells
 //   step 1 at plane q:     H1(q) from E0(q), E0(q + 1) (staged by cp.async)
 //                          and H0(q); E1(q) from H1(q) of the row and the row
 //                          below (shared memory) and H1(q - 1) (registers);
-//                          then the step's source, probe cells and plane DFT;
+//                          then the step's source and probe cells, and a copy
+//                          of each monitored plane for the DFT launch after;
 //   step 2 at plane q - 1: H2(q - 1) from E1(q - 1), E1(q) and E1(q - 1) of the
 //                          row above (shared memory, by plane parity); E2(q - 1)
 //                          from H2(q - 1) of the row and the row below and
 //                          H2(q - 2).
 // Values outside the grid are forced to zero at both steps (they are the PEC
-// ghost walls).  The first step's CPML auxiliaries wait in thread-local memory,
-// by plane parity, for the second step.  Reads buffer `in`, writes buffer `out`;
-// only the owned cells of the second step are stored.
+// ghost walls).  The first step's CPML auxiliaries wait, by plane parity, for
+// the second step: an x-slab lane's in shared-memory slots, the y and z ones in
+// thread-local memory.  The CTA's tile comes from a list (the tiles clear of the
+// CPML run a build without it).  Reads buffer `in`, writes buffer `out`; only
+// the owned cells of the second step are stored.
 // ---------------------------------------------------------------------------
 constexpr int TX2 = 120;           // owned cells per tile row (lanes 1 .. 30)
 constexpr int NE2 = 4;             // E ring slots: planes q .. q + 3
-constexpr int MAXP2 = 4;           // plane monitors the kernel updates itself
+constexpr int MAXP2 = 4;           // plane monitors the kernel copies planes for
 constexpr int T2_ROWS = 13;        // owned rows per tile (16 warps)
 
 struct Extra2 {
