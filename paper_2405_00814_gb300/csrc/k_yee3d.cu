@@ -65,6 +65,7 @@ struct Scene3 {
     int* d_s2off;
     int* d_s2idx;
     int* d_s2tiles;
+    int* d_s2zb;           // z-segment bounds
     int n_s2int, n_s2pml;
     int s2_xs;             // x-slab lanes per warp of the widest tile (the CPML build's slots)
     int s2_seg;
@@ -809,7 +810,7 @@ __device__ __forceinline__ void st4m(float* base, size_t g, const float4 v, unsi
 __device__ __forceinline__ float4 ld4(const float* base, size_t g) { return *reinterpret_cast<const float4*>(base + g); }
 
 template <int TY, bool PML>
-__global__ void __launch_bounds__((TY + 3) * 32, 1) k_yee3d_t2(Dev3 S, Bufs3 B, Extra2 X, int segz, const int* tiles,
+__global__ void __launch_bounds__((TY + 3) * 32, 1) k_yee3d_t2(Dev3 S, Bufs3 B, Extra2 X, const int* zb, const int* tiles,
                                                                   int gx, int gy, int xs) {
     constexpr int NW = TY + 3, ER = TY + 4, NT = NW * 32;
     constexpr unsigned FULL = 0xffffffffu;
@@ -828,11 +829,12 @@ __global__ void __launch_bounds__((TY + 3) * 32, 1) k_yee3d_t2(Dev3 S, Bufs3 B, 
     float4* px1 = px0 + 4 * PS;                                 // [2][4][PS]
 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, tid = threadIdx.x;
-    // this CTA's tile of the (gx, gy, planes / segz) tiling, from the list
+    // this CTA's tile of the (gx, gy, z-segments) tiling, from the list; segment
+    // bz holds planes [zb[bz], zb[bz + 1])
     const int tile = tiles[blockIdx.x];
     const int bx = tile % gx, by = (tile / gx) % gy, bz = tile / (gx * gy);
     const int xo = bx * TX2, yo = by * TY;
-    const int kA = bz * segz, kB = min(kA + segz, S.nz);
+    const int kA = zb[bz], kB = zb[bz + 1];
     const int pitch = S.pitch, rows = S.rows, nx = S.nx, ny = S.ny, nz = S.nz;
     const int r = yo - 2 + w;                  // this warp's row
     const int xc = xo - 4 + 4 * lane;          // first of this lane's cells
@@ -1260,6 +1262,7 @@ void scene3_free(Scene3* s) {
     if (s->d_s2off) cudaFree(s->d_s2off);
     if (s->d_s2idx) cudaFree(s->d_s2idx);
     if (s->d_s2tiles) cudaFree(s->d_s2tiles);
+    if (s->d_s2zb) cudaFree(s->d_s2zb);
     if (s->ev_fork) cudaEventDestroy(s->ev_fork);
     if (s->ev_join) cudaEventDestroy(s->ev_join);
     if (s->aux) cudaStreamDestroy(s->aux);
@@ -1376,7 +1379,8 @@ int fdtd_create3(const fdtd_grid* g, double dx, double dt, double courant, const
     for (int q = 0; q < G_COUNT; q++) s->f[q] = s->g[q] = nullptr;
     s->d_mat = nullptr; s->d_coef = nullptr; s->d_prof = nullptr; s->d_src = nullptr; s->d_samp = nullptr;
     s->d_rec = nullptr;
-    s->d_s2off = nullptr; s->d_s2idx = nullptr; s->d_s2tiles = nullptr; s->n_s2int = s->n_s2pml = 0; s->s2_seg = -1;
+    s->d_s2off = nullptr; s->d_s2idx = nullptr; s->d_s2tiles = nullptr; s->d_s2zb = nullptr;
+    s->n_s2int = s->n_s2pml = 0; s->s2_seg = -1;
     s->s2_xs = 1;
     s->aux = nullptr; s->ev_fork = s->ev_join = nullptr;
     s->nx = g->nx; s->ny = g->ny; s->nz = g->nz; s->npml = npml;
@@ -1538,13 +1542,35 @@ int fdtd_add_dft_plane3(fdtd_ctx* c, int k, int comp_mask, const double* freqs, 
     return FDTD_OK;
 }
 
-// samples by owning CTA of the two-step kernel's tiling (TX2 x T2_ROWS x segz)
-static int build_s2(fdtd_ctx* c, Scene3* s, int segz, const dim3& g2) {
-    if (s->s2_seg == segz) return FDTD_OK;
+// z-segments of the two-step kernel: [zb[b], zb[b + 1]).  Uniform segments of
+// segz planes; with `align` and a CPML, the planes whose two-step footprint
+// meets the z-slabs' reach get segments of their own at both ends, and the
+// planes between are split evenly into segments of at most segz, so that the
+// tiles there can run the build without the CPML.
+static std::vector<int> z_bounds(int nz, int npml, int segz, bool align) {
+    std::vector<int> zb{0};
+    const int z1 = npml + 3, z2 = nz - npml - 2;   // [z1, z2): footprints clear of the z-slabs
+    if (align && npml > 0 && z2 - z1 >= 1) {
+        zb.push_back(z1);
+        const int m = (z2 - z1 + segz - 1) / segz;
+        for (int q = 1; q <= m; q++) zb.push_back(z1 + (int)((long long)(z2 - z1) * q / m));
+        zb.push_back(nz);
+    } else {
+        for (int k = segz; k < nz; k += segz) zb.push_back(k);
+        zb.push_back(nz);
+    }
+    return zb;
+}
+
+// samples by owning CTA of the two-step kernel's tiling (TX2 x T2_ROWS x the
+// z-segments zb), the tile lists and the segment bounds on the device
+static int build_s2(fdtd_ctx* c, Scene3* s, int key, const std::vector<int>& zb, const dim3& g2) {
+    if (s->s2_seg == key) return FDTD_OK;
     const int ncta = (int)(g2.x * g2.y * g2.z);
     std::vector<int> cnt((size_t)ncta + 1, 0), idx(std::max<size_t>(1, s->samples.size()));
+    auto seg_of = [&](int k) { return (int)(std::upper_bound(zb.begin(), zb.end(), k) - zb.begin()) - 1; };
     auto cta_of = [&](const Sample3& sp) {
-        return (int)(sp.i / TX2 + g2.x * (sp.j / T2_ROWS + g2.y * (sp.k / segz)));
+        return (int)(sp.i / TX2 + g2.x * (sp.j / T2_ROWS + g2.y * seg_of(sp.k)));
     };
     for (const Sample3& sp : s->samples) cnt[cta_of(sp) + 1]++;
     for (int b = 0; b < ncta; b++) cnt[b + 1] += cnt[b];
@@ -1576,7 +1602,7 @@ static int build_s2(fdtd_ctx* c, Scene3* s, int segz, const dim3& g2) {
                 p = xc + 3 >= 0 && xc < s->nx && (xc - 1 < np + 1 || xc + 4 >= s->nx - np - 1);
             }
             for (int r = by * T2_ROWS - 2; r <= by * T2_ROWS + T2_ROWS && !p; r++) p = reach(r, s->ny);
-            for (int k = bz * segz - 2; k <= std::min(bz * segz + segz, s->nz) && !p; k++) p = reach(k, s->nz);
+            for (int k = zb[bz] - 2; k <= zb[bz + 1] && !p; k++) p = reach(k, s->nz);
         }
         (p ? tpml : tint).push_back(t);
     }
@@ -1586,11 +1612,13 @@ static int build_s2(fdtd_ctx* c, Scene3* s, int segz, const dim3& g2) {
     if (s->d_s2off) cudaFree(s->d_s2off);
     if (s->d_s2idx) cudaFree(s->d_s2idx);
     if (s->d_s2tiles) cudaFree(s->d_s2tiles);
-    s->d_s2off = s->d_s2idx = s->d_s2tiles = nullptr;
+    if (s->d_s2zb) cudaFree(s->d_s2zb);
+    s->d_s2off = s->d_s2idx = s->d_s2tiles = s->d_s2zb = nullptr;
     s->s2_seg = -1;
     if (cudaMalloc(&s->d_s2off, cnt.size() * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&s->d_s2idx, idx.size() * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&s->d_s2tiles, tint.size() * sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&s->d_s2tiles, tint.size() * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&s->d_s2zb, zb.size() * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         return fail3(c, FDTD_ENOMEM, "tables of the two-step kernel");
     }
@@ -1605,8 +1633,9 @@ static int build_s2(fdtd_ctx* c, Scene3* s, int segz, const dim3& g2) {
     CK3(cudaMemcpyAsync(s->d_s2off, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream), "samples");
     CK3(cudaMemcpyAsync(s->d_s2idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream), "samples");
     CK3(cudaMemcpyAsync(s->d_s2tiles, tint.data(), tint.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream), "tiles");
+    CK3(cudaMemcpyAsync(s->d_s2zb, zb.data(), zb.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream), "segments");
     CK3(cudaStreamSynchronize(c->stream), "samples");
-    s->s2_seg = segz;
+    s->s2_seg = key;
     return FDTD_OK;
 }
 
@@ -1630,7 +1659,9 @@ int fdtd_step3(fdtd_ctx* c, int64_t n_steps) {
     int n_plane = 0;
     for (const DftMon& m : c->mons) n_plane += m.plane_k >= 0 ? 1 : 0;
     bool two = c->opt_kernel != 1 && c->opt_tblock == 2 && n_plane <= MAXP2 && n_steps >= 2;
-    const dim3 g2((s->nx + TX2 - 1) / TX2, (s->ny + T2_ROWS - 1) / T2_ROWS, (s->nz + seg2 - 1) / seg2);
+    // automatic segments are cut at the z-slabs' reach (see z_bounds)
+    const std::vector<int> zb2 = z_bounds(s->nz, s->npml, seg2, c->opt_segment <= 0);
+    const dim3 g2((s->nx + TX2 - 1) / TX2, (s->ny + T2_ROWS - 1) / T2_ROWS, (unsigned)zb2.size() - 1);
     const size_t smem2i = t2_smem<T2_ROWS, false>(0);
     if (c->opt_kernel != 1) {
         cudaError_t ea = ensure_dyn_smem((const void*)k_yee3d_fused, smem3);
@@ -1639,7 +1670,7 @@ int fdtd_step3(fdtd_ctx* c, int64_t n_steps) {
     }
     size_t smem2p = 0;
     if (two) {
-        rc = build_s2(c, s, seg2, g2);
+        rc = build_s2(c, s, 2 * seg2 + (c->opt_segment <= 0 ? 1 : 0), zb2, g2);
         if (rc) return rc;
         smem2p = t2_smem<T2_ROWS, true>(s->s2_xs);
         // a CPML so thick that a tile's slab lanes overflow shared memory: steps
@@ -1736,12 +1767,12 @@ int fdtd_step3(fdtd_ctx* c, int64_t n_steps) {
             }
             if (s->n_s2int > 0) {
                 k_yee3d_t2<T2_ROWS, false><<<s->n_s2int, nthr, smem2i, fork ? s->aux : c->stream>>>(
-                    d, b2, x, seg2, s->d_s2tiles, (int)g2.x, (int)g2.y, 0);
+                    d, b2, x, s->d_s2zb, s->d_s2tiles, (int)g2.x, (int)g2.y, 0);
                 c->launches++;
             }
             if (s->n_s2pml > 0) {
                 k_yee3d_t2<T2_ROWS, true><<<s->n_s2pml, nthr, smem2p, c->stream>>>(
-                    d, b2, x, seg2, s->d_s2tiles + s->n_s2int, (int)g2.x, (int)g2.y, s->s2_xs);
+                    d, b2, x, s->d_s2zb, s->d_s2tiles + s->n_s2int, (int)g2.x, (int)g2.y, s->s2_xs);
                 c->launches++;
             }
             if (fork) {

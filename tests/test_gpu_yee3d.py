@@ -121,7 +121,9 @@ def _random_state3(nx, ny, nz, seed):
     (2, 4, 41, 5, (250, 23, 19)), (2, 19, 40, 5, (250, 23, 19)), (2, 3, 23, 0, (250, 23, 19)),
     (1, 4, 41, 5, (250, 23, 19)),
     # tiles clear of the CPML (the build without it, on the second stream) beside tiles in its reach
-    (2, 8, 30, 4, (370, 40, 40))])
+    (2, 8, 30, 4, (370, 40, 40)),
+    # automatic segments: thin segments at the z-slabs, the planes between clear of them
+    (2, 0, 31, 4, (370, 40, 40))])
 def test_3d_rectangular_three_x_tiles(tblock, segz, n, npml, shape):
     """A 250 x 23 x 19 grid (three 120-cell x-tiles of the two-step kernel, the
     last one 10 cells wide; or 370 x 40 x 40, where some tiles are clear of the
