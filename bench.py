@@ -476,6 +476,9 @@ def main():
     ap.add_argument("--warps", type=int, default=None)
     ap.add_argument("--segment-b", type=int, default=None, help="FDTD_OPT_SEGMENT_B (boundary task rows; 0 = automatic)")
     ap.add_argument("--kernel", type=int, default=None, help="FDTD_OPT_KERNEL (default 0)")
+    ap.add_argument("--warps-b", type=int, default=None, help="FDTD_OPT_WARPS_B (warps per CPML CTA)")
+    ap.add_argument("--taper", type=int, default=None, help="FDTD_OPT_TAPER (percent of interior rows in "
+                    "half-height tail segments; 0 = uniform)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-sample", type=int, default=20)
@@ -535,10 +538,11 @@ def main():
     nsteps = args.nsteps or sc.nsteps
     sim = fdtd.from_scene(sc, stream=stream)
     # kernel options: the library's autotuner on this scene, unless given
-    manual = any(getattr(args, k) is not None for k in ("tblock", "segment", "warps", "kernel", "segment_b"))
+    manual = any(getattr(args, k) is not None for k in ("tblock", "segment", "warps", "kernel", "segment_b", "taper",
+                                                   "warps_b"))
     if manual:
-        tune = {"tblock": 4, "segment": 24, "warps": 8, "segment_b": 0}
-        for k in ("tblock", "segment", "warps", "segment_b"):
+        tune = {"tblock": 4, "segment": 24, "warps": 8, "segment_b": 0, "taper": 0, "warps_b": 2}
+        for k in ("tblock", "segment", "warps", "segment_b", "taper", "warps_b"):
             if getattr(args, k) is not None:
                 tune[k] = getattr(args, k)
         if args.kernel is None:
@@ -549,7 +553,7 @@ def main():
     else:
         sim.autotune(trial_steps=32)
         args.kernel = sim.get_option("kernel")
-        tune = {k: sim.get_option(k) for k in ("tblock", "segment", "warps", "segment_b")}
+        tune = {k: sim.get_option(k) for k in ("tblock", "segment", "warps", "segment_b", "taper", "warps_b")}
     # each solve (reset + n steps from t = 0) is recorded once into a CUDA graph
     # and replayed (FDTD_OPT_GRAPH); the warm-up solves record it
     graph = not args.no_graph and args.kernel != 1
@@ -617,7 +621,7 @@ def main():
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": workload, "cells": sc.cells, "leapfrog_steps_per_bench_step": nsteps,
                       "tblock": T, "segment": tune["segment"], "warps_per_cta": tune["warps"],
-                      "segment_b": tune["segment_b"],
+                      "segment_b": tune["segment_b"], "taper": tune["taper"], "warps_b": tune["warps_b"],
                       "kernel_options": "manual" if manual else "fdtd_autotune on this scene",
                       "cuda_graph": graph,
                       "l2": "inputs larger than L2 (fields 2x3x70 MB + material 17 MB)",

@@ -118,6 +118,15 @@ extern "C" {
                                   passes a multiple of N (at the end of that T-step block; one extra launch over
                                   Ez, Hx, Hy), into a sticky device flag that fdtd_sync reports as FDTD_EUNSTABLE
                                   -- a blow-up found without synchronising the time loop; 0 (default) = off */
+#define FDTD_OPT_TAPER 10    /* 2D, kernel 0: percent (0..60) of each strip's interior rows cut into tail
+                                segments of half the FDTD_OPT_SEGMENT height; the interior list then runs
+                                its CTAs tallest first (on the GPU, CTAs start in launch order), so the short
+                                tasks fill the SMs the tall ones leave at the end of a T-step block.  0 (default)
+                                = uniform segments in space order.  Results do not depend on it */
+#define FDTD_OPT_WARPS_B 11  /* 2D, kernels 0 and 2: warps per CTA of the CPML kernels of the forward step, 1..8
+                                (default 2).  A CPML CTA holds 7 staged rows of 7 arrays per warp and about 220
+                                registers per thread, so it leaves room for fewer interior CTAs on its SM; wider
+                                CPML CTAs put the CPML warps on fewer SMs.  Results do not depend on it */
 
 typedef struct fdtd_ctx fdtd_ctx;
 
@@ -320,11 +329,14 @@ int fdtd_sync(fdtd_ctx* ctx);
 
 /* Pick the 2D kernel options for the current scenes (one large scene, or a
  * batch: Sec. V-A runs many simulations of varying size): time every candidate
- * of (kernel 0: T 2..4, segment 16..96 in steps of 4, warps 2, 4 or 8; kernel 2,
+ * of (kernel 0: T 2..4, segment 16..96 in steps of 4, warps 2, 4 or 8, CPML warps
+ * (FDTD_OPT_WARPS_B) 2, 4 or 8; kernel 2,
  * not for a split-field PML: T 2..4, segment 32, 64, 96 or 128) for trial_steps
  * steps, time the four fastest twice more for 4 x trial_steps, keep the best,
- * then for kernel 0 try FDTD_OPT_SEGMENT_B values against the automatic one
- * (kept only if 1 % faster).  Leaves the context reset (t = 0, zero fields).
+ * then for kernel 0 try FDTD_OPT_SEGMENT_B
+ * values against the automatic one, then FDTD_OPT_TAPER 10, 20, 30, 45 with the
+ * segment height raised by 0, 8, 16 or 24 rows (each kept only if 1 % faster).
+ * Leaves the context reset (t = 0, zero fields).
  * *best_ms gets the best time per step. */
 int fdtd_autotune(fdtd_ctx* ctx, int trial_steps, double* best_ms);
 

@@ -356,6 +356,9 @@ fdtd_ctx* ctx_new(void* stream) {
     c->opt_warps = 8;
     c->opt_segment = 64;
     c->opt_segment_b = 0;
+    c->opt_taper = 0;
+    c->opt_warps_b = 2;
+    c->task_warps_b = 0;
     c->dirty = true;
     c->d_scenes = nullptr;
     c->d_tasks = nullptr;
@@ -510,7 +513,7 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     const int wout = STRIP - 2 * HALO;
     std::vector<Task> tasks, tasks_b, tasks_l, tasks_s, tasks_bd, tasks_n;
     std::vector<Sample2> tsamp;
-    const int warps_b = 2;
+    const int warps_b = c->opt_warps_b;
     const bool want_narrow = c->opt_kernel == 0 || c->opt_kernel == 2;   // not the unfused pair
     bool any_design = false;
     for (const Scene2* s : c->s2) any_design = any_design || s->d_dsg != nullptr;
@@ -613,8 +616,14 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
                 y_lo = std::min(s->ny, std::max(0, s->npml - s->yoff + MAX_TB));
                 y_hi = std::max(y_lo, std::min(s->ny, s->ny_glob - s->npml - s->yoff - MAX_TB));
             }
+            // FDTD_OPT_TAPER (kernel 0): the last taper % of the rows between in
+            // half-height tail segments, which the interior list runs last
+            const int y_tail = c->opt_kernel == 0 && c->opt_taper > 0
+                                   ? y_hi - (y_hi - y_lo) * c->opt_taper / 100 / 4 * 4 : y_hi;
+            const int seg_t = std::max(8, seg / 2 / 4 * 4);
             for (int y = 0; y < y_lo; y += seg_b) segs.emplace_back(y, std::min(y + seg_b, y_lo));
-            for (int y = y_lo; y < y_hi; y += seg) segs.emplace_back(y, std::min(y + seg, y_hi));
+            for (int y = y_lo; y < y_tail; y += seg) segs.emplace_back(y, std::min(y + seg, y_tail));
+            for (int y = y_tail; y < y_hi; y += seg_t) segs.emplace_back(y, std::min(y + seg_t, y_hi));
             for (int y = y_hi; y < s->ny; y += seg_b) segs.emplace_back(y, std::min(y + seg_b, s->ny));
         }
         for (const auto& sg : segs) {
@@ -644,6 +653,26 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
             while ((tasks_bd.size() - first_bd) % warps_b) tasks_bd.push_back(pad);
         if (tasks_n.size() > first_n)   // whole CTAs of warps_b warps; a padding warp returns
             while ((tasks_n.size() - first_n) % (warps_b * 32 / NG_LANES)) tasks_n.push_back(pad);
+    }
+    // FDTD_OPT_TAPER: the interior list's CTAs (whole blocks of one scene each)
+    // tallest first, in space order among equals
+    if (c->opt_kernel == 0 && c->opt_taper > 0 && !tasks.empty()) {
+        const size_t nb = tasks.size() / (size_t)warps;
+        std::vector<std::pair<int, size_t>> key(nb);
+        for (size_t b = 0; b < nb; b++) {
+            int h = 0;
+            for (int q = 0; q < warps; q++) {
+                const Task& t = tasks[b * warps + q];
+                if (t.scene >= 0) h = std::max(h, t.yb - t.ya);
+            }
+            key[b] = {-h, b};
+        }
+        std::stable_sort(key.begin(), key.end());
+        std::vector<Task> sorted;
+        sorted.reserve(tasks.size());
+        for (const auto& kb : key)
+            sorted.insert(sorted.end(), tasks.begin() + kb.second * warps, tasks.begin() + (kb.second + 1) * warps);
+        tasks.swap(sorted);
     }
     // every list is launched in blocks of its own width: a block holds tasks of one
     // scene and starts with a real task, and every task lies inside its scene
@@ -867,6 +896,7 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     c->task_pers = c->opt_kernel == 2 ? 1 : 0;
     c->warps_l = warps_l;
     c->warps_b = warps_b;
+    c->task_warps_b = warps_b;
     c->task_tb = T;
     c->task_seg = seg;
     c->dirty = false;
@@ -903,7 +933,7 @@ int step_prepare(fdtd_ctx* c, int64_t n_steps) {
     int rc = ensure_capacity(c, c->t + n_steps);
     if (rc) return rc;
     if (c->dirty || c->task_seg != c->opt_segment || c->task_narrow != (c->opt_kernel != 1 ? 1 : 0) ||
-        c->task_pers != (c->opt_kernel == 2 ? 1 : 0)) {
+        c->task_pers != (c->opt_kernel == 2 ? 1 : 0) || c->task_warps_b != c->opt_warps_b) {
         rc = rebuild(c, c->opt_tblock, c->opt_segment, c->opt_warps);
         if (rc) return rc;
     }
@@ -1171,6 +1201,16 @@ int fdtd_set_option(fdtd_ctx* c, int option, int64_t v) {
             c->opt_segment_b = (int)v;
             c->dirty = true;
             return FDTD_OK;
+        case FDTD_OPT_TAPER:
+            if (v < 0 || v > 60) return fail(c, FDTD_EINVAL, "taper %lld outside 0..60 percent", (long long)v);
+            c->opt_taper = (int)v;
+            c->dirty = true;
+            return FDTD_OK;
+        case FDTD_OPT_WARPS_B:
+            if (v < 1 || v > 8) return fail(c, FDTD_EINVAL, "CPML warps %lld outside 1..8", (long long)v);
+            c->opt_warps_b = (int)v;
+            c->dirty = true;
+            return FDTD_OK;
         case FDTD_OPT_WARPS:
             if (v < 1 || v > 8) return fail(c, FDTD_EINVAL, "warps %lld outside 1..8", (long long)v);
             c->opt_warps = (int)v;
@@ -1193,6 +1233,8 @@ int64_t fdtd_get_option(const fdtd_ctx* c, int option) {
         case FDTD_OPT_ADJ_STORE: return c->opt_adj_store;
         case FDTD_OPT_SEGMENT_B: return c->opt_segment_b;
         case FDTD_OPT_CHECK_EVERY: return c->opt_check_every;
+        case FDTD_OPT_TAPER: return c->opt_taper;
+        case FDTD_OPT_WARPS_B: return c->opt_warps_b;
     }
     return -1;
 }
@@ -1608,26 +1650,31 @@ int fdtd_autotune(fdtd_ctx* c, int trial_steps, double* best_ms) {
     if (trial_steps < 4) return fail(c, FDTD_EINVAL, "trial_steps must be >= 4");
     if (c->adj) return fail(c, FDTD_EINVAL, "disable checkpointing before autotuning");
     if (ctx_has_slab(c)) return fail(c, FDTD_EINVAL, "autotuning covers whole grids, not slab sub-domains");
-    struct Cand { int kernel, T, seg, warps; };
+    struct Cand { int kernel, T, seg, warps, warps_b; };
     std::vector<Cand> cand;
     // the segment height sets how many CTAs a block launches, so the sweep is
-    // fine-grained: a list that fills whole waves of the 152 SMs wins
+    // fine-grained: a list that fills whole waves of the 152 SMs wins; the CPML
+    // CTAs' width sets how many SMs they share with interior CTAs
     for (int T = 2; T <= MAX_TB; T++)
         for (int seg = 16; seg <= 96; seg += 4)
-            for (int w : {2, 4, 8}) cand.push_back({0, T, seg, w});
+            for (int w : {2, 4, 8})
+                for (int wb : {2, 4, 8}) cand.push_back({0, T, seg, w, wb});
     if (!any_split(c))   // the persistent kernel has no split-field variant
         for (int T = 2; T <= MAX_TB; T++)
-            for (int seg : {32, 64, 96, 128}) cand.push_back({2, T, seg, 8});
+            for (int seg : {32, 64, 96, 128}) cand.push_back({2, T, seg, 8, 2});
     const int graph = c->opt_graph;
     c->opt_graph = 0;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "autotune");
     CK(cudaEventCreate(&e1), "autotune");
     double best = 1e30;
-    Cand win = {c->opt_kernel, c->opt_tblock, c->opt_segment, c->opt_warps};
+    Cand win = {c->opt_kernel, c->opt_tblock, c->opt_segment, c->opt_warps, c->opt_warps_b};
+    const int taper0 = c->opt_taper;
+    c->opt_taper = 0;   // the coarse pass and the boundary pass run uniform segments
     int rc = FDTD_OK;
     auto time_of = [&](const Cand& k, int steps, double* per) {
         c->opt_kernel = k.kernel; c->opt_tblock = k.T; c->opt_segment = k.seg; c->opt_warps = k.warps;
+        c->opt_warps_b = k.warps_b;
         c->dirty = true;
         int r = fdtd_reset(c);
         if (!r) r = fdtd_step(c, k.T);   // warm-up (and build) outside the timing
@@ -1686,9 +1733,36 @@ int fdtd_autotune(fdtd_ctx* c, int trial_steps, double* best_ms) {
         if (rc != FDTD_OK) win_b = saved_b;
         best = std::min(best, base);
     }
+    // then tapered interior lists (taller segments in front, half-height ones
+    // behind them, run tallest first) for the winner's T and warps
+    int win_taper = 0;
+    if (rc == FDTD_OK && win.kernel == 0) {
+        c->opt_segment_b = win_b;
+        const Cand base_k = win;
+        for (int tp : {10, 20, 30, 45}) {
+            for (int ds : {0, 8, 16, 24}) {
+                if (rc != FDTD_OK) break;
+                Cand k = base_k;
+                k.seg = base_k.seg + ds;
+                c->opt_taper = tp;
+                double per = 0, per2 = 0;
+                rc = time_of(k, 4 * trial_steps, &per);
+                if (rc == FDTD_OK) rc = time_of(k, 4 * trial_steps, &per2);
+                per = std::min(per, per2);
+                if (rc == FDTD_OK && per < 0.99 * best) {
+                    best = per;
+                    win_taper = tp;
+                    win.seg = k.seg;
+                }
+            }
+        }
+        if (rc != FDTD_OK) win_taper = taper0;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->opt_kernel = win.kernel; c->opt_tblock = win.T; c->opt_segment = win.seg; c->opt_warps = win.warps;
+    c->opt_warps_b = win.warps_b;
+    c->opt_taper = win.kernel == 0 ? win_taper : taper0;
     c->opt_segment_b = win_b;
     c->opt_graph = graph;
     c->dirty = true;

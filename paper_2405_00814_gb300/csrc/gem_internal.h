@@ -194,6 +194,8 @@ struct fdtd_ctx {
     // options
     int opt_kernel, opt_tblock, opt_segment, opt_warps;
     int opt_segment_b;           // FDTD_OPT_SEGMENT_B (0: max(8, opt_segment / 2))
+    int opt_taper;               // FDTD_OPT_TAPER: percent of interior rows in half-height tail segments
+    int opt_warps_b;             // FDTD_OPT_WARPS_B: warps per CTA of the forward CPML kernels
     // device copies for the fused kernel, rebuilt when dirty
     bool dirty;
     gem::TmzDev* d_scenes;
@@ -207,6 +209,7 @@ struct fdtd_ctx {
     gem::Task* d_tasks_n;          // narrow x-slab CPML tasks, NG_LANES lanes each (4 per warp)
     int n_tasks_n;
     int task_narrow;               // the lists were built with narrow x-slab tasks (kernels 0, 2)
+    int task_warps_b;              // the CPML lists are padded to CTAs of this many warps
     int task_pers;                 // the persistent kernel's items were built (kernel 2)
     gem::Task* d_tasks_l;          // lite tasks: design, source, probes or ragged edge, no CPML
     int n_tasks_l, warps_l;

@@ -22,7 +22,8 @@ PEC, CPML, SPLIT_PML = 0, 1, 2
 COMP = {"ex": 0, "ey": 1, "ez": 2, "hx": 3, "hy": 4, "hz": 5}
 SRC = {"ricker": 0, "gauss_mod": 1, "gauss": 2, "sampled": 3, "sine": 4}
 OPT = {"kernel": 0, "tblock": 1, "segment": 2, "warps": 3, "graph": 4, "spin_limit": 5, "debug_stall_item": 6,
-       "adj_store": 7, "segment_b": 8, "check_every": 9}
+       "adj_store": 7, "segment_b": 8, "check_every": 9, "taper": 10,
+       "warps_b": 11}
 
 
 class FDTDError(RuntimeError):
@@ -436,7 +437,8 @@ class Simulation:
         best = C.c_double(0.0)
         self._check(self._L.fdtd_autotune(self._h, int(trial_steps), C.byref(best)))
         res = {"ms_per_step": best.value,
-               "options": {k: self.get_option(k) for k in ("kernel", "tblock", "segment", "warps", "segment_b")}}
+               "options": {k: self.get_option(k) for k in ("kernel", "tblock", "segment", "warps", "segment_b", "taper",
+                                                      "warps_b")}}
         if cache and key:
             data = json.load(open(cache)) if os.path.exists(cache) else {}
             data[ck] = res

@@ -27,13 +27,15 @@ def oracle_run(scene, nsteps, probes=None, monitors=None, freqs=None):
     return res
 
 
-def gpu_run(scene, nsteps, *, kernel=0, tblock=4, segment=128, warps=2, probes=True, monitors=True):
+def gpu_run(scene, nsteps, *, kernel=0, tblock=4, segment=128, warps=2, probes=True, monitors=True, options=None):
     from paper_2405_00814_gb300 import fdtd
     sim = fdtd.from_scene(scene, probes=probes, monitors=monitors)
     sim.set_option("kernel", kernel)
     sim.set_option("tblock", tblock)
     sim.set_option("segment", segment)
     sim.set_option("warps", warps)
+    for k, v in (options or {}).items():
+        sim.set_option(k, v)
     sim.step(nsteps)
     shape = (scene.ny, scene.nx)
     res = {c: sim.get_field(c, shape) for c in ("ez", "hx", "hy")}

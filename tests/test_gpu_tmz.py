@@ -41,6 +41,60 @@ def test_heterogeneous_cpml_ragged(side, segment, warps, tblock):
     assert rel_l2(g["probes"], o["probes"]) <= TOL_FIELD
 
 
+@pytest.mark.parametrize("segment,taper,warps", [(24, 30, 4), (40, 45, 2), (16, 10, 3)])
+def test_tapered_interior_list(segment, taper, warps):
+    """Half-height tail segments, the interior CTAs run tallest first.  The
+    fields match the oracle within TOL and the uniform run to rounding (other
+    segment bounds move a few rows between the interior and the general kernel,
+    whose FMA contraction may differ)."""
+    sc = scenes.ellipse_scene(side=512, nsteps=300)
+    o = oracle_run(sc, sc.nsteps, probes=sc.probes)
+    a = gpu_run(sc, sc.nsteps, tblock=4, segment=segment, warps=warps)
+    b = gpu_run(sc, sc.nsteps, tblock=4, segment=segment, warps=warps, options={"taper": taper})
+    for c in ("ez", "hx", "hy"):
+        assert rel_l2(b[c], a[c]) < 1e-5, c
+    assert rel_l2(b["probes"], a["probes"]) < 1e-5
+    assert_fields_close(b, o)
+    assert rel_l2(b["probes"], o["probes"]) <= TOL_FIELD
+
+
+@pytest.mark.parametrize("warps_b,tblock,segment", [(1, 4, 24), (4, 4, 40), (8, 3, 16), (8, 4, 48)])
+def test_cpml_cta_width(warps_b, tblock, segment):
+    """The CPML kernels' CTAs of 1 to 8 warps (FDTD_OPT_WARPS_B): the CPML,
+    narrow x-slab and lite lists padded to other widths; oracle within TOL and
+    the 2-warp run to rounding."""
+    sc = scenes.ellipse_scene(side=384, nsteps=400)
+    o = oracle_run(sc, sc.nsteps, probes=sc.probes)
+    a = gpu_run(sc, sc.nsteps, tblock=tblock, segment=segment, warps=4)
+    b = gpu_run(sc, sc.nsteps, tblock=tblock, segment=segment, warps=4, options={"warps_b": warps_b})
+    for c in ("ez", "hx", "hy"):
+        assert rel_l2(b[c], a[c]) < 1e-5, c
+    assert_fields_close(b, o)
+    assert rel_l2(b["probes"], o["probes"]) <= TOL_FIELD
+
+
+def test_tapered_batch_of_uneven_scenes():
+    """The tallest-first order moves whole CTAs between scenes of a batch."""
+    from paper_2405_00814_gb300 import fdtd
+    scs = scenes.batch_scenes(n_scenes=3, nsteps=400, side_lo=96, side_hi=300)
+    sim = fdtd.Simulation.batch(scs)
+    for k, s in enumerate(scs):
+        sim.select(k)
+        sim.set_scene_source(s.source)
+    sim.set_option("segment", 24)
+    sim.set_option("warps", 4)
+    sim.set_option("taper", 40)
+    sim.set_option("warps_b", 8)
+    assert sim.get_option("taper") == 40 and sim.get_option("warps_b") == 8
+    sim.step(400)
+    for k, s in enumerate(scs):
+        o = oracle_run(s, 400)
+        sim.select(k)
+        g = {c: sim.get_field(c, (s.ny, s.nx)) for c in ("ez", "hx", "hy")}
+        assert_fields_close(g, o)
+    sim.close()
+
+
 def test_unfused_and_fused_agree_to_rounding():
     sc = scenes.ellipse_scene(side=200, nsteps=500)
     a = gpu_run(sc, sc.nsteps, kernel=1)
@@ -169,6 +223,12 @@ def test_invalid_inputs_rejected():
         sim.add_probe(40, 3)
     with pytest.raises(fdtd.FDTDError):
         sim.set_option("tblock", 9)
+    for bad_taper in (-1, 61):
+        with pytest.raises(fdtd.FDTDError):
+            sim.set_option("taper", bad_taper)
+    for bad_wb in (0, 9):
+        with pytest.raises(fdtd.FDTDError):
+            sim.set_option("warps_b", bad_wb)
     sim.step(3)
     with pytest.raises(fdtd.FDTDError):
         sim.add_probe(3, 3)                                   # after stepping
