@@ -257,16 +257,18 @@ def batch_throughput(stream, reps=2):
     # the same solve as one persistent cooperative launch (FDTD_OPT_KERNEL = 2:
     # every scene's work items, all 2000 steps, each item waiting only for its
     # neighbours' previous block), captured in a CUDA graph: the autotuner's
-    # persistent options if it chose them, else T = 4 and the better of two
-    # segment heights
+    # persistent options if it chose them, else T = 4 and the best of three
+    # segment heights and five CTA layouts (FDTD_OPT_PLAYOUT)
     opts = tune["options"]
     sim.set_option("kernel", 2)
-    segs = [opts["segment"]] if opts["kernel"] == 2 else [64, 96, 128]
-    pbest, pseg = None, None
-    for seg in segs:
+    trials = ([(opts["segment"], opts["playout"])] if opts["kernel"] == 2 else
+              [(seg, pl) for seg in (64, 96, 128) for pl in (0, 16, 24, 32, 48)])
+    pbest, pseg, pplay = None, None, None
+    for seg, pl in trials:
         if opts["kernel"] != 2:
             sim.set_option("tblock", 4)
             sim.set_option("segment", seg)
+            sim.set_option("playout", pl)
         for _ in range(reps + 1):
             sim.reset()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -276,7 +278,7 @@ def batch_throughput(stream, reps=2):
             sim.sync()
             ms = e0.elapsed_time(e1)
             if pbest is None or ms < pbest:
-                pbest, pseg = ms, seg
+                pbest, pseg, pplay = ms, seg, pl
     sim.close()
     cells = sum(s.cells for s in scs)
     return {"workload": "batch64_tmz2d_sides256-2048_cpml12_2000steps", "cells": cells,
@@ -284,7 +286,7 @@ def batch_throughput(stream, reps=2):
             "autotuned": tune["options"], "graph": True,
             "persistent_one_launch": {"cell_updates_per_s": cells * nsteps / (pbest / 1e3), "ms_per_solve": pbest,
                                       "tblock": 4 if opts["kernel"] != 2 else opts["tblock"],
-                                      "segment": pseg},
+                                      "segment": pseg, "playout": pplay},
             "timing": "CUDA events around one solve replayed from a CUDA graph, best of %d after one warm-up" % reps}
 
 

@@ -127,6 +127,11 @@ extern "C" {
                                 (default 2).  A CPML CTA holds 7 staged rows of 7 arrays per warp and about 220
                                 registers per thread, so it leaves room for fewer interior CTAs on its SM; wider
                                 CPML CTAs put the CPML warps on fewer SMs.  Results do not depend on it */
+#define FDTD_OPT_PLAYOUT 12  /* 2D, kernel 2 (T 2..4, not in edge-weight mode): the persistent launch's CTAs.
+                                0 (default) = one 12-warp CTA per SM, 8 interior warps at 128 registers and 4
+                                general warps at 248; k >= 1 = one 16-warp CTA per SM, the first k (at most all
+                                but one) running general and narrow items on 8 warps at 232 registers, every
+                                other CTA 16 interior warps at 128.  Results do not depend on it */
 
 typedef struct fdtd_ctx fdtd_ctx;
 
@@ -331,7 +336,8 @@ int fdtd_sync(fdtd_ctx* ctx);
  * batch: Sec. V-A runs many simulations of varying size): time every candidate
  * of (kernel 0: T 2..4, segment 16..96 in steps of 4, warps 2, 4 or 8, CPML warps
  * (FDTD_OPT_WARPS_B) 2, 4 or 8; kernel 2,
- * not for a split-field PML: T 2..4, segment 32, 64, 96 or 128) for trial_steps
+ * not for a split-field PML: T 2..4, segment 32, 64, 96 or 128, FDTD_OPT_PLAYOUT
+ * 0, 16, 24, 32 or 48) for trial_steps
  * steps, time the four fastest twice more for 4 x trial_steps, keep the best,
  * then for kernel 0 try FDTD_OPT_SEGMENT_B
  * values against the automatic one, then FDTD_OPT_TAPER 10, 20, 30, 45 with the

@@ -358,6 +358,7 @@ fdtd_ctx* ctx_new(void* stream) {
     c->opt_segment_b = 0;
     c->opt_taper = 0;
     c->opt_warps_b = 2;
+    c->opt_playout = 0;
     c->task_warps_b = 0;
     c->dirty = true;
     c->d_scenes = nullptr;
@@ -1206,6 +1207,14 @@ int fdtd_set_option(fdtd_ctx* c, int option, int64_t v) {
             c->opt_taper = (int)v;
             c->dirty = true;
             return FDTD_OK;
+        case FDTD_OPT_PLAYOUT:
+            if (v < 0 || v > 4096) return fail(c, FDTD_EINVAL, "persistent layout %lld outside 0..4096", (long long)v);
+            c->opt_playout = (int)v;
+            if (c->graph_exec) {   // a recorded step sequence holds the other launch
+                cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
+                c->graph_exec = nullptr;
+            }
+            return FDTD_OK;
         case FDTD_OPT_WARPS_B:
             if (v < 1 || v > 8) return fail(c, FDTD_EINVAL, "CPML warps %lld outside 1..8", (long long)v);
             c->opt_warps_b = (int)v;
@@ -1235,6 +1244,7 @@ int64_t fdtd_get_option(const fdtd_ctx* c, int option) {
         case FDTD_OPT_CHECK_EVERY: return c->opt_check_every;
         case FDTD_OPT_TAPER: return c->opt_taper;
         case FDTD_OPT_WARPS_B: return c->opt_warps_b;
+        case FDTD_OPT_PLAYOUT: return c->opt_playout;
     }
     return -1;
 }
@@ -1650,7 +1660,7 @@ int fdtd_autotune(fdtd_ctx* c, int trial_steps, double* best_ms) {
     if (trial_steps < 4) return fail(c, FDTD_EINVAL, "trial_steps must be >= 4");
     if (c->adj) return fail(c, FDTD_EINVAL, "disable checkpointing before autotuning");
     if (ctx_has_slab(c)) return fail(c, FDTD_EINVAL, "autotuning covers whole grids, not slab sub-domains");
-    struct Cand { int kernel, T, seg, warps, warps_b; };
+    struct Cand { int kernel, T, seg, warps, warps_b, playout; };
     std::vector<Cand> cand;
     // the segment height sets how many CTAs a block launches, so the sweep is
     // fine-grained: a list that fills whole waves of the 152 SMs wins; the CPML
@@ -1658,23 +1668,25 @@ int fdtd_autotune(fdtd_ctx* c, int trial_steps, double* best_ms) {
     for (int T = 2; T <= MAX_TB; T++)
         for (int seg = 16; seg <= 96; seg += 4)
             for (int w : {2, 4, 8})
-                for (int wb : {2, 4, 8}) cand.push_back({0, T, seg, w, wb});
+                for (int wb : {2, 4, 8}) cand.push_back({0, T, seg, w, wb, 0});
     if (!any_split(c))   // the persistent kernel has no split-field variant
         for (int T = 2; T <= MAX_TB; T++)
-            for (int seg : {32, 64, 96, 128}) cand.push_back({2, T, seg, 8, 2});
+            for (int seg : {32, 64, 96, 128})
+                for (int pl : {0, 16, 24, 32, 48}) cand.push_back({2, T, seg, 8, 2, pl});
     const int graph = c->opt_graph;
     c->opt_graph = 0;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "autotune");
     CK(cudaEventCreate(&e1), "autotune");
     double best = 1e30;
-    Cand win = {c->opt_kernel, c->opt_tblock, c->opt_segment, c->opt_warps, c->opt_warps_b};
+    Cand win = {c->opt_kernel, c->opt_tblock, c->opt_segment, c->opt_warps, c->opt_warps_b, c->opt_playout};
     const int taper0 = c->opt_taper;
     c->opt_taper = 0;   // the coarse pass and the boundary pass run uniform segments
     int rc = FDTD_OK;
     auto time_of = [&](const Cand& k, int steps, double* per) {
         c->opt_kernel = k.kernel; c->opt_tblock = k.T; c->opt_segment = k.seg; c->opt_warps = k.warps;
         c->opt_warps_b = k.warps_b;
+        c->opt_playout = k.playout;
         c->dirty = true;
         int r = fdtd_reset(c);
         if (!r) r = fdtd_step(c, k.T);   // warm-up (and build) outside the timing
@@ -1762,6 +1774,7 @@ int fdtd_autotune(fdtd_ctx* c, int trial_steps, double* best_ms) {
     cudaEventDestroy(e1);
     c->opt_kernel = win.kernel; c->opt_tblock = win.T; c->opt_segment = win.seg; c->opt_warps = win.warps;
     c->opt_warps_b = win.warps_b;
+    c->opt_playout = win.playout;
     c->opt_taper = win.kernel == 0 ? win_taper : taper0;
     c->opt_segment_b = win_b;
     c->opt_graph = graph;

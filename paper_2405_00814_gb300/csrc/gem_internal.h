@@ -196,6 +196,7 @@ struct fdtd_ctx {
     int opt_segment_b;           // FDTD_OPT_SEGMENT_B (0: max(8, opt_segment / 2))
     int opt_taper;               // FDTD_OPT_TAPER: percent of interior rows in half-height tail segments
     int opt_warps_b;             // FDTD_OPT_WARPS_B: warps per CTA of the forward CPML kernels
+    int opt_playout;             // FDTD_OPT_PLAYOUT: persistent CTAs (0: 12-warp; k: 16-warp, k general)
     // device copies for the fused kernel, rebuilt when dirty
     bool dirty;
     gem::TmzDev* d_scenes;

@@ -22,6 +22,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "gem_internal.h"
 
 namespace gem {
@@ -910,6 +912,43 @@ __global__ void __launch_bounds__((PW_INT + PW_GEN) * 32, 1) k_tmz_persistent(
     }
 }
 
+// Second layout (FDTD_OPT_PLAYOUT = k > 0): 16-warp CTAs of two kinds, so
+// that most SMs hold 16 interior warps as the per-block launches do.  The first
+// k CTAs run general and narrow items: warpgroups 0 and 1 take registers up to
+// 232 (setmaxnreg.inc), warpgroups 2 and 3 give theirs back down to 24 and
+// return, which balances the CTA's 512 x 128 launch registers exactly (and each
+// SM sub-partition's share: every warpgroup has one warp on each).  The other
+// CTAs run 16 interior warps at the launch's 128 registers.  Both kinds take
+// items from the same two ordered queues as the first layout.
+constexpr int PW2_WARPS = 16, PREG2_LAUNCH = 128, PREG2_GEN = 232, PREG2_IDLE = 24;
+static_assert(8 * PREG2_GEN + 8 * PREG2_IDLE == PW2_WARPS * PREG2_LAUNCH,
+              "the wide layout's register split must spend exactly the CTA's launch allocation");
+
+template <int T, bool WREC>
+__global__ void __launch_bounds__(PW2_WARPS * 32, 1) k_tmz_persistent_wide(
+    const TmzDev* __restrict__ scenes, const Task* __restrict__ ptasks, const int2* __restrict__ items,
+    const int* __restrict__ queue, int n_int, int n_gen, const int* __restrict__ dep_off,
+    const int* __restrict__ dep_idx, const Sample2* __restrict__ samps, int parity0, long long n0, int n_blocks,
+    unsigned* ctl, unsigned* done, long long spin_limit, int stall_item, int n_gcta) {
+    extern __shared__ float4 smem_f4[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    if ((int)blockIdx.x < n_gcta) {
+        if (wib >= 8) {
+            asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(PREG2_IDLE) : "memory");
+            return;
+        }
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(PREG2_GEN) : "memory");
+        float4* stage0 = smem_f4 + (size_t)wib * pstage_gen<T>();
+        persistent_loop<T, WREC, true>(scenes, ptasks, items, queue, n_int, n_gen, dep_off, dep_idx, samps, parity0,
+                                       n0, n_blocks, ctl, done, spin_limit, stall_item, stage0, lane);
+    } else {
+        float4* stage0 = smem_f4 + (size_t)wib * pstage_int<T>();
+        persistent_loop<T, WREC, false>(scenes, ptasks, items, queue, n_int, n_gen, dep_off, dep_idx, samps, parity0,
+                                        n0, n_blocks, ctl, done, spin_limit, stall_item, stage0, lane);
+    }
+}
+
 // dynamic shared memory of the persistent kernel: the interior warps' staging,
 // then the general warps'
 static size_t persistent_smem(int T) {
@@ -955,13 +994,63 @@ static cudaError_t launch_persistent_T(const fdtd_ctx* c, cudaStream_t st, int p
                               n0, n_blocks, c->d_ctl, c->d_done, spin_limit, c->opt_debug_skip);
 }
 
+// the wide layout: grid = one 16-warp CTA per SM, the first n_gcta of them for
+// general items (at least one CTA of each kind)
+template <int T, bool WREC>
+static cudaError_t launch_persistent_wide_T(const fdtd_ctx* c, cudaStream_t st, int parity, long long n0,
+                                            int n_blocks, long long spin_limit, int n_gcta, int* grid_out) {
+    const int threads = PW2_WARPS * 32;
+    const size_t smem = std::max((size_t)PW2_WARPS * pstage_int<T>(), (size_t)8 * pstage_gen<T>()) * sizeof(float4);
+    cudaError_t e = ensure_dyn_smem((const void*)k_tmz_persistent_wide<T, WREC>, smem);
+    if (e != cudaSuccess) return e;
+    // the register split is exact only for a kernel built at PREG2_LAUNCH
+    // registers; any other count could leave setmaxnreg.inc waiting forever
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, (const void*)k_tmz_persistent_wide<T, WREC>);
+    if (e != cudaSuccess) return e;
+    if (fa.numRegs != PREG2_LAUNCH) return cudaErrorInvalidConfiguration;
+    int per_sm = 0, dev = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tmz_persistent_wide<T, WREC>, threads, smem);
+    if (e != cudaSuccess) return e;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int grid = per_sm * sms;
+    const int ng = std::min(std::max(n_gcta, 1), grid - 1);
+    *grid_out = grid;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;   // every CTA resident: a waited-on item is always being worked
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_tmz_persistent_wide<T, WREC>, (const TmzDev*)c->d_scenes,
+                              (const Task*)c->d_ptasks, (const int2*)c->d_pitems, (const int*)c->d_pq, c->n_pint,
+                              c->n_pgen, (const int*)c->d_dep_off, (const int*)c->d_dep_idx,
+                              (const Sample2*)c->d_samp, parity, n0, n_blocks, c->d_ctl, c->d_done, spin_limit,
+                              c->opt_debug_skip, ng);
+}
+
 int tmz_persistent_launch(fdtd_ctx* c, int T, long long n0, int n_blocks, int parity) {
     cudaError_t e = cudaMemsetAsync(c->d_ctl, 0, 2 * sizeof(unsigned), c->stream);
     if (e == cudaSuccess && c->n_pitems > 0)
         e = cudaMemsetAsync(c->d_done, 0, (size_t)c->n_pitems * sizeof(unsigned), c->stream);
     int grid = 0;
     const bool wrec = adj_edge_mode(c);   // edge-weight reverse mode: keep the design window
-    if (e == cudaSuccess && c->n_pitems > 0) {
+    // the wide layout has builds for T = 2..4 without the window writes
+    const int ng = (T >= 2 && !wrec) ? c->opt_playout : 0;
+    const long long sl = c->spin_limit;
+    if (e == cudaSuccess && c->n_pitems > 0 && ng > 0) {
+        switch (T) {
+            case 2: e = launch_persistent_wide_T<2, false>(c, c->stream, parity, n0, n_blocks, sl, ng, &grid); break;
+            case 3: e = launch_persistent_wide_T<3, false>(c, c->stream, parity, n0, n_blocks, sl, ng, &grid); break;
+            default: e = launch_persistent_wide_T<4, false>(c, c->stream, parity, n0, n_blocks, sl, ng, &grid); break;
+        }
+    } else if (e == cudaSuccess && c->n_pitems > 0) {
         switch (T) {
             case 1: e = wrec ? launch_persistent_T<1, true>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid)
                              : launch_persistent_T<1, false>(c, c->stream, parity, n0, n_blocks, c->spin_limit, &grid);

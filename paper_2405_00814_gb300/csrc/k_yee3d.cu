@@ -1337,7 +1337,7 @@ int fdtd_create3(const fdtd_grid* g, double dx, double dt, double courant, const
     c->stream = (cudaStream_t)stream;
     c->s3 = nullptr;
     c->cur = 0; c->t = 0; c->parity = 0; c->launches = 0;
-    c->opt_kernel = 0; c->opt_tblock = 2; c->opt_segment = 0; c->opt_warps = 8; c->opt_segment_b = 0; c->opt_warps_b = 2;
+    c->opt_kernel = 0; c->opt_tblock = 2; c->opt_segment = 0; c->opt_warps = 8; c->opt_segment_b = 0; c->opt_warps_b = 2; c->opt_playout = 0;
     c->dirty = true;
     c->d_scenes = nullptr; c->d_tasks = nullptr; c->d_tasks_b = nullptr; c->n_tasks_b = 0; c->warps_b = 2; c->d_tasks_l = nullptr; c->n_tasks_l = 0; c->warps_l = 4; c->d_tasks_s = nullptr; c->n_tasks_s = 0; c->d_tasks_bd = nullptr; c->n_tasks_bd = 0;
     c->d_dft = nullptr; c->n_dft = 0; c->opt_adj_store = 1;

@@ -23,7 +23,7 @@ COMP = {"ex": 0, "ey": 1, "ez": 2, "hx": 3, "hy": 4, "hz": 5}
 SRC = {"ricker": 0, "gauss_mod": 1, "gauss": 2, "sampled": 3, "sine": 4}
 OPT = {"kernel": 0, "tblock": 1, "segment": 2, "warps": 3, "graph": 4, "spin_limit": 5, "debug_stall_item": 6,
        "adj_store": 7, "segment_b": 8, "check_every": 9, "taper": 10,
-       "warps_b": 11}
+       "warps_b": 11, "playout": 12}
 
 
 class FDTDError(RuntimeError):
@@ -438,7 +438,7 @@ class Simulation:
         self._check(self._L.fdtd_autotune(self._h, int(trial_steps), C.byref(best)))
         res = {"ms_per_step": best.value,
                "options": {k: self.get_option(k) for k in ("kernel", "tblock", "segment", "warps", "segment_b", "taper",
-                                                      "warps_b")}}
+                                                      "warps_b", "playout")}}
         if cache and key:
             data = json.load(open(cache)) if os.path.exists(cache) else {}
             data[ck] = res

@@ -36,12 +36,18 @@ def _fields(sim, scs):
     return out
 
 
-@pytest.mark.parametrize("tblock,segment", [(4, 24), (3, 16), (2, 48)])
-def test_persistent_kernel_batch_parity(tblock, segment):
+@pytest.mark.parametrize("tblock,segment,playout", [(4, 24, 0), (3, 16, 0), (2, 48, 0), (4, 24, 16), (3, 16, 3),
+                                                    (2, 48, 100), (4, 32, 1), (4, 32, 4096)])
+def test_persistent_kernel_batch_parity(tblock, segment, playout):
+    """playout 0: 12-warp CTAs of both item classes; k > 0: 16-warp CTAs, k of
+    them for general items (4096 leaves a single interior CTA, 1 a single
+    general one)."""
     scs, sim, pids = _batch(nsteps=402)
     sim.set_option("kernel", 2)
     sim.set_option("tblock", tblock)
     sim.set_option("segment", segment)
+    sim.set_option("playout", playout)
+    assert sim.get_option("playout") == playout
     sim.step(402)          # whole blocks in the persistent launch, the remainder in a fused launch
     sim.sync()
     got = _fields(sim, scs)
@@ -93,13 +99,15 @@ def test_autotune_keeps_results_exact(tmp_path):
     sim.close()
 
 
-def test_persistent_barrier_timeout_is_reported_and_recoverable():
+@pytest.mark.parametrize("playout", [0, 16])
+def test_persistent_barrier_timeout_is_reported_and_recoverable(playout):
     """One work item never reports its first block done: every item that waits
     for it gives up after its bounded wait, the kernel returns, fdtd_sync
     reports FDTD_ETIMEOUT, and the same context then runs correctly."""
     from paper_2405_00814_gb300 import fdtd
     scs, sim, _ = _batch(n=2, nsteps=64, lo=96, hi=160)
     sim.set_option("kernel", 2)
+    sim.set_option("playout", playout)
     sim.set_option("spin_limit", 20000)
     sim.set_option("debug_stall_item", 0)
     sim.step(64)
@@ -237,8 +245,9 @@ def cfg4_subset():
     return scs, refs
 
 
-@pytest.mark.parametrize("kernel,tblock,segment,warps", [(0, 4, 48, 4), (2, 4, 32, 8)])
-def test_batch_workload_scenes_at_full_length(cfg4_subset, kernel, tblock, segment, warps):
+@pytest.mark.parametrize("kernel,tblock,segment,warps,playout", [(0, 4, 48, 4, 0), (2, 4, 32, 8, 0),
+                                                                (2, 4, 64, 8, 24)])
+def test_batch_workload_scenes_at_full_length(cfg4_subset, kernel, tblock, segment, warps, playout):
     """The batch workload's scenes at its full 2000 steps, in one context as the
     benchmark runs them: the per-block kernels (the options the autotuner
     picks) and the single persistent launch, each replayed from a CUDA graph,
@@ -255,6 +264,7 @@ def test_batch_workload_scenes_at_full_length(cfg4_subset, kernel, tblock, segme
     sim.set_option("tblock", tblock)
     sim.set_option("segment", segment)
     sim.set_option("warps", warps)
+    sim.set_option("playout", playout)
     sim.set_option("graph", 1)
     n = scs[0].nsteps
     sim.step(n)                 # records the graph and runs it
