@@ -337,7 +337,7 @@ int fdtd_sync(fdtd_ctx* ctx);
  * of (kernel 0: T 2..4, segment 16..96 in steps of 4, warps 2, 4 or 8, CPML warps
  * (FDTD_OPT_WARPS_B) 2, 4 or 8; kernel 2,
  * not for a split-field PML: T 2..4, segment 32, 64, 96 or 128, FDTD_OPT_PLAYOUT
- * 0, 16, 24, 32 or 48) for trial_steps
+ * 0, 24, 48 or 64) for trial_steps
  * steps, time the four fastest twice more for 4 x trial_steps, keep the best,
  * then for kernel 0 try FDTD_OPT_SEGMENT_B
  * values against the automatic one, then FDTD_OPT_TAPER 10, 20, 30, 45 with the

@@ -1672,7 +1672,7 @@ int fdtd_autotune(fdtd_ctx* c, int trial_steps, double* best_ms) {
     if (!any_split(c))   // the persistent kernel has no split-field variant
         for (int T = 2; T <= MAX_TB; T++)
             for (int seg : {32, 64, 96, 128})
-                for (int pl : {0, 16, 24, 32, 48}) cand.push_back({2, T, seg, 8, 2, pl});
+                for (int pl : {0, 24, 48, 64}) cand.push_back({2, T, seg, 8, 2, pl});
     const int graph = c->opt_graph;
     c->opt_graph = 0;
     cudaEvent_t e0, e1;
