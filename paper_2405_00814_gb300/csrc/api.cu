@@ -898,6 +898,8 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     c->warps_l = warps_l;
     c->warps_b = warps_b;
     c->task_warps_b = warps_b;
+    c->coef_sq = 1;
+    for (const Scene2* s : c->s2) c->coef_sq = c->coef_sq && s->dx == s->dy;
     c->task_tb = T;
     c->task_seg = seg;
     c->dirty = false;

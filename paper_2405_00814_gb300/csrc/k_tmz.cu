@@ -23,6 +23,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "gem_internal.h"
 
@@ -96,6 +97,11 @@ __device__ __forceinline__ void add4(float4& v, int c, float a) {
 // Ez = Ca Ez + Cb/dx (dhy + psi_x) - Cb/dy (dhx + psi_y)
 __device__ __forceinline__ float e_upd(float e, float dhy, float dhx, const float4& co) {
     return co.x * e + co.y * dhy - co.z * dhx;
+}
+// square cells (dx = dy, so Cb/dx = Cb/dy): co = (Ca, Cb/dx), one product for
+// the curl
+__device__ __forceinline__ float e_upd(float e, float dhy, float dhx, const float2& co) {
+    return co.x * e + co.y * (dhy - dhx);
 }
 
 struct Prof {
@@ -655,9 +661,10 @@ __device__ __forceinline__ void ring_shift_in(Ring<T>& R, const float4* st, int 
     R.M[0] = reinterpret_cast<const uint32_t*>(st + 3 * 32)[lane];
 }
 
-// one level t (H then E) on ring slot t
-template <int T>
-__device__ __forceinline__ void level(Ring<T>& R, int t, float dbx, float dby, const float4* coef_s) {
+// one level t (H then E) on ring slot t; CT is the coefficient table's entry:
+// float4 (Ca, Cb/dx, Cb/dy, Cb) or, for square cells, float2 (Ca, Cb/dx)
+template <int T, typename CT>
+__device__ __forceinline__ void level(Ring<T>& R, int t, float dbx, float dby, const CT* coef_s) {
     const float4 e = R.E[t], eu = R.E[t - 1];
     const float er = __shfl_down_sync(0xffffffffu, e.x, 1);
     R.X[t].x -= dby * (eu.x - e.x);
@@ -671,8 +678,8 @@ __device__ __forceinline__ void level(Ring<T>& R, int t, float dbx, float dby, c
     const float4 y = R.Y[t];
     const float yl = __shfl_up_sync(0xffffffffu, y.w, 1);
     const uint32_t m = R.M[t];
-    const float4 c0 = coef_s[m & 255u], c1 = coef_s[(m >> 8) & 255u];
-    const float4 c2 = coef_s[(m >> 16) & 255u], c3 = coef_s[m >> 24];
+    const CT c0 = coef_s[m & 255u], c1 = coef_s[(m >> 8) & 255u];
+    const CT c2 = coef_s[(m >> 16) & 255u], c3 = coef_s[m >> 24];
     R.E[t].x = e_upd(e.x, y.x - yl, R.X[t].x - R.X[t + 1].x, c0);
     R.E[t].y = e_upd(e.y, y.y - y.x, R.X[t].y - R.X[t + 1].y, c1);
     R.E[t].z = e_upd(e.z, y.z - y.y, R.X[t].z - R.X[t + 1].z, c2);
@@ -681,10 +688,11 @@ __device__ __forceinline__ void level(Ring<T>& R, int t, float dbx, float dby, c
 
 // One warp's interior task: T levels of the wavefront over the strip's rows,
 // no boundary work.  coef_s is the scene's coefficient table (shared or global
-// memory), stage0 the warp's Q_I x stage_f4(false) float4 staging area.
-template <int T>
+// memory; float4 entries, or float2 (Ca, Cb/dx) for square cells), stage0 the
+// warp's Q_I x stage_f4(false) float4 staging area.
+template <int T, typename CT = float4>
 __device__ __forceinline__ void interior_task(const TmzDev* __restrict__ S, const Task& tk, int parity,
-                                              const float4* coef_s, float4* stage0, int lane) {
+                                              const CT* coef_s, float4* stage0, int lane) {
     constexpr int PF = pf_of(T, false);
     constexpr int SF4 = stage_f4(false);
     constexpr int Q = stages_for(T, false);
@@ -737,7 +745,7 @@ __device__ __forceinline__ void interior_task(const TmzDev* __restrict__ S, cons
         cp_wait<PF - 1>();
         ring_shift_in<T>(R, stage0 + ((r - s_row) & (Q - 1)) * SF4, lane);
 #pragma unroll
-        for (int t = 1; t <= T; t++) level<T>(R, t, dbx, dby, coef_s);
+        for (int t = 1; t <= T; t++) level<T, CT>(R, t, dbx, dby, coef_s);
         if (r >= r_steady) {
             const size_t g = (size_t)(r - T + PAD_Y) * pitch + cs;
             if (out_lane) {
@@ -753,26 +761,34 @@ __device__ __forceinline__ void interior_task(const TmzDev* __restrict__ S, cons
 }
 
 
-template <int T>
+// SQ: every scene has square cells, so the table is staged as (Ca, Cb/dx):
+// half the shared-memory bandwidth of the lookups, which (four gathers per
+// lane and level) share the pipe with the staging and the shuffles
+template <int T, bool SQ>
 __global__ void __launch_bounds__(256, 2) k_tmz_interior(const TmzDev* __restrict__ scenes,
                                                         const Task* __restrict__ tasks, int n_tasks,
                                                         int parity) {
     constexpr int SF4 = stage_f4(false);
     constexpr int Q = stages_for(T, false);
+    using CT = typename std::conditional<SQ, float2, float4>::type;
     extern __shared__ float4 smem_f4[];
-    __shared__ float4 coef_s[256];
+    __shared__ CT coef_s[256];
 
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int warps = blockDim.x >> 5;
     const int tid = blockIdx.x * warps + wib;
     const TmzDev* S = scenes + tasks[blockIdx.x * warps].scene;
-    for (int k = threadIdx.x; k < 256; k += blockDim.x) coef_s[k] = S->coef[k];
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) {
+        const float4 c = S->coef[k];
+        if constexpr (SQ) coef_s[k] = make_float2(c.x, c.y);
+        else coef_s[k] = c;
+    }
     __syncthreads();
     if (tid >= n_tasks) return;
     const Task tk = tasks[tid];
     if (tk.scene < 0) return;
-    interior_task<T>(S, tk, parity, coef_s, smem_f4 + (size_t)wib * Q * SF4, lane);
+    interior_task<T, CT>(S, tk, parity, coef_s, smem_f4 + (size_t)wib * Q * SF4, lane);
 }
 
 // ===========================================================================
@@ -1279,10 +1295,14 @@ static cudaError_t launch_fused_T(const Task* tasks, int n_tasks, int warps, con
         e = ensure_dyn_smem((const void*)k_tmz_fused<T, false>, smem);
         if (e != cudaSuccess) return e;
         k_tmz_fused<T, false><<<blocks, warps * 32, smem, st>>>(c->d_scenes, tasks, n_tasks, c->d_samp, parity, n0);
-    } else {
-        e = ensure_dyn_smem((const void*)k_tmz_interior<T>, smem);
+    } else if (c->coef_sq) {
+        e = ensure_dyn_smem((const void*)k_tmz_interior<T, true>, smem);
         if (e != cudaSuccess) return e;
-        k_tmz_interior<T><<<blocks, warps * 32, smem, st>>>(c->d_scenes, tasks, n_tasks, parity);
+        k_tmz_interior<T, true><<<blocks, warps * 32, smem, st>>>(c->d_scenes, tasks, n_tasks, parity);
+    } else {
+        e = ensure_dyn_smem((const void*)k_tmz_interior<T, false>, smem);
+        if (e != cudaSuccess) return e;
+        k_tmz_interior<T, false><<<blocks, warps * 32, smem, st>>>(c->d_scenes, tasks, n_tasks, parity);
     }
     return cudaGetLastError();
 }

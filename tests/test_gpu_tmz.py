@@ -95,6 +95,20 @@ def test_tapered_batch_of_uneven_scenes():
     sim.close()
 
 
+def test_rectangular_cells():
+    """dx != dy: the interior kernel keeps the full (Ca, Cb/dx, Cb/dy) table
+    (square cells stage (Ca, Cb/dx) only); both against the oracle."""
+    sc = scenes.ellipse_scene(side=320, nsteps=500)
+    sq = gpu_run(sc, sc.nsteps, tblock=4, segment=32, warps=4)
+    assert_fields_close(sq, oracle_run(sc, sc.nsteps))
+    sc.dy = 1.25 * sc.dx
+    sc.dt = 0.99 / (299792458.0 * np.sqrt(1.0 / sc.dx ** 2 + 1.0 / sc.dy ** 2))
+    o = oracle_run(sc, sc.nsteps, probes=sc.probes)
+    g = gpu_run(sc, sc.nsteps, tblock=4, segment=32, warps=4)
+    assert_fields_close(g, o)
+    assert rel_l2(g["probes"], o["probes"]) <= TOL_FIELD
+
+
 def test_unfused_and_fused_agree_to_rounding():
     sc = scenes.ellipse_scene(side=200, nsteps=500)
     a = gpu_run(sc, sc.nsteps, kernel=1)
