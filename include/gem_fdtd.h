@@ -334,16 +334,16 @@ int fdtd_sync(fdtd_ctx* ctx);
 
 /* Pick the 2D kernel options for the current scenes (one large scene, or a
  * batch: Sec. V-A runs many simulations of varying size): time every candidate
- * of (kernel 0: T 2..4, segment 16..96 in steps of 4, warps 2, 4 or 8, CPML warps
- * (FDTD_OPT_WARPS_B) 2, 4 or 8; kernel 2,
- * not for a split-field PML: T 2..4, segment 32, 64, 96 or 128, FDTD_OPT_PLAYOUT
- * 0, 24, 48 or 64) for trial_steps
- * steps, time the four fastest twice more for 4 x trial_steps, keep the best,
- * then for kernel 0 try FDTD_OPT_SEGMENT_B
- * values against the automatic one, then FDTD_OPT_TAPER 10, 20, 30, 45 with the
- * segment height raised by 0, 8, 16 or 24 rows (each kept only if 1 % faster).
- * Leaves the context reset (t = 0, zero fields).
- * *best_ms gets the best time per step. */
+ * of (kernel 0: T 2..4, segment 16..96 in steps of 4, warps 2, 4 or 8, CPML
+ * warps (FDTD_OPT_WARPS_B) 2, 4 or 8; kernel 2, not for a split-field PML:
+ * T 2..4, segment 32, 64, 96 or 128, FDTD_OPT_PLAYOUT 0, 24, 48 or 64) for
+ * trial_steps steps, time the four fastest twice more for 4 x trial_steps, keep
+ * the best; then, for kernel 0, search the segment height (-8..+8 rows around
+ * the candidate's, in steps of 4) and FDTD_OPT_SEGMENT_B (automatic, 12..32 in
+ * steps of 4) jointly around the two best (T, warps, CPML warps) settings of
+ * the first pass, then FDTD_OPT_TAPER 10, 20, 30, 45 with the segment height
+ * raised by 0, 8, 16 or 24 rows (each kept only if 1 % faster).  Leaves the
+ * context reset (t = 0, zero fields).  *best_ms gets the best time per step. */
 int fdtd_autotune(fdtd_ctx* ctx, int trial_steps, double* best_ms);
 
 /* Returns FDTD_EUNSTABLE if any field of any scene is not finite. Synchronises. */

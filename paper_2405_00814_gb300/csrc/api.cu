@@ -1721,8 +1721,13 @@ int fdtd_autotune(fdtd_ctx* c, int trial_steps, double* best_ms) {
             win = k;
         }
     }
-    // then the boundary tasks' height for the winner (the automatic choice is
-    // the incumbent): their warps set the critical path beside the interior ones
+    // then a joint local search over the segment height and the boundary
+    // tasks' height (the automatic choice included) around the two best
+    // (T, warps, CPML warps) settings of the coarse pass: a block ends at the
+    // later of the CPML chains and the interior's last wave, the two heights
+    // move both (how many CTAs each launch has, how long a CPML chain is), and
+    // the landscape has cliffs a coarse pass with the automatic boundary
+    // height does not see
     int win_b = c->opt_segment_b;
     if (rc == FDTD_OK && win.kernel == 0) {
         const int saved_b = c->opt_segment_b;
@@ -1732,16 +1737,39 @@ int fdtd_autotune(fdtd_ctx* c, int trial_steps, double* best_ms) {
         if (rc == FDTD_OK) rc = time_of(win, 4 * trial_steps, &base2);
         base = std::min(base, base2);
         win_b = 0;
-        for (int b : {4, 8, 12, 16, 20, 24, 32, 40, win.seg}) {
-            if (rc != FDTD_OK) break;
-            c->opt_segment_b = b;
+        std::vector<Cand> seeds;
+        for (size_t q = 0; q < coarse.size() && seeds.size() < 2; q++) {
+            const Cand& k = cand[coarse[q].second];
+            if (k.kernel != 0) continue;
+            bool seen = false;
+            for (const Cand& o : seeds) seen = seen || (o.T == k.T && o.warps == k.warps && o.warps_b == k.warps_b);
+            if (!seen) seeds.push_back(k);
+        }
+        struct Trial { double ms; Cand k; int b; };
+        std::vector<Trial> trials;
+        for (const Cand& sd : seeds)
+            for (int ds : {-8, -4, 0, 4, 8})
+                for (int b : {0, 12, 16, 20, 24, 28, 32}) {
+                    if (rc != FDTD_OK) break;
+                    Cand k = sd;
+                    k.seg = sd.seg + ds;
+                    if (k.seg < 8) continue;
+                    c->opt_segment_b = b;
+                    double per = 0;
+                    rc = time_of(k, 4 * trial_steps, &per);
+                    if (rc == FDTD_OK) trials.push_back({per, k, b});
+                }
+        std::sort(trials.begin(), trials.end(), [](const Trial& a, const Trial& b) { return a.ms < b.ms; });
+        for (size_t q = 0; q < trials.size() && q < 3 && rc == FDTD_OK; q++) {
+            c->opt_segment_b = trials[q].b;
             double per = 0, per2 = 0;
-            rc = time_of(win, 4 * trial_steps, &per);
-            if (rc == FDTD_OK) rc = time_of(win, 4 * trial_steps, &per2);
+            rc = time_of(trials[q].k, 4 * trial_steps, &per);
+            if (rc == FDTD_OK) rc = time_of(trials[q].k, 4 * trial_steps, &per2);
             per = std::min(per, per2);
             if (rc == FDTD_OK && per < 0.99 * base) {   // a clear gain over the incumbent
                 base = per;
-                win_b = b;
+                win = trials[q].k;
+                win_b = trials[q].b;
             }
         }
         if (rc != FDTD_OK) win_b = saved_b;
