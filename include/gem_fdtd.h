@@ -339,7 +339,7 @@ int fdtd_sync(fdtd_ctx* ctx);
  * T 2..4, segment 32, 64, 96 or 128, FDTD_OPT_PLAYOUT 0, 24, 48 or 64) for
  * trial_steps steps, time the four fastest twice more for 4 x trial_steps, keep
  * the best; then, for kernel 0, search the segment height (-8..+8 rows around
- * the candidate's, in steps of 4) and FDTD_OPT_SEGMENT_B (automatic, 12..32 in
+ * the candidate's, in steps of 4) and FDTD_OPT_SEGMENT_B (automatic, 4..32 in
  * steps of 4) jointly around the two best (T, warps, CPML warps) settings of
  * the first pass, then FDTD_OPT_TAPER 10, 20, 30, 45 with the segment height
  * raised by 0, 8, 16 or 24 rows (each kept only if 1 % faster).  Leaves the

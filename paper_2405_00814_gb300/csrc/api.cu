@@ -1749,7 +1749,7 @@ int fdtd_autotune(fdtd_ctx* c, int trial_steps, double* best_ms) {
         std::vector<Trial> trials;
         for (const Cand& sd : seeds)
             for (int ds : {-8, -4, 0, 4, 8})
-                for (int b : {0, 12, 16, 20, 24, 28, 32}) {
+                for (int b : {0, 4, 8, 12, 16, 20, 24, 28, 32}) {
                     if (rc != FDTD_OK) break;
                     Cand k = sd;
                     k.seg = sd.seg + ds;
