@@ -132,6 +132,12 @@ extern "C" {
                                 general warps at 248; k >= 1 = one 16-warp CTA per SM, the first k (at most all
                                 but one) running general and narrow items on 8 warps at 232 registers, every
                                 other CTA 16 interior warps at 128.  Results do not depend on it */
+#define FDTD_OPT_BULK 13     /* 2D, kernel 0: 1 = the interior kernel brings each row in with cp.async.bulk
+                                copies (the TMA engine; one lane per row: Ez, Hx, Hy and the material window,
+                                completing on a per-stage mbarrier) instead of 16-byte cp.async per lane; used
+                                where every interior task's field rows start on 16 bytes.  Each mbarrier wait is
+                                bounded by FDTD_OPT_SPIN_LIMIT polls, after which fdtd_sync reports
+                                FDTD_ETIMEOUT.  0 (default) = cp.async.  Results do not depend on it */
 
 typedef struct fdtd_ctx fdtd_ctx;
 

@@ -359,6 +359,9 @@ fdtd_ctx* ctx_new(void* stream) {
     c->opt_taper = 0;
     c->opt_warps_b = 2;
     c->opt_playout = 0;
+    c->opt_bulk = 0;
+    c->use_bulk = 0;
+    c->d_bulk_err = nullptr;
     c->task_warps_b = 0;
     c->dirty = true;
     c->d_scenes = nullptr;
@@ -900,6 +903,15 @@ int rebuild(fdtd_ctx* c, int T, int seg, int warps) {
     c->task_warps_b = warps_b;
     c->coef_sq = 1;
     for (const Scene2* s : c->s2) c->coef_sq = c->coef_sq && s->dx == s->dy;
+    // bulk row copies: each interior task's field rows start on 16 bytes and its
+    // 144-byte material window (from the 16-byte boundary at or below its first
+    // column) stays inside the row
+    c->use_bulk = c->opt_bulk && c->d_bulk_err != nullptr;
+    for (const Task& t : tasks) {
+        if (t.scene < 0) continue;
+        const int cs0 = t.x0 - HALO + PAD_X;
+        if ((cs0 * 4) % 16 != 0 || (cs0 & ~15) + STRIP + 16 > c->s2[t.scene]->pitch) c->use_bulk = 0;
+    }
     c->task_tb = T;
     c->task_seg = seg;
     c->dirty = false;
@@ -1131,6 +1143,7 @@ void fdtd_destroy(fdtd_ctx* c) {
     dfree(c->d_ctl);
     if (c->h_err) cudaFreeHost(c->h_err);
     dfree(c->d_bad);
+    dfree(c->d_bulk_err);
     if (c->h_bad) cudaFreeHost(c->h_bad);
     if (c->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -1209,6 +1222,17 @@ int fdtd_set_option(fdtd_ctx* c, int option, int64_t v) {
             c->opt_taper = (int)v;
             c->dirty = true;
             return FDTD_OK;
+        case FDTD_OPT_BULK:
+            if (v < 0 || v > 1) return fail(c, FDTD_EINVAL, "bulk option must be 0 or 1");
+            if (c->dims != 2) return fail(c, FDTD_EINVAL, "bulk row copies are a 2D option");
+            if (v == 1 && !c->d_bulk_err) {
+                int rc = dalloc(c, &c->d_bulk_err, sizeof(int), "bulk-copy error word");
+                if (rc) return rc;
+                CK(cudaMemsetAsync(c->d_bulk_err, 0, sizeof(int), c->stream), "bulk-copy error word");
+            }
+            c->opt_bulk = (int)v;
+            c->dirty = true;
+            return FDTD_OK;
         case FDTD_OPT_PLAYOUT:
             if (v < 0 || v > 4096) return fail(c, FDTD_EINVAL, "persistent layout %lld outside 0..4096", (long long)v);
             c->opt_playout = (int)v;
@@ -1247,6 +1271,7 @@ int64_t fdtd_get_option(const fdtd_ctx* c, int option) {
         case FDTD_OPT_TAPER: return c->opt_taper;
         case FDTD_OPT_WARPS_B: return c->opt_warps_b;
         case FDTD_OPT_PLAYOUT: return c->opt_playout;
+        case FDTD_OPT_BULK: return c->opt_bulk;
     }
     return -1;
 }
@@ -1644,6 +1669,15 @@ int fdtd_sync(fdtd_ctx* c) {
         if (c->d_bad) CK(cudaMemset(c->d_bad, 0, sizeof(int)), "clear the finite-check flag");
         return fail(c, FDTD_ETIMEOUT, "a wait of the persistent kernel for another work item gave up (spin limit %lld)",
                     (long long)c->spin_limit);
+    }
+    if (c->d_bulk_err) {
+        int v = 0;
+        CK(cudaMemcpy(&v, c->d_bulk_err, sizeof(int), cudaMemcpyDeviceToHost), "read the bulk-copy error word");
+        if (v) {
+            CK(cudaMemset(c->d_bulk_err, 0, sizeof(int)), "clear the bulk-copy error word");
+            return fail(c, FDTD_ETIMEOUT, "a wait of the interior kernel for its bulk row copies gave up "
+                                          "(spin limit %lld)", (long long)c->spin_limit);
+        }
     }
     if (c->h_bad && *c->h_bad) {
         if (c->d_bad) CK(cudaMemset(c->d_bad, 0, sizeof(int)), "clear the finite-check flag");

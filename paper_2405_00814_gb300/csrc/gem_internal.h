@@ -212,6 +212,9 @@ struct fdtd_ctx {
     int task_narrow;               // the lists were built with narrow x-slab tasks (kernels 0, 2)
     int task_warps_b;              // the CPML lists are padded to CTAs of this many warps
     int coef_sq;                   // every scene has dx == dy: the interior kernel stages (Ca, Cb/dx)
+    int opt_bulk;                  // FDTD_OPT_BULK: interior rows by cp.async.bulk
+    int use_bulk;                  // opt_bulk and every interior task's rows suit the bulk copies
+    int* d_bulk_err;               // sticky device word: a bulk-copy wait gave up
     int task_pers;                 // the persistent kernel's items were built (kernel 2)
     gem::Task* d_tasks_l;          // lite tasks: design, source, probes or ragged edge, no CPML
     int n_tasks_l, warps_l;

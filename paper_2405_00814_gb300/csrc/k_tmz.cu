@@ -791,6 +791,183 @@ __global__ void __launch_bounds__(256, 2) k_tmz_interior(const TmzDev* __restric
     interior_task<T, CT>(S, tk, parity, coef_s, smem_f4 + (size_t)wib * Q * SF4, lane);
 }
 
+// ---------------------------------------------------------------------------
+// The same interior task with its rows brought in by the TMA engine
+// (FDTD_OPT_BULK): per row one lane issues four cp.async.bulk copies -- the
+// strip's 512 bytes of Ez, Hx and Hy and 144 bytes of material map around its
+// 128 (the bulk copy wants a 16-byte aligned start) -- into a stage whose
+// mbarrier counts the 1680 bytes, instead of four 16-byte cp.async per lane.
+// The host uses it only where every interior task's field rows start on 16
+// bytes and the material window stays inside the row.  Every mbarrier wait is
+// bounded: past spin_limit polls the warp sets *err, waits for its copies in
+// flight (bounded again, by at least 2^22 polls, so that no copy lands in
+// shared memory the CTA has left) and returns; fdtd_sync reports
+// FDTD_ETIMEOUT.
+// ---------------------------------------------------------------------------
+constexpr int BULK_FIELD_BYTES = STRIP * 4;                  // 512
+constexpr int BULK_MAT_BYTES = STRIP + 16;                   // 144: 128 bytes from any start
+constexpr int BULK_STAGE_BYTES = 3 * BULK_FIELD_BYTES + BULK_MAT_BYTES;   // 1680
+constexpr int BULK_STAGE_F4 = BULK_STAGE_BYTES / 16;         // 105
+static_assert(BULK_STAGE_BYTES % 16 == 0, "a bulk stage must keep every copy 16-byte aligned");
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+// true once the phase of the given parity has completed
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+// bounded wait; false when it gave up
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
+    for (long long k = 0; k < limit; k++)
+        if (mbar_try(bar, parity)) return true;
+    return false;
+}
+
+template <int T, typename CT>
+__device__ __forceinline__ void interior_task_bulk(const TmzDev* __restrict__ S, const Task& tk, int parity,
+                                                   const CT* coef_s, float4* stage0, uint64_t* bars, int lane,
+                                                   long long spin_limit, int* err) {
+    constexpr int PF = pf_of(T, false);
+    constexpr int Q = stages_for(T, false);
+    static_assert((Q & (Q - 1)) == 0, "interior stage count must be a power of two");
+    const int pitch = S->pitch;
+    const float* __restrict__ ez_in = S->f[F_EZ][parity];
+    const float* __restrict__ hx_in = S->f[F_HX][parity];
+    const float* __restrict__ hy_in = S->f[F_HY][parity];
+    float* __restrict__ ez_out = S->f[F_EZ][parity ^ 1];
+    float* __restrict__ hx_out = S->f[F_HX][parity ^ 1];
+    float* __restrict__ hy_out = S->f[F_HY][parity ^ 1];
+    const uint8_t* __restrict__ mat = S->mat;
+    const float dbx = S->dbx, dby = S->dby;
+
+    const int cs0 = tk.x0 - HALO + PAD_X;          // first loaded column (16-byte aligned field rows)
+    const int m0 = cs0 & ~15, moff = cs0 - m0;     // material window start and the strip's offset in it
+    const int cs = cs0 + 4 * lane;
+    const bool out_lane = (lane >= HALO / 4) && (lane < 32 - HALO / 4) && (tk.xe == 0 || cs - PAD_X < tk.xe);
+    const int s_row = tk.ya - T;
+    const int r_last = tk.yb + T - 1;
+    const uint32_t bar0 = smem_u32(bars);
+    if (lane == 0)
+        for (int k = 0; k < Q; k++) mbar_init(bar0 + 8 * k);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    __syncwarp();
+    // rows past r_last are still inside the pad rows: the prefetch never needs a guard
+    auto issue = [&](int row) {
+        __syncwarp();   // every lane has read the stage's previous row
+        if (lane == 0) {
+            const int k = (row - s_row) & (Q - 1);
+            const uint32_t st = smem_u32(stage0 + (size_t)k * BULK_STAGE_F4), bar = bar0 + 8 * k;
+            const size_t g = (size_t)(row + PAD_Y) * pitch;
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            mbar_expect(bar, BULK_STAGE_BYTES);
+            bulk_g2s(st, ez_in + g + cs0, BULK_FIELD_BYTES, bar);
+            bulk_g2s(st + BULK_FIELD_BYTES, hx_in + g + cs0, BULK_FIELD_BYTES, bar);
+            bulk_g2s(st + 2 * BULK_FIELD_BYTES, hy_in + g + cs0, BULK_FIELD_BYTES, bar);
+            bulk_g2s(st + 3 * BULK_FIELD_BYTES, mat + g + m0, BULK_MAT_BYTES, bar);
+        }
+    };
+
+    Ring<T> R;
+#pragma unroll
+    for (int k = 0; k < T + 1; k++) {
+        R.E[k] = make_float4(0, 0, 0, 0);
+        R.Y[k] = R.E[k];
+        R.M[k] = 0;
+    }
+#pragma unroll
+    for (int k = 0; k < T + 2; k++) R.X[k] = make_float4(0, 0, 0, 0);
+    for (int k = 0; k < PF; k++) issue(s_row + k);
+    const int r_steady = tk.ya + T;
+    bool ok = true;
+    int r = s_row;
+    for (; r <= r_last; ++r) {
+        const int u = r - s_row, k = u & (Q - 1);
+        if (!mbar_wait(bar0 + 8 * k, (uint32_t)(u / Q) & 1u, spin_limit)) {
+            ok = false;
+            break;
+        }
+        const float4* st = stage0 + (size_t)k * BULK_STAGE_F4;
+        // shift the ring: the staged row enters at slot 0 (field rows at 0, 32,
+        // 64 float4; the material row 4 bytes per lane from its offset)
+#pragma unroll
+        for (int q = T + 1; q >= 1; q--) R.X[q] = R.X[q - 1];
+#pragma unroll
+        for (int q = T; q >= 1; q--) {
+            R.E[q] = R.E[q - 1];
+            R.Y[q] = R.Y[q - 1];
+            R.M[q] = R.M[q - 1];
+        }
+        R.E[0] = st[0 * 32 + lane];
+        R.X[0] = st[1 * 32 + lane];
+        R.Y[0] = st[2 * 32 + lane];
+        R.M[0] = *reinterpret_cast<const uint32_t*>(reinterpret_cast<const uint8_t*>(st + 3 * 32) + moff + 4 * lane);
+#pragma unroll
+        for (int t = 1; t <= T; t++) level<T, CT>(R, t, dbx, dby, coef_s);
+        if (r >= r_steady) {
+            const size_t g = (size_t)(r - T + PAD_Y) * pitch + cs;
+            if (out_lane) {
+                *reinterpret_cast<float4*>(ez_out + g) = R.E[T];
+                *reinterpret_cast<float4*>(hx_out + g) = R.X[T];
+                *reinterpret_cast<float4*>(hy_out + g) = R.Y[T];
+            }
+        }
+        issue(r + PF);
+    }
+    // drain: every copy issued and not yet consumed lands before the warp leaves
+    // (rows r .. r - 1 + PF: the last row issued, whether the loop finished or
+    // gave up at row r; bounded waits)
+    const long long drain_limit = spin_limit > (1ll << 22) ? spin_limit : (1ll << 22);
+    for (int q = r; q <= r - 1 + PF; q++) {
+        const int u = q - s_row;
+        if (!mbar_wait(bar0 + 8 * (u & (Q - 1)), (uint32_t)(u / Q) & 1u, drain_limit)) ok = false;
+    }
+    if (!ok && lane == 0) atomicExch(err, 1);
+}
+
+// interior kernel with bulk row copies; the dynamic shared memory holds each
+// warp's Q_I stages of BULK_STAGE_BYTES, then each warp's Q_I mbarriers
+template <int T, bool SQ>
+__global__ void __launch_bounds__(256, 2) k_tmz_interior_bulk(const TmzDev* __restrict__ scenes,
+                                                             const Task* __restrict__ tasks, int n_tasks,
+                                                             int parity, long long spin_limit, int* err) {
+    constexpr int Q = stages_for(T, false);
+    using CT = typename std::conditional<SQ, float2, float4>::type;
+    extern __shared__ float4 smem_f4[];
+    __shared__ CT coef_s[256];
+
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int warps = blockDim.x >> 5;
+    const int tid = blockIdx.x * warps + wib;
+    const TmzDev* S = scenes + tasks[blockIdx.x * warps].scene;
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) {
+        const float4 c = S->coef[k];
+        if constexpr (SQ) coef_s[k] = make_float2(c.x, c.y);
+        else coef_s[k] = c;
+    }
+    __syncthreads();
+    if (tid >= n_tasks) return;
+    const Task tk = tasks[tid];
+    if (tk.scene < 0) return;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_f4 + (size_t)warps * Q * BULK_STAGE_F4) + (size_t)wib * Q;
+    interior_task_bulk<T, CT>(S, tk, parity, coef_s, smem_f4 + (size_t)wib * Q * BULK_STAGE_F4, bars, lane,
+                              spin_limit, err);
+}
+
 // ===========================================================================
 // persistent kernel: one cooperative launch advances every scene of a batch
 // by n_blocks * T steps.  The work is a list of items per T-step block -- an
@@ -1295,6 +1472,19 @@ static cudaError_t launch_fused_T(const Task* tasks, int n_tasks, int warps, con
         e = ensure_dyn_smem((const void*)k_tmz_fused<T, false>, smem);
         if (e != cudaSuccess) return e;
         k_tmz_fused<T, false><<<blocks, warps * 32, smem, st>>>(c->d_scenes, tasks, n_tasks, c->d_samp, parity, n0);
+    } else if (c->use_bulk) {
+        const size_t sm = (size_t)warps * stages_for(T, false) * (BULK_STAGE_BYTES + 8);
+        if (c->coef_sq) {
+            e = ensure_dyn_smem((const void*)k_tmz_interior_bulk<T, true>, sm);
+            if (e != cudaSuccess) return e;
+            k_tmz_interior_bulk<T, true><<<blocks, warps * 32, sm, st>>>(c->d_scenes, tasks, n_tasks, parity,
+                                                                           c->spin_limit, c->d_bulk_err);
+        } else {
+            e = ensure_dyn_smem((const void*)k_tmz_interior_bulk<T, false>, sm);
+            if (e != cudaSuccess) return e;
+            k_tmz_interior_bulk<T, false><<<blocks, warps * 32, sm, st>>>(c->d_scenes, tasks, n_tasks, parity,
+                                                                            c->spin_limit, c->d_bulk_err);
+        }
     } else if (c->coef_sq) {
         e = ensure_dyn_smem((const void*)k_tmz_interior<T, true>, smem);
         if (e != cudaSuccess) return e;

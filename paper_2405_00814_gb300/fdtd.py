@@ -23,7 +23,7 @@ COMP = {"ex": 0, "ey": 1, "ez": 2, "hx": 3, "hy": 4, "hz": 5}
 SRC = {"ricker": 0, "gauss_mod": 1, "gauss": 2, "sampled": 3, "sine": 4}
 OPT = {"kernel": 0, "tblock": 1, "segment": 2, "warps": 3, "graph": 4, "spin_limit": 5, "debug_stall_item": 6,
        "adj_store": 7, "segment_b": 8, "check_every": 9, "taper": 10,
-       "warps_b": 11, "playout": 12}
+       "warps_b": 11, "playout": 12, "bulk": 13}
 
 
 class FDTDError(RuntimeError):

@@ -95,6 +95,47 @@ def test_tapered_batch_of_uneven_scenes():
     sim.close()
 
 
+@pytest.mark.parametrize("tblock,segment,warps,side", [(4, 68, 8, 512), (3, 24, 4, 384), (2, 16, 2, 250),
+                                                        (1, 40, 3, 200)])
+def test_bulk_row_copies(tblock, segment, warps, side):
+    """FDTD_OPT_BULK: the interior kernel's rows by cp.async.bulk into
+    mbarrier-tracked stages.  Same arithmetic on the same values, so the fields
+    and probes equal the cp.async run bit for bit; the oracle within TOL."""
+    sc = scenes.ellipse_scene(side=side, nsteps=400)
+    o = oracle_run(sc, sc.nsteps, probes=sc.probes)
+    a = gpu_run(sc, sc.nsteps, tblock=tblock, segment=segment, warps=warps)
+    b = gpu_run(sc, sc.nsteps, tblock=tblock, segment=segment, warps=warps, options={"bulk": 1, "warps_b": 8})
+    c = gpu_run(sc, sc.nsteps, tblock=tblock, segment=segment, warps=warps, options={"warps_b": 8})
+    for f in ("ez", "hx", "hy"):
+        assert np.array_equal(b[f], c[f]), f
+    assert np.array_equal(b["probes"], c["probes"])
+    assert_fields_close(b, o)
+    assert rel_l2(b["probes"], o["probes"]) <= TOL_FIELD
+    for f in ("ez", "hx", "hy"):
+        assert rel_l2(b[f], a[f]) < 1e-5, f
+
+
+def test_bulk_row_copies_rectangular_cells_and_graph():
+    """Bulk row copies with the float4 table (dx != dy), replayed from a CUDA
+    graph after a reset."""
+    from paper_2405_00814_gb300 import fdtd
+    sc = scenes.ellipse_scene(side=300, nsteps=360)
+    sc.dy = 1.25 * sc.dx
+    sc.dt = 0.99 / (299792458.0 * np.sqrt(1.0 / sc.dx ** 2 + 1.0 / sc.dy ** 2))
+    o = oracle_run(sc, sc.nsteps)
+    sim = fdtd.from_scene(sc, probes=False, monitors=False)
+    for k, v in {"kernel": 0, "tblock": 4, "segment": 32, "warps": 4, "bulk": 1, "graph": 1}.items():
+        sim.set_option(k, v)
+    assert sim.get_option("bulk") == 1
+    sim.step(sc.nsteps)
+    sim.reset()
+    sim.step(sc.nsteps)
+    sim.sync()
+    g = {f: sim.get_field(f, (sc.ny, sc.nx)) for f in ("ez", "hx", "hy")}
+    sim.close()
+    assert_fields_close(g, o)
+
+
 def test_rectangular_cells():
     """dx != dy: the interior kernel keeps the full (Ca, Cb/dx, Cb/dy) table
     (square cells stage (Ca, Cb/dx) only); both against the oracle."""
@@ -243,6 +284,8 @@ def test_invalid_inputs_rejected():
     for bad_wb in (0, 9):
         with pytest.raises(fdtd.FDTDError):
             sim.set_option("warps_b", bad_wb)
+    with pytest.raises(fdtd.FDTDError):
+        sim.set_option("bulk", 2)
     sim.step(3)
     with pytest.raises(fdtd.FDTDError):
         sim.add_probe(3, 3)                                   # after stepping
