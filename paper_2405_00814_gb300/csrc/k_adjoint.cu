@@ -34,6 +34,7 @@
 
 #include <algorithm>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "gem_internal.h"
@@ -86,11 +87,12 @@ __device__ __forceinline__ float cget(const float4& v, int c) { return c == 0 ? 
 // per lane group, as in the forward general task: width-G shuffles, every group
 // streams as many rows as the warp's longest task and stores nothing past its
 // own, adjoint sources read from memory).  coef_s: the scene's coefficient
-// table; stage0: the warp's staging area.
-template <int T, bool GEN, bool PMLV, bool DSGV = true, int G = 32>
+// table, float4 (Ca, Cb/dx, Cb/dy, Cb) or, for square cells, float2
+// (Ca, Cb/dx) (Cb/dy is then the same float); stage0: the warp's staging area.
+template <int T, bool GEN, bool PMLV, bool DSGV = true, int G = 32, typename CT = float4>
 __device__ __forceinline__ void adj_task(const TmzDev* __restrict__ S, const Task& tk,
                                          const Sample2* __restrict__ srcs, int parity, long long n_top,
-                                         const float4* coef_s, float4* stage0, int lane) {
+                                         const CT* coef_s, float4* stage0, int lane) {
     static_assert(G == 32 || (GEN && PMLV && G >= 4 && G < 32 && (G & (G - 1)) == 0), "narrow groups are CPML tasks");
     constexpr bool PV = GEN && PMLV;
     constexpr bool SD = GEN && !PMLV;   // design band staged
@@ -192,10 +194,19 @@ __device__ __forceinline__ void adj_task(const TmzDev* __restrict__ S, const Tas
     };
     // coefficients of row `row` (material table, or the design override)
     auto coefs = [&](uint32_t m, int row, float4* c) {
-        c[0] = coef_s[m & 255u];
-        c[1] = coef_s[(m >> 8) & 255u];
-        c[2] = coef_s[(m >> 16) & 255u];
-        c[3] = coef_s[m >> 24];
+        if constexpr (std::is_same<CT, float2>::value) {
+            const float2 a0 = coef_s[m & 255u], a1 = coef_s[(m >> 8) & 255u];
+            const float2 a2 = coef_s[(m >> 16) & 255u], a3 = coef_s[m >> 24];
+            c[0] = make_float4(a0.x, a0.y, a0.y, 0.f);
+            c[1] = make_float4(a1.x, a1.y, a1.y, 0.f);
+            c[2] = make_float4(a2.x, a2.y, a2.y, 0.f);
+            c[3] = make_float4(a3.x, a3.y, a3.y, 0.f);
+        } else {
+            c[0] = coef_s[m & 255u];
+            c[1] = coef_s[(m >> 8) & 255u];
+            c[2] = coef_s[(m >> 16) & 255u];
+            c[3] = coef_s[m >> 24];
+        }
         if constexpr (GEN) {
             if (dsg) {
                 const int dj = row - dsg_j0;
@@ -512,7 +523,8 @@ __device__ __forceinline__ void adj_task(const TmzDev* __restrict__ S, const Tas
     await_<0>();
 }
 
-template <int T, bool GEN, bool PMLV, bool DSGV = true>
+// SQ (interior tasks of square-cell scenes): the table staged as (Ca, Cb/dx)
+template <int T, bool GEN, bool PMLV, bool DSGV = true, bool SQ = false>
 __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 : (GEN ? 3 : 2)) k_adj(const TmzDev* __restrict__ scenes,
                                                           const Task* __restrict__ tasks, int n_tasks,
                                                           const Sample2* __restrict__ srcs, int parity,
@@ -520,19 +532,24 @@ __global__ void __launch_bounds__((GEN && !PMLV) ? 128 : 256, (GEN && PMLV) ? 1 
     constexpr bool PV = GEN && PMLV;
     constexpr int Q = a_stages(T, PV);
     constexpr int SF4 = a_stage_f4(GEN, PV);
+    using CT = typename std::conditional<SQ, float2, float4>::type;
     extern __shared__ float4 smem_f4[];
-    __shared__ float4 coef_s[256];
+    __shared__ CT coef_s[256];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int warps = blockDim.x >> 5;
     const int tid = blockIdx.x * warps + wib;
     const TmzDev* S = scenes + tasks[blockIdx.x * warps].scene;
-    for (int k = threadIdx.x; k < 256; k += blockDim.x) coef_s[k] = S->coef[k];
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) {
+        const float4 c = S->coef[k];
+        if constexpr (SQ) coef_s[k] = make_float2(c.x, c.y);
+        else coef_s[k] = c;
+    }
     __syncthreads();
     if (tid >= n_tasks) return;
     const Task tk = tasks[tid];
     if (tk.scene < 0) return;
-    adj_task<T, GEN, PMLV, DSGV>(S, tk, srcs, parity, n_top, coef_s, smem_f4 + (size_t)wib * Q * SF4, lane);
+    adj_task<T, GEN, PMLV, DSGV, 32, CT>(S, tk, srcs, parity, n_top, coef_s, smem_f4 + (size_t)wib * Q * SF4, lane);
 }
 
 // the reverse sweep's CPML tasks without a design in reach, in one launch: the
@@ -572,14 +589,14 @@ __global__ void __launch_bounds__(256, 1) k_adj_cpml_mixed(const TmzDev* __restr
     }
 }
 
-template <int T, bool GEN, bool PMLV, bool DSGV = true>
+template <int T, bool GEN, bool PMLV, bool DSGV = true, bool SQ = false>
 cudaError_t launch_adj_v(const TmzDev* dev, const Task* tasks, int n, int warps, const Sample2* srcs, int parity,
                          long long n_top, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const size_t sm = adj_smem(T, warps, GEN, GEN && PMLV);
-    cudaError_t e = ensure_dyn_smem((const void*)k_adj<T, GEN, PMLV, DSGV>, sm);
+    cudaError_t e = ensure_dyn_smem((const void*)k_adj<T, GEN, PMLV, DSGV, SQ>, sm);
     if (e != cudaSuccess) return e;
-    k_adj<T, GEN, PMLV, DSGV><<<n / warps, warps * 32, sm, st>>>(dev, tasks, n, srcs, parity, n_top);
+    k_adj<T, GEN, PMLV, DSGV, SQ><<<n / warps, warps * 32, sm, st>>>(dev, tasks, n, srcs, parity, n_top);
     return cudaGetLastError();
 }
 
@@ -587,6 +604,7 @@ struct AdjLists {
     const Task *t0, *t1, *t2, *t3;   // interior, CPML without a design in reach, lite, CPML with one
     const Task* tn;                  // narrow x-slab CPML tasks (32 / NG_LANES per warp)
     int n0, n1, n2, n3, nn, w0, w1, w2;
+    int sq;                          // every scene has square cells: interior tasks stage (Ca, Cb/dx)
 };
 
 template <int T>
@@ -608,7 +626,9 @@ cudaError_t launch_adj_T(const TmzDev* dev, const AdjLists& L, const Sample2* sr
                              : launch_adj_v<T, true, true, false>(dev, L.t1, L.n1, L.w1, srcs, parity, n_top, s1);
     if (e == cudaSuccess) e = launch_adj_v<T, true, true>(dev, L.t3, L.n3, L.w1, srcs, parity, n_top, s1);
     if (e == cudaSuccess) e = launch_adj_v<T, true, false>(dev, L.t2, L.n2, L.w2, srcs, parity, n_top, s2);
-    if (e == cudaSuccess) e = launch_adj_v<T, false, false>(dev, L.t0, L.n0, L.w0, srcs, parity, n_top, s0);
+    if (e == cudaSuccess)
+        e = L.sq ? launch_adj_v<T, false, false, true, true>(dev, L.t0, L.n0, L.w0, srcs, parity, n_top, s0)
+                 : launch_adj_v<T, false, false>(dev, L.t0, L.n0, L.w0, srcs, parity, n_top, s0);
     return e;
 }
 
@@ -1174,6 +1194,8 @@ static int reverse_run(fdtd_ctx* c, const float* dLdF_re, const float* dLdF_im, 
         // variants run on their own streams beside the interior one
         AdjLists L;
         L.t0 = d_t; L.n0 = (int)tasks.size(); L.w0 = warps;
+        L.sq = 1;
+        for (const Scene2* s : c->s2) L.sq = L.sq && s->dx == s->dy;
         L.t1 = d_tg; L.n1 = (int)tasks_g.size(); L.w1 = gwarps;
         L.t2 = d_tl; L.n2 = (int)tasks_l.size(); L.w2 = lwarps;
         L.t3 = d_tgd; L.n3 = (int)tasks_gd.size();
