@@ -23,3 +23,22 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["config"]["workload"].startswith("tmz2d_4096x4096")
+
+
+def test_traffic_record_matches_options_and_source():
+    """roofline.traffic comes from the committed ncu record whose kernel options
+    equal the run's, and only while k_tmz.cu is the file it was taken with."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import hashlib
+    rec = json.load(open(os.path.join(ROOT, "profiles", "k_tmz_fused_traffic.json")))
+    r = rec["records"][0]
+    opts = {k: r["options"][k] for k in bench.TRAFFIC_KEYS}
+    src = os.path.join(ROOT, "paper_2405_00814_gb300", "csrc", "k_tmz.cu")
+    current = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == rec["source_sha256_16"]
+    assert bench._traffic_record(opts) == (r["dram_bytes_per_block"] if current else None)
+    assert 0.95 < r["dram_bytes_per_block"] / rec["algorithmic_bytes_per_block"] < 1.2
+    other = dict(opts, segment=opts["segment"] + 1)
+    assert bench._traffic_record(other) is None
+    for x in rec["records"]:
+        assert len(x["blocks"]) == 2 and "ncu" in x["command"] and "--clock-control none" in x["command"]
