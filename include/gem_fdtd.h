@@ -122,22 +122,23 @@ extern "C" {
                                 segments of half the FDTD_OPT_SEGMENT height; the interior list then runs
                                 its CTAs tallest first (on the GPU, CTAs start in launch order), so the short
                                 tasks fill the SMs the tall ones leave at the end of a T-step block.  0 (default)
-                                = uniform segments in space order.  Results do not depend on it */
+                                = uniform segments in space order.  Results agree to FP32 rounding (other task
+                                bounds move a few rows between the interior and the general kernels) */
 #define FDTD_OPT_WARPS_B 11  /* 2D, kernels 0 and 2: warps per CTA of the CPML kernels of the forward step, 1..8
                                 (default 2).  A CPML CTA holds 7 staged rows of 7 arrays per warp and about 220
                                 registers per thread, so it leaves room for fewer interior CTAs on its SM; wider
-                                CPML CTAs put the CPML warps on fewer SMs.  Results do not depend on it */
+                                CPML CTAs put the CPML warps on fewer SMs.  Results agree to FP32 rounding */
 #define FDTD_OPT_PLAYOUT 12  /* 2D, kernel 2 (T 2..4, not in edge-weight mode): the persistent launch's CTAs.
                                 0 (default) = one 12-warp CTA per SM, 8 interior warps at 128 registers and 4
                                 general warps at 248; k >= 1 = one 16-warp CTA per SM, the first k (at most all
                                 but one) running general and narrow items on 8 warps at 232 registers, every
-                                other CTA 16 interior warps at 128.  Results do not depend on it */
+                                other CTA 16 interior warps at 128.  Results agree to FP32 rounding */
 #define FDTD_OPT_BULK 13     /* 2D, kernel 0: 1 = the interior kernel brings each row in with cp.async.bulk
                                 copies (the TMA engine; one lane per row: Ez, Hx, Hy and the material window,
                                 completing on a per-stage mbarrier) instead of 16-byte cp.async per lane; used
                                 where every interior task's field rows start on 16 bytes.  Each mbarrier wait is
                                 bounded by FDTD_OPT_SPIN_LIMIT polls, after which fdtd_sync reports
-                                FDTD_ETIMEOUT.  0 (default) = cp.async.  Results do not depend on it */
+                                FDTD_ETIMEOUT.  0 (default) = cp.async.  Results are bit-identical */
 
 typedef struct fdtd_ctx fdtd_ctx;
 
